@@ -1,0 +1,221 @@
+"""ctypes front end of the plain C FP64 oracle (lmood_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the benchmark's
+CPU-baseline / reference leg. The product path (the CUDA library and its binding) never
+imports this package, and this package imports nothing from the product path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lmood_oracle.c")
+_LIB = os.path.join(_HERE, "liblmood_oracle.so")
+
+F_X, F_VP, F_VSTAR, F_V, F_E, F_F, F_TAU, F_ORDER, F_MASS, F_PKM, F_PKR = range(11)
+ERR = {0: "ok", 1: "bad argument", 2: "bad mesh", 5: "parachute failure", 6: "MOOD iteration limit"}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with plain gcc (-O2, no FP contraction, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [("cfl", C.c_double), ("Cv", C.c_double), ("Ci", C.c_double),
+                ("delta0", C.c_double), ("delta1", C.c_double), ("dt_fixed", C.c_double),
+                ("max_mood_iters", C.c_int), ("order", C.c_int), ("mood", C.c_int),
+                ("vol_coeff", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt_used", C.c_double), ("dt_next", C.c_double),
+                ("step", C.c_long), ("n_troubled", C.c_int), ("n_p0", C.c_int),
+                ("mood_iters", C.c_int), ("n_parachute", C.c_int), ("n_p0_eps", C.c_int),
+                ("mass", C.c_double),
+                ("mom", C.c_double * 3), ("energy", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+        ip = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+        L = _lib
+        L.orc_mesh_new.argtypes = [C.c_int, C.c_long, dp, C.c_long, ip, C.c_long, C.c_void_p,
+                                   C.c_void_p, C.POINTER(C.c_void_p)]
+        L.orc_mesh_free.argtypes = [C.c_void_p]
+        L.orc_state_new.argtypes = [C.c_void_p, C.c_double, C.c_double, dp, dp, C.c_void_p,
+                                    C.POINTER(Params), C.POINTER(C.c_void_p)]
+        L.orc_state_free.argtypes = [C.c_void_p]
+        L.orc_step.argtypes = [C.c_void_p, C.POINTER(Info)]
+        L.orc_get.argtypes = [C.c_void_p, C.c_int, dp]
+        L.orc_get_dt.argtypes = [C.c_void_p]
+        L.orc_get_dt.restype = C.c_double
+        L.orc_get_t.argtypes = [C.c_void_p]
+        L.orc_get_t.restype = C.c_double
+        L.orc_set_state.argtypes = [C.c_void_p] + [C.c_void_p] * 5 + [C.c_double]
+        L.orc_cell_geometry.argtypes = [C.c_int, dp, dp, dp, dp, dp, dp]
+        L.orc_stress.argtypes = [C.c_int, dp, C.c_double, C.c_double, dp]
+        L.orc_free_energy.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double]
+        L.orc_free_energy.restype = C.c_double
+        L.orc_sound_speed.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double]
+        L.orc_sound_speed.restype = C.c_double
+        L.orc_mesh_stencil.argtypes = [C.c_void_p, C.c_long, np.ctypeslib.ndpointer(np.int64), C.c_long]
+        L.orc_mesh_stencil.restype = C.c_long
+        L.orc_mesh_bc_ndof.argtypes = [C.c_void_p, C.c_long]
+        L.orc_mesh_bc_ndof.restype = C.c_int
+    return _lib
+
+
+def default_params(cfl=0.4, **kw) -> Params:
+    p = Params(cfl=cfl, Cv=0.2, Ci=0.1, delta0=1e-4, delta1=1e-3, dt_fixed=0.0,
+               max_mood_iters=32, order=2, mood=1, vol_coeff=0)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+# ----------------------------------------------------------------------------- unit functions
+def cell_geometry(xs: np.ndarray):
+    """xs [d+1, d] -> (V, xc[d], N[d+1,d] outward face area vectors, ln[d+1,d], Lc)."""
+    xs = np.ascontiguousarray(xs, dtype=np.float64)
+    nv, d = xs.shape
+    V, xc, N, ln, Lc = np.zeros(1), np.zeros(d), np.zeros(nv * d), np.zeros(nv * d), np.zeros(1)
+    lib().orc_cell_geometry(d, xs.ravel(), V, xc, N, ln, Lc)
+    return V[0], xc, N.reshape(nv, d), ln.reshape(nv, d), Lc[0]
+
+
+def stress(F: np.ndarray, mu: float, kappa: float) -> np.ndarray:
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    d = F.shape[0]
+    T = np.zeros(d * d)
+    lib().orc_stress(d, F.ravel(), mu, kappa, T)
+    return T.reshape(d, d)
+
+
+def free_energy(F, rho0, mu, kappa) -> float:
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    return lib().orc_free_energy(F.shape[0], F.ravel(), rho0, mu, kappa)
+
+
+def sound_speed(F, rho, mu, kappa) -> float:
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    return lib().orc_sound_speed(F.shape[0], F.ravel(), rho, mu, kappa)
+
+
+# ----------------------------------------------------------------------------- step driver
+class OracleError(RuntimeError):
+    pass
+
+
+@dataclass
+class _Handles:
+    mesh: C.c_void_p
+    state: C.c_void_p
+
+
+class Oracle:
+    """One mesh + state advanced by the oracle. Arrays are SoA like the library's ABI."""
+
+    def __init__(self, problem, params: Params | None = None, **kw):
+        L = lib()
+        m = problem.mesh
+        self.d = m.dim
+        self.nc, self.np = m.n_cells, m.n_nodes
+        self.params = params or default_params(problem.cfl, **kw)
+        x = np.ascontiguousarray(m.x, dtype=np.float64)
+        c2n = np.ascontiguousarray(m.c2n, dtype=np.int32)
+        bf = np.ascontiguousarray(m.bface, dtype=np.int32)
+        bt = np.ascontiguousarray(m.btag, dtype=np.int32)
+        self._keep = (bf, bt)
+        hm = C.c_void_p()
+        rc = L.orc_mesh_new(self.d, self.np, x.ravel(), self.nc, c2n.ravel(), bt.size,
+                            bf.ctypes.data if bt.size else None, bt.ctypes.data if bt.size else None,
+                            C.byref(hm))
+        if rc:
+            raise OracleError(f"orc_mesh_new: {ERR.get(rc, rc)}")
+        hs = C.c_void_p()
+        mu = np.ascontiguousarray(problem.mu, dtype=np.float64)
+        v = np.ascontiguousarray(problem.v, dtype=np.float64)
+        F = None if problem.F is None else np.ascontiguousarray(problem.F, dtype=np.float64)
+        rc = L.orc_state_new(hm, problem.rho0, problem.lam, mu, v.ravel(),
+                             None if F is None else F.ctypes.data, C.byref(self.params), C.byref(hs))
+        if rc:
+            L.orc_mesh_free(hm)
+            raise OracleError(f"orc_state_new: {ERR.get(rc, rc)}")
+        self._h = _Handles(hm, hs)
+        self.info = Info()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().orc_state_free(self._h.state)
+            lib().orc_mesh_free(self._h.mesh)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def step(self, n: int = 1, check: bool = True) -> int:
+        rc = 0
+        for _ in range(n):
+            rc = lib().orc_step(self._h.state, C.byref(self.info))
+            if rc:
+                if check:
+                    raise OracleError(f"orc_step: {ERR.get(rc, rc)}")
+                break
+        return rc
+
+    def get(self, field: int) -> np.ndarray:
+        d, nc, np_, nv = self.d, self.nc, self.np, self.d + 1
+        shape = {F_X: (d, np_), F_VP: (d, np_), F_VSTAR: (d, np_), F_V: (d, nc), F_E: (nc,),
+                 F_F: (d * d, nc), F_TAU: (nc,), F_ORDER: (nc,), F_MASS: (nc,),
+                 F_PKM: (d * d, nv, nc), F_PKR: (d, nv, nc)}[field]
+        out = np.zeros(int(np.prod(shape)))
+        lib().orc_get(self._h.state, field, out)
+        return out.reshape(shape)
+
+    def set_state(self, x=None, vp=None, v=None, e=None, F=None, dt=0.0):
+        keep = []
+
+        def ptr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            return a.ctypes.data
+        lib().orc_set_state(self._h.state, ptr(x), ptr(vp), ptr(v), ptr(e), ptr(F), float(dt))
+
+    @property
+    def dt(self) -> float:
+        return lib().orc_get_dt(self._h.state)
+
+    @property
+    def t(self) -> float:
+        return lib().orc_get_t(self._h.state)
+
+    def stencil(self, c: int) -> np.ndarray:
+        buf = np.zeros(4096, dtype=np.int64)
+        n = lib().orc_mesh_stencil(self._h.mesh, c, buf, buf.size)
+        return buf[:n].copy()
+
+    def bc_ndof(self, p: int) -> int:
+        return lib().orc_mesh_bc_ndof(self._h.mesh, p)
+
+    def state(self) -> dict:
+        return {"x": self.get(F_X), "vp": self.get(F_VP), "v": self.get(F_V), "e": self.get(F_E),
+                "F": self.get(F_F), "tau": self.get(F_TAU)}

@@ -1,0 +1,1020 @@
+/*
+ * lmood_oracle.c -- plain, slow, FP64 CPU reference of one explicit time step of the
+ * cell-centered Lagrangian ADER-MOOD scheme for neo-Hookean hyper-elasticity
+ * (Boscheri, Loubere, Maire, arXiv 2104.02139) on triangle (d=2) and tetrahedral (d=3)
+ * meshes.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the oracle that the CUDA library is checked
+ * against. Only the test-suite, the smoke check and the CPU-baseline leg of the benchmark
+ * may load it. It shares no code, header, table or helper with the CUDA path.
+ *
+ * Style: one function per passage of the paper, in the paper's order and notation,
+ * plain loops, arrays of structures, no fusion, sums in a fixed order (ascending cell id
+ * around a node), compiled with -ffp-contract=off. Per-entity loops carry an OpenMP
+ * pragma; every iteration writes only its own entity, so the result does not depend on
+ * the thread count.
+ *
+ * Readings of passages that are garbled, ambiguous or deferred to another paper (each is
+ * also listed in the design notes):
+ *  R1  the state stores the deformation gradient F (d x d; 2D is plane strain, F33 = 1);
+ *      B = F F^t. The Crank-Nicolson update of B (Eq. CN_B) is applied to F:
+ *      (I - dt/2 L^{n+1}) F^{n+1} = (I + dt/2 L^n) F^n, with the dt/2 on the left that the
+ *      printed second line drops.
+ *  R2  L_c is the velocity gradient with L_ij = dv_i/dx_j, i.e. (1/|w_c|) sum_p v_p (x) l n
+ *      (the transpose of the printed ln (x) v_p, which is what dF/dt = L F needs).
+ *  R3  volumetric coefficient: Psi_v = kappa/(4 rho0) ((J-1)^2 + (log J)^2) with
+ *      kappa = lambda + 2 mu / 3 (small-strain bulk modulus), so the scheme reduces to
+ *      Lame (lambda, mu) linear elasticity at small strain; vol_coeff = 1 selects the
+ *      printed kappa = mu (Eq. EOS_neoHook).
+ *  R4  sound speed a^2 = (K(J) + 4 mu / (3 J)) / rho with K = -J dp/dJ; z_c = rho_c a_c at t^n.
+ *  R5  M_cp = z_c sum_{f in F(c) cap F(p)} l_cpf n_cpf (x) n_cpf (the printed extra sum over
+ *      C(p) in Eq. Mcp is dropped); l_cpf n_cpf = (1/d) x outward area vector of face f.
+ *  R6  the stress term of Eq. nodal_solver^n is summed over C(p); x^{n+1} = x^n + dt v*_p.
+ *  R7  tau^{n+1} = |w_c(x^{n+1})| / m_c: the GCL-exact form of Eq. tau_c^n (equal to
+ *      tau^n + dt/m sum (ln)(x^{n+1/2}) . v*_p in 2D).
+ *  R8  ADER predictor (details are deferred to another paper): cell-local second-order
+ *      Cauchy-Kowalevski step on the P1 reconstruction with frozen geometry:
+ *      v*_cp = v_h(x_p) + dt/2 (1/m_c) sum_q T(F_h(x_q)) (ln)_cq,
+ *      F*_cp = F_h(x_p) + dt/2 L^_c F_c with L^_c the reconstructed velocity gradient,
+ *      T*_cp = T(F*_cp). First-order (P0) cells use v*_cp = v_c^n, T*_cp = T(F_c^n).
+ *  R9  reconstruction: unweighted least squares about cell centroids over the stencil V_c =
+ *      all cells sharing a node with c (the "Voronoi neighbours" of Sect. "Algorithm"; the
+ *      same set bounds the RDMP), for v and F only; a near-singular normal matrix gives
+ *      zero slopes. Face neighbours alone give an observed order near 1.3 on irregular
+ *      meshes, below the table of Sect. "2D swinging plate"; this stencil gives about 2.
+ *  R10 v_p^n is stored per node; v_p^{n+1} = 2 v*_p - v_p^n; v_p^0 is the first-order
+ *      nodal solution at t^0.
+ *  R11 MOOD: two-level cascade P1 -> P0. Troubled cells become P0; the step is recomputed
+ *      from t^n with the new order mask (neighbours keep their order but see the new node
+ *      velocities); repeat until no new troubled cell. A P0 candidate that cannot be
+ *      advanced further (non-finite value, tau <= 0 or det F <= 0) is a parachute failure;
+ *      a P0 candidate whose only defect is eps < 0 is accepted and counted (eps does not
+ *      enter the stress of this model).
+ *  R12 PAD: finite values, tau > 0, det F > 0, eps = e - |v|^2/2 >= -1e-10 max(|e|, |v|^2/2);
+ *      theta is not modelled. RDMP on rho over V_c and c at t^n, delta0 absolute.
+ *  R13 dt^{n+1} = min(C_CFL min L_c/a_c, C_v dt^n min V^n/|V^{n+1}-V^n|, (1+C_i) dt^n),
+ *      evaluated on the accepted state; dt^0 is the acoustic bound.
+ *  R14 BCs: per node, clamped > slip > free; k independent slip planes leave the
+ *      intersection subspace; the node velocity is the Galerkin solution of
+ *      M_p v_p = b_p on that subspace (Eq. sBC1).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MAXD 3
+#define MAXV 4
+
+enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_MESH = 2, ORC_ERR_PARACHUTE = 5, ORC_ERR_MOOD_ITERS = 6 };
+
+typedef struct {
+    double cfl, Cv, Ci, delta0, delta1, dt_fixed;
+    int max_mood_iters; /* MOOD iterations allowed per step                          */
+    int order;          /* 2: P1 with MOOD cascade to P0; 1: first order everywhere  */
+    int mood;           /* 1: detection on; 0: unlimited (no detection)              */
+    int vol_coeff;      /* 0: kappa = lambda + 2 mu / 3; 1: kappa = mu (printed)      */
+} OrcParams;
+
+typedef struct {
+    double t, dt_used, dt_next;
+    long step;
+    int n_troubled, n_p0, mood_iters, n_parachute, n_p0_eps;
+    double mass, mom[3], energy;
+} OrcInfo;
+
+typedef struct {
+    int d, nv;
+    long np, nc;
+    int *c2n;              /* [nc][nv]                                                */
+    long *n2c_off;         /* [np+1]                                                  */
+    long *n2c_cell;        /* corners around a node, ascending cell id                */
+    int *n2c_k;            /* local vertex index of the node in that cell             */
+    long *st_off, *st_idx; /* reconstruction stencil V_c                              */
+    int *bc_ndof;          /* per node: number of free velocity directions (d = free) */
+    double *bc_t;          /* per node: [2][3] tangent vectors spanning the free space */
+    double *x0;            /* [np][d] initial positions                                */
+} OrcMesh;
+
+typedef struct {
+    OrcMesh *M;
+    OrcParams prm;
+    double rho0, lam;
+    double *mu;                   /* [nc]                                         */
+    double *m;                    /* [nc] constant cell masses                    */
+    double *x, *vp;               /* [np][d] positions and v_p^n                  */
+    double *v, *e, *F, *tau;      /* [nc][d], [nc], [nc][d*d], [nc]               */
+    double t, dt;
+    long step;
+    /* last accepted step's intermediates (for kernel-level parity) */
+    int *order;                   /* [nc] 1 or 2                                  */
+    double *pkM, *pkR;            /* [nc][nv][d*d], [nc][nv][d]                   */
+    double *vstar;                /* [np][d]                                      */
+    OrcInfo last;
+} OrcState;
+
+/* --------------------------------------------------------------------------------------
+ * small dense algebra
+ * ------------------------------------------------------------------------------------ */
+static double det_n(int d, const double *A) {
+    if (d == 2) return A[0] * A[3] - A[1] * A[2];
+    return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+           A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+/* inverse by adjugate / determinant; returns the determinant */
+static double inv_n(int d, const double *A, double *Ai) {
+    double det = det_n(d, A);
+    if (d == 2) {
+        Ai[0] = A[3] / det; Ai[1] = -A[1] / det;
+        Ai[2] = -A[2] / det; Ai[3] = A[0] / det;
+    } else {
+        Ai[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+        Ai[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+        Ai[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+        Ai[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+        Ai[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+        Ai[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+        Ai[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+        Ai[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+        Ai[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+    }
+    return det;
+}
+
+static void matmul_n(int d, const double *A, const double *B, double *C) {
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += A[i * d + k] * B[k * d + j];
+            C[i * d + j] = s;
+        }
+}
+
+static void matvec_n(int d, const double *A, const double *x, double *y) {
+    for (int i = 0; i < d; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += A[i * d + k] * x[k];
+        y[i] = s;
+    }
+}
+
+/* --------------------------------------------------------------------------------------
+ * Geometry of one simplex (Sect. "Mesh and notation", Eq. def_lcpncp).
+ *   xs[k][d]   vertex positions, positively oriented
+ *   V          measure |w_c|
+ *   xc         centroid (vertex average)
+ *   N[k][d]    outward area vector of the face opposite vertex k
+ *   ln[k][d]   corner vector l_cp n_cp = sum over faces f containing p of l_cpf n_cpf,
+ *              with l_cpf n_cpf = N_f / d (each face is split evenly among its d vertices)
+ *   Lc         in-sphere diameter 2 d |w_c| / sum_f |N_f|
+ * ------------------------------------------------------------------------------------ */
+void orc_cell_geometry(int d, const double *xs, double *V, double *xc, double *N, double *ln, double *Lc) {
+    int nv = d + 1;
+    for (int a = 0; a < d; ++a) {
+        double s = 0.0;
+        for (int k = 0; k < nv; ++k) s += xs[k * d + a];
+        xc[a] = s / nv;
+    }
+    if (d == 2) {
+        double e1x = xs[2] - xs[0], e1y = xs[3] - xs[1];
+        double e2x = xs[4] - xs[0], e2y = xs[5] - xs[1];
+        *V = 0.5 * (e1x * e2y - e1y * e2x);
+        for (int k = 0; k < 3; ++k) {
+            /* face opposite k is the edge a -> b traversed counter-clockwise */
+            int a = (k + 1) % 3, b = (k + 2) % 3;
+            N[k * 2 + 0] = xs[b * 2 + 1] - xs[a * 2 + 1];
+            N[k * 2 + 1] = xs[a * 2 + 0] - xs[b * 2 + 0];
+        }
+    } else {
+        double e[3][3];
+        for (int k = 0; k < 3; ++k)
+            for (int a = 0; a < 3; ++a) e[k][a] = xs[(k + 1) * 3 + a] - xs[a];
+        double cr[3] = {e[1][1] * e[2][2] - e[1][2] * e[2][1], e[1][2] * e[2][0] - e[1][0] * e[2][2],
+                        e[1][0] * e[2][1] - e[1][1] * e[2][0]};
+        *V = (e[0][0] * cr[0] + e[0][1] * cr[1] + e[0][2] * cr[2]) / 6.0;
+        for (int k = 0; k < 4; ++k) {
+            int f[3], q = 0;
+            for (int j = 0; j < 4; ++j)
+                if (j != k) f[q++] = j;
+            double u[3], w[3], n[3];
+            for (int a = 0; a < 3; ++a) {
+                u[a] = xs[f[1] * 3 + a] - xs[f[0] * 3 + a];
+                w[a] = xs[f[2] * 3 + a] - xs[f[0] * 3 + a];
+            }
+            n[0] = 0.5 * (u[1] * w[2] - u[2] * w[1]);
+            n[1] = 0.5 * (u[2] * w[0] - u[0] * w[2]);
+            n[2] = 0.5 * (u[0] * w[1] - u[1] * w[0]);
+            /* outward: away from the opposite vertex k */
+            double s = 0.0;
+            for (int a = 0; a < 3; ++a) s += n[a] * (xs[k * 3 + a] - xs[f[0] * 3 + a]);
+            if (s > 0)
+                for (int a = 0; a < 3; ++a) n[a] = -n[a];
+            for (int a = 0; a < 3; ++a) N[k * 3 + a] = n[a];
+        }
+    }
+    double area = 0.0;
+    for (int k = 0; k < nv; ++k) {
+        double s = 0.0;
+        for (int a = 0; a < d; ++a) s += N[k * d + a] * N[k * d + a];
+        area += sqrt(s);
+    }
+    *Lc = 2.0 * d * (*V) / area;
+    for (int p = 0; p < nv; ++p)
+        for (int a = 0; a < d; ++a) {
+            double s = 0.0;
+            for (int f = 0; f < nv; ++f)
+                if (f != p) s += N[f * d + a] / d;
+            ln[p * d + a] = s;
+        }
+}
+
+/* --------------------------------------------------------------------------------------
+ * Constitutive law (Sect. "Volumetric shear strain decomposition", "Examples of
+ * constitutive laws"): T = -p I + T_0 with
+ *   p   = -(kappa/2) (J - 1 + log J / J)                 (Eq. EOS_neoHook, reading R3)
+ *   T_0 = (mu / J) dev(Bbar),  Bbar = J^{-2/3} F F^t     (Eq. cstnh)
+ * 2D is plane strain: F is embedded as diag(F, 1) and the in-plane block of T returned.
+ * ------------------------------------------------------------------------------------ */
+static void embed3(int d, const double *F, double *F3) {
+    if (d == 3) {
+        memcpy(F3, F, 9 * sizeof(double));
+        return;
+    }
+    F3[0] = F[0]; F3[1] = F[1]; F3[2] = 0.0;
+    F3[3] = F[2]; F3[4] = F[3]; F3[5] = 0.0;
+    F3[6] = 0.0;  F3[7] = 0.0;  F3[8] = 1.0;
+}
+
+void orc_stress(int d, const double *F, double mu, double kappa, double *T) {
+    double F3[9], B[9], T3[9];
+    embed3(d, F, F3);
+    double J = det_n(3, F3);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += F3[i * 3 + k] * F3[j * 3 + k];
+            B[i * 3 + j] = s;
+        }
+    double Jm23 = pow(J, -2.0 / 3.0);
+    double trBbar = Jm23 * (B[0] + B[4] + B[8]);
+    double p = -0.5 * kappa * (J - 1.0 + log(J) / J);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double Bbar0 = Jm23 * B[i * 3 + j] - (i == j ? trBbar / 3.0 : 0.0);
+            T3[i * 3 + j] = (i == j ? -p : 0.0) + mu / J * Bbar0;
+        }
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) T[i * d + j] = T3[i * 3 + j];
+}
+
+/* specific free energy Psi = Psi_v + Psi_s (Eqs. EOS_neoHook and familiy_energies with
+ * a = -1): Psi_v = kappa/(4 rho0) ((J-1)^2 + log^2 J), Psi_s = mu/(2 rho0) (I1(Bbar) - 3) */
+double orc_free_energy(int d, const double *F, double rho0, double mu, double kappa) {
+    double F3[9];
+    embed3(d, F, F3);
+    double J = det_n(3, F3);
+    double trB = 0.0;
+    for (int i = 0; i < 9; ++i) trB += F3[i] * F3[i];
+    double I1bar = pow(J, -2.0 / 3.0) * trB;
+    double lj = log(J);
+    return kappa / (4.0 * rho0) * ((J - 1.0) * (J - 1.0) + lj * lj) + mu / (2.0 * rho0) * (I1bar - 3.0);
+}
+
+/* sound speed, reading R4: a^2 = (K + 4 mu / (3 J)) / rho, K = (kappa/2)(J + (1 - log J)/J) */
+double orc_sound_speed(int d, const double *F, double rho, double mu, double kappa) {
+    double F3[9];
+    embed3(d, F, F3);
+    double J = det_n(3, F3);
+    double K = 0.5 * kappa * (J + (1.0 - log(J)) / J);
+    return sqrt((K + 4.0 * mu / (3.0 * J)) / rho);
+}
+
+static double kappa_of(const OrcState *S, long c) {
+    return S->prm.vol_coeff == 1 ? S->mu[c] : S->lam + 2.0 * S->mu[c] / 3.0;
+}
+
+/* --------------------------------------------------------------------------------------
+ * Mesh set-up: corners around nodes, face neighbours, stencils, BC resolution
+ * ------------------------------------------------------------------------------------ */
+static int cmp_long(const void *a, const void *b) {
+    long x = *(const long *)a, y = *(const long *)b;
+    return (x > y) - (x < y);
+}
+
+void orc_mesh_free(OrcMesh *M) {
+    if (!M) return;
+    free(M->c2n); free(M->n2c_off); free(M->n2c_cell); free(M->n2c_k);
+    free(M->st_off); free(M->st_idx); free(M->bc_ndof); free(M->bc_t); free(M->x0);
+    free(M);
+}
+
+/* x_soa [d][np], c2n_soa [d+1][nc], bf_soa [d][nb], btag [nb] (0 free, 1 slip, 2 clamped) */
+int orc_mesh_new(int d, long np, const double *x_soa, long nc, const int *c2n_soa, long nb,
+                 const int *bf_soa, const int *btag, OrcMesh **out) {
+    if ((d != 2 && d != 3) || np <= 0 || nc <= 0 || !out) return ORC_ERR_ARG;
+    OrcMesh *M = calloc(1, sizeof(OrcMesh));
+    int nv = d + 1;
+    M->d = d; M->nv = nv; M->np = np; M->nc = nc;
+    M->c2n = malloc(sizeof(int) * nc * nv);
+    M->x0 = malloc(sizeof(double) * np * d);
+    for (long p = 0; p < np; ++p)
+        for (int a = 0; a < d; ++a) M->x0[p * d + a] = x_soa[a * np + p];
+    for (long c = 0; c < nc; ++c)
+        for (int k = 0; k < nv; ++k) {
+            int p = c2n_soa[k * nc + c];
+            if (p < 0 || p >= np) { orc_mesh_free(M); return ORC_ERR_MESH; }
+            M->c2n[c * nv + k] = p;
+        }
+    /* positive orientation */
+    for (long c = 0; c < nc; ++c) {
+        double xs[MAXV * MAXD], V, xc[MAXD], N[MAXV * MAXD], ln[MAXV * MAXD], Lc;
+        for (int k = 0; k < nv; ++k)
+            for (int a = 0; a < d; ++a) xs[k * d + a] = M->x0[M->c2n[c * nv + k] * d + a];
+        orc_cell_geometry(d, xs, &V, xc, N, ln, &Lc);
+        if (!(V > 0)) { orc_mesh_free(M); return ORC_ERR_MESH; }
+    }
+    /* C(p): corners around each node, ascending cell id */
+    M->n2c_off = calloc(np + 1, sizeof(long));
+    for (long c = 0; c < nc; ++c)
+        for (int k = 0; k < nv; ++k) M->n2c_off[M->c2n[c * nv + k] + 1]++;
+    for (long p = 0; p < np; ++p) M->n2c_off[p + 1] += M->n2c_off[p];
+    M->n2c_cell = malloc(sizeof(long) * nc * nv);
+    M->n2c_k = malloc(sizeof(int) * nc * nv);
+    long *fill = malloc(sizeof(long) * np);
+    for (long p = 0; p < np; ++p) fill[p] = M->n2c_off[p];
+    for (long c = 0; c < nc; ++c)
+        for (int k = 0; k < nv; ++k) {
+            int p = M->c2n[c * nv + k];
+            M->n2c_cell[fill[p]] = c;
+            M->n2c_k[fill[p]] = k;
+            fill[p]++;
+        }
+    free(fill);
+    /* stencil V_c (reading R9): every other cell sharing at least one node with c,
+     * ascending cell id */
+    M->st_off = calloc(nc + 1, sizeof(long));
+    long cap = nc * 16, used = 0;
+    M->st_idx = malloc(sizeof(long) * cap);
+    long *tmp = malloc(sizeof(long) * 8192);
+    for (long c = 0; c < nc; ++c) {
+        int n = 0;
+        for (int k = 0; k < nv; ++k) {
+            int p = M->c2n[c * nv + k];
+            for (long j = M->n2c_off[p]; j < M->n2c_off[p + 1]; ++j)
+                if (M->n2c_cell[j] != c && n < 8192) tmp[n++] = M->n2c_cell[j];
+        }
+        qsort(tmp, n, sizeof(long), cmp_long);
+        int u = 0;
+        for (int i = 0; i < n; ++i)
+            if (u == 0 || tmp[i] != tmp[u - 1]) tmp[u++] = tmp[i];
+        if (used + u > cap) {
+            cap = 2 * (used + u);
+            M->st_idx = realloc(M->st_idx, sizeof(long) * cap);
+        }
+        memcpy(M->st_idx + used, tmp, sizeof(long) * u);
+        used += u;
+        M->st_off[c + 1] = used;
+    }
+    free(tmp);
+    /* boundary conditions (Appendix B; hierarchy clamped > slip > free, reading R14) */
+    M->bc_ndof = malloc(sizeof(int) * np);
+    M->bc_t = calloc(np * 6, sizeof(double));
+    int *clamped = calloc(np, sizeof(int));
+    int *nplanes = calloc(np, sizeof(int));
+    double *planes = calloc(np * 9, sizeof(double));
+    for (long b = 0; b < nb; ++b) {
+        int fn[MAXD];
+        for (int a = 0; a < d; ++a) {
+            fn[a] = bf_soa[a * nb + b];
+            if (fn[a] < 0 || fn[a] >= np) { free(clamped); free(nplanes); free(planes); orc_mesh_free(M); return ORC_ERR_MESH; }
+        }
+        double n[3] = {0, 0, 0};
+        if (d == 2) {
+            n[0] = M->x0[fn[1] * 2 + 1] - M->x0[fn[0] * 2 + 1];
+            n[1] = M->x0[fn[0] * 2 + 0] - M->x0[fn[1] * 2 + 0];
+        } else {
+            double u[3], w[3];
+            for (int a = 0; a < 3; ++a) {
+                u[a] = M->x0[fn[1] * 3 + a] - M->x0[fn[0] * 3 + a];
+                w[a] = M->x0[fn[2] * 3 + a] - M->x0[fn[0] * 3 + a];
+            }
+            n[0] = u[1] * w[2] - u[2] * w[1];
+            n[1] = u[2] * w[0] - u[0] * w[2];
+            n[2] = u[0] * w[1] - u[1] * w[0];
+        }
+        double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int a = 0; a < 3; ++a) n[a] /= nn;
+        for (int a = 0; a < d; ++a) {
+            int p = fn[a];
+            if (btag[b] == 2) clamped[p] = 1;
+            if (btag[b] == 1) {
+                int dup = 0;
+                for (int q = 0; q < nplanes[p]; ++q) {
+                    double dot = 0.0;
+                    for (int i = 0; i < 3; ++i) dot += planes[p * 9 + q * 3 + i] * n[i];
+                    if (fabs(dot) > 1.0 - 1e-12) dup = 1;
+                }
+                if (!dup && nplanes[p] < 3) {
+                    for (int i = 0; i < 3; ++i) planes[p * 9 + nplanes[p] * 3 + i] = n[i];
+                    nplanes[p]++;
+                }
+            }
+        }
+    }
+    for (long p = 0; p < np; ++p) {
+        double *t = M->bc_t + p * 6;
+        const double *n1 = planes + p * 9, *n2 = planes + p * 9 + 3;
+        int k = clamped[p] ? d : nplanes[p];
+        if (k >= d) {
+            M->bc_ndof[p] = 0;
+        } else if (k == 0) {
+            M->bc_ndof[p] = d;
+        } else if (d == 2) {
+            M->bc_ndof[p] = 1;
+            t[0] = -n1[1]; t[1] = n1[0];
+        } else if (k == 1) {
+            /* tangent basis of the plane: t1 = e x n normalised (e = axis least aligned with n), t2 = n x t1 */
+            int ax = 0;
+            for (int a = 1; a < 3; ++a)
+                if (fabs(n1[a]) < fabs(n1[ax])) ax = a;
+            double e[3] = {0, 0, 0};
+            e[ax] = 1.0;
+            double t1[3] = {e[1] * n1[2] - e[2] * n1[1], e[2] * n1[0] - e[0] * n1[2], e[0] * n1[1] - e[1] * n1[0]};
+            double l1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+            for (int a = 0; a < 3; ++a) t1[a] /= l1;
+            double t2[3] = {n1[1] * t1[2] - n1[2] * t1[1], n1[2] * t1[0] - n1[0] * t1[2], n1[0] * t1[1] - n1[1] * t1[0]};
+            double l2 = sqrt(t2[0] * t2[0] + t2[1] * t2[1] + t2[2] * t2[2]);
+            for (int a = 0; a < 3; ++a) { t[a] = t1[a]; t[3 + a] = t2[a] / l2; }
+            M->bc_ndof[p] = 2;
+        } else {
+            double l[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2], n1[0] * n2[1] - n1[1] * n2[0]};
+            double ll = sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+            for (int a = 0; a < 3; ++a) t[a] = l[a] / ll;
+            M->bc_ndof[p] = 1;
+        }
+    }
+    free(clamped); free(nplanes); free(planes);
+    *out = M;
+    return ORC_OK;
+}
+
+/* --------------------------------------------------------------------------------------
+ * The step
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    /* geometry at x^n */
+    double *V, *xc, *ln, *N, *Lc;
+    /* slopes */
+    double *gv, *gF;
+    /* packets */
+    double *pkM, *pkR;
+    /* nodes */
+    double *vs, *x1, *vp1;
+    /* candidate */
+    double *v1, *e1, *F1, *V1;
+} Work;
+
+static Work work_new(const OrcMesh *M) {
+    int d = M->d, nv = M->nv;
+    long nc = M->nc, np = M->np;
+    Work w;
+    w.V = malloc(sizeof(double) * nc);
+    w.xc = malloc(sizeof(double) * nc * d);
+    w.ln = malloc(sizeof(double) * nc * nv * d);
+    w.N = malloc(sizeof(double) * nc * nv * d);
+    w.Lc = malloc(sizeof(double) * nc);
+    w.gv = malloc(sizeof(double) * nc * d * d);
+    w.gF = malloc(sizeof(double) * nc * d * d * d);
+    w.pkM = malloc(sizeof(double) * nc * nv * d * d);
+    w.pkR = malloc(sizeof(double) * nc * nv * d);
+    w.vs = malloc(sizeof(double) * np * d);
+    w.x1 = malloc(sizeof(double) * np * d);
+    w.vp1 = malloc(sizeof(double) * np * d);
+    w.v1 = malloc(sizeof(double) * nc * d);
+    w.e1 = malloc(sizeof(double) * nc);
+    w.F1 = malloc(sizeof(double) * nc * d * d);
+    w.V1 = malloc(sizeof(double) * nc);
+    return w;
+}
+
+static void work_free(Work *w) {
+    free(w->V); free(w->xc); free(w->ln); free(w->N); free(w->Lc); free(w->gv); free(w->gF);
+    free(w->pkM); free(w->pkR); free(w->vs); free(w->x1); free(w->vp1); free(w->v1); free(w->e1);
+    free(w->F1); free(w->V1);
+}
+
+static void gather_xs(const OrcMesh *M, const double *x, long c, double *xs) {
+    for (int k = 0; k < M->nv; ++k)
+        for (int a = 0; a < M->d; ++a) xs[k * M->d + a] = x[M->c2n[c * M->nv + k] * M->d + a];
+}
+
+/* 1. geometry of every cell at x^n */
+static void phase_geometry(const OrcState *S, const double *x, Work *w) {
+    const OrcMesh *M = S->M;
+    int d = M->d, nv = M->nv;
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < M->nc; ++c) {
+        double xs[MAXV * MAXD];
+        gather_xs(M, x, c, xs);
+        orc_cell_geometry(d, xs, &w->V[c], &w->xc[c * d], &w->N[c * nv * d], &w->ln[c * nv * d], &w->Lc[c]);
+    }
+}
+
+/* 2. piecewise-linear reconstruction of v and F by unweighted least squares (reading R9):
+ *    G = sum_k dx_k dx_k^t, slope = G^{-1} sum_k dx_k (q_k - q_c), dx_k = x_k - x_c */
+static void phase_slopes(const OrcState *S, const int *order, Work *w) {
+    const OrcMesh *M = S->M;
+    int d = M->d, nq = d + d * d;
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < M->nc; ++c) {
+        double *gv = w->gv + c * d * d, *gF = w->gF + c * d * d * d;
+        memset(gv, 0, sizeof(double) * d * d);
+        memset(gF, 0, sizeof(double) * d * d * d);
+        if (order[c] != 2) continue;
+        double G[9] = {0}, r[12][3];
+        memset(r, 0, sizeof(r));
+        for (long j = M->st_off[c]; j < M->st_off[c + 1]; ++j) {
+            long o = M->st_idx[j];
+            double dx[3], dq[12];
+            for (int a = 0; a < d; ++a) dx[a] = w->xc[o * d + a] - w->xc[c * d + a];
+            for (int i = 0; i < d; ++i) dq[i] = S->v[o * d + i] - S->v[c * d + i];
+            for (int i = 0; i < d * d; ++i) dq[d + i] = S->F[o * d * d + i] - S->F[c * d * d + i];
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) G[a * d + b] += dx[a] * dx[b];
+            for (int q = 0; q < nq; ++q)
+                for (int a = 0; a < d; ++a) r[q][a] += dx[a] * dq[q];
+        }
+        double tr = 0.0;
+        for (int a = 0; a < d; ++a) tr += G[a * d + a];
+        double det = det_n(d, G);
+        if (!(det > 1e-12 * pow(tr / d, d))) continue; /* degenerate stencil: first order slopes */
+        double Gi[9];
+        inv_n(d, G, Gi);
+        for (int q = 0; q < nq; ++q) {
+            double g[3];
+            matvec_n(d, Gi, r[q], g);
+            double *dst = q < d ? gv + q * d : gF + (q - d) * d;
+            for (int a = 0; a < d; ++a) dst[a] = g[a];
+        }
+    }
+}
+
+/* 3. predictor and corner packets (Sect. "Space-Time discretization --- ADER methodology",
+ *    reading R8; Eqs. Mcp^n, nodal_solver^n):
+ *    M_cp   = z_c sum_{f containing p} |l n|_cpf n_cpf (x) n_cpf
+ *    rhs_cp = M_cp v*_cp - T*_cp (l n)_cp         so that f_cp = M_cp v*_p - rhs_cp */
+static void phase_packets(const OrcState *S, const int *order, double dt, Work *w) {
+    const OrcMesh *M = S->M;
+    int d = M->d, nv = M->nv, dd = d * d;
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < M->nc; ++c) {
+        const double *ln = w->ln + c * nv * d, *N = w->N + c * nv * d;
+        const double *vc = S->v + c * d, *Fc = S->F + c * dd;
+        double kap = kappa_of(S, c);
+        double rho = S->m[c] / w->V[c];
+        double z = rho * orc_sound_speed(d, Fc, rho, S->mu[c], kap);
+        double vstar[MAXV][MAXD], Tstar[MAXV][9];
+        if (order[c] == 2) {
+            const double *gv = w->gv + c * dd, *gF = w->gF + c * dd * d;
+            double vh[MAXV][MAXD], Fh[MAXV][9], dvdt[MAXD] = {0, 0, 0}, dFdt[9];
+            for (int k = 0; k < nv; ++k) {
+                int p = M->c2n[c * nv + k];
+                double dx[3];
+                for (int a = 0; a < d; ++a) dx[a] = S->x[p * d + a] - w->xc[c * d + a];
+                for (int i = 0; i < d; ++i) {
+                    double s = vc[i];
+                    for (int a = 0; a < d; ++a) s += gv[i * d + a] * dx[a];
+                    vh[k][i] = s;
+                }
+                for (int i = 0; i < dd; ++i) {
+                    double s = Fc[i];
+                    for (int a = 0; a < d; ++a) s += gF[i * d + a] * dx[a];
+                    Fh[k][i] = s;
+                }
+                double Tk[9], Tn[3];
+                orc_stress(d, Fh[k], S->mu[c], kap, Tk);
+                matvec_n(d, Tk, ln + k * d, Tn);
+                for (int i = 0; i < d; ++i) dvdt[i] += Tn[i];
+            }
+            for (int i = 0; i < d; ++i) dvdt[i] /= S->m[c];
+            matmul_n(d, gv, Fc, dFdt); /* dF/dt = L^ F (Eq. GCLL) with L^ the reconstructed gradient */
+            for (int k = 0; k < nv; ++k) {
+                double Fs[9];
+                for (int i = 0; i < d; ++i) vstar[k][i] = vh[k][i] + 0.5 * dt * dvdt[i];
+                for (int i = 0; i < dd; ++i) Fs[i] = Fh[k][i] + 0.5 * dt * dFdt[i];
+                orc_stress(d, Fs, S->mu[c], kap, Tstar[k]);
+            }
+        } else {
+            double T0[9];
+            orc_stress(d, Fc, S->mu[c], kap, T0);
+            for (int k = 0; k < nv; ++k) {
+                for (int i = 0; i < d; ++i) vstar[k][i] = vc[i];
+                memcpy(Tstar[k], T0, sizeof(double) * dd);
+            }
+        }
+        for (int k = 0; k < nv; ++k) {
+            double *Mk = w->pkM + (c * nv + k) * dd, *Rk = w->pkR + (c * nv + k) * d;
+            memset(Mk, 0, sizeof(double) * dd);
+            for (int f = 0; f < nv; ++f) {
+                if (f == k) continue;
+                double lnf[3], l = 0.0;
+                for (int a = 0; a < d; ++a) { lnf[a] = N[f * d + a] / d; l += lnf[a] * lnf[a]; }
+                l = sqrt(l);
+                for (int a = 0; a < d; ++a)
+                    for (int b = 0; b < d; ++b) Mk[a * d + b] += z * lnf[a] * lnf[b] / l;
+            }
+            double Mv[3], Tn[3];
+            matvec_n(d, Mk, vstar[k], Mv);
+            matvec_n(d, Tstar[k], ln + k * d, Tn);
+            for (int i = 0; i < d; ++i) Rk[i] = Mv[i] - Tn[i];
+        }
+    }
+}
+
+/* 4. nodal solver with BCs (Eqs. nodal_solver^n, sBC1; readings R6, R10, R14):
+ *    M_p = sum_c M_cp, b_p = sum_c rhs_cp, v*_p = Galerkin solution on the free subspace,
+ *    x^{n+1} = x^n + dt v*_p, v_p^{n+1} = 2 v*_p - v_p^n */
+static void node_solve_one(const OrcMesh *M, const double *pkM, const double *pkR, long p, double *vs) {
+    int d = M->d, nv = M->nv, dd = d * d;
+    double Mp[9] = {0}, bp[3] = {0, 0, 0};
+    for (long j = M->n2c_off[p]; j < M->n2c_off[p + 1]; ++j) {
+        long c = M->n2c_cell[j];
+        int k = M->n2c_k[j];
+        for (int i = 0; i < dd; ++i) Mp[i] += pkM[(c * nv + k) * dd + i];
+        for (int i = 0; i < d; ++i) bp[i] += pkR[(c * nv + k) * d + i];
+    }
+    int nf = M->bc_ndof[p];
+    if (nf == d) {
+        double Mi[9];
+        inv_n(d, Mp, Mi);
+        matvec_n(d, Mi, bp, vs);
+    } else if (nf == 0) {
+        for (int i = 0; i < d; ++i) vs[i] = 0.0;
+    } else {
+        const double *t = M->bc_t + p * 6;
+        double A[4], r[2], al[2];
+        for (int i = 0; i < nf; ++i) {
+            r[i] = 0.0;
+            for (int a = 0; a < d; ++a) r[i] += t[3 * i + a] * bp[a];
+            for (int j = 0; j < nf; ++j) {
+                double Mtj[3], s = 0.0;
+                matvec_n(d, Mp, t + 3 * j, Mtj);
+                for (int a = 0; a < d; ++a) s += t[3 * i + a] * Mtj[a];
+                A[i * nf + j] = s;
+            }
+        }
+        if (nf == 1) {
+            al[0] = r[0] / A[0];
+        } else {
+            double Ai[4];
+            inv_n(2, A, Ai);
+            al[0] = Ai[0] * r[0] + Ai[1] * r[1];
+            al[1] = Ai[2] * r[0] + Ai[3] * r[1];
+        }
+        for (int a = 0; a < d; ++a) {
+            double s = 0.0;
+            for (int i = 0; i < nf; ++i) s += al[i] * t[3 * i + a];
+            vs[a] = s;
+        }
+    }
+}
+
+static void phase_nodes(const OrcState *S, double dt, Work *w) {
+    const OrcMesh *M = S->M;
+    int d = M->d;
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < M->np; ++p) {
+        node_solve_one(M, w->pkM, w->pkR, p, w->vs + p * d);
+        for (int a = 0; a < d; ++a) {
+            w->x1[p * d + a] = S->x[p * d + a] + dt * w->vs[p * d + a];
+            w->vp1[p * d + a] = 2.0 * w->vs[p * d + a] - S->vp[p * d + a];
+        }
+    }
+}
+
+/* velocity gradient of a cell from node velocities (Eq. div_grad_v, reading R2) */
+static void vel_gradient(int d, int nv, const double *ln, double V, const double *vnodes, double *L) {
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < nv; ++k) s += vnodes[k * d + i] * ln[k * d + j];
+            L[i * d + j] = s / V;
+        }
+}
+
+/* 5. subcell forces and cell update (Eqs. subforce^n, tau_c^n, v_c^n, e_c^n, firstB, CN_B;
+ *    readings R1, R7) */
+static void phase_update(const OrcState *S, const int *order, double dt, Work *w) {
+    const OrcMesh *M = S->M;
+    int d = M->d, nv = M->nv, dd = d * d;
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < M->nc; ++c) {
+        double sf[3] = {0, 0, 0}, sfv = 0.0;
+        double vsn[MAXV * MAXD], vpn[MAXV * MAXD], vp1n[MAXV * MAXD];
+        for (int k = 0; k < nv; ++k) {
+            int p = M->c2n[c * nv + k];
+            const double *Mk = w->pkM + (c * nv + k) * dd, *Rk = w->pkR + (c * nv + k) * d;
+            double f[3];
+            matvec_n(d, Mk, w->vs + p * d, f);
+            for (int i = 0; i < d; ++i) f[i] -= Rk[i];
+            for (int i = 0; i < d; ++i) {
+                sf[i] += f[i];
+                sfv += f[i] * w->vs[p * d + i];
+            }
+            for (int a = 0; a < d; ++a) {
+                vsn[k * d + a] = w->vs[p * d + a];
+                vpn[k * d + a] = S->vp[p * d + a];
+                vp1n[k * d + a] = w->vp1[p * d + a];
+            }
+        }
+        double m = S->m[c];
+        for (int i = 0; i < d; ++i) w->v1[c * d + i] = S->v[c * d + i] + dt / m * sf[i];
+        w->e1[c] = S->e[c] + dt / m * sfv;
+        /* volume at x^{n+1} */
+        double xs[MAXV * MAXD], V1, xc1[MAXD], N1[MAXV * MAXD], ln1[MAXV * MAXD], Lc1;
+        gather_xs(M, w->x1, c, xs);
+        orc_cell_geometry(d, xs, &V1, xc1, N1, ln1, &Lc1);
+        w->V1[c] = V1;
+        const double *Fn = S->F + c * dd;
+        double *F1 = w->F1 + c * dd;
+        if (order[c] == 2) {
+            /* Crank-Nicolson: (I - dt/2 L^{n+1}) F^{n+1} = (I + dt/2 L^n) F^n */
+            double L0[9], L1[9], A[9], Bm[9], Ai[9], R[9];
+            vel_gradient(d, nv, w->ln + c * nv * d, w->V[c], vpn, L0);
+            vel_gradient(d, nv, ln1, V1, vp1n, L1);
+            for (int i = 0; i < d; ++i)
+                for (int j = 0; j < d; ++j) {
+                    double id = i == j ? 1.0 : 0.0;
+                    A[i * d + j] = id - 0.5 * dt * L1[i * d + j];
+                    Bm[i * d + j] = id + 0.5 * dt * L0[i * d + j];
+                }
+            matmul_n(d, Bm, Fn, R);
+            inv_n(d, A, Ai);
+            matmul_n(d, Ai, R, F1);
+        } else {
+            /* first order: F^{n+1} = F^n + dt L* F^n, L* from v*_p on the x^n geometry */
+            double Ls[9], LF[9];
+            vel_gradient(d, nv, w->ln + c * nv * d, w->V[c], vsn, Ls);
+            matmul_n(d, Ls, Fn, LF);
+            for (int i = 0; i < dd; ++i) F1[i] = Fn[i] + dt * LF[i];
+        }
+    }
+}
+
+/* 6. detection (Eqs. PAD and RDMP; reading R12).
+ * pad_state: 0 admissible; 1 only eps < -tol; 2 not computable (non-finite, tau <= 0, det F <= 0) */
+static int pad_state(int d, const double *v, double e, const double *F, double V) {
+    int dd = d * d;
+    if (!isfinite(e) || !isfinite(V)) return 2;
+    for (int i = 0; i < d; ++i)
+        if (!isfinite(v[i])) return 2;
+    for (int i = 0; i < dd; ++i)
+        if (!isfinite(F[i])) return 2;
+    if (!(V > 0.0)) return 2;
+    if (!(det_n(d, F) > 0.0)) return 2;
+    double ke = 0.0;
+    for (int i = 0; i < d; ++i) ke += 0.5 * v[i] * v[i];
+    double eps = e - ke;
+    double tol = 1e-10 * fmax(fabs(e), ke);
+    return eps >= -tol ? 0 : 1;
+}
+
+static int rdmp_ok(const OrcState *S, const Work *w, long c) {
+    const OrcMesh *M = S->M;
+    double lo = S->m[c] / w->V[c], hi = lo;
+    for (long j = M->st_off[c]; j < M->st_off[c + 1]; ++j) {
+        long o = M->st_idx[j];
+        double r = S->m[o] / w->V[o];
+        lo = fmin(lo, r);
+        hi = fmax(hi, r);
+    }
+    double delta = fmax(S->prm.delta0, S->prm.delta1 * (hi - lo));
+    double r1 = S->m[c] / w->V1[c];
+    return r1 >= lo - delta && r1 <= hi + delta;
+}
+
+static void candidate(const OrcState *S, const int *order, double dt, Work *w) {
+    phase_geometry(S, S->x, w);
+    phase_slopes(S, order, w);
+    phase_packets(S, order, dt, w);
+    phase_nodes(S, dt, w);
+    phase_update(S, order, dt, w);
+}
+
+/* 7. time step (Eqs. CFL, CFL2; reading R13) */
+static double dt_acoustic_cell(const OrcState *S, long c, const double *F, double V, double Lc) {
+    double rho = S->m[c] / V;
+    return S->prm.cfl * Lc / orc_sound_speed(S->M->d, F, rho, S->mu[c], kappa_of(S, c));
+}
+
+static void totals(const OrcState *S, OrcInfo *info) {
+    int d = S->M->d;
+    info->mass = 0; info->energy = 0;
+    info->mom[0] = info->mom[1] = info->mom[2] = 0;
+    for (long c = 0; c < S->M->nc; ++c) {
+        info->mass += S->m[c];
+        info->energy += S->m[c] * S->e[c];
+        for (int i = 0; i < d; ++i) info->mom[i] += S->m[c] * S->v[c * d + i];
+    }
+}
+
+int orc_step(OrcState *S, OrcInfo *info) {
+    const OrcMesh *M = S->M;
+    int d = M->d, dd = d * d, nv = M->nv;
+    long nc = M->nc;
+    double dt = S->dt;
+    Work w = work_new(M);
+    int *order = S->order;
+    for (long c = 0; c < nc; ++c) order[c] = S->prm.order == 1 ? 1 : 2;
+    int iters = 0, n_troubled = 0, n_para = 0, n_eps = 0, status = ORC_OK;
+    for (;;) {
+        candidate(S, order, dt, &w);
+        int fresh = 0;
+        n_para = 0;
+        n_eps = 0;
+        if (S->prm.mood) {
+            /* new troubled cells are decided on this candidate before any mask change */
+            int *flag = calloc(nc, sizeof(int));
+#pragma omp parallel for schedule(static) reduction(+ : fresh, n_para, n_eps)
+            for (long c = 0; c < nc; ++c) {
+                int ps = pad_state(d, w.v1 + c * d, w.e1[c], w.F1 + c * dd, w.V1[c]);
+                if (order[c] == 2) {
+                    if (ps != 0 || !rdmp_ok(S, &w, c)) { flag[c] = 1; fresh++; }
+                } else if (ps == 2) {
+                    n_para++;
+                } else if (ps == 1) {
+                    n_eps++;
+                }
+            }
+            for (long c = 0; c < nc; ++c)
+                if (flag[c]) order[c] = 1;
+            free(flag);
+        }
+        if (fresh == 0) break;
+        n_troubled += fresh;
+        if (++iters > S->prm.max_mood_iters) { status = ORC_ERR_MOOD_ITERS; break; }
+    }
+    if (status == ORC_OK && n_para > 0) status = ORC_ERR_PARACHUTE;
+    if (status == ORC_OK) {
+        /* accept the candidate */
+        double dtn = S->prm.dt_fixed > 0 ? S->prm.dt_fixed : (1.0 + S->prm.Ci) * dt;
+        if (!(S->prm.dt_fixed > 0)) {
+            for (long c = 0; c < nc; ++c) {
+                double xs[MAXV * MAXD], V1, xc1[MAXD], N1[MAXV * MAXD], ln1[MAXV * MAXD], Lc1;
+                gather_xs(M, w.x1, c, xs);
+                orc_cell_geometry(d, xs, &V1, xc1, N1, ln1, &Lc1);
+                double dtc = dt_acoustic_cell(S, c, w.F1 + c * dd, V1, Lc1);
+                double dV = V1 - w.V[c];
+                if (dV != 0.0) dtc = fmin(dtc, S->prm.Cv * dt * w.V[c] / fabs(dV));
+                dtn = fmin(dtn, dtc);
+            }
+        }
+        memcpy(S->x, w.x1, sizeof(double) * M->np * d);
+        memcpy(S->vp, w.vp1, sizeof(double) * M->np * d);
+        memcpy(S->v, w.v1, sizeof(double) * nc * d);
+        memcpy(S->e, w.e1, sizeof(double) * nc);
+        memcpy(S->F, w.F1, sizeof(double) * nc * dd);
+        for (long c = 0; c < nc; ++c) S->tau[c] = w.V1[c] / S->m[c];
+        memcpy(S->pkM, w.pkM, sizeof(double) * nc * nv * dd);
+        memcpy(S->pkR, w.pkR, sizeof(double) * nc * nv * d);
+        memcpy(S->vstar, w.vs, sizeof(double) * M->np * d);
+        S->t += dt;
+        S->step += 1;
+        S->last.dt_used = dt;
+        S->dt = dtn;
+    }
+    int np0 = 0;
+    for (long c = 0; c < nc; ++c) np0 += order[c] == 1;
+    S->last.t = S->t;
+    S->last.dt_next = S->dt;
+    S->last.step = S->step;
+    S->last.n_troubled = n_troubled;
+    S->last.n_p0 = np0;
+    S->last.mood_iters = iters;
+    S->last.n_parachute = n_para;
+    S->last.n_p0_eps = n_eps;
+    totals(S, &S->last);
+    if (info) *info = S->last;
+    work_free(&w);
+    return status;
+}
+
+/* --------------------------------------------------------------------------------------
+ * State initialisation (Sect. "2D and 3D test problems"): m_c = rho0 |w_c(x^0)|,
+ * e = |v|^2/2 + Psi(F), v_p^0 = first-order nodal solution, dt^0 = acoustic bound.
+ * ------------------------------------------------------------------------------------ */
+void orc_state_free(OrcState *S) {
+    if (!S) return;
+    free(S->mu); free(S->m); free(S->x); free(S->vp); free(S->v); free(S->e); free(S->F);
+    free(S->tau); free(S->order); free(S->pkM); free(S->pkR); free(S->vstar);
+    free(S);
+}
+
+int orc_state_new(OrcMesh *M, double rho0, double lam, const double *mu_cell, const double *v_soa,
+                  const double *F_soa, const OrcParams *prm, OrcState **out) {
+    if (!M || !prm || !mu_cell || !v_soa || !out) return ORC_ERR_ARG;
+    int d = M->d, nv = M->nv, dd = d * d;
+    long nc = M->nc, np = M->np;
+    OrcState *S = calloc(1, sizeof(OrcState));
+    S->M = M; S->prm = *prm; S->rho0 = rho0; S->lam = lam;
+    S->mu = malloc(sizeof(double) * nc);
+    S->m = malloc(sizeof(double) * nc);
+    S->x = malloc(sizeof(double) * np * d);
+    S->vp = calloc(np * d, sizeof(double));
+    S->v = malloc(sizeof(double) * nc * d);
+    S->e = malloc(sizeof(double) * nc);
+    S->F = malloc(sizeof(double) * nc * dd);
+    S->tau = malloc(sizeof(double) * nc);
+    S->order = malloc(sizeof(int) * nc);
+    S->pkM = calloc(nc * nv * dd, sizeof(double));
+    S->pkR = calloc(nc * nv * d, sizeof(double));
+    S->vstar = calloc(np * d, sizeof(double));
+    memcpy(S->x, M->x0, sizeof(double) * np * d);
+    for (long c = 0; c < nc; ++c) {
+        S->mu[c] = mu_cell[c];
+        for (int i = 0; i < d; ++i) S->v[c * d + i] = v_soa[i * nc + c];
+        for (int i = 0; i < dd; ++i) S->F[c * dd + i] = F_soa ? F_soa[i * nc + c] : ((i % (d + 1)) == 0 ? 1.0 : 0.0);
+        S->order[c] = 1;
+    }
+    Work w = work_new(M);
+    phase_geometry(S, S->x, &w);
+    double dt0 = INFINITY;
+    for (long c = 0; c < nc; ++c) {
+        S->m[c] = rho0 * w.V[c];
+        S->tau[c] = w.V[c] / S->m[c];
+        double ke = 0.0;
+        for (int i = 0; i < d; ++i) ke += 0.5 * S->v[c * d + i] * S->v[c * d + i];
+        S->e[c] = ke + orc_free_energy(d, S->F + c * dd, rho0, S->mu[c], kappa_of(S, c));
+        dt0 = fmin(dt0, dt_acoustic_cell(S, c, S->F + c * dd, w.V[c], w.Lc[c]));
+    }
+    /* v_p^0: first-order nodal solve at t^0 */
+    phase_packets(S, S->order, 0.0, &w);
+    for (long p = 0; p < np; ++p) node_solve_one(M, w.pkM, w.pkR, p, S->vp + p * d);
+    work_free(&w);
+    S->dt = prm->dt_fixed > 0 ? prm->dt_fixed : dt0;
+    S->t = 0.0;
+    S->step = 0;
+    *out = S;
+    return ORC_OK;
+}
+
+/* field ids for orc_get (SoA [ncomp][n] output) */
+enum { F_X = 0, F_VP = 1, F_VSTAR = 2, F_V = 3, F_E = 4, F_F = 5, F_TAU = 6, F_ORDER = 7,
+       F_MASS = 8, F_PKM = 9, F_PKR = 10 };
+
+int orc_get(const OrcState *S, int field, double *dst) {
+    const OrcMesh *M = S->M;
+    int d = M->d, dd = d * d, nv = M->nv;
+    long nc = M->nc, np = M->np;
+    switch (field) {
+    case F_X: for (long p = 0; p < np; ++p) for (int a = 0; a < d; ++a) dst[a * np + p] = S->x[p * d + a]; break;
+    case F_VP: for (long p = 0; p < np; ++p) for (int a = 0; a < d; ++a) dst[a * np + p] = S->vp[p * d + a]; break;
+    case F_VSTAR: for (long p = 0; p < np; ++p) for (int a = 0; a < d; ++a) dst[a * np + p] = S->vstar[p * d + a]; break;
+    case F_V: for (long c = 0; c < nc; ++c) for (int a = 0; a < d; ++a) dst[a * nc + c] = S->v[c * d + a]; break;
+    case F_E: for (long c = 0; c < nc; ++c) dst[c] = S->e[c]; break;
+    case F_F: for (long c = 0; c < nc; ++c) for (int a = 0; a < dd; ++a) dst[a * nc + c] = S->F[c * dd + a]; break;
+    case F_TAU: for (long c = 0; c < nc; ++c) dst[c] = S->tau[c]; break;
+    case F_ORDER: for (long c = 0; c < nc; ++c) dst[c] = S->order[c]; break;
+    case F_MASS: for (long c = 0; c < nc; ++c) dst[c] = S->m[c]; break;
+    /* packets: [comp][k][c] with M as full d x d row-major comps and rhs d comps */
+    case F_PKM:
+        for (long c = 0; c < nc; ++c)
+            for (int k = 0; k < nv; ++k)
+                for (int a = 0; a < dd; ++a) dst[(a * nv + k) * nc + c] = S->pkM[(c * nv + k) * dd + a];
+        break;
+    case F_PKR:
+        for (long c = 0; c < nc; ++c)
+            for (int k = 0; k < nv; ++k)
+                for (int a = 0; a < d; ++a) dst[(a * nv + k) * nc + c] = S->pkR[(c * nv + k) * d + a];
+        break;
+    default: return ORC_ERR_ARG;
+    }
+    return ORC_OK;
+}
+
+double orc_get_dt(const OrcState *S) { return S->dt; }
+double orc_get_t(const OrcState *S) { return S->t; }
+
+/* Set the dynamic state (used to replay a state on both sides): SoA arrays, NULL = keep. */
+int orc_set_state(OrcState *S, const double *x, const double *vp, const double *v, const double *e,
+                  const double *F, double dt) {
+    const OrcMesh *M = S->M;
+    int d = M->d, dd = d * d;
+    long nc = M->nc, np = M->np;
+    if (x) for (long p = 0; p < np; ++p) for (int a = 0; a < d; ++a) S->x[p * d + a] = x[a * np + p];
+    if (vp) for (long p = 0; p < np; ++p) for (int a = 0; a < d; ++a) S->vp[p * d + a] = vp[a * np + p];
+    if (v) for (long c = 0; c < nc; ++c) for (int a = 0; a < d; ++a) S->v[c * d + a] = v[a * nc + c];
+    if (e) for (long c = 0; c < nc; ++c) S->e[c] = e[c];
+    if (F) for (long c = 0; c < nc; ++c) for (int a = 0; a < dd; ++a) S->F[c * dd + a] = F[a * nc + c];
+    if (dt > 0) S->dt = dt;
+    return ORC_OK;
+}
+
+/* Mesh queries used by tests (stencil and BC resolution). */
+long orc_mesh_stencil(const OrcMesh *M, long c, long *dst, long cap) {
+    long n = M->st_off[c + 1] - M->st_off[c];
+    for (long j = 0; j < n && j < cap; ++j) dst[j] = M->st_idx[M->st_off[c] + j];
+    return n;
+}
+int orc_mesh_bc_ndof(const OrcMesh *M, long p) { return M->bc_ndof[p]; }

@@ -1,0 +1,323 @@
+"""Seeded synthetic inputs for the Lagrangian ADER-MOOD step (meshes, initial fields, BC tags).
+
+This module is shared by the CPU oracle and the CUDA path and therefore holds none of the
+scheme's arithmetic: it only places points, connects them into simplices, tags boundary
+faces and evaluates the prescribed initial velocity / shear-modulus fields at the t=0
+vertex average of each cell (the initial data of the problem, cf. the initialisation of the
+test problems in Sect. "2D and 3D test problems").
+
+The paper's meshes come from GMSH (Sect. "2D and 3D test problems") and are not available;
+these generators stand in for them with the same element types and sizes:
+
+* 2D: a jittered n x n point lattice on a rectangle, Delaunay-triangulated (Qhull through
+  scipy), boundary points sliding along their side, corners fixed.
+* 3D: a jittered box lattice split into Kuhn (Freudenthal) tetrahedra, 6 per cube.
+
+Cells and nodes are renumbered along a Morton curve so that mesh neighbours are close in
+memory (the caller orders; the library renumbers nothing).
+
+Boundary-condition tags per boundary face: 0 free traction, 1 slip wall (symmetry plane),
+2 clamped (symmetry point), following Appendix B of the paper.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+FREE, SLIP, CLAMPED = 0, 1, 2
+
+
+@dataclass
+class Mesh:
+    dim: int
+    x: np.ndarray          # [dim, n_nodes] float64 (SoA)
+    c2n: np.ndarray        # [dim+1, n_cells] int32, positively oriented (SoA)
+    bface: np.ndarray      # [dim, n_bfaces] int32 node ids of tagged boundary faces
+    btag: np.ndarray       # [n_bfaces] int32 in {FREE, SLIP, CLAMPED}
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.x.shape[1])
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.c2n.shape[1])
+
+
+@dataclass
+class Problem:
+    """A mesh plus material and initial data: everything the step needs at t=0."""
+    name: str
+    mesh: Mesh
+    rho0: float
+    lam: float
+    mu: np.ndarray          # [n_cells] shear modulus per cell
+    v: np.ndarray           # [dim, n_cells] initial cell velocity
+    cfl: float
+    steps: int
+    F: np.ndarray | None = None   # [dim*dim, n_cells] or None for F = I
+    meta: dict = field(default_factory=dict)
+
+
+# ----------------------------------------------------------------------------- ordering
+def _morton_keys(pts: np.ndarray, bits: int = 20) -> np.ndarray:
+    """Morton (Z-order) key of each point (rows of pts, 2 or 3 columns)."""
+    d = pts.shape[1]
+    lo = pts.min(axis=0)
+    span = np.maximum(pts.max(axis=0) - lo, 1e-300)
+    q = np.floor((pts - lo) / span * ((1 << bits) - 1)).astype(np.uint64)
+    key = np.zeros(pts.shape[0], dtype=np.uint64)
+    for b in range(bits):
+        for a in range(d):
+            key |= ((q[:, a] >> np.uint64(b)) & np.uint64(1)) << np.uint64(b * d + a)
+    return key
+
+
+def _renumber(x_rows: np.ndarray, cells: np.ndarray):
+    """Morton-order nodes and cells. x_rows [np, d], cells [nc, d+1]."""
+    node_perm = np.argsort(_morton_keys(x_rows), kind="stable")
+    inv = np.empty_like(node_perm)
+    inv[node_perm] = np.arange(node_perm.size)
+    x_rows = x_rows[node_perm]
+    cells = inv[cells]
+    cent = x_rows[cells].mean(axis=1)
+    cell_perm = np.argsort(_morton_keys(cent), kind="stable")
+    return x_rows, cells[cell_perm]
+
+
+def _orient(x_rows: np.ndarray, cells: np.ndarray) -> np.ndarray:
+    """Swap two vertices of negatively oriented simplices (pure connectivity fix-up)."""
+    d = x_rows.shape[1]
+    e = x_rows[cells[:, 1:]] - x_rows[cells[:, :1]]
+    s = np.linalg.det(e) if d == 3 else e[:, 0, 0] * e[:, 1, 1] - e[:, 0, 1] * e[:, 1, 0]
+    cells = cells.copy()
+    neg = s < 0
+    cells[neg, 1], cells[neg, 2] = cells[neg, 2].copy(), cells[neg, 1].copy()
+    if np.any(np.abs(s) < 1e-14 * np.abs(s).max()):
+        raise ValueError("degenerate simplex in generated mesh")
+    return cells
+
+
+def _boundary_faces(cells: np.ndarray) -> np.ndarray:
+    """Faces (sorted node tuples) that belong to exactly one simplex."""
+    nv = cells.shape[1]
+    faces = np.concatenate([np.delete(cells, k, axis=1) for k in range(nv)], axis=0)
+    faces = np.sort(faces, axis=1)
+    uniq, cnt = np.unique(faces, axis=0, return_counts=True)
+    return uniq[cnt == 1]
+
+
+def _tag_faces(x_rows: np.ndarray, faces: np.ndarray, lo, hi, bc: dict) -> tuple[np.ndarray, np.ndarray]:
+    """Tag each boundary face by the box side it lies on. bc maps side names
+    ('x0','x1','y0','y1','z0','z1') to FREE/SLIP/CLAMPED (missing = FREE)."""
+    d = x_rows.shape[1]
+    tags = np.full(faces.shape[0], FREE, dtype=np.int32)
+    names = "xyz"
+    fx = x_rows[faces]  # [nb, d, d]
+    for a in range(d):
+        for side, val in ((0, lo[a]), (1, hi[a])):
+            on = np.all(fx[:, :, a] == val, axis=1)
+            tags[on] = bc.get(f"{names[a]}{side}", FREE)
+    keep = tags != FREE
+    return faces[keep].astype(np.int32), tags[keep]
+
+
+# ----------------------------------------------------------------------------- 2D
+def tri_mesh(n: int, seed: int, lx: float = 1.0, ly: float = 1.0, jitter: float = 0.25,
+             bc: dict | None = None) -> Mesh:
+    """Seeded jittered Delaunay triangulation of an n x n lattice on [0,lx]x[0,ly].
+
+    Interior points move by U(-jitter, jitter)*h per axis, side points only along their side,
+    corners stay. 2(n-1)^2 triangles (Euler's formula for a convex point set with 4(n-1)
+    hull points), checked.
+    """
+    from scipy.spatial import Delaunay
+
+    rng = np.random.default_rng(seed)
+    hx, hy = lx / (n - 1), ly / (n - 1)
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    x = i * hx
+    y = j * hy
+    jx = rng.uniform(-jitter, jitter, (n, n)) * hx
+    jy = rng.uniform(-jitter, jitter, (n, n)) * hy
+    jx[0, :] = 0.0
+    jx[-1, :] = 0.0
+    jy[:, 0] = 0.0
+    jy[:, -1] = 0.0
+    x = x + jx
+    y = y + jy
+    x[0, :] = 0.0
+    x[-1, :] = lx
+    y[:, 0] = 0.0
+    y[:, -1] = ly
+    pts = np.stack([x.ravel(), y.ravel()], axis=1)
+    tri = Delaunay(pts)
+    cells = tri.simplices.astype(np.int64)
+    if cells.shape[0] != 2 * (n - 1) ** 2 or len(tri.coplanar):
+        raise ValueError("unexpected triangulation size")
+    cells = _orient(pts, cells)
+    pts, cells = _renumber(pts, cells)
+    faces = _boundary_faces(cells)
+    bf, tags = _tag_faces(pts, faces, (0.0, 0.0), (lx, ly), bc or {})
+    return Mesh(2, np.ascontiguousarray(pts.T), np.ascontiguousarray(cells.T.astype(np.int32)),
+                np.ascontiguousarray(bf.T), tags)
+
+
+# ----------------------------------------------------------------------------- 3D
+def tet_mesh(nx: int, ny: int, nz: int, seed: int, lx: float = 1.0, ly: float = 1.0,
+             lz: float = 1.0, jitter: float = 0.1, bc: dict | None = None) -> Mesh:
+    """Seeded jittered box lattice of nx*ny*nz cubes, each split into 6 Kuhn tetrahedra
+    (all sharing the cube's (0,0,0)-(1,1,1) diagonal, so the split is conforming).
+    Points on a side move only within that side; edge points along the edge; corners stay.
+    """
+    rng = np.random.default_rng(seed)
+    L = np.array([lx, ly, lz])
+    nn = np.array([nx, ny, nz])
+    h = L / nn
+    idx = np.stack(np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1),
+                               indexing="ij"), axis=-1).reshape(-1, 3)
+    pts = idx * h
+    jit = rng.uniform(-jitter, jitter, pts.shape) * h
+    for a in range(3):
+        onb = (idx[:, a] == 0) | (idx[:, a] == nn[a])
+        jit[onb, a] = 0.0
+    pts = pts + jit
+    for a in range(3):
+        pts[idx[:, a] == 0, a] = 0.0
+        pts[idx[:, a] == nn[a], a] = L[a]
+
+    def nid(i, j, k):
+        return (i * (ny + 1) + j) * (nz + 1) + k
+
+    ci, cj, ck = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    tets = []
+    for perm in itertools.permutations(range(3)):
+        path = [np.zeros(3, dtype=np.int64)]
+        for a in perm:
+            nxt = path[-1].copy()
+            nxt[a] = 1
+            path.append(nxt)
+        tets.append(np.stack([nid(ci + p[0], cj + p[1], ck + p[2]) for p in path], axis=1))
+    cells = np.concatenate(tets, axis=0).astype(np.int64)
+    cells = _orient(pts, cells)
+    pts, cells = _renumber(pts, cells)
+    faces = _boundary_faces(cells)
+    bf, tags = _tag_faces(pts, faces, (0.0, 0.0, 0.0), tuple(L), bc or {})
+    return Mesh(3, np.ascontiguousarray(pts.T), np.ascontiguousarray(cells.T.astype(np.int32)),
+                np.ascontiguousarray(bf.T), tags)
+
+
+# ----------------------------------------------------------------------------- fields
+def cell_points(mesh: Mesh) -> np.ndarray:
+    """t=0 vertex average of each cell, [n_cells, dim]: where initial fields are sampled."""
+    return mesh.x.T[mesh.c2n.T].mean(axis=1)
+
+
+def gaussian_random_field(pts: np.ndarray, seed: int, n_modes: int = 64, corr: float = 0.15) -> np.ndarray:
+    """Unit-variance stationary Gaussian random field from random Fourier modes."""
+    rng = np.random.default_rng(seed)
+    d = pts.shape[1]
+    k = rng.normal(0.0, 1.0 / corr, (n_modes, d))
+    ph = rng.uniform(0.0, 2 * math.pi, n_modes)
+    return math.sqrt(2.0 / n_modes) * np.cos(pts @ k.T + ph).sum(axis=1)
+
+
+# ----------------------------------------------------------------------------- named workloads
+def plain2d(n: int = 40, seed: int = 1, steps: int = 200) -> Problem:
+    """Unit square, jittered Delaunay of an n x n lattice, slip walls on all sides;
+    rho0=1, mu=1, lambda=2; v0 = 1e-3 (sin(pi x) sin(pi y), cos(pi x) cos(pi y)); CFL 0.4."""
+    m = tri_mesh(n, seed, bc={"x0": SLIP, "x1": SLIP, "y0": SLIP, "y1": SLIP})
+    p = cell_points(m)
+    v = 1e-3 * np.stack([np.sin(np.pi * p[:, 0]) * np.sin(np.pi * p[:, 1]),
+                         np.cos(np.pi * p[:, 0]) * np.cos(np.pi * p[:, 1])])
+    return Problem(f"plain2d_n{n}", m, 1.0, 2.0, np.full(m.n_cells, 1.0), v, 0.4, steps)
+
+
+def impact2d(n: int = 708, seed: int = 2, steps: int = 2000) -> Problem:
+    """Unit square of jittered Delaunay triangles (n=708 gives 999,698 cells) moving at
+    v = (-0.1, 0) against a rigid slip wall at x = 0, other sides free;
+    rho0=8.93, mu=0.46, lambda=1.06; CFL 0.4."""
+    m = tri_mesh(n, seed, bc={"x0": SLIP})
+    v = np.zeros((2, m.n_cells))
+    v[0] = -0.1
+    return Problem(f"impact2d_n{n}", m, 8.93, 1.06, np.full(m.n_cells, 0.46), v, 0.4, steps)
+
+
+def column3d(nxy: int = 55, nz: int = 330, seed: int = 3, steps: int = 500) -> Problem:
+    """Box [0,1]x[0,1]x[0,6] of Kuhn tetrahedra (55x55x330 cubes give 5,989,500 cells),
+    base z=0 clamped, rest free; rho0=1.1, mu=0.5, lambda=2.5; v = (0.1 (z/6)^2, 0, 0); CFL 0.25."""
+    m = tet_mesh(nxy, nxy, nz, seed, 1.0, 1.0, 6.0, bc={"z0": CLAMPED})
+    p = cell_points(m)
+    v = np.zeros((3, m.n_cells))
+    v[0] = 0.1 * (p[:, 2] / 6.0) ** 2
+    return Problem(f"column3d_{nxy}x{nxy}x{nz}", m, 1.1, 2.5, np.full(m.n_cells, 0.5), v, 0.25, steps)
+
+
+def cube3d(n: int = 44, seed: int = 5, steps: int = 400) -> Problem:
+    """Unit cube of Kuhn tetrahedra (44^3 cubes give 511,104 cells), slip walls; rho0=1,
+    lambda=2; per-cell mu = 1 + 0.2 g(x) with g a seeded unit-variance Gaussian random field
+    (64 Fourier modes, correlation length 0.15); v0 = 0.05 sin(pi x) sin(pi y) sin(pi z) (1,1,1)."""
+    bc = {s: SLIP for s in ("x0", "x1", "y0", "y1", "z0", "z1")}
+    m = tet_mesh(n, n, n, seed, bc=bc)
+    p = cell_points(m)
+    mu = 1.0 + 0.2 * gaussian_random_field(p, seed + 10_000)
+    s = 0.05 * np.sin(np.pi * p[:, 0]) * np.sin(np.pi * p[:, 1]) * np.sin(np.pi * p[:, 2])
+    v = np.stack([s, s, s])
+    return Problem(f"cube3d_n{n}", m, 1.0, 2.0, mu, v, 0.25, steps)
+
+
+def swinging_plate(n: int, jitter: float = 0.0, seed: int = 7, u0: float = 5e-4) -> Problem:
+    """2D swinging plate (Sect. "2D swinging plate", Eq. (SwingIni)): [0,2]^2, slip walls,
+    rho0 = 1100, E = 1.7e7, nu = 0.45, v(x,0) = omega U0 (-sin(pi x/2) cos(pi y/2),
+    cos(pi x/2) sin(pi y/2)), omega = (pi/2) sqrt(2 mu / rho0)."""
+    E, nu, rho0 = 1.7e7, 0.45, 1100.0
+    mu = E / (2 * (1 + nu))
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    omega = 0.5 * math.pi * math.sqrt(2 * mu / rho0)
+    m = tri_mesh(n, seed, 2.0, 2.0, jitter=jitter,
+                 bc={"x0": SLIP, "x1": SLIP, "y0": SLIP, "y1": SLIP})
+    p = cell_points(m)
+    a = omega * u0
+    v = a * np.stack([-np.sin(0.5 * np.pi * p[:, 0]) * np.cos(0.5 * np.pi * p[:, 1]),
+                      np.cos(0.5 * np.pi * p[:, 0]) * np.sin(0.5 * np.pi * p[:, 1])])
+    return Problem(f"swing_n{n}", m, rho0, lam, np.full(m.n_cells, mu), v, 0.4, 0,
+                   meta={"omega": omega, "u0": u0, "t_final": math.pi / omega, "amp": a})
+
+
+def batched2d(n_inst: int = 256, seed: int = 4, lo: float = 1e3, hi: float = 2e5,
+              steps: int = 500) -> list[Problem]:
+    """Independent unit-square instances: cell counts log-uniform in [lo, hi], per-instance
+    mu ~ U[0.5, 2] and velocity amplitude A ~ U[1e-3, 0.2] applied to the plain2d field;
+    lambda=2, rho0=1, slip walls, CFL 0.4. Instance i meshes with seed 1000+i."""
+    rng = np.random.default_rng(seed)
+    ncell = np.exp(rng.uniform(math.log(lo), math.log(hi), n_inst))
+    mus = rng.uniform(0.5, 2.0, n_inst)
+    amps = rng.uniform(1e-3, 0.2, n_inst)
+    out = []
+    for i in range(n_inst):
+        n = int(math.ceil(1 + math.sqrt(ncell[i] / 2)))
+        m = tri_mesh(n, 1000 + i, bc={"x0": SLIP, "x1": SLIP, "y0": SLIP, "y1": SLIP})
+        p = cell_points(m)
+        v = amps[i] * np.stack([np.sin(np.pi * p[:, 0]) * np.sin(np.pi * p[:, 1]),
+                                np.cos(np.pi * p[:, 0]) * np.cos(np.pi * p[:, 1])])
+        out.append(Problem(f"batch{i}_n{n}", m, 1.0, 2.0, np.full(m.n_cells, mus[i]), v, 0.4, steps,
+                           meta={"amp": amps[i]}))
+    return out
+
+
+def translate_rotate(pb: Problem, R: np.ndarray, shift: np.ndarray) -> Problem:
+    """Rigidly move a problem's whole configuration: x -> R x + shift, v -> R v, F -> R F R^T.
+    (An input transformation used by objectivity tests.)"""
+    d = pb.mesh.dim
+    x = R @ pb.mesh.x + shift[:, None]
+    m = Mesh(d, np.ascontiguousarray(x), pb.mesh.c2n, pb.mesh.bface, pb.mesh.btag)
+    v = np.ascontiguousarray(R @ pb.v)
+    F = None
+    if pb.F is not None:
+        Fm = pb.F.T.reshape(-1, d, d)
+        F = np.ascontiguousarray((R @ Fm @ R.T).reshape(-1, d * d).T)
+    return Problem(pb.name + "_rot", m, pb.rho0, pb.lam, pb.mu.copy(), v, pb.cfl, pb.steps, F, dict(pb.meta))
