@@ -1,0 +1,278 @@
+#!/usr/bin/env python
+"""Benchmark: cell-steps/s of the full ADER-MOOD step (FP64) on the 2D impact workload
+(unit square of 999,698 seeded Delaunay triangles, rigid slip wall at x = 0, v = (-0.1, 0)).
+
+One step = one pass of the whole hot path: corner geometry, least-squares reconstruction,
+ADER predictor and corner packets, nodal solver with BCs, forces and cell update, MOOD
+detection and first-order recomputation, next dt. Inputs are resident in HBM before the
+timed region; the working set (~0.5 GB) is larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica on its GPU (the path does not
+shard across GPUs here); value = cell-steps of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/s of full ADER-MOOD step (FP64, 1 GB300)"
+UNIT = "cell-steps/s"
+WORKLOAD = "impact2d: 999,698 triangles (708x708 jittered Delaunay lattice), rho0=8.93 mu=0.46 lambda=1.06, v=(-0.1,0), slip wall x=0, CFL 0.4"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# nominal GB300 FP64 rate: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def kernel_bytes(dim: int, nc: int, npn: int, nnz: int) -> dict:
+    """Algorithmic (compulsory) DRAM bytes per full launch of each kernel class: every array
+    the kernel needs is read once and every output written once (gathers of neighbours'
+    data count once, as the data of the neighbour itself)."""
+    D, NV = dim, dim + 1
+    NS = D * (D + 1) // 2
+    d8 = 8
+    pk = d8 * (NS + D) * NV * nc
+    predict = (4 * NV * nc + d8 * D * npn + d8 * (2 * D + D * D) * nc + 4 * (nc + 1) + 4 * nnz
+               + 2 * d8 * nc + pk + nc)
+    nodes = 4 * (npn + 1) + 4 * NV * nc + pk + npn + 2 * d8 * D * npn + 3 * d8 * D * npn
+    update = (4 * NV * nc + 5 * d8 * D * npn + pk + d8 * (D + 1 + D * D + 2) * nc + nc + d8 * nc
+              + 4 * (nc + 1) + 4 * nnz + d8 * (D + 1 + D * D + D + 2) * nc + d8 * nc)
+    finalize = d8 * nc + 2 * nc
+    return {"predict": predict, "nodes": nodes, "update": update, "finalize": finalize}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(pb, budget_s: float = 12.0) -> dict:
+    """The oracle as it stands on the host cores: the first steps of the same workload."""
+    import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    o = O.Oracle(pb)
+    setup = time.perf_counter() - t0
+    steps, t = 0, 0.0
+    while steps < 2 or (t < budget_s and steps < 50):
+        s0 = time.perf_counter()
+        o.step()
+        t += time.perf_counter() - s0
+        steps += 1
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": pb.mesh.n_cells * steps / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {steps} steps of the same workload ({pb.mesh.n_cells} cells), {t:.1f} s of "
+                      f"stepping after {setup:.1f} s of set-up"}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 0, 1, None
+    import torch
+    import torch.distributed as dist
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    dist.init_process_group(backend=backend)
+    rank, local = dist.get_rank(), int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, local, ws, dist
+
+
+def max_over_ranks(x: float, dist) -> float:
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def run_reference(args, rank, ws, dist):
+    if rank != 0:
+        return
+    import workloads as W
+    pb = W.impact2d()
+    cb = cpu_baseline(pb, budget_s=max(10.0, 2.0 * args.steps / 100))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": pb.mesh.n_cells / cb["value"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "cells": pb.mesh.n_cells},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, local, ws, dist):
+    import torch
+    import paper_2104_02139_gb300 as L
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    L.build()
+    pb = W.impact2d()
+    N = pb.mesh.n_cells
+    stream = torch.cuda.Stream()
+    sim = L.simulation(pb, stream=stream.cuda_stream)
+    info = sim.mesh.info()
+    for _ in range(args.warmup):
+        sim.step()
+    sim.timing(True)
+    clocks = Clocks(local)
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    troubled = 0
+    for _ in range(args.steps):
+        troubled += sim.step().n_troubled
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    kt = sim.timing_read()
+    sim.timing(False)
+    ms_max = max_over_ranks(ms, dist)
+    value = ws * N * args.steps / (ms_max / 1e3)
+
+    # roofline of the dominant kernel class (full-mesh launches; MOOD rounds excluded)
+    peaks, how = _peaks()
+    kb = kernel_bytes(2, N, info["n_nodes"], info["stencil_nnz"])
+    dom = max(("predict", "nodes", "update"), key=lambda k: kt[k][0])
+    dom_ms = kt[dom][0] / max(kt[dom][1], 1)
+    achieved = kb[dom] / (dom_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": how,
+            "algorithmic_bytes_per_launch": kb[dom], "ms_per_launch": dom_ms}
+    kernels = {k: {"ms_total": v[0], "launches": v[1]} for k, v in kt.items()}
+    launches = sum(v[1] for v in kt.values())
+
+    # end to end through the C ABI with host buffers: every step uploads the state from
+    # pinned host memory, steps, and reads the new state back
+    e2e = None
+    if not args.no_e2e:
+        fields = ((L.FIELD_X, (2, info["n_nodes"])), (L.FIELD_VP, (2, info["n_nodes"])), (L.FIELD_V, (2, N)),
+                  (L.FIELD_E, (N,)), (L.FIELD_F, (4, N)), (L.FIELD_DT, (1,)))
+        bufs = {f: torch.empty(shp, dtype=torch.float64, pin_memory=True).numpy() for f, shp in fields}
+        for f, _ in fields:
+            sim.get(f, out=bufs[f])
+        nbytes = sum(b.nbytes for b in bufs.values())
+        k2 = max(5, args.steps // 4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            for f, _ in fields:
+                sim.set(f, bufs[f])
+            sim.step()
+            for f, _ in fields:
+                sim.get(f, out=bufs[f])
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0, dist)
+        e2e = {"value": ws * N * k2 / el, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "steps": k2}
+
+    cb = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(W.impact2d())
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "cells": N, "nodes": info["n_nodes"],
+                           "stencil_entries": info["stencil_nnz"], "parallelism": f"replicas x{ws}",
+                           "l2": "working set > L2 (no flush)", "troubled_cells_in_timed_steps": troubled},
+                "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": ck, "e2e": e2e,
+                "cpu_baseline": cb}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, local, ws, dist = dist_setup()
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, ws, dist)
+        else:
+            run_ours(args, rank, local, ws, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

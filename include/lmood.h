@@ -1,0 +1,197 @@
+/*
+ * lmood.h -- C ABI of the GB300 (sm_103a) library that advances the cell-centered
+ * Lagrangian ADER-MOOD scheme for neo-Hookean hyper-elasticity of Boscheri, Loubere and
+ * Maire (arXiv 2104.02139) on unstructured triangle (dim 2) or tetrahedral (dim 3) meshes,
+ * in FP64.
+ *
+ * Conventions shared by every entry point
+ *  - Arrays are structure-of-arrays: a field with k components over n entities is k
+ *    contiguous runs of n values ("[k][n]").
+ *  - Host input pointers are borrowed for the duration of the call only; the library copies
+ *    what it needs. It owns every device buffer it allocates and frees them in the matching
+ *    destroy call.
+ *  - Nothing is thrown across the ABI. Every call returns an lmood_status; on failure
+ *    lmood_last_error() returns a message (thread-local, valid until the next call on that
+ *    thread). A failed lmood_step leaves the state as it was before the call.
+ *  - All device work of a mesh and its states is ordered on the CUDA stream given to
+ *    lmood_mesh_create (NULL = legacy default stream). Calls that return data to the host
+ *    synchronise that stream.
+ *  - Cells must be positively oriented simplices (counter-clockwise triangles, tetrahedra
+ *    with (x1-x0).((x2-x0)x(x3-x0)) > 0); the library renumbers nothing.
+ */
+#ifndef LMOOD_H
+#define LMOOD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lmood_mesh_s *lmood_mesh;
+typedef struct lmood_state_s *lmood_state;
+
+typedef enum {
+    LMOOD_OK = 0,
+    LMOOD_ERR_ARG = 1,        /* NULL pointer, bad dimension, bad size or field id          */
+    LMOOD_ERR_MESH = 2,       /* node index out of range, non-positive simplex volume       */
+    LMOOD_ERR_CUDA = 3,       /* a CUDA runtime call failed (message names it)               */
+    LMOOD_ERR_OOM = 4,        /* device allocation failed                                    */
+    LMOOD_ERR_PARACHUTE = 5,  /* a first-order (P0) candidate is not computable: non-finite,
+                                 tau <= 0 or det F <= 0 (Sect. "Limiting: a posteriori MOOD
+                                 loop", the parachute scheme); the state is left unchanged   */
+    LMOOD_ERR_MOOD_ITERS = 6, /* troubled cells remain after max_mood_iters iterations      */
+    LMOOD_ERR_TIMEOUT = 7,    /* reserved: a bounded device-side wait gave up                */
+    LMOOD_ERR_STATE = 8       /* the handle is unusable after an earlier CUDA failure        */
+} lmood_status;
+
+/* Material constants (Sect. "Examples of constitutive laws"). The shear modulus mu is given
+ * per cell to lmood_state_init. Volumetric free energy
+ *   Psi_v = kappa / (4 rho0) ((J - 1)^2 + (log J)^2)          (Eq. EOS_neoHook)
+ * with kappa = lambda + 2 mu / 3 when vol_coeff = 0 (small-strain bulk modulus), or
+ * kappa = mu when vol_coeff = 1 (the coefficient as printed). */
+typedef struct {
+    double rho0;     /* initial density (> 0)                 */
+    double lambda;   /* first Lame coefficient                */
+    int32_t vol_coeff;
+    int32_t reserved;
+} lmood_material;
+
+/* Scheme parameters (Sect. "Time-step monitoring", "Limiting: a posteriori MOOD loop"). */
+typedef struct {
+    double cfl;             /* C_CFL: 0.4 in 2D, 0.25 in 3D                               */
+    double Cv;              /* C_v = 0.2: volume-change bound of Eq. CFL2                  */
+    double Ci;              /* C_i = 0.1: dt^{n+1} <= (1 + C_i) dt^n                       */
+    double delta0;          /* 1e-4: absolute RDMP relaxation (Eq. RDMP)                   */
+    double delta1;          /* 1e-3: relative RDMP relaxation                              */
+    double dt_fixed;        /* > 0: use this dt for every step instead of Eq. CFL           */
+    int32_t max_mood_iters; /* MOOD iterations allowed per step (default 32)               */
+    int32_t order;          /* 2: second order with the P1 -> P0 cascade; 1: first order    */
+    int32_t mood;           /* 1: a-posteriori detection on (default); 0: unlimited         */
+    int32_t reserved;
+} lmood_params;
+
+/* Per-step report. */
+typedef struct {
+    double t;            /* time after the step                               */
+    double dt_used;      /* dt of the step (instance 0 for batches)            */
+    double dt_next;      /* dt of the next step (instance 0 for batches)       */
+    int64_t step;        /* steps taken so far                                */
+    int32_t n_troubled;  /* cells decremented to P0 during the step            */
+    int32_t n_p0;        /* cells advanced with the first-order scheme         */
+    int32_t mood_iters;  /* MOOD iterations the step needed                    */
+    int32_t n_parachute; /* P0 candidates that were not computable (then the status is an error) */
+    int32_t n_p0_eps;    /* P0 cells accepted with a negative specific internal energy */
+    int32_t reserved;
+} lmood_step_info;
+
+/* Field ids for lmood_get / lmood_set (layout, entity count n, components k). */
+enum {
+    LMOOD_FIELD_X = 0,     /* node positions x_p                 [dim][n_nodes]            */
+    LMOOD_FIELD_VP = 1,    /* node velocities v_p^n              [dim][n_nodes]            */
+    LMOOD_FIELD_VSTAR = 2, /* last step's nodal-solver velocity  [dim][n_nodes]   get only */
+    LMOOD_FIELD_V = 3,     /* cell velocities v_c                [dim][n_cells]            */
+    LMOOD_FIELD_E = 4,     /* specific total energy e_c          [n_cells]                 */
+    LMOOD_FIELD_F = 5,     /* deformation gradient F_c, row-major [dim*dim][n_cells]       */
+    LMOOD_FIELD_TAU = 6,   /* specific volume tau_c = |w_c| / m_c [n_cells]       get only */
+    LMOOD_FIELD_ORDER = 7, /* last step's order per cell, 1 or 2, as double [n_cells] get only */
+    LMOOD_FIELD_MASS = 8,  /* cell masses m_c                    [n_cells]        get only */
+    LMOOD_FIELD_PKM = 9,   /* last step's corner matrices M_cp, symmetric storage
+                              [dim(dim+1)/2][dim+1][n_cells] (xx,xy,yy | xx,xy,xz,yy,yz,zz) get only */
+    LMOOD_FIELD_PKR = 10,  /* last step's corner right-hand sides M_cp v*_cp - T*_cp l_cp n_cp
+                              [dim][dim+1][n_cells]                                get only */
+    LMOOD_FIELD_DT = 11    /* dt of the next step per instance   [n_instances]             */
+};
+
+/* Fill *p with the paper's defaults for dim (2: cfl 0.4, 3: cfl 0.25). */
+lmood_status lmood_params_default(int dim, lmood_params *p);
+
+/*
+ * Build a mesh on the device (Sect. "Mesh and notation").
+ *   dim            2 or 3
+ *   x              host, [dim][n_nodes] initial node positions
+ *   c2n            host, [dim+1][n_cells] node ids of each simplex (positively oriented)
+ *   bface, btag    host, [dim][n_bfaces] node ids and [n_bfaces] tags of boundary faces that
+ *                  carry a condition (Appendix B): 0 free traction, 1 slip wall (symmetry
+ *                  plane through the face), 2 clamped (symmetry point, v = 0). Faces not
+ *                  listed are traction-free. A node takes the strongest condition of its
+ *                  faces (clamped > slip > free); several distinct slip planes leave their
+ *                  intersection. May be NULL when n_bfaces = 0.
+ *   cell_inst      host, [n_cells] instance id of each cell for a batch of independent meshes
+ *                  concatenated into one (cells of different instances share no node), or
+ *                  NULL for a single instance. Each instance keeps its own dt.
+ *   n_inst         number of instances (1 when cell_inst is NULL)
+ *   stream         cudaStream_t on which every device operation of this mesh is ordered
+ * Builds the node-to-corner and reconstruction-stencil adjacency and the per-node boundary
+ * conditions. Errors: LMOOD_ERR_ARG, LMOOD_ERR_MESH (index out of range, |w_c| <= 0),
+ * LMOOD_ERR_OOM, LMOOD_ERR_CUDA.
+ */
+lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double *x, int64_t n_cells,
+                               const int32_t *c2n, int64_t n_bfaces, const int32_t *bface,
+                               const int32_t *btag, const int32_t *cell_inst, int32_t n_inst,
+                               void *stream, lmood_mesh *out);
+lmood_status lmood_mesh_destroy(lmood_mesh m);
+
+/*
+ * Create a state at t = 0 on mesh m (initialisation of Sect. "2D and 3D test problems"):
+ * m_c = rho0 |w_c(x^0)|, v_c = v_cell, F_c = F_cell (NULL: identity), e_c = |v_c|^2 / 2 +
+ * Psi(F_c), node velocities v_p^0 = first-order nodal solution, dt^0 = acoustic bound of
+ * Eq. CFL2 (or prm->dt_fixed).
+ *   mu_cell  host, [n_cells] shear modulus per cell (> 0)
+ *   v_cell   host, [dim][n_cells]
+ *   F_cell   host, [dim*dim][n_cells] row-major, or NULL
+ * The state keeps a reference to m: destroy the state before the mesh.
+ */
+lmood_status lmood_state_init(lmood_mesh m, const lmood_material *mat, const double *mu_cell,
+                              const double *v_cell, const double *F_cell, const lmood_params *prm,
+                              lmood_state *out);
+lmood_status lmood_state_destroy(lmood_state s);
+
+/*
+ * Advance one full explicit step t^n -> t^{n+1} (Sects. "Space-Time discretization ---
+ * ADER methodology", "Limiting: a posteriori MOOD loop", "Time-step monitoring"): corner
+ * geometry, least-squares reconstruction of v and F, ADER predictor and corner matrices,
+ * Eucclhyd nodal solver with boundary conditions, subcell forces and update of tau, v, e, F,
+ * node motion, MOOD detection and first-order recomputation of troubled cells, next dt.
+ * info may be NULL. Synchronises the stream (the MOOD loop reads the troubled count).
+ * Errors: LMOOD_ERR_PARACHUTE, LMOOD_ERR_MOOD_ITERS (state unchanged), LMOOD_ERR_CUDA.
+ */
+lmood_status lmood_step(lmood_state s, lmood_step_info *info);
+
+/* nsteps calls of lmood_step; stops at the first error. last (may be NULL) gets the report
+ * of the last step taken. */
+lmood_status lmood_run(lmood_state s, int64_t nsteps, lmood_step_info *last);
+
+/*
+ * Copy a field out of (get) or into (set) the state. dst/src is a device pointer when
+ * is_device != 0 (ordered on the mesh's stream), else a host pointer (the call
+ * synchronises). Sizes and layouts are those of the field ids above; set accepts X, VP, V,
+ * E, F and DT (replacing the dynamic state, e.g. to restart from a checkpoint; setting X
+ * also refreshes the derived cell geometry).
+ * Errors: LMOOD_ERR_ARG for an unknown or read-only field id.
+ */
+lmood_status lmood_get(lmood_state s, int field, void *dst, int is_device);
+lmood_status lmood_set(lmood_state s, int field, const void *src, int is_device);
+
+/* Sums over cells of m_c, m_c v_c and m_c e_c (out: mass, mom[dim], energy; 5 doubles). */
+lmood_status lmood_totals(lmood_state s, double *out5);
+
+/* Counts of the mesh: out[0] n_nodes, [1] n_cells, [2] dim, [3] stencil entries,
+ * [4] largest number of corners around a node, [5] instances. */
+lmood_status lmood_mesh_info(lmood_mesh m, int64_t *out6);
+
+/* Kernel timing with CUDA events on the mesh's stream, for profiling the step.
+ * lmood_timing(s, 1) resets and starts the per-class accumulators, lmood_timing(s, 0) stops.
+ * lmood_timing_read fills ms[LMOOD_NK] (summed device time per class) and launches[LMOOD_NK]
+ * (kernel launches per class since the last reset; counted whether or not timing is on). */
+enum { LMOOD_K_PREDICT = 0, LMOOD_K_NODES = 1, LMOOD_K_UPDATE = 2, LMOOD_K_MOOD = 3, LMOOD_K_FINALIZE = 4,
+       LMOOD_NK = 5 };
+lmood_status lmood_timing(lmood_state s, int enable);
+lmood_status lmood_timing_read(lmood_state s, double *ms, int64_t *launches);
+
+const char *lmood_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LMOOD_H */

@@ -1,0 +1,232 @@
+"""Thin Python binding of the GB300 Lagrangian ADER-MOOD library (C ABI in include/lmood.h).
+
+Argument marshalling only: every step of the scheme runs in the CUDA kernels of
+liblmood.so. Host arrays are numpy; device buffers may be torch CUDA tensors (their data
+pointers are passed through), and the CUDA stream defaults to torch's current stream when
+torch has a device. There is no CPU fallback: without the compiled library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB, build  # noqa: F401  (build() compiles the library in-tree)
+
+OK, ERR_ARG, ERR_MESH, ERR_CUDA, ERR_OOM, ERR_PARACHUTE, ERR_MOOD_ITERS, ERR_TIMEOUT, ERR_STATE = range(9)
+FIELD_X, FIELD_VP, FIELD_VSTAR, FIELD_V, FIELD_E, FIELD_F, FIELD_TAU, FIELD_ORDER, FIELD_MASS, \
+    FIELD_PKM, FIELD_PKR, FIELD_DT = range(12)
+
+
+class LmoodError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+class Material(C.Structure):
+    _fields_ = [("rho0", C.c_double), ("lambda_", C.c_double), ("vol_coeff", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("cfl", C.c_double), ("Cv", C.c_double), ("Ci", C.c_double), ("delta0", C.c_double),
+                ("delta1", C.c_double), ("dt_fixed", C.c_double), ("max_mood_iters", C.c_int32),
+                ("order", C.c_int32), ("mood", C.c_int32), ("reserved", C.c_int32)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt_used", C.c_double), ("dt_next", C.c_double), ("step", C.c_int64),
+                ("n_troubled", C.c_int32), ("n_p0", C.c_int32), ("mood_iters", C.c_int32),
+                ("n_parachute", C.c_int32), ("n_p0_eps", C.c_int32), ("reserved", C.c_int32)]
+
+
+_lib = None
+EXPORTS = ("lmood_params_default", "lmood_mesh_create", "lmood_mesh_destroy", "lmood_mesh_info",
+           "lmood_state_init", "lmood_state_destroy", "lmood_step", "lmood_run", "lmood_get", "lmood_set",
+           "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_last_error")
+K_PREDICT, K_NODES, K_UPDATE, K_MOOD, K_FINALIZE, NK = range(6)
+K_NAMES = ("predict", "nodes", "update", "mood", "finalize")
+
+
+def lib():
+    """Load liblmood.so (raises if it has not been built; see build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"CUDA library {LIB} is missing: run paper_2104_02139_gb300.build()")
+        L = C.CDLL(LIB)
+        vp = C.c_void_p
+        L.lmood_params_default.argtypes = [C.c_int, C.POINTER(Params)]
+        L.lmood_mesh_create.argtypes = [C.c_int, C.c_int64, vp, C.c_int64, vp, C.c_int64, vp, vp, vp, C.c_int32,
+                                        vp, C.POINTER(vp)]
+        L.lmood_mesh_destroy.argtypes = [vp]
+        L.lmood_mesh_info.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.lmood_state_init.argtypes = [vp, C.POINTER(Material), vp, vp, vp, C.POINTER(Params), C.POINTER(vp)]
+        L.lmood_state_destroy.argtypes = [vp]
+        L.lmood_step.argtypes = [vp, C.POINTER(StepInfo)]
+        L.lmood_run.argtypes = [vp, C.c_int64, C.POINTER(StepInfo)]
+        L.lmood_get.argtypes = [vp, C.c_int, vp, C.c_int]
+        L.lmood_set.argtypes = [vp, C.c_int, vp, C.c_int]
+        L.lmood_totals.argtypes = [vp, C.POINTER(C.c_double)]
+        L.lmood_timing.argtypes = [vp, C.c_int]
+        L.lmood_timing_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.lmood_last_error.restype = C.c_char_p
+        for name in EXPORTS:
+            if name != "lmood_last_error":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise LmoodError(rc, lib().lmood_last_error().decode(errors="replace"))
+
+
+def _host(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def current_stream_handle():
+    """torch's current CUDA stream as a raw handle (None for the legacy default stream)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream or None
+    except Exception:
+        pass
+    return None
+
+
+def params_default(dim: int, **kw) -> Params:
+    p = Params()
+    _check(lib().lmood_params_default(dim, C.byref(p)))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Mesh:
+    """lmood_mesh_create / lmood_mesh_destroy."""
+
+    def __init__(self, dim, x, c2n, bface=None, btag=None, cell_inst=None, n_inst=1, stream=None):
+        x = _host(x, np.float64)
+        c2n = _host(c2n, np.int32)
+        bface = _host(bface, np.int32)
+        btag = _host(btag, np.int32)
+        ci = _host(cell_inst, np.int32)
+        nb = 0 if btag is None else btag.size
+        self.dim, self.n_nodes, self.n_cells = dim, x.shape[-1], c2n.shape[-1]
+        self.n_inst = n_inst if ci is not None else 1
+        self.stream = current_stream_handle() if stream is None else stream
+        h = C.c_void_p()
+        _check(lib().lmood_mesh_create(dim, self.n_nodes, _ptr(x), self.n_cells, _ptr(c2n), nb,
+                                       _ptr(bface) if nb else None, _ptr(btag) if nb else None, _ptr(ci),
+                                       self.n_inst, self.stream, C.byref(h)))
+        self.h = h
+
+    def info(self) -> dict:
+        o = (C.c_int64 * 6)()
+        _check(lib().lmood_mesh_info(self.h, o))
+        return dict(zip(("n_nodes", "n_cells", "dim", "stencil_nnz", "max_corners", "n_inst"), list(o)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lmood_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+class State:
+    """lmood_state_init / step / run / get / set / totals / destroy."""
+
+    def __init__(self, mesh: Mesh, rho0, lam, mu, v, F=None, params: Params | None = None, vol_coeff=0):
+        self.mesh = mesh
+        self.params = params or params_default(mesh.dim)
+        mat = Material(rho0=rho0, lambda_=lam, vol_coeff=vol_coeff)
+        mu = _host(mu, np.float64)
+        v = _host(v, np.float64)
+        F = _host(F, np.float64)
+        h = C.c_void_p()
+        _check(lib().lmood_state_init(mesh.h, C.byref(mat), _ptr(mu), _ptr(v), _ptr(F), C.byref(self.params),
+                                      C.byref(h)))
+        self.h = h
+        self.info = StepInfo()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lmood_state_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def step(self) -> StepInfo:
+        _check(lib().lmood_step(self.h, C.byref(self.info)))
+        return self.info
+
+    def step_status(self) -> int:
+        """lmood_step without raising: returns the status code."""
+        return lib().lmood_step(self.h, C.byref(self.info))
+
+    def run(self, n: int) -> StepInfo:
+        _check(lib().lmood_run(self.h, n, C.byref(self.info)))
+        return self.info
+
+    def shape(self, field: int) -> tuple:
+        d, nc, npn, nv = self.mesh.dim, self.mesh.n_cells, self.mesh.n_nodes, self.mesh.dim + 1
+        return {FIELD_X: (d, npn), FIELD_VP: (d, npn), FIELD_VSTAR: (d, npn), FIELD_V: (d, nc), FIELD_E: (nc,),
+                FIELD_F: (d * d, nc), FIELD_TAU: (nc,), FIELD_ORDER: (nc,), FIELD_MASS: (nc,),
+                FIELD_PKM: (d * (d + 1) // 2, nv, nc), FIELD_PKR: (d, nv, nc), FIELD_DT: (self.mesh.n_inst,)}[field]
+
+    def get(self, field: int, out=None):
+        """Host copy as numpy (out None or a numpy array), or into a torch CUDA tensor."""
+        if out is None:
+            out = np.empty(self.shape(field))
+        if isinstance(out, np.ndarray):
+            _check(lib().lmood_get(self.h, field, out.ctypes.data, 0))
+        else:
+            _check(lib().lmood_get(self.h, field, C.c_void_p(out.data_ptr()), 1))
+        return out
+
+    def set(self, field: int, src):
+        if isinstance(src, np.ndarray) or not hasattr(src, "data_ptr"):
+            a = np.ascontiguousarray(src, dtype=np.float64)
+            _check(lib().lmood_set(self.h, field, a.ctypes.data, 0))
+        else:
+            _check(lib().lmood_set(self.h, field, C.c_void_p(src.data_ptr()), 1))
+
+    def totals(self) -> np.ndarray:
+        o = (C.c_double * 5)()
+        _check(lib().lmood_totals(self.h, o))
+        return np.array(list(o))
+
+    def timing(self, enable: bool):
+        _check(lib().lmood_timing(self.h, 1 if enable else 0))
+
+    def timing_read(self) -> dict:
+        ms = (C.c_double * NK)()
+        n = (C.c_int64 * NK)()
+        _check(lib().lmood_timing_read(self.h, ms, n))
+        return {K_NAMES[i]: (ms[i], n[i]) for i in range(NK)}
+
+    def state(self) -> dict:
+        return {"x": self.get(FIELD_X), "vp": self.get(FIELD_VP), "v": self.get(FIELD_V), "e": self.get(FIELD_E),
+                "F": self.get(FIELD_F), "tau": self.get(FIELD_TAU)}
+
+
+def simulation(problem, stream=None, **params) -> State:
+    """Mesh + state of a workload problem (anything with .mesh, .rho0, .lam, .mu, .v, .F, .cfl)."""
+    m = problem.mesh
+    mesh = Mesh(m.dim, m.x, m.c2n, m.bface, m.btag, stream=stream)
+    p = params_default(m.dim, cfl=problem.cfl)
+    for k, v in params.items():
+        setattr(p, k, v)
+    return State(mesh, problem.rho0, problem.lam, problem.mu, problem.v, problem.F, p)

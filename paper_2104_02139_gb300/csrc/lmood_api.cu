@@ -1,0 +1,763 @@
+// lmood_api.cu -- C ABI of the library (declared in include/lmood.h): mesh set-up (node ->
+// corner and stencil adjacency, boundary-condition resolution), state buffers, and the host
+// side of the step (kernel sequence and the MOOD loop over compacted lists).
+#include <algorithm>
+#include <array>
+#include <functional>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "lmood.h"
+#include "lmood_ops.h"
+
+using namespace lmood;
+
+namespace {
+
+thread_local std::string g_err;
+
+lmood_status fail(lmood_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+#define LM_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) return fail(LMOOD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct DevAllocs {
+    std::vector<void *> ptrs;
+    lmood_status alloc(void **p, size_t bytes) {
+        *p = nullptr;
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LMOOD_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        }
+        ptrs.push_back(*p);
+        return LMOOD_OK;
+    }
+    void release() {
+        for (void *p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+template <class T> lmood_status upload(DevAllocs &A, T **dst, const T *src, size_t n, cudaStream_t st) {
+    lmood_status s = A.alloc((void **)dst, n * sizeof(T));
+    if (s) return s;
+    if (n && src) LM_CUDA(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, st));
+    return LMOOD_OK;
+}
+
+void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)> &fn) {
+    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    if (n < 20000) nt = 1;
+    std::vector<std::thread> th;
+    const int64_t chunk = (n + nt - 1) / nt;
+    for (unsigned t = 0; t < nt; ++t) {
+        const int64_t b = t * chunk, e = std::min<int64_t>(n, b + chunk);
+        if (b < e) th.emplace_back(fn, b, e);
+    }
+    for (auto &t : th) t.join();
+}
+
+}  // namespace
+
+// =======================================================================================
+// mesh
+// =======================================================================================
+struct lmood_mesh_s {
+    int dim = 0, n_inst = 1;
+    int64_t np = 0, nc = 0, st_nnz = 0;
+    int max_deg = 0;
+    cudaStream_t st = nullptr;
+    const Ops *ops = nullptr;
+    Geo geo{};
+    double *x0 = nullptr;
+    DevAllocs mem;
+};
+
+static double host_volume(int d, const double *x, int64_t np, const int32_t *c2n, int64_t nc, int64_t c) {
+    int p[4];
+    for (int k = 0; k <= d; ++k) p[k] = c2n[k * nc + c];
+    auto X = [&](int k, int a) { return x[a * np + p[k]]; };
+    if (d == 2) return 0.5 * ((X(1, 0) - X(0, 0)) * (X(2, 1) - X(0, 1)) - (X(1, 1) - X(0, 1)) * (X(2, 0) - X(0, 0)));
+    double e[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 3; ++a) e[k][a] = X(k + 1, a) - X(0, a);
+    return (e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) - e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+            e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0])) /
+           6.0;
+}
+
+extern "C" lmood_status lmood_params_default(int dim, lmood_params *p) {
+    if (!p || (dim != 2 && dim != 3)) return fail(LMOOD_ERR_ARG, "lmood_params_default: bad dim or NULL");
+    std::memset(p, 0, sizeof(*p));
+    p->cfl = dim == 2 ? 0.4 : 0.25;
+    p->Cv = 0.2;
+    p->Ci = 0.1;
+    p->delta0 = 1e-4;
+    p->delta1 = 1e-3;
+    p->dt_fixed = 0.0;
+    p->max_mood_iters = 32;
+    p->order = 2;
+    p->mood = 1;
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double *x, int64_t n_cells,
+                                          const int32_t *c2n, int64_t n_bfaces, const int32_t *bface,
+                                          const int32_t *btag, const int32_t *cell_inst, int32_t n_inst,
+                                          void *stream, lmood_mesh *out) {
+    if (!out) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: out is NULL");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: dim must be 2 or 3");
+    if (n_nodes <= 0 || n_cells <= 0 || !x || !c2n) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: empty mesh or NULL array");
+    const int nv = dim + 1;
+    if (n_cells * nv >= (int64_t)INT32_MAX || n_nodes >= (int64_t)INT32_MAX)
+        return fail(LMOOD_ERR_ARG, "lmood_mesh_create: mesh too large for 32-bit corner ids");
+    if (n_bfaces < 0 || (n_bfaces > 0 && (!bface || !btag))) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: boundary faces");
+    if (cell_inst ? n_inst < 1 : n_inst > 1) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: bad instance count");
+    if (!cell_inst) n_inst = 1;
+    const int64_t N = n_cells, Np = n_nodes;
+    // validation: indices and orientation
+    for (int64_t i = 0; i < N * nv; ++i)
+        if (c2n[i] < 0 || c2n[i] >= Np) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: node index out of range in c2n");
+    for (int64_t c = 0; c < N; ++c)
+        if (!(host_volume(dim, x, Np, c2n, N, c) > 0.0))
+            return fail(LMOOD_ERR_MESH, "lmood_mesh_create: cell " + std::to_string(c) + " has non-positive volume");
+    for (int64_t i = 0; i < n_bfaces * dim; ++i)
+        if (bface[i] < 0 || bface[i] >= Np) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: node index out of range in bface");
+    for (int64_t i = 0; i < n_bfaces; ++i)
+        if (btag[i] < 0 || btag[i] > 2) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: boundary tag must be 0, 1 or 2");
+    std::vector<int> node_inst;
+    if (cell_inst) {
+        node_inst.assign(Np, -1);
+        for (int64_t c = 0; c < N; ++c) {
+            const int ci = cell_inst[c];
+            if (ci < 0 || ci >= n_inst) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: cell instance out of range");
+            for (int k = 0; k < nv; ++k) {
+                int &ni = node_inst[c2n[k * N + c]];
+                if (ni >= 0 && ni != ci) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: a node is shared by two instances");
+                ni = ci;
+            }
+        }
+    }
+    // node -> corner CSR: corners of each node in ascending cell id; corner id = k N + c
+    std::vector<int> off(Np + 1, 0), n2c(N * nv);
+    for (int64_t c = 0; c < N; ++c)
+        for (int k = 0; k < nv; ++k) off[c2n[k * N + c] + 1]++;
+    for (int64_t p = 0; p < Np; ++p) off[p + 1] += off[p];
+    int max_deg = 0;
+    for (int64_t p = 0; p < Np; ++p) max_deg = std::max(max_deg, off[p + 1] - off[p]);
+    {
+        std::vector<int> pos(off.begin(), off.end() - 1);
+        for (int64_t c = 0; c < N; ++c)
+            for (int k = 0; k < nv; ++k) n2c[pos[c2n[k * N + c]]++] = (int)(k * N + c);
+    }
+    // reconstruction stencil: every other cell sharing a node, ascending id
+    std::vector<int> scount(N + 1, 0);
+    auto gather = [&](int64_t c, std::vector<int> &buf) {
+        buf.clear();
+        for (int k = 0; k < nv; ++k) {
+            const int p = c2n[k * N + c];
+            for (int j = off[p]; j < off[p + 1]; ++j) {
+                const int o = (int)(n2c[j] % N);
+                if (o != c) buf.push_back(o);
+            }
+        }
+        std::sort(buf.begin(), buf.end());
+        buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+    };
+    parallel_for(N, [&](int64_t b, int64_t e) {
+        std::vector<int> buf;
+        for (int64_t c = b; c < e; ++c) {
+            gather(c, buf);
+            scount[c + 1] = (int)buf.size();
+        }
+    });
+    for (int64_t c = 0; c < N; ++c) scount[c + 1] += scount[c];
+    const int64_t nnz = scount[N];
+    if (nnz >= (int64_t)INT32_MAX) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: stencil too large");
+    std::vector<int> sidx_(nnz);
+    parallel_for(N, [&](int64_t b, int64_t e) {
+        std::vector<int> buf;
+        for (int64_t c = b; c < e; ++c) {
+            gather(c, buf);
+            std::copy(buf.begin(), buf.end(), sidx_.begin() + scount[c]);
+        }
+    });
+    // boundary conditions (Appendix B; strongest first: clamped, slip, free)
+    std::vector<unsigned char> ndof(Np, (unsigned char)dim);
+    std::vector<double> bct(6 * Np, 0.0);
+    {
+        std::vector<unsigned char> clamped(Np, 0);
+        std::vector<std::vector<std::array<double, 3>>> planes(Np);
+        for (int64_t f = 0; f < n_bfaces; ++f) {
+            int q[3];
+            for (int a = 0; a < dim; ++a) q[a] = bface[a * n_bfaces + f];
+            std::array<double, 3> nrm{0, 0, 0};
+            if (dim == 2) {
+                nrm[0] = x[1 * Np + q[1]] - x[1 * Np + q[0]];
+                nrm[1] = x[0 * Np + q[0]] - x[0 * Np + q[1]];
+            } else {
+                double u[3], w[3];
+                for (int a = 0; a < 3; ++a) {
+                    u[a] = x[a * Np + q[1]] - x[a * Np + q[0]];
+                    w[a] = x[a * Np + q[2]] - x[a * Np + q[0]];
+                }
+                nrm = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+            }
+            const double len = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+            if (!(len > 0)) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: degenerate boundary face");
+            for (double &v : nrm) v /= len;
+            for (int a = 0; a < dim; ++a) {
+                const int p = q[a];
+                if (btag[f] == 2) clamped[p] = 1;
+                if (btag[f] != 1) continue;
+                bool known = false;
+                for (auto &pl : planes[p])
+                    if (std::fabs(pl[0] * nrm[0] + pl[1] * nrm[1] + pl[2] * nrm[2]) > 1.0 - 1e-12) known = true;
+                if (!known) planes[p].push_back(nrm);
+            }
+        }
+        for (int64_t p = 0; p < Np; ++p) {
+            const int k = clamped[p] ? dim : (int)planes[p].size();
+            auto T = [&](int i, int a) -> double & { return bct[(i * 3 + a) * Np + p]; };
+            if (k == 0) continue;
+            if (k >= dim) {
+                ndof[p] = 0;
+                continue;
+            }
+            const auto &n1 = planes[p][0];
+            if (dim == 2) {  // one wall line: the free direction is its tangent
+                ndof[p] = 1;
+                T(0, 0) = n1[1];
+                T(0, 1) = -n1[0];
+            } else if (k == 1) {  // one wall plane: Gram-Schmidt of the two axes least aligned with n
+                int ax[3] = {0, 1, 2};
+                std::sort(ax, ax + 3, [&](int i, int j) { return std::fabs(n1[i]) < std::fabs(n1[j]); });
+                double t1[3] = {0, 0, 0};
+                t1[ax[0]] = 1.0;
+                const double dn = t1[0] * n1[0] + t1[1] * n1[1] + t1[2] * n1[2];
+                for (int a = 0; a < 3; ++a) t1[a] -= dn * n1[a];
+                const double l1 = std::sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+                for (int a = 0; a < 3; ++a) t1[a] /= l1;
+                double t2[3] = {n1[1] * t1[2] - n1[2] * t1[1], n1[2] * t1[0] - n1[0] * t1[2], n1[0] * t1[1] - n1[1] * t1[0]};
+                const double l2 = std::sqrt(t2[0] * t2[0] + t2[1] * t2[1] + t2[2] * t2[2]);
+                for (int a = 0; a < 3; ++a) {
+                    T(0, a) = t1[a];
+                    T(1, a) = t2[a] / l2;
+                }
+                ndof[p] = 2;
+            } else {  // two wall planes: their intersection line
+                const auto &n2 = planes[p][1];
+                double l[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2], n1[0] * n2[1] - n1[1] * n2[0]};
+                const double ll = std::sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+                for (int a = 0; a < 3; ++a) T(0, a) = l[a] / ll;
+                ndof[p] = 1;
+            }
+        }
+    }
+    // device copies
+    cudaStream_t st = (cudaStream_t)stream;
+    auto *m = new lmood_mesh_s();
+    m->dim = dim;
+    m->n_inst = n_inst;
+    m->np = Np;
+    m->nc = N;
+    m->st_nnz = nnz;
+    m->max_deg = max_deg;
+    m->st = st;
+    m->ops = dim == 2 ? &ops_dim2() : &ops_dim3();
+    Geo &g = m->geo;
+    g.N = (int)N;
+    g.Np = (int)Np;
+    g.n_inst = n_inst;
+    lmood_status s;
+    int *d_c2n, *d_off, *d_n2c, *d_soff, *d_sidx, *d_ci = nullptr, *d_ni = nullptr;
+    unsigned char *d_nd;
+    double *d_bt;
+    std::vector<int> c2n_i(c2n, c2n + N * nv);
+    if ((s = upload(m->mem, &d_c2n, c2n_i.data(), c2n_i.size(), st)) ||
+        (s = upload(m->mem, &d_off, off.data(), off.size(), st)) ||
+        (s = upload(m->mem, &d_n2c, n2c.data(), n2c.size(), st)) ||
+        (s = upload(m->mem, &d_soff, scount.data(), scount.size(), st)) ||
+        (s = upload(m->mem, &d_sidx, sidx_.data(), sidx_.size(), st)) ||
+        (s = upload(m->mem, &d_nd, ndof.data(), ndof.size(), st)) ||
+        (s = upload(m->mem, &d_bt, bct.data(), bct.size(), st)) ||
+        (s = upload(m->mem, &m->x0, x, (size_t)(dim * Np), st))) {
+        m->mem.release();
+        delete m;
+        return s;
+    }
+    if (cell_inst) {
+        std::vector<int> ci(cell_inst, cell_inst + N);
+        if ((s = upload(m->mem, &d_ci, ci.data(), ci.size(), st)) ||
+            (s = upload(m->mem, &d_ni, node_inst.data(), node_inst.size(), st))) {
+            m->mem.release();
+            delete m;
+            return s;
+        }
+    }
+    g.c2n = d_c2n;
+    g.n2c_off = d_off;
+    g.n2c = d_n2c;
+    g.st_off = d_soff;
+    g.st_idx = d_sidx;
+    g.bc_ndof = d_nd;
+    g.bc_t = d_bt;
+    g.cell_inst = d_ci;
+    g.node_inst = d_ni;
+    cudaError_t e = cudaStreamSynchronize(st);  // host vectors die at return
+    if (e != cudaSuccess) {
+        m->mem.release();
+        delete m;
+        return fail(LMOOD_ERR_CUDA, std::string("lmood_mesh_create: ") + cudaGetErrorString(e));
+    }
+    *out = m;
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_mesh_destroy(lmood_mesh m) {
+    if (!m) return fail(LMOOD_ERR_ARG, "lmood_mesh_destroy: NULL");
+    cudaStreamSynchronize(m->st);
+    m->mem.release();
+    delete m;
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_mesh_info(lmood_mesh m, int64_t *o) {
+    if (!m || !o) return fail(LMOOD_ERR_ARG, "lmood_mesh_info: NULL");
+    o[0] = m->np;
+    o[1] = m->nc;
+    o[2] = m->dim;
+    o[3] = m->st_nnz;
+    o[4] = m->max_deg;
+    o[5] = m->n_inst;
+    return LMOOD_OK;
+}
+
+// =======================================================================================
+// state
+// =======================================================================================
+struct lmood_state_s {
+    lmood_mesh M = nullptr;
+    lmood_params prm{};
+    lmood_material mat{};
+    Prm kp{};
+    Fld f{};
+    double *tau = nullptr, *m = nullptr, *mu = nullptr;
+    int *tl[2] = {nullptr, nullptr}, *nlist = nullptr, *clist = nullptr, *node_mark = nullptr, *cell_mark = nullptr;
+    double *totals = nullptr;
+    int *h_cnt = nullptr;      // pinned mirror of the device counters
+    double *h_dt = nullptr;    // pinned: dt used, dt next (instance 0)
+    double t = 0.0;
+    int64_t step = 0;
+    int stamp = 0;
+    bool broken = false;
+    lmood_step_info last{};
+    // kernel timing (CUDA events around launches, drained at the step's sync points)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;            // pool of 2 * kMaxPending events
+    std::vector<int> pend_cls;              // class of each pending pair
+    double kms[LMOOD_NK] = {0, 0, 0, 0, 0};
+    int64_t klaunch[LMOOD_NK] = {0, 0, 0, 0, 0};
+    DevAllocs mem;
+};
+
+static constexpr int kMaxPending = 64;
+
+static void timing_drain(lmood_state s) {
+    for (size_t i = 0; i < s->pend_cls.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, s->ev[2 * i], s->ev[2 * i + 1]) == cudaSuccess) s->kms[s->pend_cls[i]] += ms;
+    }
+    s->pend_cls.clear();
+}
+
+// Launch helper: counts the launch and, with timing on, brackets it with a pair of events.
+template <class F> static void timed(lmood_state s, int cls, int n_launch, F &&launch) {
+    s->klaunch[cls] += n_launch;
+    if (!s->timing || s->pend_cls.size() >= (size_t)kMaxPending) {
+        launch();
+        return;
+    }
+    const size_t i = s->pend_cls.size();
+    cudaEventRecord(s->ev[2 * i], s->M->st);
+    launch();
+    cudaEventRecord(s->ev[2 * i + 1], s->M->st);
+    s->pend_cls.push_back(cls);
+}
+
+static void swap_state(lmood_state s) {
+    Fld &f = s->f;
+    std::swap(f.x, f.x1);
+    std::swap(f.vp, f.vp1);
+    std::swap(f.v, f.v1);
+    std::swap(f.e, f.e1);
+    std::swap(f.F, f.F1);
+    std::swap(f.xc, f.xc1);
+    std::swap(f.rho, f.rho1);
+    std::swap(s->tau, f.tau1);
+    double *dt = const_cast<double *>(f.dt);
+    f.dt = (const double *)f.dtn;
+    f.dtn = (unsigned long long *)dt;
+}
+
+static Prm kernel_params(const lmood_params &p, const lmood_material &m) {
+    Prm k{};
+    k.cfl = p.cfl;
+    k.Cv = p.Cv;
+    k.Ci = p.Ci;
+    k.delta0 = p.delta0;
+    k.delta1 = p.delta1;
+    k.dt_fixed = p.dt_fixed;
+    k.lam = m.lambda;
+    k.base_order = p.order == 1 ? 1 : 2;
+    k.mood = p.mood ? 1 : 0;
+    k.vol_coeff = m.vol_coeff ? 1 : 0;
+    return k;
+}
+
+static void state_free(lmood_state s) {
+    if (s->M) cudaStreamSynchronize(s->M->st);
+    for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+    s->mem.release();
+    if (s->h_cnt) cudaFreeHost(s->h_cnt);
+    if (s->h_dt) cudaFreeHost(s->h_dt);
+    delete s;
+}
+
+extern "C" lmood_status lmood_state_destroy(lmood_state s) {
+    if (!s) return fail(LMOOD_ERR_ARG, "lmood_state_destroy: NULL");
+    state_free(s);
+    return LMOOD_OK;
+}
+
+static lmood_status sync_check(lmood_state s, const char *where) {
+    cudaError_t e = cudaStreamSynchronize(s->M->st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        s->broken = true;
+        return fail(LMOOD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    }
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat, const double *mu_cell,
+                                         const double *v_cell, const double *F_cell, const lmood_params *prm,
+                                         lmood_state *out) {
+    if (!out) return fail(LMOOD_ERR_ARG, "lmood_state_init: out is NULL");
+    *out = nullptr;
+    if (!M || !mat || !mu_cell || !v_cell || !prm) return fail(LMOOD_ERR_ARG, "lmood_state_init: NULL argument");
+    if (!(mat->rho0 > 0)) return fail(LMOOD_ERR_ARG, "lmood_state_init: rho0 must be positive");
+    if (!(prm->cfl > 0) || prm->max_mood_iters < 0 || (prm->order != 1 && prm->order != 2))
+        return fail(LMOOD_ERR_ARG, "lmood_state_init: bad parameters");
+    const int D = M->dim, NV = D + 1, NS = D * (D + 1) / 2;
+    const int64_t N = M->nc, Np = M->np;
+    for (int64_t c = 0; c < N; ++c)
+        if (!(mu_cell[c] > 0)) return fail(LMOOD_ERR_ARG, "lmood_state_init: mu must be positive");
+    auto *s = new lmood_state_s();
+    s->M = M;
+    s->prm = *prm;
+    s->mat = *mat;
+    s->kp = kernel_params(*prm, *mat);
+    cudaStream_t st = M->st;
+    Fld &f = s->f;
+    lmood_status r = LMOOD_OK;
+    auto A = [&](void **p, size_t bytes) {
+        if (r == LMOOD_OK) r = s->mem.alloc(p, bytes);
+    };
+    const size_t nd = sizeof(double);
+    A((void **)&f.x, D * Np * nd);
+    A((void **)&f.x1, D * Np * nd);
+    A((void **)&f.vp, D * Np * nd);
+    A((void **)&f.vp1, D * Np * nd);
+    A((void **)&f.vs, D * Np * nd);
+    A((void **)&f.v, D * N * nd);
+    A((void **)&f.v1, D * N * nd);
+    A((void **)&f.e, N * nd);
+    A((void **)&f.e1, N * nd);
+    A((void **)&f.F, D * D * N * nd);
+    A((void **)&f.F1, D * D * N * nd);
+    A((void **)&f.xc, D * N * nd);
+    A((void **)&f.xc1, D * N * nd);
+    A((void **)&f.rho, N * nd);
+    A((void **)&f.rho1, N * nd);
+    A((void **)&s->tau, N * nd);
+    A((void **)&f.tau1, N * nd);
+    A((void **)&s->m, N * nd);
+    A((void **)&s->mu, N * nd);
+    A((void **)&f.pkM, (size_t)NS * NV * N * nd);
+    A((void **)&f.pkR, (size_t)D * NV * N * nd);
+    A((void **)&f.order, N);
+    A((void **)&f.pflag, N);
+    A((void **)&f.dtc, N * nd);
+    double *dt0 = nullptr, *dt1 = nullptr;
+    A((void **)&dt0, M->n_inst * nd);
+    A((void **)&dt1, M->n_inst * nd);
+    A((void **)&f.cnt, CNT_N * sizeof(int));
+    A((void **)&s->tl[0], N * sizeof(int));
+    A((void **)&s->tl[1], N * sizeof(int));
+    A((void **)&s->nlist, Np * sizeof(int));
+    A((void **)&s->clist, N * sizeof(int));
+    A((void **)&s->node_mark, Np * sizeof(int));
+    A((void **)&s->cell_mark, N * sizeof(int));
+    A((void **)&s->totals, 8 * nd);
+    if (r) {
+        state_free(s);
+        return r;
+    }
+    if (cudaMallocHost((void **)&s->h_cnt, CNT_N * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void **)&s->h_dt, 4 * nd) != cudaSuccess) {
+        cudaGetLastError();
+        state_free(s);
+        return fail(LMOOD_ERR_OOM, "lmood_state_init: pinned host allocation failed");
+    }
+    f.m = s->m;
+    f.mu = s->mu;
+    f.dt = dt0;
+    f.dtn = (unsigned long long *)dt1;
+    auto H2D = [&](void *d, const void *h, size_t b) {
+        if (r == LMOOD_OK && cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            r = fail(LMOOD_ERR_CUDA, "lmood_state_init: upload");
+    };
+    if (cudaMemcpyAsync(f.x, M->x0, D * Np * nd, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        r = fail(LMOOD_ERR_CUDA, "lmood_state_init: copy positions");
+    H2D(s->mu, mu_cell, N * nd);
+    H2D(f.v, v_cell, D * N * nd);
+    if (F_cell) H2D(f.F, F_cell, D * D * N * nd);
+    if (r == LMOOD_OK) {
+        cudaMemsetAsync(s->node_mark, 0, Np * sizeof(int), st);
+        cudaMemsetAsync(s->cell_mark, 0, N * sizeof(int), st);
+        cudaMemsetAsync(f.vp, 0, D * Np * nd, st);
+        cudaMemsetAsync(dt0, 0, M->n_inst * nd, st);
+        cudaMemsetAsync(f.cnt, 0, CNT_N * sizeof(int), st);
+        const Ops &op = *M->ops;
+        Prm p0 = s->kp;
+        p0.base_order = 1;
+        op.init_cells(M->geo, f, p0, mat->rho0, s->m, F_cell ? 1 : 0, st);
+        std::swap(s->tau, f.tau1);
+        op.predict(M->geo, f, p0, nullptr, nullptr, (int)N, st);
+        op.nodes(M->geo, f, nullptr, nullptr, (int)Np, 1, st);
+        op.dt_init(f, p0, M->n_inst, 1, st);
+        op.finalize(M->geo, f, p0, st);
+        double *dt = const_cast<double *>(f.dt);
+        f.dt = (const double *)f.dtn;
+        f.dtn = (unsigned long long *)dt;
+        r = sync_check(s, "lmood_state_init");
+    }
+    if (r) {
+        state_free(s);
+        return r;
+    }
+    *out = s;
+    return LMOOD_OK;
+}
+
+// =======================================================================================
+// step
+// =======================================================================================
+extern "C" lmood_status lmood_step(lmood_state s, lmood_step_info *info) {
+    if (!s) return fail(LMOOD_ERR_ARG, "lmood_step: NULL state");
+    if (s->broken) return fail(LMOOD_ERR_STATE, "lmood_step: state unusable after an earlier CUDA error");
+    lmood_mesh M = s->M;
+    const Ops &op = *M->ops;
+    const Geo &g = M->geo;
+    Fld &f = s->f;
+    cudaStream_t st = M->st;
+    const int N = (int)M->nc, Np = (int)M->np, NV = M->dim + 1;
+    LM_CUDA(cudaMemsetAsync(f.cnt, 0, CNT_N * sizeof(int), st));
+    timed(s, LMOOD_K_PREDICT, 1, [&] { op.predict(g, f, s->kp, nullptr, nullptr, N, st); });
+    timed(s, LMOOD_K_NODES, 1, [&] { op.nodes(g, f, nullptr, nullptr, Np, 0, st); });
+    int cur = 0;
+    timed(s, LMOOD_K_UPDATE, 1, [&] { op.update(g, f, s->kp, nullptr, nullptr, N, s->tl[cur], f.cnt + CNT_T0 + cur, st); });
+    LM_CUDA(cudaMemcpyAsync(s->h_cnt, f.cnt, CNT_N * sizeof(int), cudaMemcpyDeviceToHost, st));
+    lmood_status r = sync_check(s, "lmood_step");
+    if (r) return r;
+    timing_drain(s);
+    int nT = s->h_cnt[CNT_T0];
+    int iters = 0, n_troubled = 0;
+    while (nT > 0) {
+        if (++iters > s->prm.max_mood_iters)
+            return fail(LMOOD_ERR_MOOD_ITERS, "lmood_step: troubled cells remain after max_mood_iters MOOD iterations");
+        n_troubled += nT;
+        ++s->stamp;
+        const int nxt = cur ^ 1;
+        LM_CUDA(cudaMemsetAsync(f.cnt + CNT_T0 + nxt, 0, sizeof(int), st));
+        LM_CUDA(cudaMemsetAsync(f.cnt + CNT_NODES, 0, 2 * sizeof(int), st));
+        const int nb_nodes = (int)std::min<int64_t>(Np, (int64_t)NV * nT);
+        const int nb_cells = (int)std::min<int64_t>(N, (int64_t)M->max_deg * nb_nodes);
+        timed(s, LMOOD_K_MOOD, 5, [&] {
+            op.mark_nodes(g, f, s->tl[cur], f.cnt + CNT_T0 + cur, nT, s->node_mark, s->stamp, s->nlist, st);
+            op.mark_cells(g, f, s->nlist, nb_nodes, s->cell_mark, s->stamp, s->clist, st);
+            op.predict(g, f, s->kp, s->tl[cur], f.cnt + CNT_T0 + cur, nT, st);
+            op.nodes(g, f, s->nlist, f.cnt + CNT_NODES, nb_nodes, 0, st);
+            op.update(g, f, s->kp, s->clist, f.cnt + CNT_CELLS, nb_cells, s->tl[nxt], f.cnt + CNT_T0 + nxt, st);
+        });
+        LM_CUDA(cudaMemcpyAsync(s->h_cnt, f.cnt, CNT_N * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if ((r = sync_check(s, "lmood_step (MOOD)"))) return r;
+        timing_drain(s);
+        cur = nxt;
+        nT = s->h_cnt[CNT_T0 + cur];
+    }
+    timed(s, LMOOD_K_FINALIZE, 2, [&] {
+        op.dt_init(f, s->kp, M->n_inst, 0, st);
+        op.finalize(g, f, s->kp, st);
+    });
+    LM_CUDA(cudaMemcpyAsync(s->h_cnt, f.cnt, CNT_N * sizeof(int), cudaMemcpyDeviceToHost, st));
+    LM_CUDA(cudaMemcpyAsync(s->h_dt, f.dt, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LM_CUDA(cudaMemcpyAsync(s->h_dt + 1, f.dtn, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if ((r = sync_check(s, "lmood_step (finalize)"))) return r;
+    timing_drain(s);
+    lmood_step_info in{};
+    in.n_troubled = n_troubled;
+    in.mood_iters = iters;
+    in.n_p0 = s->h_cnt[CNT_P0];
+    in.n_parachute = s->h_cnt[CNT_PARA];
+    in.n_p0_eps = s->h_cnt[CNT_EPS];
+    in.dt_used = s->h_dt[0];
+    in.dt_next = s->h_dt[1];
+    if (in.n_parachute > 0) {
+        in.t = s->t;
+        in.step = s->step;
+        if (info) *info = in;
+        return fail(LMOOD_ERR_PARACHUTE, "lmood_step: " + std::to_string(in.n_parachute) +
+                                             " first-order cells are not computable (parachute failure)");
+    }
+    swap_state(s);
+    s->t += in.dt_used;
+    s->step += 1;
+    in.t = s->t;
+    in.step = s->step;
+    s->last = in;
+    if (info) *info = in;
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_run(lmood_state s, int64_t nsteps, lmood_step_info *last) {
+    if (!s || nsteps < 0) return fail(LMOOD_ERR_ARG, "lmood_run: bad argument");
+    for (int64_t i = 0; i < nsteps; ++i) {
+        lmood_status r = lmood_step(s, last);
+        if (r) return r;
+    }
+    if (last && nsteps == 0) *last = s->last;
+    return LMOOD_OK;
+}
+
+// =======================================================================================
+// fields
+// =======================================================================================
+__global__ static void k_u8_to_f64(const unsigned char *a, double *b, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+extern "C" lmood_status lmood_get(lmood_state s, int field, void *dst, int is_device) {
+    if (!s || !dst) return fail(LMOOD_ERR_ARG, "lmood_get: NULL argument");
+    lmood_mesh M = s->M;
+    const int D = M->dim, NV = D + 1, NS = D * (D + 1) / 2;
+    const size_t N = M->nc, Np = M->np, nd = sizeof(double);
+    cudaStream_t st = M->st;
+    const Fld &f = s->f;
+    const void *src = nullptr;
+    size_t bytes = 0;
+    switch (field) {
+    case LMOOD_FIELD_X: src = f.x; bytes = D * Np * nd; break;
+    case LMOOD_FIELD_VP: src = f.vp; bytes = D * Np * nd; break;
+    case LMOOD_FIELD_VSTAR: src = f.vs; bytes = D * Np * nd; break;
+    case LMOOD_FIELD_V: src = f.v; bytes = D * N * nd; break;
+    case LMOOD_FIELD_E: src = f.e; bytes = N * nd; break;
+    case LMOOD_FIELD_F: src = f.F; bytes = D * D * N * nd; break;
+    case LMOOD_FIELD_TAU: src = s->tau; bytes = N * nd; break;
+    case LMOOD_FIELD_MASS: src = s->m; bytes = N * nd; break;
+    case LMOOD_FIELD_PKM: src = f.pkM; bytes = NS * NV * N * nd; break;
+    case LMOOD_FIELD_PKR: src = f.pkR; bytes = D * NV * N * nd; break;
+    case LMOOD_FIELD_DT: src = f.dt; bytes = M->n_inst * nd; break;
+    case LMOOD_FIELD_ORDER: {
+        double *tmp = (double *)f.dtc;  // the dt candidates are rebuilt every step
+        k_u8_to_f64<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(f.order, tmp, (int)N);
+        src = tmp;
+        bytes = N * nd;
+        break;
+    }
+    default: return fail(LMOOD_ERR_ARG, "lmood_get: unknown field id");
+    }
+    LM_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (!is_device) return sync_check(s, "lmood_get");
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_set(lmood_state s, int field, const void *src, int is_device) {
+    if (!s || !src) return fail(LMOOD_ERR_ARG, "lmood_set: NULL argument");
+    lmood_mesh M = s->M;
+    const int D = M->dim;
+    const size_t N = M->nc, Np = M->np, nd = sizeof(double);
+    cudaStream_t st = M->st;
+    Fld &f = s->f;
+    void *dst = nullptr;
+    size_t bytes = 0;
+    switch (field) {
+    case LMOOD_FIELD_X: dst = f.x; bytes = D * Np * nd; break;
+    case LMOOD_FIELD_VP: dst = f.vp; bytes = D * Np * nd; break;
+    case LMOOD_FIELD_V: dst = f.v; bytes = D * N * nd; break;
+    case LMOOD_FIELD_E: dst = f.e; bytes = N * nd; break;
+    case LMOOD_FIELD_F: dst = f.F; bytes = D * D * N * nd; break;
+    case LMOOD_FIELD_DT: dst = const_cast<double *>(f.dt); bytes = M->n_inst * nd; break;
+    default: return fail(LMOOD_ERR_ARG, "lmood_set: unknown or read-only field id");
+    }
+    LM_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (field == LMOOD_FIELD_X) {
+        std::swap(s->tau, f.tau1);
+        M->ops->refresh(M->geo, f, st);
+        std::swap(s->tau, f.tau1);
+    }
+    if (!is_device) return sync_check(s, "lmood_set");
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_totals(lmood_state s, double *out5) {
+    if (!s || !out5) return fail(LMOOD_ERR_ARG, "lmood_totals: NULL argument");
+    cudaStream_t st = s->M->st;
+    LM_CUDA(cudaMemsetAsync(s->totals, 0, 5 * sizeof(double), st));
+    s->M->ops->totals(s->M->geo, s->f, s->totals, st);
+    LM_CUDA(cudaMemcpyAsync(out5, s->totals, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return sync_check(s, "lmood_totals");
+}
+
+extern "C" lmood_status lmood_timing(lmood_state s, int enable) {
+    if (!s) return fail(LMOOD_ERR_ARG, "lmood_timing: NULL state");
+    if (enable && s->ev.empty()) {
+        s->ev.resize(2 * kMaxPending);
+        for (auto &e : s->ev) LM_CUDA(cudaEventCreate(&e));
+    }
+    LM_CUDA(cudaStreamSynchronize(s->M->st));
+    timing_drain(s);
+    if (enable) {
+        for (int i = 0; i < LMOOD_NK; ++i) {
+            s->kms[i] = 0;
+            s->klaunch[i] = 0;
+        }
+    }
+    s->timing = enable != 0;
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_timing_read(lmood_state s, double *ms, int64_t *launches) {
+    if (!s || !ms || !launches) return fail(LMOOD_ERR_ARG, "lmood_timing_read: NULL argument");
+    for (int i = 0; i < LMOOD_NK; ++i) {
+        ms[i] = s->kms[i];
+        launches[i] = s->klaunch[i];
+    }
+    return LMOOD_OK;
+}
+
+extern "C" const char *lmood_last_error(void) { return g_err.c_str(); }

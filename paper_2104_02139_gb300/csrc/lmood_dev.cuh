@@ -1,0 +1,253 @@
+// lmood_dev.cuh -- device-side data views and per-entity arithmetic of the Lagrangian
+// ADER-MOOD step (arXiv 2104.02139), templated on the space dimension D (2 or 3).
+//
+// Layout in HBM (all FP64 unless noted, structure of arrays, "[k][n]" = k runs of n):
+//   nodes : x, v_p^n, x^{n+1}, v_p^{n+1}, v*_p            [D][Np]
+//   cells : v [D][N], e [N], F [D*D][N] (row-major), and the same for the candidate;
+//           centroid x_c [D][N], rho [N] and tau [N] of the current and the candidate state;
+//           m, mu [N]; order, pad flag (u8) [N]; dt candidate [N]
+//   corner packets (corner id = k*N + c, k = local vertex):
+//           M_cp symmetric [D(D+1)/2][D+1][N], rhs_cp [D][D+1][N]
+//   adjacency (int32): c2n [D+1][N]; node -> corner CSR (ascending cell id);
+//           reconstruction stencil CSR (all cells sharing a node, ascending id)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lmood {
+
+struct Prm {
+    double cfl, Cv, Ci, delta0, delta1, dt_fixed, lam;
+    int base_order;  // order every cell starts the step with (2: P1, 1: P0)
+    int mood;        // detection on/off
+    int vol_coeff;   // 0: kappa = lambda + 2 mu / 3; 1: kappa = mu
+    int pad_;
+};
+
+struct Geo {
+    int N, Np, n_inst, pad_;
+    const int *c2n;
+    const int *n2c_off, *n2c;
+    const int *st_off, *st_idx;
+    const unsigned char *bc_ndof;  // free directions per node (D = free, 0 = clamped)
+    const double *bc_t;            // tangent vectors [2][3][Np]
+    const int *cell_inst, *node_inst;  // NULL for one instance
+};
+
+struct Fld {
+    const double *m, *mu;
+    double *x, *vp, *x1, *vp1, *vs;
+    double *v, *e, *F, *v1, *e1, *F1;
+    double *xc, *xc1, *rho, *rho1, *tau1;
+    double *pkM, *pkR;
+    unsigned char *order, *pflag;
+    double *dtc;
+    const double *dt;            // [n_inst] dt of this step
+    unsigned long long *dtn;     // [n_inst] bit pattern of the next dt (positive doubles order as integers)
+    int *cnt;                    // device counters, see CNT_*
+};
+
+enum { CNT_T0 = 0, CNT_T1 = 1, CNT_NODES = 2, CNT_CELLS = 3, CNT_P0 = 4, CNT_PARA = 5, CNT_EPS = 6, CNT_N = 8 };
+
+template <int D> struct Dim {
+    static constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2;
+};
+
+// index of (a,b) in symmetric storage: 2D (xx,xy,yy), 3D (xx,xy,xz,yy,yz,zz)
+template <int D> __host__ __device__ constexpr int sidx(int a, int b) {
+    return D == 2 ? a + b
+                  : (a <= b ? (a == 0 ? b : (a == 1 ? 2 + b : 5)) : (b == 0 ? a : (b == 1 ? 2 + a : 5)));
+}
+
+// ---------------------------------------------------------------------------------------
+// Simplex geometry (Sect. "Mesh and notation", Eq. def_lcpncp): outward area vector N_k of
+// the face opposite vertex k, corner vector l n_p = sum_{f != p} N_f / D (= d|w_c|/dx_p),
+// measure |w_c|.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void simplex_geometry(const double (&xs)[D + 1][D], double &V, double (&Nf)[D + 1][D],
+                                                 double (&ln)[D + 1][D]) {
+    if constexpr (D == 2) {
+        const double e1x = xs[1][0] - xs[0][0], e1y = xs[1][1] - xs[0][1];
+        const double e2x = xs[2][0] - xs[0][0], e2y = xs[2][1] - xs[0][1];
+        V = 0.5 * (e1x * e2y - e1y * e2x);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int a = (k + 1) % 3, b = (k + 2) % 3;
+            Nf[k][0] = xs[b][1] - xs[a][1];
+            Nf[k][1] = xs[a][0] - xs[b][0];
+        }
+    } else {
+        double e[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) e[k][a] = xs[k + 1][a] - xs[0][a];
+        const double c0 = e[1][1] * e[2][2] - e[1][2] * e[2][1];
+        const double c1 = e[1][2] * e[2][0] - e[1][0] * e[2][2];
+        const double c2 = e[1][0] * e[2][1] - e[1][1] * e[2][0];
+        V = (e[0][0] * c0 + e[0][1] * c1 + e[0][2] * c2) / 6.0;
+        // For a positively oriented tet the face opposite k, taken as (k+1, k+2, k+3) mod 4
+        // in this order, has normal (x_b - x_a) x (x_c - x_a) pointing outward for even k
+        // and inward for odd k.
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int fa = (k + 1) & 3, fb = (k + 2) & 3, fc = (k + 3) & 3;
+            const double u0 = xs[fb][0] - xs[fa][0], u1 = xs[fb][1] - xs[fa][1], u2 = xs[fb][2] - xs[fa][2];
+            const double w0 = xs[fc][0] - xs[fa][0], w1 = xs[fc][1] - xs[fa][1], w2 = xs[fc][2] - xs[fa][2];
+            const double s = (k & 1) ? -0.5 : 0.5;
+            Nf[k][0] = s * (u1 * w2 - u2 * w1);
+            Nf[k][1] = s * (u2 * w0 - u0 * w2);
+            Nf[k][2] = s * (u0 * w1 - u1 * w0);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < D + 1; ++p)
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            double s = 0.0;
+#pragma unroll
+            for (int f = 0; f < D + 1; ++f)
+                if (f != p) s += Nf[f][a] / D;
+            ln[p][a] = s;
+        }
+}
+
+// in-sphere diameter 2 D |w_c| / sum_f |N_f| (Sect. "Limiting", the characteristic length L_c)
+template <int D> __device__ __forceinline__ double insphere(double V, const double (&Nf)[D + 1][D]) {
+    double area = 0.0;
+#pragma unroll
+    for (int k = 0; k < D + 1; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) s += Nf[k][a] * Nf[k][a];
+        area += sqrt(s);
+    }
+    return 2.0 * D * V / area;
+}
+
+template <int D> __device__ __forceinline__ double det(const double (&A)[D * D]) {
+    if constexpr (D == 2) return A[0] * A[3] - A[1] * A[2];
+    else
+        return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+               A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+// adjugate / determinant
+template <int D> __device__ __forceinline__ void inverse(const double (&A)[D * D], double (&Ai)[D * D]) {
+    const double dt = det<D>(A);
+    if constexpr (D == 2) {
+        Ai[0] = A[3] / dt; Ai[1] = -A[1] / dt;
+        Ai[2] = -A[2] / dt; Ai[3] = A[0] / dt;
+    } else {
+        Ai[0] = (A[4] * A[8] - A[5] * A[7]) / dt;
+        Ai[1] = (A[2] * A[7] - A[1] * A[8]) / dt;
+        Ai[2] = (A[1] * A[5] - A[2] * A[4]) / dt;
+        Ai[3] = (A[5] * A[6] - A[3] * A[8]) / dt;
+        Ai[4] = (A[0] * A[8] - A[2] * A[6]) / dt;
+        Ai[5] = (A[2] * A[3] - A[0] * A[5]) / dt;
+        Ai[6] = (A[3] * A[7] - A[4] * A[6]) / dt;
+        Ai[7] = (A[1] * A[6] - A[0] * A[7]) / dt;
+        Ai[8] = (A[0] * A[4] - A[1] * A[3]) / dt;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void matmul(const double (&A)[D * D], const double (&B)[D * D], double (&C)[D * D]) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += A[i * D + k] * B[k * D + j];
+            C[i * D + j] = s;
+        }
+}
+
+// ---------------------------------------------------------------------------------------
+// Neo-Hookean Cauchy stress (Eqs. T_psi, EOS_neoHook, cstnh): T = -p I + (mu/J) dev(Bbar),
+// p = -(kappa/2)(J - 1 + log J / J), Bbar = J^{-2/3} F F^t. 2D is plane strain (F33 = 1).
+// ---------------------------------------------------------------------------------------
+struct Invariants {
+    double J, invJ, logJ;
+};
+
+template <int D> __device__ __forceinline__ Invariants invariants(const double (&F)[D * D]) {
+    Invariants r;
+    r.J = det<D>(F);
+    r.invJ = 1.0 / r.J;
+    r.logJ = log(r.J);
+    return r;
+}
+
+template <int D>
+__device__ __forceinline__ void stress(const double (&F)[D * D], double mu, double kappa, double (&T)[D * D]) {
+    const Invariants I = invariants<D>(F);
+    const double rc = rcbrt(I.J);
+    const double Jm23 = rc * rc;
+    const double p = -0.5 * kappa * (I.J - 1.0 + I.logJ * I.invJ);
+    const double coef = mu * I.invJ;
+    double B[D * D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += F[i * D + k] * F[j * D + k];
+            B[i * D + j] = s;
+        }
+    double tr = (D == 2) ? B[0] + B[3] + 1.0 : B[0] + B[4] + B[8];
+    const double third_trbar = Jm23 * tr / 3.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const double bb = Jm23 * B[i * D + j] - (i == j ? third_trbar : 0.0);
+            T[i * D + j] = (i == j ? -p : 0.0) + coef * bb;
+        }
+}
+
+// sound speed: a^2 = (K + 4 mu / (3 J)) / rho, K = -J dp/dJ = (kappa/2)(J + (1 - log J)/J)
+template <int D>
+__device__ __forceinline__ double sound_speed(const double (&F)[D * D], double rho, double mu, double kappa) {
+    const Invariants I = invariants<D>(F);
+    const double K = 0.5 * kappa * (I.J + (1.0 - I.logJ) * I.invJ);
+    return sqrt((K + 4.0 * mu / (3.0 * I.J)) / rho);
+}
+
+// specific free energy Psi = kappa/(4 rho0)((J-1)^2 + log^2 J) + mu/(2 rho0)(I1(Bbar) - 3)
+template <int D>
+__device__ __forceinline__ double free_energy(const double (&F)[D * D], double rho0, double mu, double kappa) {
+    const Invariants I = invariants<D>(F);
+    double trB = (D == 2) ? 1.0 : 0.0;
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) trB += F[i] * F[i];
+    const double rc = rcbrt(I.J);
+    const double I1bar = rc * rc * trB;
+    return kappa / (4.0 * rho0) * ((I.J - 1.0) * (I.J - 1.0) + I.logJ * I.logJ) +
+           mu / (2.0 * rho0) * (I1bar - 3.0);
+}
+
+__device__ __forceinline__ double kappa_of(const Prm &prm, double mu) {
+    return prm.vol_coeff ? mu : prm.lam + 2.0 * mu / 3.0;
+}
+
+// physical admissibility (Eq. PAD): 0 admissible, 1 only eps < -tol, 2 not computable
+template <int D>
+__device__ __forceinline__ int pad_state(const double (&v)[D], double e, const double (&F)[D * D], double V) {
+    bool fin = isfinite(e) && isfinite(V);
+#pragma unroll
+    for (int i = 0; i < D; ++i) fin = fin && isfinite(v[i]);
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) fin = fin && isfinite(F[i]);
+    if (!fin || !(V > 0.0) || !(det<D>(F) > 0.0)) return 2;
+    double ke = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) ke += 0.5 * v[i] * v[i];
+    const double eps = e - ke;
+    return eps >= -1e-10 * fmax(fabs(e), ke) ? 0 : 1;
+}
+
+}  // namespace lmood

@@ -1,0 +1,664 @@
+// lmood_kernels.cuh -- the kernels of one explicit Lagrangian ADER-MOOD step, templated
+// on the space dimension. Included by one translation unit per dimension.
+//
+// Per step (all cells / all nodes, then MOOD rounds over compacted lists):
+//   k_predict  cells : geometry at x^n, least-squares slopes of v and F, ADER predictor,
+//                      corner packets (M_cp, rhs_cp)
+//   k_nodes    nodes : ordered gather of the packets around the node, Eucclhyd solve with
+//                      boundary conditions, node motion
+//   k_update   cells : subcell forces, update of v, e, tau, F, detection, dt candidate
+//   k_mark_*         : troubled cells -> their nodes -> the cells around those nodes
+//   k_finalize       : next dt (exact min over cells) and the per-step counters
+#pragma once
+#include "lmood_dev.cuh"
+
+namespace lmood {
+
+constexpr int kCellBlock = 128;
+constexpr int kNodeBlock = 256;
+
+__device__ __forceinline__ bool list_entity(const int *list, const int *cnt, int n, int i, int &e) {
+    const int nn = list ? *cnt : n;
+    if (i >= nn) return false;
+    e = list ? list[i] : i;
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// k_predict: corner packets of a cell (Sect. "Space-Time discretization --- ADER
+// methodology", Eqs. Mcp^n, nodal_solver^n, subforce^n).
+//   P1: v and F reconstructed by least squares over the stencil, then the predictor
+//       v*_cp = v_h(x_p) + dt/2 (1/m_c) sum_q T(F_h(x_q)) ln_q,  F*_cp = F_h(x_p) + dt/2 L^ F_c
+//   P0: v*_cp = v_c, F*_cp = F_c.
+//   M_cp = z_c sum_{f containing p} |ln_f| n_f (x) n_f, rhs_cp = M_cp v*_cp - T(F*_cp) ln_p.
+// With a list, only the listed cells (troubled ones, already marked P0) are recomputed.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, const int *__restrict__ list,
+                                                        const int *__restrict__ cnt, int n) {
+    constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + DD;
+    int c;
+    if (!list_entity(list, cnt, n, blockIdx.x * blockDim.x + threadIdx.x, c)) return;
+    const int N = g.N, Np = g.Np;
+    int ord;
+    if (list) {
+        ord = f.order[c];
+    } else {
+        ord = prm.base_order;
+        f.order[c] = (unsigned char)ord;
+    }
+    const double dt = f.dt[g.cell_inst ? __ldg(g.cell_inst + c) : 0];
+    double xs[NV][D];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int p = __ldg(g.c2n + k * N + c);
+#pragma unroll
+        for (int a = 0; a < D; ++a) xs[k][a] = f.x[a * Np + p];
+    }
+    double V, Nf[NV][D], ln[NV][D];
+    simplex_geometry<D>(xs, V, Nf, ln);
+    double xcc[D], vc[D], Fc[DD];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        xcc[a] = f.xc[a * N + c];
+        vc[a] = f.v[a * N + c];
+    }
+#pragma unroll
+    for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
+    const double mc = f.m[c], muc = f.mu[c], kap = kappa_of(prm, muc);
+    const double rho = mc / V;
+    const double z = rho * sound_speed<D>(Fc, rho, muc, kap);
+    double wf[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) s += (Nf[k][a] / D) * (Nf[k][a] / D);
+        wf[k] = z / sqrt(s);
+    }
+    const int NC = NV * N;
+    auto emit = [&](int k, const double(&vst)[D], const double(&Tst)[DD]) {
+        double M[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) M[s] = 0.0;
+#pragma unroll
+        for (int fq = 0; fq < NV; ++fq) {
+            if (fq == k) continue;
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = a; b < D; ++b) M[sidx<D>(a, b)] += wf[fq] * (Nf[fq][a] / D) * (Nf[fq][b] / D);
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s) f.pkM[s * NC + k * N + c] = M[s];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            double mv = 0.0, tn = 0.0;
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+                mv += M[sidx<D>(a, b)] * vst[b];
+                tn += Tst[a * D + b] * ln[k][b];
+            }
+            f.pkR[a * NC + k * N + c] = mv - tn;
+        }
+    };
+    if (ord == 2) {
+        // least-squares slopes about centroids over the stencil (reading of Sect. "Algorithm")
+        double G[NS], r[NQ][D];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) G[s] = 0.0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int a = 0; a < D; ++a) r[q][a] = 0.0;
+        const int j1 = __ldg(g.st_off + c + 1);
+        for (int j = __ldg(g.st_off + c); j < j1; ++j) {
+            const int o = __ldg(g.st_idx + j);
+            double dx[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) dx[a] = f.xc[a * N + o] - xcc[a];
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = a; b < D; ++b) G[sidx<D>(a, b)] += dx[a] * dx[b];
+#pragma unroll
+            for (int q = 0; q < D; ++q) {
+                const double dq = f.v[q * N + o] - vc[q];
+#pragma unroll
+                for (int a = 0; a < D; ++a) r[q][a] += dx[a] * dq;
+            }
+#pragma unroll
+            for (int q = 0; q < DD; ++q) {
+                const double dq = f.F[q * N + o] - Fc[q];
+#pragma unroll
+                for (int a = 0; a < D; ++a) r[D + q][a] += dx[a] * dq;
+            }
+        }
+        double Gf[DD], Gi[DD], gs[NQ][D];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = 0; b < D; ++b) Gf[a * D + b] = G[sidx<D>(a, b)];
+        double tr = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) tr += Gf[a * D + a];
+        const double t = tr / D;
+        const double tD = D == 2 ? t * t : t * t * t;
+        const bool ok = det<D>(Gf) > 1e-12 * tD;
+        inverse<D>(Gf, Gi);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                double s = 0.0;
+#pragma unroll
+                for (int b = 0; b < D; ++b) s += Gi[a * D + b] * r[q][b];
+                gs[q][a] = ok ? s : 0.0;
+            }
+        // predictor, pass 1: cell-averaged time derivative of v from the corner stresses
+        double dvdt[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) dvdt[a] = 0.0;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double dx[D], Fh[DD], T[DD];
+#pragma unroll
+            for (int a = 0; a < D; ++a) dx[a] = xs[k][a] - xcc[a];
+#pragma unroll
+            for (int q = 0; q < DD; ++q) {
+                double s = Fc[q];
+#pragma unroll
+                for (int a = 0; a < D; ++a) s += gs[D + q][a] * dx[a];
+                Fh[q] = s;
+            }
+            stress<D>(Fh, muc, kap, T);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                double s = 0.0;
+#pragma unroll
+                for (int b = 0; b < D; ++b) s += T[i * D + b] * ln[k][b];
+                dvdt[i] += s;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) dvdt[a] /= mc;
+        double gv[DD], dFdt[DD];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int a = 0; a < D; ++a) gv[i * D + a] = gs[i][a];
+        matmul<D>(gv, Fc, dFdt);
+        // pass 2: corner values at t^{n+1/2} and packets
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double dx[D], vst[D], Fs[DD], T[DD];
+#pragma unroll
+            for (int a = 0; a < D; ++a) dx[a] = xs[k][a] - xcc[a];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                double s = vc[i];
+#pragma unroll
+                for (int a = 0; a < D; ++a) s += gs[i][a] * dx[a];
+                vst[i] = s + 0.5 * dt * dvdt[i];
+            }
+#pragma unroll
+            for (int q = 0; q < DD; ++q) {
+                double s = Fc[q];
+#pragma unroll
+                for (int a = 0; a < D; ++a) s += gs[D + q][a] * dx[a];
+                Fs[q] = s + 0.5 * dt * dFdt[q];
+            }
+            stress<D>(Fs, muc, kap, T);
+            emit(k, vst, T);
+        }
+    } else {
+        double T[DD];
+        stress<D>(Fc, muc, kap, T);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) emit(k, vc, T);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// k_nodes: Eucclhyd nodal solver (Eqs. nodal_solver^n, Mcp^n) with the BCs of Appendix B:
+// M_p = sum_c M_cp, b_p = sum_c rhs_cp in ascending cell id, v*_p the Galerkin solution of
+// M_p v = b_p on the node's free directions (Eq. sBC1); then x^{n+1} = x^n + dt v*_p and
+// v_p^{n+1} = 2 v*_p - v_p^n. init_mode stores v*_p as v_p^0 and moves nothing.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kNodeBlock) k_nodes(Geo g, Fld f, const int *__restrict__ list,
+                                                      const int *__restrict__ cnt, int n, int init_mode) {
+    constexpr int NV = D + 1, NS = D * (D + 1) / 2, DD = D * D;
+    int p;
+    if (!list_entity(list, cnt, n, blockIdx.x * blockDim.x + threadIdx.x, p)) return;
+    const int Np = g.Np, NC = NV * g.N;
+    double Ms[NS], b[D];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) Ms[s] = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) b[a] = 0.0;
+    const int j1 = __ldg(g.n2c_off + p + 1);
+    for (int j = __ldg(g.n2c_off + p); j < j1; ++j) {
+        const int cid = __ldg(g.n2c + j);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) Ms[s] += f.pkM[s * NC + cid];
+#pragma unroll
+        for (int a = 0; a < D; ++a) b[a] += f.pkR[a * NC + cid];
+    }
+    double M[DD];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int c = 0; c < D; ++c) M[a * D + c] = Ms[sidx<D>(a, c)];
+    const int nd = g.bc_ndof[p];
+    double v[D];
+    if (nd == D) {
+        double Mi[DD];
+        inverse<D>(M, Mi);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) s += Mi[a * D + c] * b[c];
+            v[a] = s;
+        }
+    } else if (nd == 0) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) v[a] = 0.0;
+    } else {
+        double t[2][D], A[4], r[2], al[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int a = 0; a < D; ++a) t[i][a] = g.bc_t[(i * 3 + a) * Np + p];
+        for (int i = 0; i < nd; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a < D; ++a) s += t[i][a] * b[a];
+            r[i] = s;
+            for (int j = 0; j < nd; ++j) {
+                double q = 0.0;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    double mt = 0.0;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) mt += M[a * D + c] * t[j][c];
+                    q += t[i][a] * mt;
+                }
+                A[i * nd + j] = q;
+            }
+        }
+        if (nd == 1) {
+            al[0] = r[0] / A[0];
+            al[1] = 0.0;
+        } else {
+            const double dA = A[0] * A[3] - A[1] * A[2];
+            al[0] = (A[3] / dA) * r[0] + (-A[1] / dA) * r[1];
+            al[1] = (-A[2] / dA) * r[0] + (A[0] / dA) * r[1];
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            double s = 0.0;
+            for (int i = 0; i < nd; ++i) s += al[i] * t[i][a];
+            v[a] = s;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) f.vs[a * Np + p] = v[a];
+    if (init_mode) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) f.vp[a * Np + p] = v[a];
+        return;
+    }
+    const double dt = f.dt[g.node_inst ? __ldg(g.node_inst + p) : 0];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        f.x1[a * Np + p] = f.x[a * Np + p] + dt * v[a];
+        f.vp1[a * Np + p] = 2.0 * v[a] - f.vp[a * Np + p];
+    }
+}
+
+// velocity gradient L_ij = (1/|w_c|) sum_p v_{p,i} ln_{p,j} (Eq. div_grad_v, read so that
+// dF/dt = L F)
+template <int D>
+__device__ __forceinline__ void vel_gradient(const double (&vn)[D + 1][D], const double (&ln)[D + 1][D], double V,
+                                             double (&L)[D * D]) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < D + 1; ++k) s += vn[k][i] * ln[k][j];
+            L[i * D + j] = s / V;
+        }
+}
+
+// ---------------------------------------------------------------------------------------
+// k_update: subcell forces f_cp = M_cp v*_p - rhs_cp and the cell update (Eqs. tau_c^n,
+// v_c^n, e_c^n, firstB, CN_B): tau^{n+1} = |w_c(x^{n+1})| / m_c; F by Crank-Nicolson (P1)
+// or explicit Euler (P0). Then detection (Eqs. PAD, RDMP) and the dt candidate (Eq. CFL2).
+// P1 cells that fail are appended to tlist.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kCellBlock) k_update(Geo g, Fld f, Prm prm, const int *__restrict__ list,
+                                                       const int *__restrict__ cnt, int n, int *tlist, int *tcnt) {
+    constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2;
+    int c;
+    if (!list_entity(list, cnt, n, blockIdx.x * blockDim.x + threadIdx.x, c)) return;
+    const int N = g.N, Np = g.Np, NC = NV * N;
+    const int ord = f.order[c];
+    const double dt = f.dt[g.cell_inst ? __ldg(g.cell_inst + c) : 0];
+    int nod[NV];
+    double xs0[NV][D], xs1[NV][D], vsn[NV][D];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        nod[k] = __ldg(g.c2n + k * N + c);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            xs0[k][a] = f.x[a * Np + nod[k]];
+            xs1[k][a] = f.x1[a * Np + nod[k]];
+            vsn[k][a] = f.vs[a * Np + nod[k]];
+        }
+    }
+    double sf[D], sfv = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) sf[a] = 0.0;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double M[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) M[s] = f.pkM[s * NC + k * N + c];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            double s = 0.0;
+#pragma unroll
+            for (int b = 0; b < D; ++b) s += M[sidx<D>(a, b)] * vsn[k][b];
+            const double fa = s - f.pkR[a * NC + k * N + c];
+            sf[a] += fa;
+            sfv += fa * vsn[k][a];
+        }
+    }
+    const double mc = f.m[c], muc = f.mu[c], kap = kappa_of(prm, muc);
+    double v1[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) v1[a] = f.v[a * N + c] + dt / mc * sf[a];
+    const double e1 = f.e[c] + dt / mc * sfv;
+    double V0, Nf0[NV][D], ln0[NV][D], V1, Nf1[NV][D], ln1[NV][D];
+    simplex_geometry<D>(xs0, V0, Nf0, ln0);
+    simplex_geometry<D>(xs1, V1, Nf1, ln1);
+    double Fn[DD], F1[DD];
+#pragma unroll
+    for (int q = 0; q < DD; ++q) Fn[q] = f.F[q * N + c];
+    if (ord == 2) {
+        double vn[NV][D], L0[DD], L1[DD], A[DD], Bm[DD], Ai[DD], R[DD];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+            for (int a = 0; a < D; ++a) vn[k][a] = f.vp[a * Np + nod[k]];
+        vel_gradient<D>(vn, ln0, V0, L0);
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+            for (int a = 0; a < D; ++a) vn[k][a] = f.vp1[a * Np + nod[k]];
+        vel_gradient<D>(vn, ln1, V1, L1);
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const double id = i == j ? 1.0 : 0.0;
+                A[i * D + j] = id - 0.5 * dt * L1[i * D + j];
+                Bm[i * D + j] = id + 0.5 * dt * L0[i * D + j];
+            }
+        matmul<D>(Bm, Fn, R);
+        inverse<D>(A, Ai);
+        matmul<D>(Ai, R, F1);
+    } else {
+        double Ls[DD], LF[DD];
+        vel_gradient<D>(vsn, ln0, V0, Ls);
+        matmul<D>(Ls, Fn, LF);
+#pragma unroll
+        for (int q = 0; q < DD; ++q) F1[q] = Fn[q] + dt * LF[q];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        f.v1[a * N + c] = v1[a];
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s += xs1[k][a];
+        f.xc1[a * N + c] = s / NV;
+    }
+    f.e1[c] = e1;
+#pragma unroll
+    for (int q = 0; q < DD; ++q) f.F1[q * N + c] = F1[q];
+    const double rho1 = mc / V1;
+    f.rho1[c] = rho1;
+    f.tau1[c] = V1 / mc;
+    if (prm.mood) {
+        const int ps = pad_state<D>(v1, e1, F1, V1);
+        if (ord == 2) {
+            bool bad = ps != 0;
+            if (!bad) {
+                double lo = f.rho[c], hi = lo;
+                const int j1 = __ldg(g.st_off + c + 1);
+                for (int j = __ldg(g.st_off + c); j < j1; ++j) {
+                    const double r = f.rho[__ldg(g.st_idx + j)];
+                    lo = fmin(lo, r);
+                    hi = fmax(hi, r);
+                }
+                const double delta = fmax(prm.delta0, prm.delta1 * (hi - lo));
+                bad = !(rho1 >= lo - delta && rho1 <= hi + delta);
+            }
+            if (bad) tlist[atomicAdd(tcnt, 1)] = c;
+        } else {
+            f.pflag[c] = (unsigned char)ps;
+        }
+    }
+    double dtc = prm.cfl * insphere<D>(V1, Nf1) / sound_speed<D>(F1, rho1, muc, kap);
+    const double dV = V1 - V0;
+    if (dV != 0.0) dtc = fmin(dtc, prm.Cv * dt * V0 / fabs(dV));
+    f.dtc[c] = dtc;
+}
+
+// troubled cells become P0; their nodes are appended (once) to the node list
+template <int D>
+__global__ void k_mark_nodes(Geo g, Fld f, const int *__restrict__ tlist, const int *__restrict__ tcnt,
+                             int *node_mark, int stamp, int *nlist) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *tcnt) return;
+    const int c = tlist[i];
+    f.order[c] = 1;
+#pragma unroll
+    for (int k = 0; k < D + 1; ++k) {
+        const int p = __ldg(g.c2n + k * g.N + c);
+        if (atomicExch(node_mark + p, stamp) != stamp) nlist[atomicAdd(f.cnt + CNT_NODES, 1)] = p;
+    }
+}
+
+// every cell around a listed node is appended (once) to the cell list
+static __global__ void k_mark_cells(Geo g, Fld f, const int *__restrict__ nlist, int *cell_mark, int stamp, int *clist) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= f.cnt[CNT_NODES]) return;
+    const int p = nlist[i];
+    const int j1 = g.n2c_off[p + 1];
+    for (int j = g.n2c_off[p]; j < j1; ++j) {
+        const int c = g.n2c[j] % g.N;
+        if (atomicExch(cell_mark + c, stamp) != stamp) clist[atomicAdd(f.cnt + CNT_CELLS, 1)] = c;
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// dtn[inst] = (1 + C_i) dt[inst] (or dt_fixed, or +inf when ci < 0: initial acoustic dt)
+static __global__ void k_dt_init(Fld f, Prm prm, int n_inst, int first) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inst) return;
+    double d;
+    if (prm.dt_fixed > 0) d = prm.dt_fixed;
+    else if (first) d = __longlong_as_double(0x7ff0000000000000LL);
+    else d = (1.0 + prm.Ci) * f.dt[i];
+    f.dtn[i] = (unsigned long long)__double_as_longlong(d);
+}
+
+// min of the dt candidates per instance (positive doubles compare as their bit patterns, so
+// the result is exact and independent of the order) and the P0 / parachute counters
+static __global__ void __launch_bounds__(256) k_finalize(Geo g, Fld f, Prm prm) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = c < g.N;
+    unsigned long long bits = ~0ull;
+    int p0 = 0, para = 0, eps = 0;
+    int inst = 0;
+    if (in) {
+        if (!(prm.dt_fixed > 0)) bits = (unsigned long long)__double_as_longlong(f.dtc[c]);
+        const int o = f.order[c];
+        p0 = o == 1;
+        const int pf = f.pflag[c];
+        para = p0 && pf == 2;
+        eps = p0 && pf == 1;
+        inst = g.cell_inst ? g.cell_inst[c] : 0;
+    }
+    // blocks whose cells all belong to one instance reduce before the atomic
+    const int c0 = blockIdx.x * blockDim.x, c1 = min(g.N, c0 + (int)blockDim.x) - 1;
+    const bool uniform = !g.cell_inst || g.cell_inst[c0] == g.cell_inst[c1];
+    __shared__ unsigned long long sb[8];
+    __shared__ int si[8][3];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    p0 = warp_sum_i(p0);
+    para = warp_sum_i(para);
+    eps = warp_sum_i(eps);
+    if (lane == 0) {
+        si[w][0] = p0;
+        si[w][1] = para;
+        si[w][2] = eps;
+    }
+    if (uniform) {
+        const unsigned long long m = warp_min_u64(bits);
+        if (lane == 0) sb[w] = m;
+    } else if (in && bits != ~0ull) {
+        atomicMin(f.dtn + inst, bits);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a = 0, b = 0, e = 0;
+        unsigned long long m = ~0ull;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            a += si[q][0];
+            b += si[q][1];
+            e += si[q][2];
+            if (uniform) m = sb[q] < m ? sb[q] : m;
+        }
+        if (a) atomicAdd(f.cnt + CNT_P0, a);
+        if (b) atomicAdd(f.cnt + CNT_PARA, b);
+        if (e) atomicAdd(f.cnt + CNT_EPS, e);
+        if (uniform && m != ~0ull) atomicMin(f.dtn + (g.cell_inst ? g.cell_inst[c0] : 0), m);
+    }
+}
+
+// initial cell state: m = rho0 |w_c|, centroid, rho, tau, F (identity when not given),
+// e = |v|^2/2 + Psi(F), acoustic dt candidate
+template <int D>
+__global__ void __launch_bounds__(kCellBlock) k_init_cells(Geo g, Fld f, Prm prm, double rho0, double *m_out,
+                                                           int f_given) {
+    constexpr int NV = D + 1, DD = D * D;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    const int N = g.N, Np = g.Np;
+    double xs[NV][D];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int p = g.c2n[k * N + c];
+#pragma unroll
+        for (int a = 0; a < D; ++a) xs[k][a] = f.x[a * Np + p];
+    }
+    double V, Nf[NV][D], ln[NV][D];
+    simplex_geometry<D>(xs, V, Nf, ln);
+    const double mc = rho0 * V;
+    m_out[c] = mc;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s += xs[k][a];
+        f.xc[a * N + c] = s / NV;
+    }
+    const double rho = mc / V;
+    f.rho[c] = rho;
+    f.tau1[c] = V / mc;
+    double F[DD];
+#pragma unroll
+    for (int q = 0; q < DD; ++q) {
+        F[q] = f_given ? f.F[q * N + c] : ((q % (D + 1)) == 0 ? 1.0 : 0.0);
+        f.F[q * N + c] = F[q];
+    }
+    const double muc = f.mu[c], kap = kappa_of(prm, muc);
+    double ke = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const double va = f.v[a * N + c];
+        ke += 0.5 * va * va;
+    }
+    f.e[c] = ke + free_energy<D>(F, rho0, muc, kap);
+    f.order[c] = 1;
+    f.pflag[c] = 0;
+    f.dtc[c] = prm.cfl * insphere<D>(V, Nf) / sound_speed<D>(F, rho, muc, kap);
+}
+
+// derived geometry of the current positions: centroid, rho = m / |w_c|, tau = |w_c| / m
+template <int D> __global__ void __launch_bounds__(kCellBlock) k_refresh(Geo g, Fld f) {
+    constexpr int NV = D + 1;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    double xs[NV][D];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int p = g.c2n[k * g.N + c];
+#pragma unroll
+        for (int a = 0; a < D; ++a) xs[k][a] = f.x[a * g.Np + p];
+    }
+    double V, Nf[NV][D], ln[NV][D];
+    simplex_geometry<D>(xs, V, Nf, ln);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s += xs[k][a];
+        f.xc[a * g.N + c] = s / NV;
+    }
+    f.rho[c] = f.m[c] / V;
+    f.tau1[c] = V / f.m[c];
+}
+
+// sums of m, m v, m e (diagnostic; atomics, so the last bits depend on scheduling)
+template <int D> __global__ void __launch_bounds__(256) k_totals(Geo g, Fld f, double *out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    double q[5] = {0, 0, 0, 0, 0};
+    if (c < g.N) {
+        const double m = f.m[c];
+        q[0] = m;
+#pragma unroll
+        for (int a = 0; a < D; ++a) q[1 + a] = m * f.v[a * g.N + c];
+        q[4] = m * f.e[c];
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        double v = q[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out + i, v);
+    }
+}
+
+}  // namespace lmood

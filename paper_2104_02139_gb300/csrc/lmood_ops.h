@@ -1,0 +1,28 @@
+// lmood_ops.h -- per-dimension launch table of the step kernels (one translation unit per
+// dimension fills it).
+#pragma once
+#include "lmood_dev.cuh"
+
+namespace lmood {
+
+struct Ops {
+    int dim;
+    void (*predict)(const Geo &, const Fld &, const Prm &, const int *list, const int *cnt, int n, cudaStream_t);
+    void (*nodes)(const Geo &, const Fld &, const int *list, const int *cnt, int n, int init_mode, cudaStream_t);
+    void (*update)(const Geo &, const Fld &, const Prm &, const int *list, const int *cnt, int n, int *tlist,
+                   int *tcnt, cudaStream_t);
+    void (*mark_nodes)(const Geo &, const Fld &, const int *tlist, const int *tcnt, int n, int *node_mark,
+                       int stamp, int *nlist, cudaStream_t);
+    void (*mark_cells)(const Geo &, const Fld &, const int *nlist, int n, int *cell_mark, int stamp, int *clist,
+                       cudaStream_t);
+    void (*dt_init)(const Fld &, const Prm &, int n_inst, int first, cudaStream_t);
+    void (*finalize)(const Geo &, const Fld &, const Prm &, cudaStream_t);
+    void (*init_cells)(const Geo &, const Fld &, const Prm &, double rho0, double *m, int f_given, cudaStream_t);
+    void (*refresh)(const Geo &, const Fld &, cudaStream_t);
+    void (*totals)(const Geo &, const Fld &, double *out, cudaStream_t);
+};
+
+const Ops &ops_dim2();
+const Ops &ops_dim3();
+
+}  // namespace lmood
