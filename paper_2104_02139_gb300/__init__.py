@@ -182,6 +182,8 @@ class State:
 
     def shape(self, field: int) -> tuple:
         d, nc, npn, nv = self.mesh.dim, self.mesh.n_cells, self.mesh.n_nodes, self.mesh.dim + 1
+        if not 0 <= field <= FIELD_DT:
+            return (1,)  # the library rejects the id
         return {FIELD_X: (d, npn), FIELD_VP: (d, npn), FIELD_VSTAR: (d, npn), FIELD_V: (d, nc), FIELD_E: (nc,),
                 FIELD_F: (d * d, nc), FIELD_TAU: (nc,), FIELD_ORDER: (nc,), FIELD_MASS: (nc,),
                 FIELD_PKM: (d * (d + 1) // 2, nv, nc), FIELD_PKR: (d, nv, nc), FIELD_DT: (self.mesh.n_inst,)}[field]

@@ -17,7 +17,7 @@ def _status(fn):
 
 
 def test_mesh_errors():
-    m = W.tri_mesh(6, 1)
+    m = W.tri_mesh(6, 1, bc={"x0": W.SLIP})
     bad = m.c2n.copy()
     bad[[1, 2]] = bad[[2, 1]]  # clockwise triangles
     assert _status(lambda: L.Mesh(2, m.x, bad)) == L.ERR_MESH

@@ -260,13 +260,16 @@ def column3d(nxy: int = 55, nz: int = 330, seed: int = 3, steps: int = 500) -> P
 def cube3d(n: int = 44, seed: int = 5, steps: int = 400) -> Problem:
     """Unit cube of Kuhn tetrahedra (44^3 cubes give 511,104 cells), slip walls; rho0=1,
     lambda=2; per-cell mu = 1 + 0.2 g(x) with g a seeded unit-variance Gaussian random field
-    (64 Fourier modes, correlation length 0.15); v0 = 0.05 sin(pi x) sin(pi y) sin(pi z) (1,1,1)."""
+    (64 Fourier modes, correlation length 0.15); v0 a smooth divergence-free Taylor-Green field
+    with zero normal component on the walls, 0.05 (sin(pi x) cos(pi y) cos(pi z),
+    cos(pi x) sin(pi y) cos(pi z), -2 cos(pi x) cos(pi y) sin(pi z))."""
     bc = {s: SLIP for s in ("x0", "x1", "y0", "y1", "z0", "z1")}
     m = tet_mesh(n, n, n, seed, bc=bc)
     p = cell_points(m)
     mu = 1.0 + 0.2 * gaussian_random_field(p, seed + 10_000)
-    s = 0.05 * np.sin(np.pi * p[:, 0]) * np.sin(np.pi * p[:, 1]) * np.sin(np.pi * p[:, 2])
-    v = np.stack([s, s, s])
+    sx, sy, sz = (np.sin(np.pi * p[:, a]) for a in range(3))
+    cx, cy, cz = (np.cos(np.pi * p[:, a]) for a in range(3))
+    v = 0.05 * np.stack([sx * cy * cz, cx * sy * cz, -2.0 * cx * cy * sz])
     return Problem(f"cube3d_n{n}", m, 1.0, 2.0, mu, v, 0.25, steps)
 
 
