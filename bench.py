@@ -54,13 +54,45 @@ def kernel_bytes(dim: int, nc: int, npn: int, nnz: int) -> dict:
     NS = D * (D + 1) // 2
     d8 = 8
     pk = d8 * (NS + D) * NV * nc
+    # predict: c2n, x, own (xc, v, F) (neighbours' are the same arrays), stencil CSR,
+    # mu, z, 1/m; writes packets and the order byte
     predict = (4 * NV * nc + d8 * D * npn + d8 * (2 * D + D * D) * nc + 4 * (nc + 1) + 4 * nnz
-               + 2 * d8 * nc + pk + nc)
+               + 3 * d8 * nc + pk + nc)
+    # nodes: CSR, packets, BC byte, x, v_p^n; writes v*, x^{n+1}, v_p^{n+1}
     nodes = 4 * (npn + 1) + 4 * NV * nc + pk + npn + 2 * d8 * D * npn + 3 * d8 * D * npn
-    update = (4 * NV * nc + 5 * d8 * D * npn + pk + d8 * (D + 1 + D * D + 2) * nc + nc + d8 * nc
-              + 4 * (nc + 1) + 4 * nnz + d8 * (D + 1 + D * D + D + 2) * nc + d8 * nc)
+    # update: c2n, 5 node arrays, packets, v e F m 1/m mu, order, rho (stencil), stencil CSR;
+    # writes v e F xc rho tau z, dt candidate
+    update = (4 * NV * nc + 5 * d8 * D * npn + pk + d8 * (D + 1 + D * D + 3) * nc + nc + d8 * nc
+              + 4 * (nc + 1) + 4 * nnz + d8 * (D + 1 + D * D + D + 3) * nc + d8 * nc)
     finalize = d8 * nc + 2 * nc
     return {"predict": predict, "nodes": nodes, "update": update, "finalize": finalize}
+
+
+# FP64 floating-point operations per cell executed by each full-mesh kernel launch on the 2D
+# workload: ncu counts (dadd + dmul + 2 dfma thread instructions) of the current kernels,
+# divided by the cell count; they include the FP64 expansions of division, sqrt, log, cbrt.
+# Re-measured whenever a kernel changes (profiles/ holds the capture); None = not measured
+# for the current kernel.
+FP64_FLOP_PER_CELL = {"predict": None, "update": None, "nodes": None}
+# DRAM bytes (read + write) per full launch from the same ncu capture, or None.
+TRAFFIC_PER_LAUNCH = {"predict": None, "update": None, "nodes": None}
+
+
+def fp64_peak_tflops(device) -> float:
+    """Measured FP64 peak: cuBLAS DGEMM 4096^3, best of 3 (CUDA events)."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=device)
+    b = torch.randn(n, n, dtype=torch.float64, device=device)
+    best = float("inf")
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2 * n ** 3 / (best / 1e3) / 1e12
 
 
 class Clocks:
@@ -202,15 +234,28 @@ def run_ours(args, rank, local, ws, dist):
     ms_max = max_over_ranks(ms, dist)
     value = ws * N * args.steps / (ms_max / 1e3)
 
-    # roofline of the dominant kernel class (full-mesh launches; MOOD rounds excluded)
+    # roofline of the dominant kernel class (full-mesh launches; MOOD rounds excluded). The
+    # step is bound by the FP64 pipe: roofline = FP64 FLOP/s against the FP64 peak, with the
+    # HBM figure beside it.
     peaks, how = _peaks()
     kb = kernel_bytes(2, N, info["n_nodes"], info["stencil_nnz"])
     dom = max(("predict", "nodes", "update"), key=lambda k: kt[k][0])
     dom_ms = kt[dom][0] / max(kt[dom][1], 1)
-    achieved = kb[dom] / (dom_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": how,
-            "algorithmic_bytes_per_launch": kb[dom], "ms_per_launch": dom_ms}
+    gbs = kb[dom] / (dom_ms / 1e3) / 1e9
+    fp64_meas = fp64_peak_tflops(f"cuda:{local}")
+    hbm = {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+           "algorithmic_bytes_per_launch": kb[dom], "peak_source": how}
+    fpc = FP64_FLOP_PER_CELL.get(dom)
+    if fpc:
+        tf = fpc * N / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": tf, "peak": fp64_meas, "unit": "TFLOP/s",
+                "frac": tf / fp64_meas, "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+                "peak_source": "measured cuBLAS DGEMM in this run (nominal 1.26)",
+                "fp64_flop_per_cell": fpc, "ms_per_launch": dom_ms, "hbm": hbm}
+    else:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": how,
+                "algorithmic_bytes_per_launch": kb[dom], "ms_per_launch": dom_ms, "fp64_peak_measured": fp64_meas}
     kernels = {k: {"ms_total": v[0], "launches": v[1]} for k, v in kt.items()}
     launches = sum(v[1] for v in kt.values())
 

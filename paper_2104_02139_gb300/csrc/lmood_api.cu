@@ -354,7 +354,7 @@ struct lmood_state_s {
     lmood_material mat{};
     Prm kp{};
     Fld f{};
-    double *tau = nullptr, *m = nullptr, *mu = nullptr;
+    double *tau = nullptr, *m = nullptr, *im = nullptr, *mu = nullptr;
     int *tl[2] = {nullptr, nullptr}, *nlist = nullptr, *clist = nullptr, *node_mark = nullptr, *cell_mark = nullptr;
     double *totals = nullptr;
     int *h_cnt = nullptr;      // pinned mirror of the device counters
@@ -407,6 +407,7 @@ static void swap_state(lmood_state s) {
     std::swap(f.xc, f.xc1);
     std::swap(f.rho, f.rho1);
     std::swap(s->tau, f.tau1);
+    std::swap(f.z, f.z1);
     double *dt = const_cast<double *>(f.dt);
     f.dt = (const double *)f.dtn;
     f.dtn = (unsigned long long *)dt;
@@ -495,6 +496,9 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
     A((void **)&s->tau, N * nd);
     A((void **)&f.tau1, N * nd);
     A((void **)&s->m, N * nd);
+    A((void **)&s->im, N * nd);
+    A((void **)&f.z, N * nd);
+    A((void **)&f.z1, N * nd);
     A((void **)&s->mu, N * nd);
     A((void **)&f.pkM, (size_t)NS * NV * N * nd);
     A((void **)&f.pkR, (size_t)D * NV * N * nd);
@@ -523,6 +527,7 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
         return fail(LMOOD_ERR_OOM, "lmood_state_init: pinned host allocation failed");
     }
     f.m = s->m;
+    f.im = s->im;
     f.mu = s->mu;
     f.dt = dt0;
     f.dtn = (unsigned long long *)dt1;
@@ -544,7 +549,7 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
         const Ops &op = *M->ops;
         Prm p0 = s->kp;
         p0.base_order = 1;
-        op.init_cells(M->geo, f, p0, mat->rho0, s->m, F_cell ? 1 : 0, st);
+        op.init_cells(M->geo, f, p0, mat->rho0, s->m, s->im, F_cell ? 1 : 0, st);
         std::swap(s->tau, f.tau1);
         op.predict(M->geo, f, p0, nullptr, nullptr, (int)N, st);
         op.nodes(M->geo, f, nullptr, nullptr, (int)Np, 1, st);
@@ -715,9 +720,9 @@ extern "C" lmood_status lmood_set(lmood_state s, int field, const void *src, int
     default: return fail(LMOOD_ERR_ARG, "lmood_set: unknown or read-only field id");
     }
     LM_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    if (field == LMOOD_FIELD_X) {
+    if (field == LMOOD_FIELD_X || field == LMOOD_FIELD_F) {
         std::swap(s->tau, f.tau1);
-        M->ops->refresh(M->geo, f, st);
+        M->ops->refresh(M->geo, f, s->kp, st);
         std::swap(s->tau, f.tau1);
     }
     if (!is_device) return sync_check(s, "lmood_set");

@@ -4,8 +4,8 @@
 // Layout in HBM (all FP64 unless noted, structure of arrays, "[k][n]" = k runs of n):
 //   nodes : x, v_p^n, x^{n+1}, v_p^{n+1}, v*_p            [D][Np]
 //   cells : v [D][N], e [N], F [D*D][N] (row-major), and the same for the candidate;
-//           centroid x_c [D][N], rho [N] and tau [N] of the current and the candidate state;
-//           m, mu [N]; order, pad flag (u8) [N]; dt candidate [N]
+//           centroid x_c [D][N], rho, tau and impedance z [N] of the current and the
+//           candidate state; m, 1/m, mu [N]; order, pad flag (u8) [N]; dt candidate [N]
 //   corner packets (corner id = k*N + c, k = local vertex):
 //           M_cp symmetric [D(D+1)/2][D+1][N], rhs_cp [D][D+1][N]
 //   adjacency (int32): c2n [D+1][N]; node -> corner CSR (ascending cell id);
@@ -39,6 +39,8 @@ struct Fld {
     double *x, *vp, *x1, *vp1, *vs;
     double *v, *e, *F, *v1, *e1, *F1;
     double *xc, *xc1, *rho, *rho1, *tau1;
+    double *z, *z1;              // acoustic impedance rho a of the current / candidate state
+    const double *im;            // 1 / m_c
     double *pkM, *pkR;
     unsigned char *order, *pflag;
     double *dtc;
@@ -61,12 +63,11 @@ template <int D> __host__ __device__ constexpr int sidx(int a, int b) {
 
 // ---------------------------------------------------------------------------------------
 // Simplex geometry (Sect. "Mesh and notation", Eq. def_lcpncp): outward area vector N_k of
-// the face opposite vertex k, corner vector l n_p = sum_{f != p} N_f / D (= d|w_c|/dx_p),
-// measure |w_c|.
+// the face opposite vertex k and the measure |w_c|. The corner vector is
+// l n_p = sum_{f != p} N_f / D = -N_p / D (the face vectors of a closed simplex sum to zero).
 // ---------------------------------------------------------------------------------------
 template <int D>
-__device__ __forceinline__ void simplex_geometry(const double (&xs)[D + 1][D], double &V, double (&Nf)[D + 1][D],
-                                                 double (&ln)[D + 1][D]) {
+__device__ __forceinline__ void simplex_faces(const double (&xs)[D + 1][D], double &V, double (&Nf)[D + 1][D]) {
     if constexpr (D == 2) {
         const double e1x = xs[1][0] - xs[0][0], e1y = xs[1][1] - xs[0][1];
         const double e2x = xs[2][0] - xs[0][0], e2y = xs[2][1] - xs[0][1];
@@ -86,7 +87,7 @@ __device__ __forceinline__ void simplex_geometry(const double (&xs)[D + 1][D], d
         const double c0 = e[1][1] * e[2][2] - e[1][2] * e[2][1];
         const double c1 = e[1][2] * e[2][0] - e[1][0] * e[2][2];
         const double c2 = e[1][0] * e[2][1] - e[1][1] * e[2][0];
-        V = (e[0][0] * c0 + e[0][1] * c1 + e[0][2] * c2) / 6.0;
+        V = (e[0][0] * c0 + e[0][1] * c1 + e[0][2] * c2) * (1.0 / 6.0);
         // For a positively oriented tet the face opposite k, taken as (k+1, k+2, k+3) mod 4
         // in this order, has normal (x_b - x_a) x (x_c - x_a) pointing outward for even k
         // and inward for odd k.
@@ -101,19 +102,24 @@ __device__ __forceinline__ void simplex_geometry(const double (&xs)[D + 1][D], d
             Nf[k][2] = s * (u0 * w1 - u1 * w0);
         }
     }
+}
+
+template <int D>
+__device__ __forceinline__ void corner_vectors(const double (&Nf)[D + 1][D], double (&ln)[D + 1][D]) {
 #pragma unroll
     for (int p = 0; p < D + 1; ++p)
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            double s = 0.0;
-#pragma unroll
-            for (int f = 0; f < D + 1; ++f)
-                if (f != p) s += Nf[f][a] / D;
-            ln[p][a] = s;
-        }
+        for (int a = 0; a < D; ++a) ln[p][a] = Nf[p][a] * (-1.0 / D);
 }
 
-// in-sphere diameter 2 D |w_c| / sum_f |N_f| (Sect. "Limiting", the characteristic length L_c)
+template <int D>
+__device__ __forceinline__ void simplex_geometry(const double (&xs)[D + 1][D], double &V, double (&Nf)[D + 1][D],
+                                                 double (&ln)[D + 1][D]) {
+    simplex_faces<D>(xs, V, Nf);
+    corner_vectors<D>(Nf, ln);
+}
+
+// in-sphere diameter 2 D |w_c| / sum_f |N_f| (the characteristic length L_c of Eq. CFL2)
 template <int D> __device__ __forceinline__ double insphere(double V, const double (&Nf)[D + 1][D]) {
     double area = 0.0;
 #pragma unroll
@@ -133,22 +139,22 @@ template <int D> __device__ __forceinline__ double det(const double (&A)[D * D])
                A[2] * (A[3] * A[7] - A[4] * A[6]);
 }
 
-// adjugate / determinant
+// adjugate times the reciprocal of the determinant
 template <int D> __device__ __forceinline__ void inverse(const double (&A)[D * D], double (&Ai)[D * D]) {
-    const double dt = det<D>(A);
+    const double r = 1.0 / det<D>(A);
     if constexpr (D == 2) {
-        Ai[0] = A[3] / dt; Ai[1] = -A[1] / dt;
-        Ai[2] = -A[2] / dt; Ai[3] = A[0] / dt;
+        Ai[0] = A[3] * r; Ai[1] = -A[1] * r;
+        Ai[2] = -A[2] * r; Ai[3] = A[0] * r;
     } else {
-        Ai[0] = (A[4] * A[8] - A[5] * A[7]) / dt;
-        Ai[1] = (A[2] * A[7] - A[1] * A[8]) / dt;
-        Ai[2] = (A[1] * A[5] - A[2] * A[4]) / dt;
-        Ai[3] = (A[5] * A[6] - A[3] * A[8]) / dt;
-        Ai[4] = (A[0] * A[8] - A[2] * A[6]) / dt;
-        Ai[5] = (A[2] * A[3] - A[0] * A[5]) / dt;
-        Ai[6] = (A[3] * A[7] - A[4] * A[6]) / dt;
-        Ai[7] = (A[1] * A[6] - A[0] * A[7]) / dt;
-        Ai[8] = (A[0] * A[4] - A[1] * A[3]) / dt;
+        Ai[0] = (A[4] * A[8] - A[5] * A[7]) * r;
+        Ai[1] = (A[2] * A[7] - A[1] * A[8]) * r;
+        Ai[2] = (A[1] * A[5] - A[2] * A[4]) * r;
+        Ai[3] = (A[5] * A[6] - A[3] * A[8]) * r;
+        Ai[4] = (A[0] * A[8] - A[2] * A[6]) * r;
+        Ai[5] = (A[2] * A[3] - A[0] * A[5]) * r;
+        Ai[6] = (A[3] * A[7] - A[4] * A[6]) * r;
+        Ai[7] = (A[1] * A[6] - A[0] * A[7]) * r;
+        Ai[8] = (A[0] * A[4] - A[1] * A[3]) * r;
     }
 }
 
@@ -166,68 +172,90 @@ __device__ __forceinline__ void matmul(const double (&A)[D * D], const double (&
 }
 
 // ---------------------------------------------------------------------------------------
+// Scalar functions of J = det F with few FP64 instructions (the FP64 pipe bounds the step).
+// ---------------------------------------------------------------------------------------
+// J^{-1/3}: single-precision seed y, then one third-order correction in FP64,
+// y (1 - e)^{-1/3} = y (1 + e/3 + 2 e^2/9 + O(e^3)) with e = 1 - J y^3. The seed is good to
+// ~1e-7, so the truncation is ~1e-20 and the result is within a couple of ulp.
+__device__ __forceinline__ double rcbrt_j(double J) {
+    const double y = (double)rcbrtf((float)J);
+    const double y3 = y * y * y;
+    const double e = fma(-J, y3, 1.0);
+    const double q = e * fma(e, 2.0 / 9.0, 1.0 / 3.0);
+    return fma(y, q, y);
+}
+
+// log J: for |J - 1| <= 1/8, ln J = 2 atanh(s) = 2 (s + s^3/3 + ... + s^13/13 + ...) with
+// s = (J - 1)/(J + 1), |s| <= 1/15 (the dropped tail is below 2e-17 relative); elsewhere
+// (large strains, and J <= 0 which gives NaN / -inf) the CUDA log.
+__device__ __forceinline__ double log_j(double J) {
+    const double d = J - 1.0;
+    if (!(fabs(d) <= 0.125)) return log(J);
+    const double s = d / (J + 1.0);
+    const double s2 = s * s;
+    double p = 1.0 / 13.0;
+    p = fma(p, s2, 1.0 / 11.0);
+    p = fma(p, s2, 1.0 / 9.0);
+    p = fma(p, s2, 1.0 / 7.0);
+    p = fma(p, s2, 1.0 / 5.0);
+    p = fma(p, s2, 1.0 / 3.0);
+    p = fma(p, s2, 1.0);
+    return 2.0 * s * p;
+}
+
+// ---------------------------------------------------------------------------------------
 // Neo-Hookean Cauchy stress (Eqs. T_psi, EOS_neoHook, cstnh): T = -p I + (mu/J) dev(Bbar),
 // p = -(kappa/2)(J - 1 + log J / J), Bbar = J^{-2/3} F F^t. 2D is plane strain (F33 = 1).
 // ---------------------------------------------------------------------------------------
-struct Invariants {
-    double J, invJ, logJ;
-};
-
-template <int D> __device__ __forceinline__ Invariants invariants(const double (&F)[D * D]) {
-    Invariants r;
-    r.J = det<D>(F);
-    r.invJ = 1.0 / r.J;
-    r.logJ = log(r.J);
-    return r;
-}
-
 template <int D>
 __device__ __forceinline__ void stress(const double (&F)[D * D], double mu, double kappa, double (&T)[D * D]) {
-    const Invariants I = invariants<D>(F);
-    const double rc = rcbrt(I.J);
+    const double J = det<D>(F);
+    const double rc = rcbrt_j(J);
     const double Jm23 = rc * rc;
-    const double p = -0.5 * kappa * (I.J - 1.0 + I.logJ * I.invJ);
-    const double coef = mu * I.invJ;
+    const double invJ = Jm23 * rc;
+    const double p = -0.5 * kappa * (J - 1.0 + log_j(J) * invJ);
+    const double coef = mu * invJ;
     double B[D * D];
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
+        for (int j = i; j < D; ++j) {
             double s = 0.0;
 #pragma unroll
             for (int k = 0; k < D; ++k) s += F[i * D + k] * F[j * D + k];
             B[i * D + j] = s;
+            B[j * D + i] = s;
         }
-    double tr = (D == 2) ? B[0] + B[3] + 1.0 : B[0] + B[4] + B[8];
-    const double third_trbar = Jm23 * tr / 3.0;
+    const double tr = (D == 2) ? B[0] + B[3] + 1.0 : B[0] + B[4] + B[8];
+    const double cj = coef * Jm23;
+    const double diag = -p - cj * tr * (1.0 / 3.0);
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
-            const double bb = Jm23 * B[i * D + j] - (i == j ? third_trbar : 0.0);
-            T[i * D + j] = (i == j ? -p : 0.0) + coef * bb;
-        }
+        for (int j = 0; j < D; ++j) T[i * D + j] = cj * B[i * D + j] + (i == j ? diag : 0.0);
 }
 
-// sound speed: a^2 = (K + 4 mu / (3 J)) / rho, K = -J dp/dJ = (kappa/2)(J + (1 - log J)/J)
+// acoustic impedance z = rho a with a^2 = (K + 4 mu / (3 J)) / rho, K = -J dp/dJ =
+// (kappa/2)(J + (1 - log J)/J): z = sqrt(rho (K + 4 mu / (3 J)))
 template <int D>
-__device__ __forceinline__ double sound_speed(const double (&F)[D * D], double rho, double mu, double kappa) {
-    const Invariants I = invariants<D>(F);
-    const double K = 0.5 * kappa * (I.J + (1.0 - I.logJ) * I.invJ);
-    return sqrt((K + 4.0 * mu / (3.0 * I.J)) / rho);
+__device__ __forceinline__ double impedance(const double (&F)[D * D], double rho, double mu, double kappa) {
+    const double J = det<D>(F);
+    const double invJ = 1.0 / J;
+    const double K = 0.5 * kappa * (J + (1.0 - log_j(J)) * invJ);
+    return sqrt(rho * (K + (4.0 / 3.0) * mu * invJ));
 }
 
 // specific free energy Psi = kappa/(4 rho0)((J-1)^2 + log^2 J) + mu/(2 rho0)(I1(Bbar) - 3)
 template <int D>
 __device__ __forceinline__ double free_energy(const double (&F)[D * D], double rho0, double mu, double kappa) {
-    const Invariants I = invariants<D>(F);
+    const double J = det<D>(F);
+    const double lJ = log_j(J);
     double trB = (D == 2) ? 1.0 : 0.0;
 #pragma unroll
     for (int i = 0; i < D * D; ++i) trB += F[i] * F[i];
-    const double rc = rcbrt(I.J);
+    const double rc = rcbrt_j(J);
     const double I1bar = rc * rc * trB;
-    return kappa / (4.0 * rho0) * ((I.J - 1.0) * (I.J - 1.0) + I.logJ * I.logJ) +
-           mu / (2.0 * rho0) * (I1bar - 3.0);
+    return kappa / (4.0 * rho0) * ((J - 1.0) * (J - 1.0) + lJ * lJ) + mu / (2.0 * rho0) * (I1bar - 3.0);
 }
 
 __device__ __forceinline__ double kappa_of(const Prm &prm, double mu) {

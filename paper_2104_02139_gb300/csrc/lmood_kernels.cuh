@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, c
     constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + DD;
     int c;
     if (!list_entity(list, cnt, n, blockIdx.x * blockDim.x + threadIdx.x, c)) return;
-    const int N = g.N, Np = g.Np;
+    const int N = g.N, Np = g.Np, NC = NV * N;
     int ord;
     if (list) {
         ord = f.order[c];
@@ -47,7 +47,6 @@ __global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, c
         ord = prm.base_order;
         f.order[c] = (unsigned char)ord;
     }
-    const double dt = f.dt[g.cell_inst ? __ldg(g.cell_inst + c) : 0];
     double xs[NV][D];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
@@ -55,58 +54,67 @@ __global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, c
 #pragma unroll
         for (int a = 0; a < D; ++a) xs[k][a] = f.x[a * Np + p];
     }
-    double V, Nf[NV][D], ln[NV][D];
-    simplex_geometry<D>(xs, V, Nf, ln);
-    double xcc[D], vc[D], Fc[DD];
+    double V, Nf[NV][D];
+    simplex_faces<D>(xs, V, Nf);
+    double vc[D], Fc[DD];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-        xcc[a] = f.xc[a * N + c];
-        vc[a] = f.v[a * N + c];
-    }
+    for (int a = 0; a < D; ++a) vc[a] = f.v[a * N + c];
 #pragma unroll
     for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
-    const double mc = f.m[c], muc = f.mu[c], kap = kappa_of(prm, muc);
-    const double rho = mc / V;
-    const double z = rho * sound_speed<D>(Fc, rho, muc, kap);
-    double wf[NV];
+    const double muc = f.mu[c], kap = kappa_of(prm, muc);
+    // face matrices W_f = z |l n_f| n_f (x) n_f with l n_f = N_f / D; M_cp = sum_{f != p} W_f
+    double W[NV][NS];
+    {
+        const double z = f.z[c];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double s = 0.0;
+        for (int k = 0; k < NV; ++k) {
+            double u[D], s = 0.0;
 #pragma unroll
-        for (int a = 0; a < D; ++a) s += (Nf[k][a] / D) * (Nf[k][a] / D);
-        wf[k] = z / sqrt(s);
-    }
-    const int NC = NV * N;
-    auto emit = [&](int k, const double(&vst)[D], const double(&Tst)[DD]) {
-        double M[NS];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) M[s] = 0.0;
-#pragma unroll
-        for (int fq = 0; fq < NV; ++fq) {
-            if (fq == k) continue;
+            for (int a = 0; a < D; ++a) {
+                u[a] = Nf[k][a] * (1.0 / D);
+                s += u[a] * u[a];
+            }
+            const double w = z * rsqrt(s);
 #pragma unroll
             for (int a = 0; a < D; ++a)
 #pragma unroll
-                for (int b = a; b < D; ++b) M[sidx<D>(a, b)] += wf[fq] * (Nf[fq][a] / D) * (Nf[fq][b] / D);
+                for (int b = a; b < D; ++b) W[k][sidx<D>(a, b)] = w * u[a] * u[b];
         }
+    }
+    // packet of corner k: M_cp and rhs_cp = M_cp v* - T* l n_p, with l n_p = -N_p / D
+    auto emit = [&](int k, const double(&vst)[D], const double(&Tst)[DD]) {
+        double M[NS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) f.pkM[s * NC + k * N + c] = M[s];
+        for (int s = 0; s < NS; ++s) {
+            double acc = 0.0;
+#pragma unroll
+            for (int fq = 0; fq < NV; ++fq)
+                if (fq != k) acc += W[fq][s];
+            M[s] = acc;
+            f.pkM[s * NC + k * N + c] = acc;
+        }
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             double mv = 0.0, tn = 0.0;
 #pragma unroll
             for (int b = 0; b < D; ++b) {
                 mv += M[sidx<D>(a, b)] * vst[b];
-                tn += Tst[a * D + b] * ln[k][b];
+                tn += Tst[a * D + b] * Nf[k][b];
             }
-            f.pkR[a * NC + k * N + c] = mv - tn;
+            f.pkR[a * NC + k * N + c] = fma(tn, 1.0 / D, mv);
         }
     };
     if (ord == 2) {
-        // least-squares slopes about centroids over the stencil (reading of Sect. "Algorithm")
-        double G[NS], r[NQ][D];
+        // least-squares slopes about centroids over the stencil (reading of Sect. "Algorithm"):
+        // G = sum dx dx^t, r = sum dx (q_o - q_c) = sum dx q_o - (sum dx) q_c
+        double xcc[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) xcc[a] = f.xc[a * N + c];
+        double G[NS], r[NQ][D], sdx[D];
 #pragma unroll
         for (int s = 0; s < NS; ++s) G[s] = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) sdx[a] = 0.0;
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
 #pragma unroll
@@ -116,23 +124,33 @@ __global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, c
             const int o = __ldg(g.st_idx + j);
             double dx[D];
 #pragma unroll
-            for (int a = 0; a < D; ++a) dx[a] = f.xc[a * N + o] - xcc[a];
+            for (int a = 0; a < D; ++a) {
+                dx[a] = f.xc[a * N + o] - xcc[a];
+                sdx[a] += dx[a];
+            }
 #pragma unroll
             for (int a = 0; a < D; ++a)
 #pragma unroll
-                for (int b = a; b < D; ++b) G[sidx<D>(a, b)] += dx[a] * dx[b];
+                for (int b = a; b < D; ++b) G[sidx<D>(a, b)] = fma(dx[a], dx[b], G[sidx<D>(a, b)]);
 #pragma unroll
             for (int q = 0; q < D; ++q) {
-                const double dq = f.v[q * N + o] - vc[q];
+                const double qo = f.v[q * N + o];
 #pragma unroll
-                for (int a = 0; a < D; ++a) r[q][a] += dx[a] * dq;
+                for (int a = 0; a < D; ++a) r[q][a] = fma(dx[a], qo, r[q][a]);
             }
 #pragma unroll
             for (int q = 0; q < DD; ++q) {
-                const double dq = f.F[q * N + o] - Fc[q];
+                const double qo = f.F[q * N + o];
 #pragma unroll
-                for (int a = 0; a < D; ++a) r[D + q][a] += dx[a] * dq;
+                for (int a = 0; a < D; ++a) r[D + q][a] = fma(dx[a], qo, r[D + q][a]);
             }
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+#pragma unroll
+            for (int q = 0; q < D; ++q) r[q][a] = fma(-sdx[a], vc[q], r[q][a]);
+#pragma unroll
+            for (int q = 0; q < DD; ++q) r[D + q][a] = fma(-sdx[a], Fc[q], r[D + q][a]);
         }
         double Gf[DD], Gi[DD], gs[NQ][D];
 #pragma unroll
@@ -142,9 +160,8 @@ __global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, c
         double tr = 0.0;
 #pragma unroll
         for (int a = 0; a < D; ++a) tr += Gf[a * D + a];
-        const double t = tr / D;
-        const double tD = D == 2 ? t * t : t * t * t;
-        const bool ok = det<D>(Gf) > 1e-12 * tD;
+        const double t = tr * (1.0 / D);
+        const bool ok = det<D>(Gf) > 1e-12 * (D == 2 ? t * t : t * t * t);
         inverse<D>(Gf, Gi);
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
@@ -155,20 +172,23 @@ __global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, c
                 for (int b = 0; b < D; ++b) s += Gi[a * D + b] * r[q][b];
                 gs[q][a] = ok ? s : 0.0;
             }
-        // predictor, pass 1: cell-averaged time derivative of v from the corner stresses
+        double dxs[NV][D];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+            for (int a = 0; a < D; ++a) dxs[k][a] = xs[k][a] - xcc[a];
+        // predictor, pass 1: dv/dt = (1/m) sum_q T(F_h(x_q)) l n_q
         double dvdt[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) dvdt[a] = 0.0;
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double dx[D], Fh[DD], T[DD];
-#pragma unroll
-            for (int a = 0; a < D; ++a) dx[a] = xs[k][a] - xcc[a];
+            double Fh[DD], T[DD];
 #pragma unroll
             for (int q = 0; q < DD; ++q) {
                 double s = Fc[q];
 #pragma unroll
-                for (int a = 0; a < D; ++a) s += gs[D + q][a] * dx[a];
+                for (int a = 0; a < D; ++a) s += gs[D + q][a] * dxs[k][a];
                 Fh[q] = s;
             }
             stress<D>(Fh, muc, kap, T);
@@ -176,12 +196,15 @@ __global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, c
             for (int i = 0; i < D; ++i) {
                 double s = 0.0;
 #pragma unroll
-                for (int b = 0; b < D; ++b) s += T[i * D + b] * ln[k][b];
+                for (int b = 0; b < D; ++b) s += T[i * D + b] * Nf[k][b];
                 dvdt[i] += s;
             }
         }
+        // half step: dt/2 dv/dt and dt/2 dF/dt with dF/dt = L^ F_c (Eq. GCLL)
+        const double dt = f.dt[g.cell_inst ? __ldg(g.cell_inst + c) : 0];
+        const double hv = -0.5 * dt * f.im[c] * (1.0 / D);
 #pragma unroll
-        for (int a = 0; a < D; ++a) dvdt[a] /= mc;
+        for (int a = 0; a < D; ++a) dvdt[a] *= hv;
         double gv[DD], dFdt[DD];
 #pragma unroll
         for (int i = 0; i < D; ++i)
@@ -191,22 +214,20 @@ __global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, c
         // pass 2: corner values at t^{n+1/2} and packets
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double dx[D], vst[D], Fs[DD], T[DD];
-#pragma unroll
-            for (int a = 0; a < D; ++a) dx[a] = xs[k][a] - xcc[a];
+            double vst[D], Fs[DD], T[DD];
 #pragma unroll
             for (int i = 0; i < D; ++i) {
                 double s = vc[i];
 #pragma unroll
-                for (int a = 0; a < D; ++a) s += gs[i][a] * dx[a];
-                vst[i] = s + 0.5 * dt * dvdt[i];
+                for (int a = 0; a < D; ++a) s += gs[i][a] * dxs[k][a];
+                vst[i] = s + dvdt[i];
             }
 #pragma unroll
             for (int q = 0; q < DD; ++q) {
                 double s = Fc[q];
 #pragma unroll
-                for (int a = 0; a < D; ++a) s += gs[D + q][a] * dx[a];
-                Fs[q] = s + 0.5 * dt * dFdt[q];
+                for (int a = 0; a < D; ++a) s += gs[D + q][a] * dxs[k][a];
+                Fs[q] = fma(0.5 * dt, dFdt[q], s);
             }
             stress<D>(Fs, muc, kap, T);
             emit(k, vst, T);
@@ -319,26 +340,28 @@ __global__ void __launch_bounds__(kNodeBlock) k_nodes(Geo g, Fld f, const int *_
 }
 
 // velocity gradient L_ij = (1/|w_c|) sum_p v_{p,i} ln_{p,j} (Eq. div_grad_v, read so that
-// dF/dt = L F)
+// dF/dt = L F), with ln_p = -N_p / D: L = -(1 / (D |w_c|)) sum_p v_p (x) N_p
 template <int D>
-__device__ __forceinline__ void vel_gradient(const double (&vn)[D + 1][D], const double (&ln)[D + 1][D], double V,
+__device__ __forceinline__ void vel_gradient(const double (&vn)[D + 1][D], const double (&Nf)[D + 1][D], double V,
                                              double (&L)[D * D]) {
+    const double s0 = -1.0 / (D * V);
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             double s = 0.0;
 #pragma unroll
-            for (int k = 0; k < D + 1; ++k) s += vn[k][i] * ln[k][j];
-            L[i * D + j] = s / V;
+            for (int k = 0; k < D + 1; ++k) s += vn[k][i] * Nf[k][j];
+            L[i * D + j] = s * s0;
         }
 }
 
 // ---------------------------------------------------------------------------------------
 // k_update: subcell forces f_cp = M_cp v*_p - rhs_cp and the cell update (Eqs. tau_c^n,
 // v_c^n, e_c^n, firstB, CN_B): tau^{n+1} = |w_c(x^{n+1})| / m_c; F by Crank-Nicolson (P1)
-// or explicit Euler (P0). Then detection (Eqs. PAD, RDMP) and the dt candidate (Eq. CFL2).
-// P1 cells that fail are appended to tlist.
+// or explicit Euler (P0). Then detection (Eqs. PAD, RDMP), the dt candidate (Eq. CFL2) and
+// the impedance of the candidate (used by the next step's packets). P1 cells that fail are
+// appended to tlist.
 // ---------------------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(kCellBlock) k_update(Geo g, Fld f, Prm prm, const int *__restrict__ list,
@@ -379,14 +402,15 @@ __global__ void __launch_bounds__(kCellBlock) k_update(Geo g, Fld f, Prm prm, co
             sfv += fa * vsn[k][a];
         }
     }
-    const double mc = f.m[c], muc = f.mu[c], kap = kappa_of(prm, muc);
+    const double mc = f.m[c], im = f.im[c], muc = f.mu[c], kap = kappa_of(prm, muc);
+    const double dtm = dt * im;
     double v1[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) v1[a] = f.v[a * N + c] + dt / mc * sf[a];
-    const double e1 = f.e[c] + dt / mc * sfv;
-    double V0, Nf0[NV][D], ln0[NV][D], V1, Nf1[NV][D], ln1[NV][D];
-    simplex_geometry<D>(xs0, V0, Nf0, ln0);
-    simplex_geometry<D>(xs1, V1, Nf1, ln1);
+    for (int a = 0; a < D; ++a) v1[a] = fma(dtm, sf[a], f.v[a * N + c]);
+    const double e1 = fma(dtm, sfv, f.e[c]);
+    double V0, Nf0[NV][D], V1, Nf1[NV][D];
+    simplex_faces<D>(xs0, V0, Nf0);
+    simplex_faces<D>(xs1, V1, Nf1);
     double Fn[DD], F1[DD];
 #pragma unroll
     for (int q = 0; q < DD; ++q) Fn[q] = f.F[q * N + c];
@@ -396,29 +420,29 @@ __global__ void __launch_bounds__(kCellBlock) k_update(Geo g, Fld f, Prm prm, co
         for (int k = 0; k < NV; ++k)
 #pragma unroll
             for (int a = 0; a < D; ++a) vn[k][a] = f.vp[a * Np + nod[k]];
-        vel_gradient<D>(vn, ln0, V0, L0);
+        vel_gradient<D>(vn, Nf0, V0, L0);
 #pragma unroll
         for (int k = 0; k < NV; ++k)
 #pragma unroll
             for (int a = 0; a < D; ++a) vn[k][a] = f.vp1[a * Np + nod[k]];
-        vel_gradient<D>(vn, ln1, V1, L1);
+        vel_gradient<D>(vn, Nf1, V1, L1);
 #pragma unroll
         for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 const double id = i == j ? 1.0 : 0.0;
-                A[i * D + j] = id - 0.5 * dt * L1[i * D + j];
-                Bm[i * D + j] = id + 0.5 * dt * L0[i * D + j];
+                A[i * D + j] = fma(-0.5 * dt, L1[i * D + j], id);
+                Bm[i * D + j] = fma(0.5 * dt, L0[i * D + j], id);
             }
         matmul<D>(Bm, Fn, R);
         inverse<D>(A, Ai);
         matmul<D>(Ai, R, F1);
     } else {
         double Ls[DD], LF[DD];
-        vel_gradient<D>(vsn, ln0, V0, Ls);
+        vel_gradient<D>(vsn, Nf0, V0, Ls);
         matmul<D>(Ls, Fn, LF);
 #pragma unroll
-        for (int q = 0; q < DD; ++q) F1[q] = Fn[q] + dt * LF[q];
+        for (int q = 0; q < DD; ++q) F1[q] = fma(dt, LF[q], Fn[q]);
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -426,14 +450,14 @@ __global__ void __launch_bounds__(kCellBlock) k_update(Geo g, Fld f, Prm prm, co
         double s = 0.0;
 #pragma unroll
         for (int k = 0; k < NV; ++k) s += xs1[k][a];
-        f.xc1[a * N + c] = s / NV;
+        f.xc1[a * N + c] = s * (1.0 / NV);
     }
     f.e1[c] = e1;
 #pragma unroll
     for (int q = 0; q < DD; ++q) f.F1[q * N + c] = F1[q];
     const double rho1 = mc / V1;
     f.rho1[c] = rho1;
-    f.tau1[c] = V1 / mc;
+    f.tau1[c] = V1 * im;
     if (prm.mood) {
         const int ps = pad_state<D>(v1, e1, F1, V1);
         if (ord == 2) {
@@ -454,7 +478,10 @@ __global__ void __launch_bounds__(kCellBlock) k_update(Geo g, Fld f, Prm prm, co
             f.pflag[c] = (unsigned char)ps;
         }
     }
-    double dtc = prm.cfl * insphere<D>(V1, Nf1) / sound_speed<D>(F1, rho1, muc, kap);
+    // next impedance and dt candidate: C_CFL L_c / a = C_CFL L_c rho / z
+    const double z1 = impedance<D>(F1, rho1, muc, kap);
+    f.z1[c] = z1;
+    double dtc = prm.cfl * insphere<D>(V1, Nf1) * rho1 / z1;
     const double dV = V1 - V0;
     if (dV != 0.0) dtc = fmin(dtc, prm.Cv * dt * V0 / fabs(dV));
     f.dtc[c] = dtc;
@@ -567,11 +594,11 @@ static __global__ void __launch_bounds__(256) k_finalize(Geo g, Fld f, Prm prm) 
     }
 }
 
-// initial cell state: m = rho0 |w_c|, centroid, rho, tau, F (identity when not given),
-// e = |v|^2/2 + Psi(F), acoustic dt candidate
+// initial cell state: m = rho0 |w_c|, 1/m, centroid, rho, tau, F (identity when not given),
+// e = |v|^2/2 + Psi(F), impedance, acoustic dt candidate
 template <int D>
 __global__ void __launch_bounds__(kCellBlock) k_init_cells(Geo g, Fld f, Prm prm, double rho0, double *m_out,
-                                                           int f_given) {
+                                                           double *im_out, int f_given) {
     constexpr int NV = D + 1, DD = D * D;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
@@ -583,16 +610,17 @@ __global__ void __launch_bounds__(kCellBlock) k_init_cells(Geo g, Fld f, Prm prm
 #pragma unroll
         for (int a = 0; a < D; ++a) xs[k][a] = f.x[a * Np + p];
     }
-    double V, Nf[NV][D], ln[NV][D];
-    simplex_geometry<D>(xs, V, Nf, ln);
+    double V, Nf[NV][D];
+    simplex_faces<D>(xs, V, Nf);
     const double mc = rho0 * V;
     m_out[c] = mc;
+    im_out[c] = 1.0 / mc;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         double s = 0.0;
 #pragma unroll
         for (int k = 0; k < NV; ++k) s += xs[k][a];
-        f.xc[a * N + c] = s / NV;
+        f.xc[a * N + c] = s * (1.0 / NV);
     }
     const double rho = mc / V;
     f.rho[c] = rho;
@@ -613,12 +641,15 @@ __global__ void __launch_bounds__(kCellBlock) k_init_cells(Geo g, Fld f, Prm prm
     f.e[c] = ke + free_energy<D>(F, rho0, muc, kap);
     f.order[c] = 1;
     f.pflag[c] = 0;
-    f.dtc[c] = prm.cfl * insphere<D>(V, Nf) / sound_speed<D>(F, rho, muc, kap);
+    const double z = impedance<D>(F, rho, muc, kap);
+    f.z[c] = z;
+    f.dtc[c] = prm.cfl * insphere<D>(V, Nf) * rho / z;
 }
 
-// derived geometry of the current positions: centroid, rho = m / |w_c|, tau = |w_c| / m
-template <int D> __global__ void __launch_bounds__(kCellBlock) k_refresh(Geo g, Fld f) {
-    constexpr int NV = D + 1;
+// derived quantities of the current positions and F: centroid, rho = m / |w_c|,
+// tau = |w_c| / m, impedance z
+template <int D> __global__ void __launch_bounds__(kCellBlock) k_refresh(Geo g, Fld f, Prm prm) {
+    constexpr int NV = D + 1, DD = D * D;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     double xs[NV][D];
@@ -628,17 +659,23 @@ template <int D> __global__ void __launch_bounds__(kCellBlock) k_refresh(Geo g, 
 #pragma unroll
         for (int a = 0; a < D; ++a) xs[k][a] = f.x[a * g.Np + p];
     }
-    double V, Nf[NV][D], ln[NV][D];
-    simplex_geometry<D>(xs, V, Nf, ln);
+    double V, Nf[NV][D];
+    simplex_faces<D>(xs, V, Nf);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         double s = 0.0;
 #pragma unroll
         for (int k = 0; k < NV; ++k) s += xs[k][a];
-        f.xc[a * g.N + c] = s / NV;
+        f.xc[a * g.N + c] = s * (1.0 / NV);
     }
-    f.rho[c] = f.m[c] / V;
-    f.tau1[c] = V / f.m[c];
+    const double rho = f.m[c] / V;
+    f.rho[c] = rho;
+    f.tau1[c] = V * f.im[c];
+    double F[DD];
+#pragma unroll
+    for (int q = 0; q < DD; ++q) F[q] = f.F[q * g.N + c];
+    const double muc = f.mu[c];
+    f.z[c] = impedance<D>(F, rho, muc, kappa_of(prm, muc));
 }
 
 // sums of m, m v, m e (diagnostic; atomics, so the last bits depend on scheduling)

@@ -17,8 +17,9 @@ struct Ops {
                        cudaStream_t);
     void (*dt_init)(const Fld &, const Prm &, int n_inst, int first, cudaStream_t);
     void (*finalize)(const Geo &, const Fld &, const Prm &, cudaStream_t);
-    void (*init_cells)(const Geo &, const Fld &, const Prm &, double rho0, double *m, int f_given, cudaStream_t);
-    void (*refresh)(const Geo &, const Fld &, cudaStream_t);
+    void (*init_cells)(const Geo &, const Fld &, const Prm &, double rho0, double *m, double *im, int f_given,
+                       cudaStream_t);
+    void (*refresh)(const Geo &, const Fld &, const Prm &, cudaStream_t);
     void (*totals)(const Geo &, const Fld &, double *out, cudaStream_t);
 };
 

@@ -37,11 +37,12 @@ void finalize(const Geo &g, const Fld &f, const Prm &p, cudaStream_t s) {
     k_finalize<<<blocks(g.N, 256), 256, 0, s>>>(g, f, p);
 }
 template <int D>
-void init_cells(const Geo &g, const Fld &f, const Prm &p, double rho0, double *m, int f_given, cudaStream_t s) {
-    k_init_cells<D><<<blocks(g.N, kCellBlock), kCellBlock, 0, s>>>(g, f, p, rho0, m, f_given);
+void init_cells(const Geo &g, const Fld &f, const Prm &p, double rho0, double *m, double *im, int f_given,
+                cudaStream_t s) {
+    k_init_cells<D><<<blocks(g.N, kCellBlock), kCellBlock, 0, s>>>(g, f, p, rho0, m, im, f_given);
 }
-template <int D> void refresh(const Geo &g, const Fld &f, cudaStream_t s) {
-    k_refresh<D><<<blocks(g.N, kCellBlock), kCellBlock, 0, s>>>(g, f);
+template <int D> void refresh(const Geo &g, const Fld &f, const Prm &p, cudaStream_t s) {
+    k_refresh<D><<<blocks(g.N, kCellBlock), kCellBlock, 0, s>>>(g, f, p);
 }
 template <int D> void totals(const Geo &g, const Fld &f, double *out, cudaStream_t s) {
     k_totals<D><<<blocks(g.N, 256), 256, 0, s>>>(g, f, out);

@@ -1,0 +1,32 @@
+"""The step's own FP64 log and J^{-1/3} (atanh series near 1 / single-precision seed with a
+third-order correction) against CUDA's log and rcbrt on the device (-m gpu)."""
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2104_02139_gb300", "csrc")
+
+
+def test_log_and_rcbrt_against_cuda():
+    so = os.path.join(tempfile.mkdtemp(), "mathcheck.so")
+    subprocess.check_call(["nvcc", "-shared", "-Xcompiler", "-fPIC", "-O3", "-std=c++17",
+                           "-gencode", "arch=compute_103a,code=sm_103a", "-I", CSRC,
+                           os.path.join(HERE, "gpu_math_check.cu"), "-o", so])
+    lib = ctypes.CDLL(so)
+    rng = np.random.default_rng(0)
+    J = np.concatenate([np.linspace(0.3, 3.0, 100001), 1 + np.linspace(-0.13, 0.13, 100001),
+                        1 + rng.normal(0, 1e-4, 50000), [1.0, 0.875, 1.125, np.nextafter(1.125, 2)]])
+    out = np.zeros(4 * J.size)
+    assert lib.eval_math(J.ctypes.data_as(ctypes.c_void_p), J.size, out.ctypes.data_as(ctypes.c_void_p)) == 0
+    lg, lg_ref, rc, rc_ref = out.reshape(4, -1)
+    # log: within 2 ulp of |log J| (absolute 2 ulp of 1/8 ~ 6e-17 near the switch-over)
+    assert np.all(np.abs(lg - lg_ref) <= 4.5e-16 * np.abs(lg_ref) + 1e-17)
+    assert lg[np.where(J == 1.0)[0][0]] == 0.0
+    # J^{-1/3}: within 2 ulp
+    assert np.all(np.abs(rc - rc_ref) <= 4.5e-16 * rc_ref)
