@@ -224,10 +224,11 @@ class State:
                 "F": self.get(FIELD_F), "tau": self.get(FIELD_TAU)}
 
 
-def simulation(problem, stream=None, **params) -> State:
-    """Mesh + state of a workload problem (anything with .mesh, .rho0, .lam, .mu, .v, .F, .cfl)."""
+def simulation(problem, stream=None, cell_inst=None, n_inst=1, **params) -> State:
+    """Mesh + state of a workload problem (anything with .mesh, .rho0, .lam, .mu, .v, .F, .cfl);
+    cell_inst / n_inst describe a batch of independent instances concatenated into one mesh."""
     m = problem.mesh
-    mesh = Mesh(m.dim, m.x, m.c2n, m.bface, m.btag, stream=stream)
+    mesh = Mesh(m.dim, m.x, m.c2n, m.bface, m.btag, cell_inst=cell_inst, n_inst=n_inst, stream=stream)
     p = params_default(m.dim, cfl=problem.cfl)
     for k, v in params.items():
         setattr(p, k, v)

@@ -26,3 +26,16 @@ def test_seeded_determinism():
     assert np.array_equal(a.mesh.x, b.mesh.x) and np.array_equal(a.mesh.c2n, b.mesh.c2n)
     c = W.cube3d(n=4)
     assert np.all(np.abs(c.mu - 1) < 1.0) and c.mu.std() > 0.05
+
+
+def test_concat_offsets():
+    probs = W.batched2d(n_inst=3, lo=100, hi=300)
+    pb, inst = W.concat(probs)
+    assert pb.mesh.n_cells == sum(q.mesh.n_cells for q in probs) == inst.size
+    assert np.array_equal(np.bincount(inst), [q.mesh.n_cells for q in probs])
+    # no node is shared between instances
+    owner = np.full(pb.mesh.n_nodes, -1)
+    for k in range(3):
+        owner[pb.mesh.c2n[k]] = inst
+    for k in range(3):
+        assert np.array_equal(owner[pb.mesh.c2n[k]], inst)

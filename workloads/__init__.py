@@ -312,6 +312,32 @@ def batched2d(n_inst: int = 256, seed: int = 4, lo: float = 1e3, hi: float = 2e5
     return out
 
 
+def concat(problems: list[Problem], name: str = "batch") -> tuple[Problem, np.ndarray]:
+    """Concatenate independent problems into one mesh (node and cell ids offset, no shared
+    nodes) and return it with the instance id of every cell. All must share dim, rho0, lam
+    and CFL; mu and v are per cell already."""
+    d = problems[0].mesh.dim
+    xs, c2ns, bfs, bts, mus, vs, inst = [], [], [], [], [], [], []
+    off = 0
+    for i, pb in enumerate(problems):
+        assert pb.mesh.dim == d and pb.rho0 == problems[0].rho0 and pb.lam == problems[0].lam
+        xs.append(pb.mesh.x)
+        c2ns.append(pb.mesh.c2n + off)
+        bfs.append(pb.mesh.bface + off)
+        bts.append(pb.mesh.btag)
+        mus.append(pb.mu)
+        vs.append(pb.v)
+        inst.append(np.full(pb.mesh.n_cells, i, dtype=np.int32))
+        off += pb.mesh.n_nodes
+    m = Mesh(d, np.ascontiguousarray(np.concatenate(xs, axis=1)), np.ascontiguousarray(np.concatenate(c2ns, axis=1)),
+             np.ascontiguousarray(np.concatenate(bfs, axis=1)), np.concatenate(bts))
+    pb = Problem(name, m, problems[0].rho0, problems[0].lam, np.concatenate(mus),
+                 np.ascontiguousarray(np.concatenate(vs, axis=1)), problems[0].cfl, problems[0].steps,
+                 meta={"n_inst": len(problems), "cells": [q.mesh.n_cells for q in problems],
+                       "nodes": [q.mesh.n_nodes for q in problems]})
+    return pb, np.concatenate(inst)
+
+
 def translate_rotate(pb: Problem, R: np.ndarray, shift: np.ndarray) -> Problem:
     """Rigidly move a problem's whole configuration: x -> R x + shift, v -> R v, F -> R F R^T.
     (An input transformation used by objectivity tests.)"""
