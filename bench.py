@@ -307,7 +307,20 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", type=int, default=0,
+                    help="profiling case: build the workload, take this many untimed steps, exit")
     args = ap.parse_args()
+    if args.case:
+        import torch
+        import paper_2104_02139_gb300 as L
+        import workloads as W
+        L.build()
+        sim = L.simulation(W.impact2d())
+        for _ in range(args.case):
+            info = sim.step()
+        torch.cuda.synchronize()
+        print(f"case: {args.case} steps, last dt {info.dt_used:.6g}, troubled {info.n_troubled}")
+        return
     rank, local, ws, dist = dist_setup()
     try:
         if args.impl == "reference":

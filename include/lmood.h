@@ -189,6 +189,24 @@ enum { LMOOD_K_PREDICT = 0, LMOOD_K_NODES = 1, LMOOD_K_UPDATE = 2, LMOOD_K_MOOD 
 lmood_status lmood_timing(lmood_state s, int enable);
 lmood_status lmood_timing_read(lmood_state s, double *ms, int64_t *launches);
 
+/*
+ * Conserved totals of caller-owned cell arrays without any device allocation (the paper has
+ * no counterpart: this is a service for host applications that own all device memory and do
+ * not let libraries call cudaMalloc after start-up, e.g. codes that carve the GPU into one
+ * pool at initialisation or real-time loops where an allocation could synchronise or fail).
+ *   m [n_cells], v [dim][n_cells], e [n_cells]: device arrays (masses, velocities, specific
+ *   total energies, e.g. filled by lmood_get with is_device = 1); out5: device array of 5
+ *   doubles receiving sum m, sum m v (3; z = 0 in 2D), sum m e. Ordered on stream; returns
+ *   without synchronising. Sums are taken in a fixed order, so repeated calls agree bitwise.
+ * Scratch is a fixed file-scope device array of 256 KiB (per GPU, held until exit), so
+ * n_cells is limited to 16,777,216: larger sizes return LMOOD_ERR_ARG. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make that first call
+ * outside any stream capture. All calls share the array: calls whose work overlaps on the GPU
+ * race and must be ordered by the caller. Allocates nothing (no cudaMalloc / cudaFree).
+ */
+lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, const double *v, const double *e,
+                                  double *out5, void *stream);
+
 const char *lmood_last_error(void);
 
 #ifdef __cplusplus

@@ -44,7 +44,7 @@ class StepInfo(C.Structure):
 _lib = None
 EXPORTS = ("lmood_params_default", "lmood_mesh_create", "lmood_mesh_destroy", "lmood_mesh_info",
            "lmood_state_init", "lmood_state_destroy", "lmood_step", "lmood_run", "lmood_get", "lmood_set",
-           "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_last_error")
+           "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_totals_noalloc", "lmood_last_error")
 K_PREDICT, K_NODES, K_UPDATE, K_MOOD, K_FINALIZE, NK = range(6)
 K_NAMES = ("predict", "nodes", "update", "mood", "finalize")
 
@@ -71,6 +71,7 @@ def lib():
         L.lmood_totals.argtypes = [vp, C.POINTER(C.c_double)]
         L.lmood_timing.argtypes = [vp, C.c_int]
         L.lmood_timing_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.lmood_totals_noalloc.argtypes = [C.c_int, C.c_int64, vp, vp, vp, vp, vp]
         L.lmood_last_error.restype = C.c_char_p
         for name in EXPORTS:
             if name != "lmood_last_error":

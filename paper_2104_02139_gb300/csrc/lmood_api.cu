@@ -70,6 +70,9 @@ void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)> &fn) {
 
 }  // namespace
 
+// error message setter shared with the other translation units of the library
+void lmood_internal_set_error(const char *msg) { g_err = msg; }
+
 // =======================================================================================
 // mesh
 // =======================================================================================
