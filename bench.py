@@ -58,12 +58,14 @@ def kernel_bytes(dim: int, nc: int, npn: int, nnz: int) -> dict:
     # mu, z, 1/m; writes packets and the order byte
     predict = (4 * NV * nc + d8 * D * npn + d8 * (2 * D + D * D) * nc + 4 * (nc + 1) + 4 * nnz
                + 3 * d8 * nc + pk + nc)
-    # nodes: CSR, packets, BC byte, x, v_p^n; writes v*, x^{n+1}, v_p^{n+1}
-    nodes = 4 * (npn + 1) + 4 * NV * nc + pk + npn + 2 * d8 * D * npn + 3 * d8 * D * npn
-    # update: c2n, 5 node arrays, packets, v e F m 1/m mu, order, rho (stencil), stencil CSR;
+    # nodes: CSR, packets, BC byte, x, v_p^n, rho (per cell, once); writes v*, x^{n+1},
+    # v_p^{n+1} and the rho range per node
+    nodes = (4 * (npn + 1) + 4 * NV * nc + pk + npn + 2 * d8 * D * npn + d8 * nc + 3 * d8 * D * npn
+             + 2 * d8 * npn)
+    # update: c2n, 5 node arrays + the node rho range, packets, v e F m 1/m mu, order;
     # writes v e F xc rho tau z, dt candidate
-    update = (4 * NV * nc + 5 * d8 * D * npn + pk + d8 * (D + 1 + D * D + 3) * nc + nc + d8 * nc
-              + 4 * (nc + 1) + 4 * nnz + d8 * (D + 1 + D * D + D + 3) * nc + d8 * nc)
+    update = (4 * NV * nc + 5 * d8 * D * npn + 2 * d8 * npn + pk + d8 * (D + 1 + D * D + 3) * nc + nc
+              + d8 * (D + 1 + D * D + D + 3) * nc + d8 * nc)
     finalize = d8 * nc + 2 * nc
     return {"predict": predict, "nodes": nodes, "update": update, "finalize": finalize}
 
@@ -73,9 +75,9 @@ def kernel_bytes(dim: int, nc: int, npn: int, nnz: int) -> dict:
 # divided by the cell count; they include the FP64 expansions of division, sqrt, log, cbrt.
 # Re-measured whenever a kernel changes (profiles/ holds the capture); None = not measured
 # for the current kernel.
-FP64_FLOP_PER_CELL = {"predict": 1381.2, "update": 445.1, "nodes": 31.1}
+FP64_FLOP_PER_CELL = {"predict": None, "update": None, "nodes": None}
 # DRAM bytes (read + write) per full launch from the same ncu capture, or None.
-TRAFFIC_PER_LAUNCH = {"predict": 244.54e6, "update": 397.55e6, "nodes": 164.90e6}
+TRAFFIC_PER_LAUNCH = {"predict": None, "update": None, "nodes": None}
 
 
 def fp64_peak_tflops(device) -> float:

@@ -68,7 +68,9 @@ typedef struct {
     int32_t max_mood_iters; /* MOOD iterations allowed per step (default 128)               */
     int32_t order;          /* 2: second order with the P1 -> P0 cascade; 1: first order    */
     int32_t mood;           /* 1: a-posteriori detection on (default); 0: unlimited         */
-    int32_t reserved;
+    int32_t graph;          /* 1: each step is one CUDA graph with the MOOD loop as a device-side
+                               conditional while node (default); 0: host-driven MOOD rounds.
+                               Results are identical.                                        */
 } lmood_params;
 
 /* Per-step report. */

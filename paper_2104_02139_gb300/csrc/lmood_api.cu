@@ -112,6 +112,7 @@ extern "C" lmood_status lmood_params_default(int dim, lmood_params *p) {
     p->max_mood_iters = 128;
     p->order = 2;
     p->mood = 1;
+    p->graph = 1;
     return LMOOD_OK;
 }
 
@@ -360,6 +361,17 @@ struct lmood_state_s {
     double *tau = nullptr, *m = nullptr, *im = nullptr, *mu = nullptr;
     int *tl[2] = {nullptr, nullptr}, *nlist = nullptr, *clist = nullptr, *node_mark = nullptr, *cell_mark = nullptr;
     double *totals = nullptr;
+    Ctl *ctl = nullptr;        // device MOOD control block
+    Report *d_report = nullptr;
+    Report *h_report = nullptr;  // pinned
+    // graph-captured steps: one executable graph per buffer parity (the state swaps pointers)
+    int parity = 0;
+    bool graphs_built = false;
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaEvent_t gev[2][6] = {};
+    cudaStream_t cap_st = nullptr;   // private streams for capturing (the mesh's stream may be the
+    cudaStream_t body_st = nullptr;  // legacy default stream, which cannot be captured)
     int *h_cnt = nullptr;      // pinned mirror of the device counters
     double *h_dt = nullptr;    // pinned: dt used, dt next (instance 0)
     double t = 0.0;
@@ -401,6 +413,7 @@ template <class F> static void timed(lmood_state s, int cls, int n_launch, F &&l
 }
 
 static void swap_state(lmood_state s) {
+    s->parity ^= 1;
     Fld &f = s->f;
     std::swap(f.x, f.x1);
     std::swap(f.vp, f.vp1);
@@ -434,6 +447,15 @@ static Prm kernel_params(const lmood_params &p, const lmood_material &m) {
 static void state_free(lmood_state s) {
     if (s->M) cudaStreamSynchronize(s->M->st);
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+    for (int p = 0; p < 2; ++p) {
+        if (s->gexec[p]) cudaGraphExecDestroy(s->gexec[p]);
+        if (s->graph[p]) cudaGraphDestroy(s->graph[p]);
+        for (cudaEvent_t e : s->gev[p])
+            if (e) cudaEventDestroy(e);
+    }
+    if (s->body_st) cudaStreamDestroy(s->body_st);
+    if (s->cap_st) cudaStreamDestroy(s->cap_st);
+    if (s->h_report) cudaFreeHost(s->h_report);
     s->mem.release();
     if (s->h_cnt) cudaFreeHost(s->h_cnt);
     if (s->h_dt) cudaFreeHost(s->h_dt);
@@ -502,6 +524,8 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
     A((void **)&s->im, N * nd);
     A((void **)&f.z, N * nd);
     A((void **)&f.z1, N * nd);
+    A((void **)&f.rlo, Np * nd);
+    A((void **)&f.rhi, Np * nd);
     A((void **)&s->mu, N * nd);
     A((void **)&f.pkM, (size_t)NS * NV * N * nd);
     A((void **)&f.pkR, (size_t)D * NV * N * nd);
@@ -519,12 +543,15 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
     A((void **)&s->node_mark, Np * sizeof(int));
     A((void **)&s->cell_mark, N * sizeof(int));
     A((void **)&s->totals, 8 * nd);
+    A((void **)&s->ctl, sizeof(Ctl));
+    A((void **)&s->d_report, sizeof(Report));
     if (r) {
         state_free(s);
         return r;
     }
     if (cudaMallocHost((void **)&s->h_cnt, CNT_N * sizeof(int)) != cudaSuccess ||
-        cudaMallocHost((void **)&s->h_dt, 4 * nd) != cudaSuccess) {
+        cudaMallocHost((void **)&s->h_dt, 4 * nd) != cudaSuccess ||
+        cudaMallocHost((void **)&s->h_report, sizeof(Report)) != cudaSuccess) {
         cudaGetLastError();
         state_free(s);
         return fail(LMOOD_ERR_OOM, "lmood_state_init: pinned host allocation failed");
@@ -549,6 +576,7 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
         cudaMemsetAsync(f.vp, 0, D * Np * nd, st);
         cudaMemsetAsync(dt0, 0, M->n_inst * nd, st);
         cudaMemsetAsync(f.cnt, 0, CNT_N * sizeof(int), st);
+        cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), st);
         const Ops &op = *M->ops;
         Prm p0 = s->kp;
         p0.base_order = 1;
@@ -574,69 +602,129 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
 // =======================================================================================
 // step
 // =======================================================================================
-extern "C" lmood_status lmood_step(lmood_state s, lmood_step_info *info) {
-    if (!s) return fail(LMOOD_ERR_ARG, "lmood_step: NULL state");
-    if (s->broken) return fail(LMOOD_ERR_STATE, "lmood_step: state unusable after an earlier CUDA error");
+// The kernels of one step on stream st for the state's current buffers. Host mode stops after
+// the full-mesh update (the host then drives the MOOD rounds); for graph capture the MOOD loop
+// is a conditional while node whose body (two rounds, T0 -> T1 -> T0) is captured on body_st.
+static void enqueue_mood_round(lmood_state s, const Fld &f, int cur, int n_in, cudaStream_t st) {
     lmood_mesh M = s->M;
     const Ops &op = *M->ops;
     const Geo &g = M->geo;
-    Fld &f = s->f;
-    cudaStream_t st = M->st;
     const int N = (int)M->nc, Np = (int)M->np, NV = M->dim + 1;
-    LM_CUDA(cudaMemsetAsync(f.cnt, 0, CNT_N * sizeof(int), st));
-    timed(s, LMOOD_K_PREDICT, 1, [&] { op.predict(g, f, s->kp, nullptr, nullptr, N, st); });
-    timed(s, LMOOD_K_NODES, 1, [&] { op.nodes(g, f, nullptr, nullptr, Np, 0, st); });
-    int cur = 0;
-    timed(s, LMOOD_K_UPDATE, 1, [&] { op.update(g, f, s->kp, nullptr, nullptr, N, s->tl[cur], f.cnt + CNT_T0 + cur, st); });
-    LM_CUDA(cudaMemcpyAsync(s->h_cnt, f.cnt, CNT_N * sizeof(int), cudaMemcpyDeviceToHost, st));
-    lmood_status r = sync_check(s, "lmood_step");
-    if (r) return r;
-    timing_drain(s);
-    int nT = s->h_cnt[CNT_T0];
-    int iters = 0, n_troubled = 0;
-    while (nT > 0) {
-        if (++iters > s->prm.max_mood_iters)
-            return fail(LMOOD_ERR_MOOD_ITERS, "lmood_step: troubled cells remain after max_mood_iters MOOD iterations");
-        n_troubled += nT;
-        ++s->stamp;
-        const int nxt = cur ^ 1;
-        LM_CUDA(cudaMemsetAsync(f.cnt + CNT_T0 + nxt, 0, sizeof(int), st));
-        LM_CUDA(cudaMemsetAsync(f.cnt + CNT_NODES, 0, 2 * sizeof(int), st));
-        const int nb_nodes = (int)std::min<int64_t>(Np, (int64_t)NV * nT);
-        const int nb_cells = (int)std::min<int64_t>(N, (int64_t)M->max_deg * nb_nodes);
-        timed(s, LMOOD_K_MOOD, 5, [&] {
-            op.mark_nodes(g, f, s->tl[cur], f.cnt + CNT_T0 + cur, nT, s->node_mark, s->stamp, s->nlist, st);
-            op.mark_cells(g, f, s->nlist, nb_nodes, s->cell_mark, s->stamp, s->clist, st);
-            op.predict(g, f, s->kp, s->tl[cur], f.cnt + CNT_T0 + cur, nT, st);
-            op.nodes(g, f, s->nlist, f.cnt + CNT_NODES, nb_nodes, 0, st);
-            op.update(g, f, s->kp, s->clist, f.cnt + CNT_CELLS, nb_cells, s->tl[nxt], f.cnt + CNT_T0 + nxt, st);
-        });
-        LM_CUDA(cudaMemcpyAsync(s->h_cnt, f.cnt, CNT_N * sizeof(int), cudaMemcpyDeviceToHost, st));
-        if ((r = sync_check(s, "lmood_step (MOOD)"))) return r;
-        timing_drain(s);
-        cur = nxt;
-        nT = s->h_cnt[CNT_T0 + cur];
+    const int in = CNT_T0 + cur, out = CNT_T0 + (cur ^ 1);
+    const int nb_nodes = (int)std::min<int64_t>(Np, (int64_t)NV * n_in);
+    const int nb_cells = (int)std::min<int64_t>(N, (int64_t)M->max_deg * nb_nodes);
+    op.round_begin(f, s->ctl, in, out, s->prm.max_mood_iters, st);
+    op.mark_nodes(g, f, s->tl[cur], f.cnt + in, n_in, s->node_mark, s->ctl, s->nlist, st);
+    op.mark_cells(g, f, s->nlist, nb_nodes, s->cell_mark, s->ctl, s->clist, st);
+    op.predict(g, f, s->kp, s->tl[cur], f.cnt + in, n_in, st);
+    op.nodes(g, f, s->nlist, f.cnt + CNT_NODES, nb_nodes, 0, st);
+    op.update(g, f, s->kp, s->clist, f.cnt + CNT_CELLS, nb_cells, s->tl[cur ^ 1], f.cnt + out, st);
+}
+
+static lmood_status build_graph(lmood_state s, int par) {
+    lmood_mesh M = s->M;
+    const Ops &op = *M->ops;
+    const Geo &g = M->geo;
+    cudaStream_t st = s->cap_st;
+    const Fld &f = s->f;
+    const int N = (int)M->nc, Np = (int)M->np;
+    cudaGraph_t G = nullptr;
+    LM_CUDA(cudaGraphCreate(&G, 0));
+    s->graph[par] = G;
+    cudaGraphConditionalHandle h;
+    LM_CUDA(cudaGraphConditionalHandleCreate(&h, G, 0, cudaGraphCondAssignDefault));
+    for (auto &e : s->gev[par]) LM_CUDA(cudaEventCreate(&e));
+    cudaEvent_t *ev = s->gev[par];
+    LM_CUDA(cudaStreamBeginCaptureToGraph(st, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(f.cnt, 0, CNT_N * sizeof(int), st);
+    op.ctl_reset(s->ctl, st);
+    cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+    op.predict(g, f, s->kp, nullptr, nullptr, N, st);
+    cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
+    op.nodes(g, f, nullptr, nullptr, Np, 0, st);
+    cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
+    op.update(g, f, s->kp, nullptr, nullptr, N, s->tl[0], f.cnt + CNT_T0, st);
+    cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
+    op.loop_cond(h, f, s->ctl, st);
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+    cudaGraphNode_t wnode = nullptr;
+    cudaGraphNodeParams cp = {};
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&wnode, G, deps, nullptr, ndeps, &cp);
     }
-    timed(s, LMOOD_K_FINALIZE, 2, [&] {
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(s->body_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            enqueue_mood_round(s, f, 0, N, s->body_st);
+            enqueue_mood_round(s, f, 1, N, s->body_st);
+            op.loop_cond(h, f, s->ctl, s->body_st);
+            cudaGraph_t bg = nullptr;
+            e = cudaStreamEndCapture(s->body_st, &bg);
+        }
+    }
+    if (e == cudaSuccess) {
+        cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
         op.dt_init(f, s->kp, M->n_inst, 0, st);
         op.finalize(g, f, s->kp, st);
-    });
-    LM_CUDA(cudaMemcpyAsync(s->h_cnt, f.cnt, CNT_N * sizeof(int), cudaMemcpyDeviceToHost, st));
-    LM_CUDA(cudaMemcpyAsync(s->h_dt, f.dt, sizeof(double), cudaMemcpyDeviceToHost, st));
-    LM_CUDA(cudaMemcpyAsync(s->h_dt + 1, f.dtn, sizeof(double), cudaMemcpyDeviceToHost, st));
-    if ((r = sync_check(s, "lmood_step (finalize)"))) return r;
-    timing_drain(s);
+        op.report(f, s->ctl, s->d_report, st);
+        cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
+        cudaMemcpyAsync(s->h_report, s->d_report, sizeof(Report), cudaMemcpyDeviceToHost, st);
+    }
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(st, &out);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->gexec[par], G, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LMOOD_ERR_CUDA, std::string("lmood_step: building the step graph failed: ") + cudaGetErrorString(e));
+    }
+    return LMOOD_OK;
+}
+
+static lmood_status ensure_graphs(lmood_state s) {
+    if (s->graphs_built) return LMOOD_OK;
+    if (!s->body_st) LM_CUDA(cudaStreamCreateWithFlags(&s->body_st, cudaStreamNonBlocking));
+    if (!s->cap_st) LM_CUDA(cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking));
+    LM_CUDA(cudaStreamSynchronize(s->M->st));
+    // graph[p] is captured with the buffers the state has when its parity is p
+    for (int k = 0; k < 2; ++k) {
+        const int par = s->parity;
+        lmood_status r = build_graph(s, par);
+        swap_state(s);
+        if (r) {
+            if (k == 0) swap_state(s);
+            return r;
+        }
+    }
+    s->graphs_built = true;
+    return LMOOD_OK;
+}
+
+static lmood_status finish_step(lmood_state s, const Report &rep, lmood_step_info *info) {
     lmood_step_info in{};
-    in.n_troubled = n_troubled;
-    in.mood_iters = iters;
-    in.n_p0 = s->h_cnt[CNT_P0];
-    in.n_parachute = s->h_cnt[CNT_PARA];
-    in.n_p0_eps = s->h_cnt[CNT_EPS];
-    in.dt_used = s->h_dt[0];
-    in.dt_next = s->h_dt[1];
+    in.n_troubled = rep.n_troubled;
+    in.mood_iters = rep.mood_iters;
+    in.n_p0 = rep.n_p0;
+    in.n_parachute = rep.n_para;
+    in.n_p0_eps = rep.n_eps;
+    in.dt_used = rep.dt_used;
+    in.dt_next = rep.dt_next;
+    in.t = s->t;
+    in.step = s->step;
+    if (rep.err) {
+        if (info) *info = in;
+        return fail(LMOOD_ERR_MOOD_ITERS, "lmood_step: troubled cells remain after max_mood_iters MOOD iterations");
+    }
     if (in.n_parachute > 0) {
-        in.t = s->t;
-        in.step = s->step;
         if (info) *info = in;
         return fail(LMOOD_ERR_PARACHUTE, "lmood_step: " + std::to_string(in.n_parachute) +
                                              " first-order cells are not computable (parachute failure)");
@@ -649,6 +737,76 @@ extern "C" lmood_status lmood_step(lmood_state s, lmood_step_info *info) {
     s->last = in;
     if (info) *info = in;
     return LMOOD_OK;
+}
+
+static lmood_status step_graph(lmood_state s, lmood_step_info *info) {
+    lmood_status r = ensure_graphs(s);
+    if (r) return r;
+    const int par = s->parity;
+    LM_CUDA(cudaGraphLaunch(s->gexec[par], s->M->st));
+    if ((r = sync_check(s, "lmood_step (graph)"))) return r;
+    const Report rep = *s->h_report;
+    if (s->timing) {
+        float ms[5];
+        for (int i = 0; i < 5; ++i)
+            if (cudaEventElapsedTime(&ms[i], s->gev[par][i], s->gev[par][i + 1]) != cudaSuccess) {
+                ms[i] = 0.f;
+                cudaGetLastError();
+            }
+        const int cls[5] = {LMOOD_K_PREDICT, LMOOD_K_NODES, LMOOD_K_UPDATE, LMOOD_K_MOOD, LMOOD_K_FINALIZE};
+        for (int i = 0; i < 5; ++i) s->kms[cls[i]] += ms[i];
+    }
+    s->klaunch[LMOOD_K_PREDICT] += 1;
+    s->klaunch[LMOOD_K_NODES] += 1;
+    s->klaunch[LMOOD_K_UPDATE] += 1;
+    s->klaunch[LMOOD_K_MOOD] += 2 + 13 * ((rep.mood_iters + 1) / 2);  // ctl reset, first condition, bodies
+    s->klaunch[LMOOD_K_FINALIZE] += 3;
+    return finish_step(s, rep, info);
+}
+
+static lmood_status step_host(lmood_state s, lmood_step_info *info) {
+    lmood_mesh M = s->M;
+    const Ops &op = *M->ops;
+    const Geo &g = M->geo;
+    Fld &f = s->f;
+    cudaStream_t st = M->st;
+    const int N = (int)M->nc, Np = (int)M->np;
+    LM_CUDA(cudaMemsetAsync(f.cnt, 0, CNT_N * sizeof(int), st));
+    op.ctl_reset(s->ctl, st);
+    timed(s, LMOOD_K_PREDICT, 1, [&] { op.predict(g, f, s->kp, nullptr, nullptr, N, st); });
+    timed(s, LMOOD_K_NODES, 1, [&] { op.nodes(g, f, nullptr, nullptr, Np, 0, st); });
+    timed(s, LMOOD_K_UPDATE, 1, [&] { op.update(g, f, s->kp, nullptr, nullptr, N, s->tl[0], f.cnt + CNT_T0, st); });
+    LM_CUDA(cudaMemcpyAsync(s->h_cnt, f.cnt, CNT_N * sizeof(int), cudaMemcpyDeviceToHost, st));
+    lmood_status r = sync_check(s, "lmood_step");
+    if (r) return r;
+    timing_drain(s);
+    int cur = 0;
+    int nT = s->h_cnt[CNT_T0];
+    while (nT > 0) {
+        timed(s, LMOOD_K_MOOD, 6, [&] { enqueue_mood_round(s, f, cur, nT, st); });
+        LM_CUDA(cudaMemcpyAsync(s->h_cnt, f.cnt, CNT_N * sizeof(int), cudaMemcpyDeviceToHost, st));
+        LM_CUDA(cudaMemcpyAsync(s->h_report, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        if ((r = sync_check(s, "lmood_step (MOOD)"))) return r;
+        timing_drain(s);
+        if (reinterpret_cast<const Ctl *>(s->h_report)->err) break;
+        cur ^= 1;
+        nT = s->h_cnt[CNT_T0 + cur];
+    }
+    timed(s, LMOOD_K_FINALIZE, 3, [&] {
+        op.dt_init(f, s->kp, M->n_inst, 0, st);
+        op.finalize(g, f, s->kp, st);
+        op.report(f, s->ctl, s->d_report, st);
+    });
+    LM_CUDA(cudaMemcpyAsync(s->h_report, s->d_report, sizeof(Report), cudaMemcpyDeviceToHost, st));
+    if ((r = sync_check(s, "lmood_step (finalize)"))) return r;
+    timing_drain(s);
+    return finish_step(s, *s->h_report, info);
+}
+
+extern "C" lmood_status lmood_step(lmood_state s, lmood_step_info *info) {
+    if (!s) return fail(LMOOD_ERR_ARG, "lmood_step: NULL state");
+    if (s->broken) return fail(LMOOD_ERR_STATE, "lmood_step: state unusable after an earlier CUDA error");
+    return s->prm.graph ? step_graph(s, info) : step_host(s, info);
 }
 
 extern "C" lmood_status lmood_run(lmood_state s, int64_t nsteps, lmood_step_info *last) {

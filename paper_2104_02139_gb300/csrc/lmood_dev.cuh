@@ -40,6 +40,7 @@ struct Fld {
     double *v, *e, *F, *v1, *e1, *F1;
     double *xc, *xc1, *rho, *rho1, *tau1;
     double *z, *z1;              // acoustic impedance rho a of the current / candidate state
+    double *rlo, *rhi;           // [Np] range of rho^n over the cells around each node
     const double *im;            // 1 / m_c
     double *pkM, *pkR;
     unsigned char *order, *pflag;
@@ -47,6 +48,17 @@ struct Fld {
     const double *dt;            // [n_inst] dt of this step
     unsigned long long *dtn;     // [n_inst] bit pattern of the next dt (positive doubles order as integers)
     int *cnt;                    // device counters, see CNT_*
+};
+
+// MOOD control block (device): mark stamp, rounds taken, troubled cells, error flag
+struct Ctl {
+    int stamp, iters, troubled, err;
+};
+
+// per-step report written by the last kernel of a step and copied to the host
+struct Report {
+    int n_troubled, mood_iters, err, n_p0, n_para, n_eps, pad0, pad1;
+    double dt_used, dt_next;
 };
 
 enum { CNT_T0 = 0, CNT_T1 = 1, CNT_NODES = 2, CNT_CELLS = 3, CNT_P0 = 4, CNT_PARA = 5, CNT_EPS = 6, CNT_N = 8 };
@@ -185,12 +197,28 @@ __device__ __forceinline__ double rcbrt_j(double J) {
     return fma(y, q, y);
 }
 
-// log J: for |J - 1| <= 1/8, ln J = 2 atanh(s) = 2 (s + s^3/3 + ... + s^13/13 + ...) with
-// s = (J - 1)/(J + 1), |s| <= 1/15 (the dropped tail is below 2e-17 relative); elsewhere
-// (large strains, and J <= 0 which gives NaN / -inf) the CUDA log.
+// log J with few FP64 operations (d = J - 1):
+//  |d| <= 1/64 : Taylor series ln(1 + d) = d - d^2/2 + ... - d^10/10 (tail < 1e-20 relative);
+//  |d| <= 1/8  : ln J = 2 atanh(s) = 2 (s + s^3/3 + ... + s^13/13), s = d/(J + 1), |s| <= 1/15
+//                (tail below 2e-17 relative);
+//  elsewhere (large strains, and J <= 0 which gives NaN / -inf): the CUDA log.
 __device__ __forceinline__ double log_j(double J) {
     const double d = J - 1.0;
-    if (!(fabs(d) <= 0.125)) return log(J);
+    const double ad = fabs(d);
+    if (ad <= 0.015625) {
+        double p = -1.0 / 10.0;
+        p = fma(p, d, 1.0 / 9.0);
+        p = fma(p, d, -1.0 / 8.0);
+        p = fma(p, d, 1.0 / 7.0);
+        p = fma(p, d, -1.0 / 6.0);
+        p = fma(p, d, 1.0 / 5.0);
+        p = fma(p, d, -1.0 / 4.0);
+        p = fma(p, d, 1.0 / 3.0);
+        p = fma(p, d, -1.0 / 2.0);
+        p = fma(p, d, 1.0);
+        return d * p;
+    }
+    if (!(ad <= 0.125)) return log(J);
     const double s = d / (J + 1.0);
     const double s2 = s * s;
     double p = 1.0 / 13.0;

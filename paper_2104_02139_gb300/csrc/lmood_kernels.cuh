@@ -17,12 +17,8 @@ namespace lmood {
 constexpr int kCellBlock = 128;
 constexpr int kNodeBlock = 256;
 
-__device__ __forceinline__ bool list_entity(const int *list, const int *cnt, int n, int i, int &e) {
-    const int nn = list ? *cnt : n;
-    if (i >= nn) return false;
-    e = list ? list[i] : i;
-    return true;
-}
+// list launches use at most this many blocks and loop over the device-counted list
+constexpr int kListBlocks = 152 * 8;
 
 // ---------------------------------------------------------------------------------------
 // k_predict: corner packets of a cell (Sect. "Space-Time discretization --- ADER
@@ -34,14 +30,11 @@ __device__ __forceinline__ bool list_entity(const int *list, const int *cnt, int
 // With a list, only the listed cells (troubled ones, already marked P0) are recomputed.
 // ---------------------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, const int *__restrict__ list,
-                                                        const int *__restrict__ cnt, int n) {
+__device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const Prm &prm, int c, bool listed) {
     constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + DD;
-    int c;
-    if (!list_entity(list, cnt, n, blockIdx.x * blockDim.x + threadIdx.x, c)) return;
     const int N = g.N, Np = g.Np, NC = NV * N;
     int ord;
-    if (list) {
+    if (listed) {
         ord = f.order[c];
     } else {
         ord = prm.base_order;
@@ -177,7 +170,10 @@ __global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, c
         for (int k = 0; k < NV; ++k)
 #pragma unroll
             for (int a = 0; a < D; ++a) dxs[k][a] = xs[k][a] - xcc[a];
-        // predictor, pass 1: dv/dt = (1/m) sum_q T(F_h(x_q)) l n_q
+        // predictor, pass 1: dv/dt = (1/m) sum_q T(F_h(x_q)) l n_q. The corner values F_h are
+        // kept for pass 2 in 2D; in 3D (registers) pass 2 recomputes them.
+        constexpr int KEEP = D == 2 ? NV : 1;
+        double Fhk[KEEP][DD];
         double dvdt[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) dvdt[a] = 0.0;
@@ -190,6 +186,7 @@ __global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, c
 #pragma unroll
                 for (int a = 0; a < D; ++a) s += gs[D + q][a] * dxs[k][a];
                 Fh[q] = s;
+                if constexpr (D == 2) Fhk[k][q] = s;
             }
             stress<D>(Fh, muc, kap, T);
 #pragma unroll
@@ -224,9 +221,14 @@ __global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, c
             }
 #pragma unroll
             for (int q = 0; q < DD; ++q) {
-                double s = Fc[q];
+                double s;
+                if constexpr (D == 2) {
+                    s = Fhk[k][q];
+                } else {
+                    s = Fc[q];
 #pragma unroll
-                for (int a = 0; a < D; ++a) s += gs[D + q][a] * dxs[k][a];
+                    for (int a = 0; a < D; ++a) s += gs[D + q][a] * dxs[k][a];
+                }
                 Fs[q] = fma(0.5 * dt, dFdt[q], s);
             }
             stress<D>(Fs, muc, kap, T);
@@ -240,6 +242,21 @@ __global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, c
     }
 }
 
+// LISTED = false: one thread per cell of the whole mesh; true: a grid-stride loop over a
+// device-counted list (separate instances, so each gets its own register allocation)
+template <int D, bool LISTED>
+__global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, const int *__restrict__ list,
+                                                        const int *__restrict__ cnt, int n) {
+    if constexpr (!LISTED) {
+        const int c = blockIdx.x * blockDim.x + threadIdx.x;
+        if (c < n) predict_cell<D>(g, f, prm, c, false);
+    } else {
+        const int nn = *cnt;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
+            predict_cell<D>(g, f, prm, list[i], true);
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // k_nodes: Eucclhyd nodal solver (Eqs. nodal_solver^n, Mcp^n) with the BCs of Appendix B:
 // M_p = sum_c M_cp, b_p = sum_c rhs_cp in ascending cell id, v*_p the Galerkin solution of
@@ -247,17 +264,17 @@ __global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, c
 // v_p^{n+1} = 2 v*_p - v_p^n. init_mode stores v*_p as v_p^0 and moves nothing.
 // ---------------------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(kNodeBlock) k_nodes(Geo g, Fld f, const int *__restrict__ list,
-                                                      const int *__restrict__ cnt, int n, int init_mode) {
+__device__ __forceinline__ void node_solve(const Geo &g, const Fld &f, int p, int init_mode) {
     constexpr int NV = D + 1, NS = D * (D + 1) / 2, DD = D * D;
-    int p;
-    if (!list_entity(list, cnt, n, blockIdx.x * blockDim.x + threadIdx.x, p)) return;
     const int Np = g.Np, NC = NV * g.N;
     double Ms[NS], b[D];
 #pragma unroll
     for (int s = 0; s < NS; ++s) Ms[s] = 0.0;
 #pragma unroll
     for (int a = 0; a < D; ++a) b[a] = 0.0;
+    // also the range of rho^n over the cells around the node (RDMP bounds, Eq. RDMP: the
+    // union over a cell's nodes is its stencil plus the cell itself)
+    double rlo = __longlong_as_double(0x7ff0000000000000LL), rhi = -rlo;
     const int j1 = __ldg(g.n2c_off + p + 1);
     for (int j = __ldg(g.n2c_off + p); j < j1; ++j) {
         const int cid = __ldg(g.n2c + j);
@@ -265,7 +282,16 @@ __global__ void __launch_bounds__(kNodeBlock) k_nodes(Geo g, Fld f, const int *_
         for (int s = 0; s < NS; ++s) Ms[s] += f.pkM[s * NC + cid];
 #pragma unroll
         for (int a = 0; a < D; ++a) b[a] += f.pkR[a * NC + cid];
+        int cc = cid;  // corner id k N + c -> cell c (k < 4)
+        cc -= cc >= g.N ? g.N : 0;
+        cc -= cc >= g.N ? g.N : 0;
+        cc -= cc >= g.N ? g.N : 0;
+        const double r = f.rho[cc];
+        rlo = fmin(rlo, r);
+        rhi = fmax(rhi, r);
     }
+    f.rlo[p] = rlo;
+    f.rhi[p] = rhi;
     double M[DD];
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -339,6 +365,19 @@ __global__ void __launch_bounds__(kNodeBlock) k_nodes(Geo g, Fld f, const int *_
     }
 }
 
+template <int D, bool LISTED>
+__global__ void __launch_bounds__(kNodeBlock) k_nodes(Geo g, Fld f, const int *__restrict__ list,
+                                                      const int *__restrict__ cnt, int n, int init_mode) {
+    if constexpr (!LISTED) {
+        const int p = blockIdx.x * blockDim.x + threadIdx.x;
+        if (p < n) node_solve<D>(g, f, p, init_mode);
+    } else {
+        const int nn = *cnt;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
+            node_solve<D>(g, f, list[i], init_mode);
+    }
+}
+
 // velocity gradient L_ij = (1/|w_c|) sum_p v_{p,i} ln_{p,j} (Eq. div_grad_v, read so that
 // dF/dt = L F), with ln_p = -N_p / D: L = -(1 / (D |w_c|)) sum_p v_p (x) N_p
 template <int D>
@@ -364,11 +403,8 @@ __device__ __forceinline__ void vel_gradient(const double (&vn)[D + 1][D], const
 // appended to tlist.
 // ---------------------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(kCellBlock) k_update(Geo g, Fld f, Prm prm, const int *__restrict__ list,
-                                                       const int *__restrict__ cnt, int n, int *tlist, int *tcnt) {
+__device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Prm &prm, int c, int *tlist, int *tcnt) {
     constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2;
-    int c;
-    if (!list_entity(list, cnt, n, blockIdx.x * blockDim.x + threadIdx.x, c)) return;
     const int N = g.N, Np = g.Np, NC = NV * N;
     const int ord = f.order[c];
     const double dt = f.dt[g.cell_inst ? __ldg(g.cell_inst + c) : 0];
@@ -458,17 +494,24 @@ __global__ void __launch_bounds__(kCellBlock) k_update(Geo g, Fld f, Prm prm, co
     const double rho1 = mc / V1;
     f.rho1[c] = rho1;
     f.tau1[c] = V1 * im;
+    double area1 = 0.0;  // sum of the face measures at x^{n+1} (in-sphere diameter 2 D V / area)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) s += Nf1[k][a] * Nf1[k][a];
+        area1 += sqrt(s);
+    }
     if (prm.mood) {
         const int ps = pad_state<D>(v1, e1, F1, V1);
         if (ord == 2) {
             bool bad = ps != 0;
             if (!bad) {
-                double lo = f.rho[c], hi = lo;
-                const int j1 = __ldg(g.st_off + c + 1);
-                for (int j = __ldg(g.st_off + c); j < j1; ++j) {
-                    const double r = f.rho[__ldg(g.st_idx + j)];
-                    lo = fmin(lo, r);
-                    hi = fmax(hi, r);
+                double lo = f.rlo[nod[0]], hi = f.rhi[nod[0]];
+#pragma unroll
+                for (int k = 1; k < NV; ++k) {
+                    lo = fmin(lo, f.rlo[nod[k]]);
+                    hi = fmax(hi, f.rhi[nod[k]]);
                 }
                 const double delta = fmax(prm.delta0, prm.delta1 * (hi - lo));
                 bad = !(rho1 >= lo - delta && rho1 <= hi + delta);
@@ -478,40 +521,98 @@ __global__ void __launch_bounds__(kCellBlock) k_update(Geo g, Fld f, Prm prm, co
             f.pflag[c] = (unsigned char)ps;
         }
     }
-    // next impedance and dt candidate: C_CFL L_c / a = C_CFL L_c rho / z
+    // next impedance and dt candidate: C_CFL L_c / a = C_CFL (2 D V / area) (m / V) / z
     const double z1 = impedance<D>(F1, rho1, muc, kap);
     f.z1[c] = z1;
-    double dtc = prm.cfl * insphere<D>(V1, Nf1) * rho1 / z1;
+    double dtc = prm.cfl * (2.0 * D) * mc / (area1 * z1);
     const double dV = V1 - V0;
     if (dV != 0.0) dtc = fmin(dtc, prm.Cv * dt * V0 / fabs(dV));
     f.dtc[c] = dtc;
 }
 
+template <int D, bool LISTED>
+__global__ void __launch_bounds__(kCellBlock) k_update(Geo g, Fld f, Prm prm, const int *__restrict__ list,
+                                                       const int *__restrict__ cnt, int n, int *tlist, int *tcnt) {
+    if constexpr (!LISTED) {
+        const int c = blockIdx.x * blockDim.x + threadIdx.x;
+        if (c < n) update_cell<D>(g, f, prm, c, tlist, tcnt);
+    } else {
+        const int nn = *cnt;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
+            update_cell<D>(g, f, prm, list[i], tlist, tcnt);
+    }
+}
+
+// MOOD round bookkeeping on the device (one thread): the round consumes the troubled list
+// counted in cnt[in]; a new mark stamp, the output counters cleared, the iteration bound
+// checked (exceeding it sets ctl->err and empties the round).
+static __global__ void k_round_begin(Fld f, Ctl *ctl, int in, int out, int max_iters) {
+    const int n = f.cnt[in];
+    if (n > 0) {
+        if (ctl->iters >= max_iters) {
+            ctl->err = 1;
+            f.cnt[in] = 0;
+        } else {
+            ctl->iters += 1;
+            ctl->troubled += n;
+            ctl->stamp += 1;
+        }
+    }
+    f.cnt[out] = 0;
+    f.cnt[CNT_NODES] = 0;
+    f.cnt[CNT_CELLS] = 0;
+}
+
+static __global__ void k_ctl_reset(Ctl *ctl) {
+    ctl->iters = 0;
+    ctl->troubled = 0;
+    ctl->err = 0;
+}
+
 // troubled cells become P0; their nodes are appended (once) to the node list
 template <int D>
 __global__ void k_mark_nodes(Geo g, Fld f, const int *__restrict__ tlist, const int *__restrict__ tcnt,
-                             int *node_mark, int stamp, int *nlist) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *tcnt) return;
-    const int c = tlist[i];
-    f.order[c] = 1;
+                             int *node_mark, const Ctl *ctl, int *nlist) {
+    const int n = *tcnt, stamp = ctl->stamp;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = tlist[i];
+        f.order[c] = 1;
 #pragma unroll
-    for (int k = 0; k < D + 1; ++k) {
-        const int p = __ldg(g.c2n + k * g.N + c);
-        if (atomicExch(node_mark + p, stamp) != stamp) nlist[atomicAdd(f.cnt + CNT_NODES, 1)] = p;
+        for (int k = 0; k < D + 1; ++k) {
+            const int p = __ldg(g.c2n + k * g.N + c);
+            if (atomicExch(node_mark + p, stamp) != stamp) nlist[atomicAdd(f.cnt + CNT_NODES, 1)] = p;
+        }
     }
 }
 
 // every cell around a listed node is appended (once) to the cell list
-static __global__ void k_mark_cells(Geo g, Fld f, const int *__restrict__ nlist, int *cell_mark, int stamp, int *clist) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= f.cnt[CNT_NODES]) return;
-    const int p = nlist[i];
-    const int j1 = g.n2c_off[p + 1];
-    for (int j = g.n2c_off[p]; j < j1; ++j) {
-        const int c = g.n2c[j] % g.N;
-        if (atomicExch(cell_mark + c, stamp) != stamp) clist[atomicAdd(f.cnt + CNT_CELLS, 1)] = c;
+static __global__ void k_mark_cells(Geo g, Fld f, const int *__restrict__ nlist, int *cell_mark, const Ctl *ctl,
+                                    int *clist) {
+    const int n = f.cnt[CNT_NODES], stamp = ctl->stamp;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int p = nlist[i];
+        const int j1 = g.n2c_off[p + 1];
+        for (int j = g.n2c_off[p]; j < j1; ++j) {
+            const int c = g.n2c[j] % g.N;
+            if (atomicExch(cell_mark + c, stamp) != stamp) clist[atomicAdd(f.cnt + CNT_CELLS, 1)] = c;
+        }
     }
+}
+
+// while-loop condition of a graph-captured step: another MOOD round is needed
+static __global__ void k_loop_cond(cudaGraphConditionalHandle h, Fld f, const Ctl *ctl) {
+    cudaGraphSetConditional(h, (f.cnt[CNT_T0] > 0 && ctl->err == 0) ? 1u : 0u);
+}
+
+static __global__ void k_report(Fld f, const Ctl *ctl, Report *r) {
+    r->n_troubled = ctl->troubled;
+    r->mood_iters = ctl->iters;
+    r->err = ctl->err;
+    r->n_p0 = f.cnt[CNT_P0];
+    r->n_para = f.cnt[CNT_PARA];
+    r->n_eps = f.cnt[CNT_EPS];
+    r->dt_used = f.dt[0];
+    r->dt_next = __longlong_as_double((long long)f.dtn[0]);
 }
 
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {

@@ -12,9 +12,13 @@ struct Ops {
     void (*update)(const Geo &, const Fld &, const Prm &, const int *list, const int *cnt, int n, int *tlist,
                    int *tcnt, cudaStream_t);
     void (*mark_nodes)(const Geo &, const Fld &, const int *tlist, const int *tcnt, int n, int *node_mark,
-                       int stamp, int *nlist, cudaStream_t);
-    void (*mark_cells)(const Geo &, const Fld &, const int *nlist, int n, int *cell_mark, int stamp, int *clist,
-                       cudaStream_t);
+                       const Ctl *ctl, int *nlist, cudaStream_t);
+    void (*mark_cells)(const Geo &, const Fld &, const int *nlist, int n, int *cell_mark, const Ctl *ctl,
+                       int *clist, cudaStream_t);
+    void (*round_begin)(const Fld &, Ctl *ctl, int in, int out, int max_iters, cudaStream_t);
+    void (*ctl_reset)(Ctl *ctl, cudaStream_t);
+    void (*loop_cond)(cudaGraphConditionalHandle h, const Fld &, const Ctl *ctl, cudaStream_t);
+    void (*report)(const Fld &, const Ctl *ctl, Report *r, cudaStream_t);
     void (*dt_init)(const Fld &, const Prm &, int n_inst, int first, cudaStream_t);
     void (*finalize)(const Geo &, const Fld &, const Prm &, cudaStream_t);
     void (*init_cells)(const Geo &, const Fld &, const Prm &, double rho0, double *m, double *im, int f_given,

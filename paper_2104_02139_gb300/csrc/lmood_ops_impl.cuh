@@ -8,28 +8,49 @@ namespace {
 
 inline int blocks(int n, int b) { return (n + b - 1) / b; }
 
+// a full launch covers n entities one per thread; a list launch (list != NULL) uses at most
+// kListBlocks blocks and loops over the device-counted list (n only bounds the grid)
+inline int grid_for(const int *list, int n, int b) {
+    const int g = blocks(n, b);
+    return list && g > kListBlocks ? kListBlocks : g;
+}
+
 template <int D>
 void predict(const Geo &g, const Fld &f, const Prm &p, const int *list, const int *cnt, int n, cudaStream_t s) {
-    if (n > 0) k_predict<D><<<blocks(n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n);
+    if (n <= 0) return;
+    if (list) k_predict<D, true><<<grid_for(list, n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n);
+    else k_predict<D, false><<<blocks(n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n);
 }
 template <int D>
 void nodes(const Geo &g, const Fld &f, const int *list, const int *cnt, int n, int init_mode, cudaStream_t s) {
-    if (n > 0) k_nodes<D><<<blocks(n, kNodeBlock), kNodeBlock, 0, s>>>(g, f, list, cnt, n, init_mode);
+    if (n <= 0) return;
+    if (list) k_nodes<D, true><<<grid_for(list, n, kNodeBlock), kNodeBlock, 0, s>>>(g, f, list, cnt, n, init_mode);
+    else k_nodes<D, false><<<blocks(n, kNodeBlock), kNodeBlock, 0, s>>>(g, f, list, cnt, n, init_mode);
 }
 template <int D>
 void update(const Geo &g, const Fld &f, const Prm &p, const int *list, const int *cnt, int n, int *tlist, int *tcnt,
             cudaStream_t s) {
-    if (n > 0) k_update<D><<<blocks(n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n, tlist, tcnt);
+    if (n <= 0) return;
+    if (list) k_update<D, true><<<grid_for(list, n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n, tlist, tcnt);
+    else k_update<D, false><<<blocks(n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n, tlist, tcnt);
 }
 template <int D>
-void mark_nodes(const Geo &g, const Fld &f, const int *tlist, const int *tcnt, int n, int *node_mark, int stamp,
+void mark_nodes(const Geo &g, const Fld &f, const int *tlist, const int *tcnt, int n, int *node_mark, const Ctl *ctl,
                 int *nlist, cudaStream_t s) {
-    if (n > 0) k_mark_nodes<D><<<blocks(n, 256), 256, 0, s>>>(g, f, tlist, tcnt, node_mark, stamp, nlist);
+    if (n > 0) k_mark_nodes<D><<<grid_for(tlist, n, 256), 256, 0, s>>>(g, f, tlist, tcnt, node_mark, ctl, nlist);
 }
-void mark_cells(const Geo &g, const Fld &f, const int *nlist, int n, int *cell_mark, int stamp, int *clist,
+void mark_cells(const Geo &g, const Fld &f, const int *nlist, int n, int *cell_mark, const Ctl *ctl, int *clist,
                 cudaStream_t s) {
-    if (n > 0) k_mark_cells<<<blocks(n, 256), 256, 0, s>>>(g, f, nlist, cell_mark, stamp, clist);
+    if (n > 0) k_mark_cells<<<grid_for(nlist, n, 256), 256, 0, s>>>(g, f, nlist, cell_mark, ctl, clist);
 }
+void round_begin(const Fld &f, Ctl *ctl, int in, int out, int max_iters, cudaStream_t s) {
+    k_round_begin<<<1, 1, 0, s>>>(f, ctl, in, out, max_iters);
+}
+void ctl_reset(Ctl *ctl, cudaStream_t s) { k_ctl_reset<<<1, 1, 0, s>>>(ctl); }
+void loop_cond(cudaGraphConditionalHandle h, const Fld &f, const Ctl *ctl, cudaStream_t s) {
+    k_loop_cond<<<1, 1, 0, s>>>(h, f, ctl);
+}
+void report(const Fld &f, const Ctl *ctl, Report *r, cudaStream_t s) { k_report<<<1, 1, 0, s>>>(f, ctl, r); }
 void dt_init(const Fld &f, const Prm &p, int n_inst, int first, cudaStream_t s) {
     k_dt_init<<<blocks(n_inst, 128), 128, 0, s>>>(f, p, n_inst, first);
 }
@@ -51,8 +72,9 @@ template <int D> void totals(const Geo &g, const Fld &f, double *out, cudaStream
 }  // namespace
 
 #define LMOOD_OPS_TABLE(D)                                                                                  \
-    static const Ops table = {D,          predict<D>,  nodes<D>,   update<D>, mark_nodes<D>, mark_cells, \
-                              dt_init,    finalize,    init_cells<D>, refresh<D>, totals<D>};            \
+    static const Ops table = {D,           predict<D>, nodes<D>,  update<D>,     mark_nodes<D>, mark_cells, \
+                              round_begin, ctl_reset,  loop_cond, report,        dt_init,       finalize,   \
+                              init_cells<D>, refresh<D>, totals<D>};                                      \
     return table;
 
 }  // namespace lmood

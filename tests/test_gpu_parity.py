@@ -112,3 +112,28 @@ def test_energy_conservation_full_size():
     t1 = g.totals()
     assert abs(t1[4] - t0[4]) <= 1e-12 * abs(t0[4])
     assert t1[0] == pytest.approx(t0[0], rel=1e-14)
+
+
+def test_graph_and_host_modes_bitwise():
+    """The graph-captured step (MOOD loop as a device-side while node) and the host-driven
+    MOOD rounds give bitwise identical results and reports."""
+    for pb in (W.impact2d(n=120), W.cube3d(n=5)):
+        a, b = L.simulation(pb, graph=1), L.simulation(pb, graph=0)
+        for _ in range(8):
+            ia, ib = a.step(), b.step()
+            for k in ("n_troubled", "mood_iters", "n_p0", "dt_used", "dt_next"):
+                assert getattr(ia, k) == getattr(ib, k), k
+        for f in (L.FIELD_X, L.FIELD_VP, L.FIELD_V, L.FIELD_E, L.FIELD_F, L.FIELD_ORDER, L.FIELD_PKM):
+            assert np.array_equal(a.get(f), b.get(f)), f
+
+
+def test_mood_iteration_limit_reports_error():
+    """A step that would need more MOOD rounds than allowed returns LMOOD_ERR_MOOD_ITERS and
+    leaves the state unchanged (both modes)."""
+    pb = W.cube3d(n=6)
+    for graph in (1, 0):
+        s = L.simulation(pb, graph=graph, max_mood_iters=2)
+        before = s.state()
+        assert s.step_status() == L.ERR_MOOD_ITERS
+        for k, v in before.items():
+            assert np.array_equal(v, s.state()[k]), k
