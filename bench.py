@@ -211,7 +211,7 @@ def run_ours(args, rank, local, ws, dist):
     pb = W.impact2d()
     N = pb.mesh.n_cells
     stream = torch.cuda.Stream()
-    sim = L.simulation(pb, stream=stream.cuda_stream)
+    sim = L.simulation(pb, stream=stream.cuda_stream, graph=0 if args.host_mode else 1)
     info = sim.mesh.info()
     for _ in range(args.warmup):
         sim.step()
@@ -244,15 +244,17 @@ def run_ours(args, rank, local, ws, dist):
     dom = max(("predict", "nodes", "update"), key=lambda k: kt[k][0])
     dom_ms = kt[dom][0] / max(kt[dom][1], 1)
     gbs = kb[dom] / (dom_ms / 1e3) / 1e9
-    fp64_meas = fp64_peak_tflops(f"cuda:{local}")
+    fp64_meas = None if args.no_fp64_peak else fp64_peak_tflops(f"cuda:{local}")
+    fp64_peak = fp64_meas or FP64_PEAK_TFLOPS
     hbm = {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
            "algorithmic_bytes_per_launch": kb[dom], "peak_source": how}
     fpc = FP64_FLOP_PER_CELL.get(dom)
     if fpc:
         tf = fpc * N / (dom_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": tf, "peak": fp64_meas, "unit": "TFLOP/s",
-                "frac": tf / fp64_meas, "traffic": TRAFFIC_PER_LAUNCH.get(dom),
-                "peak_source": "measured cuBLAS DGEMM in this run (nominal 1.26)",
+        roof = {"bound": "alu", "kernel": dom, "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": tf / fp64_peak, "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+                "peak_source": ("measured cuBLAS DGEMM in this run (nominal 1.26)" if fp64_meas
+                                else "nominal 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"),
                 "fp64_flop_per_cell": fpc, "ms_per_launch": dom_ms, "hbm": hbm}
     else:
         roof = {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -285,6 +287,10 @@ def run_ours(args, rank, local, ws, dist):
         e2e = {"value": ws * N * k2 / el, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "steps": k2}
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(L, W, torch, local, value / ws, args)
+
     cb = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(W.impact2d())
@@ -297,8 +303,39 @@ def run_ours(args, rank, local, ws, dist):
                            "stencil_entries": info["stencil_nnz"], "parallelism": f"replicas x{ws}",
                            "l2": "working set > L2 (no flush)", "troubled_cells_in_timed_steps": troubled},
                 "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": ck, "e2e": e2e,
-                "cpu_baseline": cb}
+                "cpu_baseline": cb, "batched": batched}
         print(json.dumps(line), flush=True)
+
+
+def run_batched(L, W, torch, local, plain_value, args) -> dict:
+    """Batched configuration: 256 independent unit-square meshes (sizes log-uniform in [1e3, 2e5]
+    cells, own mu, amplitude and dt each) concatenated and advanced by one launch per stage in
+    graph-captured steps; cell-steps/s over all instances, and the ratio to the plain step."""
+    t0 = time.perf_counter()
+    probs = W.batched2d(workers=min(16, os.cpu_count() or 1))
+    pb, inst = W.concat(probs)
+    gen = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    sim = L.simulation(pb, stream=stream.cuda_stream, cell_inst=inst, n_inst=len(probs),
+                       graph=0 if args.host_mode else 1)
+    for _ in range(3):
+        sim.step()
+    k = max(10, args.steps // 5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tr = 0
+    for _ in range(k):
+        tr += sim.step().n_troubled
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    val = pb.mesh.n_cells * k / (ms / 1e3)
+    dt = sim.get(L.FIELD_DT)
+    return {"value": val, "unit": UNIT, "vs_plain": val / plain_value, "instances": len(probs),
+            "cells": pb.mesh.n_cells, "steps": k, "ms_per_step": ms / k, "troubled_cells": tr,
+            "dt_min": float(dt.min()), "dt_max": float(dt.max()), "mesh_generation_s": gen,
+            "launch": "one launch per stage for all instances, graph-captured steps"}
 
 
 def main():
@@ -309,6 +346,10 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-mode", action="store_true",
+                    help="host-driven MOOD rounds instead of graph-captured steps (same kernels; for profilers)")
+    ap.add_argument("--no-fp64-peak", action="store_true", help="skip the DGEMM FP64 peak measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-instances measurement")
     ap.add_argument("--case", type=int, default=0,
                     help="profiling case: build the workload, take this many untimed steps, exit")
     args = ap.parse_args()
@@ -317,7 +358,7 @@ def main():
         import paper_2104_02139_gb300 as L
         import workloads as W
         L.build()
-        sim = L.simulation(W.impact2d())
+        sim = L.simulation(W.impact2d(), graph=0 if args.host_mode else 1)
         for _ in range(args.case):
             info = sim.step()
         torch.cuda.synchronize()

@@ -291,25 +291,33 @@ def swinging_plate(n: int, jitter: float = 0.0, seed: int = 7, u0: float = 5e-4)
                    meta={"omega": omega, "u0": u0, "t_final": math.pi / omega, "amp": a})
 
 
+def _batch_instance(args) -> Problem:
+    i, n, mu, amp, steps = args
+    m = tri_mesh(n, 1000 + i, bc={"x0": SLIP, "x1": SLIP, "y0": SLIP, "y1": SLIP})
+    p = cell_points(m)
+    v = amp * np.stack([np.sin(np.pi * p[:, 0]) * np.sin(np.pi * p[:, 1]),
+                        np.cos(np.pi * p[:, 0]) * np.cos(np.pi * p[:, 1])])
+    return Problem(f"batch{i}_n{n}", m, 1.0, 2.0, np.full(m.n_cells, mu), v, 0.4, steps, meta={"amp": amp})
+
+
 def batched2d(n_inst: int = 256, seed: int = 4, lo: float = 1e3, hi: float = 2e5,
-              steps: int = 500) -> list[Problem]:
+              steps: int = 500, workers: int = 1) -> list[Problem]:
     """Independent unit-square instances: cell counts log-uniform in [lo, hi], per-instance
     mu ~ U[0.5, 2] and velocity amplitude A ~ U[1e-3, 0.2] applied to the plain2d field;
-    lambda=2, rho0=1, slip walls, CFL 0.4. Instance i meshes with seed 1000+i."""
+    lambda=2, rho0=1, slip walls, CFL 0.4. Instance i meshes with seed 1000+i. workers > 1
+    generates the meshes in spawned processes (same result)."""
     rng = np.random.default_rng(seed)
     ncell = np.exp(rng.uniform(math.log(lo), math.log(hi), n_inst))
     mus = rng.uniform(0.5, 2.0, n_inst)
     amps = rng.uniform(1e-3, 0.2, n_inst)
-    out = []
-    for i in range(n_inst):
-        n = int(math.ceil(1 + math.sqrt(ncell[i] / 2)))
-        m = tri_mesh(n, 1000 + i, bc={"x0": SLIP, "x1": SLIP, "y0": SLIP, "y1": SLIP})
-        p = cell_points(m)
-        v = amps[i] * np.stack([np.sin(np.pi * p[:, 0]) * np.sin(np.pi * p[:, 1]),
-                                np.cos(np.pi * p[:, 0]) * np.cos(np.pi * p[:, 1])])
-        out.append(Problem(f"batch{i}_n{n}", m, 1.0, 2.0, np.full(m.n_cells, mus[i]), v, 0.4, steps,
-                           meta={"amp": amps[i]}))
-    return out
+    jobs = [(i, int(math.ceil(1 + math.sqrt(ncell[i] / 2))), float(mus[i]), float(amps[i]), steps)
+            for i in range(n_inst)]
+    if workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_batch_instance, jobs, chunksize=4))
+    return [_batch_instance(j) for j in jobs]
 
 
 def concat(problems: list[Problem], name: str = "batch") -> tuple[Problem, np.ndarray]:
