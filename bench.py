@@ -32,6 +32,16 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-steps/s of full ADER-MOOD step (FP64, 1 GB300)"
 UNIT = "cell-steps/s"
 WORKLOAD = "impact2d: 999,698 triangles (708x708 jittered Delaunay lattice), rho0=8.93 mu=0.46 lambda=1.06, v=(-0.1,0), slip wall x=0, CFL 0.4"
+WORKLOADS = {
+    "impact2d": WORKLOAD,
+    "column3d": "column3d: 5,989,500 tetrahedra (55x55x330 jittered Kuhn cubes on 1x1x6), base clamped, rho0=1.1 mu=0.5 lambda=2.5, v=(0.1 (z/6)^2,0,0), CFL 0.25",
+    "cube3d": "cube3d: 511,104 tetrahedra (44^3 jittered Kuhn cubes), slip walls, rho0=1 lambda=2, mu=1+0.2 GRF, Taylor-Green v0 (amplitude 0.05), CFL 0.25",
+}
+
+
+def make_workload(name: str):
+    import workloads as W
+    return {"impact2d": W.impact2d, "column3d": W.column3d, "cube3d": W.cube3d}[name]()
 
 
 def _peaks():
@@ -189,13 +199,12 @@ def barrier(dist):
 def run_reference(args, rank, ws, dist):
     if rank != 0:
         return
-    import workloads as W
-    pb = W.impact2d()
+    pb = make_workload(args.workload)
     cb = cpu_baseline(pb, budget_s=max(10.0, 2.0 * args.steps / 100))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": pb.mesh.n_cells / cb["value"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "cells": pb.mesh.n_cells},
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "cells": pb.mesh.n_cells},
             "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -208,7 +217,7 @@ def run_ours(args, rank, local, ws, dist):
 
     torch.cuda.set_device(local)
     L.build()
-    pb = W.impact2d()
+    pb = make_workload(args.workload)
     N = pb.mesh.n_cells
     stream = torch.cuda.Stream()
     sim = L.simulation(pb, stream=stream.cuda_stream, graph=0 if args.host_mode else 1)
@@ -240,7 +249,7 @@ def run_ours(args, rank, local, ws, dist):
     # step is bound by the FP64 pipe: roofline = FP64 FLOP/s against the FP64 peak, with the
     # HBM figure beside it.
     peaks, how = _peaks()
-    kb = kernel_bytes(2, N, info["n_nodes"], info["stencil_nnz"])
+    kb = kernel_bytes(pb.mesh.dim, N, info["n_nodes"], info["stencil_nnz"])
     dom = max(("predict", "nodes", "update"), key=lambda k: kt[k][0])
     dom_ms = kt[dom][0] / max(kt[dom][1], 1)
     gbs = kb[dom] / (dom_ms / 1e3) / 1e9
@@ -248,7 +257,7 @@ def run_ours(args, rank, local, ws, dist):
     fp64_peak = fp64_meas or FP64_PEAK_TFLOPS
     hbm = {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
            "algorithmic_bytes_per_launch": kb[dom], "peak_source": how}
-    fpc = FP64_FLOP_PER_CELL.get(dom)
+    fpc = FP64_FLOP_PER_CELL.get(dom) if pb.mesh.dim == 2 else None
     if fpc:
         tf = fpc * N / (dom_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -267,8 +276,9 @@ def run_ours(args, rank, local, ws, dist):
     # pinned host memory, steps, and reads the new state back
     e2e = None
     if not args.no_e2e:
-        fields = ((L.FIELD_X, (2, info["n_nodes"])), (L.FIELD_VP, (2, info["n_nodes"])), (L.FIELD_V, (2, N)),
-                  (L.FIELD_E, (N,)), (L.FIELD_F, (4, N)), (L.FIELD_DT, (1,)))
+        d = pb.mesh.dim
+        fields = ((L.FIELD_X, (d, info["n_nodes"])), (L.FIELD_VP, (d, info["n_nodes"])), (L.FIELD_V, (d, N)),
+                  (L.FIELD_E, (N,)), (L.FIELD_F, (d * d, N)), (L.FIELD_DT, (1,)))
         bufs = {f: torch.empty(shp, dtype=torch.float64, pin_memory=True).numpy() for f, shp in fields}
         for f, _ in fields:
             sim.get(f, out=bufs[f])
@@ -293,13 +303,13 @@ def run_ours(args, rank, local, ws, dist):
 
     cb = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(W.impact2d())
+        cb = cpu_baseline(make_workload(args.workload))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "cells": N, "nodes": info["n_nodes"],
+                "config": {"workload": WORKLOADS[args.workload], "cells": N, "nodes": info["n_nodes"],
                            "stencil_entries": info["stencil_nnz"], "parallelism": f"replicas x{ws}",
                            "l2": "working set > L2 (no flush)", "troubled_cells_in_timed_steps": troubled},
                 "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": ck, "e2e": e2e,
@@ -346,6 +356,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="impact2d",
+                    help="impact2d (the metric's configuration, default) or a 3D configuration")
     ap.add_argument("--host-mode", action="store_true",
                     help="host-driven MOOD rounds instead of graph-captured steps (same kernels; for profilers)")
     ap.add_argument("--no-fp64-peak", action="store_true", help="skip the DGEMM FP64 peak measurement")
@@ -358,7 +370,7 @@ def main():
         import paper_2104_02139_gb300 as L
         import workloads as W
         L.build()
-        sim = L.simulation(W.impact2d(), graph=0 if args.host_mode else 1)
+        sim = L.simulation(make_workload(args.workload), graph=0 if args.host_mode else 1)
         for _ in range(args.case):
             info = sim.step()
         torch.cuda.synchronize()

@@ -302,6 +302,21 @@ static int cmp_long(const void *a, const void *b) {
     return (x > y) - (x < y);
 }
 
+/* the cells sharing at least one node with c, other than c, sorted and unique, into tmp */
+static int stencil_of(const OrcMesh *M, long c, long *tmp) {
+    int n = 0;
+    for (int k = 0; k < M->nv; ++k) {
+        int p = M->c2n[c * M->nv + k];
+        for (long j = M->n2c_off[p]; j < M->n2c_off[p + 1]; ++j)
+            if (M->n2c_cell[j] != c && n < 8192) tmp[n++] = M->n2c_cell[j];
+    }
+    qsort(tmp, n, sizeof(long), cmp_long);
+    int u = 0;
+    for (int i = 0; i < n; ++i)
+        if (u == 0 || tmp[i] != tmp[u - 1]) tmp[u++] = tmp[i];
+    return u;
+}
+
 void orc_mesh_free(OrcMesh *M) {
     if (!M) return;
     free(M->c2n); free(M->n2c_off); free(M->n2c_cell); free(M->n2c_k);
@@ -352,31 +367,27 @@ int orc_mesh_new(int d, long np, const double *x_soa, long nc, const int *c2n_so
         }
     free(fill);
     /* stencil V_c (reading R9): every other cell sharing at least one node with c,
-     * ascending cell id */
+     * ascending cell id (two passes: sizes, then entries; cells are independent) */
     M->st_off = calloc(nc + 1, sizeof(long));
-    long cap = nc * 16, used = 0;
-    M->st_idx = malloc(sizeof(long) * cap);
-    long *tmp = malloc(sizeof(long) * 8192);
-    for (long c = 0; c < nc; ++c) {
-        int n = 0;
-        for (int k = 0; k < nv; ++k) {
-            int p = M->c2n[c * nv + k];
-            for (long j = M->n2c_off[p]; j < M->n2c_off[p + 1]; ++j)
-                if (M->n2c_cell[j] != c && n < 8192) tmp[n++] = M->n2c_cell[j];
-        }
-        qsort(tmp, n, sizeof(long), cmp_long);
-        int u = 0;
-        for (int i = 0; i < n; ++i)
-            if (u == 0 || tmp[i] != tmp[u - 1]) tmp[u++] = tmp[i];
-        if (used + u > cap) {
-            cap = 2 * (used + u);
-            M->st_idx = realloc(M->st_idx, sizeof(long) * cap);
-        }
-        memcpy(M->st_idx + used, tmp, sizeof(long) * u);
-        used += u;
-        M->st_off[c + 1] = used;
+#pragma omp parallel
+    {
+        long *tmp = malloc(sizeof(long) * 8192);
+#pragma omp for schedule(static)
+        for (long c = 0; c < nc; ++c) M->st_off[c + 1] = stencil_of(M, c, tmp);
+        free(tmp);
     }
-    free(tmp);
+    for (long c = 0; c < nc; ++c) M->st_off[c + 1] += M->st_off[c];
+    M->st_idx = malloc(sizeof(long) * (M->st_off[nc] > 0 ? M->st_off[nc] : 1));
+#pragma omp parallel
+    {
+        long *tmp = malloc(sizeof(long) * 8192);
+#pragma omp for schedule(static)
+        for (long c = 0; c < nc; ++c) {
+            int u = stencil_of(M, c, tmp);
+            memcpy(M->st_idx + M->st_off[c], tmp, sizeof(long) * u);
+        }
+        free(tmp);
+    }
     /* boundary conditions (Appendix B; hierarchy clamped > slip > free, reading R14) */
     M->bc_ndof = malloc(sizeof(int) * np);
     M->bc_t = calloc(np * 6, sizeof(double));

@@ -67,3 +67,15 @@ def test_set_and_replay():
     b.step()
     for k, v in a.state().items():
         assert np.array_equal(v, b.state()[k]), k
+
+
+def test_empty_and_null_inputs():
+    m = W.tri_mesh(5, 1)
+    assert _status(lambda: L.Mesh(2, np.zeros((2, 0)), np.zeros((3, 0), np.int32))) == L.ERR_ARG
+    assert _status(lambda: L.Mesh(2, m.x, np.zeros((3, 0), np.int32))) == L.ERR_ARG
+    lib = L.lib()
+    import ctypes as C
+    h = C.c_void_p()
+    assert lib.lmood_mesh_create(2, 3, None, 1, None, 0, None, None, None, 1, None, C.byref(h)) == L.ERR_ARG
+    assert lib.lmood_step(None, None) == L.ERR_ARG
+    assert lib.lmood_get(None, 0, None, 0) == L.ERR_ARG

@@ -137,3 +137,39 @@ def test_mood_iteration_limit_reports_error():
         assert s.step_status() == L.ERR_MOOD_ITERS
         for k, v in before.items():
             assert np.array_equal(v, s.state()[k]), k
+
+
+def test_column3d_full_size_from_midrun_state():
+    """5,989,500 tetrahedra (the 3D column configuration): the GPU takes 3 steps, the oracle is
+    given that state, and both take one more step; masks identical, state within 1e-11."""
+    pb = W.column3d()
+    g = L.simulation(pb)
+    g.run(3)
+    o = O.Oracle(pb)
+    st = g.state()
+    o.set_state(x=st["x"], vp=st["vp"], v=st["v"], e=st["e"], F=st["F"], dt=float(g.get(L.FIELD_DT)[0]))
+    p = Pair.__new__(Pair)
+    p.pb, p.g, p.o = pb, g, o
+    p.run_compare(1)
+
+
+def test_tiny_meshes():
+    """One triangle, two triangles and one tetrahedron (empty or one-cell stencils, every node
+    on the boundary): same results as the oracle."""
+    for x, c2n, d in ((np.array([[0.0, 1.0, 0.0], [0.0, 0.0, 1.0]]), np.array([[0], [1], [2]]), 2),
+                      (np.array([[0.0, 1.0, 1.0, 0.0], [0.0, 0.0, 1.0, 1.0]]), np.array([[0, 0], [1, 2], [2, 3]]), 2),
+                      (np.array([[0.0, 1, 0, 0], [0.0, 0, 1, 0], [0.0, 0, 0, 1]]), np.array([[0], [1], [2], [3]]), 3)):
+        m = W.Mesh(d, x, c2n.astype(np.int32), np.zeros((d, 0), np.int32), np.zeros(0, np.int32))
+        nc = c2n.shape[1]
+        v = np.arange(1, d * nc + 1, dtype=float).reshape(d, nc) * 0.01
+        pb = W.Problem("tiny", m, 1.0, 2.0, np.ones(nc), v, 0.4, 5)
+        Pair(pb).run_compare(5)
+
+
+def test_clamped_everywhere_stays_put():
+    pb = W.plain2d(n=10)
+    pb.mesh.btag[:] = W.CLAMPED
+    p = Pair(pb)
+    x0 = p.g.get(L.FIELD_X)
+    p.run_compare(5)
+    assert np.array_equal(p.g.get(L.FIELD_X)[:, np.unique(pb.mesh.bface)], x0[:, np.unique(pb.mesh.bface)])

@@ -105,9 +105,23 @@ def _boundary_faces(cells: np.ndarray) -> np.ndarray:
     """Faces (sorted node tuples) that belong to exactly one simplex."""
     nv = cells.shape[1]
     faces = np.concatenate([np.delete(cells, k, axis=1) for k in range(nv)], axis=0)
-    faces = np.sort(faces, axis=1)
-    uniq, cnt = np.unique(faces, axis=0, return_counts=True)
-    return uniq[cnt == 1]
+    faces = np.sort(faces, axis=1).astype(np.int64)
+    n = int(cells.max()) + 1
+    key = faces[:, 0]
+    for a in range(1, faces.shape[1]):
+        key = key * n + faces[:, a]   # n^3 < 2^63 for n < 2^21 nodes
+    if n ** faces.shape[1] >= 2 ** 63:
+        uniq, cnt = np.unique(faces, axis=0, return_counts=True)
+        return uniq[cnt == 1]
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    first = np.ones(ks.size, dtype=bool)
+    first[1:] = ks[1:] != ks[:-1]
+    last = np.ones(ks.size, dtype=bool)
+    last[:-1] = ks[:-1] != ks[1:]
+    single = order[first & last]
+    out = faces[single]
+    return out[np.lexsort(out.T[::-1])]
 
 
 def _tag_faces(x_rows: np.ndarray, faces: np.ndarray, lo, hi, bc: dict) -> tuple[np.ndarray, np.ndarray]:
