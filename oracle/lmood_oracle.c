@@ -37,11 +37,13 @@
  *      v*_cp = v_h(x_p) + dt/2 (1/m_c) sum_q T(F_h(x_q)) (ln)_cq,
  *      F*_cp = F_h(x_p) + dt/2 L^_c F_c with L^_c the reconstructed velocity gradient,
  *      T*_cp = T(F*_cp). First-order (P0) cells use v*_cp = v_c^n, T*_cp = T(F_c^n).
- *  R9  reconstruction: unweighted least squares about cell centroids over the stencil V_c =
- *      all cells sharing a node with c (the "Voronoi neighbours" of Sect. "Algorithm"; the
- *      same set bounds the RDMP), for v and F only; a near-singular normal matrix gives
- *      zero slopes. Face neighbours alone give an observed order near 1.3 on irregular
- *      meshes, below the table of Sect. "2D swinging plate"; this stencil gives about 2.
+ *  R9  reconstruction: least squares about cell centroids over the stencil V_c = all cells
+ *      sharing a node with c (the "Voronoi neighbours" of Sect. "Algorithm"; the same set
+ *      bounds the RDMP), each neighbour weighted by the number of nodes it shares with c
+ *      (i.e. unweighted over the (node, neighbour) pairs), for v and F only; a near-singular
+ *      normal matrix gives zero slopes. Face neighbours alone give an observed order near 1.3
+ *      on irregular meshes, below the table of Sect. "2D swinging plate"; this stencil gives
+ *      about 2 with or without the weights (the paper gives none).
  *  R10 v_p^n is stored per node; v_p^{n+1} = 2 v*_p - v_p^n; v_p^0 is the first-order
  *      nodal solution at t^0.
  *  R11 MOOD: two-level cascade P1 -> P0. Troubled cells become P0; the step is recomputed
@@ -532,8 +534,9 @@ static void phase_geometry(const OrcState *S, const double *x, Work *w) {
     }
 }
 
-/* 2. piecewise-linear reconstruction of v and F by unweighted least squares (reading R9):
- *    G = sum_k dx_k dx_k^t, slope = G^{-1} sum_k dx_k (q_k - q_c), dx_k = x_k - x_c */
+/* 2. piecewise-linear reconstruction of v and F by least squares (reading R9):
+ *    G = sum_k w_k dx_k dx_k^t, slope = G^{-1} sum_k w_k dx_k (q_k - q_c), dx_k = x_k - x_c,
+ *    w_k = number of nodes neighbour k shares with c */
 static void phase_slopes(const OrcState *S, const int *order, Work *w) {
     const OrcMesh *M = S->M;
     int d = M->d, nq = d + d * d;
@@ -547,14 +550,19 @@ static void phase_slopes(const OrcState *S, const int *order, Work *w) {
         memset(r, 0, sizeof(r));
         for (long j = M->st_off[c]; j < M->st_off[c + 1]; ++j) {
             long o = M->st_idx[j];
+            /* weight: number of nodes o shares with c (sum over the (node, neighbour) pairs) */
+            double wt = 0.0;
+            for (int k = 0; k < M->nv; ++k)
+                for (int kk = 0; kk < M->nv; ++kk)
+                    if (M->c2n[c * M->nv + k] == M->c2n[o * M->nv + kk]) wt += 1.0;
             double dx[3], dq[12];
             for (int a = 0; a < d; ++a) dx[a] = w->xc[o * d + a] - w->xc[c * d + a];
             for (int i = 0; i < d; ++i) dq[i] = S->v[o * d + i] - S->v[c * d + i];
             for (int i = 0; i < d * d; ++i) dq[d + i] = S->F[o * d * d + i] - S->F[c * d * d + i];
             for (int a = 0; a < d; ++a)
-                for (int b = 0; b < d; ++b) G[a * d + b] += dx[a] * dx[b];
+                for (int b = 0; b < d; ++b) G[a * d + b] += wt * dx[a] * dx[b];
             for (int q = 0; q < nq; ++q)
-                for (int a = 0; a < d; ++a) r[q][a] += dx[a] * dq[q];
+                for (int a = 0; a < d; ++a) r[q][a] += wt * dx[a] * dq[q];
         }
         double tr = 0.0;
         for (int a = 0; a < d; ++a) tr += G[a * d + a];
