@@ -124,8 +124,7 @@ lmood_status lmood_params_default(int dim, lmood_params *p);
  *                  NULL for a single instance. Each instance keeps its own dt.
  *   n_inst         number of instances (1 when cell_inst is NULL)
  *   stream         cudaStream_t on which every device operation of this mesh is ordered
- * Builds the node-to-corner and reconstruction-stencil adjacency and the per-node boundary
- * conditions. Errors: LMOOD_ERR_ARG, LMOOD_ERR_MESH (index out of range, |w_c| <= 0),
+ * Builds the node-to-corner adjacency and the per-node boundary conditions. Errors: LMOOD_ERR_ARG, LMOOD_ERR_MESH (index out of range, |w_c| <= 0),
  * LMOOD_ERR_OOM, LMOOD_ERR_CUDA.
  */
 lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double *x, int64_t n_cells,
@@ -178,7 +177,8 @@ lmood_status lmood_set(lmood_state s, int field, const void *src, int is_device)
 /* Sums over cells of m_c, m_c v_c and m_c e_c (out: mass, mom[dim], energy; 5 doubles). */
 lmood_status lmood_totals(lmood_state s, double *out5);
 
-/* Counts of the mesh: out[0] n_nodes, [1] n_cells, [2] dim, [3] stencil entries,
+/* Counts of the mesh: out[0] n_nodes, [1] n_cells, [2] dim, [3] (node, neighbour) pairs of the
+ * least-squares sums, i.e. sum over nodes of deg (deg - 1),
  * [4] largest number of corners around a node, [5] instances. */
 lmood_status lmood_mesh_info(lmood_mesh m, int64_t *out6);
 
@@ -187,7 +187,7 @@ lmood_status lmood_mesh_info(lmood_mesh m, int64_t *out6);
  * lmood_timing_read fills ms[LMOOD_NK] (summed device time per class) and launches[LMOOD_NK]
  * (kernel launches per class since the last reset; counted whether or not timing is on). */
 enum { LMOOD_K_PREDICT = 0, LMOOD_K_NODES = 1, LMOOD_K_UPDATE = 2, LMOOD_K_MOOD = 3, LMOOD_K_FINALIZE = 4,
-       LMOOD_NK = 5 };
+       LMOOD_K_MOMENTS = 5, LMOOD_NK = 6 };
 lmood_status lmood_timing(lmood_state s, int enable);
 lmood_status lmood_timing_read(lmood_state s, double *ms, int64_t *launches);
 

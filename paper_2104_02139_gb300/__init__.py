@@ -45,8 +45,8 @@ _lib = None
 EXPORTS = ("lmood_params_default", "lmood_mesh_create", "lmood_mesh_destroy", "lmood_mesh_info",
            "lmood_state_init", "lmood_state_destroy", "lmood_step", "lmood_run", "lmood_get", "lmood_set",
            "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_totals_noalloc", "lmood_last_error")
-K_PREDICT, K_NODES, K_UPDATE, K_MOOD, K_FINALIZE, NK = range(6)
-K_NAMES = ("predict", "nodes", "update", "mood", "finalize")
+K_PREDICT, K_NODES, K_UPDATE, K_MOOD, K_FINALIZE, K_MOMENTS, NK = range(7)
+K_NAMES = ("predict", "nodes", "update", "mood", "finalize", "moments")
 
 
 def lib():

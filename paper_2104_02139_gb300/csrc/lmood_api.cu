@@ -1,5 +1,5 @@
 // lmood_api.cu -- C ABI of the library (declared in include/lmood.h): mesh set-up (node ->
-// corner and stencil adjacency, boundary-condition resolution), state buffers, and the host
+// corner adjacency, boundary-condition resolution), state buffers, and the host
 // side of the step (kernel sequence and the MOOD loop over compacted lists).
 #include <algorithm>
 #include <array>
@@ -166,38 +166,9 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
         for (int64_t c = 0; c < N; ++c)
             for (int k = 0; k < nv; ++k) n2c[pos[c2n[k * N + c]]++] = (int)(k * N + c);
     }
-    // reconstruction stencil: every other cell sharing a node, ascending id
-    std::vector<int> scount(N + 1, 0);
-    auto gather = [&](int64_t c, std::vector<int> &buf) {
-        buf.clear();
-        for (int k = 0; k < nv; ++k) {
-            const int p = c2n[k * N + c];
-            for (int j = off[p]; j < off[p + 1]; ++j) {
-                const int o = (int)(n2c[j] % N);
-                if (o != c) buf.push_back(o);
-            }
-        }
-        std::sort(buf.begin(), buf.end());
-        buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
-    };
-    parallel_for(N, [&](int64_t b, int64_t e) {
-        std::vector<int> buf;
-        for (int64_t c = b; c < e; ++c) {
-            gather(c, buf);
-            scount[c + 1] = (int)buf.size();
-        }
-    });
-    for (int64_t c = 0; c < N; ++c) scount[c + 1] += scount[c];
-    const int64_t nnz = scount[N];
-    if (nnz >= (int64_t)INT32_MAX) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: stencil too large");
-    std::vector<int> sidx_(nnz);
-    parallel_for(N, [&](int64_t b, int64_t e) {
-        std::vector<int> buf;
-        for (int64_t c = b; c < e; ++c) {
-            gather(c, buf);
-            std::copy(buf.begin(), buf.end(), sidx_.begin() + scount[c]);
-        }
-    });
+    // (node, neighbour) pairs of the least-squares sums: sum_p deg(p) (deg(p) - 1)
+    int64_t nnz = 0;
+    for (int64_t p = 0; p < Np; ++p) nnz += (int64_t)(off[p + 1] - off[p]) * (off[p + 1] - off[p] - 1);
     // boundary conditions (Appendix B; strongest first: clamped, slip, free)
     std::vector<unsigned char> ndof(Np, (unsigned char)dim);
     std::vector<double> bct(6 * Np, 0.0);
@@ -286,15 +257,13 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
     g.Np = (int)Np;
     g.n_inst = n_inst;
     lmood_status s;
-    int *d_c2n, *d_off, *d_n2c, *d_soff, *d_sidx, *d_ci = nullptr, *d_ni = nullptr;
+    int *d_c2n, *d_off, *d_n2c, *d_ci = nullptr, *d_ni = nullptr;
     unsigned char *d_nd;
     double *d_bt;
     std::vector<int> c2n_i(c2n, c2n + N * nv);
     if ((s = upload(m->mem, &d_c2n, c2n_i.data(), c2n_i.size(), st)) ||
         (s = upload(m->mem, &d_off, off.data(), off.size(), st)) ||
         (s = upload(m->mem, &d_n2c, n2c.data(), n2c.size(), st)) ||
-        (s = upload(m->mem, &d_soff, scount.data(), scount.size(), st)) ||
-        (s = upload(m->mem, &d_sidx, sidx_.data(), sidx_.size(), st)) ||
         (s = upload(m->mem, &d_nd, ndof.data(), ndof.size(), st)) ||
         (s = upload(m->mem, &d_bt, bct.data(), bct.size(), st)) ||
         (s = upload(m->mem, &m->x0, x, (size_t)(dim * Np), st))) {
@@ -314,8 +283,6 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
     g.c2n = d_c2n;
     g.n2c_off = d_off;
     g.n2c = d_n2c;
-    g.st_off = d_soff;
-    g.st_idx = d_sidx;
     g.bc_ndof = d_nd;
     g.bc_t = d_bt;
     g.cell_inst = d_ci;
@@ -369,7 +336,7 @@ struct lmood_state_s {
     bool graphs_built = false;
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    cudaEvent_t gev[2][6] = {};
+    cudaEvent_t gev[2][7] = {};
     cudaStream_t cap_st = nullptr;   // private streams for capturing (the mesh's stream may be the
     cudaStream_t body_st = nullptr;  // legacy default stream, which cannot be captured)
     int *h_cnt = nullptr;      // pinned mirror of the device counters
@@ -383,8 +350,8 @@ struct lmood_state_s {
     bool timing = false;
     std::vector<cudaEvent_t> ev;            // pool of 2 * kMaxPending events
     std::vector<int> pend_cls;              // class of each pending pair
-    double kms[LMOOD_NK] = {0, 0, 0, 0, 0};
-    int64_t klaunch[LMOOD_NK] = {0, 0, 0, 0, 0};
+    double kms[LMOOD_NK] = {};
+    int64_t klaunch[LMOOD_NK] = {};
     DevAllocs mem;
 };
 
@@ -524,6 +491,7 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
     A((void **)&s->im, N * nd);
     A((void **)&f.z, N * nd);
     A((void **)&f.z1, N * nd);
+    A((void **)&f.mom, (size_t)M->ops->nmom * Np * nd);
     A((void **)&f.rlo, Np * nd);
     A((void **)&f.rhi, Np * nd);
     A((void **)&s->mu, N * nd);
@@ -639,6 +607,8 @@ static lmood_status build_graph(lmood_state s, int par) {
     cudaMemsetAsync(f.cnt, 0, CNT_N * sizeof(int), st);
     op.ctl_reset(s->ctl, st);
     cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+    op.moments(g, f, st);
+    cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
     op.predict(g, f, s->kp, nullptr, nullptr, N, st);
     cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
     op.nodes(g, f, nullptr, nullptr, Np, 0, st);
@@ -747,15 +717,20 @@ static lmood_status step_graph(lmood_state s, lmood_step_info *info) {
     if ((r = sync_check(s, "lmood_step (graph)"))) return r;
     const Report rep = *s->h_report;
     if (s->timing) {
-        float ms[5];
-        for (int i = 0; i < 5; ++i)
-            if (cudaEventElapsedTime(&ms[i], s->gev[par][i], s->gev[par][i + 1]) != cudaSuccess) {
-                ms[i] = 0.f;
+        // event order: 0 moments 6 predict 1 nodes 2 update 3 MOOD loop 4 finalize 5
+        const int from[6] = {0, 6, 1, 2, 3, 4}, to[6] = {6, 1, 2, 3, 4, 5};
+        const int cls[6] = {LMOOD_K_MOMENTS, LMOOD_K_PREDICT, LMOOD_K_NODES, LMOOD_K_UPDATE, LMOOD_K_MOOD,
+                            LMOOD_K_FINALIZE};
+        for (int i = 0; i < 6; ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, s->gev[par][from[i]], s->gev[par][to[i]]) != cudaSuccess) {
+                ms = 0.f;
                 cudaGetLastError();
             }
-        const int cls[5] = {LMOOD_K_PREDICT, LMOOD_K_NODES, LMOOD_K_UPDATE, LMOOD_K_MOOD, LMOOD_K_FINALIZE};
-        for (int i = 0; i < 5; ++i) s->kms[cls[i]] += ms[i];
+            s->kms[cls[i]] += ms;
+        }
     }
+    s->klaunch[LMOOD_K_MOMENTS] += 1;
     s->klaunch[LMOOD_K_PREDICT] += 1;
     s->klaunch[LMOOD_K_NODES] += 1;
     s->klaunch[LMOOD_K_UPDATE] += 1;
@@ -773,6 +748,7 @@ static lmood_status step_host(lmood_state s, lmood_step_info *info) {
     const int N = (int)M->nc, Np = (int)M->np;
     LM_CUDA(cudaMemsetAsync(f.cnt, 0, CNT_N * sizeof(int), st));
     op.ctl_reset(s->ctl, st);
+    timed(s, LMOOD_K_MOMENTS, 1, [&] { op.moments(g, f, st); });
     timed(s, LMOOD_K_PREDICT, 1, [&] { op.predict(g, f, s->kp, nullptr, nullptr, N, st); });
     timed(s, LMOOD_K_NODES, 1, [&] { op.nodes(g, f, nullptr, nullptr, Np, 0, st); });
     timed(s, LMOOD_K_UPDATE, 1, [&] { op.update(g, f, s->kp, nullptr, nullptr, N, s->tl[0], f.cnt + CNT_T0, st); });

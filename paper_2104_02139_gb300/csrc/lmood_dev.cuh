@@ -8,8 +8,8 @@
 //           candidate state; m, 1/m, mu [N]; order, pad flag (u8) [N]; dt candidate [N]
 //   corner packets (corner id = k*N + c, k = local vertex):
 //           M_cp symmetric [D(D+1)/2][D+1][N], rhs_cp [D][D+1][N]
-//   adjacency (int32): c2n [D+1][N]; node -> corner CSR (ascending cell id);
-//           reconstruction stencil CSR (all cells sharing a node, ascending id)
+//   node moments of the least-squares sums [NMOM][Np] (see k_moments)
+//   adjacency (int32): c2n [D+1][N]; node -> corner CSR (ascending cell id)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -28,7 +28,6 @@ struct Geo {
     int N, Np, n_inst, pad_;
     const int *c2n;
     const int *n2c_off, *n2c;
-    const int *st_off, *st_idx;
     const unsigned char *bc_ndof;  // free directions per node (D = free, 0 = clamped)
     const double *bc_t;            // tangent vectors [2][3][Np]
     const int *cell_inst, *node_inst;  // NULL for one instance
@@ -41,6 +40,7 @@ struct Fld {
     double *xc, *xc1, *rho, *rho1, *tau1;
     double *z, *z1;              // acoustic impedance rho a of the current / candidate state
     double *rlo, *rhi;           // [Np] range of rho^n over the cells around each node
+    double *mom;                 // [NMOM][Np] least-squares moments of the cells around each node
     const double *im;            // 1 / m_c
     double *pkM, *pkR;
     unsigned char *order, *pflag;
@@ -64,7 +64,10 @@ struct Report {
 enum { CNT_T0 = 0, CNT_T1 = 1, CNT_NODES = 2, CNT_CELLS = 3, CNT_P0 = 4, CNT_PARA = 5, CNT_EPS = 6, CNT_N = 8 };
 
 template <int D> struct Dim {
-    static constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2;
+    static constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + D * D;
+    // node moments: count, S1 [D], S2 [NS], U [NQ], T [NQ][D]
+    static constexpr int M_N = 0, M_S1 = 1, M_S2 = 1 + D, M_U = 1 + D + NS, M_T = 1 + D + NS + NQ;
+    static constexpr int NMOM = 1 + D + NS + NQ + NQ * D;
 };
 
 // index of (a,b) in symmetric storage: 2D (xx,xy,yy), 3D (xx,xy,xz,yy,yz,zz)

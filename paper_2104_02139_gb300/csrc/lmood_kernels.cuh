@@ -23,12 +23,78 @@ constexpr int kListBlocks = 152 * 8;
 // ---------------------------------------------------------------------------------------
 // k_predict: corner packets of a cell (Sect. "Space-Time discretization --- ADER
 // methodology", Eqs. Mcp^n, nodal_solver^n, subforce^n).
-//   P1: v and F reconstructed by least squares over the stencil, then the predictor
+//   P1: v and F reconstructed by least squares (sums from the node moments), then the predictor
 //       v*_cp = v_h(x_p) + dt/2 (1/m_c) sum_q T(F_h(x_q)) ln_q,  F*_cp = F_h(x_p) + dt/2 L^ F_c
 //   P0: v*_cp = v_c, F*_cp = F_c.
 //   M_cp = z_c sum_{f containing p} |ln_f| n_f (x) n_f, rhs_cp = M_cp v*_cp - T(F*_cp) ln_p.
 // With a list, only the listed cells (troubled ones, already marked P0) are recomputed.
 // ---------------------------------------------------------------------------------------
+// ---------------------------------------------------------------------------------------
+// k_moments: per node p, moments of the cells c' around it (positions relative to x_p):
+//   n_p, S1 = sum dx, S2 = sum dx dx^t, U = sum q, T = sum dx (x) q,  dx = x_c' - x_p,
+// q = (v, F). A cell's least-squares sums over the (node, neighbour) pairs follow from the
+// moments of its D+1 nodes (reading of Sect. "Algorithm": stencil = cells sharing a node,
+// each neighbour weighted by the number of nodes it shares with the cell).
+// ---------------------------------------------------------------------------------------
+template <int D> __global__ void __launch_bounds__(kNodeBlock) k_moments(Geo g, Fld f) {
+    using Q = Dim<D>;
+    constexpr int NS = Q::NS, NQ = Q::NQ, DD = D * D;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.Np) return;
+    const int N = g.N, Np = g.Np;
+    double xp[D], S1[D], S2[NS], U[NQ], T[NQ][D], n = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        xp[a] = f.x[a * Np + p];
+        S1[a] = 0.0;
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) S2[s] = 0.0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        U[q] = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) T[q][a] = 0.0;
+    }
+    const int j1 = __ldg(g.n2c_off + p + 1);
+    for (int j = __ldg(g.n2c_off + p); j < j1; ++j) {
+        int c = __ldg(g.n2c + j);  // corner id k N + c -> cell c (k <= D)
+#pragma unroll
+        for (int k = 0; k < D; ++k) c -= c >= N ? N : 0;
+        double dx[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            dx[a] = f.xc[a * N + c] - xp[a];
+            S1[a] += dx[a];
+        }
+        n += 1.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = a; b < D; ++b) S2[sidx<D>(a, b)] = fma(dx[a], dx[b], S2[sidx<D>(a, b)]);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const double qv = q < D ? f.v[q * N + c] : f.F[(q - D) * N + c];
+            U[q] += qv;
+#pragma unroll
+            for (int a = 0; a < D; ++a) T[q][a] = fma(dx[a], qv, T[q][a]);
+        }
+    }
+    (void)DD;
+    double *m = f.mom + p;
+    m[Q::M_N * Np] = n;
+#pragma unroll
+    for (int a = 0; a < D; ++a) m[(Q::M_S1 + a) * Np] = S1[a];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) m[(Q::M_S2 + s) * Np] = S2[s];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        m[(Q::M_U + q) * Np] = U[q];
+#pragma unroll
+        for (int a = 0; a < D; ++a) m[(Q::M_T + q * D + a) * Np] = T[q][a];
+    }
+}
+
 template <int D>
 __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const Prm &prm, int c, bool listed) {
     constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + DD;
@@ -40,12 +106,13 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
         ord = prm.base_order;
         f.order[c] = (unsigned char)ord;
     }
+    int nod[NV];
     double xs[NV][D];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        const int p = __ldg(g.c2n + k * N + c);
+        nod[k] = __ldg(g.c2n + k * N + c);
 #pragma unroll
-        for (int a = 0; a < D; ++a) xs[k][a] = f.x[a * Np + p];
+        for (int a = 0; a < D; ++a) xs[k][a] = f.x[a * Np + nod[k]];
     }
     double V, Nf[NV][D];
     simplex_faces<D>(xs, V, Nf);
@@ -98,52 +165,47 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
         }
     };
     if (ord == 2) {
-        // least-squares slopes about centroids over the stencil (reading of Sect. "Algorithm"):
-        // G = sum dx dx^t, r = sum dx (q_o - q_c) = sum dx q_o - (sum dx) q_c
+        // least-squares sums over the (node, neighbour) pairs from the node moments:
+        // with d = x_p - x_c, dx' = (x_c' - x_p) + d, so
+        //   G += S2 + S1 d^t + d S1^t + n d d^t,   r_q += T_q + d U_q - (S1 + n d) q_c
+        // (the cell itself is one of the node's cells and contributes zero)
+        using Q = Dim<D>;
         double xcc[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) xcc[a] = f.xc[a * N + c];
-        double G[NS], r[NQ][D], sdx[D];
+        double G[NS], r[NQ][D];
 #pragma unroll
         for (int s = 0; s < NS; ++s) G[s] = 0.0;
-#pragma unroll
-        for (int a = 0; a < D; ++a) sdx[a] = 0.0;
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
 #pragma unroll
             for (int a = 0; a < D; ++a) r[q][a] = 0.0;
-        const int j1 = __ldg(g.st_off + c + 1);
-        for (int j = __ldg(g.st_off + c); j < j1; ++j) {
-            const int o = __ldg(g.st_idx + j);
-            double dx[D];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const double *m = f.mom + nod[k];
+            double d[D], S1[D], w[D];
+            const double nn = m[Q::M_N * Np];
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                dx[a] = f.xc[a * N + o] - xcc[a];
-                sdx[a] += dx[a];
+                d[a] = xs[k][a] - xcc[a];
+                S1[a] = m[(Q::M_S1 + a) * Np];
+                w[a] = fma(nn, d[a], S1[a]);
             }
 #pragma unroll
             for (int a = 0; a < D; ++a)
 #pragma unroll
-                for (int b = a; b < D; ++b) G[sidx<D>(a, b)] = fma(dx[a], dx[b], G[sidx<D>(a, b)]);
+                for (int b = a; b < D; ++b) {
+                    const int sb = sidx<D>(a, b);
+                    G[sb] += m[(Q::M_S2 + sb) * Np] + fma(S1[a], d[b], fma(d[a], w[b], 0.0));
+                }
 #pragma unroll
-            for (int q = 0; q < D; ++q) {
-                const double qo = f.v[q * N + o];
+            for (int q = 0; q < NQ; ++q) {
+                const double uq = m[(Q::M_U + q) * Np];
+                const double qc = q < D ? vc[q] : Fc[q - D];
 #pragma unroll
-                for (int a = 0; a < D; ++a) r[q][a] = fma(dx[a], qo, r[q][a]);
+                for (int a = 0; a < D; ++a)
+                    r[q][a] += fma(d[a], uq, fma(-w[a], qc, m[(Q::M_T + q * D + a) * Np]));
             }
-#pragma unroll
-            for (int q = 0; q < DD; ++q) {
-                const double qo = f.F[q * N + o];
-#pragma unroll
-                for (int a = 0; a < D; ++a) r[D + q][a] = fma(dx[a], qo, r[D + q][a]);
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-#pragma unroll
-            for (int q = 0; q < D; ++q) r[q][a] = fma(-sdx[a], vc[q], r[q][a]);
-#pragma unroll
-            for (int q = 0; q < DD; ++q) r[D + q][a] = fma(-sdx[a], Fc[q], r[D + q][a]);
         }
         double Gf[DD], Gi[DD], gs[NQ][D];
 #pragma unroll
@@ -245,7 +307,7 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
 // LISTED = false: one thread per cell of the whole mesh; true: a grid-stride loop over a
 // device-counted list (separate instances, so each gets its own register allocation)
 template <int D, bool LISTED>
-__global__ void __launch_bounds__(kCellBlock) k_predict(Geo g, Fld f, Prm prm, const int *__restrict__ list,
+__global__ void __launch_bounds__(kCellBlock, D == 2 ? 4 : 1) k_predict(Geo g, Fld f, Prm prm, const int *__restrict__ list,
                                                         const int *__restrict__ cnt, int n) {
     if constexpr (!LISTED) {
         const int c = blockIdx.x * blockDim.x + threadIdx.x;

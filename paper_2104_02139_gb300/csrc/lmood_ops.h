@@ -7,6 +7,8 @@ namespace lmood {
 
 struct Ops {
     int dim;
+    int nmom;  // node moments per node
+    void (*moments)(const Geo &, const Fld &, cudaStream_t);
     void (*predict)(const Geo &, const Fld &, const Prm &, const int *list, const int *cnt, int n, cudaStream_t);
     void (*nodes)(const Geo &, const Fld &, const int *list, const int *cnt, int n, int init_mode, cudaStream_t);
     void (*update)(const Geo &, const Fld &, const Prm &, const int *list, const int *cnt, int n, int *tlist,

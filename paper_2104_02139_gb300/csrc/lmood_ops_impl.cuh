@@ -15,6 +15,9 @@ inline int grid_for(const int *list, int n, int b) {
     return list && g > kListBlocks ? kListBlocks : g;
 }
 
+template <int D> void moments(const Geo &g, const Fld &f, cudaStream_t s) {
+    k_moments<D><<<blocks(g.Np, kNodeBlock), kNodeBlock, 0, s>>>(g, f);
+}
 template <int D>
 void predict(const Geo &g, const Fld &f, const Prm &p, const int *list, const int *cnt, int n, cudaStream_t s) {
     if (n <= 0) return;
@@ -72,7 +75,7 @@ template <int D> void totals(const Geo &g, const Fld &f, double *out, cudaStream
 }  // namespace
 
 #define LMOOD_OPS_TABLE(D)                                                                                  \
-    static const Ops table = {D,           predict<D>, nodes<D>,  update<D>,     mark_nodes<D>, mark_cells, \
+    static const Ops table = {D, Dim<D>::NMOM, moments<D>, predict<D>, nodes<D>,  update<D>,     mark_nodes<D>, mark_cells, \
                               round_begin, ctl_reset,  loop_cond, report,        dt_init,       finalize,   \
                               init_cells<D>, refresh<D>, totals<D>};                                      \
     return table;
