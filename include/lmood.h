@@ -65,7 +65,8 @@ typedef struct {
     double delta0;          /* 1e-4: absolute RDMP relaxation (Eq. RDMP)                   */
     double delta1;          /* 1e-3: relative RDMP relaxation                              */
     double dt_fixed;        /* > 0: use this dt for every step instead of Eq. CFL           */
-    int32_t max_mood_iters; /* MOOD iterations allowed per step (default 128)               */
+    int32_t max_mood_iters; /* MOOD rounds allowed per step (default 100000; a first step from
+                               F = I can cascade over a whole mesh)               */
     int32_t order;          /* 2: second order with the P1 -> P0 cascade; 1: first order    */
     int32_t mood;           /* 1: a-posteriori detection on (default); 0: unlimited         */
     int32_t graph;          /* 1: each step is one CUDA graph with the MOOD loop as a device-side

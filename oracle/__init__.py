@@ -84,7 +84,7 @@ def lib():
 
 def default_params(cfl=0.4, **kw) -> Params:
     p = Params(cfl=cfl, Cv=0.2, Ci=0.1, delta0=1e-4, delta1=1e-3, dt_fixed=0.0,
-               max_mood_iters=128, order=2, mood=1, vol_coeff=0)
+               max_mood_iters=100000, order=2, mood=1, vol_coeff=0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p

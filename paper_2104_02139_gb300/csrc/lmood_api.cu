@@ -109,7 +109,7 @@ extern "C" lmood_status lmood_params_default(int dim, lmood_params *p) {
     p->delta0 = 1e-4;
     p->delta1 = 1e-3;
     p->dt_fixed = 0.0;
-    p->max_mood_iters = 128;
+    p->max_mood_iters = 100000;
     p->order = 2;
     p->mood = 1;
     p->graph = 1;

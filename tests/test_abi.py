@@ -25,7 +25,7 @@ def test_header_and_exports_agree():
 def test_params_default_without_gpu():
     p = L.params_default(3)
     assert p.cfl == 0.25 and p.Cv == 0.2 and p.Ci == 0.1 and p.delta0 == 1e-4 and p.delta1 == 1e-3
-    assert p.order == 2 and p.mood == 1 and p.max_mood_iters == 128
+    assert p.order == 2 and p.mood == 1 and p.max_mood_iters == 100000
     try:
         L.params_default(4)
     except L.LmoodError as e:
