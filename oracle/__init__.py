@@ -35,13 +35,13 @@ class Params(C.Structure):
     _fields_ = [("cfl", C.c_double), ("Cv", C.c_double), ("Ci", C.c_double),
                 ("delta0", C.c_double), ("delta1", C.c_double), ("dt_fixed", C.c_double),
                 ("max_mood_iters", C.c_int), ("order", C.c_int), ("mood", C.c_int),
-                ("vol_coeff", C.c_int)]
+                ("vol_coeff", C.c_int), ("cascade", C.c_int)]
 
 
 class Info(C.Structure):
     _fields_ = [("t", C.c_double), ("dt_used", C.c_double), ("dt_next", C.c_double),
                 ("step", C.c_long), ("n_troubled", C.c_int), ("n_p0", C.c_int),
-                ("mood_iters", C.c_int), ("n_parachute", C.c_int), ("n_p0_eps", C.c_int),
+                ("mood_iters", C.c_int), ("n_parachute", C.c_int), ("n_p0_eps", C.c_int), ("n_lim", C.c_int),
                 ("mass", C.c_double),
                 ("mom", C.c_double * 3), ("energy", C.c_double)]
 
@@ -77,6 +77,7 @@ def lib():
         L.orc_sound_speed.restype = C.c_double
         L.orc_mesh_stencil.argtypes = [C.c_void_p, C.c_long, np.ctypeslib.ndpointer(np.int64), C.c_long]
         L.orc_mesh_stencil.restype = C.c_long
+        L.orc_debug_corner_values.argtypes = [C.c_void_p, C.c_long, C.c_int, dp, dp, dp]
         L.orc_mesh_bc_ndof.argtypes = [C.c_void_p, C.c_long]
         L.orc_mesh_bc_ndof.restype = C.c_int
     return _lib
@@ -84,7 +85,7 @@ def lib():
 
 def default_params(cfl=0.4, **kw) -> Params:
     p = Params(cfl=cfl, Cv=0.2, Ci=0.1, delta0=1e-4, delta1=1e-3, dt_fixed=0.0,
-               max_mood_iters=100000, order=2, mood=1, vol_coeff=0)
+               max_mood_iters=100000, order=2, mood=1, vol_coeff=0, cascade=2)
     for k, v in kw.items():
         setattr(p, k, v)
     return p
@@ -212,6 +213,13 @@ class Oracle:
         buf = np.zeros(4096, dtype=np.int64)
         n = lib().orc_mesh_stencil(self._h.mesh, c, buf, buf.size)
         return buf[:n].copy()
+
+    def corner_values(self, c: int, level: int):
+        d = self.d
+        nq = d + d * d
+        out, lo, hi = np.zeros((d + 1) * nq), np.zeros(nq), np.zeros(nq)
+        lib().orc_debug_corner_values(self._h.state, c, level, out, lo, hi)
+        return out.reshape(d + 1, nq), lo, hi
 
     def bc_ndof(self, p: int) -> int:
         return lib().orc_mesh_bc_ndof(self._h.mesh, p)

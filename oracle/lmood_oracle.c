@@ -46,7 +46,11 @@
  *      about 2 with or without the weights (the paper gives none).
  *  R10 v_p^n is stored per node; v_p^{n+1} = 2 v*_p - v_p^n; v_p^0 is the first-order
  *      nodal solution at t^0.
- *  R11 MOOD: two-level cascade P1 -> P0. Troubled cells become P0; the step is recomputed
+ *  R11 MOOD: cascade P1 -> P0 (default) or, as in Sect. "Limiting: a posteriori MOOD loop",
+ *      P1 -> P1 with Barth-Jespersen limited slopes -> P0 (order codes 2, 3, 1). The limiter
+ *      scales each field's slope by the largest factor <= 1 that keeps its values at the
+ *      cell's nodes within the field's range over the stencil and the cell (at t^n).
+ *      Troubled cells move one level down; the step is recomputed
  *      from t^n with the new order mask (neighbours keep their order but see the new node
  *      velocities); repeat until no new troubled cell. A P0 candidate that cannot be
  *      advanced further (non-finite value, tau <= 0 or det F <= 0) is a parachute failure;
@@ -76,12 +80,13 @@ typedef struct {
     int order;          /* 2: P1 with MOOD cascade to P0; 1: first order everywhere  */
     int mood;           /* 1: detection on; 0: unlimited (no detection)              */
     int vol_coeff;      /* 0: kappa = lambda + 2 mu / 3; 1: kappa = mu (printed)      */
+    int cascade;        /* 2: P1 -> P0; 3: P1 -> P1 with Barth-Jespersen slopes -> P0     */
 } OrcParams;
 
 typedef struct {
     double t, dt_used, dt_next;
     long step;
-    int n_troubled, n_p0, mood_iters, n_parachute, n_p0_eps;
+    int n_troubled, n_p0, mood_iters, n_parachute, n_p0_eps, n_lim;
     double mass, mom[3], energy;
 } OrcInfo;
 
@@ -545,7 +550,7 @@ static void phase_slopes(const OrcState *S, const int *order, Work *w) {
         double *gv = w->gv + c * d * d, *gF = w->gF + c * d * d * d;
         memset(gv, 0, sizeof(double) * d * d);
         memset(gF, 0, sizeof(double) * d * d * d);
-        if (order[c] != 2) continue;
+        if (order[c] == 1) continue;
         double G[9] = {0}, r[12][3];
         memset(r, 0, sizeof(r));
         for (long j = M->st_off[c]; j < M->st_off[c + 1]; ++j) {
@@ -573,6 +578,25 @@ static void phase_slopes(const OrcState *S, const int *order, Work *w) {
         for (int q = 0; q < nq; ++q) {
             double g[3];
             matvec_n(d, Gi, r[q], g);
+            if (order[c] == 3) {
+                /* Barth-Jespersen: largest phi <= 1 keeping q_c + phi g.(x_p - x_c) in [lo, hi] */
+                double qc = q < d ? S->v[c * d + q] : S->F[c * d * d + q - d], lo = qc, hi = qc;
+                for (long j = M->st_off[c]; j < M->st_off[c + 1]; ++j) {
+                    long o = M->st_idx[j];
+                    double qo = q < d ? S->v[o * d + q] : S->F[o * d * d + q - d];
+                    lo = fmin(lo, qo);
+                    hi = fmax(hi, qo);
+                }
+                double phi = 1.0;
+                for (int k = 0; k < M->nv; ++k) {
+                    int p = M->c2n[c * M->nv + k];
+                    double delta = 0.0;
+                    for (int a = 0; a < d; ++a) delta += g[a] * (S->x[p * d + a] - w->xc[c * d + a]);
+                    if (delta > 0.0) phi = fmin(phi, (hi - qc) / delta);
+                    if (delta < 0.0) phi = fmin(phi, (lo - qc) / delta);
+                }
+                for (int a = 0; a < d; ++a) g[a] *= phi;
+            }
             double *dst = q < d ? gv + q * d : gF + (q - d) * d;
             for (int a = 0; a < d; ++a) dst[a] = g[a];
         }
@@ -594,7 +618,7 @@ static void phase_packets(const OrcState *S, const int *order, double dt, Work *
         double rho = S->m[c] / w->V[c];
         double z = rho * orc_sound_speed(d, Fc, rho, S->mu[c], kap);
         double vstar[MAXV][MAXD], Tstar[MAXV][9];
-        if (order[c] == 2) {
+        if (order[c] != 1) {
             const double *gv = w->gv + c * dd, *gF = w->gF + c * dd * d;
             double vh[MAXV][MAXD], Fh[MAXV][9], dvdt[MAXD] = {0, 0, 0}, dFdt[9];
             for (int k = 0; k < nv; ++k) {
@@ -757,7 +781,7 @@ static void phase_update(const OrcState *S, const int *order, double dt, Work *w
         w->V1[c] = V1;
         const double *Fn = S->F + c * dd;
         double *F1 = w->F1 + c * dd;
-        if (order[c] == 2) {
+        if (order[c] != 1) {
             /* Crank-Nicolson: (I - dt/2 L^{n+1}) F^{n+1} = (I + dt/2 L^n) F^n */
             double L0[9], L1[9], A[9], Bm[9], Ai[9], R[9];
             vel_gradient(d, nv, w->ln + c * nv * d, w->V[c], vpn, L0);
@@ -858,7 +882,7 @@ int orc_step(OrcState *S, OrcInfo *info) {
 #pragma omp parallel for schedule(static) reduction(+ : fresh, n_para, n_eps)
             for (long c = 0; c < nc; ++c) {
                 int ps = pad_state(d, w.v1 + c * d, w.e1[c], w.F1 + c * dd, w.V1[c]);
-                if (order[c] == 2) {
+                if (order[c] != 1) {
                     if (ps != 0 || !rdmp_ok(S, &w, c)) { flag[c] = 1; fresh++; }
                 } else if (ps == 2) {
                     n_para++;
@@ -867,7 +891,7 @@ int orc_step(OrcState *S, OrcInfo *info) {
                 }
             }
             for (long c = 0; c < nc; ++c)
-                if (flag[c]) order[c] = 1;
+                if (flag[c]) order[c] = (order[c] == 2 && S->prm.cascade == 3) ? 3 : 1;
             free(flag);
         }
         if (fresh == 0) break;
@@ -903,8 +927,12 @@ int orc_step(OrcState *S, OrcInfo *info) {
         S->last.dt_used = dt;
         S->dt = dtn;
     }
-    int np0 = 0;
-    for (long c = 0; c < nc; ++c) np0 += order[c] == 1;
+    int np0 = 0, nlim = 0;
+    for (long c = 0; c < nc; ++c) {
+        np0 += order[c] == 1;
+        nlim += order[c] == 3;
+    }
+    S->last.n_lim = nlim;
     S->last.t = S->t;
     S->last.dt_next = S->dt;
     S->last.step = S->step;
@@ -1027,6 +1055,40 @@ int orc_set_state(OrcState *S, const double *x, const double *vp, const double *
     if (e) for (long c = 0; c < nc; ++c) S->e[c] = e[c];
     if (F) for (long c = 0; c < nc; ++c) for (int a = 0; a < dd; ++a) S->F[c * dd + a] = F[a * nc + c];
     if (dt > 0) S->dt = dt;
+    return ORC_OK;
+}
+
+/* Reconstructed values of v and F at the nodes of cell c from the current state with the
+ * given level (2 unlimited, 3 Barth-Jespersen), and each field's range over the stencil and
+ * the cell: out [nv][nq], lo [nq], hi [nq]. Used by tests. */
+int orc_debug_corner_values(const OrcState *S, long c, int level, double *out, double *lo, double *hi) {
+    const OrcMesh *M = S->M;
+    int d = M->d, nq = d + d * d, nv = M->nv;
+    Work w = work_new(M);
+    int *order = malloc(sizeof(int) * M->nc);
+    for (long i = 0; i < M->nc; ++i) order[i] = 1;
+    order[c] = level;
+    phase_geometry(S, S->x, &w);
+    phase_slopes(S, order, &w);
+    for (int q = 0; q < nq; ++q) {
+        double qc = q < d ? S->v[c * d + q] : S->F[c * d * d + q - d];
+        lo[q] = hi[q] = qc;
+        for (long j = M->st_off[c]; j < M->st_off[c + 1]; ++j) {
+            long o = M->st_idx[j];
+            double qo = q < d ? S->v[o * d + q] : S->F[o * d * d + q - d];
+            lo[q] = fmin(lo[q], qo);
+            hi[q] = fmax(hi[q], qo);
+        }
+        const double *g = q < d ? w.gv + c * d * d + q * d : w.gF + c * d * d * d + (q - d) * d;
+        for (int k = 0; k < nv; ++k) {
+            int p = M->c2n[c * nv + k];
+            double val = qc;
+            for (int a = 0; a < d; ++a) val += g[a] * (S->x[p * d + a] - w.xc[c * d + a]);
+            out[k * nq + q] = val;
+        }
+    }
+    free(order);
+    work_free(&w);
     return ORC_OK;
 }
 

@@ -320,3 +320,48 @@ def test_thread_count_independence(orc):
         env = dict(os.environ, OMP_NUM_THREADS=nt)
         outs.append(subprocess.check_output([sys.executable, "-c", code], env=env))
     assert outs[0] == outs[1]
+
+
+# ----------------------------------------------------------------------------- BJ level
+def test_barth_jespersen_bounds_and_linear_preservation(orc):
+    """Level 3 (Barth-Jespersen slopes, Sect. "Limiting: a posteriori MOOD loop"): the
+    reconstructed values at a cell's nodes stay within the field's range over the stencil and
+    the cell; on an affine field interior cells keep the unlimited (exact) reconstruction."""
+    pb = W.impact2d(n=40)
+    o = orc.Oracle(pb)
+    o.step(8)   # a state with a compression front
+    rng = np.random.default_rng(3)
+    for c in rng.choice(pb.mesh.n_cells, 200, replace=False):
+        vals, lo, hi = o.corner_values(int(c), 3)
+        span = np.maximum(hi - lo, 1e-300)
+        assert np.all(vals >= lo - 1e-12 * span) and np.all(vals <= hi + 1e-12 * span)
+    # affine velocity field, F = I: interior cells unchanged by the limiter
+    pb = W.plain2d(n=12)
+    G = np.array([[0.3, -0.2], [0.1, 0.4]])
+    xc = W.cell_points(pb.mesh)
+    pb.v = (xc @ G.T).T.copy()
+    o = orc.Oracle(pb)
+    bnd = set(pb.mesh.bface.ravel().tolist())
+    for c in range(pb.mesh.n_cells):
+        if any(int(p) in bnd for p in pb.mesh.c2n[:, c]):
+            continue
+        v2, _, _ = o.corner_values(c, 2)
+        v3, _, _ = o.corner_values(c, 3)
+        np.testing.assert_allclose(v3, v2, rtol=0, atol=1e-15)
+
+
+def test_three_level_cascade(orc):
+    """With the three-level cascade, troubled P1 cells first try the limited scheme; fewer
+    cells end at first order than with P1 -> P0, energy is still conserved."""
+    pb = W.impact2d(n=60)
+    res = {}
+    for cas in (2, 3):
+        o = orc.Oracle(pb, cascade=cas)
+        E0, _ = _totals(o, orc)
+        for _ in range(20):
+            o.step()
+        E1, _ = _totals(o, orc)
+        assert abs(E1 - E0) <= 1e-13 * E0
+        order = o.get(orc.F_ORDER)
+        res[cas] = (int((order == 1).sum()), int((order == 3).sum()))
+    assert res[2][1] == 0 and res[3][1] > 0 and res[3][0] < res[2][0]
