@@ -72,6 +72,10 @@ typedef struct {
     int32_t graph;          /* 1: each step is one CUDA graph with the MOOD loop as a device-side
                                conditional while node (default); 0: host-driven MOOD rounds.
                                Results are identical.                                        */
+    int32_t cascade;        /* 2: P1 -> P0 (default); 3: P1 -> P1 with Barth-Jespersen limited
+                               slopes -> P0, the three-scheme cascade of Sect. "Limiting: a
+                               posteriori MOOD loop" (order codes 2, 3, 1)                    */
+    int32_t reserved;
 } lmood_params;
 
 /* Per-step report. */
@@ -85,7 +89,7 @@ typedef struct {
     int32_t mood_iters;  /* MOOD iterations the step needed                    */
     int32_t n_parachute; /* P0 candidates that were not computable (then the status is an error) */
     int32_t n_p0_eps;    /* P0 cells accepted with a negative specific internal energy */
-    int32_t reserved;
+    int32_t n_lim;       /* cells advanced with Barth-Jespersen limited slopes (cascade 3) */
 } lmood_step_info;
 
 /* Field ids for lmood_get / lmood_set (layout, entity count n, components k). */
@@ -97,7 +101,8 @@ enum {
     LMOOD_FIELD_E = 4,     /* specific total energy e_c          [n_cells]                 */
     LMOOD_FIELD_F = 5,     /* deformation gradient F_c, row-major [dim*dim][n_cells]       */
     LMOOD_FIELD_TAU = 6,   /* specific volume tau_c = |w_c| / m_c [n_cells]       get only */
-    LMOOD_FIELD_ORDER = 7, /* last step's order per cell, 1 or 2, as double [n_cells] get only */
+    LMOOD_FIELD_ORDER = 7, /* last step's scheme per cell as double [n_cells] get only: 2 P1,
+                              3 P1 with limited slopes, 1 first order (P0) */
     LMOOD_FIELD_MASS = 8,  /* cell masses m_c                    [n_cells]        get only */
     LMOOD_FIELD_PKM = 9,   /* last step's corner matrices M_cp, symmetric storage
                               [dim(dim+1)/2][dim+1][n_cells] (xx,xy,yy | xx,xy,xz,yy,yz,zz) get only */

@@ -32,13 +32,14 @@ class Material(C.Structure):
 class Params(C.Structure):
     _fields_ = [("cfl", C.c_double), ("Cv", C.c_double), ("Ci", C.c_double), ("delta0", C.c_double),
                 ("delta1", C.c_double), ("dt_fixed", C.c_double), ("max_mood_iters", C.c_int32),
-                ("order", C.c_int32), ("mood", C.c_int32), ("graph", C.c_int32)]
+                ("order", C.c_int32), ("mood", C.c_int32), ("graph", C.c_int32), ("cascade", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class StepInfo(C.Structure):
     _fields_ = [("t", C.c_double), ("dt_used", C.c_double), ("dt_next", C.c_double), ("step", C.c_int64),
                 ("n_troubled", C.c_int32), ("n_p0", C.c_int32), ("mood_iters", C.c_int32),
-                ("n_parachute", C.c_int32), ("n_p0_eps", C.c_int32), ("reserved", C.c_int32)]
+                ("n_parachute", C.c_int32), ("n_p0_eps", C.c_int32), ("n_lim", C.c_int32)]
 
 
 _lib = None

@@ -113,6 +113,7 @@ extern "C" lmood_status lmood_params_default(int dim, lmood_params *p) {
     p->order = 2;
     p->mood = 1;
     p->graph = 1;
+    p->cascade = 2;
     return LMOOD_OK;
 }
 
@@ -408,6 +409,7 @@ static Prm kernel_params(const lmood_params &p, const lmood_material &m) {
     k.base_order = p.order == 1 ? 1 : 2;
     k.mood = p.mood ? 1 : 0;
     k.vol_coeff = m.vol_coeff ? 1 : 0;
+    k.cascade = p.cascade == 3 ? 3 : 2;
     return k;
 }
 
@@ -452,7 +454,8 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
     *out = nullptr;
     if (!M || !mat || !mu_cell || !v_cell || !prm) return fail(LMOOD_ERR_ARG, "lmood_state_init: NULL argument");
     if (!(mat->rho0 > 0)) return fail(LMOOD_ERR_ARG, "lmood_state_init: rho0 must be positive");
-    if (!(prm->cfl > 0) || prm->max_mood_iters < 0 || (prm->order != 1 && prm->order != 2))
+    if (!(prm->cfl > 0) || prm->max_mood_iters < 0 || (prm->order != 1 && prm->order != 2) ||
+        (prm->cascade != 2 && prm->cascade != 3))
         return fail(LMOOD_ERR_ARG, "lmood_state_init: bad parameters");
     const int D = M->dim, NV = D + 1, NS = D * (D + 1) / 2;
     const int64_t N = M->nc, Np = M->np;
@@ -582,7 +585,7 @@ static void enqueue_mood_round(lmood_state s, const Fld &f, int cur, int n_in, c
     const int nb_nodes = (int)std::min<int64_t>(Np, (int64_t)NV * n_in);
     const int nb_cells = (int)std::min<int64_t>(N, (int64_t)M->max_deg * nb_nodes);
     op.round_begin(f, s->ctl, in, out, s->prm.max_mood_iters, st);
-    op.mark_nodes(g, f, s->tl[cur], f.cnt + in, n_in, s->node_mark, s->ctl, s->nlist, st);
+    op.mark_nodes(g, f, s->kp, s->tl[cur], f.cnt + in, n_in, s->node_mark, s->ctl, s->nlist, st);
     op.mark_cells(g, f, s->nlist, nb_nodes, s->cell_mark, s->ctl, s->clist, st);
     op.predict(g, f, s->kp, s->tl[cur], f.cnt + in, n_in, st);
     op.nodes(g, f, s->nlist, f.cnt + CNT_NODES, nb_nodes, 0, st);
@@ -686,6 +689,7 @@ static lmood_status finish_step(lmood_state s, const Report &rep, lmood_step_inf
     in.n_p0 = rep.n_p0;
     in.n_parachute = rep.n_para;
     in.n_p0_eps = rep.n_eps;
+    in.n_lim = rep.n_lim;
     in.dt_used = rep.dt_used;
     in.dt_next = rep.dt_next;
     in.t = s->t;

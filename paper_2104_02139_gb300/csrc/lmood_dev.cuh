@@ -21,7 +21,7 @@ struct Prm {
     int base_order;  // order every cell starts the step with (2: P1, 1: P0)
     int mood;        // detection on/off
     int vol_coeff;   // 0: kappa = lambda + 2 mu / 3; 1: kappa = mu
-    int pad_;
+    int cascade;     // 2: P1 -> P0; 3: P1 -> P1 with Barth-Jespersen slopes -> P0
 };
 
 struct Geo {
@@ -57,11 +57,12 @@ struct Ctl {
 
 // per-step report written by the last kernel of a step and copied to the host
 struct Report {
-    int n_troubled, mood_iters, err, n_p0, n_para, n_eps, pad0, pad1;
+    int n_troubled, mood_iters, err, n_p0, n_para, n_eps, n_lim, pad1;
     double dt_used, dt_next;
 };
 
-enum { CNT_T0 = 0, CNT_T1 = 1, CNT_NODES = 2, CNT_CELLS = 3, CNT_P0 = 4, CNT_PARA = 5, CNT_EPS = 6, CNT_N = 8 };
+enum { CNT_T0 = 0, CNT_T1 = 1, CNT_NODES = 2, CNT_CELLS = 3, CNT_P0 = 4, CNT_PARA = 5, CNT_EPS = 6, CNT_LIM = 7,
+       CNT_N = 8 };
 
 template <int D> struct Dim {
     static constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + D * D;

@@ -95,12 +95,12 @@ template <int D> __global__ void __launch_bounds__(kNodeBlock) k_moments(Geo g, 
     }
 }
 
-template <int D>
-__device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const Prm &prm, int c, bool listed) {
+template <int D, bool LISTED>
+__device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const Prm &prm, int c) {
     constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + DD;
     const int N = g.N, Np = g.Np, NC = NV * N;
     int ord;
-    if (listed) {
+    if constexpr (LISTED) {
         ord = f.order[c];
     } else {
         ord = prm.base_order;
@@ -164,7 +164,7 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
             f.pkR[a * NC + k * N + c] = fma(tn, 1.0 / D, mv);
         }
     };
-    if (ord == 2) {
+    if (ord != 1) {
         // least-squares sums over the (node, neighbour) pairs from the node moments:
         // with d = x_p - x_c, dx' = (x_c' - x_p) + d, so
         //   G += S2 + S1 d^t + d S1^t + n d d^t,   r_q += T_q + d U_q - (S1 + n d) q_c
@@ -227,6 +227,43 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
                 for (int b = 0; b < D; ++b) s += Gi[a * D + b] * r[q][b];
                 gs[q][a] = ok ? s : 0.0;
             }
+        // cells reach level 3 only through a MOOD decrement, i.e. in list launches
+        if (LISTED && ord == 3) {
+            // Barth-Jespersen: scale each field's slope by the largest phi <= 1 that keeps its
+            // values at the cell's nodes within its range over the stencil and the cell
+            double lo[NQ], hi[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) lo[q] = hi[q] = q < D ? vc[q] : Fc[q - D];
+            for (int k = 0; k < NV; ++k) {
+                const int j1 = __ldg(g.n2c_off + nod[k] + 1);
+                for (int j = __ldg(g.n2c_off + nod[k]); j < j1; ++j) {
+                    int o = __ldg(g.n2c + j);
+#pragma unroll
+                    for (int kk = 0; kk < D; ++kk) o -= o >= N ? N : 0;
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        const double qo = q < D ? f.v[q * N + o] : f.F[(q - D) * N + o];
+                        lo[q] = fmin(lo[q], qo);
+                        hi[q] = fmax(hi[q], qo);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const double qc = q < D ? vc[q] : Fc[q - D];
+                double phi = 1.0;
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    double delta = 0.0;
+#pragma unroll
+                    for (int a = 0; a < D; ++a) delta += gs[q][a] * (xs[k][a] - xcc[a]);
+                    if (delta > 0.0) phi = fmin(phi, (hi[q] - qc) / delta);
+                    if (delta < 0.0) phi = fmin(phi, (lo[q] - qc) / delta);
+                }
+#pragma unroll
+                for (int a = 0; a < D; ++a) gs[q][a] *= phi;
+            }
+        }
         double dxs[NV][D];
 #pragma unroll
         for (int k = 0; k < NV; ++k)
@@ -311,11 +348,11 @@ __global__ void __launch_bounds__(kCellBlock, D == 2 ? 4 : 1) k_predict(Geo g, F
                                                         const int *__restrict__ cnt, int n) {
     if constexpr (!LISTED) {
         const int c = blockIdx.x * blockDim.x + threadIdx.x;
-        if (c < n) predict_cell<D>(g, f, prm, c, false);
+        if (c < n) predict_cell<D, false>(g, f, prm, c);
     } else {
         const int nn = *cnt;
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
-            predict_cell<D>(g, f, prm, list[i], true);
+            predict_cell<D, true>(g, f, prm, list[i]);
     }
 }
 
@@ -512,7 +549,7 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
     double Fn[DD], F1[DD];
 #pragma unroll
     for (int q = 0; q < DD; ++q) Fn[q] = f.F[q * N + c];
-    if (ord == 2) {
+    if (ord != 1) {
         double vn[NV][D], L0[DD], L1[DD], A[DD], Bm[DD], Ai[DD], R[DD];
 #pragma unroll
         for (int k = 0; k < NV; ++k)
@@ -566,7 +603,7 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
     }
     if (prm.mood) {
         const int ps = pad_state<D>(v1, e1, F1, V1);
-        if (ord == 2) {
+        if (ord != 1) {
             bool bad = ps != 0;
             if (!bad) {
                 double lo = f.rlo[nod[0]], hi = f.rhi[nod[0]];
@@ -633,12 +670,12 @@ static __global__ void k_ctl_reset(Ctl *ctl) {
 
 // troubled cells become P0; their nodes are appended (once) to the node list
 template <int D>
-__global__ void k_mark_nodes(Geo g, Fld f, const int *__restrict__ tlist, const int *__restrict__ tcnt,
+__global__ void k_mark_nodes(Geo g, Fld f, Prm prm, const int *__restrict__ tlist, const int *__restrict__ tcnt,
                              int *node_mark, const Ctl *ctl, int *nlist) {
     const int n = *tcnt, stamp = ctl->stamp;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int c = tlist[i];
-        f.order[c] = 1;
+        f.order[c] = (f.order[c] == 2 && prm.cascade == 3) ? 3 : 1;  // one level down the cascade
 #pragma unroll
         for (int k = 0; k < D + 1; ++k) {
             const int p = __ldg(g.c2n + k * g.N + c);
@@ -673,6 +710,7 @@ static __global__ void k_report(Fld f, const Ctl *ctl, Report *r) {
     r->n_p0 = f.cnt[CNT_P0];
     r->n_para = f.cnt[CNT_PARA];
     r->n_eps = f.cnt[CNT_EPS];
+    r->n_lim = f.cnt[CNT_LIM];
     r->dt_used = f.dt[0];
     r->dt_next = __longlong_as_double((long long)f.dtn[0]);
 }
@@ -709,12 +747,13 @@ static __global__ void __launch_bounds__(256) k_finalize(Geo g, Fld f, Prm prm) 
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const bool in = c < g.N;
     unsigned long long bits = ~0ull;
-    int p0 = 0, para = 0, eps = 0;
+    int p0 = 0, para = 0, eps = 0, lim = 0;
     int inst = 0;
     if (in) {
         if (!(prm.dt_fixed > 0)) bits = (unsigned long long)__double_as_longlong(f.dtc[c]);
         const int o = f.order[c];
         p0 = o == 1;
+        lim = o == 3;
         const int pf = f.pflag[c];
         para = p0 && pf == 2;
         eps = p0 && pf == 1;
@@ -724,15 +763,17 @@ static __global__ void __launch_bounds__(256) k_finalize(Geo g, Fld f, Prm prm) 
     const int c0 = blockIdx.x * blockDim.x, c1 = min(g.N, c0 + (int)blockDim.x) - 1;
     const bool uniform = !g.cell_inst || g.cell_inst[c0] == g.cell_inst[c1];
     __shared__ unsigned long long sb[8];
-    __shared__ int si[8][3];
+    __shared__ int si[8][4];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     p0 = warp_sum_i(p0);
     para = warp_sum_i(para);
     eps = warp_sum_i(eps);
+    lim = warp_sum_i(lim);
     if (lane == 0) {
         si[w][0] = p0;
         si[w][1] = para;
         si[w][2] = eps;
+        si[w][3] = lim;
     }
     if (uniform) {
         const unsigned long long m = warp_min_u64(bits);
@@ -742,17 +783,19 @@ static __global__ void __launch_bounds__(256) k_finalize(Geo g, Fld f, Prm prm) 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int a = 0, b = 0, e = 0;
+        int a = 0, b = 0, e = 0, l = 0;
         unsigned long long m = ~0ull;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
             a += si[q][0];
             b += si[q][1];
             e += si[q][2];
+            l += si[q][3];
             if (uniform) m = sb[q] < m ? sb[q] : m;
         }
         if (a) atomicAdd(f.cnt + CNT_P0, a);
         if (b) atomicAdd(f.cnt + CNT_PARA, b);
         if (e) atomicAdd(f.cnt + CNT_EPS, e);
+        if (l) atomicAdd(f.cnt + CNT_LIM, l);
         if (uniform && m != ~0ull) atomicMin(f.dtn + (g.cell_inst ? g.cell_inst[c0] : 0), m);
     }
 }

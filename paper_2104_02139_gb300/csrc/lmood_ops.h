@@ -13,7 +13,7 @@ struct Ops {
     void (*nodes)(const Geo &, const Fld &, const int *list, const int *cnt, int n, int init_mode, cudaStream_t);
     void (*update)(const Geo &, const Fld &, const Prm &, const int *list, const int *cnt, int n, int *tlist,
                    int *tcnt, cudaStream_t);
-    void (*mark_nodes)(const Geo &, const Fld &, const int *tlist, const int *tcnt, int n, int *node_mark,
+    void (*mark_nodes)(const Geo &, const Fld &, const Prm &, const int *tlist, const int *tcnt, int n, int *node_mark,
                        const Ctl *ctl, int *nlist, cudaStream_t);
     void (*mark_cells)(const Geo &, const Fld &, const int *nlist, int n, int *cell_mark, const Ctl *ctl,
                        int *clist, cudaStream_t);

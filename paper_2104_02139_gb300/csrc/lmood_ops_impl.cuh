@@ -38,9 +38,9 @@ void update(const Geo &g, const Fld &f, const Prm &p, const int *list, const int
     else k_update<D, false><<<blocks(n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n, tlist, tcnt);
 }
 template <int D>
-void mark_nodes(const Geo &g, const Fld &f, const int *tlist, const int *tcnt, int n, int *node_mark, const Ctl *ctl,
-                int *nlist, cudaStream_t s) {
-    if (n > 0) k_mark_nodes<D><<<grid_for(tlist, n, 256), 256, 0, s>>>(g, f, tlist, tcnt, node_mark, ctl, nlist);
+void mark_nodes(const Geo &g, const Fld &f, const Prm &p, const int *tlist, const int *tcnt, int n, int *node_mark,
+                const Ctl *ctl, int *nlist, cudaStream_t s) {
+    if (n > 0) k_mark_nodes<D><<<grid_for(tlist, n, 256), 256, 0, s>>>(g, f, p, tlist, tcnt, node_mark, ctl, nlist);
 }
 void mark_cells(const Geo &g, const Fld &f, const int *nlist, int n, int *cell_mark, const Ctl *ctl, int *clist,
                 cudaStream_t s) {

@@ -173,3 +173,22 @@ def test_clamped_everywhere_stays_put():
     x0 = p.g.get(L.FIELD_X)
     p.run_compare(5)
     assert np.array_equal(p.g.get(L.FIELD_X)[:, np.unique(pb.mesh.bface)], x0[:, np.unique(pb.mesh.bface)])
+
+
+def test_three_level_cascade_parity():
+    """P1 -> P1 with Barth-Jespersen slopes -> P0: identical order masks (codes 2, 3, 1) and
+    states as the oracle, in 2D and 3D; graph and host-driven modes agree bitwise."""
+    pb = W.impact2d(n=60)
+    stats = Pair(pb, cascade=3).run_compare(30)
+    assert stats["troubled"] > 0
+    pb3 = W.column3d(nxy=4, nz=24)
+    pb3.v *= 5
+    Pair(pb3, cascade=3).run_compare(15)
+    a, b = L.simulation(pb, cascade=3, graph=1), L.simulation(pb, cascade=3, graph=0)
+    lim = 0
+    for _ in range(15):
+        lim += a.step().n_lim
+        b.step()
+    assert lim > 0
+    for f in (L.FIELD_X, L.FIELD_V, L.FIELD_F, L.FIELD_ORDER):
+        assert np.array_equal(a.get(f), b.get(f)), f
