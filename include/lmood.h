@@ -215,6 +215,49 @@ lmood_status lmood_timing_read(lmood_state s, double *ms, int64_t *launches);
 lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, const double *v, const double *e,
                                   double *out5, void *stream);
 
+/*
+ * Adjoint (reverse-mode gradients) of a stretch of steps, with every step's MOOD order mask
+ * and time step frozen at their recorded values. Each step is then a smooth map of the state
+ * (x, v_p per node; v, F per cell) and of the per-cell mu; the adjoint is the exact transpose
+ * of its linearisation, written by hand kernel by kernel (no atomics, deterministic).
+ * Only the two-level cascade (P1 -> P0) is differentiated: a recorded step that used the
+ * limited level returns LMOOD_ERR_ARG. Energy e has no influence on the other fields, so it
+ * carries no adjoint.
+ *
+ * lmood_tape_record: runs n_steps ordinary lmood_step calls on s (the forward pass, with the
+ *   MOOD loop and the dt rule as configured) and records what the reverse pass needs: the dt
+ *   and the final order mask of every step, and a checkpoint of the state every
+ *   checkpoint_every steps (>= 1; 1 keeps every state). Device memory held by the tape:
+ *   about ceil(n_steps / checkpoint_every) + checkpoint_every + 1 states plus n_steps
+ *   (n_cells + 8 n_inst) bytes. last (may be NULL) gets the last step's report. If a step
+ *   fails, its status is returned, no tape is made (*out = NULL), and the state has taken the
+ *   steps before it. If s was just initialised (no step and no lmood_set since
+ *   lmood_state_init), v_p at the start is the initial nodal solve of (v, F, mu) and the
+ *   reverse pass differentiates through it.
+ * lmood_tape_backward: given the adjoints of the final state (lam_x, lam_vp [dim][n_nodes],
+ *   lam_v [dim][n_cells], lam_F [dim*dim][n_cells]; NULL = zero), computes the gradients with
+ *   respect to the state at the start of the tape: grad_x, grad_vp [dim][n_nodes] (at fixed
+ *   cell masses), grad_v [dim][n_cells], grad_F [dim*dim][n_cells], and grad_mu [n_cells]
+ *   (accumulated over the steps; mu enters the stress, the impedance and kappa). When the tape
+ *   starts from a just-initialised state, grad_v, grad_F and grad_mu are the gradients with
+ *   respect to the inputs of lmood_state_init and grad_vp is zero. Any output may be NULL.
+ *   Pointers are device pointers when is_device != 0 (ordered on the mesh's stream), else
+ *   host pointers (the call synchronises). The tape replays each step from its checkpoint on
+ *   s's buffers and restores s's current state afterwards (fields X, VP, V, E, F, TAU, DT,
+ *   ORDER; the diagnostic fields VSTAR, PKM, PKR are not kept). May be called repeatedly.
+ * lmood_tape_info: out4[0] steps, [1] checkpoint interval, [2] 1 if the tape starts from a
+ *   just-initialised state, [3] device bytes held.
+ * Destroy the tape before its state.
+ */
+typedef struct lmood_tape_s *lmood_tape;
+lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_t checkpoint_every, lmood_tape *out,
+                               lmood_step_info *last);
+lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, const double *lam_vp, const double *lam_v,
+                                 const double *lam_F, double *grad_x, double *grad_vp, double *grad_v,
+                                 double *grad_F, double *grad_mu, int is_device);
+lmood_status lmood_tape_info(lmood_tape t, int64_t *out4);
+lmood_status lmood_tape_destroy(lmood_tape t);
+
 const char *lmood_last_error(void);
 
 #ifdef __cplusplus

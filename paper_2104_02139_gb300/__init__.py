@@ -45,7 +45,8 @@ class StepInfo(C.Structure):
 _lib = None
 EXPORTS = ("lmood_params_default", "lmood_mesh_create", "lmood_mesh_destroy", "lmood_mesh_info",
            "lmood_state_init", "lmood_state_destroy", "lmood_step", "lmood_run", "lmood_get", "lmood_set",
-           "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_totals_noalloc", "lmood_last_error")
+           "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_totals_noalloc", "lmood_tape_record",
+           "lmood_tape_backward", "lmood_tape_info", "lmood_tape_destroy", "lmood_last_error")
 K_PREDICT, K_NODES, K_UPDATE, K_MOOD, K_FINALIZE, K_MOMENTS, NK = range(7)
 K_NAMES = ("predict", "nodes", "update", "mood", "finalize", "moments")
 
@@ -73,6 +74,10 @@ def lib():
         L.lmood_timing.argtypes = [vp, C.c_int]
         L.lmood_timing_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.lmood_totals_noalloc.argtypes = [C.c_int, C.c_int64, vp, vp, vp, vp, vp]
+        L.lmood_tape_record.argtypes = [vp, C.c_int64, C.c_int64, C.POINTER(vp), C.POINTER(StepInfo)]
+        L.lmood_tape_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
+        L.lmood_tape_info.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.lmood_tape_destroy.argtypes = [vp]
         L.lmood_last_error.restype = C.c_char_p
         for name in EXPORTS:
             if name != "lmood_last_error":
@@ -224,6 +229,107 @@ class State:
     def state(self) -> dict:
         return {"x": self.get(FIELD_X), "vp": self.get(FIELD_VP), "v": self.get(FIELD_V), "e": self.get(FIELD_E),
                 "F": self.get(FIELD_F), "tau": self.get(FIELD_TAU)}
+
+
+class Tape:
+    """lmood_tape_record / backward / info / destroy: reverse-mode gradients of n steps of a
+    state with each step's MOOD order mask and dt frozen at their recorded values."""
+
+    def __init__(self, state: State, n_steps: int, checkpoint_every: int = 1):
+        self.state = state
+        h = C.c_void_p()
+        _check(lib().lmood_tape_record(state.h, n_steps, checkpoint_every, C.byref(h), C.byref(state.info)))
+        self.h = h
+
+    def info(self) -> dict:
+        o = (C.c_int64 * 4)()
+        _check(lib().lmood_tape_info(self.h, o))
+        return dict(zip(("steps", "checkpoint_every", "through_init", "bytes"), list(o)))
+
+    def backward(self, lam_x=None, lam_vp=None, lam_v=None, lam_F=None, out=None) -> dict:
+        """Adjoints of the final state in (numpy host arrays, or torch CUDA tensors; None = 0);
+        gradients with respect to the start of the tape out, as a dict x, vp, v, F, mu of the
+        same kind (numpy unless the inputs are torch tensors, or given in out)."""
+        st = self.state
+        shapes = {"x": st.shape(FIELD_X), "vp": st.shape(FIELD_VP), "v": st.shape(FIELD_V), "F": st.shape(FIELD_F),
+                  "mu": (st.mesh.n_cells,)}
+        ins = (lam_x, lam_vp, lam_v, lam_F)
+        dev = any(a is not None and hasattr(a, "data_ptr") for a in ins)
+        if out is None:
+            if dev:
+                import torch
+                out = {k: torch.empty(v, dtype=torch.float64, device="cuda") for k, v in shapes.items()}
+            else:
+                out = {k: np.empty(v) for k, v in shapes.items()}
+
+        def keep(a):  # contiguous float64 copies (when needed) that stay alive for the call
+            if a is None:
+                return None
+            if dev:
+                if not hasattr(a, "data_ptr"):
+                    raise TypeError("mix of host and device adjoint inputs")
+                import torch
+                return a.to(torch.float64).contiguous()
+            return np.ascontiguousarray(a, dtype=np.float64)
+
+        kept = [keep(a) for a in ins]
+        args = [None if a is None else (C.c_void_p(a.data_ptr()) if dev else a.ctypes.data) for a in kept]
+        outs = [out.get(k) for k in ("x", "vp", "v", "F", "mu")]
+        optr = [None if o is None else (C.c_void_p(o.data_ptr()) if dev else o.ctypes.data) for o in outs]
+        _check(lib().lmood_tape_backward(self.h, *args, *optr, 1 if dev else 0))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lmood_tape_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+def rollout(problem, n_steps: int, v0, mu, F0=None, checkpoint_every: int = 1, **params):
+    """Differentiable rollout (torch.autograd.Function): the state after n_steps steps of the
+    scheme on problem's mesh and material, started from the per-cell initial velocity v0
+    [dim, n_cells], shear modulus mu [n_cells] and deformation gradient F0 [dim*dim, n_cells]
+    (None: identity), given as float64 torch CUDA tensors. Returns (x, vp, v, F) at t^N as
+    torch CUDA tensors; gradients flow back to v0, mu and F0 through the recorded steps (MOOD
+    orders and dt frozen). The forward and the reverse pass run in the library's kernels."""
+    import torch
+
+    class _Rollout(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, v0_, mu_, F0_):
+            pb = problem
+            m = pb.mesh
+            mesh = Mesh(m.dim, m.x, m.c2n, m.bface, m.btag)
+            p = params_default(m.dim, cfl=pb.cfl)
+            for k, v in params.items():
+                setattr(p, k, v)
+            Fh = None if F0_ is None else F0_.detach().cpu().numpy()
+            state = State(mesh, pb.rho0, pb.lam, mu_.detach().cpu().numpy(), v0_.detach().cpu().numpy(), Fh, p)
+            tape = Tape(state, n_steps, checkpoint_every)
+            outs = []
+            for fid in (FIELD_X, FIELD_VP, FIELD_V, FIELD_F):
+                t = torch.empty(state.shape(fid), dtype=torch.float64, device="cuda")
+                state.get(fid, t)
+                outs.append(t)
+            torch.cuda.current_stream().synchronize()
+            ctx.tape, ctx.state, ctx.mesh, ctx.has_F = tape, state, mesh, F0_ is not None
+            return tuple(outs)
+
+        @staticmethod
+        def backward(ctx, gx, gvp, gv, gF):
+            def dense(g):
+                return None if g is None else g.contiguous().to(torch.float64)
+
+            out = ctx.tape.backward(*(dense(g) if g is not None else None for g in (gx, gvp, gv, gF)))
+            if isinstance(out["v"], np.ndarray):  # all output gradients were None
+                out = {k: torch.as_tensor(v, device="cuda") for k, v in out.items()}
+            torch.cuda.current_stream().synchronize()
+            return out["v"], out["mu"], (out["F"] if ctx.has_F else None)
+
+    return _Rollout.apply(v0, mu, F0)
 
 
 def simulation(problem, stream=None, cell_inst=None, n_inst=1, **params) -> State:

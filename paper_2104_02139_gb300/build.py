@@ -11,7 +11,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblmood.so")
-SOURCES = ["lmood_api.cu", "lmood_ops2.cu", "lmood_ops3.cu", "lmood_noalloc.cu"]
+SOURCES = ["lmood_api.cu", "lmood_ops2.cu", "lmood_ops3.cu", "lmood_noalloc.cu", "lmood_tape.cu", "lmood_adj2.cu",
+           "lmood_adj3.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

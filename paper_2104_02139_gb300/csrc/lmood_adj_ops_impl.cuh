@@ -1,0 +1,41 @@
+// lmood_adj_ops_impl.cuh -- launchers of the reverse-pass kernels for one dimension.
+#pragma once
+#include "lmood_adjoint_kernels.cuh"
+
+namespace lmood {
+namespace {
+
+constexpr int kAdjCellBlock = 128, kAdjNodeBlock = 128;
+inline int adj_blocks(int n, int b) { return (n + b - 1) / b; }
+
+template <int D> void adj_update(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, cudaStream_t s) {
+    k_adj_update<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+}
+template <int D> void adj_nodes(const Geo &g, const Fld &f, const AdjBuf &a, int init_mode, cudaStream_t s) {
+    k_adj_nodes<D><<<adj_blocks(g.Np, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, f, a, init_mode);
+}
+template <int D>
+void adj_predict(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, int force_p0, cudaStream_t s) {
+    k_adj_predict<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a, force_p0);
+}
+template <int D> void adj_moments(const Geo &g, const Fld &f, const AdjBuf &a, cudaStream_t s) {
+    k_adj_moments<D><<<adj_blocks(g.Np, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, f, a);
+}
+template <int D> void adj_cells(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, cudaStream_t s) {
+    k_adj_cells<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+}
+template <int D> void adj_gather(const Geo &g, const AdjBuf &a, cudaStream_t s) {
+    k_adj_gather<D><<<adj_blocks(g.Np, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, a);
+}
+template <int D> void adj_z0(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, cudaStream_t s) {
+    k_adj_z0<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+}
+
+}  // namespace
+
+#define LMOOD_ADJ_OPS_TABLE(D)                                                                              \
+    static const AdjOps table = {D, adj_update<D>, adj_nodes<D>, adj_predict<D>, adj_moments<D>, adj_cells<D>, \
+                                 adj_gather<D>, adj_z0<D>};                                                  \
+    return table;
+
+}  // namespace lmood

@@ -10,44 +10,13 @@
 #include <thread>
 #include <vector>
 
-#include "lmood.h"
-#include "lmood_ops.h"
+#include "lmood_internal.h"
 
 using namespace lmood;
 
 namespace {
 
 thread_local std::string g_err;
-
-lmood_status fail(lmood_status st, const std::string &msg) {
-    g_err = msg;
-    return st;
-}
-
-#define LM_CUDA(call)                                                                          \
-    do {                                                                                       \
-        cudaError_t e_ = (call);                                                               \
-        if (e_ != cudaSuccess) return fail(LMOOD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
-
-struct DevAllocs {
-    std::vector<void *> ptrs;
-    lmood_status alloc(void **p, size_t bytes) {
-        *p = nullptr;
-        if (bytes == 0) bytes = 16;
-        cudaError_t e = cudaMalloc(p, bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(LMOOD_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
-        }
-        ptrs.push_back(*p);
-        return LMOOD_OK;
-    }
-    void release() {
-        for (void *p : ptrs) cudaFree(p);
-        ptrs.clear();
-    }
-};
 
 template <class T> lmood_status upload(DevAllocs &A, T **dst, const T *src, size_t n, cudaStream_t st) {
     lmood_status s = A.alloc((void **)dst, n * sizeof(T));
@@ -70,22 +39,17 @@ void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)> &fn) {
 
 }  // namespace
 
+lmood_status lmood::fail(lmood_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
 // error message setter shared with the other translation units of the library
 void lmood_internal_set_error(const char *msg) { g_err = msg; }
 
 // =======================================================================================
 // mesh
 // =======================================================================================
-struct lmood_mesh_s {
-    int dim = 0, n_inst = 1;
-    int64_t np = 0, nc = 0, st_nnz = 0;
-    int max_deg = 0;
-    cudaStream_t st = nullptr;
-    const Ops *ops = nullptr;
-    Geo geo{};
-    double *x0 = nullptr;
-    DevAllocs mem;
-};
 
 static double host_volume(int d, const double *x, int64_t np, const int32_t *c2n, int64_t nc, int64_t c) {
     int p[4];
@@ -320,42 +284,6 @@ extern "C" lmood_status lmood_mesh_info(lmood_mesh m, int64_t *o) {
 // =======================================================================================
 // state
 // =======================================================================================
-struct lmood_state_s {
-    lmood_mesh M = nullptr;
-    lmood_params prm{};
-    lmood_material mat{};
-    Prm kp{};
-    Fld f{};
-    double *tau = nullptr, *m = nullptr, *im = nullptr, *mu = nullptr;
-    int *tl[2] = {nullptr, nullptr}, *nlist = nullptr, *clist = nullptr, *node_mark = nullptr, *cell_mark = nullptr;
-    double *totals = nullptr;
-    Ctl *ctl = nullptr;        // device MOOD control block
-    Report *d_report = nullptr;
-    Report *h_report = nullptr;  // pinned
-    // graph-captured steps: one executable graph per buffer parity (the state swaps pointers)
-    int parity = 0;
-    bool graphs_built = false;
-    cudaGraph_t graph[2] = {nullptr, nullptr};
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    cudaEvent_t gev[2][7] = {};
-    cudaStream_t cap_st = nullptr;   // private streams for capturing (the mesh's stream may be the
-    cudaStream_t body_st = nullptr;  // legacy default stream, which cannot be captured)
-    int *h_cnt = nullptr;      // pinned mirror of the device counters
-    double *h_dt = nullptr;    // pinned: dt used, dt next (instance 0)
-    double t = 0.0;
-    int64_t step = 0;
-    int stamp = 0;
-    bool broken = false;
-    lmood_step_info last{};
-    // kernel timing (CUDA events around launches, drained at the step's sync points)
-    bool timing = false;
-    std::vector<cudaEvent_t> ev;            // pool of 2 * kMaxPending events
-    std::vector<int> pend_cls;              // class of each pending pair
-    double kms[LMOOD_NK] = {};
-    int64_t klaunch[LMOOD_NK] = {};
-    DevAllocs mem;
-};
-
 static constexpr int kMaxPending = 64;
 
 static void timing_drain(lmood_state s) {
@@ -380,7 +308,7 @@ template <class F> static void timed(lmood_state s, int cls, int n_launch, F &&l
     s->pend_cls.push_back(cls);
 }
 
-static void swap_state(lmood_state s) {
+void lmood::swap_state(lmood_state s) {
     s->parity ^= 1;
     Fld &f = s->f;
     std::swap(f.x, f.x1);
@@ -437,7 +365,7 @@ extern "C" lmood_status lmood_state_destroy(lmood_state s) {
     return LMOOD_OK;
 }
 
-static lmood_status sync_check(lmood_state s, const char *where) {
+lmood_status lmood::sync_check(lmood_state s, const char *where) {
     cudaError_t e = cudaStreamSynchronize(s->M->st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -566,6 +494,7 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
         state_free(s);
         return r;
     }
+    s->at_init = true;
     *out = s;
     return LMOOD_OK;
 }
@@ -704,6 +633,7 @@ static lmood_status finish_step(lmood_state s, const Report &rep, lmood_step_inf
                                              " first-order cells are not computable (parachute failure)");
     }
     swap_state(s);
+    s->at_init = false;
     s->t += in.dt_used;
     s->step += 1;
     in.t = s->t;
@@ -861,6 +791,7 @@ extern "C" lmood_status lmood_set(lmood_state s, int field, const void *src, int
     default: return fail(LMOOD_ERR_ARG, "lmood_set: unknown or read-only field id");
     }
     LM_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (field != LMOOD_FIELD_DT) s->at_init = false;
     if (field == LMOOD_FIELD_X || field == LMOOD_FIELD_F) {
         std::swap(s->tau, f.tau1);
         M->ops->refresh(M->geo, f, s->kp, st);

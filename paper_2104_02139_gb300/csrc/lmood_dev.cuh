@@ -18,7 +18,7 @@ namespace lmood {
 
 struct Prm {
     double cfl, Cv, Ci, delta0, delta1, dt_fixed, lam;
-    int base_order;  // order every cell starts the step with (2: P1, 1: P0)
+    int base_order;  // order every cell starts the step with (2: P1, 1: P0; 0: keep f.order)
     int mood;        // detection on/off
     int vol_coeff;   // 0: kappa = lambda + 2 mu / 3; 1: kappa = mu
     int cascade;     // 2: P1 -> P0; 3: P1 -> P1 with Barth-Jespersen slopes -> P0

@@ -102,6 +102,8 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
     int ord;
     if constexpr (LISTED) {
         ord = f.order[c];
+    } else if (prm.base_order == 0) {
+        ord = f.order[c];  // replay of a recorded step: the cells' orders are given
     } else {
         ord = prm.base_order;
         f.order[c] = (unsigned char)ord;

@@ -1,0 +1,289 @@
+"""Reverse-mode gradients of recorded steps (lmood_tape_*) against central finite differences
+(-m gpu). The MOOD order mask and dt are frozen: the runs use a fixed dt, and every finite
+difference pair checks that its order masks equal the recorded ones, so the difference
+quotient and the adjoint differentiate the same smooth map.
+
+Objective: J = <lam, state(t^N)> with seeded random adjoints lam of x, v_p, v and F; checked
+as the directional derivative <grad, delta> for seeded random directions delta of each input.
+FD error: truncation O(eps^2) plus rounding ~1e-16 |J| / eps; with eps = 1e-6 of each
+input's scale the quotient is good to ~1e-8 relative, so the bar is 1e-6.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2104_02139_gb300 as L
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+OUT_FIELDS = (("x", L.FIELD_X), ("vp", L.FIELD_VP), ("v", L.FIELD_V), ("F", L.FIELD_F))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available()
+    L.build()
+    O.build()
+
+
+def _setup(pb, seed):
+    """Heterogeneous mu and a non-trivial initial F; seeded adjoints of the final state."""
+    rng = np.random.default_rng(seed)
+    d, nc, npn = pb.mesh.dim, pb.mesh.n_cells, pb.mesh.n_nodes
+    F = np.zeros((d * d, nc))
+    for a in range(d):
+        F[a * d + a] = 1.0
+    F += 0.01 * rng.standard_normal((d * d, nc))
+    mu = np.asarray(pb.mu, dtype=float) * (1.0 + 0.1 * rng.random(nc))
+    pb = dataclasses.replace(pb, F=F, mu=mu)
+    lam = {"x": rng.standard_normal((d, npn)), "vp": rng.standard_normal((d, npn)),
+           "v": rng.standard_normal((d, nc)), "F": rng.standard_normal((d * d, nc))}
+    return pb, lam, rng
+
+
+def _dt_fixed(pb, frac=0.5):
+    s = L.simulation(pb)
+    return frac * float(s.get(L.FIELD_DT)[0])
+
+
+def _J(st, lam):
+    return sum(float((st.get(fid) * lam[k]).sum()) for k, fid in OUT_FIELDS)
+
+
+def _run(pb, n, prm, pre=0, setter=None):
+    """pre steps, optional setter(state), then n steps; returns (state, masks of the n steps)."""
+    st = L.simulation(pb, **prm)
+    if pre:
+        st.run(pre)
+    if setter:
+        setter(st)
+    masks = []
+    for _ in range(n):
+        st.step()
+        masks.append(st.get(L.FIELD_ORDER).astype(np.int8))
+    return st, masks
+
+
+def _fd(pb, n, prm, lam, masks, make, eps, pre=0):
+    """central difference of J along the perturbation make(sign * eps)"""
+    vals = []
+    for sgn in (+1.0, -1.0):
+        pbp, setter = make(sgn * eps)
+        st, mk = _run(pbp, n, prm, pre=pre, setter=setter)
+        for j, (a, b) in enumerate(zip(mk, masks)):
+            assert np.array_equal(a, b), f"order mask changed under the perturbation at step {j}"
+        vals.append(_J(st, lam))
+    return (vals[0] - vals[1]) / (2 * eps)
+
+
+def _grad(pb, n, prm, lam, pre=0, ckpt=1):
+    st = L.simulation(pb, **prm)
+    if pre:
+        st.run(pre)
+    tape = L.Tape(st, n, ckpt)
+    g = tape.backward(lam_x=lam["x"], lam_vp=lam["vp"], lam_v=lam["v"], lam_F=lam["F"])
+    return st, tape, g
+
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(a), abs(b), 1e-300)
+
+
+def _check_init_grads(pb, n, prm, seed, tol=1e-6, eps_rel=1e-6):
+    pb, lam, rng = _setup(pb, seed)
+    prm = dict(prm, dt_fixed=_dt_fixed(pb))
+    st, tape, g = _grad(pb, n, prm, lam)
+    assert tape.info()["through_init"] == 1
+    _, masks = _run(pb, n, prm)
+    d, nc = pb.mesh.dim, pb.mesh.n_cells
+    dv = rng.standard_normal((d, nc))
+    dmu = rng.standard_normal(nc) * np.asarray(pb.mu)
+    dF = rng.standard_normal((d * d, nc))
+    sv = eps_rel * max(np.abs(pb.v).max(), 1e-3)
+    smu = eps_rel
+    sF = eps_rel
+    cases = [
+        ("v", lambda e: (dataclasses.replace(pb, v=pb.v + e * dv), None), sv, float((g["v"] * dv).sum())),
+        ("mu", lambda e: (dataclasses.replace(pb, mu=pb.mu + e * dmu), None), smu, float((g["mu"] * dmu).sum())),
+        ("F", lambda e: (dataclasses.replace(pb, F=pb.F + e * dF), None), sF, float((g["F"] * dF).sum())),
+    ]
+    assert np.all(g["vp"] == 0.0)
+    out = {}
+    for name, make, eps, ad in cases:
+        fd = _fd(pb, n, prm, lam, masks, make, eps)
+        out[name] = (ad, fd)
+        assert _rel(ad, fd) <= tol, (name, ad, fd)
+    return out, masks
+
+
+def test_adjoint_fd_2d_p1():
+    out, masks = _check_init_grads(W.plain2d(n=10), 6, {}, seed=11)
+    assert all(np.all(m == 2) for m in masks)
+
+
+def test_adjoint_fd_2d_p0_scheme():
+    out, masks = _check_init_grads(W.plain2d(n=9), 5, {"order": 1}, seed=12)
+    assert all(np.all(m == 1) for m in masks)
+
+
+def test_adjoint_fd_2d_mood_mask():
+    """An impact with MOOD active: some cells recomputed at first order in the recorded steps."""
+    pb = W.impact2d(n=24)
+    out, masks = _check_init_grads(pb, 6, {}, seed=13)
+    assert sum(int((m == 1).sum()) for m in masks) > 0, "no first-order cells: the mixed mask is not exercised"
+
+
+def test_adjoint_fd_3d_slip():
+    out, masks = _check_init_grads(W.cube3d(n=3), 4, {}, seed=14)
+
+
+def test_adjoint_fd_3d_clamped_column():
+    pb = W.column3d(nxy=2, nz=6)
+    out, masks = _check_init_grads(pb, 4, {}, seed=15)
+
+
+def test_adjoint_fd_mid_run_state():
+    """A tape that starts after some steps: gradients of x, v_p, v, F (via lmood_set) and mu."""
+    pb, lam, rng = _setup(W.plain2d(n=10), 16)
+    prm = {"dt_fixed": _dt_fixed(pb)}
+    pre, n = 3, 5
+    st, tape, g = _grad(pb, n, prm, lam, pre=pre)
+    assert tape.info()["through_init"] == 0
+    _, masks = _run(pb, n, prm, pre=pre)
+    base = L.simulation(pb, **prm)
+    base.run(pre)
+    x0, vp0, v0, F0 = (base.get(f) for f in (L.FIELD_X, L.FIELD_VP, L.FIELD_V, L.FIELD_F))
+    d, nc, npn = pb.mesh.dim, pb.mesh.n_cells, pb.mesh.n_nodes
+    h = np.sqrt((base.get(L.FIELD_TAU) * base.get(L.FIELD_MASS)).mean())  # a cell size
+    dirs = {"x": rng.standard_normal((d, npn)), "vp": rng.standard_normal((d, npn)),
+            "v": rng.standard_normal((d, nc)), "F": rng.standard_normal((d * d, nc))}
+    scale = {"x": 1e-6 * h, "vp": 1e-6 * max(np.abs(vp0).max(), 1e-3), "v": 1e-6 * max(np.abs(v0).max(), 1e-3),
+             "F": 1e-6}
+    fields = {"x": (L.FIELD_X, x0), "vp": (L.FIELD_VP, vp0), "v": (L.FIELD_V, v0), "F": (L.FIELD_F, F0)}
+    for k, (fid, val) in fields.items():
+        dk = dirs[k]
+
+        def make(e, fid=fid, val=val, dk=dk):
+            return pb, (lambda s: s.set(fid, val + e * dk))
+        fd = _fd(pb, n, prm, lam, masks, make, scale[k], pre=pre)
+        ad = float((g[k] * dk).sum())
+        assert _rel(ad, fd) <= 1e-6, (k, ad, fd)
+
+
+def test_adjoint_vs_oracle_fd():
+    """The CUDA adjoint against finite differences of the CPU oracle (an independent forward)."""
+    pb, lam, rng = _setup(W.plain2d(n=8), 17)
+    n = 4
+    prm = {"dt_fixed": _dt_fixed(pb), "mood": 0}
+    st, tape, g = _grad(pb, n, prm, lam)
+    dv = rng.standard_normal(pb.v.shape)
+    dmu = rng.standard_normal(pb.mesh.n_cells)
+    ofields = (("x", O.F_X), ("vp", O.F_VP), ("v", O.F_V), ("F", O.F_F))
+
+    def Jo(p):
+        o = O.Oracle(p, **prm)
+        for _ in range(n):
+            o.step()
+        return sum(float((o.get(fid) * lam[k]).sum()) for k, fid in ofields)
+    for name, d, eps, ad in (("v", dv, 1e-6 * np.abs(pb.v).max(), float((g["v"] * dv).sum())),
+                             ("mu", dmu, 1e-6, float((g["mu"] * dmu).sum()))):
+        plus = dataclasses.replace(pb, **{name: getattr(pb, name) + eps * d})
+        minus = dataclasses.replace(pb, **{name: getattr(pb, name) - eps * d})
+        fd = (Jo(plus) - Jo(minus)) / (2 * eps)
+        assert _rel(ad, fd) <= 1e-6, (name, ad, fd)
+
+
+def test_checkpoint_interval_is_bitwise_invariant():
+    pb, lam, _ = _setup(W.impact2d(n=16), 18)
+    prm = {"dt_fixed": _dt_fixed(pb)}
+    n = 7
+    ref = None
+    for C in (1, 2, 3, 7, 100):
+        _, tape, g = _grad(pb, n, prm, lam, ckpt=C)
+        assert tape.info()["checkpoint_every"] == min(C, n)
+        if ref is None:
+            ref = g
+        else:
+            for k in ref:
+                assert np.array_equal(ref[k], g[k]), (C, k)
+
+
+def test_backward_restores_the_state_and_repeats():
+    pb, lam, _ = _setup(W.plain2d(n=12), 19)
+    st = L.simulation(pb)
+    twin = L.simulation(pb)
+    tape = L.Tape(st, 4, 2)
+    twin.run(4)
+    before = {f: st.get(f) for f in (L.FIELD_X, L.FIELD_VP, L.FIELD_V, L.FIELD_E, L.FIELD_F, L.FIELD_TAU,
+                                      L.FIELD_DT, L.FIELD_ORDER)}
+    g1 = tape.backward(lam_x=lam["x"], lam_v=lam["v"])
+    g2 = tape.backward(lam_x=lam["x"], lam_v=lam["v"])
+    for k in g1:
+        assert np.array_equal(g1[k], g2[k]), k
+    for f, a in before.items():
+        assert np.array_equal(st.get(f), a), f
+    st.run(3)
+    twin.run(3)
+    for f in (L.FIELD_X, L.FIELD_V, L.FIELD_F, L.FIELD_E):
+        assert np.array_equal(st.get(f), twin.get(f)), f
+
+
+def test_backward_linear_in_the_adjoints():
+    pb, lam, rng = _setup(W.cube3d(n=3), 20)
+    _, tape, _ = _grad(pb, 3, {}, lam)
+    ga = tape.backward(lam_v=lam["v"])
+    gb = tape.backward(lam_F=lam["F"])
+    gab = tape.backward(lam_v=lam["v"], lam_F=lam["F"])
+    for k in ga:
+        np.testing.assert_allclose(gab[k], ga[k] + gb[k], rtol=1e-12, atol=1e-12 * np.abs(gab[k]).max())
+    g0 = tape.backward()
+    for k in g0:
+        assert not np.any(g0[k]), k
+
+
+def test_torch_rollout_autograd():
+    import torch
+    pb, lam, rng = _setup(W.plain2d(n=10), 21)
+    prm = {"dt_fixed": _dt_fixed(pb)}
+    n = 4
+    dev = "cuda"
+    v0 = torch.tensor(pb.v, dtype=torch.float64, device=dev, requires_grad=True)
+    mu = torch.tensor(pb.mu, dtype=torch.float64, device=dev, requires_grad=True)
+    F0 = torch.tensor(pb.F, dtype=torch.float64, device=dev, requires_grad=True)
+    w = torch.tensor(lam["x"], device=dev)
+    x, vp, v, F = L.rollout(pb, n, v0, mu, F0, checkpoint_every=2, **prm)
+    loss = (v * v).sum() + (x * w).sum() + F.sum()
+    loss.backward()
+    # the same gradient from the tape with the adjoints written out
+    st = L.simulation(pb, **prm)
+    tape = L.Tape(st, n)
+    vN = st.get(L.FIELD_V)
+    g = tape.backward(lam_x=lam["x"], lam_v=2 * vN, lam_F=np.ones((pb.mesh.dim ** 2, pb.mesh.n_cells)))
+    np.testing.assert_allclose(v0.grad.cpu().numpy(), g["v"], rtol=1e-12, atol=1e-14 * np.abs(g["v"]).max())
+    np.testing.assert_allclose(mu.grad.cpu().numpy(), g["mu"], rtol=1e-12, atol=1e-14 * np.abs(g["mu"]).max())
+    np.testing.assert_allclose(F0.grad.cpu().numpy(), g["F"], rtol=1e-12, atol=1e-14 * np.abs(g["F"]).max())
+    # and a finite difference of the rollout along v0
+    d = torch.tensor(rng.standard_normal(pb.v.shape), device=dev)
+    eps = 1e-6 * float(v0.abs().max())
+    with torch.no_grad():
+        def Lf(vv):
+            x_, _, v_, F_ = L.rollout(pb, n, vv, mu, F0, **prm)
+            return float((v_ * v_).sum() + (x_ * w).sum() + F_.sum())
+        fd = (Lf(v0 + eps * d) - Lf(v0 - eps * d)) / (2 * eps)
+    ad = float((v0.grad * d).sum())
+    assert _rel(ad, fd) <= 1e-6, (ad, fd)
+
+
+def test_tape_errors():
+    pb = W.plain2d(n=6)
+    st = L.simulation(pb)
+    with pytest.raises(L.LmoodError) as e:
+        L.Tape(st, 0)
+    assert e.value.status == L.ERR_ARG
+    with pytest.raises(L.LmoodError) as e:
+        L.Tape(st, 2, 0)
+    assert e.value.status == L.ERR_ARG
