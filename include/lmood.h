@@ -245,6 +245,11 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  *   host pointers (the call synchronises). The tape replays each step from its checkpoint on
  *   s's buffers and restores s's current state afterwards (fields X, VP, V, E, F, TAU, DT,
  *   ORDER; the diagnostic fields VSTAR, PKM, PKR are not kept). May be called repeatedly.
+ * lmood_tape_replay: advances the state s2 (any state on a mesh of the same sizes, e.g. one
+ *   initialised from perturbed data) by the first n_steps recorded steps, from its current
+ *   fields, with the recorded orders and dt and no MOOD detection or dt rule: the smooth map
+ *   whose gradient lmood_tape_backward computes. s2's next dt is then set by the usual rule,
+ *   so it can go on with lmood_step. Synchronises once per step.
  * lmood_tape_info: out4[0] steps, [1] checkpoint interval, [2] 1 if the tape starts from a
  *   just-initialised state, [3] device bytes held.
  * Destroy the tape before its state.
@@ -255,6 +260,7 @@ lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_t checkpoin
 lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, const double *lam_vp, const double *lam_v,
                                  const double *lam_F, double *grad_x, double *grad_vp, double *grad_v,
                                  double *grad_F, double *grad_mu, int is_device);
+lmood_status lmood_tape_replay(lmood_tape t, lmood_state s2, int64_t n_steps);
 lmood_status lmood_tape_info(lmood_tape t, int64_t *out4);
 lmood_status lmood_tape_destroy(lmood_tape t);
 

@@ -46,7 +46,7 @@ _lib = None
 EXPORTS = ("lmood_params_default", "lmood_mesh_create", "lmood_mesh_destroy", "lmood_mesh_info",
            "lmood_state_init", "lmood_state_destroy", "lmood_step", "lmood_run", "lmood_get", "lmood_set",
            "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_totals_noalloc", "lmood_tape_record",
-           "lmood_tape_backward", "lmood_tape_info", "lmood_tape_destroy", "lmood_last_error")
+           "lmood_tape_backward", "lmood_tape_replay", "lmood_tape_info", "lmood_tape_destroy", "lmood_last_error")
 K_PREDICT, K_NODES, K_UPDATE, K_MOOD, K_FINALIZE, K_MOMENTS, NK = range(7)
 K_NAMES = ("predict", "nodes", "update", "mood", "finalize", "moments")
 
@@ -76,6 +76,7 @@ def lib():
         L.lmood_totals_noalloc.argtypes = [C.c_int, C.c_int64, vp, vp, vp, vp, vp]
         L.lmood_tape_record.argtypes = [vp, C.c_int64, C.c_int64, C.POINTER(vp), C.POINTER(StepInfo)]
         L.lmood_tape_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
+        L.lmood_tape_replay.argtypes = [vp, vp, C.c_int64]
         L.lmood_tape_info.argtypes = [vp, C.POINTER(C.c_int64)]
         L.lmood_tape_destroy.argtypes = [vp]
         L.lmood_last_error.restype = C.c_char_p
@@ -278,6 +279,13 @@ class Tape:
         optr = [None if o is None else (C.c_void_p(o.data_ptr()) if dev else o.ctypes.data) for o in outs]
         _check(lib().lmood_tape_backward(self.h, *args, *optr, 1 if dev else 0))
         return out
+
+    def replay(self, state: State, n_steps: int | None = None) -> State:
+        """Advance another state (same mesh sizes) by the recorded steps with the recorded
+        orders and dt: the frozen-mask map that backward() differentiates."""
+        n = self.info()["steps"] if n_steps is None else n_steps
+        _check(lib().lmood_tape_replay(self.h, state.h, n))
+        return state
 
     def close(self):
         if getattr(self, "h", None):

@@ -71,8 +71,7 @@ cudaError_t copy_snap(const Snap &dst, const Snap &src, int D, int64_t N, int64_
 
 // one step of the forward scheme on the state's buffers with the recorded dt and orders
 // (t^n in the current buffers -> packets, v*_p and t^{n+1} in the candidate buffers)
-lmood_status replay_step(lmood_tape t, int64_t j) {
-    lmood_state s = t->s;
+lmood_status replay_step(lmood_tape t, int64_t j, lmood_state s) {
     lmood_mesh M = s->M;
     const Ops &op = *M->ops;
     const Fld &f = s->f;
@@ -260,13 +259,13 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
         const Snap ck = snap_at(t->ck + k * sd, D, N, Np);
         LM_CUDA(copy_snap(cur, ck, D, N, Np, st));
         for (int64_t i = 0; i + 1 < len; ++i) {  // states b+1 .. b+len-1 into seg[0 ..]
-            if ((r = replay_step(t, b + i))) return r;
+            if ((r = replay_step(t, b + i, s))) return r;
             LM_CUDA(copy_snap(snap_at(t->seg + i * sd, D, N, Np), nxt, D, N, Np, st));
             LM_CUDA(copy_snap(cur, nxt, D, N, Np, st));
         }
         for (int64_t i = len - 1; i >= 0; --i) {
             if (i < len - 1) LM_CUDA(copy_snap(cur, i == 0 ? ck : snap_at(t->seg + (i - 1) * sd, D, N, Np), D, N, Np, st));
-            if ((r = replay_step(t, b + i))) return r;
+            if ((r = replay_step(t, b + i, s))) return r;
             reverse_step(t, a);
         }
     }
@@ -298,6 +297,33 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
                             st));
     LM_CUDA(cudaMemcpyAsync(f.order, t->tmp_order, N, cudaMemcpyDeviceToDevice, st));
     if (!is_device) return sync_check(s, "lmood_tape_backward");
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_tape_replay(lmood_tape t, lmood_state s2, int64_t n_steps) {
+    if (!t || !t->s || !s2) return fail(LMOOD_ERR_ARG, "lmood_tape_replay: NULL argument");
+    if (s2->broken) return fail(LMOOD_ERR_STATE, "lmood_tape_replay: state unusable after an earlier CUDA error");
+    const lmood_mesh M = s2->M, Mt = t->s->M;
+    if (M->dim != Mt->dim || M->nc != Mt->nc || M->np != Mt->np || M->n_inst != Mt->n_inst)
+        return fail(LMOOD_ERR_ARG, "lmood_tape_replay: the state's mesh differs in size from the tape's");
+    if (n_steps < 0 || n_steps > t->n) return fail(LMOOD_ERR_ARG, "lmood_tape_replay: n_steps out of range");
+    const Ops &op = *M->ops;
+    cudaStream_t st = M->st;
+    for (int64_t j = 0; j < n_steps; ++j) {
+        lmood_status r = replay_step(t, j, s2);
+        if (r) return r;
+        // next dt from the candidates, as after an ordinary step, so that s2 can step on
+        LM_CUDA(cudaMemsetAsync(s2->f.cnt, 0, CNT_N * sizeof(int), st));
+        op.dt_init(s2->f, s2->kp, M->n_inst, 0, st);
+        op.finalize(M->geo, s2->f, s2->kp, st);
+        LM_CUDA(cudaMemcpyAsync(s2->h_dt, s2->f.dt, sizeof(double), cudaMemcpyDeviceToHost, st));
+        lmood_status rs = sync_check(s2, "lmood_tape_replay");
+        if (rs) return rs;
+        swap_state(s2);
+        s2->t += s2->h_dt[0];
+        s2->step += 1;
+        s2->at_init = false;
+    }
     return LMOOD_OK;
 }
 

@@ -5,8 +5,10 @@ quotient and the adjoint differentiate the same smooth map.
 
 Objective: J = <lam, state(t^N)> with seeded random adjoints lam of x, v_p, v and F; checked
 as the directional derivative <grad, delta> for seeded random directions delta of each input.
-FD error: truncation O(eps^2) plus rounding ~1e-16 |J| / eps; with eps = 1e-6 of each
-input's scale the quotient is good to ~1e-8 relative, so the bar is 1e-6.
+The two perturbed runs' fields are differenced element by element before the contraction
+with lam. Steps of 1e-6 (absolute: the map's nonlinear scales -- sound speed, F ~ I, mu --
+are O(1)) leave a truncation error ~1e-12 and a rounding error ~1e-16 |field| / eps ~ 1e-10,
+relative; the bar is 1e-6.
 """
 import dataclasses
 
@@ -50,8 +52,8 @@ def _dt_fixed(pb, frac=0.5):
     return frac * float(s.get(L.FIELD_DT)[0])
 
 
-def _J(st, lam):
-    return sum(float((st.get(fid) * lam[k]).sum()) for k, fid in OUT_FIELDS)
+def _fields(st):
+    return {k: st.get(fid) for k, fid in OUT_FIELDS}
 
 
 def _run(pb, n, prm, pre=0, setter=None):
@@ -68,16 +70,22 @@ def _run(pb, n, prm, pre=0, setter=None):
     return st, masks
 
 
-def _fd(pb, n, prm, lam, masks, make, eps, pre=0):
-    """central difference of J along the perturbation make(sign * eps)"""
+def _fd(pb, n, prm, lam, masks, make, eps, pre=0, tape=None):
+    """central difference of J along the perturbation make(sign * eps): through ordinary steps
+    (whose masks must equal the recorded ones), or through tape.replay (orders and dt frozen)"""
     vals = []
     for sgn in (+1.0, -1.0):
         pbp, setter = make(sgn * eps)
-        st, mk = _run(pbp, n, prm, pre=pre, setter=setter)
-        for j, (a, b) in enumerate(zip(mk, masks)):
-            assert np.array_equal(a, b), f"order mask changed under the perturbation at step {j}"
-        vals.append(_J(st, lam))
-    return (vals[0] - vals[1]) / (2 * eps)
+        if tape is None:
+            st, mk = _run(pbp, n, prm, pre=pre, setter=setter)
+            for j, (a, b) in enumerate(zip(mk, masks)):
+                assert np.array_equal(a, b), f"order mask changed under the perturbation at step {j}"
+        else:
+            st = L.simulation(pbp, **prm)
+            tape.replay(st)
+        vals.append(_fields(st))
+    # difference the fields first, then contract with lam (no cancellation in a large sum)
+    return sum(float(((vals[0][k] - vals[1][k]) * lam[k]).sum()) for k in lam) / (2 * eps)
 
 
 def _grad(pb, n, prm, lam, pre=0, ckpt=1):
@@ -93,9 +101,12 @@ def _rel(a, b):
     return abs(a - b) / max(abs(a), abs(b), 1e-300)
 
 
-def _check_init_grads(pb, n, prm, seed, tol=1e-6, eps_rel=1e-6):
+def _check_init_grads(pb, n, prm, seed, tol=1e-6, eps=1e-6, frozen=False):
+    """frozen: finite differences through the tape's replay (any dt rule; MOOD masks of the
+    recorded run); else through ordinary steps at a fixed dt"""
     pb, lam, rng = _setup(pb, seed)
-    prm = dict(prm, dt_fixed=_dt_fixed(pb))
+    if not frozen:
+        prm = dict(prm, dt_fixed=_dt_fixed(pb))
     st, tape, g = _grad(pb, n, prm, lam)
     assert tape.info()["through_init"] == 1
     _, masks = _run(pb, n, prm)
@@ -103,9 +114,7 @@ def _check_init_grads(pb, n, prm, seed, tol=1e-6, eps_rel=1e-6):
     dv = rng.standard_normal((d, nc))
     dmu = rng.standard_normal(nc) * np.asarray(pb.mu)
     dF = rng.standard_normal((d * d, nc))
-    sv = eps_rel * max(np.abs(pb.v).max(), 1e-3)
-    smu = eps_rel
-    sF = eps_rel
+    sv = smu = sF = eps  # absolute: the nonlinear scales (sound speed ~ 1, F ~ I, mu ~ 1) are O(1)
     cases = [
         ("v", lambda e: (dataclasses.replace(pb, v=pb.v + e * dv), None), sv, float((g["v"] * dv).sum())),
         ("mu", lambda e: (dataclasses.replace(pb, mu=pb.mu + e * dmu), None), smu, float((g["mu"] * dmu).sum())),
@@ -114,14 +123,14 @@ def _check_init_grads(pb, n, prm, seed, tol=1e-6, eps_rel=1e-6):
     assert np.all(g["vp"] == 0.0)
     out = {}
     for name, make, eps, ad in cases:
-        fd = _fd(pb, n, prm, lam, masks, make, eps)
+        fd = _fd(pb, n, prm, lam, masks, make, eps, tape=tape if frozen else None)
         out[name] = (ad, fd)
         assert _rel(ad, fd) <= tol, (name, ad, fd)
     return out, masks
 
 
 def test_adjoint_fd_2d_p1():
-    out, masks = _check_init_grads(W.plain2d(n=10), 6, {}, seed=11)
+    out, masks = _check_init_grads(W.plain2d(n=10), 6, {"mood": 0}, seed=11)
     assert all(np.all(m == 2) for m in masks)
 
 
@@ -131,10 +140,33 @@ def test_adjoint_fd_2d_p0_scheme():
 
 
 def test_adjoint_fd_2d_mood_mask():
-    """An impact with MOOD active: some cells recomputed at first order in the recorded steps."""
+    """An impact with MOOD active and the adaptive dt: some cells recomputed at first order
+    in the recorded steps. RDMP has cells within ~1e-6 of its threshold, so the finite
+    differences go through the tape's replay (the map with the recorded masks and dt)."""
     pb = W.impact2d(n=24)
-    out, masks = _check_init_grads(pb, 6, {}, seed=13)
+    out, masks = _check_init_grads(pb, 6, {}, seed=13, frozen=True)
     assert sum(int((m == 1).sum()) for m in masks) > 0, "no first-order cells: the mixed mask is not exercised"
+
+
+def test_adjoint_fd_3d_mood_mask():
+    pb = W.cube3d(n=4)
+    pb.v *= 4.0
+    out, masks = _check_init_grads(pb, 5, {}, seed=23, frozen=True)
+    assert sum(int((m == 1).sum()) for m in masks) > 0, "no first-order cells: the mixed mask is not exercised"
+
+
+def test_replay_reproduces_the_recorded_run():
+    """The frozen-mask replay of a state's own initial data lands on the recorded run."""
+    for pb in (W.impact2d(n=24), W.cube3d(n=4)):
+        pb.v *= 1.0 if pb.mesh.dim == 2 else 4.0
+        st = L.simulation(pb)
+        tape = L.Tape(st, 5, 2)
+        other = tape.replay(L.simulation(pb))
+        for k, fid in OUT_FIELDS + (("e", L.FIELD_E),):
+            a, b = st.get(fid), other.get(fid)
+            assert np.abs(a - b).max() <= 1e-13 * max(np.abs(a).max(), 1e-300), k
+        assert np.array_equal(st.get(L.FIELD_DT), other.get(L.FIELD_DT)) or \
+            abs(st.get(L.FIELD_DT)[0] / other.get(L.FIELD_DT)[0] - 1) < 1e-12
 
 
 def test_adjoint_fd_3d_slip():
@@ -149,7 +181,7 @@ def test_adjoint_fd_3d_clamped_column():
 def test_adjoint_fd_mid_run_state():
     """A tape that starts after some steps: gradients of x, v_p, v, F (via lmood_set) and mu."""
     pb, lam, rng = _setup(W.plain2d(n=10), 16)
-    prm = {"dt_fixed": _dt_fixed(pb)}
+    prm = {"dt_fixed": _dt_fixed(pb), "mood": 0}
     pre, n = 3, 5
     st, tape, g = _grad(pb, n, prm, lam, pre=pre)
     assert tape.info()["through_init"] == 0
@@ -161,8 +193,7 @@ def test_adjoint_fd_mid_run_state():
     h = np.sqrt((base.get(L.FIELD_TAU) * base.get(L.FIELD_MASS)).mean())  # a cell size
     dirs = {"x": rng.standard_normal((d, npn)), "vp": rng.standard_normal((d, npn)),
             "v": rng.standard_normal((d, nc)), "F": rng.standard_normal((d * d, nc))}
-    scale = {"x": 1e-6 * h, "vp": 1e-6 * max(np.abs(vp0).max(), 1e-3), "v": 1e-6 * max(np.abs(v0).max(), 1e-3),
-             "F": 1e-6}
+    scale = {"x": 1e-5 * h, "vp": 1e-6, "v": 1e-6, "F": 1e-6}
     fields = {"x": (L.FIELD_X, x0), "vp": (L.FIELD_VP, vp0), "v": (L.FIELD_V, v0), "F": (L.FIELD_F, F0)}
     for k, (fid, val) in fields.items():
         dk = dirs[k]
@@ -188,12 +219,12 @@ def test_adjoint_vs_oracle_fd():
         o = O.Oracle(p, **prm)
         for _ in range(n):
             o.step()
-        return sum(float((o.get(fid) * lam[k]).sum()) for k, fid in ofields)
-    for name, d, eps, ad in (("v", dv, 1e-6 * np.abs(pb.v).max(), float((g["v"] * dv).sum())),
+        return {k: o.get(fid) for k, fid in ofields}
+    for name, d, eps, ad in (("v", dv, 1e-6, float((g["v"] * dv).sum())),
                              ("mu", dmu, 1e-6, float((g["mu"] * dmu).sum()))):
-        plus = dataclasses.replace(pb, **{name: getattr(pb, name) + eps * d})
-        minus = dataclasses.replace(pb, **{name: getattr(pb, name) - eps * d})
-        fd = (Jo(plus) - Jo(minus)) / (2 * eps)
+        plus = Jo(dataclasses.replace(pb, **{name: getattr(pb, name) + eps * d}))
+        minus = Jo(dataclasses.replace(pb, **{name: getattr(pb, name) - eps * d}))
+        fd = sum(float(((plus[k] - minus[k]) * lam[k]).sum()) for k in lam) / (2 * eps)
         assert _rel(ad, fd) <= 1e-6, (name, ad, fd)
 
 
@@ -268,12 +299,11 @@ def test_torch_rollout_autograd():
     np.testing.assert_allclose(F0.grad.cpu().numpy(), g["F"], rtol=1e-12, atol=1e-14 * np.abs(g["F"]).max())
     # and a finite difference of the rollout along v0
     d = torch.tensor(rng.standard_normal(pb.v.shape), device=dev)
-    eps = 1e-6 * float(v0.abs().max())
+    eps = 1e-6
     with torch.no_grad():
-        def Lf(vv):
-            x_, _, v_, F_ = L.rollout(pb, n, vv, mu, F0, **prm)
-            return float((v_ * v_).sum() + (x_ * w).sum() + F_.sum())
-        fd = (Lf(v0 + eps * d) - Lf(v0 - eps * d)) / (2 * eps)
+        xp_, _, vp_, Fp_ = L.rollout(pb, n, v0 + eps * d, mu, F0, **prm)
+        xm_, _, vm_, Fm_ = L.rollout(pb, n, v0 - eps * d, mu, F0, **prm)
+        fd = float(((vp_ - vm_) * (vp_ + vm_)).sum() + ((xp_ - xm_) * w).sum() + (Fp_ - Fm_).sum()) / (2 * eps)
     ad = float((v0.grad * d).sum())
     assert _rel(ad, fd) <= 1e-6, (ad, fd)
 
