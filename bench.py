@@ -303,6 +303,10 @@ def run_ours(args, rank, local, ws, dist):
     if not args.no_batched:
         batched = run_batched(L, W, torch, local, value / ws, args)
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = run_adjoint(L, torch, sim, stream, ms_max / args.steps, args)
+
     cb = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(make_workload(args.workload))
@@ -315,7 +319,7 @@ def run_ours(args, rank, local, ws, dist):
                            "lsq_pairs": info["stencil_nnz"], "parallelism": f"replicas x{ws}",
                            "l2": "working set > L2 (no flush)", "troubled_cells_in_timed_steps": troubled},
                 "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": ck, "e2e": e2e,
-                "cpu_baseline": cb, "batched": batched}
+                "cpu_baseline": cb, "batched": batched, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
 
 
@@ -350,6 +354,39 @@ def run_batched(L, W, torch, local, plain_value, args) -> dict:
             "launch": "one launch per stage for all instances, graph-captured steps"}
 
 
+def run_adjoint(L, torch, sim, stream, fwd_ms, args) -> dict:
+    """Reverse-mode gradient of K further steps of the same state (MOOD masks and dt frozen at
+    their recorded values): time to record the tape (the K ordinary steps plus checkpoints)
+    and to run the reverse pass (per step: reload the checkpoint, replay the step, the
+    reverse kernels), per step and against the plain step."""
+    k = max(10, args.steps // 10)
+    d = sim.mesh.dim
+    g = torch.Generator(device="cuda").manual_seed(7)
+    lam = {"x": torch.randn(d, sim.mesh.n_nodes, device="cuda", dtype=torch.float64, generator=g),
+           "v": torch.randn(d, sim.mesh.n_cells, device="cuda", dtype=torch.float64, generator=g)}
+    out = {k2: torch.empty(sh, device="cuda", dtype=torch.float64)
+           for k2, sh in (("x", (d, sim.mesh.n_nodes)), ("vp", (d, sim.mesh.n_nodes)), ("v", (d, sim.mesh.n_cells)),
+                          ("F", (d * d, sim.mesh.n_cells)), ("mu", (sim.mesh.n_cells,)))}
+    res = {}
+    for ck in (0, 4):
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        tape = L.Tape(sim, k, ck)
+        e1.record(stream)
+        tape.backward(lam_x=lam["x"], lam_v=lam["v"], out=out)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        rec, bwd = e0.elapsed_time(e1) / k, e1.elapsed_time(e2) / k
+        res[f"checkpoint_every_{ck}"] = {"record_ms_per_step": rec, "backward_ms_per_step": bwd,
+                                         "backward_over_forward": bwd / fwd_ms,
+                                         "tape_bytes": tape.info()["bytes"]}
+        tape.close()
+    gn = float(out["v"].abs().max())
+    return {"steps": k, "forward_ms_per_step": fwd_ms, **res, "grad_v_max_abs": gn,
+            "what": "gradient of <lam, (x, v)> at t^{n+K} w.r.t. the state and mu at t^n"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,17 +401,27 @@ def main():
                     help="host-driven MOOD rounds instead of graph-captured steps (same kernels; for profilers)")
     ap.add_argument("--no-fp64-peak", action="store_true", help="skip the DGEMM FP64 peak measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-instances measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-pass measurement")
     ap.add_argument("--case", type=int, default=0,
                     help="profiling case: build the workload, take this many untimed steps, exit")
+    ap.add_argument("--case-adjoint", type=int, default=0,
+                    help="with --case: then record this many steps on a tape and run its reverse pass once")
+    ap.add_argument("--case-n", type=int, default=0,
+                    help="with --case: a smaller impact2d (lattice n x n) for multi-pass profiler captures")
     args = ap.parse_args()
     if args.case:
         import torch
         import paper_2104_02139_gb300 as L
         import workloads as W
         L.build()
-        sim = L.simulation(make_workload(args.workload), graph=0 if args.host_mode else 1)
+        pb = W.impact2d(n=args.case_n) if args.case_n else make_workload(args.workload)
+        sim = L.simulation(pb, graph=0 if args.host_mode else 1)
         for _ in range(args.case):
             info = sim.step()
+        if args.case_adjoint:
+            tape = L.Tape(sim, args.case_adjoint)
+            g = tape.backward(lam_v=np.ones(sim.shape(L.FIELD_V)))
+            print(f"case adjoint: {args.case_adjoint} steps, |grad v| max {np.abs(g['v']).max():.6g}")
         torch.cuda.synchronize()
         print(f"case: {args.case} steps, last dt {info.dt_used:.6g}, troubled {info.n_troubled}")
         return

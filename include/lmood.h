@@ -226,10 +226,17 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  *
  * lmood_tape_record: runs n_steps ordinary lmood_step calls on s (the forward pass, with the
  *   MOOD loop and the dt rule as configured) and records what the reverse pass needs: the dt
- *   and the final order mask of every step, and a checkpoint of the state every
- *   checkpoint_every steps (>= 1; 1 keeps every state). Device memory held by the tape:
- *   about ceil(n_steps / checkpoint_every) + checkpoint_every + 1 states plus n_steps
- *   (n_cells + 8 n_inst) bytes. last (may be NULL) gets the last step's report. If a step
+ *   and the final order mask of every step, and
+ *     checkpoint_every = 0 (store mode): every state and every step's corner packets, nodal
+ *       solver velocities and node moments; the reverse pass reads them in place (fastest).
+ *       Device memory: about n_steps + 1 states plus n_steps step products (a state is
+ *       (4 dim + dim^2 + 3) doubles per cell-or-node; the products (dim+1)(dim(dim+1)/2 + dim)
+ *       doubles per cell and dim + 1 + dim + dim(dim+1)/2 + (dim + dim^2)(dim + 1) per node);
+ *     checkpoint_every = C >= 1: a checkpoint of the state every C steps; the reverse pass
+ *       rebuilds each segment from its checkpoint and replays every step once more before its
+ *       reverse kernels. Device memory: about ceil(n_steps / C) + C + 1 states.
+ *   Both modes also hold n_steps (n_cells + 8 n_inst) bytes of masks and dts, and the adjoint
+ *   work arrays (about 5 states). last (may be NULL) gets the last step's report. If a step
  *   fails, its status is returned, no tape is made (*out = NULL), and the state has taken the
  *   steps before it. If s was just initialised (no step and no lmood_set since
  *   lmood_state_init), v_p at the start is the initial nodal solve of (v, F, mu) and the
@@ -242,16 +249,17 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  *   starts from a just-initialised state, grad_v, grad_F and grad_mu are the gradients with
  *   respect to the inputs of lmood_state_init and grad_vp is zero. Any output may be NULL.
  *   Pointers are device pointers when is_device != 0 (ordered on the mesh's stream), else
- *   host pointers (the call synchronises). The tape replays each step from its checkpoint on
+ *   host pointers (the call synchronises). In checkpoint mode the tape replays the steps on
  *   s's buffers and restores s's current state afterwards (fields X, VP, V, E, F, TAU, DT,
- *   ORDER; the diagnostic fields VSTAR, PKM, PKR are not kept). May be called repeatedly.
+ *   ORDER); in either mode the diagnostic fields VSTAR, PKM, PKR are not kept. Results are
+ *   bitwise the same in both modes and for every C. May be called repeatedly.
  * lmood_tape_replay: advances the state s2 (any state on a mesh of the same sizes, e.g. one
  *   initialised from perturbed data) by the first n_steps recorded steps, from its current
  *   fields, with the recorded orders and dt and no MOOD detection or dt rule: the smooth map
  *   whose gradient lmood_tape_backward computes. s2's next dt is then set by the usual rule,
  *   so it can go on with lmood_step. Synchronises once per step.
- * lmood_tape_info: out4[0] steps, [1] checkpoint interval, [2] 1 if the tape starts from a
- *   just-initialised state, [3] device bytes held.
+ * lmood_tape_info: out4[0] steps, [1] checkpoint interval (0: store mode), [2] 1 if the tape
+ *   starts from a just-initialised state, [3] device bytes held.
  * Destroy the tape before its state.
  */
 typedef struct lmood_tape_s *lmood_tape;

@@ -236,7 +236,9 @@ class Tape:
     """lmood_tape_record / backward / info / destroy: reverse-mode gradients of n steps of a
     state with each step's MOOD order mask and dt frozen at their recorded values."""
 
-    def __init__(self, state: State, n_steps: int, checkpoint_every: int = 1):
+    def __init__(self, state: State, n_steps: int, checkpoint_every: int = 0):
+        """checkpoint_every = 0 keeps every state and step product (no replay in backward);
+        C >= 1 keeps a checkpoint every C steps and replays."""
         self.state = state
         h = C.c_void_p()
         _check(lib().lmood_tape_record(state.h, n_steps, checkpoint_every, C.byref(h), C.byref(state.info)))
@@ -296,7 +298,7 @@ class Tape:
         self.close()
 
 
-def rollout(problem, n_steps: int, v0, mu, F0=None, checkpoint_every: int = 1, **params):
+def rollout(problem, n_steps: int, v0, mu, F0=None, checkpoint_every: int = 0, **params):
     """Differentiable rollout (torch.autograd.Function): the state after n_steps steps of the
     scheme on problem's mesh and material, started from the per-cell initial velocity v0
     [dim, n_cells], shear modulus mu [n_cells] and deformation gradient F0 [dim*dim, n_cells]

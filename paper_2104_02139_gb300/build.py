@@ -3,6 +3,7 @@ parallel) into paper_2104_02139_gb300/liblmood.so."""
 from __future__ import annotations
 
 import os
+import shlex
 import subprocess
 import sys
 
@@ -15,6 +16,8 @@ SOURCES = ["lmood_api.cu", "lmood_ops2.cu", "lmood_ops3.cu", "lmood_noalloc.cu",
            "lmood_adj3.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+# extra nvcc flags for tuning builds (e.g. LMOOD_NVCC_EXTRA="-DLMOOD_ADJ_PREDICT_MINB=3")
+EXTRA = shlex.split(os.environ.get("LMOOD_NVCC_EXTRA", ""))
 
 
 def _nvcc() -> str:
@@ -40,7 +43,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src in SOURCES:
         obj = os.path.join(OUT, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [nvcc, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *NVCC_FLAGS, *EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

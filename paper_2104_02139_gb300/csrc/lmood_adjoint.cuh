@@ -8,6 +8,8 @@
 #pragma once
 #include <math.h>
 
+#include "lmood_dev.cuh"
+
 #ifdef __CUDACC__
 #define LMOOD_HD __host__ __device__ __forceinline__
 #else
@@ -16,6 +18,24 @@
 
 namespace lmood {
 namespace adj {
+
+// J^{-1/3} and log J: on the device the forward kernels' own FP64 evaluations (rcbrt_j,
+// log_j: a few ulp, far fewer instructions than pow / log), on the host the C library's
+LMOOD_HD double adj_rcbrt(double J) {
+#ifdef __CUDA_ARCH__
+    return rcbrt_j(J);
+#else
+    return 1.0 / cbrt(J);
+#endif
+}
+
+LMOOD_HD double adj_log(double J) {
+#ifdef __CUDA_ARCH__
+    return log_j(J);
+#else
+    return log(J);
+#endif
+}
 
 template <int D> struct Sz {
     static constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + D * D;
@@ -89,8 +109,8 @@ template <int D> LMOOD_HD void mmt(const double *A, const double *B, double *C) 
 // Neo-Hookean stress T(F) (plane strain in 2D) and its product lamT -> (lamF, lam_mu, lam_kappa).
 // ---------------------------------------------------------------------------------------
 template <int D> LMOOD_HD void stress(const double *F, double mu, double kap, double *T) {
-    const double J = det<D>(F), lJ = log(J), invJ = 1.0 / J;
-    const double cj = mu * pow(J, -5.0 / 3.0);
+    const double J = det<D>(F), lJ = adj_log(J), rc = adj_rcbrt(J), Jm23 = rc * rc, invJ = Jm23 * rc;
+    const double cj = mu * invJ * Jm23;
     const double p = -0.5 * kap * (J - 1.0 + lJ * invJ);
     double B[D * D];
     mmt<D>(F, F, B);
@@ -101,16 +121,23 @@ template <int D> LMOOD_HD void stress(const double *F, double mu, double kap, do
         for (int j = 0; j < D; ++j) T[i * D + j] = cj * B[i * D + j] + (i == j ? diag : 0.0);
 }
 
+// T_out (may be NULL) receives T(F) itself, sharing the scalar functions of J.
 template <int D>
 LMOOD_HD void stress_vjp(const double *F, double mu, double kap, const double *lT, double *lF, double &lmu,
-                         double &lkap) {
-    const double J = det<D>(F), lJ = log(J), invJ = 1.0 / J;
-    const double J53 = pow(J, -5.0 / 3.0);
+                         double &lkap, double *T_out = nullptr) {
+    const double J = det<D>(F), lJ = adj_log(J), rc = adj_rcbrt(J), Jm23 = rc * rc, invJ = Jm23 * rc;
+    const double J53 = invJ * Jm23;
     const double cj = mu * J53;
     double B[D * D];
     mmt<D>(F, F, B);
     double tr = D == 2 ? 1.0 : 0.0;
     for (int i = 0; i < D; ++i) tr += B[i * D + i];
+    if (T_out) {
+        const double p = -0.5 * kap * (J - 1.0 + lJ * invJ);
+        const double diag = -p - cj * tr / 3.0;
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) T_out[i * D + j] = cj * B[i * D + j] + (i == j ? diag : 0.0);
+    }
     double lcj = 0.0, ldiag = 0.0, lB[D * D];
     for (int i = 0; i < D; ++i)
         for (int j = 0; j < D; ++j) {
@@ -142,14 +169,14 @@ LMOOD_HD void stress_vjp(const double *F, double mu, double kap, const double *l
 // impedance z = sqrt(rho (K + 4 mu / (3 J))), K = (kap/2)(J + (1 - log J)/J)
 template <int D> LMOOD_HD double impedance(const double *F, double rho, double mu, double kap) {
     const double J = det<D>(F), invJ = 1.0 / J;
-    const double K = 0.5 * kap * (J + (1.0 - log(J)) * invJ);
+    const double K = 0.5 * kap * (J + (1.0 - adj_log(J)) * invJ);
     return sqrt(rho * (K + (4.0 / 3.0) * mu * invJ));
 }
 
 template <int D>
 LMOOD_HD void impedance_vjp(const double *F, double rho, double mu, double kap, double lz, double *lF, double &lrho,
                             double &lmu, double &lkap) {
-    const double J = det<D>(F), invJ = 1.0 / J, lJ = log(J);
+    const double J = det<D>(F), invJ = 1.0 / J, lJ = adj_log(J);
     const double K = 0.5 * kap * (J + (1.0 - lJ) * invJ);
     const double inner = K + (4.0 / 3.0) * mu * invJ;
     const double z = sqrt(rho * inner);
@@ -439,82 +466,93 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
     }
 }
 
-// Product of predict_fw: (lM [NV][NS], lR [NV][D]) -> accumulates lxs [NV][D], lmom [NV][NMOM],
-// lvc [D], lFc [DD], lz, lmu, lkap.
-template <int D>
+// Product of predict_fw: (lM [NV][NS], lR [NV][D]) -> accumulates lxs [NV][D], lvc [D],
+// lFc [DD], lz, lmu, lkap, and stores the adjoints of the node moments through
+// mout(k, j, value) (every (k, j) exactly once; zero where the packets do not depend on them).
+template <int D, class MO>
 LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc, const double *Fc, double z, double mu,
                           double kap, double im, double dt, int ord, const double *lM_in, const double *lR, double *lxs,
-                          double *lmom, double *lvc, double *lFc, double &lz, double &lmu, double &lkap) {
+                          MO &&mout, double *lvc, double *lFc, double &lz, double &lmu, double &lkap) {
     using Q = Sz<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ, NM = Q::NMOM;
-    double V, N[NV * D], xcc[D], W[NV][NS], u[NV][D], nu[NV];
+    double V, N[NV * D], xcc[D];
     faces<D>(xs, V, N);
     for (int a = 0; a < D; ++a) {
         double s = 0.0;
         for (int k = 0; k < NV; ++k) s += xs[k * D + a];
         xcc[a] = s / NV;
     }
-    for (int f = 0; f < NV; ++f) {
-        double ss = 0.0;
-        for (int a = 0; a < D; ++a) {
-            u[f][a] = N[f * D + a] / D;
-            ss += u[f][a] * u[f][a];
+    // M_k = sum_{f != k} W_f, W_f = (z / |u_f|) u_f u_f^t, u_f = N_f / D
+    double Mo[NV * NS], inu[NV];  // inu = 1 / |u_f|
+    {
+        double W[NV][NS];
+        for (int f = 0; f < NV; ++f) {
+            double ss = 0.0;
+            for (int a = 0; a < D; ++a) ss += N[f * D + a] * N[f * D + a];
+            inu[f] = D / sqrt(ss);
+            const double w = z * inu[f] / (D * D);
+            for (int a = 0; a < D; ++a)
+                for (int b = a; b < D; ++b) W[f][sym<D>(a, b)] = w * N[f * D + a] * N[f * D + b];
         }
-        nu[f] = sqrt(ss);
-        for (int a = 0; a < D; ++a)
-            for (int b = a; b < D; ++b) W[f][sym<D>(a, b)] = z / nu[f] * u[f][a] * u[f][b];
+        for (int k = 0; k < NV; ++k)
+            for (int s2 = 0; s2 < NS; ++s2) {
+                double acc = 0.0;
+                for (int f = 0; f < NV; ++f)
+                    if (f != k) acc += W[f][s2];
+                Mo[k * NS + s2] = acc;
+            }
     }
-    double Mo[NV * NS];
-    for (int k = 0; k < NV; ++k)
-        for (int s = 0; s < NS; ++s) {
-            double acc = 0.0;
-            for (int f = 0; f < NV; ++f)
-                if (f != k) acc += W[f][s];
-            Mo[k * NS + s] = acc;
-        }
     auto Mfull = [&](int k, int a, int b) { return Mo[k * NS + sym<D>(a, b)]; };
     double lM[NV * NS], lN[NV * D] = {}, lxcc[D] = {};
     for (int i = 0; i < NV * NS; ++i) lM[i] = lM_in[i];
-    // R_k = M_k vst_k + (1/D) T_k N_k  (vst = vc, T = T(Fc) for ord 1)
-    auto packet_rhs_vjp = [&](int k, const double *vst, const double *T, double *lvst, double *lT) {
+    // R_k = M_k vst_k + (1/D) T_k N_k: the parts that do not need T_k (lvst, lM, lT)
+    auto packet_rhs_vjp = [&](int k, const double *vst, double *lvst, double *lT) {
         for (int a = 0; a < D; ++a) {
             const double l = lR[k * D + a];
             for (int b = 0; b < D; ++b) {
                 lvst[b] += Mfull(k, a, b) * l;
-                // d/dM_sym: entry (a,b) of the full matrix
                 lM[k * NS + sym<D>(a, b)] += l * vst[b];
                 lT[a * D + b] += l * N[k * D + b] / D;
-                lN[k * D + b] += l * T[a * D + b] / D;
             }
         }
     };
+    // ... and the part that does: lN_k += (1/D) T_k^t lR_k
+    auto packet_rhs_vjp_T = [&](int k, const double *T) {
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b) lN[k * D + b] += lR[k * D + a] * T[a * D + b] / D;
+    };
+    auto zero_moments = [&]() {
+        for (int k = 0; k < NV; ++k)
+            for (int j = 0; j < NM; ++j) mout(k, j, 0.0);
+    };
     if (ord == 1) {
         double T[DD], lT[DD] = {}, lF[DD] = {};
-        stress<D>(Fc, mu, kap, T);
         for (int k = 0; k < NV; ++k) {
             double lvst[D] = {};
-            packet_rhs_vjp(k, vc, T, lvst, lT);
+            packet_rhs_vjp(k, vc, lvst, lT);
             for (int a = 0; a < D; ++a) lvc[a] += lvst[a];
         }
-        stress_vjp<D>(Fc, mu, kap, lT, lF, lmu, lkap);
+        stress_vjp<D>(Fc, mu, kap, lT, lF, lmu, lkap, T);
+        for (int k = 0; k < NV; ++k) packet_rhs_vjp_T(k, T);
         for (int q = 0; q < DD; ++q) lFc[q] += lF[q];
+        zero_moments();
     } else {
         // ---- recompute the forward intermediates
-        double G[DD] = {}, r[NQ][D] = {}, qc[NQ], dk[NV][D], S1k[NV][D], wk[NV][D], nk[NV];
+        double G[DD] = {}, r[NQ][D] = {}, qc[NQ], dk[NV][D];
         for (int q = 0; q < NQ; ++q) qc[q] = q < D ? vc[q] : Fc[q - D];
         for (int k = 0; k < NV; ++k) {
-            nk[k] = mom(k, Q::M_N);
+            const double nk = mom(k, Q::M_N);
+            double S1[D], w[D];
             for (int a = 0; a < D; ++a) {
                 dk[k][a] = xs[k * D + a] - xcc[a];
-                S1k[k][a] = mom(k, Q::M_S1 + a);
-                wk[k][a] = S1k[k][a] + nk[k] * dk[k][a];
+                S1[a] = mom(k, Q::M_S1 + a);
+                w[a] = S1[a] + nk * dk[k][a];
             }
             for (int a = 0; a < D; ++a)
-                for (int b = 0; b < D; ++b)
-                    G[a * D + b] += mom(k, Q::M_S2 + sym<D>(a, b)) + S1k[k][a] * dk[k][b] + dk[k][a] * wk[k][b];
+                for (int b = 0; b < D; ++b) G[a * D + b] += mom(k, Q::M_S2 + sym<D>(a, b)) + S1[a] * dk[k][b] + dk[k][a] * w[b];
             for (int q = 0; q < NQ; ++q)
                 for (int a = 0; a < D; ++a)
-                    r[q][a] += mom(k, Q::M_T + q * D + a) + dk[k][a] * mom(k, Q::M_U + q) - wk[k][a] * qc[q];
+                    r[q][a] += mom(k, Q::M_T + q * D + a) + dk[k][a] * mom(k, Q::M_U + q) - w[a] * qc[q];
         }
         double tr = 0.0;
         for (int a = 0; a < D; ++a) tr += G[a * D + a];
@@ -528,23 +566,26 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
                 for (int b = 0; b < D; ++b) s += Gi[a * D + b] * r[q][b];
                 gs[q][a] = ok ? s : 0.0;
             }
-        double gv[DD], dFdt[DD], dvraw[D] = {}, Fh[NV][DD];
-        const double hv = -0.5 * dt * im / D;
-        for (int k = 0; k < NV; ++k) {
-            double T[DD];
+        auto Fh_of = [&](int k, double *Fh) {
             for (int q = 0; q < DD; ++q) {
                 double s = Fc[q];
                 for (int a = 0; a < D; ++a) s += gs[D + q][a] * dk[k][a];
-                Fh[k][q] = s;
+                Fh[q] = s;
             }
-            stress<D>(Fh[k], mu, kap, T);
+        };
+        double gv[DD], dFdt[DD], dvraw[D] = {};
+        const double hv = -0.5 * dt * im / D;
+        for (int k = 0; k < NV; ++k) {
+            double Fh[DD], T[DD];
+            Fh_of(k, Fh);
+            stress<D>(Fh, mu, kap, T);
             for (int i = 0; i < D; ++i)
                 for (int b = 0; b < D; ++b) dvraw[i] += T[i * D + b] * N[k * D + b];
         }
         for (int i = 0; i < D; ++i)
             for (int a = 0; a < D; ++a) gv[i * D + a] = gs[i][a];
         mm<D>(gv, Fc, dFdt);
-        // ---- reverse of pass 2
+        // ---- reverse of pass 2 (the corner predictor and packets)
         double lgs[NQ][D] = {}, ldk[NV][D] = {}, ldv[D] = {}, ldFdt[DD] = {}, lFh[NV][DD] = {};
         for (int k = 0; k < NV; ++k) {
             double vst[D], Fs[DD], T[DD], lvst[D] = {}, lT[DD] = {}, lFs[DD] = {};
@@ -553,10 +594,11 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
                 for (int a = 0; a < D; ++a) s += gs[i][a] * dk[k][a];
                 vst[i] = s + hv * dvraw[i];
             }
-            for (int q = 0; q < DD; ++q) Fs[q] = Fh[k][q] + 0.5 * dt * dFdt[q];
-            stress<D>(Fs, mu, kap, T);
-            packet_rhs_vjp(k, vst, T, lvst, lT);
-            stress_vjp<D>(Fs, mu, kap, lT, lFs, lmu, lkap);
+            Fh_of(k, Fs);
+            for (int q = 0; q < DD; ++q) Fs[q] += 0.5 * dt * dFdt[q];
+            packet_rhs_vjp(k, vst, lvst, lT);
+            stress_vjp<D>(Fs, mu, kap, lT, lFs, lmu, lkap, T);
+            packet_rhs_vjp_T(k, T);
             for (int q = 0; q < DD; ++q) {
                 lFh[k][q] += lFs[q];
                 ldFdt[q] += 0.5 * dt * lFs[q];
@@ -584,14 +626,13 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
         double lacc[D];
         for (int i = 0; i < D; ++i) lacc[i] = hv * ldv[i];
         for (int k = 0; k < NV; ++k) {
-            double T[DD], lT[DD], lF[DD] = {};
-            stress<D>(Fh[k], mu, kap, T);
+            double Fh[DD], T[DD], lT[DD], lF[DD] = {};
+            Fh_of(k, Fh);
             for (int i = 0; i < D; ++i)
-                for (int b = 0; b < D; ++b) {
-                    lT[i * D + b] = lacc[i] * N[k * D + b];
-                    lN[k * D + b] += lacc[i] * T[i * D + b];
-                }
-            stress_vjp<D>(Fh[k], mu, kap, lT, lF, lmu, lkap);
+                for (int b = 0; b < D; ++b) lT[i * D + b] = lacc[i] * N[k * D + b];
+            stress_vjp<D>(Fh, mu, kap, lT, lF, lmu, lkap, T);
+            for (int i = 0; i < D; ++i)
+                for (int b = 0; b < D; ++b) lN[k * D + b] += lacc[i] * T[i * D + b];
             for (int q = 0; q < DD; ++q) lFh[k][q] += lF[q];
         }
         // Fh_k = Fc + gsF dk
@@ -605,52 +646,73 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
             }
         // ---- least squares: gs = Gi r
         if (ok) {
-            double lr[NQ][D], lGi[DD] = {};
+            // gs_q = G^{-1} r_q, G symmetric: lr_q = G^{-1} lgs_q, lG = -sum_q lr_q gs_q^t
+            double lr[NQ][D], lG[DD] = {};
             for (int q = 0; q < NQ; ++q)
                 for (int a = 0; a < D; ++a) {
                     double s = 0.0;
-                    for (int b = 0; b < D; ++b) s += Gi[b * D + a] * lgs[q][b];
+                    for (int b = 0; b < D; ++b) s += Gi[a * D + b] * lgs[q][b];
                     lr[q][a] = s;
-                    for (int b = 0; b < D; ++b) lGi[a * D + b] += lgs[q][a] * r[q][b];
                 }
-            // Gi = G^{-1}: lG = -Gi^t lGi Gi^t
-            double t1[DD], lG[DD];
-            mtm<D>(Gi, lGi, t1);
-            mmt<D>(t1, Gi, lG);
-            for (int q = 0; q < DD; ++q) lG[q] = -lG[q];
+            for (int q = 0; q < NQ; ++q)
+                for (int a = 0; a < D; ++a)
+                    for (int b = 0; b < D; ++b) lG[a * D + b] -= lr[q][a] * gs[q][b];
+            // the -w_k q_c terms of r summed over k: lw_k += lwq (the same for every k), and
+            // lq_c -= lr_q . sum_k w_k
+            double lwq[D] = {}, wsum[D] = {};
+            for (int q = 0; q < NQ; ++q)
+                for (int a = 0; a < D; ++a) lwq[a] -= lr[q][a] * qc[q];
             for (int k = 0; k < NV; ++k) {
-                double lS1[D] = {}, lw[D] = {}, ln_ = 0.0;
+                const double nk = mom(k, Q::M_N);
+                double S1[D], w[D], lS1[D] = {}, lw[D] = {}, lS2[NS] = {}, ln_ = 0.0;
+                for (int a = 0; a < D; ++a) {
+                    S1[a] = mom(k, Q::M_S1 + a);
+                    w[a] = S1[a] + nk * dk[k][a];
+                }
                 // G += S2 + S1 d^t + d w^t
                 for (int a = 0; a < D; ++a)
                     for (int b = 0; b < D; ++b) {
                         const double l = lG[a * D + b];
-                        lmom[k * NM + Q::M_S2 + sym<D>(a, b)] += l;
+                        lS2[sym<D>(a, b)] += l;
                         lS1[a] += l * dk[k][b];
-                        ldk[k][b] += l * S1k[k][a];
-                        ldk[k][a] += l * wk[k][b];
+                        ldk[k][b] += l * S1[a];
+                        ldk[k][a] += l * w[b];
                         lw[b] += l * dk[k][a];
                     }
                 // r_q += T_q + d U_q - w q_c
-                for (int q = 0; q < NQ; ++q)
+                for (int q = 0; q < NQ; ++q) {
+                    const double Uq = mom(k, Q::M_U + q);
+                    double lU = 0.0;
                     for (int a = 0; a < D; ++a) {
                         const double l = lr[q][a];
-                        lmom[k * NM + Q::M_T + q * D + a] += l;
-                        ldk[k][a] += l * mom(k, Q::M_U + q);
-                        lmom[k * NM + Q::M_U + q] += l * dk[k][a];
-                        lw[a] -= l * qc[q];
-                        const double lq = -l * wk[k][a];
-                        if (q < D) lvc[q] += lq;
-                        else lFc[q - D] += lq;
+                        mout(k, Q::M_T + q * D + a, l);
+                        ldk[k][a] += l * Uq;
+                        lU += l * dk[k][a];
                     }
+                    mout(k, Q::M_U + q, lU);
+                }
+                for (int a = 0; a < D; ++a) {
+                    lw[a] += lwq[a];
+                    wsum[a] += w[a];
+                }
                 // w = S1 + n d
                 for (int a = 0; a < D; ++a) {
                     lS1[a] += lw[a];
-                    ldk[k][a] += nk[k] * lw[a];
+                    ldk[k][a] += nk * lw[a];
                     ln_ += lw[a] * dk[k][a];
                 }
-                for (int a = 0; a < D; ++a) lmom[k * NM + Q::M_S1 + a] += lS1[a];
-                lmom[k * NM + Q::M_N] += ln_;
+                for (int a = 0; a < D; ++a) mout(k, Q::M_S1 + a, lS1[a]);
+                for (int s2 = 0; s2 < NS; ++s2) mout(k, Q::M_S2 + s2, lS2[s2]);
+                mout(k, Q::M_N, ln_);
             }
+            for (int q = 0; q < NQ; ++q) {
+                double lq = 0.0;
+                for (int a = 0; a < D; ++a) lq -= lr[q][a] * wsum[a];
+                if (q < D) lvc[q] += lq;
+                else lFc[q - D] += lq;
+            }
+        } else {
+            zero_moments();
         }
         // d_k = xs_k - xcc
         for (int k = 0; k < NV; ++k)
@@ -661,23 +723,23 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
     }
     // ---- M_k = sum_{f != k} W_f;  W_f = (z / |u_f|) u_f u_f^t, u_f = N_f / D
     for (int f = 0; f < NV; ++f) {
-        double lW[NS] = {};
+        double lW[NS] = {}, u[D];
         for (int k = 0; k < NV; ++k)
             if (k != f)
-                for (int s = 0; s < NS; ++s) lW[s] += lM[k * NS + s];
+                for (int s2 = 0; s2 < NS; ++s2) lW[s2] += lM[k * NS + s2];
+        for (int a = 0; a < D; ++a) u[a] = N[f * D + a] * (1.0 / D);
         // full symmetric lW: stored entry s = (a <= b) used once
-        double uWu = 0.0, lWu[D] = {}, zl = 0.0;
+        double uWu = 0.0, lWu[D] = {};
         for (int a = 0; a < D; ++a)
             for (int b = a; b < D; ++b) {
                 const double l = lW[sym<D>(a, b)];
-                zl += l * u[f][a] * u[f][b];
-                uWu += l * u[f][a] * u[f][b];
-                lWu[a] += l * u[f][b];
-                lWu[b] += l * u[f][a];
+                uWu += l * u[a] * u[b];
+                lWu[a] += l * u[b];
+                lWu[b] += l * u[a];
             }
-        lz += zl / nu[f];
-        const double c1 = z / nu[f], c3 = z / (nu[f] * nu[f] * nu[f]);
-        for (int a = 0; a < D; ++a) lN[f * D + a] += (c1 * lWu[a] - c3 * uWu * u[f][a]) / D;
+        lz += uWu * inu[f];
+        const double c1 = z * inu[f], c3 = c1 * inu[f] * inu[f];
+        for (int a = 0; a < D; ++a) lN[f * D + a] += (c1 * lWu[a] - c3 * uWu * u[a]) * (1.0 / D);
     }
     // ---- geometry: N(xs), xcc = mean(xs)
     faces_vjp<D>(xs, 0.0, lN, lxs);
@@ -729,7 +791,8 @@ LMOOD_HD void update_fw(const double *xs0, const double *xs1, const double *vs, 
 }
 
 // Product of update_fw: (lv1, lF1, lz1) -> accumulates lxs0, lxs1, lvs, lvp0, lvp1 [NV][D],
-// lM [NV][NS], lR [NV][D], lv [D], lF [DD], lmu, lkap.
+// lM [NV][NS], lR [NV][D], lv [D], lF [DD], lmu, lkap. Recomputes only what the product
+// needs (F1 and the impedance term only where used; lz1 = 0 drops the impedance).
 template <int D>
 LMOOD_HD void update_vjp(const double *xs0, const double *xs1, const double *vs, const double *vp0, const double *vp1,
                          const double *M, const double *R, const double *v, const double *F, double m, double im,
@@ -738,19 +801,15 @@ LMOOD_HD void update_vjp(const double *xs0, const double *xs1, const double *vs,
                          double *lv, double *lF, double &lmu, double &lkap) {
     using Q = Sz<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS;
-    double v1[D], F1[DD], z1;
-    update_fw<D>(xs0, xs1, vs, vp0, vp1, M, R, v, F, m, im, mu, kap, dt, ord, v1, F1, z1);
+    (void)R;
+    (void)v;
     double V0, N0[NV * D], V1, N1[NV * D], lN0[NV * D] = {}, lN1[NV * D] = {}, lV0 = 0.0, lV1 = 0.0;
     faces<D>(xs0, V0, N0);
     faces<D>(xs1, V1, N1);
     double lF1[DD];
     for (int q = 0; q < DD; ++q) lF1[q] = lF1_in[q];
-    // z1 = Z(F1, m / V1)
-    double lrho = 0.0;
-    impedance_vjp<D>(F1, m / V1, mu, kap, lz1, lF1, lrho, lmu, lkap);
-    lV1 += lrho * (-m / (V1 * V1));
     if (ord != 1) {
-        double L0[DD], L1[DD], A[DD], Bm[DD], Ai[DD];
+        double L0[DD], L1[DD], A[DD], Bm[DD], Ai[DD], Rm[DD], F1[DD];
         velgrad<D>(vp0, N0, V0, L0);
         velgrad<D>(vp1, N1, V1, L1);
         for (int i = 0; i < D; ++i)
@@ -758,7 +817,14 @@ LMOOD_HD void update_vjp(const double *xs0, const double *xs1, const double *vs,
                 A[i * D + j] = (i == j ? 1.0 : 0.0) - 0.5 * dt * L1[i * D + j];
                 Bm[i * D + j] = (i == j ? 1.0 : 0.0) + 0.5 * dt * L0[i * D + j];
             }
+        mm<D>(Bm, F, Rm);
         inverse<D>(A, Ai);
+        mm<D>(Ai, Rm, F1);
+        if (lz1 != 0.0) {  // z1 = Z(F1, m / V1)
+            double lrho = 0.0;
+            impedance_vjp<D>(F1, m / V1, mu, kap, lz1, lF1, lrho, lmu, lkap);
+            lV1 += lrho * (-m / (V1 * V1));
+        }
         // F1 = Ai Rm, Rm = Bm F
         double lRm[DD], lA[DD], lBm[DD], t[DD], lL0[DD], lL1[DD];
         mtm<D>(Ai, lF1, lRm);       // lRm = Ai^t lF1
@@ -775,6 +841,13 @@ LMOOD_HD void update_vjp(const double *xs0, const double *xs1, const double *vs,
     } else {
         double Ls[DD], t[DD], lLs[DD];
         velgrad<D>(vs, N0, V0, Ls);
+        if (lz1 != 0.0) {
+            double LF[DD], F1[DD], lrho = 0.0;
+            mm<D>(Ls, F, LF);
+            for (int q = 0; q < DD; ++q) F1[q] = F[q] + dt * LF[q];
+            impedance_vjp<D>(F1, m / V1, mu, kap, lz1, lF1, lrho, lmu, lkap);
+            lV1 += lrho * (-m / (V1 * V1));
+        }
         mtm<D>(Ls, lF1, t);
         for (int q = 0; q < DD; ++q) lF[q] += lF1[q] + dt * t[q];
         mmt<D>(lF1, F, lLs);

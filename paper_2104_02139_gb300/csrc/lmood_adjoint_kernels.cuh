@@ -131,9 +131,13 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_nodes(Geo g, Fld f
 
 // ---------------------------------------------------------------------------------------
 // force_p0: the t^0 packets (every cell first order)
-template <int D> __global__ void __launch_bounds__(128) k_adj_predict(Geo g, Fld f, Prm prm, AdjBuf a, int force_p0) {
+#ifndef LMOOD_ADJ_PREDICT_MINB
+#define LMOOD_ADJ_PREDICT_MINB 1  // resident blocks of 128 asked of the compiler (2D)
+#endif
+template <int D>
+__global__ void __launch_bounds__(128, D == 2 ? LMOOD_ADJ_PREDICT_MINB : 1) k_adj_predict(Geo g, Fld f, Prm prm, AdjBuf a, int force_p0) {
     using Q = adj::Sz<D>;
-    constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NX = NV * D, NM = Q::NMOM;
+    constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NX = NV * D;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     const int N = g.N, Np = g.Np, NC = NV * N;
@@ -153,13 +157,12 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_predict(Geo g, Fld
     for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
     const double mu = f.mu[c], kap = kappa_of(prm, mu), dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
     const int ord = force_p0 ? 1 : f.order[c];
-    double lxs[NX] = {}, lmom[NV * NM] = {}, lvc[D] = {}, lF[DD] = {}, lz = 0.0, lmu = 0.0, lkap = 0.0;
-    adj::predict_vjp<D>(xs, mom, vc, Fc, f.z[c], mu, kap, f.im[c], dt, ord, lM, lR, lxs, lmom, lvc, lF, lz, lmu, lkap);
-    for (int k = 0; k < NV; ++k) {
-        const int cid = k * N + c;
-        for (int b = 0; b < D; ++b) a.cb[b * NC + cid] = lxs[k * D + b];
-        for (int j = 0; j < NM; ++j) a.cb[(D + j) * NC + cid] = lmom[k * NM + j];
-    }
+    double lxs[NX] = {}, lvc[D] = {}, lF[DD] = {}, lz = 0.0, lmu = 0.0, lkap = 0.0;
+    double *cbm = a.cb + (size_t)D * NC + c;  // moment adjoints of corner (k, c): cbm[j NC + k N]
+    adj::predict_vjp<D>(xs, mom, vc, Fc, f.z[c], mu, kap, f.im[c], dt, ord, lM, lR, lxs,
+                        [&](int k, int j, double v) { cbm[(size_t)j * NC + k * N] = v; }, lvc, lF, lz, lmu, lkap);
+    for (int k = 0; k < NV; ++k)
+        for (int b = 0; b < D; ++b) a.cb[b * NC + k * N + c] = lxs[k * D + b];
     for (int b = 0; b < D; ++b) a.lv0[b * N + c] += lvc[b];
     for (int q = 0; q < DD; ++q) a.lF0[q * N + c] += lF[q];
     a.lz0[c] = lz;

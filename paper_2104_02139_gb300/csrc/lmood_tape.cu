@@ -7,6 +7,8 @@
 // checkpoint by replaying the steps (the step kernels with the recorded dt and orders given,
 // no detection), then for each step from the last, the state t^n is loaded, the step replayed
 // once more (packets, v*_p, t^{n+1} in the state's buffers) and the reverse kernels run.
+// Store mode (C = 0): every state and every step's products (corner packets, v*_p, node
+// moments) are kept, and the reverse kernels read them in place: no replay, no copies.
 #include <algorithm>
 #include <string>
 
@@ -18,8 +20,9 @@ using namespace lmood;
 struct lmood_tape_s {
     lmood_state s = nullptr;
     const AdjOps *aop = nullptr;
-    int64_t n = 0, C = 1, n_ck = 0, bytes = 0;
-    bool at_init = false;
+    int64_t n = 0, C = 1, n_ck = 0, bytes = 0, pd = 0;
+    bool at_init = false, store = false;
+    double *prod = nullptr;         // store mode: [n] products of each step (pkM, pkR, v*, moments)
     double *dts = nullptr;          // [n][n_inst]
     unsigned char *masks = nullptr; // [n][N]
     double *ck = nullptr;           // [n_ck] snapshots of the states at steps 0, C, 2C, ...
@@ -56,6 +59,25 @@ Snap snap_at(double *base, int D, int64_t N, int64_t Np) {
 Snap cur_of(const Fld &f) { return Snap{f.x, f.vp, f.v, f.F, f.e, f.z, f.rho, f.xc}; }
 Snap next_of(const Fld &f) { return Snap{f.x1, f.vp1, f.v1, f.F1, f.e1, f.z1, f.rho1, f.xc1}; }
 
+// the products of one step the reverse kernels read, one contiguous block
+struct Prod {
+    double *pkM, *pkR, *vs, *mom;
+};
+
+int64_t prod_doubles(int D, int nmom, int64_t N, int64_t Np) {
+    return (int64_t)(D * (D + 1) / 2 + D) * (D + 1) * N + (int64_t)(D + nmom) * Np;
+}
+
+Prod prod_at(double *base, int D, int64_t N, int64_t Np) {
+    const int64_t NC = (int64_t)(D + 1) * N;
+    Prod q;
+    q.pkM = base;
+    q.pkR = q.pkM + (int64_t)D * (D + 1) / 2 * NC;
+    q.vs = q.pkR + D * NC;
+    q.mom = q.vs + D * Np;
+    return q;
+}
+
 cudaError_t copy_snap(const Snap &dst, const Snap &src, int D, int64_t N, int64_t Np, cudaStream_t st) {
     const size_t nd = sizeof(double);
     const std::pair<double *, const double *> ps[8] = {{dst.x, src.x}, {dst.vp, src.vp}, {dst.v, src.v},
@@ -90,11 +112,11 @@ lmood_status replay_step(lmood_tape t, int64_t j, lmood_state s) {
     return LMOOD_OK;
 }
 
-void reverse_step(lmood_tape t, AdjBuf &a) {
+// the reverse kernels of one step, reading t^n, t^{n+1} and the step's products through f
+void reverse_step(lmood_tape t, AdjBuf &a, const Fld &f) {
     lmood_state s = t->s;
     lmood_mesh M = s->M;
     const AdjOps &ao = *t->aop;
-    const Fld &f = s->f;
     cudaStream_t st = M->st;
     Prm kr = s->kp;
     kr.base_order = 0;
@@ -140,8 +162,8 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     *out = nullptr;
     if (!s) return fail(LMOOD_ERR_ARG, "lmood_tape_record: NULL state");
     if (s->broken) return fail(LMOOD_ERR_STATE, "lmood_tape_record: state unusable after an earlier CUDA error");
-    if (n_steps < 1 || checkpoint_every < 1)
-        return fail(LMOOD_ERR_ARG, "lmood_tape_record: n_steps and checkpoint_every must be >= 1");
+    if (n_steps < 1 || checkpoint_every < 0)
+        return fail(LMOOD_ERR_ARG, "lmood_tape_record: n_steps must be >= 1 and checkpoint_every >= 0");
     lmood_mesh M = s->M;
     const int D = M->dim, NV = D + 1, NS = D * (D + 1) / 2, DD = D * D;
     const int64_t N = M->nc, Np = M->np, NC = NV * N;
@@ -150,10 +172,12 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     t->s = s;
     t->aop = D == 2 ? &adj_ops_dim2() : &adj_ops_dim3();
     t->n = n_steps;
-    t->C = std::min(checkpoint_every, n_steps);
-    t->n_ck = (n_steps + t->C - 1) / t->C;
+    t->store = checkpoint_every == 0;
+    t->C = t->store ? 1 : std::min(checkpoint_every, n_steps);
+    t->n_ck = t->store ? n_steps + 1 : (n_steps + t->C - 1) / t->C;
     t->at_init = s->at_init;
     const int64_t sd = snap_doubles(D, N, Np);
+    t->pd = prod_doubles(D, nmom, N, Np);
     const size_t nd = sizeof(double);
     lmood_status r = LMOOD_OK;
     auto A = [&](void **p, size_t bytes) {
@@ -165,8 +189,12 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     A((void **)&t->dts, n_steps * M->n_inst * nd);
     A((void **)&t->masks, (size_t)(n_steps * N));
     A((void **)&t->ck, t->n_ck * sd * nd);
-    A((void **)&t->seg, (t->C - 1) * sd * nd);
-    A((void **)&t->tmp, sd * nd);
+    if (t->store) {
+        A((void **)&t->prod, n_steps * t->pd * nd);
+    } else {
+        A((void **)&t->seg, (t->C - 1) * sd * nd);
+        A((void **)&t->tmp, sd * nd);
+    }
     A((void **)&t->tmp_dt, M->n_inst * nd);
     A((void **)&t->tmp_order, (size_t)N);
     AdjBuf &a = t->a;
@@ -213,6 +241,21 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
                                            " used the limited (Barth-Jespersen) level, which has no adjoint");
         }
         e = cudaMemcpyAsync(t->masks + j * N, f.order, N, cudaMemcpyDeviceToDevice, st);
+        if (t->store && e == cudaSuccess) {
+            const Prod q = prod_at(t->prod + j * t->pd, D, N, Np);
+            const std::pair<double *, const double *> cp[4] = {{q.pkM, f.pkM}, {q.pkR, f.pkR}, {q.vs, f.vs},
+                                                               {q.mom, f.mom}};
+            const int64_t len[4] = {NS * NC, D * NC, D * Np, nmom * Np};
+            for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+                e = cudaMemcpyAsync(cp[i].first, cp[i].second, len[i] * nd, cudaMemcpyDeviceToDevice, st);
+        }
+        if (e != cudaSuccess) {
+            tape_free(t);
+            return fail(LMOOD_ERR_CUDA, std::string("lmood_tape_record: ") + cudaGetErrorString(e));
+        }
+    }
+    if (t->store) {  // the final state, t^{n+1} of the last step
+        cudaError_t e = copy_snap(snap_at(t->ck + n_steps * sd, D, N, Np), cur_of(f), D, N, Np, st);
         if (e != cudaSuccess) {
             tape_free(t);
             return fail(LMOOD_ERR_CUDA, std::string("lmood_tape_record: ") + cudaGetErrorString(e));
@@ -241,11 +284,12 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
     Fld &f = s->f;
     const Ops &op = *M->ops;
     const AdjOps &ao = *t->aop;
-    // keep the state's current fields
-    const Snap tmp = snap_at(t->tmp, D, N, Np);
-    LM_CUDA(copy_snap(tmp, cur_of(f), D, N, Np, st));
-    LM_CUDA(cudaMemcpyAsync(t->tmp_dt, f.dt, M->n_inst * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    LM_CUDA(cudaMemcpyAsync(t->tmp_order, f.order, N, cudaMemcpyDeviceToDevice, st));
+    const Snap tmp = t->store ? Snap{} : snap_at(t->tmp, D, N, Np);
+    if (!t->store) {  // keep the state's current fields (the replays run on its buffers)
+        LM_CUDA(copy_snap(tmp, cur_of(f), D, N, Np, st));
+        LM_CUDA(cudaMemcpyAsync(t->tmp_dt, f.dt, M->n_inst * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        LM_CUDA(cudaMemcpyAsync(t->tmp_order, f.order, N, cudaMemcpyDeviceToDevice, st));
+    }
     // adjoints of the final state
     AdjBuf a = t->a;
     lmood_status r;
@@ -254,7 +298,32 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
         return r;
     LM_CUDA(cudaMemsetAsync(a.lmu, 0, N * sizeof(double), st));
     const Snap cur = cur_of(f), nxt = next_of(f);
-    for (int64_t k = t->n_ck - 1; k >= 0; --k) {
+    // store mode: a view of step j's recorded data (state fields not read stay the state's own)
+    auto stored = [&](int64_t j) {
+        Fld fr = f;
+        const Snap s0 = snap_at(t->ck + j * sd, D, N, Np), s1 = snap_at(t->ck + (j + 1) * sd, D, N, Np);
+        const Prod q = prod_at(t->prod + j * t->pd, D, N, Np);
+        fr.x = s0.x;
+        fr.vp = s0.vp;
+        fr.v = s0.v;
+        fr.F = s0.F;
+        fr.e = s0.e;
+        fr.z = s0.z;
+        fr.rho = s0.rho;
+        fr.xc = s0.xc;
+        fr.x1 = s1.x;
+        fr.vp1 = s1.vp;
+        fr.pkM = q.pkM;
+        fr.pkR = q.pkR;
+        fr.vs = q.vs;
+        fr.mom = q.mom;
+        fr.dt = t->dts + j * M->n_inst;
+        fr.order = t->masks + j * N;
+        return fr;
+    };
+    if (t->store)
+        for (int64_t j = t->n - 1; j >= 0; --j) reverse_step(t, a, stored(j));
+    for (int64_t k = t->store ? -1 : t->n_ck - 1; k >= 0; --k) {
         const int64_t b = k * t->C, len = std::min(t->C, t->n - b);
         const Snap ck = snap_at(t->ck + k * sd, D, N, Np);
         LM_CUDA(copy_snap(cur, ck, D, N, Np, st));
@@ -266,20 +335,29 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
         for (int64_t i = len - 1; i >= 0; --i) {
             if (i < len - 1) LM_CUDA(copy_snap(cur, i == 0 ? ck : snap_at(t->seg + (i - 1) * sd, D, N, Np), D, N, Np, st));
             if ((r = replay_step(t, b + i, s))) return r;
-            reverse_step(t, a);
+            reverse_step(t, a, f);
         }
     }
     if (t->at_init) {
-        // v_p^0 = v* of the first-order packets of the initial state (the state's buffers hold t^0)
+        // v_p^0 = v* of the first-order packets of the initial state: the packets are rebuilt
+        // into the state's packet buffers (replay mode: the state's buffers hold t^0; store
+        // mode: t^0 is read from the tape, the orders written to a scratch array)
+        Fld f0 = f;
+        if (t->store) {
+            f0 = stored(0);
+            f0.pkM = f.pkM;
+            f0.pkR = f.pkR;
+            f0.order = t->tmp_order;
+        }
         Prm p0 = s->kp;
         p0.base_order = 1;
-        op.predict(M->geo, f, p0, nullptr, nullptr, (int)N, st);
+        op.predict(M->geo, f0, p0, nullptr, nullptr, (int)N, st);
         AdjBuf ai = a;
         ai.lv0 = a.lv1;
         ai.lF0 = a.lF1;
-        ao.nodes(M->geo, f, ai, 1, st);
-        ao.predict(M->geo, f, p0, ai, 1, st);
-        ao.z0(M->geo, f, p0, ai, st);
+        ao.nodes(M->geo, f0, ai, 1, st);
+        ao.predict(M->geo, f0, p0, ai, 1, st);
+        ao.z0(M->geo, f0, p0, ai, st);
         LM_CUDA(cudaMemsetAsync(a.lvp1, 0, D * Np * sizeof(double), st));
     }
     cudaError_t le = cudaGetLastError();
@@ -291,11 +369,12 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
         (r = copy_out(grad_v, a.lv1, D * N, is_device, st)) || (r = copy_out(grad_F, a.lF1, D * D * N, is_device, st)) ||
         (r = copy_out(grad_mu, a.lmu, N, is_device, st)))
         return r;
-    // the state's current fields back
-    LM_CUDA(copy_snap(cur, tmp, D, N, Np, st));
-    LM_CUDA(cudaMemcpyAsync(const_cast<double *>(f.dt), t->tmp_dt, M->n_inst * sizeof(double), cudaMemcpyDeviceToDevice,
-                            st));
-    LM_CUDA(cudaMemcpyAsync(f.order, t->tmp_order, N, cudaMemcpyDeviceToDevice, st));
+    if (!t->store) {  // the state's current fields back
+        LM_CUDA(copy_snap(cur, tmp, D, N, Np, st));
+        LM_CUDA(cudaMemcpyAsync(const_cast<double *>(f.dt), t->tmp_dt, M->n_inst * sizeof(double),
+                                cudaMemcpyDeviceToDevice, st));
+        LM_CUDA(cudaMemcpyAsync(f.order, t->tmp_order, N, cudaMemcpyDeviceToDevice, st));
+    }
     if (!is_device) return sync_check(s, "lmood_tape_backward");
     return LMOOD_OK;
 }
@@ -330,7 +409,7 @@ extern "C" lmood_status lmood_tape_replay(lmood_tape t, lmood_state s2, int64_t 
 extern "C" lmood_status lmood_tape_info(lmood_tape t, int64_t *out4) {
     if (!t || !out4) return fail(LMOOD_ERR_ARG, "lmood_tape_info: NULL argument");
     out4[0] = t->n;
-    out4[1] = t->C;
+    out4[1] = t->store ? 0 : t->C;
     out4[2] = t->at_init ? 1 : 0;
     out4[3] = t->bytes;
     return LMOOD_OK;

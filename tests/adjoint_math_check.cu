@@ -261,8 +261,9 @@ template <int D> void check_predict(int ord) {
         for (int i = 0; i < NV * NS; ++i) fd += lM[i] * (Mp[i] - Mm[i]) / (2 * h);
         for (int i = 0; i < NV * D; ++i) fd += lR[i] * (Rp[i] - Rm[i]) / (2 * h);
         double lxs[NV * D] = {}, lmom[NV * NM] = {}, lvc[D] = {}, lF[DD] = {}, lz = 0, lmu = 0, lkap = 0;
-        predict_vjp<D>(P.xs, P.acc(P.mom), P.vc, P.Fc, P.z, P.mu, P.kap, P.im, P.dt, ord, lM, lR, lxs, lmom, lvc, lF,
-                       lz, lmu, lkap);
+        for (int i = 0; i < NV * NM; ++i) lmom[i] = 1e300;  // every entry must be stored exactly once
+        predict_vjp<D>(P.xs, P.acc(P.mom), P.vc, P.Fc, P.z, P.mu, P.kap, P.im, P.dt, ord, lM, lR, lxs,
+                       [&](int k, int j, double v) { lmom[k * NM + j] = v; }, lvc, lF, lz, lmu, lkap);
         double an = lz * dz + lmu * dmu + lkap * dk;
         for (int i = 0; i < NV * D; ++i) an += lxs[i] * dxs[i];
         for (int i = 0; i < NV * NM; ++i) an += lmom[i] * dmom[i];

@@ -88,7 +88,7 @@ def _fd(pb, n, prm, lam, masks, make, eps, pre=0, tape=None):
     return sum(float(((vals[0][k] - vals[1][k]) * lam[k]).sum()) for k in lam) / (2 * eps)
 
 
-def _grad(pb, n, prm, lam, pre=0, ckpt=1):
+def _grad(pb, n, prm, lam, pre=0, ckpt=0):
     st = L.simulation(pb, **prm)
     if pre:
         st.run(pre)
@@ -233,7 +233,7 @@ def test_checkpoint_interval_is_bitwise_invariant():
     prm = {"dt_fixed": _dt_fixed(pb)}
     n = 7
     ref = None
-    for C in (1, 2, 3, 7, 100):
+    for C in (0, 1, 2, 3, 7, 100):
         _, tape, g = _grad(pb, n, prm, lam, ckpt=C)
         assert tape.info()["checkpoint_every"] == min(C, n)
         if ref is None:
@@ -244,10 +244,15 @@ def test_checkpoint_interval_is_bitwise_invariant():
 
 
 def test_backward_restores_the_state_and_repeats():
+    for C in (0, 2):
+        _restore_case(C)
+
+
+def _restore_case(C):
     pb, lam, _ = _setup(W.plain2d(n=12), 19)
     st = L.simulation(pb)
     twin = L.simulation(pb)
-    tape = L.Tape(st, 4, 2)
+    tape = L.Tape(st, 4, C)
     twin.run(4)
     before = {f: st.get(f) for f in (L.FIELD_X, L.FIELD_VP, L.FIELD_V, L.FIELD_E, L.FIELD_F, L.FIELD_TAU,
                                       L.FIELD_DT, L.FIELD_ORDER)}
@@ -315,5 +320,5 @@ def test_tape_errors():
         L.Tape(st, 0)
     assert e.value.status == L.ERR_ARG
     with pytest.raises(L.LmoodError) as e:
-        L.Tape(st, 2, 0)
+        L.Tape(st, 2, -1)
     assert e.value.status == L.ERR_ARG
