@@ -8,17 +8,33 @@ namespace lmood {
 
 // Device buffers of the reverse pass. "1" = adjoint of the t^{n+1} state (input of the
 // reverse of step n), "0" = adjoint of the t^n state (its output); the host swaps the pairs
-// between steps. Corner arrays are [component][(D+1) N], corner id k N + c.
+// between steps. Cell and node adjoints of the state are structure-of-arrays ([comp][n]);
+// the records the reverse kernels pass to one another are arrays of structures (one
+// contiguous record per corner, cell or node), so that the node-side gathers read whole
+// sectors. Corner id k N + c.
+template <int D> struct AdjRec {
+    static constexpr int NS = D * (D + 1) / 2, NQ = D + D * D, NMOM = 1 + D + NS + NQ + NQ * D;
+    // corner record of the update and nodal solve: packet adjoints lM [NS], lR [D], then the
+    // update's products lvs, lx0, lx1, lvp0, lvp1 [D] each
+    static constexpr int CR = NS + D + 5 * D, CR_M = 0, CR_R = NS, CR_U = NS + D;
+    // corner record of the predictor: lxs [D], then the per-corner moment adjoints lU [NQ],
+    // lS1 [D], ln
+    static constexpr int CP = D + NQ + D + 1, CP_X = 0, CP_U = D, CP_S1 = D + NQ, CP_N = D + NQ + D;
+    // cell record of the predictor: the moment adjoints equal at all its corners, lT [NQ][D],
+    // lS2 [NS]
+    static constexpr int CC = NQ * D + NS, CC_T = 0, CC_S2 = NQ * D;
+};
+
 struct AdjBuf {
-    double *lv1, *lF1, *lv0, *lF0;  // cells: [D][N], [D*D][N]
-    double *lz0;                    // cells: adjoint of z^n (scratch of one step)
-    double *lmu;                    // cells: d/d mu, accumulated over the steps
+    double *lv1, *lF1, *lv0, *lF0;    // cells: [D][N], [D*D][N]
+    double *lz0;                      // cells: adjoint of z^n (scratch of one step)
+    double *lmu;                      // cells: d/d mu, accumulated over the steps
     double *lx1, *lvp1, *lx0, *lvp0;  // nodes: [D][Np]
-    double *pkM, *pkR;              // corners: packet adjoints [NS], [D]
-    double *ca;                     // corners: update products lvs, lx0, lx1, lvp0, lvp1 [5 D];
-                                    //          later the moment products lxc, lq [D + D + D*D]
-    double *cb;                     // corners: predictor products lxs [D], lmom [NMOM]
-    double *cd;                     // corners: centroid / measure products lx [D] (aliases pkM)
+    double *cr;                       // corner records of update and nodal solve [NC][CR]
+    double *cp;                       // corner records of the predictor [NC][CP]
+    double *cc;                       // cell records of the predictor [N][CC]
+    double *lm;                       // node moment adjoints [Np][NMOM] (aliases cr)
+    double *cd;                       // corner records of the cell gather: lx [NC][D]
 };
 
 struct AdjOps {
@@ -29,9 +45,9 @@ struct AdjOps {
     void (*nodes)(const Geo &, const Fld &, const AdjBuf &, int init_mode, cudaStream_t);
     // cells: reverse of geometry, least squares, predictor and packets (force_p0: all cells P0)
     void (*predict)(const Geo &, const Fld &, const Prm &, const AdjBuf &, int force_p0, cudaStream_t);
-    // nodes: reverse of the node moments
-    void (*moments)(const Geo &, const Fld &, const AdjBuf &, cudaStream_t);
-    // cells: gathers of the moment products, centroid and impedance of the t^n state
+    // nodes: adjoints of the node moments, summed over the corners around each node
+    void (*momsum)(const Geo &, const Fld &, const AdjBuf &, cudaStream_t);
+    // cells: reverse of the node moments (per corner of the cell), centroid and impedance of t^n
     void (*cells)(const Geo &, const Fld &, const Prm &, const AdjBuf &, cudaStream_t);
     // nodes: gather of the per-corner position adjoints
     void (*gather)(const Geo &, const AdjBuf &, cudaStream_t);

@@ -18,8 +18,9 @@ template <int D>
 void adj_predict(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, int force_p0, cudaStream_t s) {
     k_adj_predict<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a, force_p0);
 }
-template <int D> void adj_moments(const Geo &g, const Fld &f, const AdjBuf &a, cudaStream_t s) {
-    k_adj_moments<D><<<adj_blocks(g.Np, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, f, a);
+template <int D> void adj_momsum(const Geo &g, const Fld &f, const AdjBuf &a, cudaStream_t s) {
+    (void)f;
+    k_adj_momsum<D><<<adj_blocks(g.Np, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, a);
 }
 template <int D> void adj_cells(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, cudaStream_t s) {
     k_adj_cells<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
@@ -34,7 +35,7 @@ template <int D> void adj_z0(const Geo &g, const Fld &f, const Prm &p, const Adj
 }  // namespace
 
 #define LMOOD_ADJ_OPS_TABLE(D)                                                                              \
-    static const AdjOps table = {D, adj_update<D>, adj_nodes<D>, adj_predict<D>, adj_moments<D>, adj_cells<D>, \
+    static const AdjOps table = {D, adj_update<D>, adj_nodes<D>, adj_predict<D>, adj_momsum<D>, adj_cells<D>, \
                                  adj_gather<D>, adj_z0<D>};                                                  \
     return table;
 

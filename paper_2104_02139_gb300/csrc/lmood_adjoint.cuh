@@ -870,27 +870,28 @@ LMOOD_HD void update_vjp(const double *xs0, const double *xs1, const double *vs,
 }
 
 // Node moments: product for one corner (node p, cell c'): with dx = x_c' - x_p, accumulate
-// the adjoints of x_c' (lxc), of (v, F) of c' (lq [NQ]) and of x_p (lxp) from lmom [NMOM].
-template <int D>
-LMOOD_HD void moments_corner_vjp(const double *lmom, const double *xc, const double *xp, const double *q, double *lxc,
+// the adjoints of x_c' (lxc), of (v, F) of c' (lq [NQ]) and of x_p (lxp) from the adjoints of
+// node p's moments, read through lmom(j), j < NMOM.
+template <int D, class LM>
+LMOOD_HD void moments_corner_vjp(LM &&lmom, const double *xc, const double *xp, const double *q, double *lxc,
                                  double *lq, double *lxp) {
     using Q = Sz<D>;
     constexpr int NQ = Q::NQ;
     double dx[D], ldx[D];
     for (int a = 0; a < D; ++a) {
         dx[a] = xc[a] - xp[a];
-        ldx[a] = lmom[Q::M_S1 + a];
+        ldx[a] = lmom(Q::M_S1 + a);
     }
     for (int a = 0; a < D; ++a)
         for (int b = a; b < D; ++b) {
-            const double l = lmom[Q::M_S2 + sym<D>(a, b)];
+            const double l = lmom(Q::M_S2 + sym<D>(a, b));
             ldx[a] += l * dx[b];
             ldx[b] += l * dx[a];
         }
     for (int qi = 0; qi < NQ; ++qi) {
-        double lqq = lmom[Q::M_U + qi];
+        double lqq = lmom(Q::M_U + qi);
         for (int a = 0; a < D; ++a) {
-            const double l = lmom[Q::M_T + qi * D + a];
+            const double l = lmom(Q::M_T + qi * D + a);
             lqq += l * dx[a];
             ldx[a] += l * q[qi];
         }

@@ -1,19 +1,22 @@
 // lmood_adjoint_kernels.cuh -- kernels of the reverse pass of one step (adjoint with the
-// MOOD order mask and dt frozen), templated on the dimension. The forward step is first
-// replayed from the stored state t^n (same kernels, recorded mask and dt), so that the
-// packets, v*_p and the state t^{n+1} are in the state's buffers; then, with the adjoints of
-// the t^{n+1} state (lam x, lam v_p per node; lam v, lam F per cell; the impedance z of a
-// state is a function of its F and x, so its adjoint is applied where the state is read):
-//   k_adj_update   cells : product of the cell update -> packet adjoints and per-corner
-//                          contributions to the node adjoints
-//   k_adj_nodes    nodes : node motion and nodal solve with BCs -> packet adjoints
-//   k_adj_predict  cells : predictor, least squares, geometry -> node-moment adjoints
-//   k_adj_moments  nodes : node moments -> per-corner adjoints of the cells' x_c, v, F
-//   k_adj_cells    cells : gather of those, centroid and impedance of the t^n state
-//   k_adj_gather   nodes : node adjoints of t^n
-// The stored masses m_c stay fixed: the position adjoints are those of the map at fixed m.
+// MOOD order mask and dt frozen), templated on the dimension. They read the t^n state, the
+// t^{n+1} node positions and velocities and the step's products (corner packets, v*_p, node
+// moments) -- from the state's buffers after a replay of the step, or from a tape that kept
+// them -- and, with the adjoints of the t^{n+1} state (lam x, lam v_p per node; lam v, lam F
+// per cell; the impedance z of a state is a function of its F and x, so its adjoint is
+// applied where the state is read), produce those of t^n:
+//   k_adj_update   cells : reverse of the cell update -> corner records: packet adjoints and
+//                          the update's products for the node adjoints
+//   k_adj_nodes    nodes : reverse of node motion and nodal solve with BCs -> packet adjoints
+//   k_adj_predict  cells : reverse of predictor, least squares, geometry -> position adjoints
+//                          per corner, node-moment adjoints (per corner and per cell)
+//   k_adj_momsum   nodes : node-moment adjoints summed over the corners around each node
+//   k_adj_cells    cells : reverse of the node moments at the cell's corners, of the centroid
+//                          and of the impedance of t^n
+//   k_adj_gather   nodes : position adjoints of t^n
 // Contributions are written per corner (corner id k N + c, one writer each) and gathered
-// through the node -> corner CSR or the cell's own corners: no atomics, deterministic.
+// through the node -> corner CSR or the cell's own corners: no atomics, deterministic. The
+// stored masses m_c stay fixed: the position adjoints are those of the map at fixed m.
 #pragma once
 #include "lmood_adj_ops.h"
 #include "lmood_adjoint.cuh"
@@ -33,11 +36,12 @@ template <int D> __device__ __forceinline__ double kappa_mu_factor(const Prm &pr
 // ---------------------------------------------------------------------------------------
 template <int D> __global__ void __launch_bounds__(128) k_adj_update(Geo g, Fld f, Prm prm, AdjBuf a) {
     using Q = adj::Sz<D>;
+    using R = AdjRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NX = NV * D;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     const int N = g.N, Np = g.Np, NC = NV * N;
-    double xs0[NX], xs1[NX], vs[NX], vp0[NX], vp1[NX], M[NV * NS], R[NX], v[D], F[DD];
+    double xs0[NX], xs1[NX], vs[NX], vp0[NX], vp1[NX], M[NV * NS], v[D], F[DD];
     for (int k = 0; k < NV; ++k) {
         const int p = g.c2n[k * N + c];
         for (int b = 0; b < D; ++b) {
@@ -46,7 +50,6 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_update(Geo g, Fld 
             vs[k * D + b] = f.vs[b * Np + p];
             vp0[k * D + b] = f.vp[b * Np + p];
             vp1[k * D + b] = f.vp1[b * Np + p];
-            R[k * D + b] = f.pkR[b * NC + k * N + c];
         }
         for (int s = 0; s < NS; ++s) M[k * NS + s] = f.pkM[s * NC + k * N + c];
     }
@@ -59,18 +62,18 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_update(Geo g, Fld 
     const int ord = f.order[c];
     double l0[NX] = {}, l1[NX] = {}, lvs[NX] = {}, lp0[NX] = {}, lp1[NX] = {}, lM[NV * NS] = {}, lR[NX] = {},
            lv[D] = {}, lF[DD] = {}, lmu = 0.0, lkap = 0.0;
-    adj::update_vjp<D>(xs0, xs1, vs, vp0, vp1, M, R, v, F, f.m[c], f.im[c], mu, kap, dt, ord, lv1, lF1, 0.0, l0,
-                       l1, lvs, lp0, lp1, lM, lR, lv, lF, lmu, lkap);
+    adj::update_vjp<D>(xs0, xs1, vs, vp0, vp1, M, nullptr, v, F, f.m[c], f.im[c], mu, kap, dt, ord, lv1, lF1, 0.0,
+                       l0, l1, lvs, lp0, lp1, lM, lR, lv, lF, lmu, lkap);
     for (int k = 0; k < NV; ++k) {
-        const int cid = k * N + c;
-        for (int s = 0; s < NS; ++s) a.pkM[s * NC + cid] = lM[k * NS + s];
+        double *r = a.cr + (size_t)(k * N + c) * R::CR;
+        for (int s = 0; s < NS; ++s) r[R::CR_M + s] = lM[k * NS + s];
         for (int b = 0; b < D; ++b) {
-            a.pkR[b * NC + cid] = lR[k * D + b];
-            a.ca[(0 * D + b) * NC + cid] = lvs[k * D + b];
-            a.ca[(1 * D + b) * NC + cid] = l0[k * D + b];
-            a.ca[(2 * D + b) * NC + cid] = l1[k * D + b];
-            a.ca[(3 * D + b) * NC + cid] = lp0[k * D + b];
-            a.ca[(4 * D + b) * NC + cid] = lp1[k * D + b];
+            r[R::CR_R + b] = lR[k * D + b];
+            r[R::CR_U + 0 * D + b] = lvs[k * D + b];
+            r[R::CR_U + 1 * D + b] = l0[k * D + b];
+            r[R::CR_U + 2 * D + b] = l1[k * D + b];
+            r[R::CR_U + 3 * D + b] = lp0[k * D + b];
+            r[R::CR_U + 4 * D + b] = lp1[k * D + b];
         }
     }
     for (int b = 0; b < D; ++b) a.lv0[b * N + c] = lv[b];
@@ -81,7 +84,8 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_update(Geo g, Fld 
 // ---------------------------------------------------------------------------------------
 // init_mode: the t^0 nodal solve v_p^0 = v*_p (no motion); lam v*_p = lam v_p^0.
 template <int D> __global__ void __launch_bounds__(128) k_adj_nodes(Geo g, Fld f, AdjBuf a, int init_mode) {
-    constexpr int NV = adj::Sz<D>::NV;
+    using R = AdjRec<D>;
+    constexpr int NV = D + 1;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.Np) return;
     const int N = g.N, Np = g.Np, NC = NV * N;
@@ -91,14 +95,15 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_nodes(Geo g, Fld f
         const int cid = g.n2c[j];
         for (int r = 0; r < D; ++r)
             for (int s = 0; s < D; ++s) M[r * D + s] += f.pkM[adj::sym<D>(r, s) * NC + cid];
-        for (int r = 0; r < D; ++r) {
-            b[r] += f.pkR[r * NC + cid];
-            if (!init_mode) {
-                lvs[r] += a.ca[(0 * D + r) * NC + cid];
-                lx0[r] += a.ca[(1 * D + r) * NC + cid];
-                lx1[r] += a.ca[(2 * D + r) * NC + cid];
-                lvp0[r] += a.ca[(3 * D + r) * NC + cid];
-                lvp1[r] += a.ca[(4 * D + r) * NC + cid];
+        for (int r = 0; r < D; ++r) b[r] += f.pkR[r * NC + cid];
+        if (!init_mode) {
+            const double *rc = a.cr + (size_t)cid * R::CR + R::CR_U;
+            for (int r = 0; r < D; ++r) {
+                lvs[r] += rc[0 * D + r];
+                lx0[r] += rc[1 * D + r];
+                lx1[r] += rc[2 * D + r];
+                lvp0[r] += rc[3 * D + r];
+                lvp1[r] += rc[4 * D + r];
             }
         }
     }
@@ -118,13 +123,13 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_nodes(Geo g, Fld f
     }
     adj::node_solve_vjp<D>(M, b, g.bc_ndof[p], tv, lvs, lb, lM);
     for (int j = j0; j < j1; ++j) {
-        const int cid = g.n2c[j];
-        for (int r = 0; r < D; ++r) a.pkR[r * NC + cid] = (init_mode ? 0.0 : a.pkR[r * NC + cid]) + lb[r];
-        for (int r = 0; r < D; ++r)
-            for (int s = r; s < D; ++s) {
-                const double l = r == s ? lM[r * D + r] : lM[r * D + s] + lM[s * D + r];
-                const int sx = adj::sym<D>(r, s) * NC + cid;
-                a.pkM[sx] = (init_mode ? 0.0 : a.pkM[sx]) + l;
+        double *r = a.cr + (size_t)g.n2c[j] * R::CR;
+        for (int q = 0; q < D; ++q) r[R::CR_R + q] = (init_mode ? 0.0 : r[R::CR_R + q]) + lb[q];
+        for (int q = 0; q < D; ++q)
+            for (int s = q; s < D; ++s) {
+                const double l = q == s ? lM[q * D + q] : lM[q * D + s] + lM[s * D + q];
+                double &m = r[R::CR_M + adj::sym<D>(q, s)];
+                m = (init_mode ? 0.0 : m) + l;
             }
     }
 }
@@ -135,34 +140,51 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_nodes(Geo g, Fld f
 #define LMOOD_ADJ_PREDICT_MINB 1  // resident blocks of 128 asked of the compiler (2D)
 #endif
 template <int D>
-__global__ void __launch_bounds__(128, D == 2 ? LMOOD_ADJ_PREDICT_MINB : 1) k_adj_predict(Geo g, Fld f, Prm prm, AdjBuf a, int force_p0) {
+__global__ void __launch_bounds__(128, D == 2 ? LMOOD_ADJ_PREDICT_MINB : 1) k_adj_predict(Geo g, Fld f, Prm prm,
+                                                                                          AdjBuf a, int force_p0) {
     using Q = adj::Sz<D>;
+    using R = AdjRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NX = NV * D;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
-    const int N = g.N, Np = g.Np, NC = NV * N;
+    const int N = g.N, Np = g.Np;
     double xs[NX], vc[D], Fc[DD], lM[NV * NS], lR[NX];
     adj::Mom<D> mom;
     mom.stride = Np;
     for (int k = 0; k < NV; ++k) {
         const int p = g.c2n[k * N + c];
         mom.p[k] = f.mom + p;
-        for (int b = 0; b < D; ++b) {
-            xs[k * D + b] = f.x[b * Np + p];
-            lR[k * D + b] = a.pkR[b * NC + k * N + c];
-        }
-        for (int s = 0; s < NS; ++s) lM[k * NS + s] = a.pkM[s * NC + k * N + c];
+        for (int b = 0; b < D; ++b) xs[k * D + b] = f.x[b * Np + p];
+        const double *r = a.cr + (size_t)(k * N + c) * R::CR;
+        for (int b = 0; b < D; ++b) lR[k * D + b] = r[R::CR_R + b];
+        for (int s = 0; s < NS; ++s) lM[k * NS + s] = r[R::CR_M + s];
     }
     for (int b = 0; b < D; ++b) vc[b] = f.v[b * N + c];
     for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
     const double mu = f.mu[c], kap = kappa_of(prm, mu), dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
     const int ord = force_p0 ? 1 : f.order[c];
     double lxs[NX] = {}, lvc[D] = {}, lF[DD] = {}, lz = 0.0, lmu = 0.0, lkap = 0.0;
-    double *cbm = a.cb + (size_t)D * NC + c;  // moment adjoints of corner (k, c): cbm[j NC + k N]
-    adj::predict_vjp<D>(xs, mom, vc, Fc, f.z[c], mu, kap, f.im[c], dt, ord, lM, lR, lxs,
-                        [&](int k, int j, double v) { cbm[(size_t)j * NC + k * N] = v; }, lvc, lF, lz, lmu, lkap);
+    double *ccr = a.cc + (size_t)c * R::CC;
+    // node-moment adjoints: the parts equal at every corner (lT, lS2) into the cell record
+    // (stored once, at k = 0), the others into the corner records
+    auto mout = [&](int k, int j, double v) {
+        double *cpr = a.cp + (size_t)(k * N + c) * R::CP;
+        if (j >= Q::M_T) {
+            if (k == 0) ccr[R::CC_T + (j - Q::M_T)] = v;
+        } else if (j >= Q::M_U) {
+            cpr[R::CP_U + (j - Q::M_U)] = v;
+        } else if (j >= Q::M_S2) {
+            if (k == 0) ccr[R::CC_S2 + (j - Q::M_S2)] = v;
+        } else if (j >= Q::M_S1) {
+            cpr[R::CP_S1 + (j - Q::M_S1)] = v;
+        } else {
+            cpr[R::CP_N] = v;
+        }
+    };
+    adj::predict_vjp<D>(xs, mom, vc, Fc, f.z[c], mu, kap, f.im[c], dt, ord, lM, lR, lxs, mout, lvc, lF, lz, lmu,
+                        lkap);
     for (int k = 0; k < NV; ++k)
-        for (int b = 0; b < D; ++b) a.cb[b * NC + k * N + c] = lxs[k * D + b];
+        for (int b = 0; b < D; ++b) a.cp[(size_t)(k * N + c) * R::CP + R::CP_X + b] = lxs[k * D + b];
     for (int b = 0; b < D; ++b) a.lv0[b * N + c] += lvc[b];
     for (int q = 0; q < DD; ++q) a.lF0[q * N + c] += lF[q];
     a.lz0[c] = lz;
@@ -170,86 +192,82 @@ __global__ void __launch_bounds__(128, D == 2 ? LMOOD_ADJ_PREDICT_MINB : 1) k_ad
 }
 
 // ---------------------------------------------------------------------------------------
-template <int D> __global__ void __launch_bounds__(128) k_adj_moments(Geo g, Fld f, AdjBuf a) {
+// node-moment adjoints of node p: the corner parts of its corners and the cell parts of the
+// cells around it, in the corners' CSR order
+template <int D> __global__ void __launch_bounds__(128) k_adj_momsum(Geo g, AdjBuf a) {
     using Q = adj::Sz<D>;
-    constexpr int NV = Q::NV, NQ = Q::NQ, NM = Q::NMOM;
+    using R = AdjRec<D>;
+    constexpr int NQ = Q::NQ, NS = Q::NS, NM = Q::NMOM;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.Np) return;
-    const int N = g.N, Np = g.Np, NC = NV * N;
-    double lmom[NM] = {}, xp[D], lxp[D] = {};
-    const int j0 = g.n2c_off[p], j1 = g.n2c_off[p + 1];
-    for (int j = j0; j < j1; ++j) {
+    const int N = g.N;
+    double lm[NM];
+    for (int j = 0; j < NM; ++j) lm[j] = 0.0;
+    for (int j = g.n2c_off[p]; j < g.n2c_off[p + 1]; ++j) {
         const int cid = g.n2c[j];
-        for (int m = 0; m < NM; ++m) lmom[m] += a.cb[(D + m) * NC + cid];
+        const double *cp = a.cp + (size_t)cid * R::CP;
+        const double *cc = a.cc + (size_t)cell_of_corner<D>(cid, N) * R::CC;
+        lm[Q::M_N] += cp[R::CP_N];
+        for (int b = 0; b < D; ++b) lm[Q::M_S1 + b] += cp[R::CP_S1 + b];
+        for (int s = 0; s < NS; ++s) lm[Q::M_S2 + s] += cc[R::CC_S2 + s];
+        for (int q = 0; q < NQ; ++q) lm[Q::M_U + q] += cp[R::CP_U + q];
+        for (int i = 0; i < NQ * D; ++i) lm[Q::M_T + i] += cc[R::CC_T + i];
     }
-    for (int b = 0; b < D; ++b) xp[b] = f.x[b * Np + p];
-    for (int j = j0; j < j1; ++j) {
-        const int cid = g.n2c[j];
-        const int c = cell_of_corner<D>(cid, N);
-        double xc[D], q[NQ], lxc[D] = {}, lq[NQ] = {};
-        for (int b = 0; b < D; ++b) xc[b] = f.xc[b * N + c];
-        for (int i = 0; i < NQ; ++i) q[i] = i < D ? f.v[i * N + c] : f.F[(i - D) * N + c];
-        adj::moments_corner_vjp<D>(lmom, xc, xp, q, lxc, lq, lxp);
-        for (int b = 0; b < D; ++b) a.ca[b * NC + cid] = lxc[b];
-        for (int i = 0; i < NQ; ++i) a.ca[(D + i) * NC + cid] = lq[i];
-    }
-    for (int b = 0; b < D; ++b) a.lx0[b * Np + p] += lxp[b];
+    double *o = a.lm + (size_t)p * NM;
+    for (int j = 0; j < NM; ++j) o[j] = lm[j];
 }
 
 // ---------------------------------------------------------------------------------------
-// gather of the moment products at the cell; the centroid x_c = mean of its nodes; the
-// impedance z^n = Z(F^n, m / V(x^n), mu) (has_z: z^n was produced by the previous update or
-// by the initialisation from F^n and x^n)
+// per cell: the reverse of the node moments at its corners (the cell as a neighbour of each
+// of its nodes), of its centroid x_c = mean of its nodes, and of the impedance
+// z^n = Z(F^n, m / V(x^n), mu)
 template <int D> __global__ void __launch_bounds__(128) k_adj_cells(Geo g, Fld f, Prm prm, AdjBuf a) {
     using Q = adj::Sz<D>;
-    constexpr int NV = Q::NV, DD = Q::DD, NQ = Q::NQ, NX = NV * D;
+    constexpr int NV = Q::NV, DD = Q::DD, NQ = Q::NQ, NX = NV * D, NM = Q::NMOM;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
-    const int N = g.N, Np = g.Np, NC = NV * N;
-    double lxc[D] = {}, xs[NX];
+    const int N = g.N, Np = g.Np;
+    double xs[NX], xc[D], q[NQ], lxc[D] = {}, lq[NQ] = {}, lxp[NX] = {};
+    for (int b = 0; b < D; ++b) xc[b] = f.xc[b * N + c];
+    for (int i = 0; i < NQ; ++i) q[i] = i < D ? f.v[i * N + c] : f.F[(i - D) * N + c];
     for (int k = 0; k < NV; ++k) {
-        const int cid = k * N + c;
         const int p = g.c2n[k * N + c];
-        for (int b = 0; b < D; ++b) {
-            lxc[b] += a.ca[b * NC + cid];
-            xs[k * D + b] = f.x[b * Np + p];
-        }
-        for (int i = 0; i < NQ; ++i) {
-            const double l = a.ca[(D + i) * NC + cid];
-            if (i < D) a.lv0[i * N + c] += l;
-            else a.lF0[(i - D) * N + c] += l;
-        }
+        for (int b = 0; b < D; ++b) xs[k * D + b] = f.x[b * Np + p];
+        const double *lm = a.lm + (size_t)p * NM;
+        adj::moments_corner_vjp<D>([&](int j) { return lm[j]; }, xc, xs + k * D, q, lxc, lq, lxp + k * D);
     }
+    for (int b = 0; b < D; ++b) a.lv0[b * N + c] += lq[b];
     // z^n
     double F[DD], lF[DD] = {}, lrho = 0.0, lmu = 0.0, lkap = 0.0;
-    for (int q = 0; q < DD; ++q) F[q] = f.F[q * N + c];
+    for (int i = 0; i < DD; ++i) F[i] = q[D + i];
     double V, Nf[NX];
     adj::faces<D>(xs, V, Nf);
     const double mu = f.mu[c], kap = kappa_of(prm, mu);
     adj::impedance_vjp<D>(F, f.m[c] / V, mu, kap, a.lz0[c], lF, lrho, lmu, lkap);
-    for (int q = 0; q < DD; ++q) a.lF0[q * N + c] += lF[q];
+    for (int i = 0; i < DD; ++i) a.lF0[i * N + c] += lF[i] + lq[D + i];
     a.lmu[c] += lmu + lkap * kappa_mu_factor<D>(prm);
     const double lV = lrho * (-f.m[c] / (V * V));
     double lxs[NX] = {}, lN0[NX] = {};
     adj::faces_vjp<D>(xs, lV, lN0, lxs);
     for (int k = 0; k < NV; ++k)
-        for (int b = 0; b < D; ++b) a.cd[b * NC + k * N + c] = lxs[k * D + b] + lxc[b] / NV;
+        for (int b = 0; b < D; ++b)
+            a.cd[(size_t)(k * N + c) * D + b] = lxs[k * D + b] + lxc[b] * (1.0 / NV) + lxp[k * D + b];
 }
 
 template <int D> __global__ void __launch_bounds__(128) k_adj_gather(Geo g, AdjBuf a) {
-    constexpr int NV = D + 1;
+    using R = AdjRec<D>;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.Np) return;
-    const int NC = NV * g.N, Np = g.Np;
+    const int Np = g.Np;
     double l[D] = {};
     for (int j = g.n2c_off[p]; j < g.n2c_off[p + 1]; ++j) {
-        const int cid = g.n2c[j];
-        for (int b = 0; b < D; ++b) l[b] += a.cb[b * NC + cid] + a.cd[b * NC + cid];
+        const size_t cid = g.n2c[j];
+        for (int b = 0; b < D; ++b) l[b] += a.cp[cid * R::CP + R::CP_X + b] + a.cd[cid * D + b];
     }
     for (int b = 0; b < D; ++b) a.lx0[b * Np + p] += l[b];
 }
 
-// impedance of the initial state only (the t^0 packets' z): lmu from lz0
+// impedance of the initial state only (the t^0 packets' z): lmu and lF from lz0
 template <int D> __global__ void __launch_bounds__(128) k_adj_z0(Geo g, Fld f, Prm prm, AdjBuf a) {
     using Q = adj::Sz<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NX = NV * D;

@@ -124,7 +124,7 @@ void reverse_step(lmood_tape t, AdjBuf &a, const Fld &f) {
     ao.update(M->geo, f, kr, a, st);
     ao.nodes(M->geo, f, a, 0, st);
     ao.predict(M->geo, f, kr, a, 0, st);
-    ao.moments(M->geo, f, a, st);
+    ao.momsum(M->geo, f, a, st);
     ao.cells(M->geo, f, kr, a, st);
     ao.gather(M->geo, a, st);
     std::swap(a.lv0, a.lv1);
@@ -208,11 +208,13 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     A((void **)&a.lx0, D * Np * nd);
     A((void **)&a.lvp1, D * Np * nd);
     A((void **)&a.lvp0, D * Np * nd);
-    A((void **)&a.pkM, NS * NC * nd);
-    A((void **)&a.pkR, D * NC * nd);
-    A((void **)&a.ca, 5 * D * NC * nd);  // >= (D + D + D*D) NC: reused for the moment products
-    A((void **)&a.cb, (D + nmom) * NC * nd);
-    a.cd = a.pkM;  // NS >= D; written after the packets' adjoints are consumed
+    const int CR = NS + D + 5 * D, CP = D + (D + DD) + D + 1, CC = (D + DD) * D + NS;
+    A((void **)&a.cr, (size_t)CR * NC * nd);
+    A((void **)&a.cp, (size_t)CP * NC * nd);
+    A((void **)&a.cc, (size_t)CC * N * nd);
+    A((void **)&a.cd, (size_t)D * NC * nd);
+    if ((int64_t)nmom * Np <= (int64_t)CR * NC) a.lm = a.cr;  // written after the corner records are consumed
+    else A((void **)&a.lm, (size_t)nmom * Np * nd);          // (meshes with unreferenced nodes)
     if (r) {
         tape_free(t);
         return r;

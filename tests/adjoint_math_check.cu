@@ -384,7 +384,7 @@ template <int D> void check_moments() {
         double fd = 0.0;
         for (int j = 0; j < NM; ++j) fd += lmom[j] * (mp[j] - mm_[j]) / (2 * h);
         double lxc[D] = {}, lq[NQ] = {}, lxp[D] = {};
-        moments_corner_vjp<D>(lmom, xc, xp, q, lxc, lq, lxp);
+        moments_corner_vjp<D>([&](int j) { return lmom[j]; }, xc, xp, q, lxc, lq, lxp);
         double an = 0.0;
         for (int a = 0; a < D; ++a) an += lxc[a] * dxc[a] + lxp[a] * dxp[a];
         for (int i = 0; i < NQ; ++i) an += lq[i] * dq[i];
