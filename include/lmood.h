@@ -233,8 +233,9 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  *       (4 dim + dim^2 + 3) doubles per cell-or-node; the products (dim+1)(dim(dim+1)/2 + dim)
  *       doubles per cell and dim + 1 + dim + dim(dim+1)/2 + (dim + dim^2)(dim + 1) per node);
  *     checkpoint_every = C >= 1: a checkpoint of the state every C steps; the reverse pass
- *       rebuilds each segment from its checkpoint and replays every step once more before its
- *       reverse kernels. Device memory: about ceil(n_steps / C) + C + 1 states.
+ *       rebuilds each segment from its checkpoint (one replay of each step, keeping the
+ *       segment's states and products) and runs its reverse kernels on them. Device memory:
+ *       about ceil(n_steps / C) + C states plus C step products.
  *   Both modes also hold n_steps (n_cells + 8 n_inst) bytes of masks and dts, and the adjoint
  *   work arrays (about 5 states). last (may be NULL) gets the last step's report. If a step
  *   fails, its status is returned, no tape is made (*out = NULL), and the state has taken the
@@ -249,10 +250,9 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  *   starts from a just-initialised state, grad_v, grad_F and grad_mu are the gradients with
  *   respect to the inputs of lmood_state_init and grad_vp is zero. Any output may be NULL.
  *   Pointers are device pointers when is_device != 0 (ordered on the mesh's stream), else
- *   host pointers (the call synchronises). In checkpoint mode the tape replays the steps on
- *   s's buffers and restores s's current state afterwards (fields X, VP, V, E, F, TAU, DT,
- *   ORDER); in either mode the diagnostic fields VSTAR, PKM, PKR are not kept. Results are
- *   bitwise the same in both modes and for every C. May be called repeatedly.
+ *   host pointers (the call synchronises). s's fields are left as they are, except the
+ *   diagnostic fields PKM and PKR when the tape starts from a just-initialised state. Results
+ *   are bitwise the same in both modes and for every C. May be called repeatedly.
  * lmood_tape_replay: advances the state s2 (any state on a mesh of the same sizes, e.g. one
  *   initialised from perturbed data) by the first n_steps recorded steps, from its current
  *   fields, with the recorded orders and dt and no MOOD detection or dt rule: the smooth map

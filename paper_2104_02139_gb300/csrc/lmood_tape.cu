@@ -3,12 +3,13 @@
 //
 // Record: ordinary steps; before each, the dt it will use; after each, its final order mask;
 // every C steps, a checkpoint of the state (x, v_p, v, F, e, z, rho, x_c).
-// Reverse, per segment of C steps from the last: the segment's states are rebuilt from its
-// checkpoint by replaying the steps (the step kernels with the recorded dt and orders given,
-// no detection), then for each step from the last, the state t^n is loaded, the step replayed
-// once more (packets, v*_p, t^{n+1} in the state's buffers) and the reverse kernels run.
-// Store mode (C = 0): every state and every step's products (corner packets, v*_p, node
-// moments) are kept, and the reverse kernels read them in place: no replay, no copies.
+// Reverse, per segment of C steps from the last: the segment is rebuilt from its checkpoint by
+// replaying its steps (the step kernels with the recorded dt and orders given, no detection),
+// each replay writing the next state and the step's products (corner packets, v*_p, node
+// moments) straight into segment storage; then the reverse kernels of the segment's steps run,
+// last step first, reading that storage in place. Store mode (C = 0): the recording keeps
+// every state and every step's products, and the reverse kernels read them in place: no
+// replay. In both modes the state's own fields are left as they are.
 #include <algorithm>
 #include <string>
 
@@ -22,14 +23,14 @@ struct lmood_tape_s {
     const AdjOps *aop = nullptr;
     int64_t n = 0, C = 1, n_ck = 0, bytes = 0, pd = 0;
     bool at_init = false, store = false;
-    double *prod = nullptr;         // store mode: [n] products of each step (pkM, pkR, v*, moments)
+    double *prod = nullptr;         // store mode: [n] products of each step (pkM, pkR, v*, moments);
+                                    // checkpoint mode: [C] products of the segment's steps
     double *dts = nullptr;          // [n][n_inst]
     unsigned char *masks = nullptr; // [n][N]
     double *ck = nullptr;           // [n_ck] snapshots of the states at steps 0, C, 2C, ...
-    double *seg = nullptr;          // [C - 1] snapshots of a segment's inner states
-    double *tmp = nullptr;          // snapshot of the state's current fields during a reverse pass
-    double *tmp_dt = nullptr;       // [n_inst]
-    unsigned char *tmp_order = nullptr;  // [N]
+    double *seg = nullptr;          // checkpoint mode: [C] snapshots of a segment's states after
+                                    // its first (the first is its checkpoint)
+    unsigned char *tmp_order = nullptr;  // [N] scratch orders of the initial packets
     AdjBuf a{};
     DevAllocs mem;
 };
@@ -57,7 +58,6 @@ Snap snap_at(double *base, int D, int64_t N, int64_t Np) {
 }
 
 Snap cur_of(const Fld &f) { return Snap{f.x, f.vp, f.v, f.F, f.e, f.z, f.rho, f.xc}; }
-Snap next_of(const Fld &f) { return Snap{f.x1, f.vp1, f.v1, f.F1, f.e1, f.z1, f.rho1, f.xc1}; }
 
 // the products of one step the reverse kernels read, one contiguous block
 struct Prod {
@@ -110,6 +110,51 @@ lmood_status replay_step(lmood_tape t, int64_t j, lmood_state s) {
     op.nodes(M->geo, f, nullptr, nullptr, Np, 0, st);
     op.update(M->geo, f, kr, nullptr, nullptr, N, s->tl[0], f.cnt + CNT_T0, st);
     return LMOOD_OK;
+}
+
+// a view of the state's fields with t^n = cur, t^{n+1} = nxt, the step's products in q and
+// the recorded dt and orders of step j (fields outside these stay the state's own scratch)
+Fld view(lmood_tape t, const Fld &base, const Snap &cur, const Snap &nxt, const Prod &q, int64_t j) {
+    const lmood_mesh M = t->s->M;
+    Fld fr = base;
+    fr.x = cur.x;
+    fr.vp = cur.vp;
+    fr.v = cur.v;
+    fr.F = cur.F;
+    fr.e = cur.e;
+    fr.z = cur.z;
+    fr.rho = cur.rho;
+    fr.xc = cur.xc;
+    fr.x1 = nxt.x;
+    fr.vp1 = nxt.vp;
+    fr.v1 = nxt.v;
+    fr.F1 = nxt.F;
+    fr.e1 = nxt.e;
+    fr.z1 = nxt.z;
+    fr.rho1 = nxt.rho;
+    fr.xc1 = nxt.xc;
+    fr.pkM = q.pkM;
+    fr.pkR = q.pkR;
+    fr.vs = q.vs;
+    fr.mom = q.mom;
+    fr.dt = t->dts + j * M->n_inst;
+    fr.order = t->masks + j * M->nc;
+    return fr;
+}
+
+// the step kernels through a view (orders as recorded, no detection): t^n -> products, t^{n+1}
+void replay_view(lmood_tape t, const Fld &fr) {
+    lmood_state s = t->s;
+    lmood_mesh M = s->M;
+    const Ops &op = *M->ops;
+    cudaStream_t st = M->st;
+    Prm kr = s->kp;
+    kr.base_order = 0;
+    kr.mood = 0;
+    op.moments(M->geo, fr, st);
+    op.predict(M->geo, fr, kr, nullptr, nullptr, (int)M->nc, st);
+    op.nodes(M->geo, fr, nullptr, nullptr, (int)M->np, 0, st);
+    op.update(M->geo, fr, kr, nullptr, nullptr, (int)M->nc, s->tl[0], fr.cnt + CNT_T0, st);
 }
 
 // the reverse kernels of one step, reading t^n, t^{n+1} and the step's products through f
@@ -192,10 +237,9 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     if (t->store) {
         A((void **)&t->prod, n_steps * t->pd * nd);
     } else {
-        A((void **)&t->seg, (t->C - 1) * sd * nd);
-        A((void **)&t->tmp, sd * nd);
+        A((void **)&t->prod, t->C * t->pd * nd);
+        A((void **)&t->seg, t->C * sd * nd);
     }
-    A((void **)&t->tmp_dt, M->n_inst * nd);
     A((void **)&t->tmp_order, (size_t)N);
     AdjBuf &a = t->a;
     A((void **)&a.lv1, D * N * nd);
@@ -286,12 +330,6 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
     Fld &f = s->f;
     const Ops &op = *M->ops;
     const AdjOps &ao = *t->aop;
-    const Snap tmp = t->store ? Snap{} : snap_at(t->tmp, D, N, Np);
-    if (!t->store) {  // keep the state's current fields (the replays run on its buffers)
-        LM_CUDA(copy_snap(tmp, cur_of(f), D, N, Np, st));
-        LM_CUDA(cudaMemcpyAsync(t->tmp_dt, f.dt, M->n_inst * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        LM_CUDA(cudaMemcpyAsync(t->tmp_order, f.order, N, cudaMemcpyDeviceToDevice, st));
-    }
     // adjoints of the final state
     AdjBuf a = t->a;
     lmood_status r;
@@ -299,58 +337,29 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
         (r = copy_in(a.lv1, lam_v, D * N, is_device, st)) || (r = copy_in(a.lF1, lam_F, D * D * N, is_device, st)))
         return r;
     LM_CUDA(cudaMemsetAsync(a.lmu, 0, N * sizeof(double), st));
-    const Snap cur = cur_of(f), nxt = next_of(f);
-    // store mode: a view of step j's recorded data (state fields not read stay the state's own)
-    auto stored = [&](int64_t j) {
-        Fld fr = f;
-        const Snap s0 = snap_at(t->ck + j * sd, D, N, Np), s1 = snap_at(t->ck + (j + 1) * sd, D, N, Np);
-        const Prod q = prod_at(t->prod + j * t->pd, D, N, Np);
-        fr.x = s0.x;
-        fr.vp = s0.vp;
-        fr.v = s0.v;
-        fr.F = s0.F;
-        fr.e = s0.e;
-        fr.z = s0.z;
-        fr.rho = s0.rho;
-        fr.xc = s0.xc;
-        fr.x1 = s1.x;
-        fr.vp1 = s1.vp;
-        fr.pkM = q.pkM;
-        fr.pkR = q.pkR;
-        fr.vs = q.vs;
-        fr.mom = q.mom;
-        fr.dt = t->dts + j * M->n_inst;
-        fr.order = t->masks + j * N;
-        return fr;
-    };
-    if (t->store)
+    auto ck = [&](int64_t i) { return snap_at(t->ck + i * sd, D, N, Np); };
+    // store mode: step j reads states j, j+1 and products j of the tape
+    auto stored = [&](int64_t j) { return view(t, f, ck(j), ck(j + 1), prod_at(t->prod + j * t->pd, D, N, Np), j); };
+    if (t->store) {
         for (int64_t j = t->n - 1; j >= 0; --j) reverse_step(t, a, stored(j));
-    for (int64_t k = t->store ? -1 : t->n_ck - 1; k >= 0; --k) {
-        const int64_t b = k * t->C, len = std::min(t->C, t->n - b);
-        const Snap ck = snap_at(t->ck + k * sd, D, N, Np);
-        LM_CUDA(copy_snap(cur, ck, D, N, Np, st));
-        for (int64_t i = 0; i + 1 < len; ++i) {  // states b+1 .. b+len-1 into seg[0 ..]
-            if ((r = replay_step(t, b + i, s))) return r;
-            LM_CUDA(copy_snap(snap_at(t->seg + i * sd, D, N, Np), nxt, D, N, Np, st));
-            LM_CUDA(copy_snap(cur, nxt, D, N, Np, st));
-        }
-        for (int64_t i = len - 1; i >= 0; --i) {
-            if (i < len - 1) LM_CUDA(copy_snap(cur, i == 0 ? ck : snap_at(t->seg + (i - 1) * sd, D, N, Np), D, N, Np, st));
-            if ((r = replay_step(t, b + i, s))) return r;
-            reverse_step(t, a, f);
+    } else {
+        // the segment's states: S(0) = its checkpoint, S(i) = seg[i - 1]; products P(i) = prod[i]
+        for (int64_t k = t->n_ck - 1; k >= 0; --k) {
+            const int64_t b = k * t->C, len = std::min(t->C, t->n - b);
+            auto S = [&](int64_t i) { return i == 0 ? ck(k) : snap_at(t->seg + (i - 1) * sd, D, N, Np); };
+            auto P = [&](int64_t i) { return prod_at(t->prod + i * t->pd, D, N, Np); };
+            for (int64_t i = 0; i < len; ++i) replay_view(t, view(t, f, S(i), S(i + 1), P(i), b + i));
+            for (int64_t i = len - 1; i >= 0; --i) reverse_step(t, a, view(t, f, S(i), S(i + 1), P(i), b + i));
         }
     }
     if (t->at_init) {
-        // v_p^0 = v* of the first-order packets of the initial state: the packets are rebuilt
-        // into the state's packet buffers (replay mode: the state's buffers hold t^0; store
-        // mode: t^0 is read from the tape, the orders written to a scratch array)
-        Fld f0 = f;
-        if (t->store) {
-            f0 = stored(0);
-            f0.pkM = f.pkM;
-            f0.pkR = f.pkR;
-            f0.order = t->tmp_order;
-        }
+        // v_p^0 = v* of the first-order packets of the initial state (read from the tape's
+        // first checkpoint): the packets are rebuilt into the state's packet buffers, the
+        // orders into a scratch array
+        Fld f0 = view(t, f, ck(0), ck(0), prod_at(t->prod, D, N, Np), 0);
+        f0.pkM = f.pkM;
+        f0.pkR = f.pkR;
+        f0.order = t->tmp_order;
         Prm p0 = s->kp;
         p0.base_order = 1;
         op.predict(M->geo, f0, p0, nullptr, nullptr, (int)N, st);
@@ -371,12 +380,6 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
         (r = copy_out(grad_v, a.lv1, D * N, is_device, st)) || (r = copy_out(grad_F, a.lF1, D * D * N, is_device, st)) ||
         (r = copy_out(grad_mu, a.lmu, N, is_device, st)))
         return r;
-    if (!t->store) {  // the state's current fields back
-        LM_CUDA(copy_snap(cur, tmp, D, N, Np, st));
-        LM_CUDA(cudaMemcpyAsync(const_cast<double *>(f.dt), t->tmp_dt, M->n_inst * sizeof(double),
-                                cudaMemcpyDeviceToDevice, st));
-        LM_CUDA(cudaMemcpyAsync(f.order, t->tmp_order, N, cudaMemcpyDeviceToDevice, st));
-    }
     if (!is_device) return sync_check(s, "lmood_tape_backward");
     return LMOOD_OK;
 }
