@@ -80,6 +80,8 @@ def lib():
         L.orc_debug_corner_values.argtypes = [C.c_void_p, C.c_long, C.c_int, dp, dp, dp]
         L.orc_mesh_bc_ndof.argtypes = [C.c_void_p, C.c_long]
         L.orc_mesh_bc_ndof.restype = C.c_int
+        L.orc_mesh_set_bc_values.argtypes = [C.c_void_p, dp]
+        L.orc_mesh_set_btag.argtypes = [C.c_void_p, ip]
     return _lib
 
 
@@ -150,6 +152,9 @@ class Oracle:
                             C.byref(hm))
         if rc:
             raise OracleError(f"orc_mesh_new: {ERR.get(rc, rc)}")
+        bcval = getattr(problem, "bcval", None)
+        if bcval is not None:
+            L.orc_mesh_set_bc_values(hm, np.ascontiguousarray(bcval, dtype=np.float64).ravel())
         hs = C.c_void_p()
         mu = np.ascontiguousarray(problem.mu, dtype=np.float64)
         v = np.ascontiguousarray(problem.v, dtype=np.float64)
@@ -223,6 +228,18 @@ class Oracle:
 
     def bc_ndof(self, p: int) -> int:
         return lib().orc_mesh_bc_ndof(self._h.mesh, p)
+
+    def set_bc_values(self, values):
+        """boundary-face values [d][n_bfaces] (traction / pressure / prescribed velocity)"""
+        rc = lib().orc_mesh_set_bc_values(self._h.mesh, np.ascontiguousarray(values, dtype=np.float64).ravel())
+        if rc:
+            raise OracleError(f"orc_mesh_set_bc_values: {ERR.get(rc, rc)}")
+
+    def set_btag(self, btag):
+        """new boundary-face tags [n_bfaces]; per-node conditions re-derived"""
+        rc = lib().orc_mesh_set_btag(self._h.mesh, np.ascontiguousarray(btag, dtype=np.int32).ravel())
+        if rc:
+            raise OracleError(f"orc_mesh_set_btag: {ERR.get(rc, rc)}")
 
     def state(self) -> dict:
         return {"x": self.get(F_X), "vp": self.get(F_VP), "v": self.get(F_V), "e": self.get(F_E),

@@ -63,6 +63,14 @@
  *  R14 BCs: per node, clamped > slip > free; k independent slip planes leave the
  *      intersection subspace; the node velocity is the Galerkin solution of
  *      M_p v_p = b_p on that subspace (Eq. sBC1).
+ *  R15 traction, pressure and prescribed-velocity faces (Eqs. pBC, vBC1, vBC), with N_f
+ *      the face's outward area vector at x^n and each of its d nodes taking N_f / d:
+ *      a traction vector t_f adds |N_f| t_f / d to b_p, a pressure p_f adds -p_f N_f / d
+ *      (the external force on the node's share of the face); prescribed-velocity faces
+ *      give d_p = sum N_f / d and g_p = sum V_f . N_f / d, and v*_p = K b_p - T K d_p with
+ *      T = (K b_p . d_p - g_p) / (K d_p . d_p), K the solve of R14 (so v*_p . d_p = g_p;
+ *      skipped when K d_p . d_p = 0, e.g. at clamped nodes). Hierarchy: clamped >
+ *      prescribed velocity > slip > free; traction and pressure forces add at any node.
  */
 #include <math.h>
 #include <stdint.h>
@@ -101,6 +109,14 @@ typedef struct {
     int *bc_ndof;          /* per node: number of free velocity directions (d = free) */
     double *bc_t;          /* per node: [2][3] tangent vectors spanning the free space */
     double *x0;            /* [np][d] initial positions                                */
+    long nb;               /* boundary faces                                          */
+    int *bf_nodes;         /* [nb][d] face nodes, ordered so that the face's area vector
+                              points out of the mesh (reading R15)                     */
+    int *bf_tag;           /* [nb] 0 free, 1 slip, 2 clamped, 3 traction, 4 pressure,
+                              5 prescribed velocity                                     */
+    double *bf_val;        /* [nb][d] traction vector / pressure (first entry) /
+                              prescribed velocity vector; zero until set               */
+    long *nbf_off, *nbf_idx; /* boundary faces around each node, ascending face id     */
 } OrcMesh;
 
 typedef struct {
@@ -328,7 +344,96 @@ void orc_mesh_free(OrcMesh *M) {
     if (!M) return;
     free(M->c2n); free(M->n2c_off); free(M->n2c_cell); free(M->n2c_k);
     free(M->st_off); free(M->st_idx); free(M->bc_ndof); free(M->bc_t); free(M->x0);
+    free(M->bf_nodes); free(M->bf_tag); free(M->bf_val); free(M->nbf_off); free(M->nbf_idx);
     free(M);
+}
+
+/* area vector of boundary face b at positions x ([np][d]): 2D edge (q0, q1):
+ * (y1 - y0, x0 - x1); 3D triangle: (1/2) (x1 - x0) x (x2 - x0); its length is the face measure */
+static void face_area_vector(const OrcMesh *M, const double *x, long b, double *N) {
+    int d = M->d;
+    const int *q = M->bf_nodes + b * d;
+    if (d == 2) {
+        N[0] = x[q[1] * 2 + 1] - x[q[0] * 2 + 1];
+        N[1] = x[q[0] * 2 + 0] - x[q[1] * 2 + 0];
+    } else {
+        double u[3], w[3];
+        for (int a = 0; a < 3; ++a) {
+            u[a] = x[q[1] * 3 + a] - x[q[0] * 3 + a];
+            w[a] = x[q[2] * 3 + a] - x[q[0] * 3 + a];
+        }
+        N[0] = 0.5 * (u[1] * w[2] - u[2] * w[1]);
+        N[1] = 0.5 * (u[2] * w[0] - u[0] * w[2]);
+        N[2] = 0.5 * (u[0] * w[1] - u[1] * w[0]);
+    }
+}
+
+/* per-node boundary conditions from the face tags (Appendix B; hierarchy clamped > slip >
+ * free for the velocity subspace, reading R14; traction, pressure and prescribed velocity
+ * faces act in the nodal solve, reading R15) */
+static void resolve_bcs(OrcMesh *M) {
+    int d = M->d;
+    long np = M->np, nb = M->nb;
+    int *clamped = calloc(np, sizeof(int));
+    int *nplanes = calloc(np, sizeof(int));
+    double *planes = calloc(np * 9, sizeof(double));
+    memset(M->bc_t, 0, sizeof(double) * np * 6);
+    for (long b = 0; b < nb; ++b) {
+        const int *fn = M->bf_nodes + b * d;
+        double n[3] = {0, 0, 0};
+        face_area_vector(M, M->x0, b, n);
+        double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int a = 0; a < 3; ++a) n[a] /= nn;
+        for (int a = 0; a < d; ++a) {
+            int p = fn[a];
+            if (M->bf_tag[b] == 2) clamped[p] = 1;
+            if (M->bf_tag[b] == 1) {
+                int dup = 0;
+                for (int q = 0; q < nplanes[p]; ++q) {
+                    double dot = 0.0;
+                    for (int i = 0; i < 3; ++i) dot += planes[p * 9 + q * 3 + i] * n[i];
+                    if (fabs(dot) > 1.0 - 1e-12) dup = 1;
+                }
+                if (!dup && nplanes[p] < 3) {
+                    for (int i = 0; i < 3; ++i) planes[p * 9 + nplanes[p] * 3 + i] = n[i];
+                    nplanes[p]++;
+                }
+            }
+        }
+    }
+    for (long p = 0; p < np; ++p) {
+        double *t = M->bc_t + p * 6;
+        const double *n1 = planes + p * 9, *n2 = planes + p * 9 + 3;
+        int k = clamped[p] ? d : nplanes[p];
+        if (k >= d) {
+            M->bc_ndof[p] = 0;
+        } else if (k == 0) {
+            M->bc_ndof[p] = d;
+        } else if (d == 2) {
+            M->bc_ndof[p] = 1;
+            t[0] = -n1[1]; t[1] = n1[0];
+        } else if (k == 1) {
+            /* tangent basis of the plane: t1 = e x n normalised (e = axis least aligned with n), t2 = n x t1 */
+            int ax = 0;
+            for (int a = 1; a < 3; ++a)
+                if (fabs(n1[a]) < fabs(n1[ax])) ax = a;
+            double e[3] = {0, 0, 0};
+            e[ax] = 1.0;
+            double t1[3] = {e[1] * n1[2] - e[2] * n1[1], e[2] * n1[0] - e[0] * n1[2], e[0] * n1[1] - e[1] * n1[0]};
+            double l1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+            for (int a = 0; a < 3; ++a) t1[a] /= l1;
+            double t2[3] = {n1[1] * t1[2] - n1[2] * t1[1], n1[2] * t1[0] - n1[0] * t1[2], n1[0] * t1[1] - n1[1] * t1[0]};
+            double l2 = sqrt(t2[0] * t2[0] + t2[1] * t2[1] + t2[2] * t2[2]);
+            for (int a = 0; a < 3; ++a) { t[a] = t1[a]; t[3 + a] = t2[a] / l2; }
+            M->bc_ndof[p] = 2;
+        } else {
+            double l[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2], n1[0] * n2[1] - n1[1] * n2[0]};
+            double ll = sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+            for (int a = 0; a < 3; ++a) t[a] = l[a] / ll;
+            M->bc_ndof[p] = 1;
+        }
+    }
+    free(clamped); free(nplanes); free(planes);
 }
 
 /* x_soa [d][np], c2n_soa [d+1][nc], bf_soa [d][nb], btag [nb] (0 free, 1 slip, 2 clamped) */
@@ -395,84 +500,62 @@ int orc_mesh_new(int d, long np, const double *x_soa, long nc, const int *c2n_so
         }
         free(tmp);
     }
-    /* boundary conditions (Appendix B; hierarchy clamped > slip > free, reading R14) */
-    M->bc_ndof = malloc(sizeof(int) * np);
-    M->bc_t = calloc(np * 6, sizeof(double));
-    int *clamped = calloc(np, sizeof(int));
-    int *nplanes = calloc(np, sizeof(int));
-    double *planes = calloc(np * 9, sizeof(double));
+    /* boundary faces: nodes oriented outward (the face's area vector points away from the
+     * vertex of its cell that is not on the face), tags, values, node -> face CSR */
+    M->nb = nb;
+    M->bf_nodes = malloc(sizeof(int) * (nb > 0 ? nb : 1) * d);
+    M->bf_tag = malloc(sizeof(int) * (nb > 0 ? nb : 1));
+    M->bf_val = calloc((nb > 0 ? nb : 1) * d, sizeof(double));
     for (long b = 0; b < nb; ++b) {
-        int fn[MAXD];
+        int *fn = M->bf_nodes + b * d;
         for (int a = 0; a < d; ++a) {
             fn[a] = bf_soa[a * nb + b];
-            if (fn[a] < 0 || fn[a] >= np) { free(clamped); free(nplanes); free(planes); orc_mesh_free(M); return ORC_ERR_MESH; }
+            if (fn[a] < 0 || fn[a] >= np) { orc_mesh_free(M); return ORC_ERR_MESH; }
         }
-        double n[3] = {0, 0, 0};
-        if (d == 2) {
-            n[0] = M->x0[fn[1] * 2 + 1] - M->x0[fn[0] * 2 + 1];
-            n[1] = M->x0[fn[0] * 2 + 0] - M->x0[fn[1] * 2 + 0];
-        } else {
-            double u[3], w[3];
-            for (int a = 0; a < 3; ++a) {
-                u[a] = M->x0[fn[1] * 3 + a] - M->x0[fn[0] * 3 + a];
-                w[a] = M->x0[fn[2] * 3 + a] - M->x0[fn[0] * 3 + a];
+        if (btag[b] < 0 || btag[b] > 5) { orc_mesh_free(M); return ORC_ERR_ARG; }
+        M->bf_tag[b] = btag[b];
+        long owner = -1;
+        int opp = -1;
+        for (long j = M->n2c_off[fn[0]]; j < M->n2c_off[fn[0] + 1] && owner < 0; ++j) {
+            long c = M->n2c_cell[j];
+            int hits = 0, other = -1;
+            for (int k = 0; k < nv; ++k) {
+                int q = M->c2n[c * nv + k], on = 0;
+                for (int a = 0; a < d; ++a) on |= q == fn[a];
+                if (on) hits++;
+                else other = q;
             }
-            n[0] = u[1] * w[2] - u[2] * w[1];
-            n[1] = u[2] * w[0] - u[0] * w[2];
-            n[2] = u[0] * w[1] - u[1] * w[0];
+            if (hits == d) { owner = c; opp = other; }
         }
-        double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-        for (int a = 0; a < 3; ++a) n[a] /= nn;
+        if (owner < 0) { orc_mesh_free(M); return ORC_ERR_MESH; }
+        double N[3] = {0, 0, 0}, dot = 0.0;
+        face_area_vector(M, M->x0, b, N);
         for (int a = 0; a < d; ++a) {
-            int p = fn[a];
-            if (btag[b] == 2) clamped[p] = 1;
-            if (btag[b] == 1) {
-                int dup = 0;
-                for (int q = 0; q < nplanes[p]; ++q) {
-                    double dot = 0.0;
-                    for (int i = 0; i < 3; ++i) dot += planes[p * 9 + q * 3 + i] * n[i];
-                    if (fabs(dot) > 1.0 - 1e-12) dup = 1;
-                }
-                if (!dup && nplanes[p] < 3) {
-                    for (int i = 0; i < 3; ++i) planes[p * 9 + nplanes[p] * 3 + i] = n[i];
-                    nplanes[p]++;
-                }
-            }
+            double xf = 0.0;
+            for (int i = 0; i < d; ++i) xf += M->x0[fn[i] * d + a];
+            dot += N[a] * (xf / d - M->x0[opp * d + a]);
         }
+        if (dot < 0.0) { int tmp = fn[0]; fn[0] = fn[1]; fn[1] = tmp; }
+        double nn = 0.0;
+        face_area_vector(M, M->x0, b, N);
+        for (int a = 0; a < d; ++a) nn += N[a] * N[a];
+        if (!(nn > 0.0)) { orc_mesh_free(M); return ORC_ERR_MESH; }
     }
-    for (long p = 0; p < np; ++p) {
-        double *t = M->bc_t + p * 6;
-        const double *n1 = planes + p * 9, *n2 = planes + p * 9 + 3;
-        int k = clamped[p] ? d : nplanes[p];
-        if (k >= d) {
-            M->bc_ndof[p] = 0;
-        } else if (k == 0) {
-            M->bc_ndof[p] = d;
-        } else if (d == 2) {
-            M->bc_ndof[p] = 1;
-            t[0] = -n1[1]; t[1] = n1[0];
-        } else if (k == 1) {
-            /* tangent basis of the plane: t1 = e x n normalised (e = axis least aligned with n), t2 = n x t1 */
-            int ax = 0;
-            for (int a = 1; a < 3; ++a)
-                if (fabs(n1[a]) < fabs(n1[ax])) ax = a;
-            double e[3] = {0, 0, 0};
-            e[ax] = 1.0;
-            double t1[3] = {e[1] * n1[2] - e[2] * n1[1], e[2] * n1[0] - e[0] * n1[2], e[0] * n1[1] - e[1] * n1[0]};
-            double l1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
-            for (int a = 0; a < 3; ++a) t1[a] /= l1;
-            double t2[3] = {n1[1] * t1[2] - n1[2] * t1[1], n1[2] * t1[0] - n1[0] * t1[2], n1[0] * t1[1] - n1[1] * t1[0]};
-            double l2 = sqrt(t2[0] * t2[0] + t2[1] * t2[1] + t2[2] * t2[2]);
-            for (int a = 0; a < 3; ++a) { t[a] = t1[a]; t[3 + a] = t2[a] / l2; }
-            M->bc_ndof[p] = 2;
-        } else {
-            double l[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2], n1[0] * n2[1] - n1[1] * n2[0]};
-            double ll = sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
-            for (int a = 0; a < 3; ++a) t[a] = l[a] / ll;
-            M->bc_ndof[p] = 1;
-        }
+    M->nbf_off = calloc(np + 1, sizeof(long));
+    for (long b = 0; b < nb; ++b)
+        for (int a = 0; a < d; ++a) M->nbf_off[M->bf_nodes[b * d + a] + 1]++;
+    for (long p = 0; p < np; ++p) M->nbf_off[p + 1] += M->nbf_off[p];
+    M->nbf_idx = malloc(sizeof(long) * (nb > 0 ? nb * d : 1));
+    {
+        long *fill = malloc(sizeof(long) * np);
+        for (long p = 0; p < np; ++p) fill[p] = M->nbf_off[p];
+        for (long b = 0; b < nb; ++b)
+            for (int a = 0; a < d; ++a) M->nbf_idx[fill[M->bf_nodes[b * d + a]]++] = b;
+        free(fill);
     }
-    free(clamped); free(nplanes); free(planes);
+    M->bc_ndof = malloc(sizeof(int) * np);
+    M->bc_t = calloc(np * 6, sizeof(double));
+    resolve_bcs(M);
     *out = M;
     return ORC_OK;
 }
@@ -675,31 +758,26 @@ static void phase_packets(const OrcState *S, const int *order, double dt, Work *
     }
 }
 
-/* 4. nodal solver with BCs (Eqs. nodal_solver^n, sBC1; readings R6, R10, R14):
- *    M_p = sum_c M_cp, b_p = sum_c rhs_cp, v*_p = Galerkin solution on the free subspace,
- *    x^{n+1} = x^n + dt v*_p, v_p^{n+1} = 2 v*_p - v_p^n */
-static void node_solve_one(const OrcMesh *M, const double *pkM, const double *pkR, long p, double *vs) {
-    int d = M->d, nv = M->nv, dd = d * d;
-    double Mp[9] = {0}, bp[3] = {0, 0, 0};
-    for (long j = M->n2c_off[p]; j < M->n2c_off[p + 1]; ++j) {
-        long c = M->n2c_cell[j];
-        int k = M->n2c_k[j];
-        for (int i = 0; i < dd; ++i) Mp[i] += pkM[(c * nv + k) * dd + i];
-        for (int i = 0; i < d; ++i) bp[i] += pkR[(c * nv + k) * d + i];
-    }
+/* 4. nodal solver with BCs (Eqs. nodal_solver^n, sBC1, pBC, vBC1, vBC; readings R6, R10,
+ *    R14, R15): M_p = sum_c M_cp, b_p = sum_c rhs_cp + the forces of the traction and
+ *    pressure faces around p; v*_p = K b_p with K the Galerkin solve on the node's free
+ *    subspace; with prescribed-velocity faces around p, v*_p = K b_p - T_p K d_p with T_p
+ *    chosen so that v*_p . d_p = g_p; x^{n+1} = x^n + dt v*_p, v_p^{n+1} = 2 v*_p - v_p^n */
+static void solve_K(const OrcMesh *M, const double *Mp, long p, const double *rhs, double *out) {
+    int d = M->d;
     int nf = M->bc_ndof[p];
     if (nf == d) {
         double Mi[9];
         inv_n(d, Mp, Mi);
-        matvec_n(d, Mi, bp, vs);
+        matvec_n(d, Mi, rhs, out);
     } else if (nf == 0) {
-        for (int i = 0; i < d; ++i) vs[i] = 0.0;
+        for (int i = 0; i < d; ++i) out[i] = 0.0;
     } else {
         const double *t = M->bc_t + p * 6;
         double A[4], r[2], al[2];
         for (int i = 0; i < nf; ++i) {
             r[i] = 0.0;
-            for (int a = 0; a < d; ++a) r[i] += t[3 * i + a] * bp[a];
+            for (int a = 0; a < d; ++a) r[i] += t[3 * i + a] * rhs[a];
             for (int j = 0; j < nf; ++j) {
                 double Mtj[3], s = 0.0;
                 matvec_n(d, Mp, t + 3 * j, Mtj);
@@ -718,7 +796,58 @@ static void node_solve_one(const OrcMesh *M, const double *pkM, const double *pk
         for (int a = 0; a < d; ++a) {
             double s = 0.0;
             for (int i = 0; i < nf; ++i) s += al[i] * t[3 * i + a];
-            vs[a] = s;
+            out[a] = s;
+        }
+    }
+}
+
+static void node_solve_one(const OrcMesh *M, const double *x, const double *pkM, const double *pkR, long p,
+                           double *vs) {
+    int d = M->d, nv = M->nv, dd = d * d;
+    double Mp[9] = {0}, bp[3] = {0, 0, 0};
+    for (long j = M->n2c_off[p]; j < M->n2c_off[p + 1]; ++j) {
+        long c = M->n2c_cell[j];
+        int k = M->n2c_k[j];
+        for (int i = 0; i < dd; ++i) Mp[i] += pkM[(c * nv + k) * dd + i];
+        for (int i = 0; i < d; ++i) bp[i] += pkR[(c * nv + k) * d + i];
+    }
+    /* faces around p with a prescribed traction, pressure or normal velocity (reading R15) */
+    double dp[3] = {0, 0, 0}, gp = 0.0;
+    int nvel = 0;
+    for (long j = M->nbf_off[p]; j < M->nbf_off[p + 1]; ++j) {
+        long b = M->nbf_idx[j];
+        int tag = M->bf_tag[b];
+        if (tag < 3) continue;
+        double N[3] = {0, 0, 0};
+        face_area_vector(M, x, b, N);
+        const double *val = M->bf_val + b * d;
+        if (tag == 3) {
+            double area = 0.0;
+            for (int a = 0; a < d; ++a) area += N[a] * N[a];
+            area = sqrt(area);
+            for (int a = 0; a < d; ++a) bp[a] += area / d * val[a];
+        } else if (tag == 4) {
+            for (int a = 0; a < d; ++a) bp[a] -= val[0] * N[a] / d;
+        } else {
+            for (int a = 0; a < d; ++a) {
+                dp[a] += N[a] / d;
+                gp += val[a] * N[a] / d;
+            }
+            nvel++;
+        }
+    }
+    solve_K(M, Mp, p, bp, vs);
+    if (nvel > 0) {
+        double w[3];
+        solve_K(M, Mp, p, dp, w);
+        double wd = 0.0, vd = 0.0;
+        for (int a = 0; a < d; ++a) {
+            wd += w[a] * dp[a];
+            vd += vs[a] * dp[a];
+        }
+        if (wd > 0.0) {
+            double T = (vd - gp) / wd;
+            for (int a = 0; a < d; ++a) vs[a] -= T * w[a];
         }
     }
 }
@@ -728,7 +857,7 @@ static void phase_nodes(const OrcState *S, double dt, Work *w) {
     int d = M->d;
 #pragma omp parallel for schedule(static)
     for (long p = 0; p < M->np; ++p) {
-        node_solve_one(M, w->pkM, w->pkR, p, w->vs + p * d);
+        node_solve_one(M, S->x, w->pkM, w->pkR, p, w->vs + p * d);
         for (int a = 0; a < d; ++a) {
             w->x1[p * d + a] = S->x[p * d + a] + dt * w->vs[p * d + a];
             w->vp1[p * d + a] = 2.0 * w->vs[p * d + a] - S->vp[p * d + a];
@@ -997,7 +1126,7 @@ int orc_state_new(OrcMesh *M, double rho0, double lam, const double *mu_cell, co
     }
     /* v_p^0: first-order nodal solve at t^0 */
     phase_packets(S, S->order, 0.0, &w);
-    for (long p = 0; p < np; ++p) node_solve_one(M, w.pkM, w.pkR, p, S->vp + p * d);
+    for (long p = 0; p < np; ++p) node_solve_one(M, S->x, w.pkM, w.pkR, p, S->vp + p * d);
     work_free(&w);
     S->dt = prm->dt_fixed > 0 ? prm->dt_fixed : dt0;
     S->t = 0.0;
@@ -1099,3 +1228,23 @@ long orc_mesh_stencil(const OrcMesh *M, long c, long *dst, long cap) {
     return n;
 }
 int orc_mesh_bc_ndof(const OrcMesh *M, long p) { return M->bc_ndof[p]; }
+
+/* values of the boundary faces, [d][nb] (traction vectors; pressures in the first row;
+ * prescribed velocities), applied from the next nodal solve on */
+int orc_mesh_set_bc_values(OrcMesh *M, const double *val_soa) {
+    if (!M || !val_soa) return ORC_ERR_ARG;
+    for (long b = 0; b < M->nb; ++b)
+        for (int a = 0; a < M->d; ++a) M->bf_val[b * M->d + a] = val_soa[a * M->nb + b];
+    return ORC_OK;
+}
+
+/* new tags of the boundary faces [nb] (a boundary condition that changes type during the
+ * run, Sect. "Boundary condition treatments"); the per-node conditions are re-derived */
+int orc_mesh_set_btag(OrcMesh *M, const int *btag) {
+    if (!M || !btag) return ORC_ERR_ARG;
+    for (long b = 0; b < M->nb; ++b)
+        if (btag[b] < 0 || btag[b] > 5) return ORC_ERR_ARG;
+    for (long b = 0; b < M->nb; ++b) M->bf_tag[b] = btag[b];
+    resolve_bcs(M);
+    return ORC_OK;
+}

@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-FREE, SLIP, CLAMPED = 0, 1, 2
+FREE, SLIP, CLAMPED, TRACTION, PRESSURE, VELOCITY = 0, 1, 2, 3, 4, 5
 
 
 @dataclass
@@ -36,7 +36,7 @@ class Mesh:
     x: np.ndarray          # [dim, n_nodes] float64 (SoA)
     c2n: np.ndarray        # [dim+1, n_cells] int32, positively oriented (SoA)
     bface: np.ndarray      # [dim, n_bfaces] int32 node ids of tagged boundary faces
-    btag: np.ndarray       # [n_bfaces] int32 in {FREE, SLIP, CLAMPED}
+    btag: np.ndarray       # [n_bfaces] int32 in {FREE, SLIP, CLAMPED, TRACTION, PRESSURE, VELOCITY}
 
     @property
     def n_nodes(self) -> int:
@@ -60,6 +60,8 @@ class Problem:
     steps: int
     F: np.ndarray | None = None   # [dim*dim, n_cells] or None for F = I
     meta: dict = field(default_factory=dict)
+    bcval: np.ndarray | None = None  # [dim, n_bfaces] boundary-face values (traction vector,
+                                     # pressure in row 0, prescribed velocity) or None
 
 
 # ----------------------------------------------------------------------------- ordering
@@ -126,7 +128,7 @@ def _boundary_faces(cells: np.ndarray) -> np.ndarray:
 
 def _tag_faces(x_rows: np.ndarray, faces: np.ndarray, lo, hi, bc: dict) -> tuple[np.ndarray, np.ndarray]:
     """Tag each boundary face by the box side it lies on. bc maps side names
-    ('x0','x1','y0','y1','z0','z1') to FREE/SLIP/CLAMPED (missing = FREE)."""
+    ('x0','x1','y0','y1','z0','z1') to a face tag (missing = FREE)."""
     d = x_rows.shape[1]
     tags = np.full(faces.shape[0], FREE, dtype=np.int32)
     names = "xyz"
@@ -249,6 +251,23 @@ def plain2d(n: int = 40, seed: int = 1, steps: int = 200) -> Problem:
     v = 1e-3 * np.stack([np.sin(np.pi * p[:, 0]) * np.sin(np.pi * p[:, 1]),
                          np.cos(np.pi * p[:, 0]) * np.cos(np.pi * p[:, 1])])
     return Problem(f"plain2d_n{n}", m, 1.0, 2.0, np.full(m.n_cells, 1.0), v, 0.4, steps)
+
+
+def side_values(m: Mesh, tag: int, value) -> np.ndarray:
+    """[dim, n_bfaces] boundary-face values: value (a vector of dim entries; a pressure goes
+    in entry 0) on the faces tagged tag, zero elsewhere."""
+    out = np.zeros((m.dim, m.btag.size))
+    out[:, m.btag == tag] = np.asarray(value, dtype=float)[:, None]
+    return out
+
+
+def piston2d(n: int = 40, seed: int = 6, V: float = 0.02, steps: int = 200) -> Problem:
+    """Unit square at rest (rho0=1, mu=1, lambda=2) pushed by a piston: the side x = 0 has the
+    prescribed normal velocity V e_x (Appendix B, velocity condition), y = 0 and y = 1 are slip
+    walls, x = 1 is free; CFL 0.4."""
+    m = tri_mesh(n, seed, bc={"x0": VELOCITY, "y0": SLIP, "y1": SLIP})
+    return Problem(f"piston2d_n{n}", m, 1.0, 2.0, np.full(m.n_cells, 1.0), np.zeros((2, m.n_cells)), 0.4, steps,
+                   bcval=side_values(m, VELOCITY, (V, 0.0)))
 
 
 def impact2d(n: int = 708, seed: int = 2, steps: int = 2000) -> Problem:
