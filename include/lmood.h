@@ -121,10 +121,19 @@ lmood_status lmood_params_default(int dim, lmood_params *p);
  *   c2n            host, [dim+1][n_cells] node ids of each simplex (positively oriented)
  *   bface, btag    host, [dim][n_bfaces] node ids and [n_bfaces] tags of boundary faces that
  *                  carry a condition (Appendix B): 0 free traction, 1 slip wall (symmetry
- *                  plane through the face), 2 clamped (symmetry point, v = 0). Faces not
- *                  listed are traction-free. A node takes the strongest condition of its
- *                  faces (clamped > slip > free); several distinct slip planes leave their
- *                  intersection. May be NULL when n_bfaces = 0.
+ *                  plane through the face), 2 clamped (symmetry point, v = 0), 3 prescribed
+ *                  traction vector t_f, 4 prescribed pressure p_f, 5 prescribed velocity V_f
+ *                  (its normal component is imposed; Eqs. pBC, vBC1, vBC). The values of tags
+ *                  3-5 are set with lmood_mesh_set_bc_values (zero until then). Faces not
+ *                  listed are traction-free. Each face must be a face of one cell; the library
+ *                  orders its nodes so that its area vector N_f points out of the mesh. Per
+ *                  node: clamped > prescribed velocity > slip > free for the velocity (several
+ *                  distinct slip planes leave their intersection; a prescribed velocity
+ *                  imposes v_p . d_p = g_p with d_p = sum N_f / dim, g_p = sum V_f . N_f / dim
+ *                  over the node's velocity faces, on top of the slip / free solve); traction
+ *                  faces add |N_f| t_f / dim and pressure faces -p_f N_f / dim to the node's
+ *                  force balance, with N_f at the current positions. May be NULL when
+ *                  n_bfaces = 0.
  *   cell_inst      host, [n_cells] instance id of each cell for a batch of independent meshes
  *                  concatenated into one (cells of different instances share no node), or
  *                  NULL for a single instance. Each instance keeps its own dt.
@@ -138,6 +147,19 @@ lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double *x, int64_
                                const int32_t *btag, const int32_t *cell_inst, int32_t n_inst,
                                void *stream, lmood_mesh *out);
 lmood_status lmood_mesh_destroy(lmood_mesh m);
+
+/* Values of the boundary faces, [dim][n_bfaces] in the order given to lmood_mesh_create:
+ * traction vectors (tag 3), pressures in row 0 (tag 4), prescribed velocities (tag 5); other
+ * faces' values are ignored. Host (is_device = 0, the call synchronises) or device pointer.
+ * They act from the next nodal solve on (set them before lmood_state_init for the initial
+ * one); all states on the mesh see them. */
+lmood_status lmood_mesh_set_bc_values(lmood_mesh m, const double *values, int is_device);
+
+/* New tags [n_bfaces] (host) for the mesh's boundary faces, e.g. a wall that becomes free at
+ * a given time (Sect. "Boundary condition treatments"); the per-node conditions are re-derived
+ * and take effect from the next nodal solve. Synchronises. Errors: LMOOD_ERR_ARG for a tag
+ * outside 0-5. */
+lmood_status lmood_mesh_set_btag(lmood_mesh m, const int32_t *btag);
 
 /*
  * Create a state at t = 0 on mesh m (initialisation of Sect. "2D and 3D test problems"):
@@ -221,7 +243,8 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  * (x, v_p per node; v, F per cell) and of the per-cell mu; the adjoint is the exact transpose
  * of its linearisation, written by hand kernel by kernel (no atomics, deterministic).
  * Only the two-level cascade (P1 -> P0) is differentiated: a recorded step that used the
- * limited level returns LMOOD_ERR_ARG. Energy e has no influence on the other fields, so it
+ * limited level returns LMOOD_ERR_ARG, and so does a mesh with traction, pressure or
+ * prescribed-velocity faces. Energy e has no influence on the other fields, so it
  * carries no adjoint.
  *
  * lmood_tape_record: runs n_steps ordinary lmood_step calls on s (the forward pass, with the

@@ -56,8 +56,11 @@
  *      advanced further (non-finite value, tau <= 0 or det F <= 0) is a parachute failure;
  *      a P0 candidate whose only defect is eps < 0 is accepted and counted (eps does not
  *      enter the stress of this model).
- *  R12 PAD: finite values, tau > 0, det F > 0, eps = e - |v|^2/2 >= -1e-10 max(|e|, |v|^2/2);
- *      theta is not modelled. RDMP on rho over V_c and c at t^n, delta0 absolute.
+ *  R12 PAD: finite values, tau > 0, det F > 0, eps = e - |v|^2/2 >= -1e-10 max(|e|, |v|^2/2,
+ *      a0^2) with a0^2 = (kappa + 4 mu / 3) / rho0 the squared P-wave speed at rest (the
+ *      material's energy scale: in a cell at rest e and |v|^2/2 are both at rounding level,
+ *      and eps's sign is noise); theta is not modelled. RDMP on rho over V_c and c at t^n,
+ *      delta0 absolute.
  *  R13 dt^{n+1} = min(C_CFL min L_c/a_c, C_v dt^n min V^n/|V^{n+1}-V^n|, (1+C_i) dt^n),
  *      evaluated on the accepted state; dt^0 is the acoustic bound.
  *  R14 BCs: per node, clamped > slip > free; k independent slip planes leave the
@@ -936,7 +939,7 @@ static void phase_update(const OrcState *S, const int *order, double dt, Work *w
 
 /* 6. detection (Eqs. PAD and RDMP; reading R12).
  * pad_state: 0 admissible; 1 only eps < -tol; 2 not computable (non-finite, tau <= 0, det F <= 0) */
-static int pad_state(int d, const double *v, double e, const double *F, double V) {
+static int pad_state(int d, const double *v, double e, const double *F, double V, double a0sq) {
     int dd = d * d;
     if (!isfinite(e) || !isfinite(V)) return 2;
     for (int i = 0; i < d; ++i)
@@ -948,7 +951,7 @@ static int pad_state(int d, const double *v, double e, const double *F, double V
     double ke = 0.0;
     for (int i = 0; i < d; ++i) ke += 0.5 * v[i] * v[i];
     double eps = e - ke;
-    double tol = 1e-10 * fmax(fabs(e), ke);
+    double tol = 1e-10 * fmax(fmax(fabs(e), ke), a0sq);
     return eps >= -tol ? 0 : 1;
 }
 
@@ -1010,7 +1013,8 @@ int orc_step(OrcState *S, OrcInfo *info) {
             int *flag = calloc(nc, sizeof(int));
 #pragma omp parallel for schedule(static) reduction(+ : fresh, n_para, n_eps)
             for (long c = 0; c < nc; ++c) {
-                int ps = pad_state(d, w.v1 + c * d, w.e1[c], w.F1 + c * dd, w.V1[c]);
+                int ps = pad_state(d, w.v1 + c * d, w.e1[c], w.F1 + c * dd, w.V1[c],
+                                   (kappa_of(S, c) + 4.0 / 3.0 * S->mu[c]) / S->rho0);
                 if (order[c] != 1) {
                     if (ps != 0 || !rdmp_ok(S, &w, c)) { flag[c] = 1; fresh++; }
                 } else if (ps == 2) {

@@ -44,6 +44,7 @@ class StepInfo(C.Structure):
 
 _lib = None
 EXPORTS = ("lmood_params_default", "lmood_mesh_create", "lmood_mesh_destroy", "lmood_mesh_info",
+           "lmood_mesh_set_bc_values", "lmood_mesh_set_btag",
            "lmood_state_init", "lmood_state_destroy", "lmood_step", "lmood_run", "lmood_get", "lmood_set",
            "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_totals_noalloc", "lmood_tape_record",
            "lmood_tape_backward", "lmood_tape_replay", "lmood_tape_info", "lmood_tape_destroy", "lmood_last_error")
@@ -64,6 +65,8 @@ def lib():
                                         vp, C.POINTER(vp)]
         L.lmood_mesh_destroy.argtypes = [vp]
         L.lmood_mesh_info.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.lmood_mesh_set_bc_values.argtypes = [vp, vp, C.c_int]
+        L.lmood_mesh_set_btag.argtypes = [vp, vp]
         L.lmood_state_init.argtypes = [vp, C.POINTER(Material), vp, vp, vp, C.POINTER(Params), C.POINTER(vp)]
         L.lmood_state_destroy.argtypes = [vp]
         L.lmood_step.argtypes = [vp, C.POINTER(StepInfo)]
@@ -137,6 +140,20 @@ class Mesh:
                                        _ptr(bface) if nb else None, _ptr(btag) if nb else None, _ptr(ci),
                                        self.n_inst, self.stream, C.byref(h)))
         self.h = h
+
+    def set_bc_values(self, values):
+        """boundary-face values [dim, n_bfaces]: traction vectors (tag 3), pressures in row 0
+        (tag 4), prescribed velocities (tag 5); numpy (host) or a torch CUDA tensor"""
+        if hasattr(values, "data_ptr"):
+            _check(lib().lmood_mesh_set_bc_values(self.h, C.c_void_p(values.contiguous().data_ptr()), 1))
+        else:
+            a = np.ascontiguousarray(values, dtype=np.float64)
+            _check(lib().lmood_mesh_set_bc_values(self.h, a.ctypes.data, 0))
+
+    def set_btag(self, btag):
+        """new boundary-face tags [n_bfaces] (0-5); per-node conditions re-derived"""
+        a = np.ascontiguousarray(btag, dtype=np.int32)
+        _check(lib().lmood_mesh_set_btag(self.h, a.ctypes.data))
 
     def info(self) -> dict:
         o = (C.c_int64 * 6)()
@@ -347,6 +364,8 @@ def simulation(problem, stream=None, cell_inst=None, n_inst=1, **params) -> Stat
     cell_inst / n_inst describe a batch of independent instances concatenated into one mesh."""
     m = problem.mesh
     mesh = Mesh(m.dim, m.x, m.c2n, m.bface, m.btag, cell_inst=cell_inst, n_inst=n_inst, stream=stream)
+    if getattr(problem, "bcval", None) is not None:
+        mesh.set_bc_values(problem.bcval)
     p = params_default(m.dim, cfl=problem.cfl)
     for k, v in params.items():
         setattr(p, k, v)

@@ -81,101 +81,56 @@ extern "C" lmood_status lmood_params_default(int dim, lmood_params *p) {
     return LMOOD_OK;
 }
 
-extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double *x, int64_t n_cells,
-                                          const int32_t *c2n, int64_t n_bfaces, const int32_t *bface,
-                                          const int32_t *btag, const int32_t *cell_inst, int32_t n_inst,
-                                          void *stream, lmood_mesh *out) {
-    if (!out) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: out is NULL");
-    *out = nullptr;
-    if (dim != 2 && dim != 3) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: dim must be 2 or 3");
-    if (n_nodes <= 0 || n_cells <= 0 || !x || !c2n) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: empty mesh or NULL array");
-    const int nv = dim + 1;
-    if (n_cells * nv >= (int64_t)INT32_MAX || n_nodes >= (int64_t)INT32_MAX)
-        return fail(LMOOD_ERR_ARG, "lmood_mesh_create: mesh too large for 32-bit corner ids");
-    if (n_bfaces < 0 || (n_bfaces > 0 && (!bface || !btag))) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: boundary faces");
-    if (cell_inst ? n_inst < 1 : n_inst > 1) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: bad instance count");
-    if (!cell_inst) n_inst = 1;
-    const int64_t N = n_cells, Np = n_nodes;
-    // validation: indices and orientation
-    for (int64_t i = 0; i < N * nv; ++i)
-        if (c2n[i] < 0 || c2n[i] >= Np) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: node index out of range in c2n");
-    for (int64_t c = 0; c < N; ++c)
-        if (!(host_volume(dim, x, Np, c2n, N, c) > 0.0))
-            return fail(LMOOD_ERR_MESH, "lmood_mesh_create: cell " + std::to_string(c) + " has non-positive volume");
-    for (int64_t i = 0; i < n_bfaces * dim; ++i)
-        if (bface[i] < 0 || bface[i] >= Np) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: node index out of range in bface");
-    for (int64_t i = 0; i < n_bfaces; ++i)
-        if (btag[i] < 0 || btag[i] > 2) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: boundary tag must be 0, 1 or 2");
-    std::vector<int> node_inst;
-    if (cell_inst) {
-        node_inst.assign(Np, -1);
-        for (int64_t c = 0; c < N; ++c) {
-            const int ci = cell_inst[c];
-            if (ci < 0 || ci >= n_inst) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: cell instance out of range");
-            for (int k = 0; k < nv; ++k) {
-                int &ni = node_inst[c2n[k * N + c]];
-                if (ni >= 0 && ni != ci) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: a node is shared by two instances");
-                ni = ci;
+// Per-node boundary conditions from the face tags (Appendix B). The velocity subspace:
+// strongest first, clamped > slip > free (k distinct slip planes leave their intersection);
+// nodes touched by a traction, pressure or prescribed-velocity face get BC_EXT (their forces
+// and constraint act in the nodal solve). Faces are [dim][nb], oriented outward.
+static lmood_status resolve_bcs(int dim, int64_t Np, int64_t n_bfaces, const double *x, const int *bface,
+                                const int *btag, std::vector<unsigned char> &ndof, std::vector<double> &bct,
+                                bool &has_ext) {
+    ndof.assign(Np, (unsigned char)dim);
+    bct.assign(6 * Np, 0.0);
+    has_ext = false;
+    std::vector<unsigned char> clamped(Np, 0), ext(Np, 0);
+    std::vector<std::vector<std::array<double, 3>>> planes(Np);
+    for (int64_t f = 0; f < n_bfaces; ++f) {
+        int q[3];
+        for (int a = 0; a < dim; ++a) q[a] = bface[a * n_bfaces + f];
+        std::array<double, 3> nrm{0, 0, 0};
+        if (dim == 2) {
+            nrm[0] = x[1 * Np + q[1]] - x[1 * Np + q[0]];
+            nrm[1] = x[0 * Np + q[0]] - x[0 * Np + q[1]];
+        } else {
+            double u[3], w[3];
+            for (int a = 0; a < 3; ++a) {
+                u[a] = x[a * Np + q[1]] - x[a * Np + q[0]];
+                w[a] = x[a * Np + q[2]] - x[a * Np + q[0]];
             }
+            nrm = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        }
+        const double len = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+        if (!(len > 0)) return fail(LMOOD_ERR_MESH, "degenerate boundary face");
+        for (double &v : nrm) v /= len;
+        for (int a = 0; a < dim; ++a) {
+            const int p = q[a];
+            if (btag[f] == TAG_CLAMPED) clamped[p] = 1;
+            if (btag[f] >= TAG_TRACTION) {
+                ext[p] = 1;
+                has_ext = true;
+            }
+            if (btag[f] != TAG_SLIP) continue;
+            bool known = false;
+            for (auto &pl : planes[p])
+                if (std::fabs(pl[0] * nrm[0] + pl[1] * nrm[1] + pl[2] * nrm[2]) > 1.0 - 1e-12) known = true;
+            if (!known) planes[p].push_back(nrm);
         }
     }
-    // node -> corner CSR: corners of each node in ascending cell id; corner id = k N + c
-    std::vector<int> off(Np + 1, 0), n2c(N * nv);
-    for (int64_t c = 0; c < N; ++c)
-        for (int k = 0; k < nv; ++k) off[c2n[k * N + c] + 1]++;
-    for (int64_t p = 0; p < Np; ++p) off[p + 1] += off[p];
-    int max_deg = 0;
-    for (int64_t p = 0; p < Np; ++p) max_deg = std::max(max_deg, off[p + 1] - off[p]);
-    {
-        std::vector<int> pos(off.begin(), off.end() - 1);
-        for (int64_t c = 0; c < N; ++c)
-            for (int k = 0; k < nv; ++k) n2c[pos[c2n[k * N + c]]++] = (int)(k * N + c);
-    }
-    // (node, neighbour) pairs of the least-squares sums: sum_p deg(p) (deg(p) - 1)
-    int64_t nnz = 0;
-    for (int64_t p = 0; p < Np; ++p) nnz += (int64_t)(off[p + 1] - off[p]) * (off[p + 1] - off[p] - 1);
-    // boundary conditions (Appendix B; strongest first: clamped, slip, free)
-    std::vector<unsigned char> ndof(Np, (unsigned char)dim);
-    std::vector<double> bct(6 * Np, 0.0);
-    {
-        std::vector<unsigned char> clamped(Np, 0);
-        std::vector<std::vector<std::array<double, 3>>> planes(Np);
-        for (int64_t f = 0; f < n_bfaces; ++f) {
-            int q[3];
-            for (int a = 0; a < dim; ++a) q[a] = bface[a * n_bfaces + f];
-            std::array<double, 3> nrm{0, 0, 0};
-            if (dim == 2) {
-                nrm[0] = x[1 * Np + q[1]] - x[1 * Np + q[0]];
-                nrm[1] = x[0 * Np + q[0]] - x[0 * Np + q[1]];
-            } else {
-                double u[3], w[3];
-                for (int a = 0; a < 3; ++a) {
-                    u[a] = x[a * Np + q[1]] - x[a * Np + q[0]];
-                    w[a] = x[a * Np + q[2]] - x[a * Np + q[0]];
-                }
-                nrm = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
-            }
-            const double len = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
-            if (!(len > 0)) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: degenerate boundary face");
-            for (double &v : nrm) v /= len;
-            for (int a = 0; a < dim; ++a) {
-                const int p = q[a];
-                if (btag[f] == 2) clamped[p] = 1;
-                if (btag[f] != 1) continue;
-                bool known = false;
-                for (auto &pl : planes[p])
-                    if (std::fabs(pl[0] * nrm[0] + pl[1] * nrm[1] + pl[2] * nrm[2]) > 1.0 - 1e-12) known = true;
-                if (!known) planes[p].push_back(nrm);
-            }
-        }
-        for (int64_t p = 0; p < Np; ++p) {
-            const int k = clamped[p] ? dim : (int)planes[p].size();
-            auto T = [&](int i, int a) -> double & { return bct[(i * 3 + a) * Np + p]; };
-            if (k == 0) continue;
-            if (k >= dim) {
-                ndof[p] = 0;
-                continue;
-            }
+    for (int64_t p = 0; p < Np; ++p) {
+        const int k = clamped[p] ? dim : (int)planes[p].size();
+        auto T = [&](int i, int a) -> double & { return bct[(i * 3 + a) * Np + p]; };
+        if (k >= dim) {
+            ndof[p] = 0;
+        } else if (k > 0) {
             const auto &n1 = planes[p][0];
             if (dim == 2) {  // one wall line: the free direction is its tangent
                 ndof[p] = 1;
@@ -205,6 +160,121 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
                 ndof[p] = 1;
             }
         }
+        if (ext[p]) ndof[p] |= BC_EXT;
+    }
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double *x, int64_t n_cells,
+                                          const int32_t *c2n, int64_t n_bfaces, const int32_t *bface,
+                                          const int32_t *btag, const int32_t *cell_inst, int32_t n_inst,
+                                          void *stream, lmood_mesh *out) {
+    if (!out) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: out is NULL");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: dim must be 2 or 3");
+    if (n_nodes <= 0 || n_cells <= 0 || !x || !c2n) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: empty mesh or NULL array");
+    const int nv = dim + 1;
+    if (n_cells * nv >= (int64_t)INT32_MAX || n_nodes >= (int64_t)INT32_MAX)
+        return fail(LMOOD_ERR_ARG, "lmood_mesh_create: mesh too large for 32-bit corner ids");
+    if (n_bfaces < 0 || (n_bfaces > 0 && (!bface || !btag))) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: boundary faces");
+    if (cell_inst ? n_inst < 1 : n_inst > 1) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: bad instance count");
+    if (!cell_inst) n_inst = 1;
+    const int64_t N = n_cells, Np = n_nodes;
+    // validation: indices and orientation
+    for (int64_t i = 0; i < N * nv; ++i)
+        if (c2n[i] < 0 || c2n[i] >= Np) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: node index out of range in c2n");
+    for (int64_t c = 0; c < N; ++c)
+        if (!(host_volume(dim, x, Np, c2n, N, c) > 0.0))
+            return fail(LMOOD_ERR_MESH, "lmood_mesh_create: cell " + std::to_string(c) + " has non-positive volume");
+    for (int64_t i = 0; i < n_bfaces * dim; ++i)
+        if (bface[i] < 0 || bface[i] >= Np) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: node index out of range in bface");
+    for (int64_t i = 0; i < n_bfaces; ++i)
+        if (btag[i] < 0 || btag[i] > 5) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: boundary tag must be 0 to 5");
+    std::vector<int> node_inst;
+    if (cell_inst) {
+        node_inst.assign(Np, -1);
+        for (int64_t c = 0; c < N; ++c) {
+            const int ci = cell_inst[c];
+            if (ci < 0 || ci >= n_inst) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: cell instance out of range");
+            for (int k = 0; k < nv; ++k) {
+                int &ni = node_inst[c2n[k * N + c]];
+                if (ni >= 0 && ni != ci) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: a node is shared by two instances");
+                ni = ci;
+            }
+        }
+    }
+    // node -> corner CSR: corners of each node in ascending cell id; corner id = k N + c
+    std::vector<int> off(Np + 1, 0), n2c(N * nv);
+    for (int64_t c = 0; c < N; ++c)
+        for (int k = 0; k < nv; ++k) off[c2n[k * N + c] + 1]++;
+    for (int64_t p = 0; p < Np; ++p) off[p + 1] += off[p];
+    int max_deg = 0;
+    for (int64_t p = 0; p < Np; ++p) max_deg = std::max(max_deg, off[p + 1] - off[p]);
+    {
+        std::vector<int> pos(off.begin(), off.end() - 1);
+        for (int64_t c = 0; c < N; ++c)
+            for (int k = 0; k < nv; ++k) n2c[pos[c2n[k * N + c]]++] = (int)(k * N + c);
+    }
+    // (node, neighbour) pairs of the least-squares sums: sum_p deg(p) (deg(p) - 1)
+    int64_t nnz = 0;
+    for (int64_t p = 0; p < Np; ++p) nnz += (int64_t)(off[p + 1] - off[p]) * (off[p + 1] - off[p] - 1);
+    // boundary faces: oriented outward (the area vector points away from the vertex of the
+    // face's cell that is not on the face), tags, the faces around each node
+    std::vector<int> bf(bface, bface + n_bfaces * dim), tags(btag, btag + n_bfaces);
+    for (int64_t f = 0; f < n_bfaces; ++f) {
+        int q[3];
+        for (int a = 0; a < dim; ++a) q[a] = bf[a * n_bfaces + f];
+        int opp = -1;
+        for (int j = off[q[0]]; j < off[q[0] + 1] && opp < 0; ++j) {
+            const int64_t c = n2c[j] % N;
+            int hits = 0, other = -1;
+            for (int k = 0; k < nv; ++k) {
+                const int r = c2n[k * N + c];
+                bool on = false;
+                for (int a = 0; a < dim; ++a) on |= r == q[a];
+                if (on) ++hits;
+                else other = r;
+            }
+            if (hits == dim) opp = other;
+        }
+        if (opp < 0) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: boundary face " + std::to_string(f) + " is not a cell face");
+        double nrm[3] = {0, 0, 0};
+        if (dim == 2) {
+            nrm[0] = x[1 * Np + q[1]] - x[1 * Np + q[0]];
+            nrm[1] = x[0 * Np + q[0]] - x[0 * Np + q[1]];
+        } else {
+            double u[3], w[3];
+            for (int a = 0; a < 3; ++a) {
+                u[a] = x[a * Np + q[1]] - x[a * Np + q[0]];
+                w[a] = x[a * Np + q[2]] - x[a * Np + q[0]];
+            }
+            nrm[0] = u[1] * w[2] - u[2] * w[1];
+            nrm[1] = u[2] * w[0] - u[0] * w[2];
+            nrm[2] = u[0] * w[1] - u[1] * w[0];
+        }
+        double dot = 0.0;
+        for (int a = 0; a < dim; ++a) {
+            double xf = 0.0;
+            for (int i = 0; i < dim; ++i) xf += x[a * Np + q[i]];
+            dot += nrm[a] * (xf / dim - x[a * Np + opp]);
+        }
+        if (dot < 0.0) std::swap(bf[0 * n_bfaces + f], bf[1 * n_bfaces + f]);
+    }
+    std::vector<int> nbf_off(Np + 1, 0), nbf_idx(n_bfaces * dim);
+    for (int64_t f = 0; f < n_bfaces; ++f)
+        for (int a = 0; a < dim; ++a) nbf_off[bf[a * n_bfaces + f] + 1]++;
+    for (int64_t p = 0; p < Np; ++p) nbf_off[p + 1] += nbf_off[p];
+    {
+        std::vector<int> pos(nbf_off.begin(), nbf_off.end() - 1);
+        for (int64_t f = 0; f < n_bfaces; ++f)
+            for (int a = 0; a < dim; ++a) nbf_idx[pos[bf[a * n_bfaces + f]]++] = (int)f;
+    }
+    std::vector<unsigned char> ndof;
+    std::vector<double> bct;
+    bool has_ext = false;
+    {
+        lmood_status r = resolve_bcs(dim, Np, n_bfaces, x, bf.data(), tags.data(), ndof, bct, has_ext);
+        if (r) return fail(r, std::string("lmood_mesh_create: ") + lmood_last_error());
     }
     // device copies
     cudaStream_t st = (cudaStream_t)stream;
@@ -252,6 +322,33 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
     g.bc_t = d_bt;
     g.cell_inst = d_ci;
     g.node_inst = d_ni;
+    m->d_ndof = d_nd;
+    m->d_bct = d_bt;
+    m->nb = n_bfaces;
+    m->has_ext = has_ext;
+    m->h_x0.assign(x, x + dim * Np);
+    m->h_bf = bf;
+    m->h_btag = tags;
+    g.nbf = (int)n_bfaces;
+    if (n_bfaces > 0) {
+        int *d_bfn, *d_noff, *d_nidx;
+        std::vector<unsigned char> t8(tags.begin(), tags.end());
+        std::vector<double> zeros((size_t)dim * n_bfaces, 0.0);
+        if ((s = upload(m->mem, &d_bfn, bf.data(), bf.size(), st)) ||
+            (s = upload(m->mem, &m->d_btag, t8.data(), t8.size(), st)) ||
+            (s = upload(m->mem, &m->d_bfval, zeros.data(), zeros.size(), st)) ||
+            (s = upload(m->mem, &d_noff, nbf_off.data(), nbf_off.size(), st)) ||
+            (s = upload(m->mem, &d_nidx, nbf_idx.data(), nbf_idx.size(), st))) {
+            m->mem.release();
+            delete m;
+            return s;
+        }
+        g.bf_nodes = d_bfn;
+        g.bf_tag = m->d_btag;
+        g.bf_val = m->d_bfval;
+        g.nbf_off = d_noff;
+        g.nbf_idx = d_nidx;
+    }
     cudaError_t e = cudaStreamSynchronize(st);  // host vectors die at return
     if (e != cudaSuccess) {
         m->mem.release();
@@ -278,6 +375,36 @@ extern "C" lmood_status lmood_mesh_info(lmood_mesh m, int64_t *o) {
     o[3] = m->st_nnz;
     o[4] = m->max_deg;
     o[5] = m->n_inst;
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_mesh_set_bc_values(lmood_mesh m, const double *values, int is_device) {
+    if (!m || !values) return fail(LMOOD_ERR_ARG, "lmood_mesh_set_bc_values: NULL argument");
+    if (m->nb == 0) return LMOOD_OK;
+    LM_CUDA(cudaMemcpyAsync(m->d_bfval, values, (size_t)m->dim * m->nb * sizeof(double),
+                            is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->st));
+    if (!is_device) LM_CUDA(cudaStreamSynchronize(m->st));
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_mesh_set_btag(lmood_mesh m, const int32_t *btag) {
+    if (!m || (!btag && m->nb > 0)) return fail(LMOOD_ERR_ARG, "lmood_mesh_set_btag: NULL argument");
+    for (int64_t f = 0; f < m->nb; ++f)
+        if (btag[f] < 0 || btag[f] > 5) return fail(LMOOD_ERR_ARG, "lmood_mesh_set_btag: boundary tag must be 0 to 5");
+    std::vector<int> tags(btag, btag + m->nb);
+    std::vector<unsigned char> ndof;
+    std::vector<double> bct;
+    bool has_ext = false;
+    lmood_status r = resolve_bcs(m->dim, m->np, m->nb, m->h_x0.data(), m->h_bf.data(), tags.data(), ndof, bct, has_ext);
+    if (r) return fail(r, std::string("lmood_mesh_set_btag: ") + lmood_last_error());
+    // in place: graphs captured on this mesh stay valid
+    LM_CUDA(cudaMemcpyAsync(m->d_ndof, ndof.data(), ndof.size(), cudaMemcpyHostToDevice, m->st));
+    LM_CUDA(cudaMemcpyAsync(m->d_bct, bct.data(), bct.size() * sizeof(double), cudaMemcpyHostToDevice, m->st));
+    std::vector<unsigned char> t8(tags.begin(), tags.end());
+    if (m->nb > 0) LM_CUDA(cudaMemcpyAsync(m->d_btag, t8.data(), t8.size(), cudaMemcpyHostToDevice, m->st));
+    LM_CUDA(cudaStreamSynchronize(m->st));
+    m->h_btag = tags;
+    m->has_ext = has_ext;
     return LMOOD_OK;
 }
 
@@ -334,6 +461,7 @@ static Prm kernel_params(const lmood_params &p, const lmood_material &m) {
     k.delta1 = p.delta1;
     k.dt_fixed = p.dt_fixed;
     k.lam = m.lambda;
+    k.irho0 = 1.0 / m.rho0;
     k.base_order = p.order == 1 ? 1 : 2;
     k.mood = p.mood ? 1 : 0;
     k.vol_coeff = m.vol_coeff ? 1 : 0;

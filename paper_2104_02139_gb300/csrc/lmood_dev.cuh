@@ -18,6 +18,7 @@ namespace lmood {
 
 struct Prm {
     double cfl, Cv, Ci, delta0, delta1, dt_fixed, lam;
+    double irho0;    // 1 / rho0
     int base_order;  // order every cell starts the step with (2: P1, 1: P0; 0: keep f.order)
     int mood;        // detection on/off
     int vol_coeff;   // 0: kappa = lambda + 2 mu / 3; 1: kappa = mu
@@ -25,13 +26,24 @@ struct Prm {
 };
 
 struct Geo {
-    int N, Np, n_inst, pad_;
+    int N, Np, n_inst, nbf;
     const int *c2n;
     const int *n2c_off, *n2c;
-    const unsigned char *bc_ndof;  // free directions per node (D = free, 0 = clamped)
+    const unsigned char *bc_ndof;  // free directions per node (D = free, 0 = clamped), | BC_EXT
+                                   // when a traction / pressure / velocity face touches the node
     const double *bc_t;            // tangent vectors [2][3][Np]
     const int *cell_inst, *node_inst;  // NULL for one instance
+    // boundary faces (NULL when the mesh has none): nodes [D][nbf] ordered so that the area
+    // vector points outward, tag [nbf], values [D][nbf], the faces around each node
+    // (ascending face id)
+    const int *bf_nodes;
+    const unsigned char *bf_tag;
+    const double *bf_val;
+    const int *nbf_off, *nbf_idx;
 };
+
+constexpr unsigned char BC_EXT = 0x80;  // node has traction / pressure / velocity faces
+enum { TAG_FREE = 0, TAG_SLIP = 1, TAG_CLAMPED = 2, TAG_TRACTION = 3, TAG_PRESSURE = 4, TAG_VELOCITY = 5 };
 
 struct Fld {
     const double *m, *mu;
@@ -294,9 +306,13 @@ __device__ __forceinline__ double kappa_of(const Prm &prm, double mu) {
     return prm.vol_coeff ? mu : prm.lam + 2.0 * mu / 3.0;
 }
 
-// physical admissibility (Eq. PAD): 0 admissible, 1 only eps < -tol, 2 not computable
+// physical admissibility (Eq. PAD): 0 admissible, 1 only eps < -tol, 2 not computable;
+// tol = 1e-10 max(|e|, |v|^2/2, a0sq) with a0sq the material's energy scale
+// (kappa + 4 mu / 3) / rho0, the squared P-wave speed at rest: in a cell at rest e and
+// |v|^2/2 are at rounding level and the sign of eps is noise
 template <int D>
-__device__ __forceinline__ int pad_state(const double (&v)[D], double e, const double (&F)[D * D], double V) {
+__device__ __forceinline__ int pad_state(const double (&v)[D], double e, const double (&F)[D * D], double V,
+                                         double a0sq) {
     bool fin = isfinite(e) && isfinite(V);
 #pragma unroll
     for (int i = 0; i < D; ++i) fin = fin && isfinite(v[i]);
@@ -307,7 +323,7 @@ __device__ __forceinline__ int pad_state(const double (&v)[D], double e, const d
 #pragma unroll
     for (int i = 0; i < D; ++i) ke += 0.5 * v[i] * v[i];
     const double eps = e - ke;
-    return eps >= -1e-10 * fmax(fabs(e), ke) ? 0 : 1;
+    return eps >= -1e-10 * fmax(fmax(fabs(e), ke), a0sq) ? 0 : 1;
 }
 
 }  // namespace lmood

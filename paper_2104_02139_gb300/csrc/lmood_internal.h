@@ -44,12 +44,19 @@ struct DevAllocs {
 
 struct lmood_mesh_s {
     int dim = 0, n_inst = 1;
-    int64_t np = 0, nc = 0, st_nnz = 0;
+    int64_t np = 0, nc = 0, st_nnz = 0, nb = 0;
     int max_deg = 0;
     cudaStream_t st = nullptr;
     const lmood::Ops *ops = nullptr;
     lmood::Geo geo{};
     double *x0 = nullptr;
+    // host copies for re-deriving the node conditions when the face tags change
+    std::vector<double> h_x0;     // [dim][np]
+    std::vector<int> h_bf;        // [dim][nb], oriented outward
+    std::vector<int> h_btag;      // [nb]
+    unsigned char *d_ndof = nullptr, *d_btag = nullptr;
+    double *d_bct = nullptr, *d_bfval = nullptr;
+    bool has_ext = false;         // some face has a traction / pressure / velocity tag
     lmood::DevAllocs mem;
 };
 

@@ -360,10 +360,95 @@ __global__ void __launch_bounds__(kCellBlock, D == 2 ? 4 : 1) k_predict(Geo g, F
 
 // ---------------------------------------------------------------------------------------
 // k_nodes: Eucclhyd nodal solver (Eqs. nodal_solver^n, Mcp^n) with the BCs of Appendix B:
-// M_p = sum_c M_cp, b_p = sum_c rhs_cp in ascending cell id, v*_p the Galerkin solution of
-// M_p v = b_p on the node's free directions (Eq. sBC1); then x^{n+1} = x^n + dt v*_p and
-// v_p^{n+1} = 2 v*_p - v_p^n. init_mode stores v*_p as v_p^0 and moves nothing.
+// M_p = sum_c M_cp, b_p = sum_c rhs_cp in ascending cell id (plus the forces of traction and
+// pressure faces, Eq. pBC), v*_p the Galerkin solution of M_p v = b_p on the node's free
+// directions (Eq. sBC1), corrected along d_p to meet a prescribed normal velocity (Eqs. vBC1,
+// vBC); then x^{n+1} = x^n + dt v*_p and v_p^{n+1} = 2 v*_p - v_p^n. init_mode stores v*_p as
+// v_p^0 and moves nothing.
 // ---------------------------------------------------------------------------------------
+// Galerkin solve of M v = rhs on the node's free subspace (Eq. sBC1): nd = D free, 0 clamped,
+// else the span of the node's nd tangent vectors
+template <int D>
+__device__ __forceinline__ void solve_K(const Geo &g, const double (&M)[D * D], int nd, int p, const double (&rhs)[D],
+                                        double (&v)[D]) {
+    constexpr int DD = D * D;
+    const int Np = g.Np;
+    if (nd == D) {
+        double Mi[DD];
+        inverse<D>(M, Mi);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) s += Mi[a * D + c] * rhs[c];
+            v[a] = s;
+        }
+    } else if (nd == 0) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) v[a] = 0.0;
+    } else {
+        double t[2][D], A[4], r[2], al[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int a = 0; a < D; ++a) t[i][a] = g.bc_t[(i * 3 + a) * Np + p];
+        for (int i = 0; i < nd; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a < D; ++a) s += t[i][a] * rhs[a];
+            r[i] = s;
+            for (int j = 0; j < nd; ++j) {
+                double q = 0.0;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    double mt = 0.0;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) mt += M[a * D + c] * t[j][c];
+                    q += t[i][a] * mt;
+                }
+                A[i * nd + j] = q;
+            }
+        }
+        if (nd == 1) {
+            al[0] = r[0] / A[0];
+            al[1] = 0.0;
+        } else {
+            const double dA = A[0] * A[3] - A[1] * A[2];
+            al[0] = (A[3] / dA) * r[0] + (-A[1] / dA) * r[1];
+            al[1] = (-A[2] / dA) * r[0] + (A[0] / dA) * r[1];
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            double s = 0.0;
+            for (int i = 0; i < nd; ++i) s += al[i] * t[i][a];
+            v[a] = s;
+        }
+    }
+}
+
+// outward area vector of boundary face fid at positions x: 2D edge (q0, q1): (y1 - y0,
+// x0 - x1); 3D triangle: (1/2) (x1 - x0) x (x2 - x0)
+template <int D>
+__device__ __forceinline__ void face_area_vector(const Geo &g, const double *x, int fid, double (&N)[D]) {
+    const int Np = g.Np, nb = g.nbf;
+    if constexpr (D == 2) {
+        const int q0 = g.bf_nodes[fid], q1 = g.bf_nodes[nb + fid];
+        N[0] = x[Np + q1] - x[Np + q0];
+        N[1] = x[q0] - x[q1];
+    } else {
+        const int q0 = g.bf_nodes[fid], q1 = g.bf_nodes[nb + fid], q2 = g.bf_nodes[2 * nb + fid];
+        double u[3], w[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            u[a] = x[a * Np + q1] - x[a * Np + q0];
+            w[a] = x[a * Np + q2] - x[a * Np + q0];
+        }
+        N[0] = 0.5 * (u[1] * w[2] - u[2] * w[1]);
+        N[1] = 0.5 * (u[2] * w[0] - u[0] * w[2]);
+        N[2] = 0.5 * (u[0] * w[1] - u[1] * w[0]);
+    }
+}
+
 template <int D>
 __device__ __forceinline__ void node_solve(const Geo &g, const Fld &f, int p, int init_mode) {
     constexpr int NV = D + 1, NS = D * (D + 1) / 2, DD = D * D;
@@ -398,57 +483,58 @@ __device__ __forceinline__ void node_solve(const Geo &g, const Fld &f, int p, in
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int c = 0; c < D; ++c) M[a * D + c] = Ms[sidx<D>(a, c)];
-    const int nd = g.bc_ndof[p];
+    const int ndf = g.bc_ndof[p];
+    const int nd = ndf & ~BC_EXT;
     double v[D];
-    if (nd == D) {
-        double Mi[DD];
-        inverse<D>(M, Mi);
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            double s = 0.0;
-#pragma unroll
-            for (int c = 0; c < D; ++c) s += Mi[a * D + c] * b[c];
-            v[a] = s;
-        }
-    } else if (nd == 0) {
-#pragma unroll
-        for (int a = 0; a < D; ++a) v[a] = 0.0;
+    if (!(ndf & BC_EXT)) {
+        solve_K<D>(g, M, nd, p, b, v);
     } else {
-        double t[2][D], A[4], r[2], al[2];
+        // traction, pressure and prescribed-velocity faces around the node (Eqs. pBC, vBC1,
+        // vBC): N_f = outward area vector at x^n, the node's share N_f / D
+        double dv[D], gsum = 0.0;
+        int nvel = 0;
 #pragma unroll
-        for (int i = 0; i < 2; ++i)
+        for (int a = 0; a < D; ++a) dv[a] = 0.0;
+        for (int j = g.nbf_off[p]; j < g.nbf_off[p + 1]; ++j) {
+            const int fid = g.nbf_idx[j];
+            const int tag = g.bf_tag[fid];
+            if (tag < TAG_TRACTION) continue;
+            double N[D];
+            face_area_vector<D>(g, f.x, fid, N);
+            if (tag == TAG_TRACTION) {
+                double ar = 0.0;
 #pragma unroll
-            for (int a = 0; a < D; ++a) t[i][a] = g.bc_t[(i * 3 + a) * Np + p];
-        for (int i = 0; i < nd; ++i) {
-            double s = 0.0;
+                for (int a = 0; a < D; ++a) ar += N[a] * N[a];
+                ar = sqrt(ar) / D;
 #pragma unroll
-            for (int a = 0; a < D; ++a) s += t[i][a] * b[a];
-            r[i] = s;
-            for (int j = 0; j < nd; ++j) {
-                double q = 0.0;
+                for (int a = 0; a < D; ++a) b[a] += ar * g.bf_val[a * g.nbf + fid];
+            } else if (tag == TAG_PRESSURE) {
+                const double pr = g.bf_val[fid];
+#pragma unroll
+                for (int a = 0; a < D; ++a) b[a] -= pr * N[a] / D;
+            } else {
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
-                    double mt = 0.0;
-#pragma unroll
-                    for (int c = 0; c < D; ++c) mt += M[a * D + c] * t[j][c];
-                    q += t[i][a] * mt;
+                    dv[a] += N[a] / D;
+                    gsum += g.bf_val[a * g.nbf + fid] * N[a] / D;
                 }
-                A[i * nd + j] = q;
+                ++nvel;
             }
         }
-        if (nd == 1) {
-            al[0] = r[0] / A[0];
-            al[1] = 0.0;
-        } else {
-            const double dA = A[0] * A[3] - A[1] * A[2];
-            al[0] = (A[3] / dA) * r[0] + (-A[1] / dA) * r[1];
-            al[1] = (-A[2] / dA) * r[0] + (A[0] / dA) * r[1];
-        }
+        solve_K<D>(g, M, nd, p, b, v);
+        if (nvel > 0) {  // v = K b - T K d with v . d = g
+            double w[D], wd = 0.0, vd = 0.0;
+            solve_K<D>(g, M, nd, p, dv, w);
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            double s = 0.0;
-            for (int i = 0; i < nd; ++i) s += al[i] * t[i][a];
-            v[a] = s;
+            for (int a = 0; a < D; ++a) {
+                wd += w[a] * dv[a];
+                vd += v[a] * dv[a];
+            }
+            if (wd > 0.0) {
+                const double T = (vd - gsum) / wd;
+#pragma unroll
+                for (int a = 0; a < D; ++a) v[a] -= T * w[a];
+            }
         }
     }
 #pragma unroll
@@ -604,7 +690,7 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
         area1 += sqrt(s);
     }
     if (prm.mood) {
-        const int ps = pad_state<D>(v1, e1, F1, V1);
+        const int ps = pad_state<D>(v1, e1, F1, V1, (kap + (4.0 / 3.0) * muc) * prm.irho0);
         if (ord != 1) {
             bool bad = ps != 0;
             if (!bad) {
