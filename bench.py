@@ -226,6 +226,9 @@ def run_ours(args, rank, local, ws, dist):
     info = sim.mesh.info()
     for _ in range(args.warmup):
         sim.step()
+    tuned = None if args.no_autotune else sim.autotune()
+    for _ in range(2):  # re-capture the step graphs with the chosen launch shapes
+        sim.step()
     sim.timing(True)
     clocks = Clocks(local)
     barrier(dist)
@@ -321,7 +324,8 @@ def run_ours(args, rank, local, ws, dist):
                            "lsq_pairs": info["stencil_nnz"], "parallelism": f"replicas x{ws}",
                            "l2": "working set > L2 (no flush)", "troubled_cells_in_timed_steps": troubled},
                 "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": ck, "e2e": e2e,
-                "cpu_baseline": cb, "batched": batched, "adjoint": adjoint}
+                "cpu_baseline": cb, "batched": batched, "adjoint": adjoint,
+                "launch": None if tuned is None else {k: v["chosen"] for k, v in tuned.items()}}
         print(json.dumps(line), flush=True)
 
 
@@ -337,6 +341,9 @@ def run_batched(L, W, torch, local, plain_value, args) -> dict:
     sim = L.simulation(pb, stream=stream.cuda_stream, cell_inst=inst, n_inst=len(probs),
                        graph=0 if args.host_mode else 1)
     for _ in range(3):
+        sim.step()
+    if not args.no_autotune:
+        sim.autotune()
         sim.step()
     k = max(10, args.steps // 5)
     torch.cuda.synchronize()
@@ -443,6 +450,7 @@ def main():
     ap.add_argument("--no-fp64-peak", action="store_true", help="skip the DGEMM FP64 peak measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-instances measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-pass measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--adjoint-steps", type=int, default=400, help="steps recorded for the adjoint measurement")
     ap.add_argument("--case", type=int, default=0,
                     help="profiling case: build the workload, take this many untimed steps, exit")

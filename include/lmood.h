@@ -214,6 +214,17 @@ lmood_status lmood_mesh_info(lmood_mesh m, int64_t *out6);
  * lmood_timing(s, 1) resets and starts the per-class accumulators, lmood_timing(s, 0) stops.
  * lmood_timing_read fills ms[LMOOD_NK] (summed device time per class) and launches[LMOOD_NK]
  * (kernel launches per class since the last reset; counted whether or not timing is on). */
+/* Autotuning of the launch shapes: times the full-mesh kernels of the step with each
+ * candidate block size on the state's current fields (moments and nodes: 128, 256, 512
+ * threads; predictor and update: 64, 128, 256), reps launches each (<= 0: 5), with detection
+ * off, and keeps the fastest for the mesh (every state on it launches with them from then on;
+ * this state's captured step graphs are re-captured at its next step). The state's fields are
+ * not changed (only per-step scratch and the diagnostic fields VSTAR, PKM, PKR); results of
+ * later steps are bitwise the same as without tuning. ms12 (may be NULL) gets the mean
+ * times [4][3] (moments, predict, nodes, update x the candidates in the order above);
+ * chosen4 (may be NULL) the chosen sizes in the same kernel order. Synchronises. */
+lmood_status lmood_autotune(lmood_state s, int reps, double *ms12, int32_t *chosen4);
+
 enum { LMOOD_K_PREDICT = 0, LMOOD_K_NODES = 1, LMOOD_K_UPDATE = 2, LMOOD_K_MOOD = 3, LMOOD_K_FINALIZE = 4,
        LMOOD_K_MOMENTS = 5, LMOOD_NK = 6 };
 lmood_status lmood_timing(lmood_state s, int enable);

@@ -46,7 +46,8 @@ _lib = None
 EXPORTS = ("lmood_params_default", "lmood_mesh_create", "lmood_mesh_destroy", "lmood_mesh_info",
            "lmood_mesh_set_bc_values", "lmood_mesh_set_btag",
            "lmood_state_init", "lmood_state_destroy", "lmood_step", "lmood_run", "lmood_get", "lmood_set",
-           "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_totals_noalloc", "lmood_tape_record",
+           "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_autotune", "lmood_totals_noalloc",
+           "lmood_tape_record",
            "lmood_tape_backward", "lmood_tape_replay", "lmood_tape_info", "lmood_tape_destroy", "lmood_last_error")
 K_PREDICT, K_NODES, K_UPDATE, K_MOOD, K_FINALIZE, K_MOMENTS, NK = range(7)
 K_NAMES = ("predict", "nodes", "update", "mood", "finalize", "moments")
@@ -77,6 +78,7 @@ def lib():
         L.lmood_timing.argtypes = [vp, C.c_int]
         L.lmood_timing_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.lmood_totals_noalloc.argtypes = [C.c_int, C.c_int64, vp, vp, vp, vp, vp]
+        L.lmood_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
         L.lmood_tape_record.argtypes = [vp, C.c_int64, C.c_int64, C.POINTER(vp), C.POINTER(StepInfo)]
         L.lmood_tape_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
         L.lmood_tape_replay.argtypes = [vp, vp, C.c_int64]
@@ -234,6 +236,18 @@ class State:
         o = (C.c_double * 5)()
         _check(lib().lmood_totals(self.h, o))
         return np.array(list(o))
+
+    def autotune(self, reps: int = 5) -> dict:
+        """lmood_autotune: per kernel class the candidate block sizes' mean times (ms) and the
+        chosen size"""
+        ms = (C.c_double * 12)()
+        ch = (C.c_int32 * 4)()
+        _check(lib().lmood_autotune(self.h, reps, ms, ch))
+        cand = ((128, 256, 512), (64, 128, 256), (128, 256, 512), (64, 128, 256))
+        out = {}
+        for k, name in enumerate(("moments", "predict", "nodes", "update")):
+            out[name] = {"chosen": ch[k], "ms": {cand[k][v]: ms[k * 3 + v] for v in range(3)}}
+        return out
 
     def timing(self, enable: bool):
         _check(lib().lmood_timing(self.h, 1 if enable else 0))

@@ -938,6 +938,87 @@ extern "C" lmood_status lmood_totals(lmood_state s, double *out5) {
     return sync_check(s, "lmood_totals");
 }
 
+// the state's captured step graphs (re-captured at the next step)
+static void graphs_destroy(lmood_state s) {
+    for (int p = 0; p < 2; ++p) {
+        if (s->gexec[p]) cudaGraphExecDestroy(s->gexec[p]);
+        if (s->graph[p]) cudaGraphDestroy(s->graph[p]);
+        s->gexec[p] = nullptr;
+        s->graph[p] = nullptr;
+        for (cudaEvent_t &e : s->gev[p]) {
+            if (e) cudaEventDestroy(e);
+            e = nullptr;
+        }
+    }
+    s->graphs_built = false;
+}
+
+extern "C" lmood_status lmood_autotune(lmood_state s, int reps, double *ms12, int32_t *chosen4) {
+    if (!s) return fail(LMOOD_ERR_ARG, "lmood_autotune: NULL state");
+    if (s->broken) return fail(LMOOD_ERR_STATE, "lmood_autotune: state unusable after an earlier CUDA error");
+    if (reps <= 0) reps = 5;
+    lmood_mesh M = s->M;
+    const Ops &op = *M->ops;
+    cudaStream_t st = M->st;
+    Fld &f = s->f;
+    const int N = (int)M->nc, Np = (int)M->np;
+    // the kernels run on the state's current fields with their current orders and no
+    // detection: they only rewrite scratch (moments, packets, v*, candidate state)
+    Prm kt = s->kp;
+    kt.base_order = 0;
+    kt.mood = 0;
+    cudaEvent_t e0, e1;
+    LM_CUDA(cudaEventCreate(&e0));
+    LM_CUDA(cudaEventCreate(&e1));
+    const int cand[4][3] = {{128, 256, 512}, {64, 128, 256}, {128, 256, 512}, {64, 128, 256}};  // moments, predict, nodes, update
+    int *slot[4] = {&M->geo.blk.moments, &M->geo.blk.predict, &M->geo.blk.nodes, &M->geo.blk.update};
+    double times[4][3] = {};
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < 4 && err == cudaSuccess; ++k) {
+        int best = *slot[k];
+        double best_ms = 1e300;
+        for (int v = 0; v < 3 && err == cudaSuccess; ++v) {
+            *slot[k] = cand[k][v];
+            const Geo &g = M->geo;
+            auto launch = [&] {
+                switch (k) {
+                case 0: op.moments(g, f, st); break;
+                case 1: op.predict(g, f, kt, nullptr, nullptr, N, st); break;
+                case 2: op.nodes(g, f, nullptr, nullptr, Np, 0, st); break;
+                default: op.update(g, f, kt, nullptr, nullptr, N, s->tl[0], f.cnt + CNT_T0, st); break;
+                }
+            };
+            launch();  // warm
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < reps; ++r) launch();
+            cudaEventRecord(e1, st);
+            err = cudaEventSynchronize(e1);
+            if (err == cudaSuccess) err = cudaGetLastError();
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            times[k][v] = ms / reps;
+            if (times[k][v] < best_ms) {
+                best_ms = times[k][v];
+                best = cand[k][v];
+            }
+        }
+        *slot[k] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) {
+        s->broken = true;
+        return fail(LMOOD_ERR_CUDA, std::string("lmood_autotune: ") + cudaGetErrorString(err));
+    }
+    graphs_destroy(s);  // re-captured with the chosen launch shapes at the next step
+    if (ms12)
+        for (int k = 0; k < 4; ++k)
+            for (int v = 0; v < 3; ++v) ms12[k * 3 + v] = times[k][v];
+    if (chosen4)
+        for (int k = 0; k < 4; ++k) chosen4[k] = *slot[k];
+    return LMOOD_OK;
+}
+
 extern "C" lmood_status lmood_timing(lmood_state s, int enable) {
     if (!s) return fail(LMOOD_ERR_ARG, "lmood_timing: NULL state");
     if (enable && s->ev.empty()) {

@@ -25,8 +25,15 @@ struct Prm {
     int cascade;     // 2: P1 -> P0; 3: P1 -> P1 with Barth-Jespersen slopes -> P0
 };
 
+// threads per block of the full-mesh launches (autotuned per mesh; the arithmetic per cell or
+// node does not depend on it)
+struct Blk {
+    int predict = 128, update = 128, nodes = 256, moments = 256;
+};
+
 struct Geo {
     int N, Np, n_inst, nbf;
+    Blk blk;
     const int *c2n;
     const int *n2c_off, *n2c;
     const unsigned char *bc_ndof;  // free directions per node (D = free, 0 = clamped), | BC_EXT

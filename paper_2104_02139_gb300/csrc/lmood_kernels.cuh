@@ -36,7 +36,8 @@ constexpr int kListBlocks = 152 * 8;
 // moments of its D+1 nodes (reading of Sect. "Algorithm": stencil = cells sharing a node,
 // each neighbour weighted by the number of nodes it shares with the cell).
 // ---------------------------------------------------------------------------------------
-template <int D> __global__ void __launch_bounds__(kNodeBlock) k_moments(Geo g, Fld f) {
+// B: threads per block (a launch-shape variant chosen by the autotuner; same arithmetic)
+template <int D, int B = kNodeBlock> __global__ void __launch_bounds__(B) k_moments(Geo g, Fld f) {
     using Q = Dim<D>;
     constexpr int NS = Q::NS, NQ = Q::NQ, DD = D * D;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -345,8 +346,9 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
 
 // LISTED = false: one thread per cell of the whole mesh; true: a grid-stride loop over a
 // device-counted list (separate instances, so each gets its own register allocation)
-template <int D, bool LISTED>
-__global__ void __launch_bounds__(kCellBlock, D == 2 ? 4 : 1) k_predict(Geo g, Fld f, Prm prm, const int *__restrict__ list,
+// (the 2D bound keeps the register cap at 128 per thread for every block size B)
+template <int D, bool LISTED, int B = kCellBlock>
+__global__ void __launch_bounds__(B, D == 2 ? 512 / B : 1) k_predict(Geo g, Fld f, Prm prm, const int *__restrict__ list,
                                                         const int *__restrict__ cnt, int n) {
     if constexpr (!LISTED) {
         const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -552,8 +554,8 @@ __device__ __forceinline__ void node_solve(const Geo &g, const Fld &f, int p, in
     }
 }
 
-template <int D, bool LISTED>
-__global__ void __launch_bounds__(kNodeBlock) k_nodes(Geo g, Fld f, const int *__restrict__ list,
+template <int D, bool LISTED, int B = kNodeBlock>
+__global__ void __launch_bounds__(B) k_nodes(Geo g, Fld f, const int *__restrict__ list,
                                                       const int *__restrict__ cnt, int n, int init_mode) {
     if constexpr (!LISTED) {
         const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -717,8 +719,8 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
     f.dtc[c] = dtc;
 }
 
-template <int D, bool LISTED>
-__global__ void __launch_bounds__(kCellBlock) k_update(Geo g, Fld f, Prm prm, const int *__restrict__ list,
+template <int D, bool LISTED, int B = kCellBlock>
+__global__ void __launch_bounds__(B) k_update(Geo g, Fld f, Prm prm, const int *__restrict__ list,
                                                        const int *__restrict__ cnt, int n, int *tlist, int *tcnt) {
     if constexpr (!LISTED) {
         const int c = blockIdx.x * blockDim.x + threadIdx.x;

@@ -15,27 +15,53 @@ inline int grid_for(const int *list, int n, int b) {
     return list && g > kListBlocks ? kListBlocks : g;
 }
 
+// full-mesh launches take the mesh's autotuned block size (g.blk); list launches keep the default
 template <int D> void moments(const Geo &g, const Fld &f, cudaStream_t s) {
-    k_moments<D><<<blocks(g.Np, kNodeBlock), kNodeBlock, 0, s>>>(g, f);
+    switch (g.blk.moments) {
+    case 128: k_moments<D, 128><<<blocks(g.Np, 128), 128, 0, s>>>(g, f); break;
+    case 512: k_moments<D, 512><<<blocks(g.Np, 512), 512, 0, s>>>(g, f); break;
+    default: k_moments<D, 256><<<blocks(g.Np, 256), 256, 0, s>>>(g, f); break;
+    }
 }
 template <int D>
 void predict(const Geo &g, const Fld &f, const Prm &p, const int *list, const int *cnt, int n, cudaStream_t s) {
     if (n <= 0) return;
-    if (list) k_predict<D, true><<<grid_for(list, n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n);
-    else k_predict<D, false><<<blocks(n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n);
+    if (list) {
+        k_predict<D, true><<<grid_for(list, n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n);
+        return;
+    }
+    switch (g.blk.predict) {
+    case 64: k_predict<D, false, 64><<<blocks(n, 64), 64, 0, s>>>(g, f, p, list, cnt, n); break;
+    case 256: k_predict<D, false, 256><<<blocks(n, 256), 256, 0, s>>>(g, f, p, list, cnt, n); break;
+    default: k_predict<D, false, 128><<<blocks(n, 128), 128, 0, s>>>(g, f, p, list, cnt, n); break;
+    }
 }
 template <int D>
 void nodes(const Geo &g, const Fld &f, const int *list, const int *cnt, int n, int init_mode, cudaStream_t s) {
     if (n <= 0) return;
-    if (list) k_nodes<D, true><<<grid_for(list, n, kNodeBlock), kNodeBlock, 0, s>>>(g, f, list, cnt, n, init_mode);
-    else k_nodes<D, false><<<blocks(n, kNodeBlock), kNodeBlock, 0, s>>>(g, f, list, cnt, n, init_mode);
+    if (list) {
+        k_nodes<D, true><<<grid_for(list, n, kNodeBlock), kNodeBlock, 0, s>>>(g, f, list, cnt, n, init_mode);
+        return;
+    }
+    switch (g.blk.nodes) {
+    case 128: k_nodes<D, false, 128><<<blocks(n, 128), 128, 0, s>>>(g, f, list, cnt, n, init_mode); break;
+    case 512: k_nodes<D, false, 512><<<blocks(n, 512), 512, 0, s>>>(g, f, list, cnt, n, init_mode); break;
+    default: k_nodes<D, false, 256><<<blocks(n, 256), 256, 0, s>>>(g, f, list, cnt, n, init_mode); break;
+    }
 }
 template <int D>
 void update(const Geo &g, const Fld &f, const Prm &p, const int *list, const int *cnt, int n, int *tlist, int *tcnt,
             cudaStream_t s) {
     if (n <= 0) return;
-    if (list) k_update<D, true><<<grid_for(list, n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n, tlist, tcnt);
-    else k_update<D, false><<<blocks(n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n, tlist, tcnt);
+    if (list) {
+        k_update<D, true><<<grid_for(list, n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n, tlist, tcnt);
+        return;
+    }
+    switch (g.blk.update) {
+    case 64: k_update<D, false, 64><<<blocks(n, 64), 64, 0, s>>>(g, f, p, list, cnt, n, tlist, tcnt); break;
+    case 256: k_update<D, false, 256><<<blocks(n, 256), 256, 0, s>>>(g, f, p, list, cnt, n, tlist, tcnt); break;
+    default: k_update<D, false, 128><<<blocks(n, 128), 128, 0, s>>>(g, f, p, list, cnt, n, tlist, tcnt); break;
+    }
 }
 template <int D>
 void mark_nodes(const Geo &g, const Fld &f, const Prm &p, const int *tlist, const int *tcnt, int n, int *node_mark,
