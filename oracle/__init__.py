@@ -35,7 +35,7 @@ class Params(C.Structure):
     _fields_ = [("cfl", C.c_double), ("Cv", C.c_double), ("Ci", C.c_double),
                 ("delta0", C.c_double), ("delta1", C.c_double), ("dt_fixed", C.c_double),
                 ("max_mood_iters", C.c_int), ("order", C.c_int), ("mood", C.c_int),
-                ("vol_coeff", C.c_int), ("cascade", C.c_int)]
+                ("vol_coeff", C.c_int), ("cascade", C.c_int), ("shear_a", C.c_double)]
 
 
 class Info(C.Structure):
@@ -73,6 +73,9 @@ def lib():
         L.orc_stress.argtypes = [C.c_int, dp, C.c_double, C.c_double, dp]
         L.orc_free_energy.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double]
         L.orc_free_energy.restype = C.c_double
+        L.orc_stress_a.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double, dp]
+        L.orc_free_energy_a.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.orc_free_energy_a.restype = C.c_double
         L.orc_sound_speed.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double]
         L.orc_sound_speed.restype = C.c_double
         L.orc_mesh_stencil.argtypes = [C.c_void_p, C.c_long, np.ctypeslib.ndpointer(np.int64), C.c_long]
@@ -87,7 +90,7 @@ def lib():
 
 def default_params(cfl=0.4, **kw) -> Params:
     p = Params(cfl=cfl, Cv=0.2, Ci=0.1, delta0=1e-4, delta1=1e-3, dt_fixed=0.0,
-               max_mood_iters=100000, order=2, mood=1, vol_coeff=0, cascade=2)
+               max_mood_iters=100000, order=2, mood=1, vol_coeff=0, cascade=2, shear_a=-1.0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p
@@ -116,6 +119,20 @@ def free_energy(F, rho0, mu, kappa) -> float:
     return lib().orc_free_energy(F.shape[0], F.ravel(), rho0, mu, kappa)
 
 
+def stress_a(F: np.ndarray, mu: float, kappa: float, a: float) -> np.ndarray:
+    """stress of the shear energy family (Eq. familiy_energies) with parameter a"""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    d = F.shape[0]
+    T = np.zeros(d * d)
+    lib().orc_stress_a(d, F.ravel(), mu, kappa, a, T)
+    return T.reshape(d, d)
+
+
+def free_energy_a(F, rho0, mu, kappa, a) -> float:
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    return lib().orc_free_energy_a(F.shape[0], F.ravel(), rho0, mu, kappa, a)
+
+
 def sound_speed(F, rho, mu, kappa) -> float:
     F = np.ascontiguousarray(F, dtype=np.float64)
     return lib().orc_sound_speed(F.shape[0], F.ravel(), rho, mu, kappa)
@@ -141,6 +158,8 @@ class Oracle:
         self.d = m.dim
         self.nc, self.np = m.n_cells, m.n_nodes
         self.params = params or default_params(problem.cfl, **kw)
+        if params is None and "shear_a" not in kw:
+            self.params.shear_a = getattr(problem, "shear_a", -1.0)
         x = np.ascontiguousarray(m.x, dtype=np.float64)
         c2n = np.ascontiguousarray(m.c2n, dtype=np.int32)
         bf = np.ascontiguousarray(m.bface, dtype=np.int32)

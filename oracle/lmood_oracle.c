@@ -66,6 +66,11 @@
  *  R14 BCs: per node, clamped > slip > free; k independent slip planes leave the
  *      intersection subspace; the node velocity is the Galerkin solution of
  *      M_p v_p = b_p on that subspace (Eq. sBC1).
+ *  R16 shear energy family (Eq. familiy_energies, any a; a = -1 neo-Hookean, the default):
+ *      T = -p I + (mu/J) dev(c1 Bbar - c2 Bbar^2), c1 = -a + (1+a) I1 I2 / 3,
+ *      c2 = (1+a) I2 / 3 (the Cauchy stress of an isotropic energy of Bbar's invariants);
+ *      every member has shear modulus mu at small strain, so the impedance keeps the sound
+ *      speed of R4.
  *  R15 traction, pressure and prescribed-velocity faces (Eqs. pBC, vBC1, vBC), with N_f
  *      the face's outward area vector at x^n and each of its d nodes taking N_f / d:
  *      a traction vector t_f adds |N_f| t_f / d to b_p, a pressure p_f adds -p_f N_f / d
@@ -92,6 +97,7 @@ typedef struct {
     int mood;           /* 1: detection on; 0: unlimited (no detection)              */
     int vol_coeff;      /* 0: kappa = lambda + 2 mu / 3; 1: kappa = mu (printed)      */
     int cascade;        /* 2: P1 -> P0; 3: P1 -> P1 with Barth-Jespersen slopes -> P0     */
+    double shear_a;     /* a of the shear energy family (Eq. familiy_energies); -1: neo-Hookean */
 } OrcParams;
 
 typedef struct {
@@ -294,6 +300,47 @@ void orc_stress(int d, const double *F, double mu, double kappa, double *T) {
         for (int j = 0; j < d; ++j) T[i * d + j] = T3[i * 3 + j];
 }
 
+/* Cauchy stress of the shear energy family of Eq. familiy_energies (reading R16),
+ *   rho0 Psi_s = (mu/4) (-2a (I1 - 3) + (1+a)/3 (I2^2 - 9)),  I1, I2 the invariants of Bbar,
+ * with the volumetric part of Eq. EOS_neoHook: for an isotropic W(I1, I2) of Bbar,
+ * T = -p I + (2/J) dev((W_1 + I1 W_2) Bbar - W_2 Bbar^2), W_1 = -a mu/2, W_2 = (1+a) mu I2/6,
+ * i.e. T = -p I + (mu/J) dev(c1 Bbar - c2 Bbar^2), c1 = -a + (1+a) I1 I2/3, c2 = (1+a) I2/3.
+ * a = -1 is the neo-Hookean law of orc_stress. 2D is plane strain (F33 = 1). */
+void orc_stress_a(int d, const double *F, double mu, double kappa, double a, double *T) {
+    if (a == -1.0) {
+        orc_stress(d, F, mu, kappa, T);
+        return;
+    }
+    double F3[9], B[9], B2[9], T3[9];
+    embed3(d, F, F3);
+    double J = det_n(3, F3);
+    double Jm23 = pow(J, -2.0 / 3.0);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += F3[i * 3 + k] * F3[j * 3 + k];
+            B[i * 3 + j] = Jm23 * s;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += B[i * 3 + k] * B[k * 3 + j];
+            B2[i * 3 + j] = s;
+        }
+    double I1 = B[0] + B[4] + B[8], trB2 = B2[0] + B2[4] + B2[8];
+    double I2 = 0.5 * (I1 * I1 - trB2);
+    double c1 = -a + (1.0 + a) * I1 * I2 / 3.0, c2 = (1.0 + a) * I2 / 3.0;
+    double X[9], trX = 0.0;
+    for (int i = 0; i < 9; ++i) X[i] = c1 * B[i] - c2 * B2[i];
+    trX = X[0] + X[4] + X[8];
+    double p = -0.5 * kappa * (J - 1.0 + log(J) / J);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            T3[i * 3 + j] = (i == j ? -p : 0.0) + mu / J * (X[i * 3 + j] - (i == j ? trX / 3.0 : 0.0));
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) T[i * d + j] = T3[i * 3 + j];
+}
+
 /* specific free energy Psi = Psi_v + Psi_s (Eqs. EOS_neoHook and familiy_energies with
  * a = -1): Psi_v = kappa/(4 rho0) ((J-1)^2 + log^2 J), Psi_s = mu/(2 rho0) (I1(Bbar) - 3) */
 double orc_free_energy(int d, const double *F, double rho0, double mu, double kappa) {
@@ -305,6 +352,27 @@ double orc_free_energy(int d, const double *F, double rho0, double mu, double ka
     double I1bar = pow(J, -2.0 / 3.0) * trB;
     double lj = log(J);
     return kappa / (4.0 * rho0) * ((J - 1.0) * (J - 1.0) + lj * lj) + mu / (2.0 * rho0) * (I1bar - 3.0);
+}
+
+/* the same with the shear energy of Eq. familiy_energies for any a (reading R16) */
+double orc_free_energy_a(int d, const double *F, double rho0, double mu, double kappa, double a) {
+    if (a == -1.0) return orc_free_energy(d, F, rho0, mu, kappa);
+    double F3[9], B[9];
+    embed3(d, F, F3);
+    double J = det_n(3, F3);
+    double Jm23 = pow(J, -2.0 / 3.0);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += F3[i * 3 + k] * F3[j * 3 + k];
+            B[i * 3 + j] = Jm23 * s;
+        }
+    double I1 = B[0] + B[4] + B[8], trB2 = 0.0;
+    for (int i = 0; i < 9; ++i) trB2 += B[i] * B[i];  /* B symmetric: tr(B^2) = sum B_ij^2 */
+    double I2 = 0.5 * (I1 * I1 - trB2);
+    double lj = log(J);
+    return kappa / (4.0 * rho0) * ((J - 1.0) * (J - 1.0) + lj * lj) +
+           mu / (4.0 * rho0) * (-2.0 * a * (I1 - 3.0) + (1.0 + a) / 3.0 * (I2 * I2 - 9.0));
 }
 
 /* sound speed, reading R4: a^2 = (K + 4 mu / (3 J)) / rho, K = (kappa/2)(J + (1 - log J)/J) */
@@ -722,7 +790,7 @@ static void phase_packets(const OrcState *S, const int *order, double dt, Work *
                     Fh[k][i] = s;
                 }
                 double Tk[9], Tn[3];
-                orc_stress(d, Fh[k], S->mu[c], kap, Tk);
+                orc_stress_a(d, Fh[k], S->mu[c], kap, S->prm.shear_a, Tk);
                 matvec_n(d, Tk, ln + k * d, Tn);
                 for (int i = 0; i < d; ++i) dvdt[i] += Tn[i];
             }
@@ -732,11 +800,11 @@ static void phase_packets(const OrcState *S, const int *order, double dt, Work *
                 double Fs[9];
                 for (int i = 0; i < d; ++i) vstar[k][i] = vh[k][i] + 0.5 * dt * dvdt[i];
                 for (int i = 0; i < dd; ++i) Fs[i] = Fh[k][i] + 0.5 * dt * dFdt[i];
-                orc_stress(d, Fs, S->mu[c], kap, Tstar[k]);
+                orc_stress_a(d, Fs, S->mu[c], kap, S->prm.shear_a, Tstar[k]);
             }
         } else {
             double T0[9];
-            orc_stress(d, Fc, S->mu[c], kap, T0);
+            orc_stress_a(d, Fc, S->mu[c], kap, S->prm.shear_a, T0);
             for (int k = 0; k < nv; ++k) {
                 for (int i = 0; i < d; ++i) vstar[k][i] = vc[i];
                 memcpy(Tstar[k], T0, sizeof(double) * dd);
@@ -1125,7 +1193,7 @@ int orc_state_new(OrcMesh *M, double rho0, double lam, const double *mu_cell, co
         S->tau[c] = w.V[c] / S->m[c];
         double ke = 0.0;
         for (int i = 0; i < d; ++i) ke += 0.5 * S->v[c * d + i] * S->v[c * d + i];
-        S->e[c] = ke + orc_free_energy(d, S->F + c * dd, rho0, S->mu[c], kappa_of(S, c));
+        S->e[c] = ke + orc_free_energy_a(d, S->F + c * dd, rho0, S->mu[c], kappa_of(S, c), S->prm.shear_a);
         dt0 = fmin(dt0, dt_acoustic_cell(S, c, S->F + c * dd, w.V[c], w.Lc[c]));
     }
     /* v_p^0: first-order nodal solve at t^0 */

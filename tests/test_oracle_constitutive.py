@@ -1,9 +1,13 @@
 """Pins of the oracle's geometry and constitutive functions against closed forms, finite
 differences of independently written energies, and identities the paper states."""
+import dataclasses
 import math
 
 import numpy as np
 import pytest
+
+import oracle as O
+import workloads as W
 
 
 # ----------------------------------------------------------------------------- geometry
@@ -153,3 +157,80 @@ def test_sound_speed(orc):
     K = -J * (p(J + 1e-6) - p(J - 1e-6)) / 2e-6
     a = orc.sound_speed(s * np.eye(3), rho, mu, kappa)
     assert a * a * rho == pytest.approx(K + 4 * mu / (3 * J), rel=1e-8)
+
+
+# ----------------------------------------------------------------------------- energy family
+def _W_family(F, mu, kappa, a):
+    """rho0 Psi of Eqs. EOS_neoHook and familiy_energies for parameter a, written with numpy
+    from the invariants of Bbar = J^{-2/3} F F^t (plane strain in 2D), independently of the
+    oracle's C code"""
+    d = F.shape[0]
+    F3 = np.eye(3)
+    F3[:d, :d] = F
+    J = np.linalg.det(F3)
+    Bb = J ** (-2 / 3) * F3 @ F3.T
+    I1 = np.trace(Bb)
+    I2 = 0.5 * (I1 ** 2 - np.trace(Bb @ Bb))
+    return kappa / 4 * ((J - 1) ** 2 + np.log(J) ** 2) + mu / 4 * (-2 * a * (I1 - 3) + (1 + a) / 3 * (I2 ** 2 - 9))
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("a", [-1.0, 0.0, 0.4])
+def test_energy_family_stress_is_energy_derivative(d, a):
+    """T = (1/J) P F^t with P = d(rho0 Psi)/dF by central differences of the independently
+    written energy of the family; a = -1 reproduces the neo-Hookean stress exactly."""
+    rng = np.random.default_rng(21 + d)
+    mu, kappa, rho0 = 1.3, 2.7, 1.9
+    for _ in range(8):
+        F = _rand_F(rng, d)
+        P = np.zeros((d, d))
+        h = 1e-6
+        for i in range(d):
+            for j in range(d):
+                Fp = F.copy(); Fp[i, j] += h
+                Fm = F.copy(); Fm[i, j] -= h
+                P[i, j] = (_W_family(Fp, mu, kappa, a) - _W_family(Fm, mu, kappa, a)) / (2 * h)
+        T_fd = P @ F.T / np.linalg.det(F)
+        T = O.stress_a(F, mu, kappa, a)
+        np.testing.assert_allclose(T, T_fd, rtol=0, atol=2e-8 * (1 + np.abs(T).max()))
+        assert O.free_energy_a(F, rho0, mu, kappa, a) * rho0 == pytest.approx(_W_family(F, mu, kappa, a),
+                                                                              rel=1e-12, abs=1e-14)
+        if a == -1.0:
+            assert np.array_equal(T, O.stress(F, mu, kappa))
+
+
+@pytest.mark.parametrize("a", [0.0, 0.4])
+def test_energy_family_small_strain_shear_modulus_is_mu(a):
+    """Every member of the family has shear modulus mu and bulk modulus kappa at small strain:
+    T = 2 mu dev(E) + kappa tr(E) I + O(|E|^2), E the small strain (3D)."""
+    rng = np.random.default_rng(3)
+    mu, kappa = 0.8, 2.1
+    G = rng.normal(size=(3, 3))
+    for eps in (1e-4, 1e-5):
+        F = np.eye(3) + eps * G
+        E = 0.5 * (F + F.T) - np.eye(3)
+        T_lin = 2 * mu * (E - np.trace(E) / 3 * np.eye(3)) + kappa * np.trace(E) * np.eye(3)
+        T = O.stress_a(F, mu, kappa, a)
+        assert np.abs(T - T_lin).max() < 50 * eps ** 2 * (mu + kappa)
+
+
+def test_energy_family_scheme_conserves_energy():
+    """a = 0 through the whole scheme: an initially strained block at rest in slip walls
+    conserves total energy (which starts from the family's free energy) and stays different
+    from the neo-Hookean run."""
+    m = W.tri_mesh(10, 2, bc={k: W.SLIP for k in ("x0", "x1", "y0", "y1")})
+    rng = np.random.default_rng(5)
+    F = np.zeros((4, m.n_cells))
+    F[0] = 1.0 + 0.02 * rng.standard_normal(m.n_cells)
+    F[3] = 1.0 + 0.02 * rng.standard_normal(m.n_cells)
+    pb = W.Problem("fam", m, 1.0, 2.0, np.full(m.n_cells, 1.0), np.zeros((2, m.n_cells)), 0.4, 10, F=F)
+    o0 = O.Oracle(dataclasses.replace(pb, shear_a=0.0))
+    o1 = O.Oracle(pb)
+    e0 = (o0.get(O.F_MASS) * o0.get(O.F_E)).sum()
+    assert e0 != (o1.get(O.F_MASS) * o1.get(O.F_E)).sum()
+    for _ in range(10):
+        o0.step()
+        o1.step()
+    e1 = (o0.get(O.F_MASS) * o0.get(O.F_E)).sum()
+    assert abs(e1 - e0) <= 1e-12 * abs(e0)
+    assert np.abs(o0.get(O.F_V) - o1.get(O.F_V)).max() > 1e-6

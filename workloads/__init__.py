@@ -62,6 +62,7 @@ class Problem:
     meta: dict = field(default_factory=dict)
     bcval: np.ndarray | None = None  # [dim, n_bfaces] boundary-face values (traction vector,
                                      # pressure in row 0, prescribed velocity) or None
+    shear_a: float = -1.0            # a of the shear energy family; -1 neo-Hookean
 
 
 # ----------------------------------------------------------------------------- ordering
