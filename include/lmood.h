@@ -49,12 +49,16 @@ typedef enum {
  * per cell to lmood_state_init. Volumetric free energy
  *   Psi_v = kappa / (4 rho0) ((J - 1)^2 + (log J)^2)          (Eq. EOS_neoHook)
  * with kappa = lambda + 2 mu / 3 when vol_coeff = 0 (small-strain bulk modulus), or
- * kappa = mu when vol_coeff = 1 (the coefficient as printed). */
+ * kappa = mu when vol_coeff = 1 (the coefficient as printed). Shear free energy of the family
+ *   Psi_s = mu / (4 rho0) (-2a (I1 - 3) + (1+a)/3 (I2^2 - 9))   (Eq. familiy_energies)
+ * with I1, I2 the invariants of J^{-2/3} F F^t; a = -1 (neo-Hookean) is the default and the
+ * fastest path; a must lie in [-1, 1/2], where the paper states the system is hyperbolic. */
 typedef struct {
     double rho0;     /* initial density (> 0)                 */
     double lambda;   /* first Lame coefficient                */
     int32_t vol_coeff;
     int32_t reserved;
+    double shear_a;  /* a of the shear energy family (-1: neo-Hookean) */
 } lmood_material;
 
 /* Scheme parameters (Sect. "Time-step monitoring", "Limiting: a posteriori MOOD loop"). */
@@ -254,8 +258,8 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  * (x, v_p per node; v, F per cell) and of the per-cell mu; the adjoint is the exact transpose
  * of its linearisation, written by hand kernel by kernel (no atomics, deterministic).
  * Only the two-level cascade (P1 -> P0) is differentiated: a recorded step that used the
- * limited level returns LMOOD_ERR_ARG, and so does a mesh with traction, pressure or
- * prescribed-velocity faces. Energy e has no influence on the other fields, so it
+ * limited level returns LMOOD_ERR_ARG, and so do a mesh with traction, pressure or
+ * prescribed-velocity faces and a shear energy other than the neo-Hookean one (a = -1). Energy e has no influence on the other fields, so it
  * carries no adjoint.
  *
  * lmood_tape_record: runs n_steps ordinary lmood_step calls on s (the forward pass, with the

@@ -26,7 +26,8 @@ class LmoodError(RuntimeError):
 
 
 class Material(C.Structure):
-    _fields_ = [("rho0", C.c_double), ("lambda_", C.c_double), ("vol_coeff", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("rho0", C.c_double), ("lambda_", C.c_double), ("vol_coeff", C.c_int32), ("reserved", C.c_int32),
+                ("shear_a", C.c_double)]
 
 
 class Params(C.Structure):
@@ -174,10 +175,11 @@ class Mesh:
 class State:
     """lmood_state_init / step / run / get / set / totals / destroy."""
 
-    def __init__(self, mesh: Mesh, rho0, lam, mu, v, F=None, params: Params | None = None, vol_coeff=0):
+    def __init__(self, mesh: Mesh, rho0, lam, mu, v, F=None, params: Params | None = None, vol_coeff=0,
+                 shear_a=-1.0):
         self.mesh = mesh
         self.params = params or params_default(mesh.dim)
-        mat = Material(rho0=rho0, lambda_=lam, vol_coeff=vol_coeff)
+        mat = Material(rho0=rho0, lambda_=lam, vol_coeff=vol_coeff, shear_a=shear_a)
         mu = _host(mu, np.float64)
         v = _host(v, np.float64)
         F = _host(F, np.float64)
@@ -348,7 +350,8 @@ def rollout(problem, n_steps: int, v0, mu, F0=None, checkpoint_every: int = 0, *
             for k, v in params.items():
                 setattr(p, k, v)
             Fh = None if F0_ is None else F0_.detach().cpu().numpy()
-            state = State(mesh, pb.rho0, pb.lam, mu_.detach().cpu().numpy(), v0_.detach().cpu().numpy(), Fh, p)
+            state = State(mesh, pb.rho0, pb.lam, mu_.detach().cpu().numpy(), v0_.detach().cpu().numpy(), Fh, p,
+                          shear_a=getattr(pb, "shear_a", -1.0))
             tape = Tape(state, n_steps, checkpoint_every)
             outs = []
             for fid in (FIELD_X, FIELD_VP, FIELD_V, FIELD_F):
@@ -383,4 +386,5 @@ def simulation(problem, stream=None, cell_inst=None, n_inst=1, **params) -> Stat
     p = params_default(m.dim, cfl=problem.cfl)
     for k, v in params.items():
         setattr(p, k, v)
-    return State(mesh, problem.rho0, problem.lam, problem.mu, problem.v, problem.F, p)
+    return State(mesh, problem.rho0, problem.lam, problem.mu, problem.v, problem.F, p,
+                 shear_a=getattr(problem, "shear_a", -1.0))

@@ -462,6 +462,7 @@ static Prm kernel_params(const lmood_params &p, const lmood_material &m) {
     k.dt_fixed = p.dt_fixed;
     k.lam = m.lambda;
     k.irho0 = 1.0 / m.rho0;
+    k.shear_a = m.shear_a;
     k.base_order = p.order == 1 ? 1 : 2;
     k.mood = p.mood ? 1 : 0;
     k.vol_coeff = m.vol_coeff ? 1 : 0;
@@ -510,6 +511,8 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
     *out = nullptr;
     if (!M || !mat || !mu_cell || !v_cell || !prm) return fail(LMOOD_ERR_ARG, "lmood_state_init: NULL argument");
     if (!(mat->rho0 > 0)) return fail(LMOOD_ERR_ARG, "lmood_state_init: rho0 must be positive");
+    if (!(mat->shear_a >= -1.0 && mat->shear_a <= 0.5))
+        return fail(LMOOD_ERR_ARG, "lmood_state_init: shear_a must lie in [-1, 1/2]");
     if (!(prm->cfl > 0) || prm->max_mood_iters < 0 || (prm->order != 1 && prm->order != 2) ||
         (prm->cascade != 2 && prm->cascade != 3))
         return fail(LMOOD_ERR_ARG, "lmood_state_init: bad parameters");

@@ -19,6 +19,7 @@ namespace lmood {
 struct Prm {
     double cfl, Cv, Ci, delta0, delta1, dt_fixed, lam;
     double irho0;    // 1 / rho0
+    double shear_a;  // a of the shear energy family (Eq. familiy_energies); -1: neo-Hookean
     int base_order;  // order every cell starts the step with (2: P1, 1: P0; 0: keep f.order)
     int mood;        // detection on/off
     int vol_coeff;   // 0: kappa = lambda + 2 mu / 3; 1: kappa = mu
@@ -286,6 +287,54 @@ __device__ __forceinline__ void stress(const double (&F)[D * D], double mu, doub
         for (int j = 0; j < D; ++j) T[i * D + j] = cj * B[i * D + j] + (i == j ? diag : 0.0);
 }
 
+// Cauchy stress of the shear energy family (Eq. familiy_energies) for a != -1, with the
+// volumetric part of Eq. EOS_neoHook: T = -p I + (mu/J) dev(c1 Bbar - c2 Bbar^2),
+// c1 = -a + (1+a) I1 I2 / 3, c2 = (1+a) I2 / 3, I1 = tr Bbar, I2 = (I1^2 - tr Bbar^2) / 2,
+// evaluated on the 3x3 embedding (2D plane strain, F33 = 1).
+template <int D>
+__device__ __forceinline__ void stress_family(const double (&F)[D * D], double mu, double kappa, double a,
+                                           double (&T)[D * D]) {
+    double F3[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) F3[i * 3 + j] = (i < D && j < D) ? F[i * D + j] : (i == j ? 1.0 : 0.0);
+    const double J = F3[0] * (F3[4] * F3[8] - F3[5] * F3[7]) - F3[1] * (F3[3] * F3[8] - F3[5] * F3[6]) +
+                     F3[2] * (F3[3] * F3[7] - F3[4] * F3[6]);
+    const double rc = rcbrt_j(J), Jm23 = rc * rc, invJ = Jm23 * rc;
+    double B[9], B2[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s += F3[i * 3 + k] * F3[j * 3 + k];
+            B[i * 3 + j] = Jm23 * s;
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s += B[i * 3 + k] * B[k * 3 + j];
+            B2[i * 3 + j] = s;
+        }
+    const double I1 = B[0] + B[4] + B[8], I2 = 0.5 * (I1 * I1 - (B2[0] + B2[4] + B2[8]));
+    const double c1 = -a + (1.0 + a) * I1 * I2 * (1.0 / 3.0), c2 = (1.0 + a) * I2 * (1.0 / 3.0);
+    double X[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) X[i] = c1 * B[i] - c2 * B2[i];
+    const double trX = X[0] + X[4] + X[8];
+    const double p = -0.5 * kappa * (J - 1.0 + log_j(J) * invJ);
+    const double coef = mu * invJ;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) T[i * D + j] = coef * (X[i * 3 + j] - (i == j ? trX * (1.0 / 3.0) : 0.0)) - (i == j ? p : 0.0);
+}
+
 // acoustic impedance z = rho a with a^2 = (K + 4 mu / (3 J)) / rho, K = -J dp/dJ =
 // (kappa/2)(J + (1 - log J)/J): z = sqrt(rho (K + 4 mu / (3 J)))
 template <int D>
@@ -307,6 +356,36 @@ __device__ __forceinline__ double free_energy(const double (&F)[D * D], double r
     const double rc = rcbrt_j(J);
     const double I1bar = rc * rc * trB;
     return kappa / (4.0 * rho0) * ((J - 1.0) * (J - 1.0) + lJ * lJ) + mu / (2.0 * rho0) * (I1bar - 3.0);
+}
+
+// the same with the shear energy of the family (a != -1)
+template <int D>
+__device__ __noinline__ double free_energy_family(const double (&F)[D * D], double rho0, double mu, double kappa,
+                                                  double a) {
+    double F3[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) F3[i * 3 + j] = (i < D && j < D) ? F[i * D + j] : (i == j ? 1.0 : 0.0);
+    const double J = F3[0] * (F3[4] * F3[8] - F3[5] * F3[7]) - F3[1] * (F3[3] * F3[8] - F3[5] * F3[6]) +
+                     F3[2] * (F3[3] * F3[7] - F3[4] * F3[6]);
+    const double rc = rcbrt_j(J), Jm23 = rc * rc;
+    double B[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s += F3[i * 3 + k] * F3[j * 3 + k];
+            B[i * 3 + j] = Jm23 * s;
+        }
+    double I1 = B[0] + B[4] + B[8], trB2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) trB2 += B[i] * B[i];
+    const double I2 = 0.5 * (I1 * I1 - trB2), lJ = log_j(J);
+    return kappa / (4.0 * rho0) * ((J - 1.0) * (J - 1.0) + lJ * lJ) +
+           mu / (4.0 * rho0) * (-2.0 * a * (I1 - 3.0) + (1.0 + a) * (1.0 / 3.0) * (I2 * I2 - 9.0));
 }
 
 __device__ __forceinline__ double kappa_of(const Prm &prm, double mu) {

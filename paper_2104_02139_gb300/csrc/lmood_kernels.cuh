@@ -96,7 +96,16 @@ template <int D, int B = kNodeBlock> __global__ void __launch_bounds__(B) k_mome
     }
 }
 
-template <int D, bool LISTED>
+// FAM: a shear energy of the family other than the neo-Hookean one (separate instances, so the
+// neo-Hookean kernels are compiled as if the family did not exist)
+template <int D, bool LISTED, bool FAM>
+__device__ __forceinline__ void cell_stress(const Prm &prm, const double (&F)[D * D], double mu, double kappa,
+                                            double (&T)[D * D]) {
+    if constexpr (FAM) stress_family<D>(F, mu, kappa, prm.shear_a, T);
+    else stress<D>(F, mu, kappa, T);
+}
+
+template <int D, bool LISTED, bool FAM = false>
 __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const Prm &prm, int c) {
     constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + DD;
     const int N = g.N, Np = g.Np, NC = NV * N;
@@ -290,7 +299,7 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
                 Fh[q] = s;
                 if constexpr (D == 2) Fhk[k][q] = s;
             }
-            stress<D>(Fh, muc, kap, T);
+            cell_stress<D, LISTED, FAM>(prm, Fh, muc, kap, T);
 #pragma unroll
             for (int i = 0; i < D; ++i) {
                 double s = 0.0;
@@ -333,12 +342,12 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
                 }
                 Fs[q] = fma(0.5 * dt, dFdt[q], s);
             }
-            stress<D>(Fs, muc, kap, T);
+            cell_stress<D, LISTED, FAM>(prm, Fs, muc, kap, T);
             emit(k, vst, T);
         }
     } else {
         double T[DD];
-        stress<D>(Fc, muc, kap, T);
+        cell_stress<D, LISTED, FAM>(prm, Fc, muc, kap, T);
 #pragma unroll
         for (int k = 0; k < NV; ++k) emit(k, vc, T);
     }
@@ -347,16 +356,16 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
 // LISTED = false: one thread per cell of the whole mesh; true: a grid-stride loop over a
 // device-counted list (separate instances, so each gets its own register allocation)
 // (the 2D bound keeps the register cap at 128 per thread for every block size B)
-template <int D, bool LISTED, int B = kCellBlock>
+template <int D, bool LISTED, int B = kCellBlock, bool FAM = false>
 __global__ void __launch_bounds__(B, D == 2 ? 512 / B : 1) k_predict(Geo g, Fld f, Prm prm, const int *__restrict__ list,
                                                         const int *__restrict__ cnt, int n) {
     if constexpr (!LISTED) {
         const int c = blockIdx.x * blockDim.x + threadIdx.x;
-        if (c < n) predict_cell<D, false>(g, f, prm, c);
+        if (c < n) predict_cell<D, false, FAM>(g, f, prm, c);
     } else {
         const int nn = *cnt;
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
-            predict_cell<D, true>(g, f, prm, list[i]);
+            predict_cell<D, true, FAM>(g, f, prm, list[i]);
     }
 }
 
@@ -934,7 +943,8 @@ __global__ void __launch_bounds__(kCellBlock) k_init_cells(Geo g, Fld f, Prm prm
         const double va = f.v[a * N + c];
         ke += 0.5 * va * va;
     }
-    f.e[c] = ke + free_energy<D>(F, rho0, muc, kap);
+    f.e[c] = ke + (prm.shear_a == -1.0 ? free_energy<D>(F, rho0, muc, kap)
+                                       : free_energy_family<D>(F, rho0, muc, kap, prm.shear_a));
     f.order[c] = 1;
     f.pflag[c] = 0;
     const double z = impedance<D>(F, rho, muc, kap);
