@@ -85,6 +85,7 @@ def lib():
         L.orc_mesh_bc_ndof.restype = C.c_int
         L.orc_mesh_set_bc_values.argtypes = [C.c_void_p, dp]
         L.orc_mesh_set_btag.argtypes = [C.c_void_p, ip]
+        L.orc_mesh_set_contact.argtypes = [C.c_void_p, C.c_int, dp, C.c_double]
     return _lib
 
 
@@ -174,6 +175,11 @@ class Oracle:
         bcval = getattr(problem, "bcval", None)
         if bcval is not None:
             L.orc_mesh_set_bc_values(hm, np.ascontiguousarray(bcval, dtype=np.float64).ravel())
+        contact = getattr(problem, "contact", None)
+        if contact is not None:
+            planes, eps = contact
+            pl = np.ascontiguousarray(planes, dtype=np.float64).ravel()
+            L.orc_mesh_set_contact(hm, len(planes), pl, eps)
         hs = C.c_void_p()
         mu = np.ascontiguousarray(problem.mu, dtype=np.float64)
         v = np.ascontiguousarray(problem.v, dtype=np.float64)
@@ -253,6 +259,13 @@ class Oracle:
         rc = lib().orc_mesh_set_bc_values(self._h.mesh, np.ascontiguousarray(values, dtype=np.float64).ravel())
         if rc:
             raise OracleError(f"orc_mesh_set_bc_values: {ERR.get(rc, rc)}")
+
+    def set_contact(self, planes, eps):
+        """contact walls [n][2d] (point, unit normal into the body) and threshold eps"""
+        pl = np.ascontiguousarray(planes, dtype=np.float64).ravel()
+        rc = lib().orc_mesh_set_contact(self._h.mesh, len(planes), pl, eps)
+        if rc:
+            raise OracleError(f"orc_mesh_set_contact: {ERR.get(rc, rc)}")
 
     def set_btag(self, btag):
         """new boundary-face tags [n_bfaces]; per-node conditions re-derived"""

@@ -66,6 +66,12 @@
  *  R14 BCs: per node, clamped > slip > free; k independent slip planes leave the
  *      intersection subspace; the node velocity is the Galerkin solution of
  *      M_p v_p = b_p on that subspace (Eq. sBC1).
+ *  R17 boundary conditions that change type by a distance function (Sect. "Boundary
+ *      condition treatments"): faces tagged 6 are traction-free, but a node of such a face
+ *      whose distance to a contact wall (a plane) is below eps at x^n and whose nodal
+ *      velocity (after the other conditions) points into the wall gets v*_p . n = 0 for the
+ *      step, with the multiplier of R15 (d = n, g = 0): the wall does no work; the node
+ *      detaches when its velocity points away from the wall again.
  *  R16 shear energy family (Eq. familiy_energies, any a; a = -1 neo-Hookean, the default):
  *      T = -p I + (mu/J) dev(c1 Bbar - c2 Bbar^2), c1 = -a + (1+a) I1 I2 / 3,
  *      c2 = (1+a) I2 / 3 (the Cauchy stress of an isotropic energy of Bbar's invariants);
@@ -122,10 +128,14 @@ typedef struct {
     int *bf_nodes;         /* [nb][d] face nodes, ordered so that the face's area vector
                               points out of the mesh (reading R15)                     */
     int *bf_tag;           /* [nb] 0 free, 1 slip, 2 clamped, 3 traction, 4 pressure,
-                              5 prescribed velocity                                     */
+                              5 prescribed velocity, 6 contact (free until it touches a
+                              contact wall)                                             */
     double *bf_val;        /* [nb][d] traction vector / pressure (first entry) /
                               prescribed velocity vector; zero until set               */
     long *nbf_off, *nbf_idx; /* boundary faces around each node, ascending face id     */
+    int n_contact;         /* contact walls for faces tagged 6 (reading R17)          */
+    double contact[4][6];  /* point, unit normal from the wall into the body          */
+    double contact_eps;    /* distance threshold                                      */
 } OrcMesh;
 
 typedef struct {
@@ -583,7 +593,7 @@ int orc_mesh_new(int d, long np, const double *x_soa, long nc, const int *c2n_so
             fn[a] = bf_soa[a * nb + b];
             if (fn[a] < 0 || fn[a] >= np) { orc_mesh_free(M); return ORC_ERR_MESH; }
         }
-        if (btag[b] < 0 || btag[b] > 5) { orc_mesh_free(M); return ORC_ERR_ARG; }
+        if (btag[b] < 0 || btag[b] > 6) { orc_mesh_free(M); return ORC_ERR_ARG; }
         M->bf_tag[b] = btag[b];
         long owner = -1;
         int opp = -1;
@@ -899,7 +909,7 @@ static void node_solve_one(const OrcMesh *M, const double *x, const double *pkM,
             for (int a = 0; a < d; ++a) bp[a] += area / d * val[a];
         } else if (tag == 4) {
             for (int a = 0; a < d; ++a) bp[a] -= val[0] * N[a] / d;
-        } else {
+        } else if (tag == 5) {
             for (int a = 0; a < d; ++a) {
                 dp[a] += N[a] / d;
                 gp += val[a] * N[a] / d;
@@ -919,6 +929,28 @@ static void node_solve_one(const OrcMesh *M, const double *x, const double *pkM,
         if (wd > 0.0) {
             double T = (vd - gp) / wd;
             for (int a = 0; a < d; ++a) vs[a] -= T * w[a];
+        }
+    }
+    /* contact walls (reading R17): a node of a contact face closer than eps to a wall and
+     * moving into it gets v . n = 0 for the step, through the same multiplier as above */
+    int contact = 0;
+    for (long j = M->nbf_off[p]; j < M->nbf_off[p + 1]; ++j) contact |= M->bf_tag[M->nbf_idx[j]] == 6;
+    if (contact) {
+        for (int k = 0; k < M->n_contact; ++k) {
+            const double *P = M->contact[k], *n = M->contact[k] + d;
+            double dist = 0.0, vn = 0.0;
+            for (int a = 0; a < d; ++a) {
+                dist += n[a] * (x[p * d + a] - P[a]);
+                vn += n[a] * vs[a];
+            }
+            if (!(dist < M->contact_eps && vn < 0.0)) continue;
+            double w[3], wn = 0.0;
+            solve_K(M, Mp, p, n, w);
+            for (int a = 0; a < d; ++a) wn += w[a] * n[a];
+            if (wn > 0.0) {
+                double T = vn / wn;
+                for (int a = 0; a < d; ++a) vs[a] -= T * w[a];
+            }
         }
     }
 }
@@ -1310,12 +1342,24 @@ int orc_mesh_set_bc_values(OrcMesh *M, const double *val_soa) {
     return ORC_OK;
 }
 
+/* contact walls for the faces tagged 6: n (<= 4) planes [n][2d] (a point, then the unit
+ * normal pointing from the wall into the body) and the distance threshold eps */
+int orc_mesh_set_contact(OrcMesh *M, int n, const double *planes, double eps) {
+    if (!M || n < 0 || n > 4 || (n > 0 && !planes) || !(eps >= 0.0)) return ORC_ERR_ARG;
+    int d = M->d;
+    M->n_contact = n;
+    M->contact_eps = eps;
+    for (int k = 0; k < n; ++k)
+        for (int i = 0; i < 2 * d; ++i) M->contact[k][i] = planes[k * 2 * d + i];
+    return ORC_OK;
+}
+
 /* new tags of the boundary faces [nb] (a boundary condition that changes type during the
  * run, Sect. "Boundary condition treatments"); the per-node conditions are re-derived */
 int orc_mesh_set_btag(OrcMesh *M, const int *btag) {
     if (!M || !btag) return ORC_ERR_ARG;
     for (long b = 0; b < M->nb; ++b)
-        if (btag[b] < 0 || btag[b] > 5) return ORC_ERR_ARG;
+        if (btag[b] < 0 || btag[b] > 6) return ORC_ERR_ARG;
     for (long b = 0; b < M->nb; ++b) M->bf_tag[b] = btag[b];
     resolve_bcs(M);
     return ORC_OK;

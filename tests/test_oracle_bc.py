@@ -1,12 +1,14 @@
 """Pins of the oracle's traction, pressure and prescribed-velocity boundary conditions
-(Appendix B, Eqs. pBC, vBC1, vBC; reading R15) and of boundary conditions that change type
-during a run (Sect. "Boundary condition treatments"). CPU only.
+(Appendix B, Eqs. pBC, vBC1, vBC; reading R15), of boundary conditions that change type
+during a run and of contact walls (Sect. "Boundary condition treatments"; reading R17). CPU
+only.
 
 Each pin is fixed by mechanics, not by the oracle's own formulas: a uniformly stressed block
 held by the matching pressure stays at rest; the momentum a free block gains equals the
 impulse of the applied tractions; the energy it gains equals their work on the nodes; a
 prescribed normal velocity is met exactly at every node of the face, corners with a slip wall
-included; a block translating with the piston's velocity stays a rigid translation.
+included; a block translating with the piston's velocity stays a rigid translation; a block
+rebounding from a contact wall keeps its energy and never reaches the wall.
 """
 import dataclasses
 
@@ -154,3 +156,48 @@ def test_boundary_tags_can_change_during_a_run():
     assert np.abs(o.get(O.F_VSTAR)[:, wall]).max() == 0.0
     with pytest.raises(O.OracleError):
         o.set_btag(np.full(pb.mesh.btag.size, 7))
+
+
+def test_contact_wall_rebound():
+    """A block flying at a wall through its contact face (reading R17): free flight until the
+    face comes within eps of the wall, no node closer than the capture distance minus one
+    step's travel, total energy conserved to round-off (the wall does no work), the normal
+    momentum reversed, and after the face has detached the momentum is constant again."""
+    gap = 0.1
+    pb = W.rebound2d(n=11, gap=gap)
+    eps = pb.contact[1]
+    o = O.Oracle(pb)
+    m = o.get(O.F_MASS)
+    E0 = (m * o.get(O.F_E)).sum()
+    face = np.where(o.get(O.F_X)[0] == 0.0)[0]
+    contact_seen = detached_at = None
+    p_after = []
+    for s in range(400):
+        o.step()
+        x = o.get(O.F_X)
+        px = (m * o.get(O.F_V)[0]).sum()
+        d = x[0, face] + gap
+        assert abs((m * o.get(O.F_E)).sum() - E0) <= 1e-14 * E0
+        assert (x[0] + gap).min() >= eps - 0.1 * o.dt - 1e-15
+        if contact_seen is None:
+            if (d < eps).any():
+                contact_seen = s
+            else:
+                assert px == pytest.approx(-0.1 * m.sum(), rel=1e-13)
+        elif detached_at is None and (d > eps).all() and px > 0:
+            detached_at = s
+        elif detached_at is not None:
+            p_after.append(px)
+    assert contact_seen is not None and detached_at is not None
+    assert min(p_after) > 0.3 * 0.1 * m.sum()
+    assert max(p_after) - min(p_after) <= 1e-13 * max(p_after)
+
+
+def test_contact_face_without_walls_is_free():
+    """The same block without contact walls flies through the plane."""
+    gap = 0.1
+    pb = dataclasses.replace(W.rebound2d(n=11, gap=gap), contact=None)
+    o = O.Oracle(pb)
+    for _ in range(200):
+        o.step()
+    assert (o.get(O.F_X)[0] + gap).min() < -0.02

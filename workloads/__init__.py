@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-FREE, SLIP, CLAMPED, TRACTION, PRESSURE, VELOCITY = 0, 1, 2, 3, 4, 5
+FREE, SLIP, CLAMPED, TRACTION, PRESSURE, VELOCITY, CONTACT = 0, 1, 2, 3, 4, 5, 6
 
 
 @dataclass
@@ -63,6 +63,8 @@ class Problem:
     bcval: np.ndarray | None = None  # [dim, n_bfaces] boundary-face values (traction vector,
                                      # pressure in row 0, prescribed velocity) or None
     shear_a: float = -1.0            # a of the shear energy family; -1 neo-Hookean
+    contact: tuple | None = None     # (planes [n][2 dim]: point, unit normal into the body; eps)
+                                     # contact walls for faces tagged CONTACT
 
 
 # ----------------------------------------------------------------------------- ordering
@@ -269,6 +271,20 @@ def piston2d(n: int = 40, seed: int = 6, V: float = 0.02, steps: int = 200) -> P
     m = tri_mesh(n, seed, bc={"x0": VELOCITY, "y0": SLIP, "y1": SLIP})
     return Problem(f"piston2d_n{n}", m, 1.0, 2.0, np.full(m.n_cells, 1.0), np.zeros((2, m.n_cells)), 0.4, steps,
                    bcval=side_values(m, VELOCITY, (V, 0.0)))
+
+
+def rebound2d(n: int = 21, seed: int = 8, V: float = 0.1, gap: float = 0.02, steps: int = 400) -> Problem:
+    """Unit square (rho0=1, mu=1, lambda=2) flying at v = (-V, 0) toward a rigid wall at
+    x = -gap (Sect. "Boundary condition treatments": a boundary condition that changes type
+    with a distance function): its x = 0 side is a contact face, which becomes a slip wall
+    while within eps = h/2 of the wall and moving into it; the other sides are free."""
+    m = tri_mesh(n, seed, bc={"x0": CONTACT})
+    h = 1.0 / (n - 1)
+    v = np.zeros((2, m.n_cells))
+    v[0] = -V
+    planes = np.array([[-gap, 0.0, 1.0, 0.0]])
+    return Problem(f"rebound2d_n{n}", m, 1.0, 2.0, np.full(m.n_cells, 1.0), v, 0.4, steps,
+                   contact=(planes, 0.5 * h))
 
 
 def impact2d(n: int = 708, seed: int = 2, steps: int = 2000) -> Problem:
