@@ -127,8 +127,9 @@ lmood_status lmood_params_default(int dim, lmood_params *p);
  *                  carry a condition (Appendix B): 0 free traction, 1 slip wall (symmetry
  *                  plane through the face), 2 clamped (symmetry point, v = 0), 3 prescribed
  *                  traction vector t_f, 4 prescribed pressure p_f, 5 prescribed velocity V_f
- *                  (its normal component is imposed; Eqs. pBC, vBC1, vBC). The values of tags
- *                  3-5 are set with lmood_mesh_set_bc_values (zero until then). Faces not
+ *                  (its normal component is imposed; Eqs. pBC, vBC1, vBC), 6 contact (free,
+ *                  until it meets a contact wall, see lmood_mesh_set_contact). The values of
+ *                  tags 3-5 are set with lmood_mesh_set_bc_values (zero until then). Faces not
  *                  listed are traction-free. Each face must be a face of one cell; the library
  *                  orders its nodes so that its area vector N_f points out of the mesh. Per
  *                  node: clamped > prescribed velocity > slip > free for the velocity (several
@@ -159,10 +160,19 @@ lmood_status lmood_mesh_destroy(lmood_mesh m);
  * one); all states on the mesh see them. */
 lmood_status lmood_mesh_set_bc_values(lmood_mesh m, const double *values, int is_device);
 
+/* Contact walls for the faces tagged 6 (Sect. "Boundary condition treatments": a condition
+ * that changes type with a distance function): n_planes (0-4) planes, [n_planes][2 dim] on
+ * the host (a point, then the unit normal pointing from the wall into the body), and the
+ * distance threshold eps. In a nodal solve, a node of a contact face whose distance to a wall
+ * at x^n is below eps and whose velocity (after its other conditions) points into the wall
+ * gets v . n = 0 for that step (the wall does no work); it is free again once its velocity
+ * points away. Synchronises. Errors: LMOOD_ERR_ARG (count, eps < 0, non-unit normal). */
+lmood_status lmood_mesh_set_contact(lmood_mesh m, int n_planes, const double *planes, double eps);
+
 /* New tags [n_bfaces] (host) for the mesh's boundary faces, e.g. a wall that becomes free at
  * a given time (Sect. "Boundary condition treatments"); the per-node conditions are re-derived
  * and take effect from the next nodal solve. Synchronises. Errors: LMOOD_ERR_ARG for a tag
- * outside 0-5. */
+ * outside 0-6. */
 lmood_status lmood_mesh_set_btag(lmood_mesh m, const int32_t *btag);
 
 /*
@@ -258,8 +268,9 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  * (x, v_p per node; v, F per cell) and of the per-cell mu; the adjoint is the exact transpose
  * of its linearisation, written by hand kernel by kernel (no atomics, deterministic).
  * Only the two-level cascade (P1 -> P0) is differentiated: a recorded step that used the
- * limited level returns LMOOD_ERR_ARG, and so do a mesh with traction, pressure or
- * prescribed-velocity faces and a shear energy other than the neo-Hookean one (a = -1). Energy e has no influence on the other fields, so it
+ * limited level returns LMOOD_ERR_ARG, and so do a mesh with traction, pressure,
+ * prescribed-velocity or contact faces and a shear energy other than the neo-Hookean one
+ * (a = -1). Energy e has no influence on the other fields, so it
  * carries no adjoint.
  *
  * lmood_tape_record: runs n_steps ordinary lmood_step calls on s (the forward pass, with the

@@ -45,7 +45,7 @@ class StepInfo(C.Structure):
 
 _lib = None
 EXPORTS = ("lmood_params_default", "lmood_mesh_create", "lmood_mesh_destroy", "lmood_mesh_info",
-           "lmood_mesh_set_bc_values", "lmood_mesh_set_btag",
+           "lmood_mesh_set_bc_values", "lmood_mesh_set_btag", "lmood_mesh_set_contact",
            "lmood_state_init", "lmood_state_destroy", "lmood_step", "lmood_run", "lmood_get", "lmood_set",
            "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_autotune", "lmood_totals_noalloc",
            "lmood_tape_record",
@@ -69,6 +69,7 @@ def lib():
         L.lmood_mesh_info.argtypes = [vp, C.POINTER(C.c_int64)]
         L.lmood_mesh_set_bc_values.argtypes = [vp, vp, C.c_int]
         L.lmood_mesh_set_btag.argtypes = [vp, vp]
+        L.lmood_mesh_set_contact.argtypes = [vp, C.c_int, vp, C.c_double]
         L.lmood_state_init.argtypes = [vp, C.POINTER(Material), vp, vp, vp, C.POINTER(Params), C.POINTER(vp)]
         L.lmood_state_destroy.argtypes = [vp]
         L.lmood_step.argtypes = [vp, C.POINTER(StepInfo)]
@@ -153,8 +154,14 @@ class Mesh:
             a = np.ascontiguousarray(values, dtype=np.float64)
             _check(lib().lmood_mesh_set_bc_values(self.h, a.ctypes.data, 0))
 
+    def set_contact(self, planes, eps: float):
+        """contact walls [n][2 dim] (a point, the unit normal into the body) and threshold eps
+        for the faces tagged 6"""
+        a = np.ascontiguousarray(planes, dtype=np.float64)
+        _check(lib().lmood_mesh_set_contact(self.h, len(a), a.ctypes.data if len(a) else None, eps))
+
     def set_btag(self, btag):
-        """new boundary-face tags [n_bfaces] (0-5); per-node conditions re-derived"""
+        """new boundary-face tags [n_bfaces] (0-6); per-node conditions re-derived"""
         a = np.ascontiguousarray(btag, dtype=np.int32)
         _check(lib().lmood_mesh_set_btag(self.h, a.ctypes.data))
 
@@ -383,6 +390,8 @@ def simulation(problem, stream=None, cell_inst=None, n_inst=1, **params) -> Stat
     mesh = Mesh(m.dim, m.x, m.c2n, m.bface, m.btag, cell_inst=cell_inst, n_inst=n_inst, stream=stream)
     if getattr(problem, "bcval", None) is not None:
         mesh.set_bc_values(problem.bcval)
+    if getattr(problem, "contact", None) is not None:
+        mesh.set_contact(*problem.contact)
     p = params_default(m.dim, cfl=problem.cfl)
     for k, v in params.items():
         setattr(p, k, v)

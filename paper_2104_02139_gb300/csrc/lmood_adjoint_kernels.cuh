@@ -121,7 +121,7 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_nodes(Geo g, Fld f
             a.lvp0[r * Np + p] = -lvp1t + lvp0[r];
         }
     }
-    adj::node_solve_vjp<D>(M, b, g.bc_ndof[p] & ~BC_EXT, tv, lvs, lb, lM);
+    adj::node_solve_vjp<D>(M, b, g.bc_ndof[p] & BC_NDOF, tv, lvs, lb, lM);
     for (int j = j0; j < j1; ++j) {
         double *r = a.cr + (size_t)g.n2c[j] * R::CR;
         for (int q = 0; q < D; ++q) r[R::CR_R + q] = (init_mode ? 0.0 : r[R::CR_R + q]) + lb[q];

@@ -115,7 +115,7 @@ static lmood_status resolve_bcs(int dim, int64_t Np, int64_t n_bfaces, const dou
             const int p = q[a];
             if (btag[f] == TAG_CLAMPED) clamped[p] = 1;
             if (btag[f] >= TAG_TRACTION) {
-                ext[p] = 1;
+                ext[p] |= btag[f] == TAG_CONTACT ? 2 : 1;
                 has_ext = true;
             }
             if (btag[f] != TAG_SLIP) continue;
@@ -160,7 +160,8 @@ static lmood_status resolve_bcs(int dim, int64_t Np, int64_t n_bfaces, const dou
                 ndof[p] = 1;
             }
         }
-        if (ext[p]) ndof[p] |= BC_EXT;
+        if (ext[p] & 1) ndof[p] |= BC_EXT;
+        if (ext[p] & 2) ndof[p] |= BC_CONTACT;
     }
     return LMOOD_OK;
 }
@@ -189,7 +190,7 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
     for (int64_t i = 0; i < n_bfaces * dim; ++i)
         if (bface[i] < 0 || bface[i] >= Np) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: node index out of range in bface");
     for (int64_t i = 0; i < n_bfaces; ++i)
-        if (btag[i] < 0 || btag[i] > 5) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: boundary tag must be 0 to 5");
+        if (btag[i] < 0 || btag[i] > 6) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: boundary tag must be 0 to 6");
     std::vector<int> node_inst;
     if (cell_inst) {
         node_inst.assign(Np, -1);
@@ -330,6 +331,15 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
     m->h_bf = bf;
     m->h_btag = tags;
     g.nbf = (int)n_bfaces;
+    {
+        std::vector<double> c0(2 + 2 * 3 * kMaxContact, 0.0);  // no contact walls
+        if ((s = upload(m->mem, &m->d_contact, c0.data(), c0.size(), st))) {
+            m->mem.release();
+            delete m;
+            return s;
+        }
+        g.contact = m->d_contact;
+    }
     if (n_bfaces > 0) {
         int *d_bfn, *d_noff, *d_nidx;
         std::vector<unsigned char> t8(tags.begin(), tags.end());
@@ -387,10 +397,28 @@ extern "C" lmood_status lmood_mesh_set_bc_values(lmood_mesh m, const double *val
     return LMOOD_OK;
 }
 
+extern "C" lmood_status lmood_mesh_set_contact(lmood_mesh m, int n_planes, const double *planes, double eps) {
+    if (!m || n_planes < 0 || n_planes > kMaxContact || (n_planes > 0 && !planes) || !(eps >= 0.0))
+        return fail(LMOOD_ERR_ARG, "lmood_mesh_set_contact: bad argument (at most 4 planes, eps >= 0)");
+    const int D = m->dim;
+    std::vector<double> c(2 + 2 * 3 * kMaxContact, 0.0);
+    c[0] = n_planes;
+    c[1] = eps;
+    for (int k = 0; k < n_planes; ++k) {
+        double nn = 0.0;
+        for (int a = 0; a < D; ++a) nn += planes[k * 2 * D + D + a] * planes[k * 2 * D + D + a];
+        if (!(std::fabs(nn - 1.0) <= 1e-12)) return fail(LMOOD_ERR_ARG, "lmood_mesh_set_contact: normals must be unit vectors");
+        for (int i = 0; i < 2 * D; ++i) c[2 + 2 * D * k + i] = planes[k * 2 * D + i];
+    }
+    LM_CUDA(cudaMemcpyAsync(m->d_contact, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, m->st));
+    LM_CUDA(cudaStreamSynchronize(m->st));
+    return LMOOD_OK;
+}
+
 extern "C" lmood_status lmood_mesh_set_btag(lmood_mesh m, const int32_t *btag) {
     if (!m || (!btag && m->nb > 0)) return fail(LMOOD_ERR_ARG, "lmood_mesh_set_btag: NULL argument");
     for (int64_t f = 0; f < m->nb; ++f)
-        if (btag[f] < 0 || btag[f] > 5) return fail(LMOOD_ERR_ARG, "lmood_mesh_set_btag: boundary tag must be 0 to 5");
+        if (btag[f] < 0 || btag[f] > 6) return fail(LMOOD_ERR_ARG, "lmood_mesh_set_btag: boundary tag must be 0 to 6");
     std::vector<int> tags(btag, btag + m->nb);
     std::vector<unsigned char> ndof;
     std::vector<double> bct;

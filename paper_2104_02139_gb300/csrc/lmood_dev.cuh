@@ -48,10 +48,17 @@ struct Geo {
     const unsigned char *bf_tag;
     const double *bf_val;
     const int *nbf_off, *nbf_idx;
+    // contact walls (device, updatable in place): [0] count n <= 4, [1] distance threshold,
+    // then n planes of 2 D values (a point, the unit normal from the wall into the body)
+    const double *contact;
 };
 
-constexpr unsigned char BC_EXT = 0x80;  // node has traction / pressure / velocity faces
-enum { TAG_FREE = 0, TAG_SLIP = 1, TAG_CLAMPED = 2, TAG_TRACTION = 3, TAG_PRESSURE = 4, TAG_VELOCITY = 5 };
+constexpr unsigned char BC_EXT = 0x80;      // node has traction / pressure / velocity faces
+constexpr unsigned char BC_CONTACT = 0x40;  // node has contact faces
+constexpr unsigned char BC_NDOF = 0x3f;     // the free directions
+enum { TAG_FREE = 0, TAG_SLIP = 1, TAG_CLAMPED = 2, TAG_TRACTION = 3, TAG_PRESSURE = 4, TAG_VELOCITY = 5,
+       TAG_CONTACT = 6 };
+constexpr int kMaxContact = 4;
 
 struct Fld {
     const double *m, *mu;

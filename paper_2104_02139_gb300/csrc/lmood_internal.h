@@ -55,8 +55,8 @@ struct lmood_mesh_s {
     std::vector<int> h_bf;        // [dim][nb], oriented outward
     std::vector<int> h_btag;      // [nb]
     unsigned char *d_ndof = nullptr, *d_btag = nullptr;
-    double *d_bct = nullptr, *d_bfval = nullptr;
-    bool has_ext = false;         // some face has a traction / pressure / velocity tag
+    double *d_bct = nullptr, *d_bfval = nullptr, *d_contact = nullptr;
+    bool has_ext = false;         // some face has a traction / pressure / velocity / contact tag
     lmood::DevAllocs mem;
 };
 

@@ -495,7 +495,7 @@ __device__ __forceinline__ void node_solve(const Geo &g, const Fld &f, int p, in
 #pragma unroll
         for (int c = 0; c < D; ++c) M[a * D + c] = Ms[sidx<D>(a, c)];
     const int ndf = g.bc_ndof[p];
-    const int nd = ndf & ~BC_EXT;
+    const int nd = ndf & BC_NDOF;
     double v[D];
     if (!(ndf & BC_EXT)) {
         solve_K<D>(g, M, nd, p, b, v);
@@ -523,7 +523,7 @@ __device__ __forceinline__ void node_solve(const Geo &g, const Fld &f, int p, in
                 const double pr = g.bf_val[fid];
 #pragma unroll
                 for (int a = 0; a < D; ++a) b[a] -= pr * N[a] / D;
-            } else {
+            } else if (tag == TAG_VELOCITY) {
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
                     dv[a] += N[a] / D;
@@ -543,6 +543,32 @@ __device__ __forceinline__ void node_solve(const Geo &g, const Fld &f, int p, in
             }
             if (wd > 0.0) {
                 const double T = (vd - gsum) / wd;
+#pragma unroll
+                for (int a = 0; a < D; ++a) v[a] -= T * w[a];
+            }
+        }
+    }
+    if (ndf & BC_CONTACT) {
+        // contact walls (Sect. "Boundary condition treatments"): within the distance threshold
+        // of a wall and moving into it, the node gets v . n = 0 (the multiplier above, g = 0)
+        const int nw = (int)g.contact[0];
+        const double eps = g.contact[1];
+        for (int k = 0; k < nw; ++k) {
+            const double *P = g.contact + 2 + 2 * D * k, *nrm = P + D;
+            double dist = 0.0, vn = 0.0, n[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                n[a] = nrm[a];
+                dist += n[a] * (f.x[a * Np + p] - P[a]);
+                vn += n[a] * v[a];
+            }
+            if (!(dist < eps && vn < 0.0)) continue;
+            double w[D], wn = 0.0;
+            solve_K<D>(g, M, nd, p, n, w);
+#pragma unroll
+            for (int a = 0; a < D; ++a) wn += w[a] * n[a];
+            if (wn > 0.0) {
+                const double T = vn / wn;
 #pragma unroll
                 for (int a = 0; a < D; ++a) v[a] -= T * w[a];
             }

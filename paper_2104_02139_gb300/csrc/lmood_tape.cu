@@ -211,8 +211,8 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
         return fail(LMOOD_ERR_ARG, "lmood_tape_record: n_steps must be >= 1 and checkpoint_every >= 0");
     lmood_mesh M = s->M;
     if (M->has_ext)
-        return fail(LMOOD_ERR_ARG, "lmood_tape_record: the mesh has traction, pressure or prescribed-velocity faces, "
-                                   "which have no adjoint");
+        return fail(LMOOD_ERR_ARG, "lmood_tape_record: the mesh has traction, pressure, prescribed-velocity or "
+                                   "contact faces, which have no adjoint");
     if (s->mat.shear_a != -1.0)
         return fail(LMOOD_ERR_ARG, "lmood_tape_record: the adjoint covers the neo-Hookean shear energy (a = -1) only");
     const int D = M->dim, NV = D + 1, NS = D * (D + 1) / 2, DD = D * D;

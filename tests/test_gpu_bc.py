@@ -1,6 +1,7 @@
-"""Traction, pressure and prescribed-velocity boundary faces, and tags that change during a
-run, on the CUDA path against the oracle (-m gpu): identical MOOD masks at every step, state
-error <= 1e-11 after one step and <= 1e-8 over the run (the parity bar of the step)."""
+"""Traction, pressure and prescribed-velocity boundary faces, tags that change during a run
+and contact walls, on the CUDA path against the oracle (-m gpu): identical MOOD masks at every
+step, state error <= 1e-11 after one step and <= 1e-8 over the run (the parity bar of the
+step)."""
 import dataclasses
 
 import numpy as np
@@ -125,3 +126,39 @@ def test_tape_refuses_external_faces():
     with pytest.raises(L.LmoodError) as e:
         L.Tape(st, 2)
     assert e.value.status == L.ERR_ARG
+
+
+def test_contact_rebound_parity():
+    """approach and contact with the wall (reading R17), 2D; the whole rebound with detachment
+    is pinned on the oracle"""
+    gap = 0.1
+    pb = W.rebound2d(n=21, gap=gap)
+    eps = pb.contact[1]
+    p = Pair(pb)
+    p.run_compare(260)
+    x = p.g.get(L.FIELD_X)
+    assert (x[0] + gap).min() < eps  # in contact
+    assert (x[0] + gap).min() >= eps - 0.1 * p.o.dt - 1e-12
+
+
+def test_contact_box3d_parity():
+    m = W.tet_mesh(4, 4, 4, 9, bc={"z0": W.CONTACT, "x0": W.SLIP})
+    v = np.zeros((3, m.n_cells))
+    v[2] = -0.1
+    gap = 0.15
+    planes = np.array([[0.0, 0.0, -gap, 0.0, 0.0, 1.0]])
+    pb = W.Problem("drop3d", m, 1.0, 2.0, np.full(m.n_cells, 1.0), v, 0.25, 10, contact=(planes, 0.125))
+    p = Pair(pb)
+    p.run_compare(60)
+    assert (p.g.get(L.FIELD_X)[2] + gap).min() >= 0.125 - 0.1 * p.o.dt - 1e-12
+
+
+def test_contact_arguments():
+    mesh = L.simulation(W.rebound2d(n=6)).mesh
+    with pytest.raises(L.LmoodError) as e:
+        mesh.set_contact(np.array([[0.0, 0.0, 2.0, 0.0]]), 0.1)  # normal not unit
+    assert e.value.status == L.ERR_ARG
+    with pytest.raises(L.LmoodError) as e:
+        mesh.set_contact(np.zeros((5, 4)), 0.1)
+    assert e.value.status == L.ERR_ARG
+    mesh.set_contact(np.zeros((0, 4)), 0.0)  # no walls
