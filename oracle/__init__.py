@@ -35,7 +35,8 @@ class Params(C.Structure):
     _fields_ = [("cfl", C.c_double), ("Cv", C.c_double), ("Ci", C.c_double),
                 ("delta0", C.c_double), ("delta1", C.c_double), ("dt_fixed", C.c_double),
                 ("max_mood_iters", C.c_int), ("order", C.c_int), ("mood", C.c_int),
-                ("vol_coeff", C.c_int), ("cascade", C.c_int), ("shear_a", C.c_double)]
+                ("vol_coeff", C.c_int), ("cascade", C.c_int), ("shear_a", C.c_double),
+                ("eos", C.c_int), ("gamma", C.c_double), ("p_inf", C.c_double), ("p0", C.c_double)]
 
 
 class Info(C.Structure):
@@ -161,6 +162,10 @@ class Oracle:
         self.params = params or default_params(problem.cfl, **kw)
         if params is None and "shear_a" not in kw:
             self.params.shear_a = getattr(problem, "shear_a", -1.0)
+        sg = getattr(problem, "stiffened_gas", None)
+        if params is None and sg is not None:
+            self.params.eos = 1
+            self.params.gamma, self.params.p_inf, self.params.p0 = sg
         x = np.ascontiguousarray(m.x, dtype=np.float64)
         c2n = np.ascontiguousarray(m.c2n, dtype=np.int32)
         bf = np.ascontiguousarray(m.bface, dtype=np.int32)

@@ -72,6 +72,13 @@
  *      velocity (after the other conditions) points into the wall gets v*_p . n = 0 for the
  *      step, with the multiplier of R15 (d = n, g = 0): the wall does no work; the node
  *      detaches when its velocity points away from the wall again.
+ *  R18 stiffened gas (Eq. EOS_stiffened_gas, the incomplete form): p = (gamma - 1) rho eps_v -
+ *      gamma p_inf, rho = rho0 / det F, eps_v = e - |v|^2/2 - Psi_s(F) (the volumetric part of
+ *      the specific internal energy; Psi_s the shear energy of the family); T = -p I + the
+ *      family's shear stress. The predictor evaluates it with the cell's eps at t^n (pass 1)
+ *      and eps advanced half a step by T_c : L^ / rho (pass 2); sound speed a^2 = (gamma
+ *      (p + p_inf) + 4 mu / (3 J)) / rho; PAD also asks p + p_inf > 0; the initial eps_v
+ *      comes from an initial pressure p0.
  *  R16 shear energy family (Eq. familiy_energies, any a; a = -1 neo-Hookean, the default):
  *      T = -p I + (mu/J) dev(c1 Bbar - c2 Bbar^2), c1 = -a + (1+a) I1 I2 / 3,
  *      c2 = (1+a) I2 / 3 (the Cauchy stress of an isotropic energy of Bbar's invariants);
@@ -104,6 +111,8 @@ typedef struct {
     int vol_coeff;      /* 0: kappa = lambda + 2 mu / 3; 1: kappa = mu (printed)      */
     int cascade;        /* 2: P1 -> P0; 3: P1 -> P1 with Barth-Jespersen slopes -> P0     */
     double shear_a;     /* a of the shear energy family (Eq. familiy_energies); -1: neo-Hookean */
+    int eos;            /* volumetric law: 0 Eq. EOS_neoHook, 1 stiffened gas (reading R18) */
+    double gamma, p_inf, p0; /* stiffened gas: gamma, p_infinity, initial pressure          */
 } OrcParams;
 
 typedef struct {
@@ -396,6 +405,50 @@ double orc_sound_speed(int d, const double *F, double rho, double mu, double kap
 
 static double kappa_of(const OrcState *S, long c) {
     return S->prm.vol_coeff == 1 ? S->mu[c] : S->lam + 2.0 * S->mu[c] / 3.0;
+}
+
+/* stiffened gas (Eq. EOS_stiffened_gas; reading R18): p = (gamma - 1) rho eps_v - gamma p_inf
+ * with rho = rho0 / det F and eps_v = eps - Psi_s(F) the volumetric part of the specific
+ * internal energy eps = e - |v|^2/2 (Psi_s the shear energy of Eq. familiy_energies) */
+static double sg_pressure(const OrcState *S, long c, const double *F, double eps) {
+    int d = S->M->d;
+    double F3[9];
+    embed3(d, F, F3);
+    double J = det_n(3, F3);
+    double eps_s = orc_free_energy_a(d, F, S->rho0, S->mu[c], 0.0, S->prm.shear_a);
+    return (S->prm.gamma - 1.0) * (S->rho0 / J) * (eps - eps_s) - S->prm.gamma * S->prm.p_inf;
+}
+
+/* the material's Cauchy stress at F with specific internal energy eps (used by the stiffened
+ * gas only): Eqs. EOS_neoHook + familiy_energies, or the stiffened-gas pressure plus the
+ * family's shear stress */
+static void stress_state(const OrcState *S, long c, const double *F, double eps, double *T) {
+    int d = S->M->d;
+    if (S->prm.eos == 0) {
+        orc_stress_a(d, F, S->mu[c], kappa_of(S, c), S->prm.shear_a, T);
+        return;
+    }
+    orc_stress_a(d, F, S->mu[c], 0.0, S->prm.shear_a, T);  /* shear part (no volumetric term) */
+    double p = sg_pressure(S, c, F, eps);
+    for (int i = 0; i < d; ++i) T[i * d + i] -= p;
+}
+
+/* sound speed of the material (readings R4, R18): stiffened gas a^2 = (gamma (p + p_inf) +
+ * 4 mu / (3 J)) / rho */
+static double sound_speed_state(const OrcState *S, long c, const double *F, double rho, double eps) {
+    int d = S->M->d;
+    if (S->prm.eos == 0) return orc_sound_speed(d, F, rho, S->mu[c], kappa_of(S, c));
+    double F3[9];
+    embed3(d, F, F3);
+    double J = det_n(3, F3);
+    double p = sg_pressure(S, c, F, eps);
+    return sqrt((S->prm.gamma * (p + S->prm.p_inf) + 4.0 / 3.0 * S->mu[c] / J) / rho);
+}
+
+/* the material's energy scale at rest (PAD tolerance, reading R12): the squared P-wave speed */
+static double a0sq_of(const OrcState *S, long c) {
+    if (S->prm.eos == 0) return (kappa_of(S, c) + 4.0 / 3.0 * S->mu[c]) / S->rho0;
+    return (S->prm.gamma * (S->prm.p0 + S->prm.p_inf) + 4.0 / 3.0 * S->mu[c]) / S->rho0;
 }
 
 /* --------------------------------------------------------------------------------------
@@ -778,9 +831,10 @@ static void phase_packets(const OrcState *S, const int *order, double dt, Work *
     for (long c = 0; c < M->nc; ++c) {
         const double *ln = w->ln + c * nv * d, *N = w->N + c * nv * d;
         const double *vc = S->v + c * d, *Fc = S->F + c * dd;
-        double kap = kappa_of(S, c);
         double rho = S->m[c] / w->V[c];
-        double z = rho * orc_sound_speed(d, Fc, rho, S->mu[c], kap);
+        double eps = S->e[c];  /* specific internal energy (enters the stiffened gas only) */
+        for (int i = 0; i < d; ++i) eps -= 0.5 * vc[i] * vc[i];
+        double z = rho * sound_speed_state(S, c, Fc, rho, eps);
         double vstar[MAXV][MAXD], Tstar[MAXV][9];
         if (order[c] != 1) {
             const double *gv = w->gv + c * dd, *gF = w->gF + c * dd * d;
@@ -800,21 +854,30 @@ static void phase_packets(const OrcState *S, const int *order, double dt, Work *
                     Fh[k][i] = s;
                 }
                 double Tk[9], Tn[3];
-                orc_stress_a(d, Fh[k], S->mu[c], kap, S->prm.shear_a, Tk);
+                stress_state(S, c, Fh[k], eps, Tk);
                 matvec_n(d, Tk, ln + k * d, Tn);
                 for (int i = 0; i < d; ++i) dvdt[i] += Tn[i];
             }
             for (int i = 0; i < d; ++i) dvdt[i] /= S->m[c];
             matmul_n(d, gv, Fc, dFdt); /* dF/dt = L^ F (Eq. GCLL) with L^ the reconstructed gradient */
+            /* stiffened gas: the internal energy at the half step, d eps/dt = T : L^ / rho with
+             * the cell's stress (reading R18) */
+            double eps_h = eps;
+            if (S->prm.eos != 0) {
+                double Tc[9], pw = 0.0;
+                stress_state(S, c, Fc, eps, Tc);
+                for (int i = 0; i < dd; ++i) pw += Tc[i] * gv[i];
+                eps_h = eps + 0.5 * dt * pw / rho;
+            }
             for (int k = 0; k < nv; ++k) {
                 double Fs[9];
                 for (int i = 0; i < d; ++i) vstar[k][i] = vh[k][i] + 0.5 * dt * dvdt[i];
                 for (int i = 0; i < dd; ++i) Fs[i] = Fh[k][i] + 0.5 * dt * dFdt[i];
-                orc_stress_a(d, Fs, S->mu[c], kap, S->prm.shear_a, Tstar[k]);
+                stress_state(S, c, Fs, eps_h, Tstar[k]);
             }
         } else {
             double T0[9];
-            orc_stress_a(d, Fc, S->mu[c], kap, S->prm.shear_a, T0);
+            stress_state(S, c, Fc, eps, T0);
             for (int k = 0; k < nv; ++k) {
                 for (int i = 0; i < d; ++i) vstar[k][i] = vc[i];
                 memcpy(Tstar[k], T0, sizeof(double) * dd);
@@ -1078,9 +1141,15 @@ static void candidate(const OrcState *S, const int *order, double dt, Work *w) {
 }
 
 /* 7. time step (Eqs. CFL, CFL2; reading R13) */
-static double dt_acoustic_cell(const OrcState *S, long c, const double *F, double V, double Lc) {
+static double dt_acoustic_cell(const OrcState *S, long c, const double *F, double V, double Lc, double eps) {
     double rho = S->m[c] / V;
-    return S->prm.cfl * Lc / orc_sound_speed(S->M->d, F, rho, S->mu[c], kappa_of(S, c));
+    return S->prm.cfl * Lc / sound_speed_state(S, c, F, rho, eps);
+}
+
+static double eps_of(int d, const double *v, double e) {
+    double ke = 0.0;
+    for (int i = 0; i < d; ++i) ke += 0.5 * v[i] * v[i];
+    return e - ke;
 }
 
 static void totals(const OrcState *S, OrcInfo *info) {
@@ -1113,8 +1182,11 @@ int orc_step(OrcState *S, OrcInfo *info) {
             int *flag = calloc(nc, sizeof(int));
 #pragma omp parallel for schedule(static) reduction(+ : fresh, n_para, n_eps)
             for (long c = 0; c < nc; ++c) {
-                int ps = pad_state(d, w.v1 + c * d, w.e1[c], w.F1 + c * dd, w.V1[c],
-                                   (kappa_of(S, c) + 4.0 / 3.0 * S->mu[c]) / S->rho0);
+                int ps = pad_state(d, w.v1 + c * d, w.e1[c], w.F1 + c * dd, w.V1[c], a0sq_of(S, c));
+                /* stiffened gas: p + p_inf > 0 (real sound speed; reading R18) */
+                if (ps == 0 && S->prm.eos != 0 &&
+                    !(sg_pressure(S, c, w.F1 + c * dd, eps_of(d, w.v1 + c * d, w.e1[c])) + S->prm.p_inf > 0.0))
+                    ps = 1;
                 if (order[c] != 1) {
                     if (ps != 0 || !rdmp_ok(S, &w, c)) { flag[c] = 1; fresh++; }
                 } else if (ps == 2) {
@@ -1140,7 +1212,7 @@ int orc_step(OrcState *S, OrcInfo *info) {
                 double xs[MAXV * MAXD], V1, xc1[MAXD], N1[MAXV * MAXD], ln1[MAXV * MAXD], Lc1;
                 gather_xs(M, w.x1, c, xs);
                 orc_cell_geometry(d, xs, &V1, xc1, N1, ln1, &Lc1);
-                double dtc = dt_acoustic_cell(S, c, w.F1 + c * dd, V1, Lc1);
+                double dtc = dt_acoustic_cell(S, c, w.F1 + c * dd, V1, Lc1, eps_of(d, w.v1 + c * d, w.e1[c]));
                 double dV = V1 - w.V[c];
                 if (dV != 0.0) dtc = fmin(dtc, S->prm.Cv * dt * w.V[c] / fabs(dV));
                 dtn = fmin(dtn, dtc);
@@ -1194,6 +1266,7 @@ void orc_state_free(OrcState *S) {
 int orc_state_new(OrcMesh *M, double rho0, double lam, const double *mu_cell, const double *v_soa,
                   const double *F_soa, const OrcParams *prm, OrcState **out) {
     if (!M || !prm || !mu_cell || !v_soa || !out) return ORC_ERR_ARG;
+    if (prm->eos != 0 && !(prm->eos == 1 && prm->gamma > 1.0 && prm->p0 + prm->p_inf > 0.0)) return ORC_ERR_ARG;
     int d = M->d, nv = M->nv, dd = d * d;
     long nc = M->nc, np = M->np;
     OrcState *S = calloc(1, sizeof(OrcState));
@@ -1225,8 +1298,16 @@ int orc_state_new(OrcMesh *M, double rho0, double lam, const double *mu_cell, co
         S->tau[c] = w.V[c] / S->m[c];
         double ke = 0.0;
         for (int i = 0; i < d; ++i) ke += 0.5 * S->v[c * d + i] * S->v[c * d + i];
-        S->e[c] = ke + orc_free_energy_a(d, S->F + c * dd, rho0, S->mu[c], kappa_of(S, c), S->prm.shear_a);
-        dt0 = fmin(dt0, dt_acoustic_cell(S, c, S->F + c * dd, w.V[c], w.Lc[c]));
+        if (S->prm.eos == 0) {
+            S->e[c] = ke + orc_free_energy_a(d, S->F + c * dd, rho0, S->mu[c], kappa_of(S, c), S->prm.shear_a);
+        } else {  /* eps_v from the initial pressure p0 at rho = rho0 / det F (reading R18) */
+            double F3[9];
+            embed3(d, S->F + c * dd, F3);
+            double J = det_n(3, F3);
+            double eps_v = (S->prm.p0 + S->prm.gamma * S->prm.p_inf) / ((S->prm.gamma - 1.0) * rho0 / J);
+            S->e[c] = ke + eps_v + orc_free_energy_a(d, S->F + c * dd, rho0, S->mu[c], 0.0, S->prm.shear_a);
+        }
+        dt0 = fmin(dt0, dt_acoustic_cell(S, c, S->F + c * dd, w.V[c], w.Lc[c], eps_of(d, S->v + c * d, S->e[c])));
     }
     /* v_p^0: first-order nodal solve at t^0 */
     phase_packets(S, S->order, 0.0, &w);

@@ -65,6 +65,7 @@ class Problem:
     shear_a: float = -1.0            # a of the shear energy family; -1 neo-Hookean
     contact: tuple | None = None     # (planes [n][2 dim]: point, unit normal into the body; eps)
                                      # contact walls for faces tagged CONTACT
+    stiffened_gas: tuple | None = None  # (gamma, p_inf, p0): stiffened-gas volumetric law
 
 
 # ----------------------------------------------------------------------------- ordering
