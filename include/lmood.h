@@ -52,13 +52,18 @@ typedef enum {
  * kappa = mu when vol_coeff = 1 (the coefficient as printed). Shear free energy of the family
  *   Psi_s = mu / (4 rho0) (-2a (I1 - 3) + (1+a)/3 (I2^2 - 9))   (Eq. familiy_energies)
  * with I1, I2 the invariants of J^{-2/3} F F^t; a = -1 (neo-Hookean) is the default and the
- * fastest path; a must lie in [-1, 1/2], where the paper states the system is hyperbolic. */
+ * fastest path; a must lie in [-1, 1/2], where the paper states the system is hyperbolic.
+ * eos = 1 replaces the volumetric law by the stiffened gas (Eq. EOS_stiffened_gas, incomplete
+ * form): p = (gamma - 1) rho eps_v - gamma p_inf with rho = rho0 / det F and eps_v the
+ * volumetric part e - |v|^2/2 - Psi_s of the specific internal energy; the initial eps_v is
+ * that of the pressure p0 (gamma > 1, p0 + p_inf > 0). lambda and vol_coeff are then unused. */
 typedef struct {
     double rho0;     /* initial density (> 0)                 */
     double lambda;   /* first Lame coefficient                */
     int32_t vol_coeff;
-    int32_t reserved;
+    int32_t eos;     /* 0: Eq. EOS_neoHook (default); 1: stiffened gas */
     double shear_a;  /* a of the shear energy family (-1: neo-Hookean) */
+    double gamma, p_inf, p0;  /* stiffened gas parameters and initial pressure */
 } lmood_material;
 
 /* Scheme parameters (Sect. "Time-step monitoring", "Limiting: a posteriori MOOD loop"). */
@@ -269,8 +274,8 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  * of its linearisation, written by hand kernel by kernel (no atomics, deterministic).
  * Only the two-level cascade (P1 -> P0) is differentiated: a recorded step that used the
  * limited level returns LMOOD_ERR_ARG, and so do a mesh with traction, pressure,
- * prescribed-velocity or contact faces and a shear energy other than the neo-Hookean one
- * (a = -1). Energy e has no influence on the other fields, so it
+ * prescribed-velocity or contact faces, a shear energy other than the neo-Hookean one
+ * (a = -1) and the stiffened gas. Energy e has no influence on the other fields, so it
  * carries no adjoint.
  *
  * lmood_tape_record: runs n_steps ordinary lmood_step calls on s (the forward pass, with the

@@ -26,8 +26,8 @@ class LmoodError(RuntimeError):
 
 
 class Material(C.Structure):
-    _fields_ = [("rho0", C.c_double), ("lambda_", C.c_double), ("vol_coeff", C.c_int32), ("reserved", C.c_int32),
-                ("shear_a", C.c_double)]
+    _fields_ = [("rho0", C.c_double), ("lambda_", C.c_double), ("vol_coeff", C.c_int32), ("eos", C.c_int32),
+                ("shear_a", C.c_double), ("gamma", C.c_double), ("p_inf", C.c_double), ("p0", C.c_double)]
 
 
 class Params(C.Structure):
@@ -183,10 +183,14 @@ class State:
     """lmood_state_init / step / run / get / set / totals / destroy."""
 
     def __init__(self, mesh: Mesh, rho0, lam, mu, v, F=None, params: Params | None = None, vol_coeff=0,
-                 shear_a=-1.0):
+                 shear_a=-1.0, stiffened_gas=None):
+        """stiffened_gas: None, or (gamma, p_inf, p0) for the stiffened-gas volumetric law"""
         self.mesh = mesh
         self.params = params or params_default(mesh.dim)
         mat = Material(rho0=rho0, lambda_=lam, vol_coeff=vol_coeff, shear_a=shear_a)
+        if stiffened_gas is not None:
+            mat.eos = 1
+            mat.gamma, mat.p_inf, mat.p0 = stiffened_gas
         mu = _host(mu, np.float64)
         v = _host(v, np.float64)
         F = _host(F, np.float64)
@@ -396,4 +400,4 @@ def simulation(problem, stream=None, cell_inst=None, n_inst=1, **params) -> Stat
     for k, v in params.items():
         setattr(p, k, v)
     return State(mesh, problem.rho0, problem.lam, problem.mu, problem.v, problem.F, p,
-                 shear_a=getattr(problem, "shear_a", -1.0))
+                 shear_a=getattr(problem, "shear_a", -1.0), stiffened_gas=getattr(problem, "stiffened_gas", None))

@@ -491,6 +491,11 @@ static Prm kernel_params(const lmood_params &p, const lmood_material &m) {
     k.lam = m.lambda;
     k.irho0 = 1.0 / m.rho0;
     k.shear_a = m.shear_a;
+    k.eos = m.eos;
+    k.gamma = m.gamma;
+    k.pinf = m.p_inf;
+    k.p0 = m.p0;
+    k.rho0 = m.rho0;
     k.base_order = p.order == 1 ? 1 : 2;
     k.mood = p.mood ? 1 : 0;
     k.vol_coeff = m.vol_coeff ? 1 : 0;
@@ -541,6 +546,8 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
     if (!(mat->rho0 > 0)) return fail(LMOOD_ERR_ARG, "lmood_state_init: rho0 must be positive");
     if (!(mat->shear_a >= -1.0 && mat->shear_a <= 0.5))
         return fail(LMOOD_ERR_ARG, "lmood_state_init: shear_a must lie in [-1, 1/2]");
+    if (mat->eos != 0 && !(mat->eos == 1 && mat->gamma > 1.0 && mat->p0 + mat->p_inf > 0.0))
+        return fail(LMOOD_ERR_ARG, "lmood_state_init: eos must be 0, or 1 with gamma > 1 and p0 + p_inf > 0");
     if (!(prm->cfl > 0) || prm->max_mood_iters < 0 || (prm->order != 1 && prm->order != 2) ||
         (prm->cascade != 2 && prm->cascade != 3))
         return fail(LMOOD_ERR_ARG, "lmood_state_init: bad parameters");

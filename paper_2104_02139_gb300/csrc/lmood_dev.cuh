@@ -20,6 +20,8 @@ struct Prm {
     double cfl, Cv, Ci, delta0, delta1, dt_fixed, lam;
     double irho0;    // 1 / rho0
     double shear_a;  // a of the shear energy family (Eq. familiy_energies); -1: neo-Hookean
+    int eos;         // volumetric law: 0 Eq. EOS_neoHook, 1 stiffened gas (Eq. EOS_stiffened_gas)
+    double gamma, pinf, p0, rho0;  // stiffened gas: gamma, p_infinity, initial pressure; rho0
     int base_order;  // order every cell starts the step with (2: P1, 1: P0; 0: keep f.order)
     int mood;        // detection on/off
     int vol_coeff;   // 0: kappa = lambda + 2 mu / 3; 1: kappa = mu
@@ -417,6 +419,48 @@ __device__ __forceinline__ int pad_state(const double (&v)[D], double e, const d
     for (int i = 0; i < D; ++i) ke += 0.5 * v[i] * v[i];
     const double eps = e - ke;
     return eps >= -1e-10 * fmax(fmax(fabs(e), ke), a0sq) ? 0 : 1;
+}
+
+// ---------------------------------------------------------------------------------------
+// Stiffened gas (Eq. EOS_stiffened_gas, incomplete form): p = (gamma - 1) rho eps_v -
+// gamma p_inf with rho = rho0 / det F and eps_v = eps - Psi_s(F), eps the specific internal
+// energy and Psi_s the shear energy of the family; T = -p I + the family's shear stress;
+// sound speed a^2 = (gamma (p + p_inf) + 4 mu / (3 J)) / rho.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ double shear_energy(const Prm &prm, const double (&F)[D * D], double mu) {
+    return prm.shear_a == -1.0 ? free_energy<D>(F, prm.rho0, mu, 0.0)
+                               : free_energy_family<D>(F, prm.rho0, mu, 0.0, prm.shear_a);
+}
+
+template <int D>
+__device__ __forceinline__ double sg_pressure(const Prm &prm, const double (&F)[D * D], double mu, double eps) {
+    const double J = det<D>(F);
+    return (prm.gamma - 1.0) * (prm.rho0 / J) * (eps - shear_energy<D>(prm, F, mu)) - prm.gamma * prm.pinf;
+}
+
+template <int D>
+__device__ __forceinline__ void stress_sg(const Prm &prm, const double (&F)[D * D], double mu, double eps,
+                                          double (&T)[D * D]) {
+    if (prm.shear_a == -1.0) stress<D>(F, mu, 0.0, T);  // shear part alone
+    else stress_family<D>(F, mu, 0.0, prm.shear_a, T);
+    const double p = sg_pressure<D>(prm, F, mu, eps);
+#pragma unroll
+    for (int i = 0; i < D; ++i) T[i * D + i] -= p;
+}
+
+template <int D>
+__device__ __forceinline__ double impedance_sg(const Prm &prm, const double (&F)[D * D], double rho, double mu,
+                                               double eps) {
+    const double J = det<D>(F);
+    const double p = sg_pressure<D>(prm, F, mu, eps);
+    return sqrt(rho * (prm.gamma * (p + prm.pinf) + (4.0 / 3.0) * mu / J));
+}
+
+// the material's energy scale at rest for the PAD tolerance: the squared P-wave speed
+__device__ __forceinline__ double a0sq_of(const Prm &prm, double mu, double kappa) {
+    return prm.eos ? (prm.gamma * (prm.p0 + prm.pinf) + (4.0 / 3.0) * mu) * prm.irho0
+                   : (kappa + (4.0 / 3.0) * mu) * prm.irho0;
 }
 
 }  // namespace lmood

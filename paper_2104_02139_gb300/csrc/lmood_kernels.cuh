@@ -96,16 +96,17 @@ template <int D, int B = kNodeBlock> __global__ void __launch_bounds__(B) k_mome
     }
 }
 
-// FAM: a shear energy of the family other than the neo-Hookean one (separate instances, so the
-// neo-Hookean kernels are compiled as if the family did not exist)
-template <int D, bool LISTED, bool FAM>
+// MAT: 0 neo-Hookean, 1 another shear energy of the family, 2 stiffened gas (separate
+// instances, so the neo-Hookean kernels are compiled as if the other materials did not exist)
+template <int D, int MAT>
 __device__ __forceinline__ void cell_stress(const Prm &prm, const double (&F)[D * D], double mu, double kappa,
-                                            double (&T)[D * D]) {
-    if constexpr (FAM) stress_family<D>(F, mu, kappa, prm.shear_a, T);
+                                            double eps, double (&T)[D * D]) {
+    if constexpr (MAT == 2) stress_sg<D>(prm, F, mu, eps, T);
+    else if constexpr (MAT == 1) stress_family<D>(F, mu, kappa, prm.shear_a, T);
     else stress<D>(F, mu, kappa, T);
 }
 
-template <int D, bool LISTED, bool FAM = false>
+template <int D, bool LISTED, int MAT = 0>
 __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const Prm &prm, int c) {
     constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + DD;
     const int N = g.N, Np = g.Np, NC = NV * N;
@@ -134,6 +135,12 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
 #pragma unroll
     for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
     const double muc = f.mu[c], kap = kappa_of(prm, muc);
+    double eps_c = 0.0;  // specific internal energy (the stiffened gas's pressure depends on it)
+    if constexpr (MAT == 2) {
+        eps_c = f.e[c];
+#pragma unroll
+        for (int a = 0; a < D; ++a) eps_c -= 0.5 * vc[a] * vc[a];
+    }
     // face matrices W_f = z |l n_f| n_f (x) n_f with l n_f = N_f / D; M_cp = sum_{f != p} W_f
     double W[NV][NS];
     {
@@ -299,7 +306,7 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
                 Fh[q] = s;
                 if constexpr (D == 2) Fhk[k][q] = s;
             }
-            cell_stress<D, LISTED, FAM>(prm, Fh, muc, kap, T);
+            cell_stress<D, MAT>(prm, Fh, muc, kap, eps_c, T);
 #pragma unroll
             for (int i = 0; i < D; ++i) {
                 double s = 0.0;
@@ -319,6 +326,15 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
 #pragma unroll
             for (int a = 0; a < D; ++a) gv[i * D + a] = gs[i][a];
         matmul<D>(gv, Fc, dFdt);
+        // stiffened gas: the internal energy at the half step, d eps/dt = T_c : L^ / rho
+        double eps_h = eps_c;
+        if constexpr (MAT == 2) {
+            double Tc[DD], pw = 0.0;
+            cell_stress<D, MAT>(prm, Fc, muc, kap, eps_c, Tc);
+#pragma unroll
+            for (int q = 0; q < DD; ++q) pw += Tc[q] * gv[q];
+            eps_h = eps_c + 0.5 * dt * pw * V / f.m[c];
+        }
         // pass 2: corner values at t^{n+1/2} and packets
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
@@ -342,12 +358,12 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
                 }
                 Fs[q] = fma(0.5 * dt, dFdt[q], s);
             }
-            cell_stress<D, LISTED, FAM>(prm, Fs, muc, kap, T);
+            cell_stress<D, MAT>(prm, Fs, muc, kap, eps_h, T);
             emit(k, vst, T);
         }
     } else {
         double T[DD];
-        cell_stress<D, LISTED, FAM>(prm, Fc, muc, kap, T);
+        cell_stress<D, MAT>(prm, Fc, muc, kap, eps_c, T);
 #pragma unroll
         for (int k = 0; k < NV; ++k) emit(k, vc, T);
     }
@@ -356,16 +372,16 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
 // LISTED = false: one thread per cell of the whole mesh; true: a grid-stride loop over a
 // device-counted list (separate instances, so each gets its own register allocation)
 // (the 2D bound keeps the register cap at 128 per thread for every block size B)
-template <int D, bool LISTED, int B = kCellBlock, bool FAM = false>
+template <int D, bool LISTED, int B = kCellBlock, int MAT = 0>
 __global__ void __launch_bounds__(B, D == 2 ? 512 / B : 1) k_predict(Geo g, Fld f, Prm prm, const int *__restrict__ list,
                                                         const int *__restrict__ cnt, int n) {
     if constexpr (!LISTED) {
         const int c = blockIdx.x * blockDim.x + threadIdx.x;
-        if (c < n) predict_cell<D, false, FAM>(g, f, prm, c);
+        if (c < n) predict_cell<D, false, MAT>(g, f, prm, c);
     } else {
         const int nn = *cnt;
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
-            predict_cell<D, true, FAM>(g, f, prm, list[i]);
+            predict_cell<D, true, MAT>(g, f, prm, list[i]);
     }
 }
 
@@ -727,7 +743,13 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
         area1 += sqrt(s);
     }
     if (prm.mood) {
-        const int ps = pad_state<D>(v1, e1, F1, V1, (kap + (4.0 / 3.0) * muc) * prm.irho0);
+        int ps = pad_state<D>(v1, e1, F1, V1, a0sq_of(prm, muc, kap));
+        if (prm.eos && ps == 0) {  // stiffened gas: p + p_inf > 0 (a real sound speed)
+            double eps1 = e1;
+#pragma unroll
+            for (int a = 0; a < D; ++a) eps1 -= 0.5 * v1[a] * v1[a];
+            if (!(sg_pressure<D>(prm, F1, muc, eps1) + prm.pinf > 0.0)) ps = 1;
+        }
         if (ord != 1) {
             bool bad = ps != 0;
             if (!bad) {
@@ -746,7 +768,15 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
         }
     }
     // next impedance and dt candidate: C_CFL L_c / a = C_CFL (2 D V / area) (m / V) / z
-    const double z1 = impedance<D>(F1, rho1, muc, kap);
+    double z1;
+    if (prm.eos) {
+        double eps1 = e1;
+#pragma unroll
+        for (int a = 0; a < D; ++a) eps1 -= 0.5 * v1[a] * v1[a];
+        z1 = impedance_sg<D>(prm, F1, rho1, muc, eps1);
+    } else {
+        z1 = impedance<D>(F1, rho1, muc, kap);
+    }
     f.z1[c] = z1;
     double dtc = prm.cfl * (2.0 * D) * mc / (area1 * z1);
     const double dV = V1 - V0;
@@ -969,11 +999,19 @@ __global__ void __launch_bounds__(kCellBlock) k_init_cells(Geo g, Fld f, Prm prm
         const double va = f.v[a * N + c];
         ke += 0.5 * va * va;
     }
-    f.e[c] = ke + (prm.shear_a == -1.0 ? free_energy<D>(F, rho0, muc, kap)
-                                       : free_energy_family<D>(F, rho0, muc, kap, prm.shear_a));
+    double z;
+    if (prm.eos) {  // stiffened gas: eps_v from the initial pressure p0 at rho0 / det F
+        const double eps_v = (prm.p0 + prm.gamma * prm.pinf) / ((prm.gamma - 1.0) * rho0 / det<D>(F));
+        const double eps = eps_v + shear_energy<D>(prm, F, muc);
+        f.e[c] = ke + eps;
+        z = impedance_sg<D>(prm, F, rho, muc, eps);
+    } else {
+        f.e[c] = ke + (prm.shear_a == -1.0 ? free_energy<D>(F, rho0, muc, kap)
+                                           : free_energy_family<D>(F, rho0, muc, kap, prm.shear_a));
+        z = impedance<D>(F, rho, muc, kap);
+    }
     f.order[c] = 1;
     f.pflag[c] = 0;
-    const double z = impedance<D>(F, rho, muc, kap);
     f.z[c] = z;
     f.dtc[c] = prm.cfl * insphere<D>(V, Nf) * rho / z;
 }
@@ -1007,7 +1045,14 @@ template <int D> __global__ void __launch_bounds__(kCellBlock) k_refresh(Geo g, 
 #pragma unroll
     for (int q = 0; q < DD; ++q) F[q] = f.F[q * g.N + c];
     const double muc = f.mu[c];
-    f.z[c] = impedance<D>(F, rho, muc, kappa_of(prm, muc));
+    if (prm.eos) {
+        double eps = f.e[c];
+#pragma unroll
+        for (int a = 0; a < D; ++a) eps -= 0.5 * f.v[a * g.N + c] * f.v[a * g.N + c];
+        f.z[c] = impedance_sg<D>(prm, F, rho, muc, eps);
+    } else {
+        f.z[c] = impedance<D>(F, rho, muc, kappa_of(prm, muc));
+    }
 }
 
 // sums of m, m v, m e (diagnostic; atomics, so the last bits depend on scheduling)

@@ -26,9 +26,14 @@ template <int D> void moments(const Geo &g, const Fld &f, cudaStream_t s) {
 template <int D>
 void predict(const Geo &g, const Fld &f, const Prm &p, const int *list, const int *cnt, int n, cudaStream_t s) {
     if (n <= 0) return;
+    if (p.eos) {  // stiffened gas: its own instances
+        if (list) k_predict<D, true, kCellBlock, 2><<<grid_for(list, n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n);
+        else k_predict<D, false, kCellBlock, 2><<<blocks(n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n);
+        return;
+    }
     if (p.shear_a != -1.0) {  // another member of the shear energy family: its own instances
-        if (list) k_predict<D, true, kCellBlock, true><<<grid_for(list, n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n);
-        else k_predict<D, false, kCellBlock, true><<<blocks(n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n);
+        if (list) k_predict<D, true, kCellBlock, 1><<<grid_for(list, n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n);
+        else k_predict<D, false, kCellBlock, 1><<<blocks(n, kCellBlock), kCellBlock, 0, s>>>(g, f, p, list, cnt, n);
         return;
     }
     if (list) {

@@ -213,8 +213,9 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     if (M->has_ext)
         return fail(LMOOD_ERR_ARG, "lmood_tape_record: the mesh has traction, pressure, prescribed-velocity or "
                                    "contact faces, which have no adjoint");
-    if (s->mat.shear_a != -1.0)
-        return fail(LMOOD_ERR_ARG, "lmood_tape_record: the adjoint covers the neo-Hookean shear energy (a = -1) only");
+    if (s->mat.shear_a != -1.0 || s->mat.eos != 0)
+        return fail(LMOOD_ERR_ARG, "lmood_tape_record: the adjoint covers the neo-Hookean material (a = -1, "
+                                   "volumetric law of Eq. EOS_neoHook) only");
     const int D = M->dim, NV = D + 1, NS = D * (D + 1) / 2, DD = D * D;
     const int64_t N = M->nc, Np = M->np, NC = NV * N;
     const int nmom = M->ops->nmom;

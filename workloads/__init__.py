@@ -288,6 +288,21 @@ def rebound2d(n: int = 21, seed: int = 8, V: float = 0.1, gap: float = 0.02, ste
                    contact=(planes, 0.5 * h))
 
 
+def jellydrop3d(n: int = 12, seed: int = 10, v: float = 2.0, shear_a: float = -1.0, steps: int = 200) -> Problem:
+    """A jelly-like block dropped on a rigid floor (Sect. "Impact of a jelly-like droplet",
+    on a box instead of the paper's cylinder): a quarter of a 12 mm x 12 mm x 8 mm block
+    (symmetry walls x = 0, y = 0), stiffened gas gamma = 2.2, p_inf = 1e6 Pa, p0 = 0,
+    mu = 85 Pa, rho0 = 1020 kg/m^3, moving at (0, 0, -v) m/s; its bottom is a contact face
+    with the floor 0.2 mm below (capture distance 0.1 mm); n^3 cubes of Kuhn tetrahedra."""
+    L0, H, gap = 6e-3, 8e-3, 2e-4
+    m = tet_mesh(n, n, n, seed, lx=L0, ly=L0, lz=H, bc={"x0": SLIP, "y0": SLIP, "z0": CONTACT})
+    vel = np.zeros((3, m.n_cells))
+    vel[2] = -v
+    planes = np.array([[0.0, 0.0, -gap, 0.0, 0.0, 1.0]])
+    return Problem(f"jellydrop3d_n{n}", m, 1020.0, 0.0, np.full(m.n_cells, 85.0), vel, 0.25, steps,
+                   shear_a=shear_a, contact=(planes, 0.5 * gap), stiffened_gas=(2.2, 1e6, 0.0))
+
+
 def impact2d(n: int = 708, seed: int = 2, steps: int = 2000) -> Problem:
     """Unit square of jittered Delaunay triangles (n=708 gives 999,698 cells) moving at
     v = (-0.1, 0) against a rigid slip wall at x = 0, other sides free;
