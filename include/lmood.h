@@ -41,7 +41,7 @@ typedef enum {
                                  tau <= 0 or det F <= 0 (Sect. "Limiting: a posteriori MOOD
                                  loop", the parachute scheme); the state is left unchanged   */
     LMOOD_ERR_MOOD_ITERS = 6, /* troubled cells remain after max_mood_iters iterations      */
-    LMOOD_ERR_TIMEOUT = 7,    /* reserved: a bounded device-side wait gave up                */
+    LMOOD_ERR_TIMEOUT = 7,    /* a bounded device-side wait gave up (graph = 2); state unchanged */
     LMOOD_ERR_STATE = 8       /* the handle is unusable after an earlier CUDA failure        */
 } lmood_status;
 
@@ -79,12 +79,18 @@ typedef struct {
     int32_t order;          /* 2: second order with the P1 -> P0 cascade; 1: first order    */
     int32_t mood;           /* 1: a-posteriori detection on (default); 0: unlimited         */
     int32_t graph;          /* 1: each step is one CUDA graph with the MOOD loop as a device-side
-                               conditional while node (default); 0: host-driven MOOD rounds.
-                               Results are identical.                                        */
+                               conditional while node (default); 0: host-driven MOOD rounds;
+                               2: each step is one persistent cooperative launch whose stages
+                               are separated by grid-wide barriers with bounded waits (a wait
+                               that gives up returns LMOOD_ERR_TIMEOUT, state unchanged;
+                               neo-Hookean material only; fastest for small meshes, where
+                               launch latency dominates). Results are identical.             */
     int32_t cascade;        /* 2: P1 -> P0 (default); 3: P1 -> P1 with Barth-Jespersen limited
                                slopes -> P0, the three-scheme cascade of Sect. "Limiting: a
                                posteriori MOOD loop" (order codes 2, 3, 1)                    */
-    int32_t reserved;
+    int32_t barrier_polls;  /* graph = 2: polls (~0.1 us each) one grid-barrier wait may take
+                               before the launch gives up with LMOOD_ERR_TIMEOUT; <= 0: the
+                               default 1e8 (~10 s, far above any stage's duration)          */
 } lmood_params;
 
 /* Per-step report. */

@@ -34,7 +34,7 @@ class Params(C.Structure):
     _fields_ = [("cfl", C.c_double), ("Cv", C.c_double), ("Ci", C.c_double), ("delta0", C.c_double),
                 ("delta1", C.c_double), ("dt_fixed", C.c_double), ("max_mood_iters", C.c_int32),
                 ("order", C.c_int32), ("mood", C.c_int32), ("graph", C.c_int32), ("cascade", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("barrier_polls", C.c_int32)]
 
 
 class StepInfo(C.Structure):

@@ -548,6 +548,8 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
         return fail(LMOOD_ERR_ARG, "lmood_state_init: shear_a must lie in [-1, 1/2]");
     if (mat->eos != 0 && !(mat->eos == 1 && mat->gamma > 1.0 && mat->p0 + mat->p_inf > 0.0))
         return fail(LMOOD_ERR_ARG, "lmood_state_init: eos must be 0, or 1 with gamma > 1 and p0 + p_inf > 0");
+    if (prm->graph < 0 || prm->graph > 2 || (prm->graph == 2 && (mat->shear_a != -1.0 || mat->eos != 0)))
+        return fail(LMOOD_ERR_ARG, "lmood_state_init: graph must be 0, 1 or 2 (2: neo-Hookean material only)");
     if (!(prm->cfl > 0) || prm->max_mood_iters < 0 || (prm->order != 1 && prm->order != 2) ||
         (prm->cascade != 2 && prm->cascade != 3))
         return fail(LMOOD_ERR_ARG, "lmood_state_init: bad parameters");
@@ -596,6 +598,7 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
     A((void **)&f.pkR, (size_t)D * NV * N * nd);
     A((void **)&f.order, N);
     A((void **)&f.pflag, N);
+    A((void **)&s->bar, 4 * sizeof(unsigned int));
     A((void **)&f.dtc, N * nd);
     double *dt0 = nullptr, *dt1 = nullptr;
     A((void **)&dt0, M->n_inst * nd);
@@ -879,9 +882,44 @@ static lmood_status step_host(lmood_state s, lmood_step_info *info) {
     return finish_step(s, *s->h_report, info);
 }
 
+// the whole step as one cooperative launch (params.graph = 2)
+static lmood_status step_persistent(lmood_state s, lmood_step_info *info) {
+    lmood_mesh M = s->M;
+    cudaStream_t st = M->st;
+    LM_CUDA(cudaMemsetAsync(s->bar, 0, 4 * sizeof(unsigned int), st));
+    PersistArgs a{};
+    a.tl0 = s->tl[0];
+    a.tl1 = s->tl[1];
+    a.nlist = s->nlist;
+    a.clist = s->clist;
+    a.node_mark = s->node_mark;
+    a.cell_mark = s->cell_mark;
+    a.ctl = s->ctl;
+    a.report = s->d_report;
+    a.bar = s->bar;
+    a.max_iters = s->prm.max_mood_iters;
+    a.n_inst = M->n_inst;
+    a.max_spin = s->prm.barrier_polls > 0 ? s->prm.barrier_polls : 100000000;  // polls of ~0.1 us
+    cudaError_t e = cudaSuccess;
+    timed(s, LMOOD_K_PREDICT, 1, [&] { e = M->ops->persistent(M->geo, s->f, s->kp, a, st); });
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LMOOD_ERR_CUDA, std::string("lmood_step (persistent): launch: ") + cudaGetErrorString(e));
+    }
+    LM_CUDA(cudaMemcpyAsync(s->h_report, s->d_report, sizeof(Report), cudaMemcpyDeviceToHost, st));
+    LM_CUDA(cudaMemcpyAsync(s->h_cnt, s->bar + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    lmood_status r = sync_check(s, "lmood_step (persistent)");
+    if (r) return r;
+    timing_drain(s);
+    if (s->h_cnt[0] != 0)
+        return fail(LMOOD_ERR_TIMEOUT, "lmood_step (persistent): a grid barrier wait gave up; the state is unchanged");
+    return finish_step(s, *s->h_report, info);
+}
+
 extern "C" lmood_status lmood_step(lmood_state s, lmood_step_info *info) {
     if (!s) return fail(LMOOD_ERR_ARG, "lmood_step: NULL state");
     if (s->broken) return fail(LMOOD_ERR_STATE, "lmood_step: state unusable after an earlier CUDA error");
+    if (s->prm.graph == 2) return step_persistent(s, info);
     return s->prm.graph ? step_graph(s, info) : step_host(s, info);
 }
 

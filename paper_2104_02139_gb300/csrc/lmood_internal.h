@@ -80,6 +80,7 @@ struct lmood_state_s {
     cudaEvent_t gev[2][7] = {};
     cudaStream_t cap_st = nullptr;   // private streams for capturing (the mesh's stream may be the
     cudaStream_t body_st = nullptr;  // legacy default stream, which cannot be captured)
+    unsigned int *bar = nullptr;  // persistent step: grid barrier state (device, 4 words)
     int *h_cnt = nullptr;      // pinned mirror of the device counters
     double *h_dt = nullptr;    // pinned: dt used, dt next (instance 0)
     double t = 0.0;

@@ -37,11 +37,9 @@ constexpr int kListBlocks = 152 * 8;
 // each neighbour weighted by the number of nodes it shares with the cell).
 // ---------------------------------------------------------------------------------------
 // B: threads per block (a launch-shape variant chosen by the autotuner; same arithmetic)
-template <int D, int B = kNodeBlock> __global__ void __launch_bounds__(B) k_moments(Geo g, Fld f) {
+template <int D> __device__ __forceinline__ void moments_node(const Geo &g, const Fld &f, int p) {
     using Q = Dim<D>;
     constexpr int NS = Q::NS, NQ = Q::NQ, DD = D * D;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= g.Np) return;
     const int N = g.N, Np = g.Np;
     double xp[D], S1[D], S2[NS], U[NQ], T[NQ][D], n = 0.0;
 #pragma unroll
@@ -94,6 +92,11 @@ template <int D, int B = kNodeBlock> __global__ void __launch_bounds__(B) k_mome
 #pragma unroll
         for (int a = 0; a < D; ++a) m[(Q::M_T + q * D + a) * Np] = T[q][a];
     }
+}
+
+template <int D, int B = kNodeBlock> __global__ void __launch_bounds__(B) k_moments(Geo g, Fld f) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < g.Np) moments_node<D>(g, f, p);
 }
 
 // MAT: 0 neo-Hookean, 1 another shear energy of the family, 2 stiffened gas (separate
@@ -825,10 +828,9 @@ static __global__ void k_ctl_reset(Ctl *ctl) {
 
 // troubled cells become P0; their nodes are appended (once) to the node list
 template <int D>
-__global__ void k_mark_nodes(Geo g, Fld f, Prm prm, const int *__restrict__ tlist, const int *__restrict__ tcnt,
-                             int *node_mark, const Ctl *ctl, int *nlist) {
-    const int n = *tcnt, stamp = ctl->stamp;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void mark_nodes_range(const Geo &g, const Fld &f, const Prm &prm, const int *tlist, int n,
+                                                 int *node_mark, int stamp, int *nlist, int i0, int di) {
+    for (int i = i0; i < n; i += di) {
         const int c = tlist[i];
         f.order[c] = (f.order[c] == 2 && prm.cascade == 3) ? 3 : 1;  // one level down the cascade
 #pragma unroll
@@ -839,11 +841,17 @@ __global__ void k_mark_nodes(Geo g, Fld f, Prm prm, const int *__restrict__ tlis
     }
 }
 
+template <int D>
+__global__ void k_mark_nodes(Geo g, Fld f, Prm prm, const int *__restrict__ tlist, const int *__restrict__ tcnt,
+                             int *node_mark, const Ctl *ctl, int *nlist) {
+    mark_nodes_range<D>(g, f, prm, tlist, *tcnt, node_mark, ctl->stamp, nlist, blockIdx.x * blockDim.x + threadIdx.x,
+                        gridDim.x * blockDim.x);
+}
+
 // every cell around a listed node is appended (once) to the cell list
-static __global__ void k_mark_cells(Geo g, Fld f, const int *__restrict__ nlist, int *cell_mark, const Ctl *ctl,
-                                    int *clist) {
-    const int n = f.cnt[CNT_NODES], stamp = ctl->stamp;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void mark_cells_range(const Geo &g, const Fld &f, const int *nlist, int n, int *cell_mark,
+                                                 int stamp, int *clist, int i0, int di) {
+    for (int i = i0; i < n; i += di) {
         const int p = nlist[i];
         const int j1 = g.n2c_off[p + 1];
         for (int j = g.n2c_off[p]; j < j1; ++j) {
@@ -851,6 +859,12 @@ static __global__ void k_mark_cells(Geo g, Fld f, const int *__restrict__ nlist,
             if (atomicExch(cell_mark + c, stamp) != stamp) clist[atomicAdd(f.cnt + CNT_CELLS, 1)] = c;
         }
     }
+}
+
+static __global__ void k_mark_cells(Geo g, Fld f, const int *__restrict__ nlist, int *cell_mark, const Ctl *ctl,
+                                    int *clist) {
+    mark_cells_range(g, f, nlist, f.cnt[CNT_NODES], cell_mark, ctl->stamp, clist, blockIdx.x * blockDim.x + threadIdx.x,
+                     gridDim.x * blockDim.x);
 }
 
 // while-loop condition of a graph-captured step: another MOOD round is needed
@@ -898,8 +912,9 @@ static __global__ void k_dt_init(Fld f, Prm prm, int n_inst, int first) {
 
 // min of the dt candidates per instance (positive doubles compare as their bit patterns, so
 // the result is exact and independent of the order) and the P0 / parachute counters
-static __global__ void __launch_bounds__(256) k_finalize(Geo g, Fld f, Prm prm) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+// the block's cells c0 .. c0 + blockDim.x - 1 (at most 256 threads); every thread of the block calls it
+__device__ __forceinline__ void finalize_block(const Geo &g, const Fld &f, const Prm &prm, int c0) {
+    const int c = c0 + threadIdx.x;
     const bool in = c < g.N;
     unsigned long long bits = ~0ull;
     int p0 = 0, para = 0, eps = 0, lim = 0;
@@ -915,7 +930,7 @@ static __global__ void __launch_bounds__(256) k_finalize(Geo g, Fld f, Prm prm) 
         inst = g.cell_inst ? g.cell_inst[c] : 0;
     }
     // blocks whose cells all belong to one instance reduce before the atomic
-    const int c0 = blockIdx.x * blockDim.x, c1 = min(g.N, c0 + (int)blockDim.x) - 1;
+    const int c1 = min(g.N, c0 + (int)blockDim.x) - 1;
     const bool uniform = !g.cell_inst || g.cell_inst[c0] == g.cell_inst[c1];
     __shared__ unsigned long long sb[8];
     __shared__ int si[8][4];
@@ -953,6 +968,10 @@ static __global__ void __launch_bounds__(256) k_finalize(Geo g, Fld f, Prm prm) 
         if (l) atomicAdd(f.cnt + CNT_LIM, l);
         if (uniform && m != ~0ull) atomicMin(f.dtn + (g.cell_inst ? g.cell_inst[c0] : 0), m);
     }
+}
+
+static __global__ void __launch_bounds__(256) k_finalize(Geo g, Fld f, Prm prm) {
+    finalize_block(g, f, prm, blockIdx.x * blockDim.x);
 }
 
 // initial cell state: m = rho0 |w_c|, 1/m, centroid, rho, tau, F (identity when not given),

@@ -5,6 +5,17 @@
 
 namespace lmood {
 
+// arguments of the persistent step (lmood_persistent.cuh)
+struct PersistArgs {
+    int *tl0, *tl1;                 // troubled lists of the two round parities
+    int *nlist, *clist, *node_mark, *cell_mark;
+    Ctl *ctl;
+    Report *report;
+    unsigned int *bar;              // [0] arrivals, [1] generation, [2] timeout flag (zero at launch)
+    int max_iters, n_inst;
+    long long max_spin;             // barrier wait bound in polls of ~0.1 us
+};
+
 struct Ops {
     int dim;
     int nmom;  // node moments per node
@@ -27,6 +38,8 @@ struct Ops {
                        cudaStream_t);
     void (*refresh)(const Geo &, const Fld &, const Prm &, cudaStream_t);
     void (*totals)(const Geo &, const Fld &, double *out, cudaStream_t);
+    // the whole step as one cooperative launch (neo-Hookean material)
+    cudaError_t (*persistent)(const Geo &, const Fld &, const Prm &, const PersistArgs &, cudaStream_t);
 };
 
 const Ops &ops_dim2();

@@ -2,6 +2,7 @@
 #pragma once
 #include "lmood_kernels.cuh"
 #include "lmood_ops.h"
+#include "lmood_persistent.cuh"
 
 namespace lmood {
 namespace {
@@ -107,13 +108,28 @@ template <int D> void refresh(const Geo &g, const Fld &f, const Prm &p, cudaStre
 template <int D> void totals(const Geo &g, const Fld &f, double *out, cudaStream_t s) {
     k_totals<D><<<blocks(g.N, 256), 256, 0, s>>>(g, f, out);
 }
+// cooperative launch of the persistent step: as many blocks as can be resident at once
+template <int D> cudaError_t persistent(const Geo &g, const Fld &f, const Prm &p, const PersistArgs &a, cudaStream_t s) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_persistent<D>, kCellBlock, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    Geo gg = g;
+    Fld ff = f;
+    Prm pp = p;
+    PersistArgs aa = a;
+    void *args[] = {&gg, &ff, &pp, &aa};
+    return cudaLaunchCooperativeKernel((const void *)k_step_persistent<D>, dim3(per_sm * sms), dim3(kCellBlock), args, 0, s);
+}
 
 }  // namespace
 
 #define LMOOD_OPS_TABLE(D)                                                                                  \
     static const Ops table = {D, Dim<D>::NMOM, moments<D>, predict<D>, nodes<D>,  update<D>,     mark_nodes<D>, mark_cells, \
                               round_begin, ctl_reset,  loop_cond, report,        dt_init,       finalize,   \
-                              init_cells<D>, refresh<D>, totals<D>};                                      \
+                              init_cells<D>, refresh<D>, totals<D>, persistent<D>};                                      \
     return table;
 
 }  // namespace lmood
