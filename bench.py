@@ -292,11 +292,9 @@ def run_ours(args, rank, local, ws, dist):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(k2):
-            for f, _ in fields:
-                sim.set(f, bufs[f])
+            sim.set_fields(bufs)
             sim.step()
-            for f, _ in fields:
-                sim.get(f, out=bufs[f])
+            sim.get_fields(bufs)
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t0, dist)
         e2e = {"value": ws * N * k2 / el, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,

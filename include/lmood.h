@@ -227,6 +227,17 @@ lmood_status lmood_run(lmood_state s, int64_t nsteps, lmood_step_info *last);
 lmood_status lmood_get(lmood_state s, int field, void *dst, int is_device);
 lmood_status lmood_set(lmood_state s, int field, const void *src, int is_device);
 
+/*
+ * Several fields in one call: the n copies are queued on the mesh's stream back to back and,
+ * for host pointers, the call synchronises once at the end (set: the derived cell geometry
+ * is refreshed once, after the last copy, when X or F is among the fields). fields[i] and
+ * dst[i] / src[i] as for lmood_get / lmood_set; all host or all device (is_device).
+ * Errors: LMOOD_ERR_ARG for a NULL pointer, an unknown or (set) read-only field id, or ORDER
+ * requested twice in one get; every argument is checked before the first copy.
+ */
+lmood_status lmood_get_fields(lmood_state s, int n, const int *fields, void *const *dst, int is_device);
+lmood_status lmood_set_fields(lmood_state s, int n, const int *fields, const void *const *src, int is_device);
+
 /* Sums over cells of m_c, m_c v_c and m_c e_c (out: mass, mom[dim], energy; 5 doubles). */
 lmood_status lmood_totals(lmood_state s, double *out5);
 

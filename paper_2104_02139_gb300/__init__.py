@@ -47,6 +47,7 @@ _lib = None
 EXPORTS = ("lmood_params_default", "lmood_mesh_create", "lmood_mesh_destroy", "lmood_mesh_info",
            "lmood_mesh_set_bc_values", "lmood_mesh_set_btag", "lmood_mesh_set_contact",
            "lmood_state_init", "lmood_state_destroy", "lmood_step", "lmood_run", "lmood_get", "lmood_set",
+           "lmood_get_fields", "lmood_set_fields",
            "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_autotune", "lmood_totals_noalloc",
            "lmood_tape_record",
            "lmood_tape_backward", "lmood_tape_replay", "lmood_tape_info", "lmood_tape_destroy", "lmood_last_error")
@@ -76,6 +77,8 @@ def lib():
         L.lmood_run.argtypes = [vp, C.c_int64, C.POINTER(StepInfo)]
         L.lmood_get.argtypes = [vp, C.c_int, vp, C.c_int]
         L.lmood_set.argtypes = [vp, C.c_int, vp, C.c_int]
+        L.lmood_get_fields.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(vp), C.c_int]
+        L.lmood_set_fields.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(vp), C.c_int]
         L.lmood_totals.argtypes = [vp, C.POINTER(C.c_double)]
         L.lmood_timing.argtypes = [vp, C.c_int]
         L.lmood_timing_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
@@ -244,6 +247,29 @@ class State:
             _check(lib().lmood_set(self.h, field, a.ctypes.data, 0))
         else:
             _check(lib().lmood_set(self.h, field, C.c_void_p(src.data_ptr()), 1))
+
+    def get_fields(self, outs: dict) -> dict:
+        """lmood_get_fields: {field id: destination} all numpy (one synchronisation at the end)
+        or all torch CUDA tensors"""
+        ids = list(outs)
+        host = isinstance(outs[ids[0]], np.ndarray)
+        for f in ids:
+            o = outs[f]
+            if host != isinstance(o, np.ndarray) or (host and not (o.dtype == np.float64 and o.flags.c_contiguous)):
+                raise ValueError("get_fields: destinations must be all contiguous float64 numpy or all CUDA tensors")
+        ptrs = [outs[f].ctypes.data if host else outs[f].data_ptr() for f in ids]
+        _check(lib().lmood_get_fields(self.h, len(ids), (C.c_int * len(ids))(*ids),
+                                      (C.c_void_p * len(ids))(*ptrs), 0 if host else 1))
+        return outs
+
+    def set_fields(self, srcs: dict):
+        """lmood_set_fields: {field id: source}, all host arrays or all torch CUDA tensors"""
+        ids = list(srcs)
+        host = not hasattr(srcs[ids[0]], "data_ptr")
+        keep = [np.ascontiguousarray(srcs[f], dtype=np.float64) if host else srcs[f].contiguous() for f in ids]
+        ptrs = [a.ctypes.data if host else a.data_ptr() for a in keep]
+        _check(lib().lmood_set_fields(self.h, len(ids), (C.c_int * len(ids))(*ids),
+                                      (C.c_void_p * len(ids))(*ptrs), 0 if host else 1))
 
     def totals(self) -> np.ndarray:
         o = (C.c_double * 5)()

@@ -941,68 +941,113 @@ __global__ static void k_u8_to_f64(const unsigned char *a, double *b, int n) {
     if (i < n) b[i] = a[i];
 }
 
-extern "C" lmood_status lmood_get(lmood_state s, int field, void *dst, int is_device) {
-    if (!s || !dst) return fail(LMOOD_ERR_ARG, "lmood_get: NULL argument");
+// device source of a readable field (ORDER is converted to doubles in scratch first)
+static lmood_status get_source(lmood_state s, int field, const void **src, size_t *bytes) {
     lmood_mesh M = s->M;
     const int D = M->dim, NV = D + 1, NS = D * (D + 1) / 2;
     const size_t N = M->nc, Np = M->np, nd = sizeof(double);
-    cudaStream_t st = M->st;
     const Fld &f = s->f;
-    const void *src = nullptr;
-    size_t bytes = 0;
     switch (field) {
-    case LMOOD_FIELD_X: src = f.x; bytes = D * Np * nd; break;
-    case LMOOD_FIELD_VP: src = f.vp; bytes = D * Np * nd; break;
-    case LMOOD_FIELD_VSTAR: src = f.vs; bytes = D * Np * nd; break;
-    case LMOOD_FIELD_V: src = f.v; bytes = D * N * nd; break;
-    case LMOOD_FIELD_E: src = f.e; bytes = N * nd; break;
-    case LMOOD_FIELD_F: src = f.F; bytes = D * D * N * nd; break;
-    case LMOOD_FIELD_TAU: src = s->tau; bytes = N * nd; break;
-    case LMOOD_FIELD_MASS: src = s->m; bytes = N * nd; break;
-    case LMOOD_FIELD_PKM: src = f.pkM; bytes = NS * NV * N * nd; break;
-    case LMOOD_FIELD_PKR: src = f.pkR; bytes = D * NV * N * nd; break;
-    case LMOOD_FIELD_DT: src = f.dt; bytes = M->n_inst * nd; break;
+    case LMOOD_FIELD_X: *src = f.x; *bytes = D * Np * nd; break;
+    case LMOOD_FIELD_VP: *src = f.vp; *bytes = D * Np * nd; break;
+    case LMOOD_FIELD_VSTAR: *src = f.vs; *bytes = D * Np * nd; break;
+    case LMOOD_FIELD_V: *src = f.v; *bytes = D * N * nd; break;
+    case LMOOD_FIELD_E: *src = f.e; *bytes = N * nd; break;
+    case LMOOD_FIELD_F: *src = f.F; *bytes = D * D * N * nd; break;
+    case LMOOD_FIELD_TAU: *src = s->tau; *bytes = N * nd; break;
+    case LMOOD_FIELD_MASS: *src = s->m; *bytes = N * nd; break;
+    case LMOOD_FIELD_PKM: *src = f.pkM; *bytes = NS * NV * N * nd; break;
+    case LMOOD_FIELD_PKR: *src = f.pkR; *bytes = D * NV * N * nd; break;
+    case LMOOD_FIELD_DT: *src = f.dt; *bytes = M->n_inst * nd; break;
     case LMOOD_FIELD_ORDER: {
         double *tmp = (double *)f.dtc;  // the dt candidates are rebuilt every step
-        k_u8_to_f64<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(f.order, tmp, (int)N);
-        src = tmp;
-        bytes = N * nd;
+        k_u8_to_f64<<<(unsigned)((N + 255) / 256), 256, 0, M->st>>>(f.order, tmp, (int)N);
+        *src = tmp;
+        *bytes = N * nd;
         break;
     }
     default: return fail(LMOOD_ERR_ARG, "lmood_get: unknown field id");
     }
-    LM_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    if (!is_device) return sync_check(s, "lmood_get");
     return LMOOD_OK;
 }
 
-extern "C" lmood_status lmood_set(lmood_state s, int field, const void *src, int is_device) {
-    if (!s || !src) return fail(LMOOD_ERR_ARG, "lmood_set: NULL argument");
+// device destination of a settable field
+static lmood_status set_target(lmood_state s, int field, void **dst, size_t *bytes) {
     lmood_mesh M = s->M;
     const int D = M->dim;
     const size_t N = M->nc, Np = M->np, nd = sizeof(double);
-    cudaStream_t st = M->st;
     Fld &f = s->f;
-    void *dst = nullptr;
-    size_t bytes = 0;
     switch (field) {
-    case LMOOD_FIELD_X: dst = f.x; bytes = D * Np * nd; break;
-    case LMOOD_FIELD_VP: dst = f.vp; bytes = D * Np * nd; break;
-    case LMOOD_FIELD_V: dst = f.v; bytes = D * N * nd; break;
-    case LMOOD_FIELD_E: dst = f.e; bytes = N * nd; break;
-    case LMOOD_FIELD_F: dst = f.F; bytes = D * D * N * nd; break;
-    case LMOOD_FIELD_DT: dst = const_cast<double *>(f.dt); bytes = M->n_inst * nd; break;
+    case LMOOD_FIELD_X: *dst = f.x; *bytes = D * Np * nd; break;
+    case LMOOD_FIELD_VP: *dst = f.vp; *bytes = D * Np * nd; break;
+    case LMOOD_FIELD_V: *dst = f.v; *bytes = D * N * nd; break;
+    case LMOOD_FIELD_E: *dst = f.e; *bytes = N * nd; break;
+    case LMOOD_FIELD_F: *dst = f.F; *bytes = D * D * N * nd; break;
+    case LMOOD_FIELD_DT: *dst = const_cast<double *>(f.dt); *bytes = M->n_inst * nd; break;
     default: return fail(LMOOD_ERR_ARG, "lmood_set: unknown or read-only field id");
     }
-    LM_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    if (field != LMOOD_FIELD_DT) s->at_init = false;
-    if (field == LMOOD_FIELD_X || field == LMOOD_FIELD_F) {
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_get_fields(lmood_state s, int n, const int *fields, void *const *dst, int is_device) {
+    if (!s || n < 0 || (n > 0 && (!fields || !dst))) return fail(LMOOD_ERR_ARG, "lmood_get_fields: bad argument");
+    for (int i = 0; i < n; ++i) {
+        if (!dst[i]) return fail(LMOOD_ERR_ARG, "lmood_get_fields: NULL destination");
+        if (fields[i] < 0 || fields[i] > LMOOD_FIELD_DT) return fail(LMOOD_ERR_ARG, "lmood_get_fields: unknown field id");
+        for (int j = 0; j < i; ++j)  // ORDER shares its scratch: at most once per call
+            if (fields[i] == LMOOD_FIELD_ORDER && fields[j] == LMOOD_FIELD_ORDER)
+                return fail(LMOOD_ERR_ARG, "lmood_get_fields: ORDER requested twice");
+    }
+    cudaStream_t st = s->M->st;
+    for (int i = 0; i < n; ++i) {
+        const void *src = nullptr;
+        size_t bytes = 0;
+        lmood_status r = get_source(s, fields[i], &src, &bytes);
+        if (r) return r;
+        LM_CUDA(cudaMemcpyAsync(dst[i], src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    }
+    if (!is_device) return sync_check(s, "lmood_get_fields");
+    return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_set_fields(lmood_state s, int n, const int *fields, const void *const *src, int is_device) {
+    if (!s || n < 0 || (n > 0 && (!fields || !src))) return fail(LMOOD_ERR_ARG, "lmood_set_fields: bad argument");
+    for (int i = 0; i < n; ++i) {  // validate everything before the first copy
+        void *dst = nullptr;
+        size_t bytes = 0;
+        if (!src[i]) return fail(LMOOD_ERR_ARG, "lmood_set_fields: NULL source");
+        lmood_status r = set_target(s, fields[i], &dst, &bytes);
+        if (r) return r;
+    }
+    lmood_mesh M = s->M;
+    cudaStream_t st = M->st;
+    bool geo = false;
+    for (int i = 0; i < n; ++i) {
+        void *dst = nullptr;
+        size_t bytes = 0;
+        set_target(s, fields[i], &dst, &bytes);
+        LM_CUDA(cudaMemcpyAsync(dst, src[i], bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        if (fields[i] != LMOOD_FIELD_DT) s->at_init = false;
+        geo = geo || fields[i] == LMOOD_FIELD_X || fields[i] == LMOOD_FIELD_F;
+    }
+    if (geo) {  // derived cell geometry, density and impedance from the new x and F
+        Fld &f = s->f;
         std::swap(s->tau, f.tau1);
         M->ops->refresh(M->geo, f, s->kp, st);
         std::swap(s->tau, f.tau1);
     }
-    if (!is_device) return sync_check(s, "lmood_set");
+    if (!is_device) return sync_check(s, "lmood_set_fields");
     return LMOOD_OK;
+}
+
+extern "C" lmood_status lmood_get(lmood_state s, int field, void *dst, int is_device) {
+    if (!s || !dst) return fail(LMOOD_ERR_ARG, "lmood_get: NULL argument");
+    return lmood_get_fields(s, 1, &field, &dst, is_device);
+}
+
+extern "C" lmood_status lmood_set(lmood_state s, int field, const void *src, int is_device) {
+    if (!s || !src) return fail(LMOOD_ERR_ARG, "lmood_set: NULL argument");
+    return lmood_set_fields(s, 1, &field, &src, is_device);
 }
 
 extern "C" lmood_status lmood_totals(lmood_state s, double *out5) {
