@@ -190,18 +190,13 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
         // least-squares sums over the (node, neighbour) pairs from the node moments:
         // with d = x_p - x_c, dx' = (x_c' - x_p) + d, so
         //   G += S2 + S1 d^t + d S1^t + n d d^t,   r_q += T_q + d U_q - (S1 + n d) q_c
-        // (the cell itself is one of the node's cells and contributes zero)
+        // (the cell itself is one of the node's cells and contributes zero); the q_c terms of
+        // the D+1 nodes are gathered into one: r_q = sum_p (T_q + d U_q) - (sum_p w) q_c
         using Q = Dim<D>;
         double xcc[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) xcc[a] = f.xc[a * N + c];
-        double G[NS], r[NQ][D];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) G[s] = 0.0;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q)
-#pragma unroll
-            for (int a = 0; a < D; ++a) r[q][a] = 0.0;
+        double G[NS], r[NQ][D], wsum[D];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             const double *m = f.mom + nod[k];
@@ -212,22 +207,31 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
                 d[a] = xs[k][a] - xcc[a];
                 S1[a] = m[(Q::M_S1 + a) * Np];
                 w[a] = fma(nn, d[a], S1[a]);
+                wsum[a] = k == 0 ? w[a] : wsum[a] + w[a];
             }
 #pragma unroll
             for (int a = 0; a < D; ++a)
 #pragma unroll
                 for (int b = a; b < D; ++b) {
                     const int sb = sidx<D>(a, b);
-                    G[sb] += m[(Q::M_S2 + sb) * Np] + fma(S1[a], d[b], fma(d[a], w[b], 0.0));
+                    const double t = m[(Q::M_S2 + sb) * Np] + fma(S1[a], d[b], d[a] * w[b]);
+                    G[sb] = k == 0 ? t : G[sb] + t;
                 }
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const double uq = m[(Q::M_U + q) * Np];
-                const double qc = q < D ? vc[q] : Fc[q - D];
 #pragma unroll
-                for (int a = 0; a < D; ++a)
-                    r[q][a] += fma(d[a], uq, fma(-w[a], qc, m[(Q::M_T + q * D + a) * Np]));
+                for (int a = 0; a < D; ++a) {
+                    const double tq = m[(Q::M_T + q * D + a) * Np];
+                    r[q][a] = k == 0 ? fma(d[a], uq, tq) : fma(d[a], uq, r[q][a] + tq);
+                }
             }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const double qc = q < D ? vc[q] : Fc[q - D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) r[q][a] = fma(-wsum[a], qc, r[q][a]);
         }
         double Gf[DD], Gi[DD], gs[NQ][D];
 #pragma unroll
