@@ -87,9 +87,9 @@ def kernel_bytes(dim: int, nc: int, npn: int, nnz: int) -> dict:
 # divided by the cell count; they include the FP64 expansions of division, sqrt, log, cbrt.
 # Re-measured whenever a kernel changes (profiles/ holds the capture); None = not measured
 # for the current kernel.
-FP64_FLOP_PER_CELL = {"predict": 921.0, "update": 404.1, "nodes": 31.1, "moments": 123.0}
+FP64_FLOP_PER_CELL = {"predict": 861.0, "update": 384.0, "nodes": 31.1, "moments": 123.0}
 # DRAM bytes (read + write) per full launch from the same ncu capture, or None.
-TRAFFIC_PER_LAUNCH = {"predict": 295.47e6, "update": 341.20e6, "nodes": 177.78e6, "moments": 134.59e6}
+TRAFFIC_PER_LAUNCH = {"predict": 295.76e6, "update": 341.39e6, "nodes": 177.94e6, "moments": 134.59e6}
 
 
 def fp64_peak_tflops(device) -> float:

@@ -548,8 +548,8 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
         return fail(LMOOD_ERR_ARG, "lmood_state_init: shear_a must lie in [-1, 1/2]");
     if (mat->eos != 0 && !(mat->eos == 1 && mat->gamma > 1.0 && mat->p0 + mat->p_inf > 0.0))
         return fail(LMOOD_ERR_ARG, "lmood_state_init: eos must be 0, or 1 with gamma > 1 and p0 + p_inf > 0");
-    if (prm->graph < 0 || prm->graph > 2 || (prm->graph == 2 && (mat->shear_a != -1.0 || mat->eos != 0)))
-        return fail(LMOOD_ERR_ARG, "lmood_state_init: graph must be 0, 1 or 2 (2: neo-Hookean material only)");
+    if (prm->graph < 0 || prm->graph > 3 || (prm->graph == 2 && (mat->shear_a != -1.0 || mat->eos != 0)))
+        return fail(LMOOD_ERR_ARG, "lmood_state_init: graph must be 0, 1, 2 or 3 (2: neo-Hookean material only)");
     if (!(prm->cfl > 0) || prm->max_mood_iters < 0 || (prm->order != 1 && prm->order != 2) ||
         (prm->cascade != 2 && prm->cascade != 3))
         return fail(LMOOD_ERR_ARG, "lmood_state_init: bad parameters");
@@ -690,6 +690,24 @@ static void enqueue_mood_round(lmood_state s, const Fld &f, int cur, int n_in, c
     op.update(g, f, s->kp, s->clist, f.cnt + CNT_CELLS, nb_cells, s->tl[cur ^ 1], f.cnt + out, st);
 }
 
+// arguments of the persistent kernels for the state's current buffers
+static PersistArgs persist_args(lmood_state s) {
+    PersistArgs a{};
+    a.tl0 = s->tl[0];
+    a.tl1 = s->tl[1];
+    a.nlist = s->nlist;
+    a.clist = s->clist;
+    a.node_mark = s->node_mark;
+    a.cell_mark = s->cell_mark;
+    a.ctl = s->ctl;
+    a.report = s->d_report;
+    a.bar = s->bar;
+    a.max_iters = s->prm.max_mood_iters;
+    a.n_inst = s->M->n_inst;
+    a.max_spin = s->prm.barrier_polls > 0 ? s->prm.barrier_polls : 100000000;  // polls of ~0.1 us
+    return a;
+}
+
 static lmood_status build_graph(lmood_state s, int par) {
     lmood_mesh M = s->M;
     const Ops &op = *M->ops;
@@ -700,8 +718,8 @@ static lmood_status build_graph(lmood_state s, int par) {
     cudaGraph_t G = nullptr;
     LM_CUDA(cudaGraphCreate(&G, 0));
     s->graph[par] = G;
-    cudaGraphConditionalHandle h;
-    LM_CUDA(cudaGraphConditionalHandleCreate(&h, G, 0, cudaGraphCondAssignDefault));
+    cudaGraphConditionalHandle h{};
+    if (s->prm.graph != 3) LM_CUDA(cudaGraphConditionalHandleCreate(&h, G, 0, cudaGraphCondAssignDefault));
     for (auto &e : s->gev[par]) LM_CUDA(cudaEventCreate(&e));
     cudaEvent_t *ev = s->gev[par];
     LM_CUDA(cudaStreamBeginCaptureToGraph(st, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -716,11 +734,19 @@ static lmood_status build_graph(lmood_state s, int par) {
     cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
     op.update(g, f, s->kp, nullptr, nullptr, N, s->tl[0], f.cnt + CNT_T0, st);
     cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
+    cudaError_t e = cudaSuccess;
+    const char *where = "capture";
+    if (s->prm.graph == 3) {
+        // the MOOD loop as one cooperative kernel node with grid barriers
+        where = "cooperative MOOD kernel node";
+        e = cudaMemsetAsync(s->bar, 0, 4 * sizeof(unsigned int), st);
+        if (e == cudaSuccess) e = op.mood_persistent(g, f, s->kp, persist_args(s), st);
+    } else {
     op.loop_cond(h, f, s->ctl, st);
     cudaStreamCaptureStatus cs;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
-    cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+    e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
     cudaGraphNode_t wnode = nullptr;
     cudaGraphNodeParams cp = {};
     if (e == cudaSuccess) {
@@ -742,6 +768,7 @@ static lmood_status build_graph(lmood_state s, int par) {
             e = cudaStreamEndCapture(s->body_st, &bg);
         }
     }
+    }
     if (e == cudaSuccess) {
         cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
         op.dt_init(f, s->kp, M->n_inst, 0, st);
@@ -752,11 +779,18 @@ static lmood_status build_graph(lmood_state s, int par) {
     }
     cudaGraph_t out = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(st, &out);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->gexec[par], G, 0);
+    if (e == cudaSuccess && e2 != cudaSuccess) {
+        e = e2;
+        where = "end of capture";
+    }
+    if (e == cudaSuccess) {
+        where = "instantiation";
+        e = cudaGraphInstantiate(&s->gexec[par], G, 0);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(LMOOD_ERR_CUDA, std::string("lmood_step: building the step graph failed: ") + cudaGetErrorString(e));
+        return fail(LMOOD_ERR_CUDA, std::string("lmood_step: building the step graph failed (") + where +
+                                        "): " + cudaGetErrorString(e));
     }
     return LMOOD_OK;
 }
@@ -792,6 +826,10 @@ static lmood_status finish_step(lmood_state s, const Report &rep, lmood_step_inf
     in.dt_next = rep.dt_next;
     in.t = s->t;
     in.step = s->step;
+    if (rep.err == 2) {
+        if (info) *info = in;
+        return fail(LMOOD_ERR_TIMEOUT, "lmood_step: a grid barrier wait of the MOOD loop gave up; the state is unchanged");
+    }
     if (rep.err) {
         if (info) *info = in;
         return fail(LMOOD_ERR_MOOD_ITERS, "lmood_step: troubled cells remain after max_mood_iters MOOD iterations");
@@ -837,7 +875,10 @@ static lmood_status step_graph(lmood_state s, lmood_step_info *info) {
     s->klaunch[LMOOD_K_PREDICT] += 1;
     s->klaunch[LMOOD_K_NODES] += 1;
     s->klaunch[LMOOD_K_UPDATE] += 1;
-    s->klaunch[LMOOD_K_MOOD] += 2 + 13 * ((rep.mood_iters + 1) / 2);  // ctl reset, first condition, bodies
+    if (s->prm.graph == 3)
+        s->klaunch[LMOOD_K_MOOD] += 2;  // ctl reset, the cooperative MOOD kernel
+    else
+        s->klaunch[LMOOD_K_MOOD] += 2 + 13 * ((rep.mood_iters + 1) / 2);  // ctl reset, first condition, bodies
     s->klaunch[LMOOD_K_FINALIZE] += 3;
     return finish_step(s, rep, info);
 }
@@ -887,19 +928,7 @@ static lmood_status step_persistent(lmood_state s, lmood_step_info *info) {
     lmood_mesh M = s->M;
     cudaStream_t st = M->st;
     LM_CUDA(cudaMemsetAsync(s->bar, 0, 4 * sizeof(unsigned int), st));
-    PersistArgs a{};
-    a.tl0 = s->tl[0];
-    a.tl1 = s->tl[1];
-    a.nlist = s->nlist;
-    a.clist = s->clist;
-    a.node_mark = s->node_mark;
-    a.cell_mark = s->cell_mark;
-    a.ctl = s->ctl;
-    a.report = s->d_report;
-    a.bar = s->bar;
-    a.max_iters = s->prm.max_mood_iters;
-    a.n_inst = M->n_inst;
-    a.max_spin = s->prm.barrier_polls > 0 ? s->prm.barrier_polls : 100000000;  // polls of ~0.1 us
+    const PersistArgs a = persist_args(s);
     cudaError_t e = cudaSuccess;
     timed(s, LMOOD_K_PREDICT, 1, [&] { e = M->ops->persistent(M->geo, s->f, s->kp, a, st); });
     if (e != cudaSuccess) {

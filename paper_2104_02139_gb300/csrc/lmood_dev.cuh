@@ -230,15 +230,26 @@ __device__ __forceinline__ double rcbrt_j(double J) {
     return fma(y, q, y);
 }
 
-// log J with few FP64 operations (d = J - 1):
-//  |d| <= 1/64 : Taylor series ln(1 + d) = d - d^2/2 + ... - d^10/10 (tail < 1e-20 relative);
-//  |d| <= 1/8  : ln J = 2 atanh(s) = 2 (s + s^3/3 + ... + s^13/13), s = d/(J + 1), |s| <= 1/15
+// log J with few FP64 operations (d = J - 1), the range chosen from the exponent of d with
+// integer operations:
+//  |d| < 2^-12 : Taylor series ln(1 + d) = d - d^2/2 + ... + d^5/5 (tail < 1e-22 relative; the
+//                weakly strained cells of an elastic body);
+//  |d| < 2^-6  : the series to d^10/10 (tail < 1e-20 relative);
+//  |d| < 2^-3  : ln J = 2 atanh(s) = 2 (s + s^3/3 + ... + s^13/13), s = d/(J + 1), |s| < 1/15
 //                (tail below 2e-17 relative);
 //  elsewhere (large strains, and J <= 0 which gives NaN / -inf): the CUDA log.
 __device__ __forceinline__ double log_j(double J) {
     const double d = J - 1.0;
-    const double ad = fabs(d);
-    if (ad <= 0.015625) {
+    const int E = (__double2hiint(d) >> 20) & 0x7ff;  // biased exponent of |d|
+    if (E <= 1023 - 13) {
+        double p = 1.0 / 5.0;
+        p = fma(p, d, -1.0 / 4.0);
+        p = fma(p, d, 1.0 / 3.0);
+        p = fma(p, d, -1.0 / 2.0);
+        p = fma(p, d, 1.0);
+        return d * p;
+    }
+    if (E <= 1023 - 7) {
         double p = -1.0 / 10.0;
         p = fma(p, d, 1.0 / 9.0);
         p = fma(p, d, -1.0 / 8.0);
@@ -251,7 +262,7 @@ __device__ __forceinline__ double log_j(double J) {
         p = fma(p, d, 1.0);
         return d * p;
     }
-    if (!(ad <= 0.125)) return log(J);
+    if (E > 1023 - 4) return log(J);
     const double s = d / (J + 1.0);
     const double s2 = s * s;
     double p = 1.0 / 13.0;
@@ -408,12 +419,14 @@ __device__ __forceinline__ double kappa_of(const Prm &prm, double mu) {
 template <int D>
 __device__ __forceinline__ int pad_state(const double (&v)[D], double e, const double (&F)[D * D], double V,
                                          double a0sq) {
-    bool fin = isfinite(e) && isfinite(V);
+    // finite: exponent field below all ones, tested on the high words with integer operations
+    auto expo = [](double x) { return (unsigned)__double2hiint(x) & 0x7ff00000u; };
+    unsigned inf = (expo(e) + 0x00100000u) | (expo(V) + 0x00100000u);
 #pragma unroll
-    for (int i = 0; i < D; ++i) fin = fin && isfinite(v[i]);
+    for (int i = 0; i < D; ++i) inf |= expo(v[i]) + 0x00100000u;
 #pragma unroll
-    for (int i = 0; i < D * D; ++i) fin = fin && isfinite(F[i]);
-    if (!fin || !(V > 0.0) || !(det<D>(F) > 0.0)) return 2;
+    for (int i = 0; i < D * D; ++i) inf |= expo(F[i]) + 0x00100000u;
+    if ((inf & 0x80000000u) || !(V > 0.0) || !(det<D>(F) > 0.0)) return 2;
     double ke = 0.0;
 #pragma unroll
     for (int i = 0; i < D; ++i) ke += 0.5 * v[i] * v[i];

@@ -628,9 +628,9 @@ __global__ void __launch_bounds__(B) k_nodes(Geo g, Fld f, const int *__restrict
 // velocity gradient L_ij = (1/|w_c|) sum_p v_{p,i} ln_{p,j} (Eq. div_grad_v, read so that
 // dF/dt = L F), with ln_p = -N_p / D: L = -(1 / (D |w_c|)) sum_p v_p (x) N_p
 template <int D>
-__device__ __forceinline__ void vel_gradient(const double (&vn)[D + 1][D], const double (&Nf)[D + 1][D], double V,
+__device__ __forceinline__ void vel_gradient(const double (&vn)[D + 1][D], const double (&Nf)[D + 1][D], double iV,
                                              double (&L)[D * D]) {
-    const double s0 = -1.0 / (D * V);
+    const double s0 = iV * (-1.0 / D);  // iV = 1 / |w_c|
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -694,6 +694,7 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
     double V0, Nf0[NV][D], V1, Nf1[NV][D];
     simplex_faces<D>(xs0, V0, Nf0);
     simplex_faces<D>(xs1, V1, Nf1);
+    const double iV0 = 1.0 / V0, iV1 = 1.0 / V1;
     double Fn[DD], F1[DD];
 #pragma unroll
     for (int q = 0; q < DD; ++q) Fn[q] = f.F[q * N + c];
@@ -703,12 +704,12 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
         for (int k = 0; k < NV; ++k)
 #pragma unroll
             for (int a = 0; a < D; ++a) vn[k][a] = f.vp[a * Np + nod[k]];
-        vel_gradient<D>(vn, Nf0, V0, L0);
+        vel_gradient<D>(vn, Nf0, iV0, L0);
 #pragma unroll
         for (int k = 0; k < NV; ++k)
 #pragma unroll
             for (int a = 0; a < D; ++a) vn[k][a] = f.vp1[a * Np + nod[k]];
-        vel_gradient<D>(vn, Nf1, V1, L1);
+        vel_gradient<D>(vn, Nf1, iV1, L1);
 #pragma unroll
         for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -722,7 +723,7 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
         matmul<D>(Ai, R, F1);
     } else {
         double Ls[DD], LF[DD];
-        vel_gradient<D>(vsn, Nf0, V0, Ls);
+        vel_gradient<D>(vsn, Nf0, iV0, Ls);
         matmul<D>(Ls, Fn, LF);
 #pragma unroll
         for (int q = 0; q < DD; ++q) F1[q] = fma(dt, LF[q], Fn[q]);
@@ -738,7 +739,7 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
     f.e1[c] = e1;
 #pragma unroll
     for (int q = 0; q < DD; ++q) f.F1[q * N + c] = F1[q];
-    const double rho1 = mc / V1;
+    const double rho1 = mc * iV1;
     f.rho1[c] = rho1;
     f.tau1[c] = V1 * im;
     double area1 = 0.0;  // sum of the face measures at x^{n+1} (in-sphere diameter 2 D V / area)
@@ -785,10 +786,12 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
         z1 = impedance<D>(F1, rho1, muc, kap);
     }
     f.z1[c] = z1;
-    double dtc = prm.cfl * (2.0 * D) * mc / (area1 * z1);
-    const double dV = V1 - V0;
-    if (dV != 0.0) dtc = fmin(dtc, prm.Cv * dt * V0 / fabs(dV));
-    f.dtc[c] = dtc;
+    // min(A / B, C / |dV|) with one division: compare A |dV| with C B (B, |dV| > 0; a NaN
+    // quotient A / B loses, as in fmin)
+    const double A = prm.cfl * (2.0 * D) * mc, B = area1 * z1;
+    const double dV = fabs(V1 - V0), C = prm.Cv * dt * V0;
+    const bool vol = dV != 0.0 && !(A * dV <= C * B);
+    f.dtc[c] = vol ? C / dV : A / B;
 }
 
 template <int D, bool LISTED, int B = kCellBlock>
@@ -1061,7 +1064,7 @@ template <int D> __global__ void __launch_bounds__(kCellBlock) k_refresh(Geo g, 
         for (int k = 0; k < NV; ++k) s += xs[k][a];
         f.xc[a * g.N + c] = s * (1.0 / NV);
     }
-    const double rho = f.m[c] / V;
+    const double rho = f.m[c] * (1.0 / V);  // as the update computes it, so that a restart is bitwise
     f.rho[c] = rho;
     f.tau1[c] = V * f.im[c];
     double F[DD];

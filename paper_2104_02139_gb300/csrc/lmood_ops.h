@@ -40,6 +40,8 @@ struct Ops {
     void (*totals)(const Geo &, const Fld &, double *out, cudaStream_t);
     // the whole step as one cooperative launch (neo-Hookean material)
     cudaError_t (*persistent)(const Geo &, const Fld &, const Prm &, const PersistArgs &, cudaStream_t);
+    // the MOOD loop alone as one cooperative launch (capturable in a graph)
+    cudaError_t (*mood_persistent)(const Geo &, const Fld &, const Prm &, const PersistArgs &, cudaStream_t);
 };
 
 const Ops &ops_dim2();

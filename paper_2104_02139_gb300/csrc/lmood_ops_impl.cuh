@@ -108,20 +108,34 @@ template <int D> void refresh(const Geo &g, const Fld &f, const Prm &p, cudaStre
 template <int D> void totals(const Geo &g, const Fld &f, double *out, cudaStream_t s) {
     k_totals<D><<<blocks(g.N, 256), 256, 0, s>>>(g, f, out);
 }
-// cooperative launch of the persistent step: as many blocks as can be resident at once
-template <int D> cudaError_t persistent(const Geo &g, const Fld &f, const Prm &p, const PersistArgs &a, cudaStream_t s) {
+// cooperative launch of a persistent kernel: as many blocks as can be resident at once
+template <typename K>
+static cudaError_t launch_cooperative(K kern, const Geo &g, const Fld &f, const Prm &p, const PersistArgs &a,
+                                      cudaStream_t s) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_persistent<D>, kCellBlock, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCellBlock, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    Geo gg = g;
-    Fld ff = f;
-    Prm pp = p;
-    PersistArgs aa = a;
-    void *args[] = {&gg, &ff, &pp, &aa};
-    return cudaLaunchCooperativeKernel((const void *)k_step_persistent<D>, dim3(per_sm * sms), dim3(kCellBlock), args, 0, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(per_sm * sms);
+    cfg.blockDim = dim3(kCellBlock);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, g, f, p, a);
+}
+template <int D> cudaError_t persistent(const Geo &g, const Fld &f, const Prm &p, const PersistArgs &a, cudaStream_t s) {
+    return launch_cooperative(k_step_persistent<D>, g, f, p, a, s);
+}
+template <int D> cudaError_t mood_persistent(const Geo &g, const Fld &f, const Prm &p, const PersistArgs &a, cudaStream_t s) {
+    if (p.eos) return launch_cooperative(k_mood_persistent<D, 2>, g, f, p, a, s);
+    if (p.shear_a != -1.0) return launch_cooperative(k_mood_persistent<D, 1>, g, f, p, a, s);
+    return launch_cooperative(k_mood_persistent<D, 0>, g, f, p, a, s);
 }
 
 }  // namespace
@@ -129,7 +143,7 @@ template <int D> cudaError_t persistent(const Geo &g, const Fld &f, const Prm &p
 #define LMOOD_OPS_TABLE(D)                                                                                  \
     static const Ops table = {D, Dim<D>::NMOM, moments<D>, predict<D>, nodes<D>,  update<D>,     mark_nodes<D>, mark_cells, \
                               round_begin, ctl_reset,  loop_cond, report,        dt_init,       finalize,   \
-                              init_cells<D>, refresh<D>, totals<D>, persistent<D>};                                      \
+                              init_cells<D>, refresh<D>, totals<D>, persistent<D>, mood_persistent<D>};                                      \
     return table;
 
 }  // namespace lmood

@@ -55,6 +55,55 @@ __device__ __forceinline__ bool grid_sync(unsigned int *bar, long long max_spin)
 
 __device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
 
+// The MOOD rounds (as k_round_begin, k_mark_nodes, k_mark_cells and the list launches of
+// the predictor, nodal solver and update) over the troubled list left in tl0 / cnt[CNT_T0];
+// tid / nth: this thread's spread index and the grid's thread count. False when a barrier
+// gave up.
+template <int D, int MAT>
+__device__ __forceinline__ bool mood_rounds(const Geo &g, const Fld &f, const Prm &prm, const PersistArgs &a, int tid,
+                                            int nth) {
+    for (int cur = 0;; cur ^= 1) {
+        const int in = CNT_T0 + cur, out = CNT_T0 + (cur ^ 1);
+        const int n_in = vload(f.cnt + in);  // written before the last barrier: the same in every block
+        if (n_in == 0) return true;
+        if (tid == 0) {
+            if (a.ctl->iters >= a.max_iters) {
+                a.ctl->err = 1;
+            } else {
+                a.ctl->iters += 1;
+                a.ctl->troubled += n_in;
+                a.ctl->stamp += 1;
+            }
+            f.cnt[out] = 0;
+            f.cnt[CNT_NODES] = 0;
+            f.cnt[CNT_CELLS] = 0;
+        }
+        if (!grid_sync(a.bar, a.max_spin)) return false;
+        if (vload(&a.ctl->err)) return true;
+        const int stamp = vload(&a.ctl->stamp);
+        int *tin = cur ? a.tl1 : a.tl0, *tout = cur ? a.tl0 : a.tl1;
+        mark_nodes_range<D>(g, f, prm, tin, n_in, a.node_mark, stamp, a.nlist, tid, nth);
+        if (!grid_sync(a.bar, a.max_spin)) return false;
+        const int nn = vload(f.cnt + CNT_NODES);
+        mark_cells_range(g, f, a.nlist, nn, a.cell_mark, stamp, a.clist, tid, nth);
+        if (!grid_sync(a.bar, a.max_spin)) return false;
+        for (int i = tid; i < n_in; i += nth) predict_cell<D, true, MAT>(g, f, prm, tin[i]);
+        if (!grid_sync(a.bar, a.max_spin)) return false;
+        for (int i = tid; i < nn; i += nth) node_solve<D>(g, f, a.nlist[i], 0);
+        if (!grid_sync(a.bar, a.max_spin)) return false;
+        const int nc = vload(f.cnt + CNT_CELLS);
+        for (int i = tid; i < nc; i += nth) update_cell<D>(g, f, prm, a.clist[i], tout, f.cnt + out);
+        if (!grid_sync(a.bar, a.max_spin)) return false;
+    }
+}
+
+// work item i goes to warp i / 32 of the grid counted block-fastest (warp w of block b is
+// warp w * gridDim.x + b), so that a small mesh's cells spread over all SMs and their
+// sub-partitions instead of filling the first blocks' warps
+__device__ __forceinline__ int spread_index() {
+    return ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
+}
+
 #ifndef LMOOD_PERSIST_MINB2
 #define LMOOD_PERSIST_MINB2 2
 #endif
@@ -62,11 +111,7 @@ __device__ __forceinline__ int vload(const int *p) { return *(const volatile int
 template <int D>
 __global__ void __launch_bounds__(kCellBlock, D == 2 ? LMOOD_PERSIST_MINB2 : 1)
     k_step_persistent(Geo g, Fld f, Prm prm, PersistArgs a) {
-    // work item i goes to warp i / 32 of the grid counted block-fastest (warp w of block b is
-    // warp w * gridDim.x + b), so that a small mesh's cells spread over all SMs and their
-    // sub-partitions instead of filling the first blocks' warps
-    const int nth = gridDim.x * blockDim.x;
-    const int tid = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
+    const int nth = gridDim.x * blockDim.x, tid = spread_index();
     const int N = g.N, Np = g.Np;
     // step set-up: counters, MOOD control, next-dt initial value (as k_ctl_reset, k_dt_init)
     if (tid == 0) {
@@ -88,40 +133,7 @@ __global__ void __launch_bounds__(kCellBlock, D == 2 ? LMOOD_PERSIST_MINB2 : 1)
     if (!grid_sync(a.bar, a.max_spin)) return;
     for (int c = tid; c < N; c += nth) update_cell<D>(g, f, prm, c, a.tl0, f.cnt + CNT_T0);
     if (!grid_sync(a.bar, a.max_spin)) return;
-    // MOOD rounds (as k_round_begin, k_mark_nodes, k_mark_cells and the list launches)
-    for (int cur = 0;; cur ^= 1) {
-        const int in = CNT_T0 + cur, out = CNT_T0 + (cur ^ 1);
-        const int n_in = vload(f.cnt + in);  // written before the last barrier: the same in every block
-        if (n_in == 0) break;
-        if (tid == 0) {
-            if (a.ctl->iters >= a.max_iters) {
-                a.ctl->err = 1;
-            } else {
-                a.ctl->iters += 1;
-                a.ctl->troubled += n_in;
-                a.ctl->stamp += 1;
-            }
-            f.cnt[out] = 0;
-            f.cnt[CNT_NODES] = 0;
-            f.cnt[CNT_CELLS] = 0;
-        }
-        if (!grid_sync(a.bar, a.max_spin)) return;
-        if (vload(&a.ctl->err)) break;
-        const int stamp = vload(&a.ctl->stamp);
-        int *tin = cur ? a.tl1 : a.tl0, *tout = cur ? a.tl0 : a.tl1;
-        mark_nodes_range<D>(g, f, prm, tin, n_in, a.node_mark, stamp, a.nlist, tid, nth);
-        if (!grid_sync(a.bar, a.max_spin)) return;
-        const int nn = vload(f.cnt + CNT_NODES);
-        mark_cells_range(g, f, a.nlist, nn, a.cell_mark, stamp, a.clist, tid, nth);
-        if (!grid_sync(a.bar, a.max_spin)) return;
-        for (int i = tid; i < n_in; i += nth) predict_cell<D, true, 0>(g, f, prm, tin[i]);
-        if (!grid_sync(a.bar, a.max_spin)) return;
-        for (int i = tid; i < nn; i += nth) node_solve<D>(g, f, a.nlist[i], 0);
-        if (!grid_sync(a.bar, a.max_spin)) return;
-        const int nc = vload(f.cnt + CNT_CELLS);
-        for (int i = tid; i < nc; i += nth) update_cell<D>(g, f, prm, a.clist[i], tout, f.cnt + out);
-        if (!grid_sync(a.bar, a.max_spin)) return;
-    }
+    if (!mood_rounds<D, 0>(g, f, prm, a, tid, nth)) return;
     // next dt and counters (as k_finalize), then the report (as k_report)
     for (int c0 = blockIdx.x * blockDim.x; c0 < N; c0 += nth) {
         finalize_block(g, f, prm, c0);
@@ -140,6 +152,15 @@ __global__ void __launch_bounds__(kCellBlock, D == 2 ? LMOOD_PERSIST_MINB2 : 1)
         r->dt_used = f.dt[0];
         r->dt_next = __longlong_as_double((long long)f.dtn[0]);
     }
+}
+
+// the MOOD loop alone as one cooperative launch (a node of the captured step graph, after
+// the full-mesh update); a barrier that gives up marks the step with ctl->err = 2
+template <int D, int MAT>
+__global__ void __launch_bounds__(kCellBlock, D == 2 ? LMOOD_PERSIST_MINB2 : 1)
+    k_mood_persistent(Geo g, Fld f, Prm prm, PersistArgs a) {
+    const int nth = gridDim.x * blockDim.x, tid = spread_index();
+    if (!mood_rounds<D, MAT>(g, f, prm, a, tid, nth) && threadIdx.x == 0) atomicExch(&a.ctl->err, 2);
 }
 
 }  // namespace lmood

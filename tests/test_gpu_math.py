@@ -1,4 +1,5 @@
-"""The step's own FP64 log and J^{-1/3} (atanh series near 1 / single-precision seed with a
+"""The step's own FP64 log and J^{-1/3} (Taylor and atanh series near 1, chosen by the exponent
+of J - 1, with the tier boundaries sampled on both sides / single-precision seed with a
 third-order correction) against CUDA's log and rcbrt on the device (-m gpu)."""
 import ctypes
 import os
@@ -21,7 +22,10 @@ def test_log_and_rcbrt_against_cuda():
     lib = ctypes.CDLL(so)
     rng = np.random.default_rng(0)
     J = np.concatenate([np.linspace(0.3, 3.0, 100001), 1 + np.linspace(-0.13, 0.13, 100001),
-                        1 + rng.normal(0, 1e-4, 50000), [1.0, 0.875, 1.125, np.nextafter(1.125, 2)]])
+                        1 + rng.normal(0, 1e-4, 50000), 1 + rng.normal(0, 1e-9, 20000),
+                        1 + rng.normal(0, 1e-14, 20000), [1.0, 0.875, 1.125, np.nextafter(1.125, 2)],
+                        [1 + sgn * 2.0 ** -k * f for k in (12, 6, 3) for sgn in (1, -1)
+                         for f in (1.0, 1 - 2.0 ** -52, 1 + 2.0 ** -52)]])
     out = np.zeros(4 * J.size)
     assert lib.eval_math(J.ctypes.data_as(ctypes.c_void_p), J.size, out.ctypes.data_as(ctypes.c_void_p)) == 0
     lg, lg_ref, rc, rc_ref = out.reshape(4, -1)

@@ -1,8 +1,10 @@
 """The persistent step (params.graph = 2: the whole step, MOOD rounds included, as one
-cooperative launch with grid-wide barriers between the stages) against the graph-captured
-step, which the parity tests pin to the oracle: bitwise identical states and reports, in 2D
-and 3D, with MOOD active, the three-level cascade, batched instances, boundary faces and
-contact walls; the error paths (MOOD iteration limit, a barrier wait that gives up) leave the
+cooperative launch with grid-wide barriers between the stages) and the graph-captured step
+whose MOOD loop is one cooperative kernel node (params.graph = 3) against the graph-captured
+step with the conditional while node (graph = 1), which the parity tests pin to the oracle:
+bitwise identical states and reports, in 2D and 3D, with MOOD active, the three-level
+cascade, batched instances, boundary faces, contact walls and (graph = 3) the other
+materials; the error paths (MOOD iteration limit, a barrier wait that gives up) leave the
 state unchanged (-m gpu)."""
 import dataclasses
 
@@ -29,8 +31,8 @@ def _built():
     O.build()
 
 
-def _same(pb, steps, **kw):
-    a = L.simulation(pb, graph=2, **kw)
+def _same(pb, steps, mode=2, **kw):
+    a = L.simulation(pb, graph=mode, **kw)
     b = L.simulation(pb, graph=1, **kw)
     tot = {k: 0 for k in REPORT}
     for s in range(steps):
@@ -125,5 +127,48 @@ def test_persistent_refuses_other_materials():
             L.simulation(dataclasses.replace(W.plain2d(n=8), **kw), graph=2)
         assert e.value.status == L.ERR_ARG
     with pytest.raises(L.LmoodError) as e:
-        L.simulation(W.plain2d(n=8), graph=3)
+        L.simulation(W.plain2d(n=8), graph=4)
     assert e.value.status == L.ERR_ARG
+
+
+MODE3 = [("impact2d", lambda: W.impact2d(n=120), 8, {}), ("cube3d", lambda: W.cube3d(n=6), 6, {}),
+         ("cascade3", lambda: W.impact2d(n=60), 15, {"cascade": 3}),
+         ("piston", lambda: W.piston2d(n=16), 10, {}), ("rebound", lambda: W.rebound2d(n=11, gap=0.02), 40, {}),
+         ("family", lambda: dataclasses.replace(W.impact2d(n=60), shear_a=0.0), 10, {}),
+         ("jellydrop", lambda: W.jellydrop3d(n=5, steps=30), 30, {})]
+
+
+@pytest.mark.parametrize("name,make,steps,kw", MODE3, ids=[m[0] for m in MODE3])
+def test_mood_kernel_node_equals_graph(name, make, steps, kw):
+    tot = _same(make(), steps, mode=3, **kw)
+    if name in ("impact2d", "cube3d", "cascade3"):
+        assert tot["n_troubled"] > 0
+
+
+def test_mood_kernel_node_batched():
+    probs = W.batched2d(n_inst=5, lo=200, hi=5000, steps=12)
+    pb, inst = W.concat(probs)
+    a = L.simulation(pb, cell_inst=inst, n_inst=len(probs), graph=3)
+    b = L.simulation(pb, cell_inst=inst, n_inst=len(probs), graph=1)
+    for _ in range(10):
+        a.step()
+        b.step()
+    for f in FIELDS:
+        assert np.array_equal(a.get(f), b.get(f)), f
+
+
+def test_mood_kernel_node_errors():
+    """iteration limit and a barrier wait that gives up (one-poll bound) in the MOOD node"""
+    s = L.simulation(W.cube3d(n=6), graph=3, max_mood_iters=2)
+    before = s.state()
+    assert s.step_status() == L.ERR_MOOD_ITERS
+    for k, v in before.items():
+        assert np.array_equal(v, s.state()[k]), k
+    s = L.simulation(W.impact2d(n=60), graph=3, barrier_polls=1)
+    before = s.state()
+    codes = [s.step_status() for _ in range(5)]
+    assert set(codes) <= {L.OK, L.ERR_TIMEOUT}
+    assert L.ERR_TIMEOUT in codes
+    if L.OK not in codes:
+        for k, v in before.items():
+            assert np.array_equal(v, s.state()[k]), k
