@@ -84,7 +84,10 @@ typedef struct {
                                are separated by grid-wide barriers with bounded waits (a wait
                                that gives up returns LMOOD_ERR_TIMEOUT, state unchanged;
                                neo-Hookean material only; fastest for small meshes, where
-                               launch latency dominates). Results are identical.             */
+                               launch latency dominates); 3: as 1 with the MOOD loop as one
+                               cooperative kernel node with such barriers instead of the
+                               conditional while node (a timeout also returns
+                               LMOOD_ERR_TIMEOUT). Results are identical.                    */
     int32_t cascade;        /* 2: P1 -> P0 (default); 3: P1 -> P1 with Barth-Jespersen limited
                                slopes -> P0, the three-scheme cascade of Sect. "Limiting: a
                                posteriori MOOD loop" (order codes 2, 3, 1)                    */
