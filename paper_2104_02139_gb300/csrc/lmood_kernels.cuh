@@ -145,8 +145,10 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
         for (int a = 0; a < D; ++a) eps_c -= 0.5 * vc[a] * vc[a];
     }
     // face matrices W_f = z |l n_f| n_f (x) n_f with l n_f = N_f / D; M_cp = sum_{f != p} W_f
+    // (filled just before the packets are emitted, so that they are not live through the
+    // reconstruction and the predictor)
     double W[NV][NS];
-    {
+    auto face_matrices = [&]() {
         const double z = f.z[c];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
@@ -162,7 +164,7 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
 #pragma unroll
                 for (int b = a; b < D; ++b) W[k][sidx<D>(a, b)] = w * u[a] * u[b];
         }
-    }
+    };
     // packet of corner k: M_cp and rhs_cp = M_cp v* - T* l n_p, with l n_p = -N_p / D
     auto emit = [&](int k, const double(&vst)[D], const double(&Tst)[DD]) {
         double M[NS];
@@ -343,6 +345,7 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
             eps_h = eps_c + 0.5 * dt * pw * V / f.m[c];
         }
         // pass 2: corner values at t^{n+1/2} and packets
+        face_matrices();
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             double vst[D], Fs[DD], T[DD];
@@ -371,6 +374,7 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
     } else {
         double T[DD];
         cell_stress<D, MAT>(prm, Fc, muc, kap, eps_c, T);
+        face_matrices();
 #pragma unroll
         for (int k = 0; k < NV; ++k) emit(k, vc, T);
     }
