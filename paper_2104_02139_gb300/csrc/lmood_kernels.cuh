@@ -344,29 +344,32 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
             for (int q = 0; q < DD; ++q) pw += Tc[q] * gv[q];
             eps_h = eps_c + 0.5 * dt * pw * V / f.m[c];
         }
-        // pass 2: corner values at t^{n+1/2} and packets
+        // pass 2: corner values at t^{n+1/2} and packets (the velocity's half-step increment
+        // added to the cell value once)
         face_matrices();
+        double vch[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) vch[i] = vc[i] + dvdt[i];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             double vst[D], Fs[DD], T[DD];
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                double s = vc[i];
+                double s = vch[i];
 #pragma unroll
                 for (int a = 0; a < D; ++a) s += gs[i][a] * dxs[k][a];
-                vst[i] = s + dvdt[i];
+                vst[i] = s;
             }
 #pragma unroll
             for (int q = 0; q < DD; ++q) {
-                double s;
                 if constexpr (D == 2) {
-                    s = Fhk[k][q];
+                    Fs[q] = fma(0.5 * dt, dFdt[q], Fhk[k][q]);
                 } else {
-                    s = Fc[q];
+                    double s = Fc[q];
 #pragma unroll
                     for (int a = 0; a < D; ++a) s += gs[D + q][a] * dxs[k][a];
+                    Fs[q] = fma(0.5 * dt, dFdt[q], s);
                 }
-                Fs[q] = fma(0.5 * dt, dFdt[q], s);
             }
             cell_stress<D, MAT>(prm, Fs, muc, kap, eps_h, T);
             emit(k, vst, T);
@@ -837,18 +840,30 @@ static __global__ void k_ctl_reset(Ctl *ctl) {
     ctl->err = 0;
 }
 
-// troubled cells become P0; their nodes are appended (once) to the node list
+// append item to list[*cnt] when take is set, one atomicAdd per converged group of lanes
+// (the lanes that take share one slot range; the order within it follows the lanes)
+__device__ __forceinline__ void append_aggregated(bool take, int item, int *list, int *cnt) {
+    const unsigned m = __activemask();
+    const unsigned b = __ballot_sync(m, take);
+    if (!take) return;  // the lanes of b alone take part in the broadcast below
+    const int lane = threadIdx.x & 31, leader = __ffs(b) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(b));
+    base = __shfl_sync(b, base, leader);
+    list[base + __popc(b & ((1u << lane) - 1u))] = item;
+}
+
+// troubled cells become P0 (or P1 with limited slopes); their nodes are appended (once) to
+// the node list. Work item i is the pair (troubled cell i / (D+1), its vertex i % (D+1)).
 template <int D>
 __device__ __forceinline__ void mark_nodes_range(const Geo &g, const Fld &f, const Prm &prm, const int *tlist, int n,
                                                  int *node_mark, int stamp, int *nlist, int i0, int di) {
-    for (int i = i0; i < n; i += di) {
-        const int c = tlist[i];
-        f.order[c] = (f.order[c] == 2 && prm.cascade == 3) ? 3 : 1;  // one level down the cascade
-#pragma unroll
-        for (int k = 0; k < D + 1; ++k) {
-            const int p = __ldg(g.c2n + k * g.N + c);
-            if (atomicExch(node_mark + p, stamp) != stamp) nlist[atomicAdd(f.cnt + CNT_NODES, 1)] = p;
-        }
+    const long long items = (long long)n * (D + 1);
+    for (long long i = i0; i < items; i += di) {
+        const int c = tlist[i / (D + 1)], k = (int)(i % (D + 1));
+        if (k == 0) f.order[c] = (f.order[c] == 2 && prm.cascade == 3) ? 3 : 1;  // one level down the cascade
+        const int p = __ldg(g.c2n + k * g.N + c);
+        append_aggregated(atomicExch(node_mark + p, stamp) != stamp, p, nlist, f.cnt + CNT_NODES);
     }
 }
 
@@ -859,23 +874,30 @@ __global__ void k_mark_nodes(Geo g, Fld f, Prm prm, const int *__restrict__ tlis
                         gridDim.x * blockDim.x);
 }
 
-// every cell around a listed node is appended (once) to the cell list
+// every cell around a listed node is appended (once) to the cell list; G consecutive lanes
+// (G divides 32, the caller's indices keep lanes of a warp consecutive) share a node and
+// take its cells in parallel
+template <int G>
 __device__ __forceinline__ void mark_cells_range(const Geo &g, const Fld &f, const int *nlist, int n, int *cell_mark,
                                                  int stamp, int *clist, int i0, int di) {
-    for (int i = i0; i < n; i += di) {
+    const int sub = i0 % G;
+    for (int i = i0 / G; i < n; i += di / G) {
         const int p = nlist[i];
         const int j1 = g.n2c_off[p + 1];
-        for (int j = g.n2c_off[p]; j < j1; ++j) {
+        for (int j = g.n2c_off[p] + sub; j < j1; j += G) {
             const int c = g.n2c[j] % g.N;
-            if (atomicExch(cell_mark + c, stamp) != stamp) clist[atomicAdd(f.cnt + CNT_CELLS, 1)] = c;
+            append_aggregated(atomicExch(cell_mark + c, stamp) != stamp, c, clist, f.cnt + CNT_CELLS);
         }
     }
 }
 
-static __global__ void k_mark_cells(Geo g, Fld f, const int *__restrict__ nlist, int *cell_mark, const Ctl *ctl,
-                                    int *clist) {
-    mark_cells_range(g, f, nlist, f.cnt[CNT_NODES], cell_mark, ctl->stamp, clist, blockIdx.x * blockDim.x + threadIdx.x,
-                     gridDim.x * blockDim.x);
+// lanes per node when marking cells: about the node degree (2D ~6, 3D Kuhn meshes ~24)
+template <int D> constexpr int kMarkLanes = D == 2 ? 8 : 32;
+
+template <int D>
+__global__ void k_mark_cells(Geo g, Fld f, const int *__restrict__ nlist, int *cell_mark, const Ctl *ctl, int *clist) {
+    mark_cells_range<kMarkLanes<D>>(g, f, nlist, f.cnt[CNT_NODES], cell_mark, ctl->stamp, clist,
+                                    blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // while-loop condition of a graph-captured step: another MOOD round is needed

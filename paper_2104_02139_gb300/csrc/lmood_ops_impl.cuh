@@ -77,11 +77,16 @@ void update(const Geo &g, const Fld &f, const Prm &p, const int *list, const int
 template <int D>
 void mark_nodes(const Geo &g, const Fld &f, const Prm &p, const int *tlist, const int *tcnt, int n, int *node_mark,
                 const Ctl *ctl, int *nlist, cudaStream_t s) {
-    if (n > 0) k_mark_nodes<D><<<grid_for(tlist, n, 256), 256, 0, s>>>(g, f, p, tlist, tcnt, node_mark, ctl, nlist);
+    if (n > 0)
+        k_mark_nodes<D><<<grid_for(tlist, (int)std::min<long long>((long long)n * (D + 1), 1 << 30), 256), 256, 0, s>>>(
+            g, f, p, tlist, tcnt, node_mark, ctl, nlist);
 }
+template <int D>
 void mark_cells(const Geo &g, const Fld &f, const int *nlist, int n, int *cell_mark, const Ctl *ctl, int *clist,
                 cudaStream_t s) {
-    if (n > 0) k_mark_cells<<<grid_for(nlist, n, 256), 256, 0, s>>>(g, f, nlist, cell_mark, ctl, clist);
+    if (n > 0)
+        k_mark_cells<D><<<grid_for(nlist, (int)std::min<long long>((long long)n * kMarkLanes<D>, 1 << 30), 256), 256, 0, s>>>(
+            g, f, nlist, cell_mark, ctl, clist);
 }
 void round_begin(const Fld &f, Ctl *ctl, int in, int out, int max_iters, cudaStream_t s) {
     k_round_begin<<<1, 1, 0, s>>>(f, ctl, in, out, max_iters);
@@ -141,7 +146,7 @@ template <int D> cudaError_t mood_persistent(const Geo &g, const Fld &f, const P
 }  // namespace
 
 #define LMOOD_OPS_TABLE(D)                                                                                  \
-    static const Ops table = {D, Dim<D>::NMOM, moments<D>, predict<D>, nodes<D>,  update<D>,     mark_nodes<D>, mark_cells, \
+    static const Ops table = {D, Dim<D>::NMOM, moments<D>, predict<D>, nodes<D>,  update<D>,     mark_nodes<D>, mark_cells<D>, \
                               round_begin, ctl_reset,  loop_cond, report,        dt_init,       finalize,   \
                               init_cells<D>, refresh<D>, totals<D>, persistent<D>, mood_persistent<D>};                                      \
     return table;

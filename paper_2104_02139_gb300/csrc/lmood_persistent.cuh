@@ -85,7 +85,7 @@ __device__ __forceinline__ bool mood_rounds(const Geo &g, const Fld &f, const Pr
         mark_nodes_range<D>(g, f, prm, tin, n_in, a.node_mark, stamp, a.nlist, tid, nth);
         if (!grid_sync(a.bar, a.max_spin)) return false;
         const int nn = vload(f.cnt + CNT_NODES);
-        mark_cells_range(g, f, a.nlist, nn, a.cell_mark, stamp, a.clist, tid, nth);
+        mark_cells_range<kMarkLanes<D>>(g, f, a.nlist, nn, a.cell_mark, stamp, a.clist, tid, nth);
         if (!grid_sync(a.bar, a.max_spin)) return false;
         for (int i = tid; i < n_in; i += nth) predict_cell<D, true, MAT>(g, f, prm, tin[i]);
         if (!grid_sync(a.bar, a.max_spin)) return false;
