@@ -514,6 +514,9 @@ static void state_free(lmood_state s) {
     }
     if (s->body_st) cudaStreamDestroy(s->body_st);
     if (s->cap_st) cudaStreamDestroy(s->cap_st);
+    if (s->aux_st) cudaStreamDestroy(s->aux_st);
+    for (cudaEvent_t e : s->set_ev)
+        if (e) cudaEventDestroy(e);
     if (s->h_report) cudaFreeHost(s->h_report);
     s->mem.release();
     if (s->h_cnt) cudaFreeHost(s->h_cnt);
@@ -1050,21 +1053,41 @@ extern "C" lmood_status lmood_set_fields(lmood_state s, int n, const int *fields
     }
     lmood_mesh M = s->M;
     cudaStream_t st = M->st;
-    bool geo = false;
-    for (int i = 0; i < n; ++i) {
-        void *dst = nullptr;
-        size_t bytes = 0;
-        set_target(s, fields[i], &dst, &bytes);
-        LM_CUDA(cudaMemcpyAsync(dst, src[i], bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        if (fields[i] != LMOOD_FIELD_DT) s->at_init = false;
-        geo = geo || fields[i] == LMOOD_FIELD_X || fields[i] == LMOOD_FIELD_F;
-    }
-    if (geo) {  // derived cell geometry, density and impedance from the new x and F
+    auto is_geo = [&](int i) { return fields[i] == LMOOD_FIELD_X || fields[i] == LMOOD_FIELD_F; };
+    int n_geo = 0;
+    for (int i = 0; i < n; ++i) n_geo += is_geo(i);
+    // derived cell geometry, density and impedance from the new x and F; the refresh reads
+    // nothing else for the volumetric law of Eq. EOS_neoHook, so it runs on a side stream while
+    // the other fields are copied (the stiffened gas's impedance also needs v and e)
+    const bool side = n_geo > 0 && n_geo < n && s->mat.eos == 0;
+    auto refresh = [&](cudaStream_t rs) {
         Fld &f = s->f;
         std::swap(s->tau, f.tau1);
-        M->ops->refresh(M->geo, f, s->kp, st);
+        M->ops->refresh(M->geo, f, s->kp, rs);
         std::swap(s->tau, f.tau1);
+    };
+    if (side && !s->aux_st) {
+        LM_CUDA(cudaStreamCreateWithFlags(&s->aux_st, cudaStreamNonBlocking));
+        for (auto &e : s->set_ev) LM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
+    for (int pass = 0; pass < 2; ++pass) {  // X and F first
+        for (int i = 0; i < n; ++i) {
+            if (is_geo(i) != (pass == 0)) continue;
+            void *dst = nullptr;
+            size_t bytes = 0;
+            set_target(s, fields[i], &dst, &bytes);
+            LM_CUDA(cudaMemcpyAsync(dst, src[i], bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+            if (fields[i] != LMOOD_FIELD_DT) s->at_init = false;
+        }
+        if (pass == 0 && side) {
+            LM_CUDA(cudaEventRecord(s->set_ev[0], st));
+            LM_CUDA(cudaStreamWaitEvent(s->aux_st, s->set_ev[0], 0));
+            refresh(s->aux_st);
+            LM_CUDA(cudaEventRecord(s->set_ev[1], s->aux_st));
+        }
+    }
+    if (side) LM_CUDA(cudaStreamWaitEvent(st, s->set_ev[1], 0));
+    else if (n_geo > 0) refresh(st);
     if (!is_device) return sync_check(s, "lmood_set_fields");
     return LMOOD_OK;
 }

@@ -81,6 +81,8 @@ struct lmood_state_s {
     cudaStream_t cap_st = nullptr;   // private streams for capturing (the mesh's stream may be the
     cudaStream_t body_st = nullptr;  // legacy default stream, which cannot be captured)
     unsigned int *bar = nullptr;  // persistent step: grid barrier state (device, 4 words)
+    cudaStream_t aux_st = nullptr;   // lmood_set_fields: the geometry refresh beside the copies
+    cudaEvent_t set_ev[2] = {};      //   (X and F copied; refresh done)
     int *h_cnt = nullptr;      // pinned mirror of the device counters
     double *h_dt = nullptr;    // pinned: dt used, dt next (instance 0)
     double t = 0.0;
