@@ -198,6 +198,12 @@ def barrier(dist):
         dist.barrier()
 
 
+def job_throughput(ws: int, cells: int, steps: int, ms_max: float) -> float:
+    """whole-job cell-steps/s: every rank advances its own replica of `cells` cells `steps`
+    times; the job takes as long as its slowest rank (ms_max, the max over ranks)"""
+    return ws * cells * steps / (ms_max / 1e3)
+
+
 def run_reference(args, rank, ws, dist):
     if rank != 0:
         return
@@ -248,7 +254,7 @@ def run_ours(args, rank, local, ws, dist):
     kt = sim.timing_read()
     sim.timing(False)
     ms_max = max_over_ranks(ms, dist)
-    value = ws * N * args.steps / (ms_max / 1e3)
+    value = job_throughput(ws, N, args.steps, ms_max)
 
     # roofline of the dominant kernel class (full-mesh launches; MOOD rounds excluded). The
     # step is bound by the FP64 pipe: roofline = FP64 FLOP/s against the FP64 peak, with the
