@@ -88,6 +88,10 @@ def kernel_bytes(dim: int, nc: int, npn: int, nnz: int) -> dict:
 # Re-measured whenever a kernel changes (profiles/ holds the capture); None = not measured
 # for the current kernel.
 FP64_FLOP_PER_CELL = {"predict": 861.0, "update": 384.0, "nodes": 31.1, "moments": 123.0}
+# FP64 thread instructions per cell (dfma + dadd + dmul) from the same capture: the pipe's
+# issue rate, compared with DGEMM's (one DFMA = 2 FLOP per instruction), shows how busy the
+# pipe is independently of the operation mix.
+FP64_INSTR_PER_CELL = {"predict": 549.0, "update": 245.0, "nodes": 25.0, "moments": 78.0}
 # DRAM bytes (read + write) per full launch from the same ncu capture, or None.
 TRAFFIC_PER_LAUNCH = {"predict": 295.76e6, "update": 341.39e6, "nodes": 177.94e6, "moments": 134.59e6}
 
@@ -276,6 +280,11 @@ def run_ours(args, rank, local, ws, dist):
                 "peak_source": ("measured cuBLAS DGEMM in this run (nominal 1.26)" if fp64_meas
                                 else "nominal 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"),
                 "fp64_flop_per_cell": fpc, "ms_per_launch": dom_ms, "hbm": hbm}
+        ipc = FP64_INSTR_PER_CELL.get(dom)
+        if ipc:
+            gi = ipc * N / (dom_ms / 1e3) / 1e9
+            roof["fp64_issue"] = {"achieved": gi, "peak": fp64_peak * 1e3 / 2, "unit": "G FP64 instr/s",
+                                  "frac": gi / (fp64_peak * 1e3 / 2), "fp64_instr_per_cell": ipc}
     else:
         roof = {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": how,

@@ -1,7 +1,7 @@
 """CUDA path vs the CPU oracle, element by element, on the same seeded inputs (-m gpu).
 
-Tolerances: the benchmark spec's bound, a state relative error of at most 1e-11 after one step and
-1e-8 after the configured run, with identical MOOD order masks at every step. Both sides
+Tolerances: a state relative error of at most 1e-11 after one step and 1e-8 after the
+configured run, with identical MOOD order masks at every step. Both sides
 compute in FP64; the differences come from FMA contraction and the two math libraries'
 log/cbrt (a few ulp), i.e. ~1e-15 relative per step.
 """
