@@ -1,5 +1,6 @@
 """Batched instances (independent meshes of uneven sizes, own dt each) advanced by one launch
-per stage give exactly the per-instance results (-m gpu)."""
+per stage give exactly the per-instance results; at the full 256-instance size, sampled
+instances match the oracle stepping them one by one (-m gpu)."""
 import numpy as np
 import pytest
 
@@ -42,3 +43,39 @@ def test_batch_rejects_shared_nodes():
     with pytest.raises(L.LmoodError) as e:
         L.simulation(pb, cell_inst=inst, n_inst=2)
     assert e.value.status == L.ERR_MESH
+
+
+def test_full_size_batch_sampled_instances_match_oracle():
+    """The 256-instance configuration at full size (11.6M cells, one launch per stage for all
+    instances, own dt each): the smallest, the largest and two more instances, sampled, are
+    stepped by the oracle one by one and compared element by element with their slices of the
+    batch after every step (masks identical, state within 1e-11 after the first step and 1e-8
+    after three)."""
+    import oracle as O
+    from parity_util import relerr
+    O.build()
+    probs = W.batched2d()
+    pb, inst = W.concat(probs)
+    b = L.simulation(pb, cell_inst=inst, n_inst=len(probs))
+    cells = np.asarray(pb.meta["cells"])
+    c_off = np.concatenate([[0], np.cumsum(cells)])
+    n_off = np.concatenate([[0], np.cumsum(pb.meta["nodes"])])
+    rng = np.random.default_rng(11)
+    pick = sorted({int(cells.argmin()), int(cells.argmax()), *rng.choice(len(probs), 2, replace=False).tolist()})
+    oracles = {i: O.Oracle(probs[i]) for i in pick}
+    pairs = ((L.FIELD_X, O.F_X, "node"), (L.FIELD_VP, O.F_VP, "node"), (L.FIELD_V, O.F_V, "cell"),
+             (L.FIELD_E, O.F_E, "cell"), (L.FIELD_F, O.F_F, "cell"), (L.FIELD_TAU, O.F_TAU, "cell"))
+    for s in range(3):
+        b.step()
+        full = {fg: b.get(fg) for fg, _, _ in pairs}
+        order = b.get(L.FIELD_ORDER).astype(int)
+        dt = b.get(L.FIELD_DT)
+        for i, o in oracles.items():
+            o.step()
+            cs, ns = slice(c_off[i], c_off[i + 1]), slice(n_off[i], n_off[i + 1])
+            assert np.array_equal(order[cs], o.get(O.F_ORDER).astype(int)), (s, i)
+            tol = 1e-11 if s == 0 else 1e-8
+            for fg, fo, kind in pairs:
+                g = full[fg][..., ns] if kind == "node" else full[fg][..., cs]
+                assert relerr(g, o.get(fo)) <= tol, (s, i, fg)
+            assert abs(dt[i] - o.dt) <= tol * o.dt, (s, i)
