@@ -116,7 +116,7 @@ template <int D> LMOOD_HD void stress(const double *F, double mu, double kap, do
     mmt<D>(F, F, B);
     double tr = D == 2 ? 1.0 : 0.0;
     for (int i = 0; i < D; ++i) tr += B[i * D + i];
-    const double diag = -p - cj * tr / 3.0;
+    const double diag = -p - cj * tr * (1.0 / 3.0);
     for (int i = 0; i < D; ++i)
         for (int j = 0; j < D; ++j) T[i * D + j] = cj * B[i * D + j] + (i == j ? diag : 0.0);
 }
@@ -134,7 +134,7 @@ LMOOD_HD void stress_vjp(const double *F, double mu, double kap, const double *l
     for (int i = 0; i < D; ++i) tr += B[i * D + i];
     if (T_out) {
         const double p = -0.5 * kap * (J - 1.0 + lJ * invJ);
-        const double diag = -p - cj * tr / 3.0;
+        const double diag = -p - cj * tr * (1.0 / 3.0);
         for (int i = 0; i < D; ++i)
             for (int j = 0; j < D; ++j) T_out[i * D + j] = cj * B[i * D + j] + (i == j ? diag : 0.0);
     }
@@ -147,8 +147,8 @@ LMOOD_HD void stress_vjp(const double *F, double mu, double kap, const double *l
     for (int i = 0; i < D; ++i) ldiag += lT[i * D + i];
     // diag = -p - cj tr / 3
     const double lp = -ldiag;
-    lcj += -ldiag * tr / 3.0;
-    const double ltr = -ldiag * cj / 3.0;
+    lcj += -ldiag * tr * (1.0 / 3.0);
+    const double ltr = -ldiag * cj * (1.0 / 3.0);
     for (int i = 0; i < D; ++i) lB[i * D + i] += ltr;
     // cj = mu J^{-5/3};  p = -(kap/2)(J - 1 + log J / J)
     lmu += lcj * J53;
@@ -179,9 +179,9 @@ LMOOD_HD void impedance_vjp(const double *F, double rho, double mu, double kap, 
     const double J = det<D>(F), invJ = 1.0 / J, lJ = adj_log(J);
     const double K = 0.5 * kap * (J + (1.0 - lJ) * invJ);
     const double inner = K + (4.0 / 3.0) * mu * invJ;
-    const double z = sqrt(rho * inner);
-    const double linner = lz * rho / (2.0 * z);
-    lrho += lz * inner / (2.0 * z);
+    const double z = sqrt(rho * inner), h = 0.5 / z;
+    const double linner = lz * rho * h;
+    lrho += lz * inner * h;
     lmu += linner * (4.0 / 3.0) * invJ;
     lkap += linner * 0.5 * (J + (1.0 - lJ) * invJ);
     const double lJv = linner * (0.5 * kap * (1.0 + (lJ - 2.0) * invJ * invJ) - (4.0 / 3.0) * mu * invJ * invJ);
@@ -227,7 +227,7 @@ template <int D> LMOOD_HD void faces_vjp(const double *xs, double lV, const doub
     double V, N[(D + 1) * D];
     faces<D>(xs, V, N);
     for (int k = 0; k < D + 1; ++k)
-        for (int a = 0; a < D; ++a) lxs[k * D + a] += lV * (-N[k * D + a] / D);
+        for (int a = 0; a < D; ++a) lxs[k * D + a] += lV * (N[k * D + a] * (-1.0 / D));
     if constexpr (D == 2) {
         for (int k = 0; k < 3; ++k) {
             const int a = (k + 1) % 3, b = (k + 2) % 3;
@@ -367,12 +367,12 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
     for (int a = 0; a < D; ++a) {
         double s = 0.0;
         for (int k = 0; k < NV; ++k) s += xs[k * D + a];
-        xcc[a] = s / NV;
+        xcc[a] = s * (1.0 / NV);
     }
     for (int f = 0; f < NV; ++f) {
         double u[D], ss = 0.0;
         for (int a = 0; a < D; ++a) {
-            u[a] = N[f * D + a] / D;
+            u[a] = N[f * D + a] * (1.0 / D);
             ss += u[a] * u[a];
         }
         const double w = z / sqrt(ss);
@@ -393,7 +393,7 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
         for (int k = 0; k < NV; ++k)
             for (int a = 0; a < D; ++a) {
                 double s = 0.0;
-                for (int b = 0; b < D; ++b) s += Mfull(k, a, b) * vc[b] + T[a * D + b] * N[k * D + b] / D;
+                for (int b = 0; b < D; ++b) s += Mfull(k, a, b) * vc[b] + T[a * D + b] * N[k * D + b] * (1.0 / D);
                 Ro[k * D + a] = s;
             }
         return;
@@ -418,7 +418,7 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
     }
     double tr = 0.0;
     for (int a = 0; a < D; ++a) tr += G[a * D + a];
-    const double t = tr / D;
+    const double t = tr * (1.0 / D);
     const bool ok = det<D>(G) > 1e-12 * (D == 2 ? t * t : t * t * t);
     double Gi[DD], gs[NQ][D];
     inverse<D>(G, Gi);
@@ -429,7 +429,7 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
             gs[q][a] = ok ? s : 0.0;
         }
     double dv[D] = {}, dFdt[DD], gv[DD];
-    const double hv = -0.5 * dt * im / D;
+    const double hv = -0.5 * dt * im * (1.0 / D);
     for (int k = 0; k < NV; ++k) {
         double Fh[DD], T[DD];
         for (int q = 0; q < DD; ++q) {
@@ -460,7 +460,7 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
         stress<D>(Fs, mu, kap, T);
         for (int a = 0; a < D; ++a) {
             double s = 0.0;
-            for (int b = 0; b < D; ++b) s += Mfull(k, a, b) * vst[b] + T[a * D + b] * N[k * D + b] / D;
+            for (int b = 0; b < D; ++b) s += Mfull(k, a, b) * vst[b] + T[a * D + b] * N[k * D + b] * (1.0 / D);
             Ro[k * D + a] = s;
         }
     }
@@ -480,7 +480,7 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
     for (int a = 0; a < D; ++a) {
         double s = 0.0;
         for (int k = 0; k < NV; ++k) s += xs[k * D + a];
-        xcc[a] = s / NV;
+        xcc[a] = s * (1.0 / NV);
     }
     // M_k = sum_{f != k} W_f, W_f = (z / |u_f|) u_f u_f^t, u_f = N_f / D
     double Mo[NV * NS], inu[NV];  // inu = 1 / |u_f|
@@ -490,7 +490,7 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
             double ss = 0.0;
             for (int a = 0; a < D; ++a) ss += N[f * D + a] * N[f * D + a];
             inu[f] = D / sqrt(ss);
-            const double w = z * inu[f] / (D * D);
+            const double w = z * inu[f] * (1.0 / (D * D));
             for (int a = 0; a < D; ++a)
                 for (int b = a; b < D; ++b) W[f][sym<D>(a, b)] = w * N[f * D + a] * N[f * D + b];
         }
@@ -512,14 +512,14 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
             for (int b = 0; b < D; ++b) {
                 lvst[b] += Mfull(k, a, b) * l;
                 lM[k * NS + sym<D>(a, b)] += l * vst[b];
-                lT[a * D + b] += l * N[k * D + b] / D;
+                lT[a * D + b] += l * N[k * D + b] * (1.0 / D);
             }
         }
     };
     // ... and the part that does: lN_k += (1/D) T_k^t lR_k
     auto packet_rhs_vjp_T = [&](int k, const double *T) {
         for (int a = 0; a < D; ++a)
-            for (int b = 0; b < D; ++b) lN[k * D + b] += lR[k * D + a] * T[a * D + b] / D;
+            for (int b = 0; b < D; ++b) lN[k * D + b] += lR[k * D + a] * T[a * D + b] * (1.0 / D);
     };
     auto zero_moments = [&]() {
         for (int k = 0; k < NV; ++k)
@@ -556,7 +556,7 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
         }
         double tr = 0.0;
         for (int a = 0; a < D; ++a) tr += G[a * D + a];
-        const double t = tr / D;
+        const double t = tr * (1.0 / D);
         const bool ok = det<D>(G) > 1e-12 * (D == 2 ? t * t : t * t * t);
         double Gi[DD], gs[NQ][D];
         inverse<D>(G, Gi);
@@ -574,7 +574,7 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
             }
         };
         double gv[DD], dFdt[DD], dvraw[D] = {};
-        const double hv = -0.5 * dt * im / D;
+        const double hv = -0.5 * dt * im * (1.0 / D);
         for (int k = 0; k < NV; ++k) {
             double Fh[DD], T[DD];
             Fh_of(k, Fh);
@@ -744,7 +744,7 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
     // ---- geometry: N(xs), xcc = mean(xs)
     faces_vjp<D>(xs, 0.0, lN, lxs);
     for (int k = 0; k < NV; ++k)
-        for (int a = 0; a < D; ++a) lxs[k * D + a] += lxcc[a] / NV;
+        for (int a = 0; a < D; ++a) lxs[k * D + a] += lxcc[a] * (1.0 / NV);
 }
 
 // ---------------------------------------------------------------------------------------
