@@ -409,7 +409,7 @@ __device__ __noinline__ double free_energy_family(const double (&F)[D * D], doub
 }
 
 __device__ __forceinline__ double kappa_of(const Prm &prm, double mu) {
-    return prm.vol_coeff ? mu : prm.lam + 2.0 * mu / 3.0;
+    return prm.vol_coeff ? mu : prm.lam + mu * (2.0 / 3.0);
 }
 
 // physical admissibility (Eq. PAD): 0 admissible, 1 only eps < -tol, 2 not computable;

@@ -455,8 +455,9 @@ __device__ __forceinline__ void solve_K(const Geo &g, const double (&M)[D * D], 
             al[1] = 0.0;
         } else {
             const double dA = A[0] * A[3] - A[1] * A[2];
-            al[0] = (A[3] / dA) * r[0] + (-A[1] / dA) * r[1];
-            al[1] = (-A[2] / dA) * r[0] + (A[0] / dA) * r[1];
+            const double idA = 1.0 / dA;
+            al[0] = (A[3] * idA) * r[0] + (-A[1] * idA) * r[1];
+            al[1] = (-A[2] * idA) * r[0] + (A[0] * idA) * r[1];
         }
 #pragma unroll
         for (int a = 0; a < D; ++a) {
@@ -546,18 +547,18 @@ __device__ __forceinline__ void node_solve(const Geo &g, const Fld &f, int p, in
                 double ar = 0.0;
 #pragma unroll
                 for (int a = 0; a < D; ++a) ar += N[a] * N[a];
-                ar = sqrt(ar) / D;
+                ar = sqrt(ar) * (1.0 / D);
 #pragma unroll
                 for (int a = 0; a < D; ++a) b[a] += ar * g.bf_val[a * g.nbf + fid];
             } else if (tag == TAG_PRESSURE) {
                 const double pr = g.bf_val[fid];
 #pragma unroll
-                for (int a = 0; a < D; ++a) b[a] -= pr * N[a] / D;
+                for (int a = 0; a < D; ++a) b[a] -= pr * N[a] * (1.0 / D);
             } else if (tag == TAG_VELOCITY) {
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
-                    dv[a] += N[a] / D;
-                    gsum += g.bf_val[a * g.nbf + fid] * N[a] / D;
+                    dv[a] += N[a] * (1.0 / D);
+                    gsum += g.bf_val[a * g.nbf + fid] * N[a] * (1.0 / D);
                 }
                 ++nvel;
             }
