@@ -41,7 +41,7 @@ template <int D> __device__ __forceinline__ void moments_node(const Geo &g, cons
     using Q = Dim<D>;
     constexpr int NS = Q::NS, NQ = Q::NQ, DD = D * D;
     const int N = g.N, Np = g.Np;
-    double xp[D], S1[D], S2[NS], U[NQ], T[NQ][D], n = 0.0;
+    double xp[D], S1[D], S2[NS], U[NQ], T[NQ][D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         xp[a] = f.x[a * Np + p];
@@ -66,7 +66,6 @@ template <int D> __device__ __forceinline__ void moments_node(const Geo &g, cons
             dx[a] = f.xc[a * N + c] - xp[a];
             S1[a] += dx[a];
         }
-        n += 1.0;
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -81,7 +80,7 @@ template <int D> __device__ __forceinline__ void moments_node(const Geo &g, cons
     }
     (void)DD;
     double *m = f.mom + p;
-    m[Q::M_N * Np] = n;
+    m[Q::M_N * Np] = (double)(j1 - __ldg(g.n2c_off + p));  // the node's cell count
 #pragma unroll
     for (int a = 0; a < D; ++a) m[(Q::M_S1 + a) * Np] = S1[a];
 #pragma unroll
@@ -702,7 +701,8 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
     double V0, Nf0[NV][D], V1, Nf1[NV][D];
     simplex_faces<D>(xs0, V0, Nf0);
     simplex_faces<D>(xs1, V1, Nf1);
-    const double iV0 = 1.0 / V0, iV1 = 1.0 / V1;
+    // 1 / |w_c| at x^n is rho^n / m_c (rho^n = m_c / |w_c(x^n)| is stored); at x^{n+1} one division
+    const double iV0 = f.rho[c] * im, iV1 = 1.0 / V1;
     double Fn[DD], F1[DD];
 #pragma unroll
     for (int q = 0; q < DD; ++q) Fn[q] = f.F[q * N + c];
