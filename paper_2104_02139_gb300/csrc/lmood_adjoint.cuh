@@ -258,9 +258,10 @@ template <int D> LMOOD_HD void faces_vjp(const double *xs, double lV, const doub
     }
 }
 
-// velocity gradient L = -(1/(D V)) sum_k v_k (x) N_k and its product
-template <int D> LMOOD_HD void velgrad(const double *vn, const double *N, double V, double *L) {
-    const double s0 = -1.0 / (D * V);
+// velocity gradient L = -(1/(D V)) sum_k v_k (x) N_k and its product; the _iv forms take
+// iV = 1 / V (shared by the callers that also need it), the product also L itself
+template <int D> LMOOD_HD void velgrad_iv(const double *vn, const double *N, double iV, double *L) {
+    const double s0 = iV * (-1.0 / D);
     for (int i = 0; i < D; ++i)
         for (int j = 0; j < D; ++j) {
             double s = 0.0;
@@ -269,12 +270,14 @@ template <int D> LMOOD_HD void velgrad(const double *vn, const double *N, double
         }
 }
 
+template <int D> LMOOD_HD void velgrad(const double *vn, const double *N, double V, double *L) {
+    velgrad_iv<D>(vn, N, 1.0 / V, L);
+}
+
 template <int D>
-LMOOD_HD void velgrad_vjp(const double *vn, const double *N, double V, const double *lL, double *lvn, double *lN,
-                          double &lV) {
-    const double s0 = -1.0 / (D * V);
-    double L[D * D];
-    velgrad<D>(vn, N, V, L);
+LMOOD_HD void velgrad_vjp_iv(const double *vn, const double *N, double iV, const double *L, const double *lL,
+                             double *lvn, double *lN, double &lV) {
+    const double s0 = iV * (-1.0 / D);
     for (int k = 0; k < D + 1; ++k)
         for (int i = 0; i < D; ++i) {
             double a = 0.0, b = 0.0;
@@ -287,7 +290,16 @@ LMOOD_HD void velgrad_vjp(const double *vn, const double *N, double V, const dou
         }
     double s = 0.0;
     for (int i = 0; i < D * D; ++i) s += lL[i] * L[i];
-    lV += -s / V;
+    lV -= s * iV;  // L is proportional to 1 / V
+}
+
+template <int D>
+LMOOD_HD void velgrad_vjp(const double *vn, const double *N, double V, const double *lL, double *lvn, double *lN,
+                          double &lV) {
+    const double iV = 1.0 / V;
+    double L[D * D];
+    velgrad_iv<D>(vn, N, iV, L);
+    velgrad_vjp_iv<D>(vn, N, iV, L, lL, lvn, lN, lV);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -806,12 +818,13 @@ LMOOD_HD void update_vjp(const double *xs0, const double *xs1, const double *vs,
     double V0, N0[NV * D], V1, N1[NV * D], lN0[NV * D] = {}, lN1[NV * D] = {}, lV0 = 0.0, lV1 = 0.0;
     faces<D>(xs0, V0, N0);
     faces<D>(xs1, V1, N1);
+    const double iV0 = 1.0 / V0, iV1 = 1.0 / V1;
     double lF1[DD];
     for (int q = 0; q < DD; ++q) lF1[q] = lF1_in[q];
     if (ord != 1) {
         double L0[DD], L1[DD], A[DD], Bm[DD], Ai[DD], Rm[DD], F1[DD];
-        velgrad<D>(vp0, N0, V0, L0);
-        velgrad<D>(vp1, N1, V1, L1);
+        velgrad_iv<D>(vp0, N0, iV0, L0);
+        velgrad_iv<D>(vp1, N1, iV1, L1);
         for (int i = 0; i < D; ++i)
             for (int j = 0; j < D; ++j) {
                 A[i * D + j] = (i == j ? 1.0 : 0.0) - 0.5 * dt * L1[i * D + j];
@@ -822,8 +835,8 @@ LMOOD_HD void update_vjp(const double *xs0, const double *xs1, const double *vs,
         mm<D>(Ai, Rm, F1);
         if (lz1 != 0.0) {  // z1 = Z(F1, m / V1)
             double lrho = 0.0;
-            impedance_vjp<D>(F1, m / V1, mu, kap, lz1, lF1, lrho, lmu, lkap);
-            lV1 += lrho * (-m / (V1 * V1));
+            impedance_vjp<D>(F1, m * iV1, mu, kap, lz1, lF1, lrho, lmu, lkap);
+            lV1 -= lrho * m * iV1 * iV1;
         }
         // F1 = Ai Rm, Rm = Bm F
         double lRm[DD], lA[DD], lBm[DD], t[DD], lL0[DD], lL1[DD];
@@ -836,23 +849,23 @@ LMOOD_HD void update_vjp(const double *xs0, const double *xs1, const double *vs,
             lL1[q] = 0.5 * dt * lA[q];  // A = I - dt/2 L1, lA was -(...) -> +dt/2
             lL0[q] = 0.5 * dt * lBm[q];
         }
-        velgrad_vjp<D>(vp1, N1, V1, lL1, lvp1, lN1, lV1);
-        velgrad_vjp<D>(vp0, N0, V0, lL0, lvp0, lN0, lV0);
+        velgrad_vjp_iv<D>(vp1, N1, iV1, L1, lL1, lvp1, lN1, lV1);
+        velgrad_vjp_iv<D>(vp0, N0, iV0, L0, lL0, lvp0, lN0, lV0);
     } else {
         double Ls[DD], t[DD], lLs[DD];
-        velgrad<D>(vs, N0, V0, Ls);
+        velgrad_iv<D>(vs, N0, iV0, Ls);
         if (lz1 != 0.0) {
             double LF[DD], F1[DD], lrho = 0.0;
             mm<D>(Ls, F, LF);
             for (int q = 0; q < DD; ++q) F1[q] = F[q] + dt * LF[q];
-            impedance_vjp<D>(F1, m / V1, mu, kap, lz1, lF1, lrho, lmu, lkap);
-            lV1 += lrho * (-m / (V1 * V1));
+            impedance_vjp<D>(F1, m * iV1, mu, kap, lz1, lF1, lrho, lmu, lkap);
+            lV1 -= lrho * m * iV1 * iV1;
         }
         mtm<D>(Ls, lF1, t);
         for (int q = 0; q < DD; ++q) lF[q] += lF1[q] + dt * t[q];
         mmt<D>(lF1, F, lLs);
         for (int q = 0; q < DD; ++q) lLs[q] *= dt;
-        velgrad_vjp<D>(vs, N0, V0, lLs, lvs, lN0, lV0);
+        velgrad_vjp_iv<D>(vs, N0, iV0, Ls, lLs, lvs, lN0, lV0);
     }
     faces_vjp<D>(xs0, lV0, lN0, lxs0);
     faces_vjp<D>(xs1, lV1, lN1, lxs1);
