@@ -319,6 +319,10 @@ def run_ours(args, rank, local, ws, dist):
     if not args.no_batched:
         batched = run_batched(L, W, torch, local, value / ws, args)
 
+    variants = None
+    if not args.no_variants:
+        variants = run_variants(L, W, torch, pb, value / ws, args)
+
     adjoint = None
     if not args.no_adjoint:
         sim.close()
@@ -337,9 +341,49 @@ def run_ours(args, rank, local, ws, dist):
                            "lsq_pairs": info["stencil_nnz"], "parallelism": f"replicas x{ws}",
                            "l2": "working set > L2 (no flush)", "troubled_cells_in_timed_steps": troubled},
                 "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": ck, "e2e": e2e,
-                "cpu_baseline": cb, "batched": batched, "adjoint": adjoint,
+                "cpu_baseline": cb, "batched": batched, "variants": variants, "adjoint": adjoint,
                 "launch": None if tuned is None else {k: v["chosen"] for k, v in tuned.items()}}
         print(json.dumps(line), flush=True)
+
+
+def run_variants(L, W, torch, pb, plain_value, args) -> dict:
+    """The scheme's variants, each timed like the plain step (graph-captured steps, CUDA events,
+    after 5 untimed steps): on the benchmark mesh the shear energy family with a = 0 and the
+    three-level cascade (P1 -> P1 with Barth-Jespersen slopes -> P0); on 316 x 316-point
+    unit squares (198,450 triangles) a piston (prescribed-velocity face, slip walls) and a block
+    pressed against a contact wall (0.7 h away at the start); on 44^3 Kuhn cubes (511,104 tets) the stiffened-gas jelly
+    block dropped on a contact floor. cell-steps/s, and for the first two the ratio to the
+    plain step on the same mesh."""
+    import dataclasses
+    cases = [("shear_family_a0", dataclasses.replace(pb, shear_a=0.0), {}, True),
+             ("cascade3_bj", pb, {"cascade": 3}, True),
+             ("piston_velocity_faces", W.piston2d(n=316), {}, False),
+             ("contact_rebound", W.rebound2d(n=316, gap=0.7 / 315), {}, False),  # in contact after ~5 steps
+             ("stiffened_gas_jelly_drop_3d", W.jellydrop3d(n=44), {}, False)]
+    out = {}
+    stream = torch.cuda.Stream()
+    for name, q, kw, same_mesh in cases:
+        sim = L.simulation(q, stream=stream.cuda_stream, graph=0 if args.host_mode else 1, **kw)
+        for _ in range(5):
+            sim.step()
+        k = 40
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        troubled = 0
+        for _ in range(k):
+            troubled += sim.step().n_troubled
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        v = q.mesh.n_cells / (ms / 1e3)
+        out[name] = {"cells": q.mesh.n_cells, "ms_per_step": ms, "value": v, "unit": UNIT, "steps": k,
+                     "troubled_cells": troubled}
+        if same_mesh:
+            out[name]["vs_plain"] = v / plain_value
+        sim.close()
+        sim.mesh.close()
+    return out
 
 
 def run_batched(L, W, torch, local, plain_value, args) -> dict:
@@ -466,6 +510,7 @@ def main():
                     help="host-driven MOOD rounds instead of graph-captured steps (same kernels; for profilers)")
     ap.add_argument("--no-fp64-peak", action="store_true", help="skip the DGEMM FP64 peak measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-instances measurement")
+    ap.add_argument("--no-variants", action="store_true", help="skip the boundary / material / cascade variants")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-pass measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--adjoint-steps", type=int, default=400, help="steps recorded for the adjoint measurement")
