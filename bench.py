@@ -352,18 +352,22 @@ def run_variants(L, W, torch, pb, plain_value, args) -> dict:
     three-level cascade (P1 -> P1 with Barth-Jespersen slopes -> P0); on 316 x 316-point
     unit squares (198,450 triangles) a piston (prescribed-velocity face, slip walls) and a block
     pressed against a contact wall (0.7 h away at the start); on 44^3 Kuhn cubes (511,104 tets) the stiffened-gas jelly
-    block dropped on a contact floor. cell-steps/s, and for the first two the ratio to the
-    plain step on the same mesh."""
+    block dropped on a contact floor; the 40 x 40-point unit square (3,042 triangles) with
+    graph-captured steps and with the persistent step (one cooperative launch per step).
+    cell-steps/s, and for the first two the ratio to the plain step on the same mesh."""
     import dataclasses
     cases = [("shear_family_a0", dataclasses.replace(pb, shear_a=0.0), {}, True),
              ("cascade3_bj", pb, {"cascade": 3}, True),
              ("piston_velocity_faces", W.piston2d(n=316), {}, False),
              ("contact_rebound", W.rebound2d(n=316, gap=0.7 / 315), {}, False),  # in contact after ~5 steps
              ("stiffened_gas_jelly_drop_3d", W.jellydrop3d(n=44), {}, False)]
+    small = W.plain2d(n=40)  # 3,042 triangles: latency-bound
+    cases += [("small_plain2d_graph", small, {}, False), ("small_plain2d_persistent", small, {"graph": 2}, False)]
     out = {}
     stream = torch.cuda.Stream()
     for name, q, kw, same_mesh in cases:
-        sim = L.simulation(q, stream=stream.cuda_stream, graph=0 if args.host_mode else 1, **kw)
+        kw = {"graph": 0 if args.host_mode else 1, **kw}
+        sim = L.simulation(q, stream=stream.cuda_stream, **kw)
         for _ in range(5):
             sim.step()
         k = 40

@@ -113,10 +113,12 @@ template <int D> void refresh(const Geo &g, const Fld &f, const Prm &p, cudaStre
 template <int D> void totals(const Geo &g, const Fld &f, double *out, cudaStream_t s) {
     k_totals<D><<<blocks(g.N, 256), 256, 0, s>>>(g, f, out);
 }
-// cooperative launch of a persistent kernel: as many blocks as can be resident at once
+// cooperative launch of a persistent kernel: as many blocks as can be resident at once, or
+// max_blocks if fewer (work is spread one warp per block first, so a small mesh needs no more
+// blocks than it has warps of work, and fewer blocks make the grid barriers cheaper)
 template <typename K>
 static cudaError_t launch_cooperative(K kern, const Geo &g, const Fld &f, const Prm &p, const PersistArgs &a,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, long long max_blocks) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -124,7 +126,7 @@ static cudaError_t launch_cooperative(K kern, const Geo &g, const Fld &f, const 
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(per_sm * sms);
+    cfg.gridDim = dim3((unsigned)std::max(1LL, std::min<long long>((long long)per_sm * sms, max_blocks)));
     cfg.blockDim = dim3(kCellBlock);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -135,12 +137,14 @@ static cudaError_t launch_cooperative(K kern, const Geo &g, const Fld &f, const 
     return cudaLaunchKernelEx(&cfg, kern, g, f, p, a);
 }
 template <int D> cudaError_t persistent(const Geo &g, const Fld &f, const Prm &p, const PersistArgs &a, cudaStream_t s) {
-    return launch_cooperative(k_step_persistent<D>, g, f, p, a, s);
+    const long long items = std::max<long long>(std::max(g.N, g.Np), a.n_inst);
+    return launch_cooperative(k_step_persistent<D>, g, f, p, a, s, (items + 31) / 32);
 }
 template <int D> cudaError_t mood_persistent(const Geo &g, const Fld &f, const Prm &p, const PersistArgs &a, cudaStream_t s) {
-    if (p.eos) return launch_cooperative(k_mood_persistent<D, 2>, g, f, p, a, s);
-    if (p.shear_a != -1.0) return launch_cooperative(k_mood_persistent<D, 1>, g, f, p, a, s);
-    return launch_cooperative(k_mood_persistent<D, 0>, g, f, p, a, s);
+    const long long all = 1LL << 40;  // the lists' lengths are known on the device only
+    if (p.eos) return launch_cooperative(k_mood_persistent<D, 2>, g, f, p, a, s, all);
+    if (p.shear_a != -1.0) return launch_cooperative(k_mood_persistent<D, 1>, g, f, p, a, s, all);
+    return launch_cooperative(k_mood_persistent<D, 0>, g, f, p, a, s, all);
 }
 
 }  // namespace
