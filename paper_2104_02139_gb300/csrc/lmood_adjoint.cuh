@@ -411,12 +411,13 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
         return;
     }
     // least squares from the node moments
-    double G[DD] = {}, r[NQ][D] = {};
+    double G[DD] = {}, r[NQ][D] = {}, npair = -NV;  // (node, other cell) pairs of the stencil
     double qc[NQ];
     for (int q = 0; q < NQ; ++q) qc[q] = q < D ? vc[q] : Fc[q - D];
     for (int k = 0; k < NV; ++k) {
         double d[D], S1[D], w[D];
         const double n = mom(k, Q::M_N);
+        npair += n;
         for (int a = 0; a < D; ++a) {
             d[a] = xs[k * D + a] - xcc[a];
             S1[a] = mom(k, Q::M_S1 + a);
@@ -431,7 +432,7 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
     double tr = 0.0;
     for (int a = 0; a < D; ++a) tr += G[a * D + a];
     const double t = tr * (1.0 / D);
-    const bool ok = det<D>(G) > 1e-12 * (D == 2 ? t * t : t * t * t);
+    const bool ok = npair > 0.0 && det<D>(G) > 1e-12 * (D == 2 ? t * t : t * t * t);
     double Gi[DD], gs[NQ][D];
     inverse<D>(G, Gi);
     for (int q = 0; q < NQ; ++q)
@@ -550,10 +551,11 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
         zero_moments();
     } else {
         // ---- recompute the forward intermediates
-        double G[DD] = {}, r[NQ][D] = {}, qc[NQ], dk[NV][D];
+        double G[DD] = {}, r[NQ][D] = {}, qc[NQ], dk[NV][D], npair = -NV;
         for (int q = 0; q < NQ; ++q) qc[q] = q < D ? vc[q] : Fc[q - D];
         for (int k = 0; k < NV; ++k) {
             const double nk = mom(k, Q::M_N);
+            npair += nk;
             double S1[D], w[D];
             for (int a = 0; a < D; ++a) {
                 dk[k][a] = xs[k * D + a] - xcc[a];
@@ -569,7 +571,7 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
         double tr = 0.0;
         for (int a = 0; a < D; ++a) tr += G[a * D + a];
         const double t = tr * (1.0 / D);
-        const bool ok = det<D>(G) > 1e-12 * (D == 2 ? t * t : t * t * t);
+        const bool ok = npair > 0.0 && det<D>(G) > 1e-12 * (D == 2 ? t * t : t * t * t);
         double Gi[DD], gs[NQ][D];
         inverse<D>(G, Gi);
         for (int q = 0; q < NQ; ++q)

@@ -151,17 +151,17 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
         const double z = f.z[c];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double u[D], s = 0.0;
+            // with u = N_f / D: z / |u| u u^t = (z / (D |N_f|)) N_f N_f^t
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a < D; ++a) s += Nf[k][a] * Nf[k][a];
+            const double w = z * rsqrt(s) * (1.0 / D);
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                u[a] = Nf[k][a] * (1.0 / D);
-                s += u[a] * u[a];
+                const double wa = w * Nf[k][a];
+#pragma unroll
+                for (int b = a; b < D; ++b) W[k][sidx<D>(a, b)] = wa * Nf[k][b];
             }
-            const double w = z * rsqrt(s);
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-#pragma unroll
-                for (int b = a; b < D; ++b) W[k][sidx<D>(a, b)] = w * u[a] * u[b];
         }
     };
     // packet of corner k: M_cp and rhs_cp = M_cp v* - T* l n_p, with l n_p = -N_p / D
@@ -197,12 +197,13 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
         double xcc[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) xcc[a] = f.xc[a * N + c];
-        double G[NS], r[NQ][D], wsum[D];
+        double G[NS], r[NQ][D], wsum[D], npair = -NV;  // (node, other cell) pairs of the stencil
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             const double *m = f.mom + nod[k];
             double d[D], S1[D], w[D];
             const double nn = m[Q::M_N * Np];
+            npair += nn;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 d[a] = xs[k][a] - xcc[a];
@@ -215,8 +216,8 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
 #pragma unroll
                 for (int b = a; b < D; ++b) {
                     const int sb = sidx<D>(a, b);
-                    const double t = m[(Q::M_S2 + sb) * Np] + fma(S1[a], d[b], d[a] * w[b]);
-                    G[sb] = k == 0 ? t : G[sb] + t;
+                    const double s2 = m[(Q::M_S2 + sb) * Np];
+                    G[sb] = fma(S1[a], d[b], fma(d[a], w[b], k == 0 ? s2 : G[sb] + s2));
                 }
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
@@ -243,7 +244,8 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
 #pragma unroll
         for (int a = 0; a < D; ++a) tr += Gf[a * D + a];
         const double t = tr * (1.0 / D);
-        const bool ok = det<D>(Gf) > 1e-12 * (D == 2 ? t * t : t * t * t);
+        // an empty stencil gives G = 0 up to the rounding of the moment sums: no slopes
+        const bool ok = npair > 0.0 && det<D>(Gf) > 1e-12 * (D == 2 ? t * t : t * t * t);
         inverse<D>(Gf, Gi);
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
@@ -317,10 +319,8 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
             cell_stress<D, MAT>(prm, Fh, muc, kap, eps_c, T);
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                double s = 0.0;
 #pragma unroll
-                for (int b = 0; b < D; ++b) s += T[i * D + b] * Nf[k][b];
-                dvdt[i] += s;
+                for (int b = 0; b < D; ++b) dvdt[i] = fma(T[i * D + b], Nf[k][b], dvdt[i]);
             }
         }
         // half step: dt/2 dv/dt and dt/2 dF/dt with dF/dt = L^ F_c (Eq. GCLL)
@@ -684,12 +684,11 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
         for (int s = 0; s < NS; ++s) M[s] = f.pkM[s * NC + k * N + c];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            double s = 0.0;
+            double fa = -f.pkR[a * NC + k * N + c];  // f_cp = M_cp v*_p - rhs_cp
 #pragma unroll
-            for (int b = 0; b < D; ++b) s += M[sidx<D>(a, b)] * vsn[k][b];
-            const double fa = s - f.pkR[a * NC + k * N + c];
+            for (int b = 0; b < D; ++b) fa = fma(M[sidx<D>(a, b)], vsn[k][b], fa);
             sf[a] += fa;
-            sfv += fa * vsn[k][a];
+            sfv = fma(fa, vsn[k][a], sfv);
         }
     }
     const double mc = f.m[c], im = f.im[c], muc = f.mu[c], kap = kappa_of(prm, muc);
