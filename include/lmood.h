@@ -158,8 +158,11 @@ lmood_status lmood_params_default(int dim, lmood_params *p);
  *                  NULL for a single instance. Each instance keeps its own dt.
  *   n_inst         number of instances (1 when cell_inst is NULL)
  *   stream         cudaStream_t on which every device operation of this mesh is ordered
- * Builds the node-to-corner adjacency and the per-node boundary conditions. Errors: LMOOD_ERR_ARG, LMOOD_ERR_MESH (index out of range, |w_c| <= 0),
- * LMOOD_ERR_OOM, LMOOD_ERR_CUDA.
+ * Builds the node-to-corner adjacency and the per-node boundary conditions. Errors:
+ * LMOOD_ERR_ARG (also for a mesh beyond the kernels' 32-bit indexing: at most 238,609,294
+ * cells and 89,478,485 nodes in 2D, 89,478,485 cells and 37,025,580 nodes in 3D, checked
+ * before anything is read), LMOOD_ERR_MESH (index out of range, |w_c| <= 0), LMOOD_ERR_OOM,
+ * LMOOD_ERR_CUDA.
  */
 lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double *x, int64_t n_cells,
                                const int32_t *c2n, int64_t n_bfaces, const int32_t *bface,

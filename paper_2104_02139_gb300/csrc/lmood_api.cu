@@ -175,8 +175,15 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
     if (dim != 2 && dim != 3) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: dim must be 2 or 3");
     if (n_nodes <= 0 || n_cells <= 0 || !x || !c2n) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: empty mesh or NULL array");
     const int nv = dim + 1;
-    if (n_cells * nv >= (int64_t)INT32_MAX || n_nodes >= (int64_t)INT32_MAX)
-        return fail(LMOOD_ERR_ARG, "lmood_mesh_create: mesh too large for 32-bit corner ids");
+    // the kernels index with 32-bit integers: the largest offsets are those of the corner
+    // matrices (NS (D+1) N), of F (D^2 N) and of the node moments (NMOM Np)
+    {
+        const int64_t ns = dim * (dim + 1) / 2, nmom = (dim == 2 ? ops_dim2() : ops_dim3()).nmom;
+        if (n_cells > INT32_MAX / (ns * nv) || n_cells > INT32_MAX / (dim * dim) || n_nodes > INT32_MAX / nmom)
+            return fail(LMOOD_ERR_ARG, "lmood_mesh_create: mesh too large for 32-bit indices (at most " +
+                                           std::to_string(INT32_MAX / (ns * nv)) + " cells and " +
+                                           std::to_string(INT32_MAX / nmom) + " nodes in " + std::to_string(dim) + "D)");
+    }
     if (n_bfaces < 0 || (n_bfaces > 0 && (!bface || !btag))) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: boundary faces");
     if (cell_inst ? n_inst < 1 : n_inst > 1) return fail(LMOOD_ERR_ARG, "lmood_mesh_create: bad instance count");
     if (!cell_inst) n_inst = 1;

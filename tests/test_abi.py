@@ -32,3 +32,19 @@ def test_params_default_without_gpu():
         assert e.status == L.ERR_ARG
     else:
         raise AssertionError("dim 4 accepted")
+
+
+def test_mesh_size_limits_checked_before_any_device_work():
+    """The kernels index with 32-bit integers: meshes whose corner matrices, F or node moments
+    would overflow them are refused with LMOOD_ERR_ARG (the sizes are checked before the arrays
+    are read or any device call is made; the limits are 3D 89,478,485 cells / 37,025,580 nodes,
+    2D 238,609,294 cells / 89,478,485 nodes)."""
+    import ctypes as C
+    lib = L.lib()
+    x = (C.c_double * 12)()
+    c2n = (C.c_int32 * 4)(0, 1, 2, 3)
+    out = C.c_void_p()
+    for dim, nodes, cells in ((3, 4, 89_478_486), (3, 37_025_581, 1), (2, 3, 238_609_295), (2, 89_478_486, 1)):
+        rc = lib.lmood_mesh_create(dim, nodes, x, cells, c2n, 0, None, None, None, 1, None, C.byref(out))
+        assert rc == L.ERR_ARG, (dim, nodes, cells)
+        assert "too large" in lib.lmood_last_error().decode()
