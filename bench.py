@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "cell-steps/s of full ADER-MOOD step (FP64, 1 GB300)"
+METRIC = "cell-steps/s of full ADER-MOOD step (FP64, 1 GB300); batched and adjoint vs plain"
 UNIT = "cell-steps/s"
 WORKLOAD = "impact2d: 999,698 triangles (708x708 jittered Delaunay lattice), rho0=8.93 mu=0.46 lambda=1.06, v=(-0.1,0), slip wall x=0, CFL 0.4"
 WORKLOADS = {
