@@ -365,3 +365,57 @@ def test_three_level_cascade(orc):
         order = o.get(orc.F_ORDER)
         res[cas] = (int((order == 1).sum()), int((order == 3).sum()))
     assert res[2][1] == 0 and res[3][1] > 0 and res[3][0] < res[2][0]
+
+
+# ----------------------------------------------------------------------------- entropy
+def _thermal(o, orc, pb):
+    """specific internal energy not stored elastically, e - |v|^2/2 - Psi(F) (theta d eta)"""
+    d = pb.mesh.dim
+    v, e, F = o.get(orc.F_V), o.get(orc.F_E), o.get(orc.F_F)
+    kap = pb.lam + 2.0 * pb.mu / 3.0
+    psi = np.array([orc.free_energy(F[:, c].reshape(d, d), pb.rho0, pb.mu[c], kap[c]) for c in range(F.shape[1])])
+    return e - 0.5 * (v * v).sum(axis=0) - psi
+
+
+def _dissipation(o, orc, pb, v_n):
+    """sum over the cell's corners of M_cp (v*_p - v_c) . (v*_p - v_c), v_c at t^n"""
+    d, c2n = pb.mesh.dim, pb.mesh.c2n
+    pk, vs = o.get(orc.F_PKM), o.get(orc.F_VSTAR)
+    out = np.zeros(pb.mesh.n_cells)
+    for c in range(pb.mesh.n_cells):
+        for k in range(d + 1):
+            w = vs[:, c2n[k, c]] - v_n[:, c]
+            out[c] += w @ pk[:, k, c].reshape(d, d) @ w
+    return out
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_first_order_entropy_production(orc, d):
+    """Sect. "Semi-discrete entropy analysis - Subcell force" (Eq. theta_deta_discr2): with the
+    subcell force of the scheme, m_c theta_c d eta_c / dt = sum_p M_cp (v_p - v_c) . (v_p - v_c)
+    >= 0, theta d eta being the change of e - |v|^2/2 - Psi(F). First-order steps from the same
+    state: every cell's production is >= 0 (to rounding) at the CFL step, and its ratio to the
+    right-hand side evaluated with the step's packets and v*_p tends to 1 linearly in dt. A sign
+    error in M_cp, a stress inconsistent with Psi or a wrong energy update fails it."""
+    pb = W.impact2d(n=16) if d == 2 else W.cube3d(n=4)
+    if d == 3:
+        pb.v *= 20
+    o = orc.Oracle(pb, order=1, mood=0)
+    o.step()  # a state with node velocities and a strained mesh
+    st, dt0 = o.state(), o.dt
+    errs = []
+    for scale in (1.0, 0.1, 0.01):
+        s = orc.Oracle(pb, order=1, mood=0, dt_fixed=dt0 * scale)
+        s.set_state(x=st["x"], vp=st["vp"], v=st["v"], e=st["e"], F=st["F"], dt=dt0 * scale)
+        h0, v_n, m = _thermal(s, orc, pb), s.get(orc.F_V).copy(), s.get(orc.F_MASS)
+        s.step()
+        dh = _thermal(s, orc, pb) - h0
+        D = _dissipation(s, orc, pb, v_n) * (dt0 * scale) / m
+        if scale == 1.0:
+            assert dh.min() >= -1e-15 * np.abs(s.get(orc.F_E)).max()
+            assert (m * dh).sum() > 0.0
+        sel = D > 1e-3 * D.max()
+        assert sel.sum() >= 20
+        errs.append(np.abs(dh[sel] / D[sel] - 1.0).max())
+    assert errs[1] < 0.05 and errs[2] < 0.005
+    assert 5.0 < errs[1] / errs[2] < 20.0  # first order in dt
