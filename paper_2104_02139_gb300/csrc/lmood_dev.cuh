@@ -412,6 +412,16 @@ __device__ __forceinline__ double kappa_of(const Prm &prm, double mu) {
     return prm.vol_coeff ? mu : prm.lam + mu * (2.0 / 3.0);
 }
 
+// A double's bits as a signed integer whose order is the numeric order (NaN aside): min / max
+// of densities on the integer pipe instead of the FP64 one
+__device__ __forceinline__ long long order_key(double x) {
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double key_value(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
 // physical admissibility (Eq. PAD): 0 admissible, 1 only eps < -tol, 2 not computable;
 // tol = 1e-10 max(|e|, |v|^2/2, a0sq) with a0sq the material's energy scale
 // (kappa + 4 mu / 3) / rho0, the squared P-wave speed at rest: in a cell at rest e and

@@ -501,7 +501,8 @@ __device__ __forceinline__ void node_solve(const Geo &g, const Fld &f, int p, in
     for (int a = 0; a < D; ++a) b[a] = 0.0;
     // also the range of rho^n over the cells around the node (RDMP bounds, Eq. RDMP: the
     // union over a cell's nodes is its stencil plus the cell itself)
-    double rlo = __longlong_as_double(0x7ff0000000000000LL), rhi = -rlo;
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    long long klo = order_key(inf), khi = order_key(-inf);
     const int j1 = __ldg(g.n2c_off + p + 1);
     for (int j = __ldg(g.n2c_off + p); j < j1; ++j) {
         const int cid = __ldg(g.n2c + j);
@@ -513,12 +514,12 @@ __device__ __forceinline__ void node_solve(const Geo &g, const Fld &f, int p, in
         cc -= cc >= g.N ? g.N : 0;
         cc -= cc >= g.N ? g.N : 0;
         cc -= cc >= g.N ? g.N : 0;
-        const double r = f.rho[cc];
-        rlo = fmin(rlo, r);
-        rhi = fmax(rhi, r);
+        const long long kr = order_key(f.rho[cc]);
+        klo = min(klo, kr);
+        khi = max(khi, kr);
     }
-    f.rlo[p] = rlo;
-    f.rhi[p] = rhi;
+    f.rlo[p] = key_value(klo);
+    f.rhi[p] = key_value(khi);
     double M[DD];
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -768,12 +769,13 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
         if (ord != 1) {
             bool bad = ps != 0;
             if (!bad) {
-                double lo = f.rlo[nod[0]], hi = f.rhi[nod[0]];
+                long long klo = order_key(f.rlo[nod[0]]), khi = order_key(f.rhi[nod[0]]);
 #pragma unroll
                 for (int k = 1; k < NV; ++k) {
-                    lo = fmin(lo, f.rlo[nod[k]]);
-                    hi = fmax(hi, f.rhi[nod[k]]);
+                    klo = min(klo, order_key(f.rlo[nod[k]]));
+                    khi = max(khi, order_key(f.rhi[nod[k]]));
                 }
+                const double lo = key_value(klo), hi = key_value(khi);
                 const double delta = fmax(prm.delta0, prm.delta1 * (hi - lo));
                 bad = !(rho1 >= lo - delta && rho1 <= hi + delta);
             }
