@@ -436,12 +436,15 @@ __device__ __forceinline__ int pad_state(const double (&v)[D], double e, const d
     for (int i = 0; i < D; ++i) inf |= expo(v[i]) + 0x00100000u;
 #pragma unroll
     for (int i = 0; i < D * D; ++i) inf |= expo(F[i]) + 0x00100000u;
-    if ((inf & 0x80000000u) || !(V > 0.0) || !(det<D>(F) > 0.0)) return 2;
+    // V finite here: V > 0 exactly when its bits are a positive integer
+    if ((inf & 0x80000000u) || __double_as_longlong(V) <= 0 || !(det<D>(F) > 0.0)) return 2;
     double ke = 0.0;
 #pragma unroll
     for (int i = 0; i < D; ++i) ke += 0.5 * v[i] * v[i];
     const double eps = e - ke;
-    return eps >= -1e-10 * fmax(fmax(fabs(e), ke), a0sq) ? 0 : 1;
+    // finite operands: the comparisons on order keys (integer pipe) equal the FP64 ones
+    const double scale = key_value(max(max(order_key(fabs(e)), order_key(ke)), order_key(a0sq)));
+    return order_key(eps) >= order_key(-1e-10 * scale) ? 0 : 1;
 }
 
 // ---------------------------------------------------------------------------------------

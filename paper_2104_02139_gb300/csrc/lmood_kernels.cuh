@@ -776,8 +776,10 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
                     khi = max(khi, order_key(f.rhi[nod[k]]));
                 }
                 const double lo = key_value(klo), hi = key_value(khi);
-                const double delta = fmax(prm.delta0, prm.delta1 * (hi - lo));
-                bad = !(rho1 >= lo - delta && rho1 <= hi + delta);
+                const long long kd = max(order_key(prm.delta0), order_key(prm.delta1 * (hi - lo)));
+                const double delta = key_value(kd);
+                const long long kr = order_key(rho1);  // finite: PAD passed
+                bad = !(kr >= order_key(lo - delta) && kr <= order_key(hi + delta));
             }
             if (bad) tlist[atomicAdd(tcnt, 1)] = c;
         } else {
