@@ -223,6 +223,15 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
         for (int64_t c = 0; c < N; ++c)
             for (int k = 0; k < nv; ++k) n2c[pos[c2n[k * N + c]]++] = (int)(k * N + c);
     }
+    // the nodes in order of their cell count (stable: the caller's order within a count), so
+    // that the per-node kernels give a warp nodes with equally long loops
+    std::vector<int> perm(Np);
+    {
+        std::vector<int64_t> first(max_deg + 2, 0);
+        for (int64_t p = 0; p < Np; ++p) first[off[p + 1] - off[p] + 1]++;
+        for (int d2 = 0; d2 <= max_deg; ++d2) first[d2 + 1] += first[d2];
+        for (int64_t p = 0; p < Np; ++p) perm[first[off[p + 1] - off[p]]++] = (int)p;
+    }
     // (node, neighbour) pairs of the least-squares sums: sum_p deg(p) (deg(p) - 1)
     int64_t nnz = 0;
     for (int64_t p = 0; p < Np; ++p) nnz += (int64_t)(off[p + 1] - off[p]) * (off[p + 1] - off[p] - 1);
@@ -300,13 +309,14 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
     g.Np = (int)Np;
     g.n_inst = n_inst;
     lmood_status s;
-    int *d_c2n, *d_off, *d_n2c, *d_ci = nullptr, *d_ni = nullptr;
+    int *d_c2n, *d_off, *d_n2c, *d_perm, *d_ci = nullptr, *d_ni = nullptr;
     unsigned char *d_nd;
     double *d_bt;
     std::vector<int> c2n_i(c2n, c2n + N * nv);
     if ((s = upload(m->mem, &d_c2n, c2n_i.data(), c2n_i.size(), st)) ||
         (s = upload(m->mem, &d_off, off.data(), off.size(), st)) ||
         (s = upload(m->mem, &d_n2c, n2c.data(), n2c.size(), st)) ||
+        (s = upload(m->mem, &d_perm, perm.data(), perm.size(), st)) ||
         (s = upload(m->mem, &d_nd, ndof.data(), ndof.size(), st)) ||
         (s = upload(m->mem, &d_bt, bct.data(), bct.size(), st)) ||
         (s = upload(m->mem, &m->x0, x, (size_t)(dim * Np), st))) {
@@ -326,6 +336,7 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
     g.c2n = d_c2n;
     g.n2c_off = d_off;
     g.n2c = d_n2c;
+    g.node_perm = d_perm;
     g.bc_ndof = d_nd;
     g.bc_t = d_bt;
     g.cell_inst = d_ci;

@@ -17,6 +17,12 @@ namespace lmood {
 constexpr int kCellBlock = 128;
 constexpr int kNodeBlock = 256;
 
+// the whole-mesh nodal solve takes the nodes in order of their cell count in 3D, where the
+// counts vary most (Kuhn tetrahedra: 6 to 24), and in the caller's order in 2D, where the
+// memory order of the node arrays matters more than the few divergent loop iterations
+// (measured: 2D 0.085 ms in the caller's order, 0.130 ms sorted; 3D 0.124 ms, 0.087 ms sorted)
+template <int D> constexpr bool kNodesByCount = D == 3;
+
 // list launches use at most this many blocks and loop over the device-counted list
 constexpr int kListBlocks = 152 * 8;
 
@@ -94,8 +100,8 @@ template <int D> __device__ __forceinline__ void moments_node(const Geo &g, cons
 }
 
 template <int D, int B = kNodeBlock> __global__ void __launch_bounds__(B) k_moments(Geo g, Fld f) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < g.Np) moments_node<D>(g, f, p);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < g.Np) moments_node<D>(g, f, g.node_perm[t]);
 }
 
 // MAT: 0 neo-Hookean, 1 another shear energy of the family, 2 stiffened gas (separate
@@ -623,9 +629,9 @@ __device__ __forceinline__ void node_solve(const Geo &g, const Fld &f, int p, in
 template <int D, bool LISTED, int B = kNodeBlock>
 __global__ void __launch_bounds__(B) k_nodes(Geo g, Fld f, const int *__restrict__ list,
                                                       const int *__restrict__ cnt, int n, int init_mode) {
-    if constexpr (!LISTED) {
-        const int p = blockIdx.x * blockDim.x + threadIdx.x;
-        if (p < n) node_solve<D>(g, f, p, init_mode);
+    if constexpr (!LISTED) {  // every node (n = Np); in 3D in order of their cell count
+        const int t = blockIdx.x * blockDim.x + threadIdx.x;
+        if (t < n) node_solve<D>(g, f, kNodesByCount<D> ? g.node_perm[t] : t, init_mode);
     } else {
         const int nn = *cnt;
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)

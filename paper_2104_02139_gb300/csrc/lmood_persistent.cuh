@@ -125,11 +125,11 @@ __global__ void __launch_bounds__(kCellBlock, D == 2 ? LMOOD_PERSIST_MINB2 : 1)
         f.dtn[i] = (unsigned long long)__double_as_longlong(d);
     }
     if (!grid_sync(a.bar, a.max_spin)) return;
-    for (int p = tid; p < Np; p += nth) moments_node<D>(g, f, p);
+    for (int p = tid; p < Np; p += nth) moments_node<D>(g, f, g.node_perm[p]);
     if (!grid_sync(a.bar, a.max_spin)) return;
     for (int c = tid; c < N; c += nth) predict_cell<D, false, 0>(g, f, prm, c);
     if (!grid_sync(a.bar, a.max_spin)) return;
-    for (int p = tid; p < Np; p += nth) node_solve<D>(g, f, p, 0);
+    for (int p = tid; p < Np; p += nth) node_solve<D>(g, f, kNodesByCount<D> ? g.node_perm[p] : p, 0);
     if (!grid_sync(a.bar, a.max_spin)) return;
     for (int c = tid; c < N; c += nth) update_cell<D>(g, f, prm, c, a.tl0, f.cnt + CNT_T0);
     if (!grid_sync(a.bar, a.max_spin)) return;
