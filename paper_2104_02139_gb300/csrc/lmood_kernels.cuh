@@ -17,12 +17,6 @@ namespace lmood {
 constexpr int kCellBlock = 128;
 constexpr int kNodeBlock = 256;
 
-// the whole-mesh nodal solve takes the nodes in order of their cell count in 3D, where the
-// counts vary most (Kuhn tetrahedra: 6 to 24), and in the caller's order in 2D, where the
-// memory order of the node arrays matters more than the few divergent loop iterations
-// (measured: 2D 0.085 ms in the caller's order, 0.130 ms sorted; 3D 0.124 ms, 0.087 ms sorted)
-template <int D> constexpr bool kNodesByCount = D == 3;
-
 // list launches use at most this many blocks and loop over the device-counted list
 constexpr int kListBlocks = 152 * 8;
 
