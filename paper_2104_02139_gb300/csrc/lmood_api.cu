@@ -223,14 +223,21 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
         for (int64_t c = 0; c < N; ++c)
             for (int k = 0; k < nv; ++k) n2c[pos[c2n[k * N + c]]++] = (int)(k * N + c);
     }
-    // the nodes in order of their cell count (stable: the caller's order within a count), so
-    // that the per-node kernels give a warp nodes with equally long loops
+    // the nodes of each window of 256 consecutive ones in order of their cell count (stable),
+    // so that the per-node kernels give a warp nodes with equally long loops while a block
+    // still reads the cells of one neighbourhood
     std::vector<int> perm(Np);
     {
-        std::vector<int64_t> first(max_deg + 2, 0);
-        for (int64_t p = 0; p < Np; ++p) first[off[p + 1] - off[p] + 1]++;
-        for (int d2 = 0; d2 <= max_deg; ++d2) first[d2 + 1] += first[d2];
-        for (int64_t p = 0; p < Np; ++p) perm[first[off[p + 1] - off[p]]++] = (int)p;
+        constexpr int64_t kWin = 256;
+        std::vector<int64_t> first(max_deg + 2);
+        for (int64_t w0 = 0; w0 < Np; w0 += kWin) {
+            const int64_t w1 = std::min(Np, w0 + kWin);
+            std::fill(first.begin(), first.end(), 0);
+            for (int64_t p = w0; p < w1; ++p) first[off[p + 1] - off[p] + 1]++;
+            first[0] = w0;
+            for (int d2 = 0; d2 <= max_deg; ++d2) first[d2 + 1] += first[d2];
+            for (int64_t p = w0; p < w1; ++p) perm[first[off[p + 1] - off[p]]++] = (int)p;
+        }
     }
     // (node, neighbour) pairs of the least-squares sums: sum_p deg(p) (deg(p) - 1)
     int64_t nnz = 0;

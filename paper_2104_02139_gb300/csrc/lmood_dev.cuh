@@ -56,11 +56,9 @@ struct Geo {
     const double *contact;
 };
 
-// the whole-mesh nodal solve takes the nodes in order of their cell count in 3D, where the
-// counts vary most (Kuhn tetrahedra: 6 to 24), and in the caller's order in 2D, where the
-// memory order of the node arrays matters more than the few divergent loop iterations
-// (measured: 2D 0.085 ms in the caller's order, 0.130 ms sorted; 3D 0.124 ms, 0.087 ms sorted)
-template <int D> constexpr bool kNodesByCount = D == 3;
+// the whole-mesh nodal solve takes the nodes in the permuted order (cell count within
+// windows of 256) in both dimensions
+template <int D> constexpr bool kNodesByCount = true;
 
 constexpr unsigned char BC_EXT = 0x80;      // node has traction / pressure / velocity faces
 constexpr unsigned char BC_CONTACT = 0x40;  // node has contact faces
