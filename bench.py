@@ -87,13 +87,13 @@ def kernel_bytes(dim: int, nc: int, npn: int, nnz: int) -> dict:
 # divided by the cell count; they include the FP64 expansions of division, sqrt, log, cbrt.
 # Re-measured whenever a kernel changes (profiles/ holds the capture); None = not measured
 # for the current kernel.
-FP64_FLOP_PER_CELL = {"predict": 838.0, "update": 365.0, "nodes": 31.1, "moments": 120.0}
+FP64_FLOP_PER_CELL = {"predict": 838.0, "update": 366.0, "nodes": 31.1, "moments": 120.0}
 # FP64 thread instructions per cell (dfma + dadd + dmul) from the same capture: the pipe's
 # issue rate, compared with DGEMM's (one DFMA = 2 FLOP per instruction), shows how busy the
 # pipe is independently of the operation mix.
-FP64_INSTR_PER_CELL = {"predict": 518.0, "update": 237.0, "nodes": 25.0, "moments": 75.0}
+FP64_INSTR_PER_CELL = {"predict": 518.0, "update": 238.0, "nodes": 25.0, "moments": 75.0}
 # DRAM bytes (read + write) per full launch from the same ncu capture, or None.
-TRAFFIC_PER_LAUNCH = {"predict": 295.40e6, "update": 349.40e6, "nodes": 178.10e6, "moments": 134.80e6}
+TRAFFIC_PER_LAUNCH = {"predict": 292.70e6, "update": 350.80e6, "nodes": 182.10e6, "moments": 150.70e6}
 
 
 def fp64_peak_tflops(device) -> float:
