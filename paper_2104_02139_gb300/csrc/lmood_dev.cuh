@@ -39,7 +39,8 @@ struct Geo {
     Blk blk;
     const int *c2n;
     const int *n2c_off, *n2c;
-    const int *node_perm;          // the nodes in order of their cell count (whole-mesh node loops)
+    const int *node_perm;          // the nodes of each window of 256 in order of their cell count
+                                   // (whole-mesh node loops)
     const unsigned char *bc_ndof;  // free directions per node (D = free, 0 = clamped), | BC_EXT
                                    // when a traction / pressure / velocity face touches the node
     const double *bc_t;            // tangent vectors [2][3][Np]

@@ -2,6 +2,7 @@
 // on the space dimension. Included by one translation unit per dimension.
 //
 // Per step (all cells / all nodes, then MOOD rounds over compacted lists):
+//   k_moments  nodes : moments of the cells around each node (the least-squares sums)
 //   k_predict  cells : geometry at x^n, least-squares slopes of v and F, ADER predictor,
 //                      corner packets (M_cp, rhs_cp)
 //   k_nodes    nodes : ordered gather of the packets around the node, Eucclhyd solve with
@@ -9,6 +10,8 @@
 //   k_update   cells : subcell forces, update of v, e, tau, F, detection, dt candidate
 //   k_mark_*         : troubled cells -> their nodes -> the cells around those nodes
 //   k_finalize       : next dt (exact min over cells) and the per-step counters
+// The whole-mesh node kernels take the nodes of each window of 256 in order of their cell
+// count (Geo::node_perm), so that the lanes of a warp run loops of one length.
 #pragma once
 #include "lmood_dev.cuh"
 
@@ -28,6 +31,7 @@ constexpr int kListBlocks = 152 * 8;
 //   P0: v*_cp = v_c, F*_cp = F_c.
 //   M_cp = z_c sum_{f containing p} |ln_f| n_f (x) n_f, rhs_cp = M_cp v*_cp - T(F*_cp) ln_p.
 // With a list, only the listed cells (troubled ones, already marked P0) are recomputed.
+// (predict_cell and k_predict follow the node moments they read.)
 // ---------------------------------------------------------------------------------------
 // ---------------------------------------------------------------------------------------
 // k_moments: per node p, moments of the cells c' around it (positions relative to x_p):
