@@ -122,9 +122,13 @@ def current_stream_handle():
 
 
 def params_default(dim: int, **kw) -> Params:
+    """lmood_params_default, then the given fields (unknown names raise TypeError)"""
     p = Params()
     _check(lib().lmood_params_default(dim, C.byref(p)))
+    known = {name for name, _ in Params._fields_}
     for k, v in kw.items():
+        if k not in known:
+            raise TypeError(f"unknown step parameter {k!r} (lmood_params has {sorted(known)})")
         setattr(p, k, v)
     return p
 
@@ -422,8 +426,6 @@ def simulation(problem, stream=None, cell_inst=None, n_inst=1, **params) -> Stat
         mesh.set_bc_values(problem.bcval)
     if getattr(problem, "contact", None) is not None:
         mesh.set_contact(*problem.contact)
-    p = params_default(m.dim, cfl=problem.cfl)
-    for k, v in params.items():
-        setattr(p, k, v)
+    p = params_default(m.dim, **{"cfl": problem.cfl, **params})
     return State(mesh, problem.rho0, problem.lam, problem.mu, problem.v, problem.F, p,
                  shear_a=getattr(problem, "shear_a", -1.0), stiffened_gas=getattr(problem, "stiffened_gas", None))

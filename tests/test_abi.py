@@ -48,3 +48,10 @@ def test_mesh_size_limits_checked_before_any_device_work():
         rc = lib.lmood_mesh_create(dim, nodes, x, cells, c2n, 0, None, None, None, 1, None, C.byref(out))
         assert rc == L.ERR_ARG, (dim, nodes, cells)
         assert "too large" in lib.lmood_last_error().decode()
+
+
+def test_unknown_step_parameter_is_an_error():
+    import pytest
+    with pytest.raises(TypeError):
+        L.params_default(2, grpah=2)
+    assert L.params_default(2, graph=2, barrier_polls=7).barrier_polls == 7
