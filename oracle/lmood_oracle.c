@@ -37,6 +37,8 @@
  *      v*_cp = v_h(x_p) + dt/2 (1/m_c) sum_q T(F_h(x_q)) (ln)_cq,
  *      F*_cp = F_h(x_p) + dt/2 L^_c F_c with L^_c the reconstructed velocity gradient,
  *      T*_cp = T(F*_cp). First-order (P0) cells use v*_cp = v_c^n, T*_cp = T(F_c^n).
+ *      Parity unpinned: the predictor's exact form has no independent reference; only its
+ *      observed second order (swinging plate) is pinned.
  *  R9  reconstruction: least squares about cell centroids over the stencil V_c = all cells
  *      sharing a node with c (the "Voronoi neighbours" of Sect. "Algorithm"; the same set
  *      bounds the RDMP), each neighbour weighted by the number of nodes it shares with c
@@ -46,7 +48,9 @@
  *      about 2 with or without the weights (the paper gives none).
  *  R10 v_p^n is stored per node; v_p^{n+1} = 2 v*_p - v_p^n; v_p^0 is the first-order
  *      nodal solution at t^0.
- *  R11 MOOD: cascade P1 -> P0 (default) or, as in Sect. "Limiting: a posteriori MOOD loop",
+ *  R11 MOOD (which cells the detection flags: parity unpinned beyond the injected-fault tests;
+ *      the CUDA path's masks are compared with these at every step): cascade P1 -> P0
+ *      (default) or, as in Sect. "Limiting: a posteriori MOOD loop",
  *      P1 -> P1 with Barth-Jespersen limited slopes -> P0 (order codes 2, 3, 1). The limiter
  *      scales each field's slope by the largest factor <= 1 that keeps its values at the
  *      cell's nodes within the field's range over the stencil and the cell (at t^n).
