@@ -419,3 +419,40 @@ def test_first_order_entropy_production(orc, d):
         errs.append(np.abs(dh[sel] / D[sel] - 1.0).max())
     assert errs[1] < 0.05 and errs[2] < 0.005
     assert 5.0 < errs[1] / errs[2] < 20.0  # first order in dt
+
+
+def test_slip_planes_in_3d_leave_their_intersection(orc):
+    """Reading R14 on a cube with slip walls on all six faces: after a step a node on one wall
+    has exactly zero velocity across it and moves freely along it (zero residual of the
+    Galerkin solve in the wall's plane); a node on an edge (two walls) moves along the edge
+    only; a corner node (three walls) does not move."""
+    pb = W.cube3d(n=4)
+    pb.v *= 20
+    o = orc.Oracle(pb)
+    o.step()
+    d, nv = 3, 4
+    x0 = pb.mesh.x
+    pkM = o.get(orc.F_PKM).reshape(d, d, nv, -1)
+    pkR = o.get(orc.F_PKR)
+    vs = o.get(orc.F_VSTAR)
+    Mp = np.zeros((pb.mesh.n_nodes, d, d))
+    bp = np.zeros((pb.mesh.n_nodes, d))
+    for k in range(nv):
+        np.add.at(Mp, pb.mesh.c2n[k], pkM[:, :, k, :].transpose(2, 0, 1))
+        np.add.at(bp, pb.mesh.c2n[k], pkR[:, k, :].T)
+    res = np.einsum("pab,bp->pa", Mp, vs) - bp
+    scale = np.abs(bp).max()
+    on = (np.abs(x0) < 1e-14) | (np.abs(x0 - 1.0) < 1e-14)  # [3, np]: on the wall normal to axis a
+    counts = {1: 0, 2: 0, 3: 0}
+    for p in range(pb.mesh.n_nodes):
+        walls = np.where(on[:, p])[0]
+        if walls.size == 0:
+            continue
+        counts[walls.size] += 1
+        assert np.all(vs[walls, p] == 0.0), (p, walls, vs[:, p])
+        free = [a for a in range(d) if a not in walls]
+        assert o.bc_ndof(p) == len(free)
+        if free:
+            assert np.abs(res[p, free]).max() <= 1e-12 * scale
+            assert np.abs(vs[free, p]).max() > 0.0
+    assert counts[1] > 0 and counts[2] > 0 and counts[3] == 8
