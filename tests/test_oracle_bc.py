@@ -201,3 +201,25 @@ def test_contact_face_without_walls_is_free():
     for _ in range(200):
         o.step()
     assert (o.get(O.F_X)[0] + gap).min() < -0.02
+
+
+def test_piston_in_3d_meets_its_velocity_exactly():
+    """A box pushed through its x = 0 face (prescribed normal velocity V, Eq. vBC; reading R15)
+    with slip walls at y = 0, y = 1: every node of the face, those on its edges with the slip
+    walls included, moves with v*_x = V exactly, and the edge nodes keep zero velocity across
+    their slip wall."""
+    m = W.tet_mesh(4, 4, 4, 9, bc={"x0": W.VELOCITY, "y0": W.SLIP, "y1": W.SLIP})
+    V = 0.03
+    pb = W.Problem("piston3d", m, 1.0, 2.0, np.full(m.n_cells, 1.0), np.zeros((3, m.n_cells)), 0.25, 5,
+                   bcval=W.side_values(m, W.VELOCITY, (V, 0.0, 0.0)))
+    o = O.Oracle(pb)
+    x = o.get(O.F_X)
+    face = np.where(np.abs(x[0]) < 1e-15)[0]
+    edges = face[(np.abs(x[1, face]) < 1e-15) | (np.abs(x[1, face] - 1.0) < 1e-15)]
+    assert face.size == 25 and edges.size == 10
+    for _ in range(4):
+        o.step()
+        vs = o.get(O.F_VSTAR)
+        np.testing.assert_allclose(vs[0, face], V, rtol=1e-13)
+        assert np.abs(vs[1, edges]).max() == 0.0
+    assert np.abs(o.get(O.F_X)[0, face] - V * o.t).max() < 1e-14
