@@ -223,3 +223,32 @@ def test_piston_in_3d_meets_its_velocity_exactly():
         np.testing.assert_allclose(vs[0, face], V, rtol=1e-13)
         assert np.abs(vs[1, edges]).max() == 0.0
     assert np.abs(o.get(O.F_X)[0, face] - V * o.t).max() < 1e-14
+
+
+def test_contact_floor_in_3d():
+    """A block falling onto a floor through its contact face (reading R17) in 3D: free fall
+    until the face comes within eps of the floor, then no node closer than eps less one step's
+    travel, total energy conserved to round-off (the floor does no work), the vertical momentum
+    reversed by the contact and constant again once the face has detached."""
+    m = W.tet_mesh(4, 4, 4, 9, bc={"z0": W.CONTACT})
+    v = np.zeros((3, m.n_cells))
+    v[2] = -0.1
+    gap, eps = 0.15, 0.125
+    planes = np.array([[0.0, 0.0, -gap, 0.0, 0.0, 1.0]])
+    pb = W.Problem("drop3d", m, 1.0, 2.0, np.full(m.n_cells, 1.0), v, 0.25, 10, contact=(planes, eps))
+    o = O.Oracle(pb)
+    mass = o.get(O.F_MASS)
+    E0 = (mass * o.get(O.F_E)).sum()
+    touched = False
+    pz = []
+    for _ in range(200):
+        o.step()
+        z = o.get(O.F_X)[2]
+        assert (z + gap).min() >= eps - 0.1 * o.dt - 1e-15
+        assert abs((mass * o.get(O.F_E)).sum() - E0) <= 1e-14 * E0
+        touched = touched or (z + gap).min() < eps
+        pz.append((mass * o.get(O.F_V)[2]).sum() / mass.sum())
+    assert touched
+    # rebounded and detached: upward, constant momentum in the last steps
+    assert min(pz[-25:]) > 0.3 * 0.1
+    assert max(pz[-25:]) - min(pz[-25:]) <= 1e-13 * max(pz[-25:])
