@@ -252,3 +252,54 @@ def test_contact_floor_in_3d():
     # rebounded and detached: upward, constant momentum in the last steps
     assert min(pz[-25:]) > 0.3 * 0.1
     assert max(pz[-25:]) - min(pz[-25:]) <= 1e-13 * max(pz[-25:])
+
+
+def _face_vectors_3d(m, x):
+    """outward area vector of every boundary triangle at positions x [3, np] (orientation from
+    the tetrahedron on the face's inner side)"""
+    c2n = m.c2n.T
+    out = np.zeros((m.bface.shape[1], 3))
+    for i, (q0, q1, q2) in enumerate(m.bface.T):
+        N = 0.5 * np.cross(x[:, q1] - x[:, q0], x[:, q2] - x[:, q0])
+        cell = np.where(np.isin(c2n, [q0, q1, q2]).sum(axis=1) == 3)[0][0]
+        opp = [q for q in c2n[cell] if q not in (q0, q1, q2)][0]
+        if N @ (x[:, q0] - x[:, opp]) < 0:
+            N = -N
+        out[i] = N
+    return out
+
+
+def test_pressure_and_traction_in_3d():
+    """3D counterparts of the 2D pins: a block under F = s I held by the pressure -sigma on all
+    six sides stays at rest; a free block at rest under random face tractions gains the momentum
+    dt sum_f |N_f| t_f and the energy dt sum_p F_p . v*_p (F_p the nodes' thirds of the faces
+    around them) in one step."""
+    s = 0.97
+    kappa = 2.0 + 2.0 / 3.0
+    sigma = O.stress(s * np.eye(3), 1.0, kappa)[0, 0]
+    sides = ("x0", "x1", "y0", "y1", "z0", "z1")
+    m = W.tet_mesh(3, 3, 3, 5, bc={k: W.PRESSURE for k in sides})
+    F = np.tile((s * np.eye(3)).reshape(9, 1), (1, m.n_cells))
+    pb = W.Problem("block3d", m, 1.0, 2.0, np.full(m.n_cells, 1.0), np.zeros((3, m.n_cells)), 0.25, 5, F=F,
+                   bcval=W.side_values(m, W.PRESSURE, (-sigma, 0.0, 0.0)))
+    o = O.Oracle(pb)
+    for _ in range(4):
+        o.step()
+    assert np.abs(o.get(O.F_V)).max() < 1e-13 and np.abs(o.get(O.F_VP)).max() < 1e-13
+
+    m = W.tet_mesh(3, 3, 3, 6, bc={k: W.TRACTION for k in sides})
+    t = np.random.default_rng(7).normal(size=(3, m.btag.size)) * 0.01
+    pb = W.Problem("free3d", m, 1.0, 2.0, np.full(m.n_cells, 1.0), np.zeros((3, m.n_cells)), 0.25, 5, bcval=t)
+    o = O.Oracle(pb)
+    x0, mass, e0, dt = o.get(O.F_X).copy(), o.get(O.F_MASS), o.get(O.F_E).copy(), o.dt
+    o.step()
+    Nf = _face_vectors_3d(m, x0)
+    area = np.linalg.norm(Nf, axis=1)
+    np.testing.assert_allclose((mass[None, :] * o.get(O.F_V)).sum(axis=1), dt * (area[None, :] * t).sum(axis=1),
+                               rtol=1e-12, atol=1e-16)
+    Fp = np.zeros_like(x0)
+    for i, q in enumerate(m.bface.T):
+        for p in q:
+            Fp[:, p] += area[i] * t[:, i] / 3
+    work = dt * (Fp * o.get(O.F_VSTAR)).sum()
+    assert abs((mass * (o.get(O.F_E) - e0)).sum() - work) <= 1e-12 * abs(work)
