@@ -87,3 +87,38 @@ def test_bad_stiffened_gas_parameters_are_rejected():
                    stiffened_gas=(0.9, 1.0, 0.0))
     with pytest.raises(O.OracleError):
         O.Oracle(pb)
+
+
+def test_stiffened_gas_in_3d_rest_and_energy():
+    """3D counterparts: a compressed block held by the outer pressure that balances its stiffened
+    gas pressure and shear stress stays at rest; in a box with slip walls and a swirling
+    velocity the total energy is conserved to round-off."""
+    s, gamma, pinf, p0, mu = 0.98, 2.2, 1.0, 0.3, 0.2
+    Ts = O.stress_a(s * np.eye(3), mu, 0.0, -1.0)  # shear part alone (zero for a pure dilation)
+    P = p0 - Ts[0, 0]
+    sides = ("x0", "x1", "y0", "y1", "z0", "z1")
+    m = W.tet_mesh(3, 3, 3, 4, bc={k: W.PRESSURE for k in sides})
+    pb = W.Problem("sgblock3d", m, 1.0, 0.0, np.full(m.n_cells, mu), np.zeros((3, m.n_cells)), 0.25, 5,
+                   F=np.tile((s * np.eye(3)).reshape(9, 1), (1, m.n_cells)),
+                   bcval=W.side_values(m, W.PRESSURE, (P, 0.0, 0.0)), stiffened_gas=(gamma, pinf, p0))
+    o = O.Oracle(pb)
+    x0 = o.get(O.F_X).copy()
+    for _ in range(4):
+        o.step()
+    assert np.abs(o.get(O.F_V)).max() < 1e-13 and np.abs(o.get(O.F_X) - x0).max() < 1e-14
+    o2 = O.Oracle(dataclasses.replace(pb, bcval=W.side_values(m, W.PRESSURE, (P + 0.05, 0.0, 0.0))))
+    for _ in range(4):
+        o2.step()
+    assert np.abs(o2.get(O.F_V)).max() > 1e-4  # a wrong outer pressure sets it moving
+
+    m = W.tet_mesh(4, 4, 4, 5, bc={k: W.SLIP for k in sides})
+    pts = m.x[:, m.c2n].mean(axis=1)
+    v = 0.05 * np.stack([np.sin(np.pi * pts[0]) * np.cos(np.pi * pts[1]), -np.cos(np.pi * pts[0]) * np.sin(np.pi * pts[1]),
+                         0.3 * np.sin(np.pi * pts[2])])
+    pb = W.Problem("sgbox3d", m, 1.0, 0.0, np.full(m.n_cells, 0.3), v, 0.25, 10, stiffened_gas=(2.2, 1.0, 0.2))
+    o = O.Oracle(pb)
+    mass = o.get(O.F_MASS)
+    E0 = (mass * o.get(O.F_E)).sum()
+    for _ in range(20):
+        o.step()
+    assert abs((mass * o.get(O.F_E)).sum() - E0) <= 1e-13 * abs(E0)
