@@ -456,3 +456,21 @@ def test_slip_planes_in_3d_leave_their_intersection(orc):
             assert np.abs(res[p, free]).max() <= 1e-12 * scale
             assert np.abs(vs[free, p]).max() > 0.0
     assert counts[1] > 0 and counts[2] > 0 and counts[3] == 8
+
+
+def test_three_level_cascade_3d(orc):
+    """The three-level cascade on tetrahedra: limited-slope cells appear, fewer cells end at first
+    order than with P1 -> P0, and energy is conserved."""
+    pb = W.column3d(nxy=4, nz=24)
+    pb.v *= 5
+    res = {}
+    for cas in (2, 3):
+        o = orc.Oracle(pb, cascade=cas)
+        E0, _ = _totals(o, orc)
+        for _ in range(10):
+            o.step()
+        E1, _ = _totals(o, orc)
+        assert abs(E1 - E0) <= 1e-13 * abs(E0)
+        order = o.get(orc.F_ORDER)
+        res[cas] = (int((order == 1).sum()), int((order == 3).sum()))
+    assert res[2][1] == 0 and res[3][1] > 0 and res[3][0] < res[2][0]
