@@ -161,8 +161,10 @@ lmood_status lmood_params_default(int dim, lmood_params *p);
  * Builds the node-to-corner adjacency and the per-node boundary conditions. Errors:
  * LMOOD_ERR_ARG (also for a mesh beyond the kernels' 32-bit indexing: at most 238,609,294
  * cells and 89,478,485 nodes in 2D, 89,478,485 cells and 37,025,580 nodes in 3D, checked
- * before anything is read), LMOOD_ERR_MESH (index out of range, |w_c| <= 0), LMOOD_ERR_OOM,
- * LMOOD_ERR_CUDA.
+ * before anything is read), LMOOD_ERR_MESH (index out of range, |w_c| <= 0, a boundary face
+ * that is not the face of exactly one cell, instances of a batch sharing a node; all checked
+ * on the host before any device call), LMOOD_ERR_OOM (device memory), LMOOD_ERR_CUDA (any
+ * other CUDA failure, e.g. no usable device).
  */
 lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double *x, int64_t n_cells,
                                const int32_t *c2n, int64_t n_bfaces, const int32_t *bface,

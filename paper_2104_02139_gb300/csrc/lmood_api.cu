@@ -248,8 +248,8 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
     for (int64_t f = 0; f < n_bfaces; ++f) {
         int q[3];
         for (int a = 0; a < dim; ++a) q[a] = bf[a * n_bfaces + f];
-        int opp = -1;
-        for (int j = off[q[0]]; j < off[q[0] + 1] && opp < 0; ++j) {
+        int opp = -1, owners = 0;  // the cells having the face: exactly one for a boundary face
+        for (int j = off[q[0]]; j < off[q[0] + 1]; ++j) {
             const int64_t c = n2c[j] % N;
             int hits = 0, other = -1;
             for (int k = 0; k < nv; ++k) {
@@ -259,9 +259,13 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
                 if (on) ++hits;
                 else other = r;
             }
-            if (hits == dim) opp = other;
+            if (hits == dim) {
+                if (owners++ == 0) opp = other;
+            }
         }
-        if (opp < 0) return fail(LMOOD_ERR_MESH, "lmood_mesh_create: boundary face " + std::to_string(f) + " is not a cell face");
+        if (owners != 1)
+            return fail(LMOOD_ERR_MESH, "lmood_mesh_create: boundary face " + std::to_string(f) + " is a face of " +
+                                            std::to_string(owners) + " cells (a boundary face belongs to exactly one)");
         double nrm[3] = {0, 0, 0};
         if (dim == 2) {
             nrm[0] = x[1 * Np + q[1]] - x[1 * Np + q[0]];

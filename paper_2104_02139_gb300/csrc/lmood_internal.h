@@ -29,7 +29,9 @@ struct DevAllocs {
         cudaError_t e = cudaMalloc(p, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            return fail(LMOOD_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+            // out of device memory, or no usable device / driver at all
+            return fail(e == cudaErrorMemoryAllocation ? LMOOD_ERR_OOM : LMOOD_ERR_CUDA,
+                        std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
         }
         ptrs.push_back(*p);
         return LMOOD_OK;
