@@ -55,3 +55,14 @@ def test_unknown_step_parameter_is_an_error():
     with pytest.raises(TypeError):
         L.params_default(2, grpah=2)
     assert L.params_default(2, graph=2, barrier_polls=7).barrier_polls == 7
+
+
+def test_field_copies_check_their_destinations_on_the_host():
+    """get_fields refuses mixed or non-float64 destinations before any library call."""
+    import numpy as np
+    import pytest
+    s = L.State.__new__(L.State)  # no device state needed: the check comes first
+    with pytest.raises(ValueError):
+        s.get_fields({L.FIELD_X: np.zeros((2, 3)), L.FIELD_V: np.zeros((2, 3), dtype=np.float32)})
+    with pytest.raises(ValueError):
+        s.get_fields({L.FIELD_X: np.zeros((3, 2)).T})  # not C-contiguous
