@@ -162,7 +162,8 @@ lmood_status lmood_params_default(int dim, lmood_params *p);
  * LMOOD_ERR_ARG (also for a mesh beyond the kernels' 32-bit indexing: at most 238,609,294
  * cells and 89,478,485 nodes in 2D, 89,478,485 cells and 37,025,580 nodes in 3D, checked
  * before anything is read), LMOOD_ERR_MESH (index out of range, |w_c| <= 0, a boundary face
- * that is not the face of exactly one cell, instances of a batch sharing a node; all checked
+ * that is not the face of exactly one cell, a face listed twice (in any node order),
+ * instances of a batch sharing a node; all checked
  * on the host before any device call), LMOOD_ERR_OOM (device memory), LMOOD_ERR_CUDA (any
  * other CUDA failure, e.g. no usable device).
  */
@@ -285,8 +286,9 @@ lmood_status lmood_timing_read(lmood_state s, double *ms, int64_t *launches);
  *   without synchronising. Sums are taken in a fixed order, so repeated calls agree bitwise.
  * Scratch is a fixed file-scope device array of 256 KiB (per GPU, held until exit), so
  * n_cells is limited to 16,777,216: larger sizes return LMOOD_ERR_ARG. The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress); make that first call
- * outside any stream capture. All calls share the array: calls whose work overlaps on the GPU
+ * device looks up the array's device address (cudaGetSymbolAddress), and so does the first
+ * call after the device's context changed (e.g. after cudaDeviceReset, which drops the array
+ * and its contents); make those calls outside any stream capture. All calls share the array: calls whose work overlaps on the GPU
  * race and must be ordered by the caller. Allocates nothing (no cudaMalloc / cudaFree).
  */
 lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, const double *v, const double *e,

@@ -110,6 +110,66 @@ def _ptr(a):
     return None if a is None else a.ctypes.data
 
 
+def _is_torch(a) -> bool:
+    return hasattr(a, "data_ptr") and hasattr(a, "is_cuda")
+
+
+def _numel(shape) -> int:
+    return int(np.prod(shape, dtype=np.int64))
+
+
+def _out_buffer(a, shape, what: str):
+    """Check a destination the library writes prod(shape) doubles into: a writeable
+    C-contiguous float64 numpy array (host) or a contiguous float64 CUDA tensor (device) of
+    exactly that many elements. Returns (pointer, is_device). Anything else raises before the
+    library is called, so no copy can run past the end of the buffer."""
+    n = _numel(shape)
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous or not a.flags.writeable:
+            raise ValueError(f"{what}: host destination must be a writeable C-contiguous float64 array "
+                             f"(got {a.dtype}, contiguous={a.flags.c_contiguous})")
+        if a.size != n:
+            raise ValueError(f"{what}: destination has {a.size} elements, the field needs {n} {tuple(shape)}")
+        return a.ctypes.data, 0
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.float64 or not a.is_cuda or not a.is_contiguous():
+            raise ValueError(f"{what}: device destination must be a contiguous float64 CUDA tensor "
+                             f"(got {a.dtype}, cuda={a.is_cuda}, contiguous={a.is_contiguous()})")
+        if a.numel() != n:
+            raise ValueError(f"{what}: destination has {a.numel()} elements, the field needs {n} {tuple(shape)}")
+        return a.data_ptr(), 1
+    raise TypeError(f"{what}: destination must be a numpy array or a torch CUDA tensor, not {type(a).__name__}")
+
+
+def _in_buffer(a, shape, what: str):
+    """A source the library reads prod(shape) doubles from. Host data (anything numpy accepts)
+    is converted to a C-contiguous float64 copy when needed; a torch tensor must be a CUDA
+    tensor and is made contiguous float64 when needed. Returns (keep, pointer, is_device,
+    copied): keep must stay alive until the library has read it -- for a device copy that is
+    until the mesh's stream has passed the call (the caller synchronises when copied)."""
+    n = _numel(shape)
+    if _is_torch(a):
+        import torch
+        if not a.is_cuda:
+            raise ValueError(f"{what}: a torch source must be a CUDA tensor (host data: pass numpy)")
+        t = a if (a.dtype == torch.float64 and a.is_contiguous()) else a.to(torch.float64).contiguous()
+        if t.numel() != n:
+            raise ValueError(f"{what}: source has {t.numel()} elements, the field needs {n} {tuple(shape)}")
+        return t, t.data_ptr(), 1, t is not a
+    h = np.ascontiguousarray(a, dtype=np.float64)
+    if h.size != n:
+        raise ValueError(f"{what}: source has {h.size} elements, the field needs {n} {tuple(shape)}")
+    return h, h.ctypes.data, 0, False
+
+
+def _sync_after_copy():
+    """A temporary device copy was handed to the library: wait until every stream (the mesh's
+    included) has finished with it before it can be freed and reused by torch's allocator."""
+    import torch
+    torch.cuda.synchronize()
+
+
 def current_stream_handle():
     """torch's current CUDA stream as a raw handle (None for the legacy default stream)."""
     try:
@@ -143,7 +203,7 @@ class Mesh:
         btag = _host(btag, np.int32)
         ci = _host(cell_inst, np.int32)
         nb = 0 if btag is None else btag.size
-        self.dim, self.n_nodes, self.n_cells = dim, x.shape[-1], c2n.shape[-1]
+        self.dim, self.n_nodes, self.n_cells, self.n_bfaces = dim, x.shape[-1], c2n.shape[-1], nb
         self.n_inst = n_inst if ci is not None else 1
         self.stream = current_stream_handle() if stream is None else stream
         h = C.c_void_p()
@@ -155,11 +215,11 @@ class Mesh:
     def set_bc_values(self, values):
         """boundary-face values [dim, n_bfaces]: traction vectors (tag 3), pressures in row 0
         (tag 4), prescribed velocities (tag 5); numpy (host) or a torch CUDA tensor"""
-        if hasattr(values, "data_ptr"):
-            _check(lib().lmood_mesh_set_bc_values(self.h, C.c_void_p(values.contiguous().data_ptr()), 1))
-        else:
-            a = np.ascontiguousarray(values, dtype=np.float64)
-            _check(lib().lmood_mesh_set_bc_values(self.h, a.ctypes.data, 0))
+        keep, ptr, dev, copied = _in_buffer(values, (self.dim, self.n_bfaces), "set_bc_values")
+        _check(lib().lmood_mesh_set_bc_values(self.h, C.c_void_p(ptr), dev))
+        if copied:
+            _sync_after_copy()
+        del keep
 
     def set_contact(self, planes, eps: float):
         """contact walls [n][2 dim] (a point, the unit normal into the body) and threshold eps
@@ -236,44 +296,45 @@ class State:
                 FIELD_PKM: (d * (d + 1) // 2, nv, nc), FIELD_PKR: (d, nv, nc), FIELD_DT: (self.mesh.n_inst,)}[field]
 
     def get(self, field: int, out=None):
-        """Host copy as numpy (out None or a numpy array), or into a torch CUDA tensor."""
+        """Host copy as numpy (out None or a numpy array), or into a torch CUDA tensor; out
+        must be float64, contiguous and of the field's size (checked before the copy)."""
         if out is None:
             out = np.empty(self.shape(field))
-        if isinstance(out, np.ndarray):
-            _check(lib().lmood_get(self.h, field, out.ctypes.data, 0))
-        else:
-            _check(lib().lmood_get(self.h, field, C.c_void_p(out.data_ptr()), 1))
+        ptr, dev = _out_buffer(out, self.shape(field), "get")
+        _check(lib().lmood_get(self.h, field, C.c_void_p(ptr), dev))
         return out
 
     def set(self, field: int, src):
-        if isinstance(src, np.ndarray) or not hasattr(src, "data_ptr"):
-            a = np.ascontiguousarray(src, dtype=np.float64)
-            _check(lib().lmood_set(self.h, field, a.ctypes.data, 0))
-        else:
-            _check(lib().lmood_set(self.h, field, C.c_void_p(src.data_ptr()), 1))
+        """Replace a field from host data (numpy-convertible) or a torch CUDA tensor of the
+        field's size."""
+        keep, ptr, dev, copied = _in_buffer(src, self.shape(field), "set")
+        _check(lib().lmood_set(self.h, field, C.c_void_p(ptr), dev))
+        if copied:
+            _sync_after_copy()
+        del keep
 
     def get_fields(self, outs: dict) -> dict:
         """lmood_get_fields: {field id: destination} all numpy (one synchronisation at the end)
         or all torch CUDA tensors"""
         ids = list(outs)
-        host = isinstance(outs[ids[0]], np.ndarray)
-        for f in ids:
-            o = outs[f]
-            if host != isinstance(o, np.ndarray) or (host and not (o.dtype == np.float64 and o.flags.c_contiguous)):
-                raise ValueError("get_fields: destinations must be all contiguous float64 numpy or all CUDA tensors")
-        ptrs = [outs[f].ctypes.data if host else outs[f].data_ptr() for f in ids]
+        checked = [_out_buffer(outs[f], self.shape(f), f"get_fields (field {f})") for f in ids]
+        if len({dev for _, dev in checked}) > 1:
+            raise ValueError("get_fields: destinations must be all host or all device")
         _check(lib().lmood_get_fields(self.h, len(ids), (C.c_int * len(ids))(*ids),
-                                      (C.c_void_p * len(ids))(*ptrs), 0 if host else 1))
+                                      (C.c_void_p * len(ids))(*[p for p, _ in checked]), checked[0][1]))
         return outs
 
     def set_fields(self, srcs: dict):
         """lmood_set_fields: {field id: source}, all host arrays or all torch CUDA tensors"""
         ids = list(srcs)
-        host = not hasattr(srcs[ids[0]], "data_ptr")
-        keep = [np.ascontiguousarray(srcs[f], dtype=np.float64) if host else srcs[f].contiguous() for f in ids]
-        ptrs = [a.ctypes.data if host else a.data_ptr() for a in keep]
+        checked = [_in_buffer(srcs[f], self.shape(f), f"set_fields (field {f})") for f in ids]
+        if len({c[2] for c in checked}) > 1:
+            raise ValueError("set_fields: sources must be all host or all device")
         _check(lib().lmood_set_fields(self.h, len(ids), (C.c_int * len(ids))(*ids),
-                                      (C.c_void_p * len(ids))(*ptrs), 0 if host else 1))
+                                      (C.c_void_p * len(ids))(*[c[1] for c in checked]), checked[0][2]))
+        if any(c[3] for c in checked):
+            _sync_after_copy()
+        del checked
 
     def totals(self) -> np.ndarray:
         o = (C.c_double * 5)()
@@ -339,21 +400,29 @@ class Tape:
             else:
                 out = {k: np.empty(v) for k, v in shapes.items()}
 
-        def keep(a):  # contiguous float64 copies (when needed) that stay alive for the call
+        kept, args = [], []
+        for a, k in zip(ins, ("x", "vp", "v", "F")):
             if a is None:
-                return None
-            if dev:
-                if not hasattr(a, "data_ptr"):
-                    raise TypeError("mix of host and device adjoint inputs")
-                import torch
-                return a.to(torch.float64).contiguous()
-            return np.ascontiguousarray(a, dtype=np.float64)
-
-        kept = [keep(a) for a in ins]
-        args = [None if a is None else (C.c_void_p(a.data_ptr()) if dev else a.ctypes.data) for a in kept]
-        outs = [out.get(k) for k in ("x", "vp", "v", "F", "mu")]
-        optr = [None if o is None else (C.c_void_p(o.data_ptr()) if dev else o.ctypes.data) for o in outs]
+                args.append(None)
+                continue
+            if dev != _is_torch(a):
+                raise TypeError("backward: adjoint inputs must be all host arrays or all CUDA tensors")
+            kept.append(_in_buffer(a, shapes[k], f"backward (lam_{k})"))
+            args.append(C.c_void_p(kept[-1][1]))
+        optr = []
+        for k in ("x", "vp", "v", "F", "mu"):
+            o = out.get(k)
+            if o is None:
+                optr.append(None)
+                continue
+            ptr, odev = _out_buffer(o, shapes[k], f"backward (grad_{k})")
+            if odev != int(dev):
+                raise ValueError("backward: gradients must live where the adjoint inputs do (host or device)")
+            optr.append(C.c_void_p(ptr))
         _check(lib().lmood_tape_backward(self.h, *args, *optr, 1 if dev else 0))
+        if any(c[3] for c in kept):
+            _sync_after_copy()
+        del kept
         return out
 
     def replay(self, state: State, n_steps: int | None = None) -> State:

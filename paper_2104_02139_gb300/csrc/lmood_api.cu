@@ -288,6 +288,22 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
         }
         if (dot < 0.0) std::swap(bf[0 * n_bfaces + f], bf[1 * n_bfaces + f]);
     }
+    // a face listed twice (in any node order) would give its nodes its traction, pressure or
+    // velocity share twice
+    {
+        std::vector<std::array<int, 4>> keys(n_bfaces);
+        for (int64_t f = 0; f < n_bfaces; ++f) {
+            std::array<int, 4> k{-1, -1, -1, (int)f};
+            for (int a = 0; a < dim; ++a) k[a] = bf[a * n_bfaces + f];
+            std::sort(k.begin(), k.begin() + dim);
+            keys[f] = k;
+        }
+        std::sort(keys.begin(), keys.end());
+        for (int64_t i = 1; i < n_bfaces; ++i)
+            if (std::equal(keys[i].begin(), keys[i].begin() + 3, keys[i - 1].begin()))
+                return fail(LMOOD_ERR_MESH, "lmood_mesh_create: boundary faces " + std::to_string(keys[i - 1][3]) +
+                                                " and " + std::to_string(keys[i][3]) + " are the same face");
+    }
     std::vector<int> nbf_off(Np + 1, 0), nbf_idx(n_bfaces * dim);
     for (int64_t f = 0; f < n_bfaces; ++f)
         for (int a = 0; a < dim; ++a) nbf_off[bf[a * n_bfaces + f] + 1]++;

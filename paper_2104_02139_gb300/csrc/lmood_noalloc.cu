@@ -14,6 +14,8 @@
 // keeps the last call's partial sums; each call overwrites exactly the rows it reads, so
 // nothing needs clearing, but calls whose kernels overlap on the GPU (different streams, or
 // other host threads) race on the array and must be ordered by the caller.
+#include <cuda.h>
+
 #include <mutex>
 #include <string>
 
@@ -35,11 +37,45 @@ constexpr int kRow = 8;  // mass, mom x, y, z, energy, 3 spare
 
 static_assert(sizeof(g_totals_scratch) == sizeof(double) * kMaxBlocks * kRow, "scratch size");
 
-// Device address of g_totals_scratch per device, looked up once (with that device current)
-// on the first call made on it; host code must not use the symbol itself as an address.
+// Device address of g_totals_scratch per device, looked up (with that device current) on the
+// first call made on it; host code must not use the symbol itself as an address. The address
+// belongs to the device's current CUDA context: after a cudaDeviceReset the runtime creates a
+// new context and loads the module again, so the cache also keeps the id of the context the
+// address was taken in and looks the address up again when that id changes.
 constexpr int kMaxDevices = 64;
 double *g_scratch_ptr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};
 std::mutex g_scratch_mu;
+
+// the driver's cuCtxGetCurrent / cuCtxGetId through the runtime's entry-point query (no link
+// against the driver library, which a machine without a GPU does not have)
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
+// id of the calling thread's current context (0 when it cannot be determined: the cache then
+// never matches and the address is looked up on every call)
+unsigned long long current_context_id() {
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (PfnCtxGetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PfnCtxGetId)f;
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 lmood_status fail(lmood_status s, const std::string &m) {
     lmood_internal_set_error(m.c_str());  // read back with lmood_last_error()
@@ -94,12 +130,16 @@ lmood_status scratch_for_current_device(double **out) {
     if (e != cudaSuccess) return fail(LMOOD_ERR_CUDA, std::string("lmood_totals_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(LMOOD_ERR_ARG, "lmood_totals_noalloc: device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    // cudaGetSymbolAddress makes the device's primary context current if none is, so the
+    // context id is read after the look-up on a first call and before it afterwards
+    const unsigned long long ctx = g_scratch_ptr[dev] ? current_context_id() : 0;
+    if (!g_scratch_ptr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         double *p = nullptr;
         e = cudaGetSymbolAddress((void **)&p, g_totals_scratch);
         if (e != cudaSuccess || !p)
             return fail(LMOOD_ERR_CUDA, std::string("lmood_totals_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = current_context_id();
     }
     *out = g_scratch_ptr[dev];
     return LMOOD_OK;

@@ -21,9 +21,11 @@ def relerr(g: np.ndarray, o: np.ndarray) -> float:
 
 class Pair:
     def __init__(self, problem, **params):
+        """params: step parameters of both sides; graph (the library's step form) goes to the
+        CUDA side only"""
         self.pb = problem
         self.g = L.simulation(problem, **params)
-        self.o = O.Oracle(problem, **params)
+        self.o = O.Oracle(problem, **{k: v for k, v in params.items() if k != "graph"})
 
     def errors(self) -> dict:
         out = {}

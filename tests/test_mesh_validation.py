@@ -42,6 +42,13 @@ def test_bad_boundary_faces():
     assert _status(lambda: L.Mesh(2, X2, C2, np.array([[0], [2]], np.int32), np.array([1], np.int32))) == L.ERR_MESH
     # (1, 3) is no cell's face
     assert _status(lambda: L.Mesh(2, X2, C2, np.array([[1], [3]], np.int32), np.array([1], np.int32))) == L.ERR_MESH
+    # the same face twice, in either node order (its nodes would take its traction share twice)
+    for dup in (np.array([[0, 0], [1, 1]], np.int32), np.array([[0, 1], [1, 0]], np.int32)):
+        assert _status(lambda: L.Mesh(2, X2, C2, dup, np.array([3, 3], np.int32))) == L.ERR_MESH
+    x3 = np.array([[0.0, 1, 0, 0], [0.0, 0, 1, 0], [0.0, 0, 0, 1]])
+    tet = np.array([[0], [1], [2], [3]], np.int32)
+    dup3 = np.array([[0, 2], [1, 0], [2, 1]], np.int32)  # face (0, 1, 2) listed as (0,1,2) and (2,0,1)
+    assert _status(lambda: L.Mesh(3, x3, tet, dup3, np.array([1, 4], np.int32))) == L.ERR_MESH
 
 
 def test_bad_batches():
