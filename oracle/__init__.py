@@ -82,6 +82,9 @@ def lib():
         L.orc_mesh_stencil.argtypes = [C.c_void_p, C.c_long, np.ctypeslib.ndpointer(np.int64), C.c_long]
         L.orc_mesh_stencil.restype = C.c_long
         L.orc_debug_corner_values.argtypes = [C.c_void_p, C.c_long, C.c_int, dp, dp, dp]
+        L.orc_debug_rdmp.argtypes = [C.c_void_p, C.c_long, C.c_double, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]
+        L.orc_debug_pad.argtypes = [C.c_void_p, C.c_long, dp, C.c_double, dp, C.c_double]
         L.orc_mesh_bc_ndof.argtypes = [C.c_void_p, C.c_long]
         L.orc_mesh_bc_ndof.restype = C.c_int
         L.orc_mesh_set_bc_values.argtypes = [C.c_void_p, dp]
@@ -255,6 +258,24 @@ class Oracle:
         out, lo, hi = np.zeros((d + 1) * nq), np.zeros(nq), np.zeros(nq)
         lib().orc_debug_corner_values(self._h.state, c, level, out, lo, hi)
         return out.reshape(d + 1, nq), lo, hi
+
+    def rdmp(self, c: int, rho_new: float):
+        """(admissible, lo, hi): the RDMP decision of Eq. RDMP for a candidate density of cell
+        c, and the density range at the current positions over the cell's stencil and itself"""
+        lo, hi = C.c_double(), C.c_double()
+        ok = lib().orc_debug_rdmp(self._h.state, c, rho_new, C.byref(lo), C.byref(hi))
+        if ok < 0:
+            raise OracleError("orc_debug_rdmp: bad cell")
+        return bool(ok), lo.value, hi.value
+
+    def pad(self, c: int, v, e: float, F, V: float) -> int:
+        """Eq. PAD for a candidate of cell c (its material): 0 admissible, 1 only eps below the
+        tolerance, 2 not computable (non-finite, V <= 0, det F <= 0)"""
+        r = lib().orc_debug_pad(self._h.state, c, np.ascontiguousarray(v, dtype=np.float64).ravel(), e,
+                                np.ascontiguousarray(F, dtype=np.float64).ravel(), V)
+        if r < 0:
+            raise OracleError("orc_debug_pad: bad cell")
+        return r
 
     def bc_ndof(self, p: int) -> int:
         return lib().orc_mesh_bc_ndof(self._h.mesh, p)

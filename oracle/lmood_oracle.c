@@ -48,8 +48,8 @@
  *      about 2 with or without the weights (the paper gives none).
  *  R10 v_p^n is stored per node; v_p^{n+1} = 2 v*_p - v_p^n; v_p^0 is the first-order
  *      nodal solution at t^0.
- *  R11 MOOD (which cells the detection flags: parity unpinned beyond the injected-fault tests;
- *      the CUDA path's masks are compared with these at every step): cascade P1 -> P0
+ *  R11 MOOD (the detection thresholds of Eqs. PAD and RDMP are pinned by closed-form cases
+ *      in the tests; the CUDA path's masks are compared with these at every step): cascade P1 -> P0
  *      (default) or, as in Sect. "Limiting: a posteriori MOOD loop",
  *      P1 -> P1 with Barth-Jespersen limited slopes -> P0 (order codes 2, 3, 1). The limiter
  *      scales each field's slope by the largest factor <= 1 that keeps its values at the
@@ -1122,18 +1122,31 @@ static int pad_state(int d, const double *v, double e, const double *F, double V
     return eps >= -tol ? 0 : 1;
 }
 
-static int rdmp_ok(const OrcState *S, const Work *w, long c) {
+/* Eq. RDMP: the range [lo, hi] of the density at t^n over the stencil V_c and the cell c
+ * itself (reading R12), from the volumes Vn at x^n */
+static void rdmp_range(const OrcState *S, const double *Vn, long c, double *lo, double *hi) {
     const OrcMesh *M = S->M;
-    double lo = S->m[c] / w->V[c], hi = lo;
+    *lo = S->m[c] / Vn[c];
+    *hi = *lo;
     for (long j = M->st_off[c]; j < M->st_off[c + 1]; ++j) {
         long o = M->st_idx[j];
-        double r = S->m[o] / w->V[o];
-        lo = fmin(lo, r);
-        hi = fmax(hi, r);
+        double r = S->m[o] / Vn[o];
+        *lo = fmin(*lo, r);
+        *hi = fmax(*hi, r);
     }
+}
+
+/* Eq. RDMP: a candidate density is admissible when it lies in [lo - delta, hi + delta],
+ * delta = max(delta0, delta1 (hi - lo)) with delta0 absolute (reading R12) */
+static int rdmp_admits(const OrcState *S, double rho_new, double lo, double hi) {
     double delta = fmax(S->prm.delta0, S->prm.delta1 * (hi - lo));
-    double r1 = S->m[c] / w->V1[c];
-    return r1 >= lo - delta && r1 <= hi + delta;
+    return rho_new >= lo - delta && rho_new <= hi + delta;
+}
+
+static int rdmp_ok(const OrcState *S, const Work *w, long c) {
+    double lo, hi;
+    rdmp_range(S, w->V, c, &lo, &hi);
+    return rdmp_admits(S, S->m[c] / w->V1[c], lo, hi);
 }
 
 static void candidate(const OrcState *S, const int *order, double dt, Work *w) {
@@ -1408,6 +1421,30 @@ int orc_debug_corner_values(const OrcState *S, long c, int level, double *out, d
     free(order);
     work_free(&w);
     return ORC_OK;
+}
+
+/* The detection of Eqs. PAD and RDMP as the step applies it, for the tests that pin its
+ * thresholds: orc_debug_rdmp gives the density range of cell c at the state's current
+ * positions (lo, hi, may be NULL) and whether a candidate density rho_new passes the RDMP;
+ * orc_debug_pad classifies a candidate (v [d], e, F [d*d] row-major, volume V) of cell c
+ * with the cell's material: 0 admissible, 1 only eps below the tolerance, 2 not computable. */
+int orc_debug_rdmp(const OrcState *S, long c, double rho_new, double *lo, double *hi) {
+    const OrcMesh *M = S->M;
+    if (c < 0 || c >= M->nc) return -1;
+    Work w = work_new(M);
+    phase_geometry(S, S->x, &w);
+    double l, h;
+    rdmp_range(S, w.V, c, &l, &h);
+    int ok = rdmp_admits(S, rho_new, l, h);
+    if (lo) *lo = l;
+    if (hi) *hi = h;
+    work_free(&w);
+    return ok;
+}
+
+int orc_debug_pad(const OrcState *S, long c, const double *v, double e, const double *F, double V) {
+    if (c < 0 || c >= S->M->nc) return -1;
+    return pad_state(S->M->d, v, e, F, V, a0sq_of(S, c));
 }
 
 /* Mesh queries used by tests (stencil and BC resolution). */
