@@ -16,18 +16,30 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lmood_oracle.c")
 _LIB = os.path.join(_HERE, "liblmood_oracle.so")
+_TSRC = os.path.join(_HERE, "lmood_tangent.cpp")
+_TLIB = os.path.join(_HERE, "liblmood_tangent.so")
 
 F_X, F_VP, F_VSTAR, F_V, F_E, F_F, F_TAU, F_ORDER, F_MASS, F_PKM, F_PKR = range(11)
 ERR = {0: "ok", 1: "bad argument", 2: "bad mesh", 5: "parachute failure", 6: "MOOD iteration limit"}
 
 
+def _stale(lib: str, *srcs: str) -> bool:
+    return not os.path.exists(lib) or any(os.path.getmtime(lib) < os.path.getmtime(f) for f in srcs)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with plain gcc (-O2, no FP contraction, OpenMP)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile the oracle with plain gcc (-O2, no FP contraction, OpenMP), and its tangent
+    build (the same source as C++ with dual numbers, lmood_tangent.cpp) with g++."""
+    if force or _stale(_LIB, _SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+    if force or _stale(_TLIB, _SRC, _TSRC):
+        tmp = _TLIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                               "-o", tmp, _TSRC, "-lm"], cwd=_HERE)
+        os.replace(tmp, _TLIB)
     return _LIB
 
 
@@ -302,3 +314,53 @@ class Oracle:
     def state(self) -> dict:
         return {"x": self.get(F_X), "vp": self.get(F_VP), "v": self.get(F_V), "e": self.get(F_E),
                 "F": self.get(F_F), "tau": self.get(F_TAU)}
+
+
+# ----------------------------------------------------------------------------- tangent build
+_tlib = None
+
+
+def tangent_lib():
+    global _tlib
+    if _tlib is None:
+        build()
+        _tlib = C.CDLL(_TLIB)
+        vp = C.c_void_p
+        _tlib.orct_run.argtypes = [C.c_int, C.c_long, vp, C.c_long, vp, C.c_long, vp, vp, C.c_double, C.c_double,
+                                   vp, vp, vp, vp, vp, vp, C.POINTER(Params), C.c_long] + [vp] * 10
+        _tlib.orct_run.restype = C.c_int
+    return _tlib
+
+
+def tangent(problem, n_steps: int, dv=None, dmu=None, dF=None, params: Params | None = None, **kw) -> dict:
+    """The oracle's n-step map and its directional derivative (forward mode, dual numbers):
+    the final state x, vp [d][np], v [d][nc], F [d*d][nc] and their derivatives dx, dvp, dv,
+    dF along the direction (dv [d][nc], dmu [nc], dF [d*d][nc]; None = 0) of the initial data,
+    with each step's order mask and dt held at the run's own (masks [n][nc] int8, dts [n])."""
+    m = problem.mesh
+    d, nc, npn = m.dim, m.n_cells, m.n_nodes
+    prm = params or default_params(problem.cfl, **kw)
+    keep = []
+
+    def arr(a, dtype=np.float64):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=dtype)
+        keep.append(a)
+        return a.ctypes.data
+
+    out = {k: np.zeros(shape) for k, shape in (("x", (d, npn)), ("dx", (d, npn)), ("vp", (d, npn)),
+                                                ("dvp", (d, npn)), ("v", (d, nc)), ("dv", (d, nc)),
+                                                ("F", (d * d, nc)), ("dF", (d * d, nc)))}
+    out["masks"] = np.zeros((n_steps, nc), np.int8)
+    out["dts"] = np.zeros(n_steps)
+    nb = m.btag.size
+    rc = tangent_lib().orct_run(d, npn, arr(m.x), nc, arr(m.c2n, np.int32), nb,
+                                arr(m.bface, np.int32) if nb else None, arr(m.btag, np.int32) if nb else None,
+                                problem.rho0, problem.lam, arr(problem.mu), arr(dmu), arr(problem.v), arr(dv),
+                                arr(problem.F), arr(dF), C.byref(prm), n_steps,
+                                *(out[k].ctypes.data for k in ("x", "dx", "vp", "dvp", "v", "dv", "F", "dF")),
+                                out["masks"].ctypes.data, out["dts"].ctypes.data)
+    if rc:
+        raise OracleError(f"orct_run: {ERR.get(rc, rc)}")
+    return out

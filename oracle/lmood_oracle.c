@@ -102,6 +102,19 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* The scalar type of every quantity the scheme computes. This file is the oracle as a plain C
+ * program with real = double. The tangent build (lmood_tangent.cpp) compiles the same file as
+ * C++ with real a dual number (a value and a directional derivative), so that the oracle's own
+ * step also gives the exact derivative of its map: the CPU reference for the library's
+ * adjoint. The parameters of the scheme (OrcParams) stay double. */
+#ifndef ORC_REAL_DEFINED
+typedef double real;
+#endif
+
+/* typed allocations (valid C and C++) */
+#define ORC_NEW(T, n) ((T *)malloc(sizeof(T) * (size_t)(n)))
+#define ORC_ZNEW(T, n) ((T *)calloc((size_t)(n), sizeof(T)))
+
 #define MAXD 3
 #define MAXV 4
 
@@ -120,10 +133,10 @@ typedef struct {
 } OrcParams;
 
 typedef struct {
-    double t, dt_used, dt_next;
+    real t, dt_used, dt_next;
     long step;
     int n_troubled, n_p0, mood_iters, n_parachute, n_p0_eps, n_lim;
-    double mass, mom[3], energy;
+    real mass, mom[3], energy;
 } OrcInfo;
 
 typedef struct {
@@ -135,51 +148,51 @@ typedef struct {
     int *n2c_k;            /* local vertex index of the node in that cell             */
     long *st_off, *st_idx; /* reconstruction stencil V_c                              */
     int *bc_ndof;          /* per node: number of free velocity directions (d = free) */
-    double *bc_t;          /* per node: [2][3] tangent vectors spanning the free space */
-    double *x0;            /* [np][d] initial positions                                */
+    real *bc_t;          /* per node: [2][3] tangent vectors spanning the free space */
+    real *x0;            /* [np][d] initial positions                                */
     long nb;               /* boundary faces                                          */
     int *bf_nodes;         /* [nb][d] face nodes, ordered so that the face's area vector
                               points out of the mesh (reading R15)                     */
     int *bf_tag;           /* [nb] 0 free, 1 slip, 2 clamped, 3 traction, 4 pressure,
                               5 prescribed velocity, 6 contact (free until it touches a
                               contact wall)                                             */
-    double *bf_val;        /* [nb][d] traction vector / pressure (first entry) /
+    real *bf_val;        /* [nb][d] traction vector / pressure (first entry) /
                               prescribed velocity vector; zero until set               */
     long *nbf_off, *nbf_idx; /* boundary faces around each node, ascending face id     */
     int n_contact;         /* contact walls for faces tagged 6 (reading R17)          */
-    double contact[4][6];  /* point, unit normal from the wall into the body          */
-    double contact_eps;    /* distance threshold                                      */
+    real contact[4][6];  /* point, unit normal from the wall into the body          */
+    real contact_eps;    /* distance threshold                                      */
 } OrcMesh;
 
 typedef struct {
     OrcMesh *M;
     OrcParams prm;
-    double rho0, lam;
-    double *mu;                   /* [nc]                                         */
-    double *m;                    /* [nc] constant cell masses                    */
-    double *x, *vp;               /* [np][d] positions and v_p^n                  */
-    double *v, *e, *F, *tau;      /* [nc][d], [nc], [nc][d*d], [nc]               */
-    double t, dt;
+    real rho0, lam;
+    real *mu;                   /* [nc]                                         */
+    real *m;                    /* [nc] constant cell masses                    */
+    real *x, *vp;               /* [np][d] positions and v_p^n                  */
+    real *v, *e, *F, *tau;      /* [nc][d], [nc], [nc][d*d], [nc]               */
+    real t, dt;
     long step;
     /* last accepted step's intermediates (for kernel-level parity) */
     int *order;                   /* [nc] 1 or 2                                  */
-    double *pkM, *pkR;            /* [nc][nv][d*d], [nc][nv][d]                   */
-    double *vstar;                /* [np][d]                                      */
+    real *pkM, *pkR;            /* [nc][nv][d*d], [nc][nv][d]                   */
+    real *vstar;                /* [np][d]                                      */
     OrcInfo last;
 } OrcState;
 
 /* --------------------------------------------------------------------------------------
  * small dense algebra
  * ------------------------------------------------------------------------------------ */
-static double det_n(int d, const double *A) {
+static real det_n(int d, const real *A) {
     if (d == 2) return A[0] * A[3] - A[1] * A[2];
     return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
            A[2] * (A[3] * A[7] - A[4] * A[6]);
 }
 
 /* inverse by adjugate / determinant; returns the determinant */
-static double inv_n(int d, const double *A, double *Ai) {
-    double det = det_n(d, A);
+static real inv_n(int d, const real *A, real *Ai) {
+    real det = det_n(d, A);
     if (d == 2) {
         Ai[0] = A[3] / det; Ai[1] = -A[1] / det;
         Ai[2] = -A[2] / det; Ai[3] = A[0] / det;
@@ -197,18 +210,18 @@ static double inv_n(int d, const double *A, double *Ai) {
     return det;
 }
 
-static void matmul_n(int d, const double *A, const double *B, double *C) {
+static void matmul_n(int d, const real *A, const real *B, real *C) {
     for (int i = 0; i < d; ++i)
         for (int j = 0; j < d; ++j) {
-            double s = 0.0;
+            real s = 0.0;
             for (int k = 0; k < d; ++k) s += A[i * d + k] * B[k * d + j];
             C[i * d + j] = s;
         }
 }
 
-static void matvec_n(int d, const double *A, const double *x, double *y) {
+static void matvec_n(int d, const real *A, const real *x, real *y) {
     for (int i = 0; i < d; ++i) {
-        double s = 0.0;
+        real s = 0.0;
         for (int k = 0; k < d; ++k) s += A[i * d + k] * x[k];
         y[i] = s;
     }
@@ -224,16 +237,16 @@ static void matvec_n(int d, const double *A, const double *x, double *y) {
  *              with l_cpf n_cpf = N_f / d (each face is split evenly among its d vertices)
  *   Lc         in-sphere diameter 2 d |w_c| / sum_f |N_f|
  * ------------------------------------------------------------------------------------ */
-void orc_cell_geometry(int d, const double *xs, double *V, double *xc, double *N, double *ln, double *Lc) {
+void orc_cell_geometry(int d, const real *xs, real *V, real *xc, real *N, real *ln, real *Lc) {
     int nv = d + 1;
     for (int a = 0; a < d; ++a) {
-        double s = 0.0;
+        real s = 0.0;
         for (int k = 0; k < nv; ++k) s += xs[k * d + a];
         xc[a] = s / nv;
     }
     if (d == 2) {
-        double e1x = xs[2] - xs[0], e1y = xs[3] - xs[1];
-        double e2x = xs[4] - xs[0], e2y = xs[5] - xs[1];
+        real e1x = xs[2] - xs[0], e1y = xs[3] - xs[1];
+        real e2x = xs[4] - xs[0], e2y = xs[5] - xs[1];
         *V = 0.5 * (e1x * e2y - e1y * e2x);
         for (int k = 0; k < 3; ++k) {
             /* face opposite k is the edge a -> b traversed counter-clockwise */
@@ -242,17 +255,17 @@ void orc_cell_geometry(int d, const double *xs, double *V, double *xc, double *N
             N[k * 2 + 1] = xs[a * 2 + 0] - xs[b * 2 + 0];
         }
     } else {
-        double e[3][3];
+        real e[3][3];
         for (int k = 0; k < 3; ++k)
             for (int a = 0; a < 3; ++a) e[k][a] = xs[(k + 1) * 3 + a] - xs[a];
-        double cr[3] = {e[1][1] * e[2][2] - e[1][2] * e[2][1], e[1][2] * e[2][0] - e[1][0] * e[2][2],
+        real cr[3] = {e[1][1] * e[2][2] - e[1][2] * e[2][1], e[1][2] * e[2][0] - e[1][0] * e[2][2],
                         e[1][0] * e[2][1] - e[1][1] * e[2][0]};
         *V = (e[0][0] * cr[0] + e[0][1] * cr[1] + e[0][2] * cr[2]) / 6.0;
         for (int k = 0; k < 4; ++k) {
             int f[3], q = 0;
             for (int j = 0; j < 4; ++j)
                 if (j != k) f[q++] = j;
-            double u[3], w[3], n[3];
+            real u[3], w[3], n[3];
             for (int a = 0; a < 3; ++a) {
                 u[a] = xs[f[1] * 3 + a] - xs[f[0] * 3 + a];
                 w[a] = xs[f[2] * 3 + a] - xs[f[0] * 3 + a];
@@ -261,23 +274,23 @@ void orc_cell_geometry(int d, const double *xs, double *V, double *xc, double *N
             n[1] = 0.5 * (u[2] * w[0] - u[0] * w[2]);
             n[2] = 0.5 * (u[0] * w[1] - u[1] * w[0]);
             /* outward: away from the opposite vertex k */
-            double s = 0.0;
+            real s = 0.0;
             for (int a = 0; a < 3; ++a) s += n[a] * (xs[k * 3 + a] - xs[f[0] * 3 + a]);
             if (s > 0)
                 for (int a = 0; a < 3; ++a) n[a] = -n[a];
             for (int a = 0; a < 3; ++a) N[k * 3 + a] = n[a];
         }
     }
-    double area = 0.0;
+    real area = 0.0;
     for (int k = 0; k < nv; ++k) {
-        double s = 0.0;
+        real s = 0.0;
         for (int a = 0; a < d; ++a) s += N[k * d + a] * N[k * d + a];
         area += sqrt(s);
     }
     *Lc = 2.0 * d * (*V) / area;
     for (int p = 0; p < nv; ++p)
         for (int a = 0; a < d; ++a) {
-            double s = 0.0;
+            real s = 0.0;
             for (int f = 0; f < nv; ++f)
                 if (f != p) s += N[f * d + a] / d;
             ln[p * d + a] = s;
@@ -291,9 +304,9 @@ void orc_cell_geometry(int d, const double *xs, double *V, double *xc, double *N
  *   T_0 = (mu / J) dev(Bbar),  Bbar = J^{-2/3} F F^t     (Eq. cstnh)
  * 2D is plane strain: F is embedded as diag(F, 1) and the in-plane block of T returned.
  * ------------------------------------------------------------------------------------ */
-static void embed3(int d, const double *F, double *F3) {
+static void embed3(int d, const real *F, real *F3) {
     if (d == 3) {
-        memcpy(F3, F, 9 * sizeof(double));
+        memcpy(F3, F, 9 * sizeof(real));
         return;
     }
     F3[0] = F[0]; F3[1] = F[1]; F3[2] = 0.0;
@@ -301,22 +314,22 @@ static void embed3(int d, const double *F, double *F3) {
     F3[6] = 0.0;  F3[7] = 0.0;  F3[8] = 1.0;
 }
 
-void orc_stress(int d, const double *F, double mu, double kappa, double *T) {
-    double F3[9], B[9], T3[9];
+void orc_stress(int d, const real *F, real mu, real kappa, real *T) {
+    real F3[9], B[9], T3[9];
     embed3(d, F, F3);
-    double J = det_n(3, F3);
+    real J = det_n(3, F3);
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
+            real s = 0.0;
             for (int k = 0; k < 3; ++k) s += F3[i * 3 + k] * F3[j * 3 + k];
             B[i * 3 + j] = s;
         }
-    double Jm23 = pow(J, -2.0 / 3.0);
-    double trBbar = Jm23 * (B[0] + B[4] + B[8]);
-    double p = -0.5 * kappa * (J - 1.0 + log(J) / J);
+    real Jm23 = pow(J, -2.0 / 3.0);
+    real trBbar = Jm23 * (B[0] + B[4] + B[8]);
+    real p = -0.5 * kappa * (J - 1.0 + log(J) / J);
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            double Bbar0 = Jm23 * B[i * 3 + j] - (i == j ? trBbar / 3.0 : 0.0);
+            real Bbar0 = Jm23 * B[i * 3 + j] - (i == j ? trBbar / 3.0 : 0.0);
             T3[i * 3 + j] = (i == j ? -p : 0.0) + mu / J * Bbar0;
         }
     for (int i = 0; i < d; ++i)
@@ -329,34 +342,34 @@ void orc_stress(int d, const double *F, double mu, double kappa, double *T) {
  * T = -p I + (2/J) dev((W_1 + I1 W_2) Bbar - W_2 Bbar^2), W_1 = -a mu/2, W_2 = (1+a) mu I2/6,
  * i.e. T = -p I + (mu/J) dev(c1 Bbar - c2 Bbar^2), c1 = -a + (1+a) I1 I2/3, c2 = (1+a) I2/3.
  * a = -1 is the neo-Hookean law of orc_stress. 2D is plane strain (F33 = 1). */
-void orc_stress_a(int d, const double *F, double mu, double kappa, double a, double *T) {
+void orc_stress_a(int d, const real *F, real mu, real kappa, real a, real *T) {
     if (a == -1.0) {
         orc_stress(d, F, mu, kappa, T);
         return;
     }
-    double F3[9], B[9], B2[9], T3[9];
+    real F3[9], B[9], B2[9], T3[9];
     embed3(d, F, F3);
-    double J = det_n(3, F3);
-    double Jm23 = pow(J, -2.0 / 3.0);
+    real J = det_n(3, F3);
+    real Jm23 = pow(J, -2.0 / 3.0);
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
+            real s = 0.0;
             for (int k = 0; k < 3; ++k) s += F3[i * 3 + k] * F3[j * 3 + k];
             B[i * 3 + j] = Jm23 * s;
         }
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
+            real s = 0.0;
             for (int k = 0; k < 3; ++k) s += B[i * 3 + k] * B[k * 3 + j];
             B2[i * 3 + j] = s;
         }
-    double I1 = B[0] + B[4] + B[8], trB2 = B2[0] + B2[4] + B2[8];
-    double I2 = 0.5 * (I1 * I1 - trB2);
-    double c1 = -a + (1.0 + a) * I1 * I2 / 3.0, c2 = (1.0 + a) * I2 / 3.0;
-    double X[9], trX = 0.0;
+    real I1 = B[0] + B[4] + B[8], trB2 = B2[0] + B2[4] + B2[8];
+    real I2 = 0.5 * (I1 * I1 - trB2);
+    real c1 = -a + (1.0 + a) * I1 * I2 / 3.0, c2 = (1.0 + a) * I2 / 3.0;
+    real X[9], trX = 0.0;
     for (int i = 0; i < 9; ++i) X[i] = c1 * B[i] - c2 * B2[i];
     trX = X[0] + X[4] + X[8];
-    double p = -0.5 * kappa * (J - 1.0 + log(J) / J);
+    real p = -0.5 * kappa * (J - 1.0 + log(J) / J);
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
             T3[i * 3 + j] = (i == j ? -p : 0.0) + mu / J * (X[i * 3 + j] - (i == j ? trX / 3.0 : 0.0));
@@ -366,91 +379,91 @@ void orc_stress_a(int d, const double *F, double mu, double kappa, double a, dou
 
 /* specific free energy Psi = Psi_v + Psi_s (Eqs. EOS_neoHook and familiy_energies with
  * a = -1): Psi_v = kappa/(4 rho0) ((J-1)^2 + log^2 J), Psi_s = mu/(2 rho0) (I1(Bbar) - 3) */
-double orc_free_energy(int d, const double *F, double rho0, double mu, double kappa) {
-    double F3[9];
+real orc_free_energy(int d, const real *F, real rho0, real mu, real kappa) {
+    real F3[9];
     embed3(d, F, F3);
-    double J = det_n(3, F3);
-    double trB = 0.0;
+    real J = det_n(3, F3);
+    real trB = 0.0;
     for (int i = 0; i < 9; ++i) trB += F3[i] * F3[i];
-    double I1bar = pow(J, -2.0 / 3.0) * trB;
-    double lj = log(J);
+    real I1bar = pow(J, -2.0 / 3.0) * trB;
+    real lj = log(J);
     return kappa / (4.0 * rho0) * ((J - 1.0) * (J - 1.0) + lj * lj) + mu / (2.0 * rho0) * (I1bar - 3.0);
 }
 
 /* the same with the shear energy of Eq. familiy_energies for any a (reading R16) */
-double orc_free_energy_a(int d, const double *F, double rho0, double mu, double kappa, double a) {
+real orc_free_energy_a(int d, const real *F, real rho0, real mu, real kappa, real a) {
     if (a == -1.0) return orc_free_energy(d, F, rho0, mu, kappa);
-    double F3[9], B[9];
+    real F3[9], B[9];
     embed3(d, F, F3);
-    double J = det_n(3, F3);
-    double Jm23 = pow(J, -2.0 / 3.0);
+    real J = det_n(3, F3);
+    real Jm23 = pow(J, -2.0 / 3.0);
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
+            real s = 0.0;
             for (int k = 0; k < 3; ++k) s += F3[i * 3 + k] * F3[j * 3 + k];
             B[i * 3 + j] = Jm23 * s;
         }
-    double I1 = B[0] + B[4] + B[8], trB2 = 0.0;
+    real I1 = B[0] + B[4] + B[8], trB2 = 0.0;
     for (int i = 0; i < 9; ++i) trB2 += B[i] * B[i];  /* B symmetric: tr(B^2) = sum B_ij^2 */
-    double I2 = 0.5 * (I1 * I1 - trB2);
-    double lj = log(J);
+    real I2 = 0.5 * (I1 * I1 - trB2);
+    real lj = log(J);
     return kappa / (4.0 * rho0) * ((J - 1.0) * (J - 1.0) + lj * lj) +
            mu / (4.0 * rho0) * (-2.0 * a * (I1 - 3.0) + (1.0 + a) / 3.0 * (I2 * I2 - 9.0));
 }
 
 /* sound speed, reading R4: a^2 = (K + 4 mu / (3 J)) / rho, K = (kappa/2)(J + (1 - log J)/J) */
-double orc_sound_speed(int d, const double *F, double rho, double mu, double kappa) {
-    double F3[9];
+real orc_sound_speed(int d, const real *F, real rho, real mu, real kappa) {
+    real F3[9];
     embed3(d, F, F3);
-    double J = det_n(3, F3);
-    double K = 0.5 * kappa * (J + (1.0 - log(J)) / J);
+    real J = det_n(3, F3);
+    real K = 0.5 * kappa * (J + (1.0 - log(J)) / J);
     return sqrt((K + 4.0 * mu / (3.0 * J)) / rho);
 }
 
-static double kappa_of(const OrcState *S, long c) {
+static real kappa_of(const OrcState *S, long c) {
     return S->prm.vol_coeff == 1 ? S->mu[c] : S->lam + 2.0 * S->mu[c] / 3.0;
 }
 
 /* stiffened gas (Eq. EOS_stiffened_gas; reading R18): p = (gamma - 1) rho eps_v - gamma p_inf
  * with rho = rho0 / det F and eps_v = eps - Psi_s(F) the volumetric part of the specific
  * internal energy eps = e - |v|^2/2 (Psi_s the shear energy of Eq. familiy_energies) */
-static double sg_pressure(const OrcState *S, long c, const double *F, double eps) {
+static real sg_pressure(const OrcState *S, long c, const real *F, real eps) {
     int d = S->M->d;
-    double F3[9];
+    real F3[9];
     embed3(d, F, F3);
-    double J = det_n(3, F3);
-    double eps_s = orc_free_energy_a(d, F, S->rho0, S->mu[c], 0.0, S->prm.shear_a);
+    real J = det_n(3, F3);
+    real eps_s = orc_free_energy_a(d, F, S->rho0, S->mu[c], 0.0, S->prm.shear_a);
     return (S->prm.gamma - 1.0) * (S->rho0 / J) * (eps - eps_s) - S->prm.gamma * S->prm.p_inf;
 }
 
 /* the material's Cauchy stress at F with specific internal energy eps (used by the stiffened
  * gas only): Eqs. EOS_neoHook + familiy_energies, or the stiffened-gas pressure plus the
  * family's shear stress */
-static void stress_state(const OrcState *S, long c, const double *F, double eps, double *T) {
+static void stress_state(const OrcState *S, long c, const real *F, real eps, real *T) {
     int d = S->M->d;
     if (S->prm.eos == 0) {
         orc_stress_a(d, F, S->mu[c], kappa_of(S, c), S->prm.shear_a, T);
         return;
     }
     orc_stress_a(d, F, S->mu[c], 0.0, S->prm.shear_a, T);  /* shear part (no volumetric term) */
-    double p = sg_pressure(S, c, F, eps);
+    real p = sg_pressure(S, c, F, eps);
     for (int i = 0; i < d; ++i) T[i * d + i] -= p;
 }
 
 /* sound speed of the material (readings R4, R18): stiffened gas a^2 = (gamma (p + p_inf) +
  * 4 mu / (3 J)) / rho */
-static double sound_speed_state(const OrcState *S, long c, const double *F, double rho, double eps) {
+static real sound_speed_state(const OrcState *S, long c, const real *F, real rho, real eps) {
     int d = S->M->d;
     if (S->prm.eos == 0) return orc_sound_speed(d, F, rho, S->mu[c], kappa_of(S, c));
-    double F3[9];
+    real F3[9];
     embed3(d, F, F3);
-    double J = det_n(3, F3);
-    double p = sg_pressure(S, c, F, eps);
+    real J = det_n(3, F3);
+    real p = sg_pressure(S, c, F, eps);
     return sqrt((S->prm.gamma * (p + S->prm.p_inf) + 4.0 / 3.0 * S->mu[c] / J) / rho);
 }
 
 /* the material's energy scale at rest (PAD tolerance, reading R12): the squared P-wave speed */
-static double a0sq_of(const OrcState *S, long c) {
+static real a0sq_of(const OrcState *S, long c) {
     if (S->prm.eos == 0) return (kappa_of(S, c) + 4.0 / 3.0 * S->mu[c]) / S->rho0;
     return (S->prm.gamma * (S->prm.p0 + S->prm.p_inf) + 4.0 / 3.0 * S->mu[c]) / S->rho0;
 }
@@ -488,14 +501,14 @@ void orc_mesh_free(OrcMesh *M) {
 
 /* area vector of boundary face b at positions x ([np][d]): 2D edge (q0, q1):
  * (y1 - y0, x0 - x1); 3D triangle: (1/2) (x1 - x0) x (x2 - x0); its length is the face measure */
-static void face_area_vector(const OrcMesh *M, const double *x, long b, double *N) {
+static void face_area_vector(const OrcMesh *M, const real *x, long b, real *N) {
     int d = M->d;
     const int *q = M->bf_nodes + b * d;
     if (d == 2) {
         N[0] = x[q[1] * 2 + 1] - x[q[0] * 2 + 1];
         N[1] = x[q[0] * 2 + 0] - x[q[1] * 2 + 0];
     } else {
-        double u[3], w[3];
+        real u[3], w[3];
         for (int a = 0; a < 3; ++a) {
             u[a] = x[q[1] * 3 + a] - x[q[0] * 3 + a];
             w[a] = x[q[2] * 3 + a] - x[q[0] * 3 + a];
@@ -512,15 +525,15 @@ static void face_area_vector(const OrcMesh *M, const double *x, long b, double *
 static void resolve_bcs(OrcMesh *M) {
     int d = M->d;
     long np = M->np, nb = M->nb;
-    int *clamped = calloc(np, sizeof(int));
-    int *nplanes = calloc(np, sizeof(int));
-    double *planes = calloc(np * 9, sizeof(double));
-    memset(M->bc_t, 0, sizeof(double) * np * 6);
+    int *clamped = ORC_ZNEW(int, np);
+    int *nplanes = ORC_ZNEW(int, np);
+    real *planes = ORC_ZNEW(real, np * 9);
+    memset(M->bc_t, 0, sizeof(real) * np * 6);
     for (long b = 0; b < nb; ++b) {
         const int *fn = M->bf_nodes + b * d;
-        double n[3] = {0, 0, 0};
+        real n[3] = {0, 0, 0};
         face_area_vector(M, M->x0, b, n);
-        double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        real nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
         for (int a = 0; a < 3; ++a) n[a] /= nn;
         for (int a = 0; a < d; ++a) {
             int p = fn[a];
@@ -528,7 +541,7 @@ static void resolve_bcs(OrcMesh *M) {
             if (M->bf_tag[b] == 1) {
                 int dup = 0;
                 for (int q = 0; q < nplanes[p]; ++q) {
-                    double dot = 0.0;
+                    real dot = 0.0;
                     for (int i = 0; i < 3; ++i) dot += planes[p * 9 + q * 3 + i] * n[i];
                     if (fabs(dot) > 1.0 - 1e-12) dup = 1;
                 }
@@ -540,8 +553,8 @@ static void resolve_bcs(OrcMesh *M) {
         }
     }
     for (long p = 0; p < np; ++p) {
-        double *t = M->bc_t + p * 6;
-        const double *n1 = planes + p * 9, *n2 = planes + p * 9 + 3;
+        real *t = M->bc_t + p * 6;
+        const real *n1 = planes + p * 9, *n2 = planes + p * 9 + 3;
         int k = clamped[p] ? d : nplanes[p];
         if (k >= d) {
             M->bc_ndof[p] = 0;
@@ -555,18 +568,18 @@ static void resolve_bcs(OrcMesh *M) {
             int ax = 0;
             for (int a = 1; a < 3; ++a)
                 if (fabs(n1[a]) < fabs(n1[ax])) ax = a;
-            double e[3] = {0, 0, 0};
+            real e[3] = {0, 0, 0};
             e[ax] = 1.0;
-            double t1[3] = {e[1] * n1[2] - e[2] * n1[1], e[2] * n1[0] - e[0] * n1[2], e[0] * n1[1] - e[1] * n1[0]};
-            double l1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+            real t1[3] = {e[1] * n1[2] - e[2] * n1[1], e[2] * n1[0] - e[0] * n1[2], e[0] * n1[1] - e[1] * n1[0]};
+            real l1 = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
             for (int a = 0; a < 3; ++a) t1[a] /= l1;
-            double t2[3] = {n1[1] * t1[2] - n1[2] * t1[1], n1[2] * t1[0] - n1[0] * t1[2], n1[0] * t1[1] - n1[1] * t1[0]};
-            double l2 = sqrt(t2[0] * t2[0] + t2[1] * t2[1] + t2[2] * t2[2]);
+            real t2[3] = {n1[1] * t1[2] - n1[2] * t1[1], n1[2] * t1[0] - n1[0] * t1[2], n1[0] * t1[1] - n1[1] * t1[0]};
+            real l2 = sqrt(t2[0] * t2[0] + t2[1] * t2[1] + t2[2] * t2[2]);
             for (int a = 0; a < 3; ++a) { t[a] = t1[a]; t[3 + a] = t2[a] / l2; }
             M->bc_ndof[p] = 2;
         } else {
-            double l[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2], n1[0] * n2[1] - n1[1] * n2[0]};
-            double ll = sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+            real l[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2], n1[0] * n2[1] - n1[1] * n2[0]};
+            real ll = sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
             for (int a = 0; a < 3; ++a) t[a] = l[a] / ll;
             M->bc_ndof[p] = 1;
         }
@@ -575,14 +588,14 @@ static void resolve_bcs(OrcMesh *M) {
 }
 
 /* x_soa [d][np], c2n_soa [d+1][nc], bf_soa [d][nb], btag [nb] (0 free, 1 slip, 2 clamped) */
-int orc_mesh_new(int d, long np, const double *x_soa, long nc, const int *c2n_soa, long nb,
+int orc_mesh_new(int d, long np, const real *x_soa, long nc, const int *c2n_soa, long nb,
                  const int *bf_soa, const int *btag, OrcMesh **out) {
     if ((d != 2 && d != 3) || np <= 0 || nc <= 0 || !out) return ORC_ERR_ARG;
-    OrcMesh *M = calloc(1, sizeof(OrcMesh));
+    OrcMesh *M = ORC_ZNEW(OrcMesh, 1);
     int nv = d + 1;
     M->d = d; M->nv = nv; M->np = np; M->nc = nc;
-    M->c2n = malloc(sizeof(int) * nc * nv);
-    M->x0 = malloc(sizeof(double) * np * d);
+    M->c2n = ORC_NEW(int, nc * nv);
+    M->x0 = ORC_NEW(real, np * d);
     for (long p = 0; p < np; ++p)
         for (int a = 0; a < d; ++a) M->x0[p * d + a] = x_soa[a * np + p];
     for (long c = 0; c < nc; ++c)
@@ -593,20 +606,20 @@ int orc_mesh_new(int d, long np, const double *x_soa, long nc, const int *c2n_so
         }
     /* positive orientation */
     for (long c = 0; c < nc; ++c) {
-        double xs[MAXV * MAXD], V, xc[MAXD], N[MAXV * MAXD], ln[MAXV * MAXD], Lc;
+        real xs[MAXV * MAXD], V, xc[MAXD], N[MAXV * MAXD], ln[MAXV * MAXD], Lc;
         for (int k = 0; k < nv; ++k)
             for (int a = 0; a < d; ++a) xs[k * d + a] = M->x0[M->c2n[c * nv + k] * d + a];
         orc_cell_geometry(d, xs, &V, xc, N, ln, &Lc);
         if (!(V > 0)) { orc_mesh_free(M); return ORC_ERR_MESH; }
     }
     /* C(p): corners around each node, ascending cell id */
-    M->n2c_off = calloc(np + 1, sizeof(long));
+    M->n2c_off = ORC_ZNEW(long, np + 1);
     for (long c = 0; c < nc; ++c)
         for (int k = 0; k < nv; ++k) M->n2c_off[M->c2n[c * nv + k] + 1]++;
     for (long p = 0; p < np; ++p) M->n2c_off[p + 1] += M->n2c_off[p];
-    M->n2c_cell = malloc(sizeof(long) * nc * nv);
-    M->n2c_k = malloc(sizeof(int) * nc * nv);
-    long *fill = malloc(sizeof(long) * np);
+    M->n2c_cell = ORC_NEW(long, nc * nv);
+    M->n2c_k = ORC_NEW(int, nc * nv);
+    long *fill = ORC_NEW(long, np);
     for (long p = 0; p < np; ++p) fill[p] = M->n2c_off[p];
     for (long c = 0; c < nc; ++c)
         for (int k = 0; k < nv; ++k) {
@@ -618,19 +631,19 @@ int orc_mesh_new(int d, long np, const double *x_soa, long nc, const int *c2n_so
     free(fill);
     /* stencil V_c (reading R9): every other cell sharing at least one node with c,
      * ascending cell id (two passes: sizes, then entries; cells are independent) */
-    M->st_off = calloc(nc + 1, sizeof(long));
+    M->st_off = ORC_ZNEW(long, nc + 1);
 #pragma omp parallel
     {
-        long *tmp = malloc(sizeof(long) * 8192);
+        long *tmp = ORC_NEW(long, 8192);
 #pragma omp for schedule(static)
         for (long c = 0; c < nc; ++c) M->st_off[c + 1] = stencil_of(M, c, tmp);
         free(tmp);
     }
     for (long c = 0; c < nc; ++c) M->st_off[c + 1] += M->st_off[c];
-    M->st_idx = malloc(sizeof(long) * (M->st_off[nc] > 0 ? M->st_off[nc] : 1));
+    M->st_idx = ORC_NEW(long, (M->st_off[nc] > 0 ? M->st_off[nc] : 1));
 #pragma omp parallel
     {
-        long *tmp = malloc(sizeof(long) * 8192);
+        long *tmp = ORC_NEW(long, 8192);
 #pragma omp for schedule(static)
         for (long c = 0; c < nc; ++c) {
             int u = stencil_of(M, c, tmp);
@@ -641,9 +654,9 @@ int orc_mesh_new(int d, long np, const double *x_soa, long nc, const int *c2n_so
     /* boundary faces: nodes oriented outward (the face's area vector points away from the
      * vertex of its cell that is not on the face), tags, values, node -> face CSR */
     M->nb = nb;
-    M->bf_nodes = malloc(sizeof(int) * (nb > 0 ? nb : 1) * d);
-    M->bf_tag = malloc(sizeof(int) * (nb > 0 ? nb : 1));
-    M->bf_val = calloc((nb > 0 ? nb : 1) * d, sizeof(double));
+    M->bf_nodes = ORC_NEW(int, (nb > 0 ? nb : 1) * d);
+    M->bf_tag = ORC_NEW(int, (nb > 0 ? nb : 1));
+    M->bf_val = ORC_ZNEW(real, (nb > 0 ? nb : 1) * d);
     for (long b = 0; b < nb; ++b) {
         int *fn = M->bf_nodes + b * d;
         for (int a = 0; a < d; ++a) {
@@ -666,33 +679,33 @@ int orc_mesh_new(int d, long np, const double *x_soa, long nc, const int *c2n_so
             if (hits == d) { owner = c; opp = other; }
         }
         if (owner < 0) { orc_mesh_free(M); return ORC_ERR_MESH; }
-        double N[3] = {0, 0, 0}, dot = 0.0;
+        real N[3] = {0, 0, 0}, dot = 0.0;
         face_area_vector(M, M->x0, b, N);
         for (int a = 0; a < d; ++a) {
-            double xf = 0.0;
+            real xf = 0.0;
             for (int i = 0; i < d; ++i) xf += M->x0[fn[i] * d + a];
             dot += N[a] * (xf / d - M->x0[opp * d + a]);
         }
         if (dot < 0.0) { int tmp = fn[0]; fn[0] = fn[1]; fn[1] = tmp; }
-        double nn = 0.0;
+        real nn = 0.0;
         face_area_vector(M, M->x0, b, N);
         for (int a = 0; a < d; ++a) nn += N[a] * N[a];
         if (!(nn > 0.0)) { orc_mesh_free(M); return ORC_ERR_MESH; }
     }
-    M->nbf_off = calloc(np + 1, sizeof(long));
+    M->nbf_off = ORC_ZNEW(long, np + 1);
     for (long b = 0; b < nb; ++b)
         for (int a = 0; a < d; ++a) M->nbf_off[M->bf_nodes[b * d + a] + 1]++;
     for (long p = 0; p < np; ++p) M->nbf_off[p + 1] += M->nbf_off[p];
-    M->nbf_idx = malloc(sizeof(long) * (nb > 0 ? nb * d : 1));
+    M->nbf_idx = ORC_NEW(long, (nb > 0 ? nb * d : 1));
     {
-        long *fill = malloc(sizeof(long) * np);
+        long *fill = ORC_NEW(long, np);
         for (long p = 0; p < np; ++p) fill[p] = M->nbf_off[p];
         for (long b = 0; b < nb; ++b)
             for (int a = 0; a < d; ++a) M->nbf_idx[fill[M->bf_nodes[b * d + a]]++] = b;
         free(fill);
     }
-    M->bc_ndof = malloc(sizeof(int) * np);
-    M->bc_t = calloc(np * 6, sizeof(double));
+    M->bc_ndof = ORC_NEW(int, np);
+    M->bc_t = ORC_ZNEW(real, np * 6);
     resolve_bcs(M);
     *out = M;
     return ORC_OK;
@@ -703,37 +716,37 @@ int orc_mesh_new(int d, long np, const double *x_soa, long nc, const int *c2n_so
  * ------------------------------------------------------------------------------------ */
 typedef struct {
     /* geometry at x^n */
-    double *V, *xc, *ln, *N, *Lc;
+    real *V, *xc, *ln, *N, *Lc;
     /* slopes */
-    double *gv, *gF;
+    real *gv, *gF;
     /* packets */
-    double *pkM, *pkR;
+    real *pkM, *pkR;
     /* nodes */
-    double *vs, *x1, *vp1;
+    real *vs, *x1, *vp1;
     /* candidate */
-    double *v1, *e1, *F1, *V1;
+    real *v1, *e1, *F1, *V1;
 } Work;
 
 static Work work_new(const OrcMesh *M) {
     int d = M->d, nv = M->nv;
     long nc = M->nc, np = M->np;
     Work w;
-    w.V = malloc(sizeof(double) * nc);
-    w.xc = malloc(sizeof(double) * nc * d);
-    w.ln = malloc(sizeof(double) * nc * nv * d);
-    w.N = malloc(sizeof(double) * nc * nv * d);
-    w.Lc = malloc(sizeof(double) * nc);
-    w.gv = malloc(sizeof(double) * nc * d * d);
-    w.gF = malloc(sizeof(double) * nc * d * d * d);
-    w.pkM = malloc(sizeof(double) * nc * nv * d * d);
-    w.pkR = malloc(sizeof(double) * nc * nv * d);
-    w.vs = malloc(sizeof(double) * np * d);
-    w.x1 = malloc(sizeof(double) * np * d);
-    w.vp1 = malloc(sizeof(double) * np * d);
-    w.v1 = malloc(sizeof(double) * nc * d);
-    w.e1 = malloc(sizeof(double) * nc);
-    w.F1 = malloc(sizeof(double) * nc * d * d);
-    w.V1 = malloc(sizeof(double) * nc);
+    w.V = ORC_NEW(real, nc);
+    w.xc = ORC_NEW(real, nc * d);
+    w.ln = ORC_NEW(real, nc * nv * d);
+    w.N = ORC_NEW(real, nc * nv * d);
+    w.Lc = ORC_NEW(real, nc);
+    w.gv = ORC_NEW(real, nc * d * d);
+    w.gF = ORC_NEW(real, nc * d * d * d);
+    w.pkM = ORC_NEW(real, nc * nv * d * d);
+    w.pkR = ORC_NEW(real, nc * nv * d);
+    w.vs = ORC_NEW(real, np * d);
+    w.x1 = ORC_NEW(real, np * d);
+    w.vp1 = ORC_NEW(real, np * d);
+    w.v1 = ORC_NEW(real, nc * d);
+    w.e1 = ORC_NEW(real, nc);
+    w.F1 = ORC_NEW(real, nc * d * d);
+    w.V1 = ORC_NEW(real, nc);
     return w;
 }
 
@@ -743,18 +756,18 @@ static void work_free(Work *w) {
     free(w->F1); free(w->V1);
 }
 
-static void gather_xs(const OrcMesh *M, const double *x, long c, double *xs) {
+static void gather_xs(const OrcMesh *M, const real *x, long c, real *xs) {
     for (int k = 0; k < M->nv; ++k)
         for (int a = 0; a < M->d; ++a) xs[k * M->d + a] = x[M->c2n[c * M->nv + k] * M->d + a];
 }
 
 /* 1. geometry of every cell at x^n */
-static void phase_geometry(const OrcState *S, const double *x, Work *w) {
+static void phase_geometry(const OrcState *S, const real *x, Work *w) {
     const OrcMesh *M = S->M;
     int d = M->d, nv = M->nv;
 #pragma omp parallel for schedule(static)
     for (long c = 0; c < M->nc; ++c) {
-        double xs[MAXV * MAXD];
+        real xs[MAXV * MAXD];
         gather_xs(M, x, c, xs);
         orc_cell_geometry(d, xs, &w->V[c], &w->xc[c * d], &w->N[c * nv * d], &w->ln[c * nv * d], &w->Lc[c]);
     }
@@ -768,20 +781,20 @@ static void phase_slopes(const OrcState *S, const int *order, Work *w) {
     int d = M->d, nq = d + d * d;
 #pragma omp parallel for schedule(static)
     for (long c = 0; c < M->nc; ++c) {
-        double *gv = w->gv + c * d * d, *gF = w->gF + c * d * d * d;
-        memset(gv, 0, sizeof(double) * d * d);
-        memset(gF, 0, sizeof(double) * d * d * d);
+        real *gv = w->gv + c * d * d, *gF = w->gF + c * d * d * d;
+        memset(gv, 0, sizeof(real) * d * d);
+        memset(gF, 0, sizeof(real) * d * d * d);
         if (order[c] == 1) continue;
-        double G[9] = {0}, r[12][3];
+        real G[9] = {0}, r[12][3];
         memset(r, 0, sizeof(r));
         for (long j = M->st_off[c]; j < M->st_off[c + 1]; ++j) {
             long o = M->st_idx[j];
             /* weight: number of nodes o shares with c (sum over the (node, neighbour) pairs) */
-            double wt = 0.0;
+            real wt = 0.0;
             for (int k = 0; k < M->nv; ++k)
                 for (int kk = 0; kk < M->nv; ++kk)
                     if (M->c2n[c * M->nv + k] == M->c2n[o * M->nv + kk]) wt += 1.0;
-            double dx[3], dq[12];
+            real dx[3], dq[12];
             for (int a = 0; a < d; ++a) dx[a] = w->xc[o * d + a] - w->xc[c * d + a];
             for (int i = 0; i < d; ++i) dq[i] = S->v[o * d + i] - S->v[c * d + i];
             for (int i = 0; i < d * d; ++i) dq[d + i] = S->F[o * d * d + i] - S->F[c * d * d + i];
@@ -790,35 +803,35 @@ static void phase_slopes(const OrcState *S, const int *order, Work *w) {
             for (int q = 0; q < nq; ++q)
                 for (int a = 0; a < d; ++a) r[q][a] += wt * dx[a] * dq[q];
         }
-        double tr = 0.0;
+        real tr = 0.0;
         for (int a = 0; a < d; ++a) tr += G[a * d + a];
-        double det = det_n(d, G);
+        real det = det_n(d, G);
         if (!(det > 1e-12 * pow(tr / d, d))) continue; /* degenerate stencil: first order slopes */
-        double Gi[9];
+        real Gi[9];
         inv_n(d, G, Gi);
         for (int q = 0; q < nq; ++q) {
-            double g[3];
+            real g[3];
             matvec_n(d, Gi, r[q], g);
             if (order[c] == 3) {
                 /* Barth-Jespersen: largest phi <= 1 keeping q_c + phi g.(x_p - x_c) in [lo, hi] */
-                double qc = q < d ? S->v[c * d + q] : S->F[c * d * d + q - d], lo = qc, hi = qc;
+                real qc = q < d ? S->v[c * d + q] : S->F[c * d * d + q - d], lo = qc, hi = qc;
                 for (long j = M->st_off[c]; j < M->st_off[c + 1]; ++j) {
                     long o = M->st_idx[j];
-                    double qo = q < d ? S->v[o * d + q] : S->F[o * d * d + q - d];
+                    real qo = q < d ? S->v[o * d + q] : S->F[o * d * d + q - d];
                     lo = fmin(lo, qo);
                     hi = fmax(hi, qo);
                 }
-                double phi = 1.0;
+                real phi = 1.0;
                 for (int k = 0; k < M->nv; ++k) {
                     int p = M->c2n[c * M->nv + k];
-                    double delta = 0.0;
+                    real delta = 0.0;
                     for (int a = 0; a < d; ++a) delta += g[a] * (S->x[p * d + a] - w->xc[c * d + a]);
                     if (delta > 0.0) phi = fmin(phi, (hi - qc) / delta);
                     if (delta < 0.0) phi = fmin(phi, (lo - qc) / delta);
                 }
                 for (int a = 0; a < d; ++a) g[a] *= phi;
             }
-            double *dst = q < d ? gv + q * d : gF + (q - d) * d;
+            real *dst = q < d ? gv + q * d : gF + (q - d) * d;
             for (int a = 0; a < d; ++a) dst[a] = g[a];
         }
     }
@@ -828,36 +841,36 @@ static void phase_slopes(const OrcState *S, const int *order, Work *w) {
  *    reading R8; Eqs. Mcp^n, nodal_solver^n):
  *    M_cp   = z_c sum_{f containing p} |l n|_cpf n_cpf (x) n_cpf
  *    rhs_cp = M_cp v*_cp - T*_cp (l n)_cp         so that f_cp = M_cp v*_p - rhs_cp */
-static void phase_packets(const OrcState *S, const int *order, double dt, Work *w) {
+static void phase_packets(const OrcState *S, const int *order, real dt, Work *w) {
     const OrcMesh *M = S->M;
     int d = M->d, nv = M->nv, dd = d * d;
 #pragma omp parallel for schedule(static)
     for (long c = 0; c < M->nc; ++c) {
-        const double *ln = w->ln + c * nv * d, *N = w->N + c * nv * d;
-        const double *vc = S->v + c * d, *Fc = S->F + c * dd;
-        double rho = S->m[c] / w->V[c];
-        double eps = S->e[c];  /* specific internal energy (enters the stiffened gas only) */
+        const real *ln = w->ln + c * nv * d, *N = w->N + c * nv * d;
+        const real *vc = S->v + c * d, *Fc = S->F + c * dd;
+        real rho = S->m[c] / w->V[c];
+        real eps = S->e[c];  /* specific internal energy (enters the stiffened gas only) */
         for (int i = 0; i < d; ++i) eps -= 0.5 * vc[i] * vc[i];
-        double z = rho * sound_speed_state(S, c, Fc, rho, eps);
-        double vstar[MAXV][MAXD], Tstar[MAXV][9];
+        real z = rho * sound_speed_state(S, c, Fc, rho, eps);
+        real vstar[MAXV][MAXD], Tstar[MAXV][9];
         if (order[c] != 1) {
-            const double *gv = w->gv + c * dd, *gF = w->gF + c * dd * d;
-            double vh[MAXV][MAXD], Fh[MAXV][9], dvdt[MAXD] = {0, 0, 0}, dFdt[9];
+            const real *gv = w->gv + c * dd, *gF = w->gF + c * dd * d;
+            real vh[MAXV][MAXD], Fh[MAXV][9], dvdt[MAXD] = {0, 0, 0}, dFdt[9];
             for (int k = 0; k < nv; ++k) {
                 int p = M->c2n[c * nv + k];
-                double dx[3];
+                real dx[3];
                 for (int a = 0; a < d; ++a) dx[a] = S->x[p * d + a] - w->xc[c * d + a];
                 for (int i = 0; i < d; ++i) {
-                    double s = vc[i];
+                    real s = vc[i];
                     for (int a = 0; a < d; ++a) s += gv[i * d + a] * dx[a];
                     vh[k][i] = s;
                 }
                 for (int i = 0; i < dd; ++i) {
-                    double s = Fc[i];
+                    real s = Fc[i];
                     for (int a = 0; a < d; ++a) s += gF[i * d + a] * dx[a];
                     Fh[k][i] = s;
                 }
-                double Tk[9], Tn[3];
+                real Tk[9], Tn[3];
                 stress_state(S, c, Fh[k], eps, Tk);
                 matvec_n(d, Tk, ln + k * d, Tn);
                 for (int i = 0; i < d; ++i) dvdt[i] += Tn[i];
@@ -866,39 +879,39 @@ static void phase_packets(const OrcState *S, const int *order, double dt, Work *
             matmul_n(d, gv, Fc, dFdt); /* dF/dt = L^ F (Eq. GCLL) with L^ the reconstructed gradient */
             /* stiffened gas: the internal energy at the half step, d eps/dt = T : L^ / rho with
              * the cell's stress (reading R18) */
-            double eps_h = eps;
+            real eps_h = eps;
             if (S->prm.eos != 0) {
-                double Tc[9], pw = 0.0;
+                real Tc[9], pw = 0.0;
                 stress_state(S, c, Fc, eps, Tc);
                 for (int i = 0; i < dd; ++i) pw += Tc[i] * gv[i];
                 eps_h = eps + 0.5 * dt * pw / rho;
             }
             for (int k = 0; k < nv; ++k) {
-                double Fs[9];
+                real Fs[9];
                 for (int i = 0; i < d; ++i) vstar[k][i] = vh[k][i] + 0.5 * dt * dvdt[i];
                 for (int i = 0; i < dd; ++i) Fs[i] = Fh[k][i] + 0.5 * dt * dFdt[i];
                 stress_state(S, c, Fs, eps_h, Tstar[k]);
             }
         } else {
-            double T0[9];
+            real T0[9];
             stress_state(S, c, Fc, eps, T0);
             for (int k = 0; k < nv; ++k) {
                 for (int i = 0; i < d; ++i) vstar[k][i] = vc[i];
-                memcpy(Tstar[k], T0, sizeof(double) * dd);
+                memcpy(Tstar[k], T0, sizeof(real) * dd);
             }
         }
         for (int k = 0; k < nv; ++k) {
-            double *Mk = w->pkM + (c * nv + k) * dd, *Rk = w->pkR + (c * nv + k) * d;
-            memset(Mk, 0, sizeof(double) * dd);
+            real *Mk = w->pkM + (c * nv + k) * dd, *Rk = w->pkR + (c * nv + k) * d;
+            memset(Mk, 0, sizeof(real) * dd);
             for (int f = 0; f < nv; ++f) {
                 if (f == k) continue;
-                double lnf[3], l = 0.0;
+                real lnf[3], l = 0.0;
                 for (int a = 0; a < d; ++a) { lnf[a] = N[f * d + a] / d; l += lnf[a] * lnf[a]; }
                 l = sqrt(l);
                 for (int a = 0; a < d; ++a)
                     for (int b = 0; b < d; ++b) Mk[a * d + b] += z * lnf[a] * lnf[b] / l;
             }
-            double Mv[3], Tn[3];
+            real Mv[3], Tn[3];
             matvec_n(d, Mk, vstar[k], Mv);
             matvec_n(d, Tstar[k], ln + k * d, Tn);
             for (int i = 0; i < d; ++i) Rk[i] = Mv[i] - Tn[i];
@@ -911,23 +924,23 @@ static void phase_packets(const OrcState *S, const int *order, double dt, Work *
  *    pressure faces around p; v*_p = K b_p with K the Galerkin solve on the node's free
  *    subspace; with prescribed-velocity faces around p, v*_p = K b_p - T_p K d_p with T_p
  *    chosen so that v*_p . d_p = g_p; x^{n+1} = x^n + dt v*_p, v_p^{n+1} = 2 v*_p - v_p^n */
-static void solve_K(const OrcMesh *M, const double *Mp, long p, const double *rhs, double *out) {
+static void solve_K(const OrcMesh *M, const real *Mp, long p, const real *rhs, real *out) {
     int d = M->d;
     int nf = M->bc_ndof[p];
     if (nf == d) {
-        double Mi[9];
+        real Mi[9];
         inv_n(d, Mp, Mi);
         matvec_n(d, Mi, rhs, out);
     } else if (nf == 0) {
         for (int i = 0; i < d; ++i) out[i] = 0.0;
     } else {
-        const double *t = M->bc_t + p * 6;
-        double A[4], r[2], al[2];
+        const real *t = M->bc_t + p * 6;
+        real A[4], r[2], al[2];
         for (int i = 0; i < nf; ++i) {
             r[i] = 0.0;
             for (int a = 0; a < d; ++a) r[i] += t[3 * i + a] * rhs[a];
             for (int j = 0; j < nf; ++j) {
-                double Mtj[3], s = 0.0;
+                real Mtj[3], s = 0.0;
                 matvec_n(d, Mp, t + 3 * j, Mtj);
                 for (int a = 0; a < d; ++a) s += t[3 * i + a] * Mtj[a];
                 A[i * nf + j] = s;
@@ -936,23 +949,23 @@ static void solve_K(const OrcMesh *M, const double *Mp, long p, const double *rh
         if (nf == 1) {
             al[0] = r[0] / A[0];
         } else {
-            double Ai[4];
+            real Ai[4];
             inv_n(2, A, Ai);
             al[0] = Ai[0] * r[0] + Ai[1] * r[1];
             al[1] = Ai[2] * r[0] + Ai[3] * r[1];
         }
         for (int a = 0; a < d; ++a) {
-            double s = 0.0;
+            real s = 0.0;
             for (int i = 0; i < nf; ++i) s += al[i] * t[3 * i + a];
             out[a] = s;
         }
     }
 }
 
-static void node_solve_one(const OrcMesh *M, const double *x, const double *pkM, const double *pkR, long p,
-                           double *vs) {
+static void node_solve_one(const OrcMesh *M, const real *x, const real *pkM, const real *pkR, long p,
+                           real *vs) {
     int d = M->d, nv = M->nv, dd = d * d;
-    double Mp[9] = {0}, bp[3] = {0, 0, 0};
+    real Mp[9] = {0}, bp[3] = {0, 0, 0};
     for (long j = M->n2c_off[p]; j < M->n2c_off[p + 1]; ++j) {
         long c = M->n2c_cell[j];
         int k = M->n2c_k[j];
@@ -960,17 +973,17 @@ static void node_solve_one(const OrcMesh *M, const double *x, const double *pkM,
         for (int i = 0; i < d; ++i) bp[i] += pkR[(c * nv + k) * d + i];
     }
     /* faces around p with a prescribed traction, pressure or normal velocity (reading R15) */
-    double dp[3] = {0, 0, 0}, gp = 0.0;
+    real dp[3] = {0, 0, 0}, gp = 0.0;
     int nvel = 0;
     for (long j = M->nbf_off[p]; j < M->nbf_off[p + 1]; ++j) {
         long b = M->nbf_idx[j];
         int tag = M->bf_tag[b];
         if (tag < 3) continue;
-        double N[3] = {0, 0, 0};
+        real N[3] = {0, 0, 0};
         face_area_vector(M, x, b, N);
-        const double *val = M->bf_val + b * d;
+        const real *val = M->bf_val + b * d;
         if (tag == 3) {
-            double area = 0.0;
+            real area = 0.0;
             for (int a = 0; a < d; ++a) area += N[a] * N[a];
             area = sqrt(area);
             for (int a = 0; a < d; ++a) bp[a] += area / d * val[a];
@@ -986,15 +999,15 @@ static void node_solve_one(const OrcMesh *M, const double *x, const double *pkM,
     }
     solve_K(M, Mp, p, bp, vs);
     if (nvel > 0) {
-        double w[3];
+        real w[3];
         solve_K(M, Mp, p, dp, w);
-        double wd = 0.0, vd = 0.0;
+        real wd = 0.0, vd = 0.0;
         for (int a = 0; a < d; ++a) {
             wd += w[a] * dp[a];
             vd += vs[a] * dp[a];
         }
         if (wd > 0.0) {
-            double T = (vd - gp) / wd;
+            real T = (vd - gp) / wd;
             for (int a = 0; a < d; ++a) vs[a] -= T * w[a];
         }
     }
@@ -1004,25 +1017,25 @@ static void node_solve_one(const OrcMesh *M, const double *x, const double *pkM,
     for (long j = M->nbf_off[p]; j < M->nbf_off[p + 1]; ++j) contact |= M->bf_tag[M->nbf_idx[j]] == 6;
     if (contact) {
         for (int k = 0; k < M->n_contact; ++k) {
-            const double *P = M->contact[k], *n = M->contact[k] + d;
-            double dist = 0.0, vn = 0.0;
+            const real *P = M->contact[k], *n = M->contact[k] + d;
+            real dist = 0.0, vn = 0.0;
             for (int a = 0; a < d; ++a) {
                 dist += n[a] * (x[p * d + a] - P[a]);
                 vn += n[a] * vs[a];
             }
             if (!(dist < M->contact_eps && vn < 0.0)) continue;
-            double w[3], wn = 0.0;
+            real w[3], wn = 0.0;
             solve_K(M, Mp, p, n, w);
             for (int a = 0; a < d; ++a) wn += w[a] * n[a];
             if (wn > 0.0) {
-                double T = vn / wn;
+                real T = vn / wn;
                 for (int a = 0; a < d; ++a) vs[a] -= T * w[a];
             }
         }
     }
 }
 
-static void phase_nodes(const OrcState *S, double dt, Work *w) {
+static void phase_nodes(const OrcState *S, real dt, Work *w) {
     const OrcMesh *M = S->M;
     int d = M->d;
 #pragma omp parallel for schedule(static)
@@ -1036,10 +1049,10 @@ static void phase_nodes(const OrcState *S, double dt, Work *w) {
 }
 
 /* velocity gradient of a cell from node velocities (Eq. div_grad_v, reading R2) */
-static void vel_gradient(int d, int nv, const double *ln, double V, const double *vnodes, double *L) {
+static void vel_gradient(int d, int nv, const real *ln, real V, const real *vnodes, real *L) {
     for (int i = 0; i < d; ++i)
         for (int j = 0; j < d; ++j) {
-            double s = 0.0;
+            real s = 0.0;
             for (int k = 0; k < nv; ++k) s += vnodes[k * d + i] * ln[k * d + j];
             L[i * d + j] = s / V;
         }
@@ -1047,17 +1060,17 @@ static void vel_gradient(int d, int nv, const double *ln, double V, const double
 
 /* 5. subcell forces and cell update (Eqs. subforce^n, tau_c^n, v_c^n, e_c^n, firstB, CN_B;
  *    readings R1, R7) */
-static void phase_update(const OrcState *S, const int *order, double dt, Work *w) {
+static void phase_update(const OrcState *S, const int *order, real dt, Work *w) {
     const OrcMesh *M = S->M;
     int d = M->d, nv = M->nv, dd = d * d;
 #pragma omp parallel for schedule(static)
     for (long c = 0; c < M->nc; ++c) {
-        double sf[3] = {0, 0, 0}, sfv = 0.0;
-        double vsn[MAXV * MAXD], vpn[MAXV * MAXD], vp1n[MAXV * MAXD];
+        real sf[3] = {0, 0, 0}, sfv = 0.0;
+        real vsn[MAXV * MAXD], vpn[MAXV * MAXD], vp1n[MAXV * MAXD];
         for (int k = 0; k < nv; ++k) {
             int p = M->c2n[c * nv + k];
-            const double *Mk = w->pkM + (c * nv + k) * dd, *Rk = w->pkR + (c * nv + k) * d;
-            double f[3];
+            const real *Mk = w->pkM + (c * nv + k) * dd, *Rk = w->pkR + (c * nv + k) * d;
+            real f[3];
             matvec_n(d, Mk, w->vs + p * d, f);
             for (int i = 0; i < d; ++i) f[i] -= Rk[i];
             for (int i = 0; i < d; ++i) {
@@ -1070,24 +1083,24 @@ static void phase_update(const OrcState *S, const int *order, double dt, Work *w
                 vp1n[k * d + a] = w->vp1[p * d + a];
             }
         }
-        double m = S->m[c];
+        real m = S->m[c];
         for (int i = 0; i < d; ++i) w->v1[c * d + i] = S->v[c * d + i] + dt / m * sf[i];
         w->e1[c] = S->e[c] + dt / m * sfv;
         /* volume at x^{n+1} */
-        double xs[MAXV * MAXD], V1, xc1[MAXD], N1[MAXV * MAXD], ln1[MAXV * MAXD], Lc1;
+        real xs[MAXV * MAXD], V1, xc1[MAXD], N1[MAXV * MAXD], ln1[MAXV * MAXD], Lc1;
         gather_xs(M, w->x1, c, xs);
         orc_cell_geometry(d, xs, &V1, xc1, N1, ln1, &Lc1);
         w->V1[c] = V1;
-        const double *Fn = S->F + c * dd;
-        double *F1 = w->F1 + c * dd;
+        const real *Fn = S->F + c * dd;
+        real *F1 = w->F1 + c * dd;
         if (order[c] != 1) {
             /* Crank-Nicolson: (I - dt/2 L^{n+1}) F^{n+1} = (I + dt/2 L^n) F^n */
-            double L0[9], L1[9], A[9], Bm[9], Ai[9], R[9];
+            real L0[9], L1[9], A[9], Bm[9], Ai[9], R[9];
             vel_gradient(d, nv, w->ln + c * nv * d, w->V[c], vpn, L0);
             vel_gradient(d, nv, ln1, V1, vp1n, L1);
             for (int i = 0; i < d; ++i)
                 for (int j = 0; j < d; ++j) {
-                    double id = i == j ? 1.0 : 0.0;
+                    real id = i == j ? 1.0 : 0.0;
                     A[i * d + j] = id - 0.5 * dt * L1[i * d + j];
                     Bm[i * d + j] = id + 0.5 * dt * L0[i * d + j];
                 }
@@ -1096,7 +1109,7 @@ static void phase_update(const OrcState *S, const int *order, double dt, Work *w
             matmul_n(d, Ai, R, F1);
         } else {
             /* first order: F^{n+1} = F^n + dt L* F^n, L* from v*_p on the x^n geometry */
-            double Ls[9], LF[9];
+            real Ls[9], LF[9];
             vel_gradient(d, nv, w->ln + c * nv * d, w->V[c], vsn, Ls);
             matmul_n(d, Ls, Fn, LF);
             for (int i = 0; i < dd; ++i) F1[i] = Fn[i] + dt * LF[i];
@@ -1106,7 +1119,7 @@ static void phase_update(const OrcState *S, const int *order, double dt, Work *w
 
 /* 6. detection (Eqs. PAD and RDMP; reading R12).
  * pad_state: 0 admissible; 1 only eps < -tol; 2 not computable (non-finite, tau <= 0, det F <= 0) */
-static int pad_state(int d, const double *v, double e, const double *F, double V, double a0sq) {
+static int pad_state(int d, const real *v, real e, const real *F, real V, real a0sq) {
     int dd = d * d;
     if (!isfinite(e) || !isfinite(V)) return 2;
     for (int i = 0; i < d; ++i)
@@ -1115,22 +1128,22 @@ static int pad_state(int d, const double *v, double e, const double *F, double V
         if (!isfinite(F[i])) return 2;
     if (!(V > 0.0)) return 2;
     if (!(det_n(d, F) > 0.0)) return 2;
-    double ke = 0.0;
+    real ke = 0.0;
     for (int i = 0; i < d; ++i) ke += 0.5 * v[i] * v[i];
-    double eps = e - ke;
-    double tol = 1e-10 * fmax(fmax(fabs(e), ke), a0sq);
+    real eps = e - ke;
+    real tol = 1e-10 * fmax(fmax(fabs(e), ke), a0sq);
     return eps >= -tol ? 0 : 1;
 }
 
 /* Eq. RDMP: the range [lo, hi] of the density at t^n over the stencil V_c and the cell c
  * itself (reading R12), from the volumes Vn at x^n */
-static void rdmp_range(const OrcState *S, const double *Vn, long c, double *lo, double *hi) {
+static void rdmp_range(const OrcState *S, const real *Vn, long c, real *lo, real *hi) {
     const OrcMesh *M = S->M;
     *lo = S->m[c] / Vn[c];
     *hi = *lo;
     for (long j = M->st_off[c]; j < M->st_off[c + 1]; ++j) {
         long o = M->st_idx[j];
-        double r = S->m[o] / Vn[o];
+        real r = S->m[o] / Vn[o];
         *lo = fmin(*lo, r);
         *hi = fmax(*hi, r);
     }
@@ -1138,18 +1151,18 @@ static void rdmp_range(const OrcState *S, const double *Vn, long c, double *lo, 
 
 /* Eq. RDMP: a candidate density is admissible when it lies in [lo - delta, hi + delta],
  * delta = max(delta0, delta1 (hi - lo)) with delta0 absolute (reading R12) */
-static int rdmp_admits(const OrcState *S, double rho_new, double lo, double hi) {
-    double delta = fmax(S->prm.delta0, S->prm.delta1 * (hi - lo));
+static int rdmp_admits(const OrcState *S, real rho_new, real lo, real hi) {
+    real delta = fmax(S->prm.delta0, S->prm.delta1 * (hi - lo));
     return rho_new >= lo - delta && rho_new <= hi + delta;
 }
 
 static int rdmp_ok(const OrcState *S, const Work *w, long c) {
-    double lo, hi;
+    real lo, hi;
     rdmp_range(S, w->V, c, &lo, &hi);
     return rdmp_admits(S, S->m[c] / w->V1[c], lo, hi);
 }
 
-static void candidate(const OrcState *S, const int *order, double dt, Work *w) {
+static void candidate(const OrcState *S, const int *order, real dt, Work *w) {
     phase_geometry(S, S->x, w);
     phase_slopes(S, order, w);
     phase_packets(S, order, dt, w);
@@ -1158,13 +1171,13 @@ static void candidate(const OrcState *S, const int *order, double dt, Work *w) {
 }
 
 /* 7. time step (Eqs. CFL, CFL2; reading R13) */
-static double dt_acoustic_cell(const OrcState *S, long c, const double *F, double V, double Lc, double eps) {
-    double rho = S->m[c] / V;
+static real dt_acoustic_cell(const OrcState *S, long c, const real *F, real V, real Lc, real eps) {
+    real rho = S->m[c] / V;
     return S->prm.cfl * Lc / sound_speed_state(S, c, F, rho, eps);
 }
 
-static double eps_of(int d, const double *v, double e) {
-    double ke = 0.0;
+static real eps_of(int d, const real *v, real e) {
+    real ke = 0.0;
     for (int i = 0; i < d; ++i) ke += 0.5 * v[i] * v[i];
     return e - ke;
 }
@@ -1184,7 +1197,7 @@ int orc_step(OrcState *S, OrcInfo *info) {
     const OrcMesh *M = S->M;
     int d = M->d, dd = d * d, nv = M->nv;
     long nc = M->nc;
-    double dt = S->dt;
+    real dt = S->dt;
     Work w = work_new(M);
     int *order = S->order;
     for (long c = 0; c < nc; ++c) order[c] = S->prm.order == 1 ? 1 : 2;
@@ -1196,7 +1209,7 @@ int orc_step(OrcState *S, OrcInfo *info) {
         n_eps = 0;
         if (S->prm.mood) {
             /* new troubled cells are decided on this candidate before any mask change */
-            int *flag = calloc(nc, sizeof(int));
+            int *flag = ORC_ZNEW(int, nc);
 #pragma omp parallel for schedule(static) reduction(+ : fresh, n_para, n_eps)
             for (long c = 0; c < nc; ++c) {
                 int ps = pad_state(d, w.v1 + c * d, w.e1[c], w.F1 + c * dd, w.V1[c], a0sq_of(S, c));
@@ -1223,27 +1236,27 @@ int orc_step(OrcState *S, OrcInfo *info) {
     if (status == ORC_OK && n_para > 0) status = ORC_ERR_PARACHUTE;
     if (status == ORC_OK) {
         /* accept the candidate */
-        double dtn = S->prm.dt_fixed > 0 ? S->prm.dt_fixed : (1.0 + S->prm.Ci) * dt;
+        real dtn = S->prm.dt_fixed > 0 ? S->prm.dt_fixed : (1.0 + S->prm.Ci) * dt;
         if (!(S->prm.dt_fixed > 0)) {
             for (long c = 0; c < nc; ++c) {
-                double xs[MAXV * MAXD], V1, xc1[MAXD], N1[MAXV * MAXD], ln1[MAXV * MAXD], Lc1;
+                real xs[MAXV * MAXD], V1, xc1[MAXD], N1[MAXV * MAXD], ln1[MAXV * MAXD], Lc1;
                 gather_xs(M, w.x1, c, xs);
                 orc_cell_geometry(d, xs, &V1, xc1, N1, ln1, &Lc1);
-                double dtc = dt_acoustic_cell(S, c, w.F1 + c * dd, V1, Lc1, eps_of(d, w.v1 + c * d, w.e1[c]));
-                double dV = V1 - w.V[c];
+                real dtc = dt_acoustic_cell(S, c, w.F1 + c * dd, V1, Lc1, eps_of(d, w.v1 + c * d, w.e1[c]));
+                real dV = V1 - w.V[c];
                 if (dV != 0.0) dtc = fmin(dtc, S->prm.Cv * dt * w.V[c] / fabs(dV));
                 dtn = fmin(dtn, dtc);
             }
         }
-        memcpy(S->x, w.x1, sizeof(double) * M->np * d);
-        memcpy(S->vp, w.vp1, sizeof(double) * M->np * d);
-        memcpy(S->v, w.v1, sizeof(double) * nc * d);
-        memcpy(S->e, w.e1, sizeof(double) * nc);
-        memcpy(S->F, w.F1, sizeof(double) * nc * dd);
+        memcpy(S->x, w.x1, sizeof(real) * M->np * d);
+        memcpy(S->vp, w.vp1, sizeof(real) * M->np * d);
+        memcpy(S->v, w.v1, sizeof(real) * nc * d);
+        memcpy(S->e, w.e1, sizeof(real) * nc);
+        memcpy(S->F, w.F1, sizeof(real) * nc * dd);
         for (long c = 0; c < nc; ++c) S->tau[c] = w.V1[c] / S->m[c];
-        memcpy(S->pkM, w.pkM, sizeof(double) * nc * nv * dd);
-        memcpy(S->pkR, w.pkR, sizeof(double) * nc * nv * d);
-        memcpy(S->vstar, w.vs, sizeof(double) * M->np * d);
+        memcpy(S->pkM, w.pkM, sizeof(real) * nc * nv * dd);
+        memcpy(S->pkR, w.pkR, sizeof(real) * nc * nv * d);
+        memcpy(S->vstar, w.vs, sizeof(real) * M->np * d);
         S->t += dt;
         S->step += 1;
         S->last.dt_used = dt;
@@ -1280,27 +1293,27 @@ void orc_state_free(OrcState *S) {
     free(S);
 }
 
-int orc_state_new(OrcMesh *M, double rho0, double lam, const double *mu_cell, const double *v_soa,
-                  const double *F_soa, const OrcParams *prm, OrcState **out) {
+int orc_state_new(OrcMesh *M, real rho0, real lam, const real *mu_cell, const real *v_soa,
+                  const real *F_soa, const OrcParams *prm, OrcState **out) {
     if (!M || !prm || !mu_cell || !v_soa || !out) return ORC_ERR_ARG;
     if (prm->eos != 0 && !(prm->eos == 1 && prm->gamma > 1.0 && prm->p0 + prm->p_inf > 0.0)) return ORC_ERR_ARG;
     int d = M->d, nv = M->nv, dd = d * d;
     long nc = M->nc, np = M->np;
-    OrcState *S = calloc(1, sizeof(OrcState));
+    OrcState *S = ORC_ZNEW(OrcState, 1);
     S->M = M; S->prm = *prm; S->rho0 = rho0; S->lam = lam;
-    S->mu = malloc(sizeof(double) * nc);
-    S->m = malloc(sizeof(double) * nc);
-    S->x = malloc(sizeof(double) * np * d);
-    S->vp = calloc(np * d, sizeof(double));
-    S->v = malloc(sizeof(double) * nc * d);
-    S->e = malloc(sizeof(double) * nc);
-    S->F = malloc(sizeof(double) * nc * dd);
-    S->tau = malloc(sizeof(double) * nc);
-    S->order = malloc(sizeof(int) * nc);
-    S->pkM = calloc(nc * nv * dd, sizeof(double));
-    S->pkR = calloc(nc * nv * d, sizeof(double));
-    S->vstar = calloc(np * d, sizeof(double));
-    memcpy(S->x, M->x0, sizeof(double) * np * d);
+    S->mu = ORC_NEW(real, nc);
+    S->m = ORC_NEW(real, nc);
+    S->x = ORC_NEW(real, np * d);
+    S->vp = ORC_ZNEW(real, np * d);
+    S->v = ORC_NEW(real, nc * d);
+    S->e = ORC_NEW(real, nc);
+    S->F = ORC_NEW(real, nc * dd);
+    S->tau = ORC_NEW(real, nc);
+    S->order = ORC_NEW(int, nc);
+    S->pkM = ORC_ZNEW(real, nc * nv * dd);
+    S->pkR = ORC_ZNEW(real, nc * nv * d);
+    S->vstar = ORC_ZNEW(real, np * d);
+    memcpy(S->x, M->x0, sizeof(real) * np * d);
     for (long c = 0; c < nc; ++c) {
         S->mu[c] = mu_cell[c];
         for (int i = 0; i < d; ++i) S->v[c * d + i] = v_soa[i * nc + c];
@@ -1309,19 +1322,19 @@ int orc_state_new(OrcMesh *M, double rho0, double lam, const double *mu_cell, co
     }
     Work w = work_new(M);
     phase_geometry(S, S->x, &w);
-    double dt0 = INFINITY;
+    real dt0 = INFINITY;
     for (long c = 0; c < nc; ++c) {
         S->m[c] = rho0 * w.V[c];
         S->tau[c] = w.V[c] / S->m[c];
-        double ke = 0.0;
+        real ke = 0.0;
         for (int i = 0; i < d; ++i) ke += 0.5 * S->v[c * d + i] * S->v[c * d + i];
         if (S->prm.eos == 0) {
             S->e[c] = ke + orc_free_energy_a(d, S->F + c * dd, rho0, S->mu[c], kappa_of(S, c), S->prm.shear_a);
         } else {  /* eps_v from the initial pressure p0 at rho = rho0 / det F (reading R18) */
-            double F3[9];
+            real F3[9];
             embed3(d, S->F + c * dd, F3);
-            double J = det_n(3, F3);
-            double eps_v = (S->prm.p0 + S->prm.gamma * S->prm.p_inf) / ((S->prm.gamma - 1.0) * rho0 / J);
+            real J = det_n(3, F3);
+            real eps_v = (S->prm.p0 + S->prm.gamma * S->prm.p_inf) / ((S->prm.gamma - 1.0) * rho0 / J);
             S->e[c] = ke + eps_v + orc_free_energy_a(d, S->F + c * dd, rho0, S->mu[c], 0.0, S->prm.shear_a);
         }
         dt0 = fmin(dt0, dt_acoustic_cell(S, c, S->F + c * dd, w.V[c], w.Lc[c], eps_of(d, S->v + c * d, S->e[c])));
@@ -1341,7 +1354,7 @@ int orc_state_new(OrcMesh *M, double rho0, double lam, const double *mu_cell, co
 enum { F_X = 0, F_VP = 1, F_VSTAR = 2, F_V = 3, F_E = 4, F_F = 5, F_TAU = 6, F_ORDER = 7,
        F_MASS = 8, F_PKM = 9, F_PKR = 10 };
 
-int orc_get(const OrcState *S, int field, double *dst) {
+int orc_get(const OrcState *S, int field, real *dst) {
     const OrcMesh *M = S->M;
     int d = M->d, dd = d * d, nv = M->nv;
     long nc = M->nc, np = M->np;
@@ -1371,12 +1384,12 @@ int orc_get(const OrcState *S, int field, double *dst) {
     return ORC_OK;
 }
 
-double orc_get_dt(const OrcState *S) { return S->dt; }
-double orc_get_t(const OrcState *S) { return S->t; }
+real orc_get_dt(const OrcState *S) { return S->dt; }
+real orc_get_t(const OrcState *S) { return S->t; }
 
 /* Set the dynamic state (used to replay a state on both sides): SoA arrays, NULL = keep. */
-int orc_set_state(OrcState *S, const double *x, const double *vp, const double *v, const double *e,
-                  const double *F, double dt) {
+int orc_set_state(OrcState *S, const real *x, const real *vp, const real *v, const real *e,
+                  const real *F, real dt) {
     const OrcMesh *M = S->M;
     int d = M->d, dd = d * d;
     long nc = M->nc, np = M->np;
@@ -1392,28 +1405,28 @@ int orc_set_state(OrcState *S, const double *x, const double *vp, const double *
 /* Reconstructed values of v and F at the nodes of cell c from the current state with the
  * given level (2 unlimited, 3 Barth-Jespersen), and each field's range over the stencil and
  * the cell: out [nv][nq], lo [nq], hi [nq]. Used by tests. */
-int orc_debug_corner_values(const OrcState *S, long c, int level, double *out, double *lo, double *hi) {
+int orc_debug_corner_values(const OrcState *S, long c, int level, real *out, real *lo, real *hi) {
     const OrcMesh *M = S->M;
     int d = M->d, nq = d + d * d, nv = M->nv;
     Work w = work_new(M);
-    int *order = malloc(sizeof(int) * M->nc);
+    int *order = ORC_NEW(int, M->nc);
     for (long i = 0; i < M->nc; ++i) order[i] = 1;
     order[c] = level;
     phase_geometry(S, S->x, &w);
     phase_slopes(S, order, &w);
     for (int q = 0; q < nq; ++q) {
-        double qc = q < d ? S->v[c * d + q] : S->F[c * d * d + q - d];
+        real qc = q < d ? S->v[c * d + q] : S->F[c * d * d + q - d];
         lo[q] = hi[q] = qc;
         for (long j = M->st_off[c]; j < M->st_off[c + 1]; ++j) {
             long o = M->st_idx[j];
-            double qo = q < d ? S->v[o * d + q] : S->F[o * d * d + q - d];
+            real qo = q < d ? S->v[o * d + q] : S->F[o * d * d + q - d];
             lo[q] = fmin(lo[q], qo);
             hi[q] = fmax(hi[q], qo);
         }
-        const double *g = q < d ? w.gv + c * d * d + q * d : w.gF + c * d * d * d + (q - d) * d;
+        const real *g = q < d ? w.gv + c * d * d + q * d : w.gF + c * d * d * d + (q - d) * d;
         for (int k = 0; k < nv; ++k) {
             int p = M->c2n[c * nv + k];
-            double val = qc;
+            real val = qc;
             for (int a = 0; a < d; ++a) val += g[a] * (S->x[p * d + a] - w.xc[c * d + a]);
             out[k * nq + q] = val;
         }
@@ -1428,12 +1441,12 @@ int orc_debug_corner_values(const OrcState *S, long c, int level, double *out, d
  * positions (lo, hi, may be NULL) and whether a candidate density rho_new passes the RDMP;
  * orc_debug_pad classifies a candidate (v [d], e, F [d*d] row-major, volume V) of cell c
  * with the cell's material: 0 admissible, 1 only eps below the tolerance, 2 not computable. */
-int orc_debug_rdmp(const OrcState *S, long c, double rho_new, double *lo, double *hi) {
+int orc_debug_rdmp(const OrcState *S, long c, real rho_new, real *lo, real *hi) {
     const OrcMesh *M = S->M;
     if (c < 0 || c >= M->nc) return -1;
     Work w = work_new(M);
     phase_geometry(S, S->x, &w);
-    double l, h;
+    real l, h;
     rdmp_range(S, w.V, c, &l, &h);
     int ok = rdmp_admits(S, rho_new, l, h);
     if (lo) *lo = l;
@@ -1442,7 +1455,7 @@ int orc_debug_rdmp(const OrcState *S, long c, double rho_new, double *lo, double
     return ok;
 }
 
-int orc_debug_pad(const OrcState *S, long c, const double *v, double e, const double *F, double V) {
+int orc_debug_pad(const OrcState *S, long c, const real *v, real e, const real *F, real V) {
     if (c < 0 || c >= S->M->nc) return -1;
     return pad_state(S->M->d, v, e, F, V, a0sq_of(S, c));
 }
@@ -1457,7 +1470,7 @@ int orc_mesh_bc_ndof(const OrcMesh *M, long p) { return M->bc_ndof[p]; }
 
 /* values of the boundary faces, [d][nb] (traction vectors; pressures in the first row;
  * prescribed velocities), applied from the next nodal solve on */
-int orc_mesh_set_bc_values(OrcMesh *M, const double *val_soa) {
+int orc_mesh_set_bc_values(OrcMesh *M, const real *val_soa) {
     if (!M || !val_soa) return ORC_ERR_ARG;
     for (long b = 0; b < M->nb; ++b)
         for (int a = 0; a < M->d; ++a) M->bf_val[b * M->d + a] = val_soa[a * M->nb + b];
@@ -1466,7 +1479,7 @@ int orc_mesh_set_bc_values(OrcMesh *M, const double *val_soa) {
 
 /* contact walls for the faces tagged 6: n (<= 4) planes [n][2d] (a point, then the unit
  * normal pointing from the wall into the body) and the distance threshold eps */
-int orc_mesh_set_contact(OrcMesh *M, int n, const double *planes, double eps) {
+int orc_mesh_set_contact(OrcMesh *M, int n, const real *planes, real eps) {
     if (!M || n < 0 || n > 4 || (n > 0 && !planes) || !(eps >= 0.0)) return ORC_ERR_ARG;
     int d = M->d;
     M->n_contact = n;

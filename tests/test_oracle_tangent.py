@@ -1,0 +1,105 @@
+"""The oracle's tangent build (lmood_tangent.cpp: the oracle's source compiled with dual numbers)
+as a CPU reference derivative of the step map (CPU).
+
+Pins: its value parts are bitwise those of the plain oracle (the same source, the same
+operations); its derivative parts equal central differences of the plain oracle's n-step map
+(step 1e-6, masks of the perturbed runs checked equal to the tangent run's, dt fixed so that
+the differenced map is the frozen-dt map the tangent differentiates) to 1e-6 relative, in 2D
+and 3D, with MOOD active and first-order cells in the mask, for directions of v0, mu and F0;
+and they are linear in the direction.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+FIELDS = ("x", "vp", "v", "F")
+
+
+def _case(name):
+    if name == "plain2d":
+        pb = W.plain2d(n=10)
+        pb.v *= 40.0
+        return pb
+    if name == "impact2d":
+        return W.impact2d(n=14)
+    pb = W.cube3d(n=3)
+    pb.v *= 6.0
+    return pb
+
+
+def _with_F(pb, rng):
+    d, nc = pb.mesh.dim, pb.mesh.n_cells
+    F = np.zeros((d * d, nc))
+    for a in range(d):
+        F[a * d + a] = 1.0
+    F += 0.01 * rng.standard_normal((d * d, nc))
+    mu = np.asarray(pb.mu, dtype=float) * (1.0 + 0.1 * rng.random(nc))
+    return dataclasses.replace(pb, F=F, mu=mu)
+
+
+def _plain(orc, pb, n, **prm):
+    o = orc.Oracle(pb, **prm)
+    masks = []
+    for _ in range(n):
+        o.step()
+        masks.append(o.get(orc.F_ORDER).astype(np.int8))
+    return {"x": o.get(orc.F_X), "vp": o.get(orc.F_VP), "v": o.get(orc.F_V), "F": o.get(orc.F_F)}, masks
+
+
+@pytest.mark.parametrize("name", ["plain2d", "impact2d", "cube3d"])
+def test_tangent_values_are_the_oracle(orc, name):
+    pb = _with_F(_case(name), np.random.default_rng(3))
+    n = 6
+    rng = np.random.default_rng(4)
+    t = orc.tangent(pb, n, dv=rng.standard_normal(pb.v.shape))
+    ref, masks = _plain(orc, pb, n)
+    for k in FIELDS:
+        assert np.array_equal(t[k], ref[k]), k
+    for s in range(n):
+        assert np.array_equal(t["masks"][s], masks[s]), s
+    assert (t["masks"] == 1).any(), "no first-order cell in the run"
+
+
+@pytest.mark.parametrize("name", ["plain2d", "impact2d", "cube3d"])
+def test_tangent_against_central_differences(orc, name):
+    rng = np.random.default_rng(11)
+    pb = _with_F(_case(name), rng)
+    n = 5
+    d, nc, npn = pb.mesh.dim, pb.mesh.n_cells, pb.mesh.n_nodes
+    dt = 0.5 * orc.Oracle(pb).dt
+    prm = {"dt_fixed": dt}
+    lam = {"x": rng.standard_normal((d, npn)), "vp": rng.standard_normal((d, npn)),
+           "v": rng.standard_normal((d, nc)), "F": rng.standard_normal((d * d, nc))}
+    dirs = {"v": rng.standard_normal((d, nc)), "mu": rng.standard_normal(nc) * pb.mu,
+            "F": rng.standard_normal((d * d, nc))}
+    h = 1e-6
+    for name_dir, delta in dirs.items():
+        t = orc.tangent(pb, n, **{"d" + name_dir: delta}, **prm)
+        assert (t["masks"] == 1).any() and (t["masks"] == 2).any(), "the mask must mix P1 and P0 cells"
+        ad = sum(float((t["d" + k] * lam[k]).sum()) for k in FIELDS)
+        runs = []
+        for sgn in (1.0, -1.0):
+            base = {"v": pb.v, "mu": pb.mu, "F": pb.F}[name_dir]
+            st, masks = _plain(orc, dataclasses.replace(pb, **{name_dir: base + sgn * h * delta}), n, **prm)
+            for s in range(n):
+                assert np.array_equal(masks[s], t["masks"][s]), f"mask changed under the perturbation at step {s}"
+            runs.append(st)
+        fd = sum(float(((runs[0][k] - runs[1][k]) * lam[k]).sum()) for k in FIELDS) / (2 * h)
+        assert abs(ad - fd) <= 1e-6 * max(abs(ad), abs(fd)), (name_dir, ad, fd)
+
+
+def test_tangent_is_linear_in_the_direction(orc):
+    rng = np.random.default_rng(5)
+    pb = _with_F(_case("cube3d"), rng)
+    a, b = rng.standard_normal(pb.v.shape), rng.standard_normal(pb.v.shape)
+    ta, tb = orc.tangent(pb, 4, dv=a), orc.tangent(pb, 4, dv=b)
+    tab = orc.tangent(pb, 4, dv=a + b)
+    for k in FIELDS:
+        np.testing.assert_allclose(tab["d" + k], ta["d" + k] + tb["d" + k], rtol=0,
+                                   atol=1e-11 * np.abs(tab["d" + k]).max())
+    t0 = orc.tangent(pb, 4)
+    for k in FIELDS:
+        assert not np.any(t0["d" + k]), k
