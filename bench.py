@@ -1,13 +1,16 @@
 #!/usr/bin/env python
-"""Benchmark: cell-steps/s of the full ADER-MOOD step (FP64) on the 2D impact workload
-(unit square of 999,698 seeded Delaunay triangles, rigid slip wall at x = 0, v = (-0.1, 0)).
+"""Benchmark: cell-steps/s of the full ADER-MOOD step (FP64) on the 3D bending column (a
+1 x 1 x 6 box of 5,989,500 seeded tetrahedra, base clamped, lateral v = 0.1 (z/6)^2), the
+largest single-mesh configuration; the 2D impact (999,698 triangles against a rigid slip wall)
+is timed beside it, in an early window and in a mid-run window of its shock problem.
 
 One step = one pass of the whole hot path: corner geometry, least-squares reconstruction,
 ADER predictor and corner packets, nodal solver with BCs, forces and cell update, MOOD
 detection and first-order recomputation, next dt. Inputs are resident in HBM before the
-timed region; the working set (~0.5 GB) is larger than L2, so no flush is needed.
+timed region; the working set (~5 GB for the column, ~0.5 GB for the impact) is larger than
+L2, so no flush is needed.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload column3d|impact2d|cube3d]
 
 Under torchrun (N > 1) every rank advances its own replica on its GPU (the path does not
 shard across GPUs here); value = cell-steps of all ranks / max time over ranks.
@@ -15,6 +18,7 @@ shard across GPUs here); value = cell-steps of all ranks / max time over ranks.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -82,18 +86,37 @@ def kernel_bytes(dim: int, nc: int, npn: int, nnz: int) -> dict:
     return {"moments": moments, "predict": predict, "nodes": nodes, "update": update, "finalize": finalize}
 
 
-# FP64 floating-point operations per cell executed by each full-mesh kernel launch on the 2D
-# workload: ncu counts (dadd + dmul + 2 dfma thread instructions) of the current kernels,
-# divided by the cell count; they include the FP64 expansions of division, sqrt, log, cbrt.
-# Re-measured whenever a kernel changes (profiles/ holds the capture); None = not measured
-# for the current kernel.
-FP64_FLOP_PER_CELL = {"predict": 838.0, "update": 366.0, "nodes": 31.1, "moments": 120.0}
-# FP64 thread instructions per cell (dfma + dadd + dmul) from the same capture: the pipe's
-# issue rate, compared with DGEMM's (one DFMA = 2 FLOP per instruction), shows how busy the
-# pipe is independently of the operation mix.
-FP64_INSTR_PER_CELL = {"predict": 518.0, "update": 238.0, "nodes": 25.0, "moments": 75.0}
-# DRAM bytes (read + write) per full launch from the same ncu capture, or None.
-TRAFFIC_PER_LAUNCH = {"predict": 292.70e6, "update": 350.80e6, "nodes": 182.10e6, "moments": 150.70e6}
+# Per dimension, from one ncu capture of the current kernels (profiles/ holds its summary):
+#  - FP64 floating-point operations per cell executed by each full-mesh kernel launch: ncu
+#    counts of dadd + dmul + 2 dfma thread instructions divided by the cell count (they include
+#    the FP64 expansions of division, sqrt, log, cbrt);
+#  - FP64 thread instructions per cell (dfma + dadd + dmul): the pipe's issue rate, compared with
+#    DGEMM's (one DFMA = 2 FLOP per instruction), shows how busy the pipe is independently of the
+#    operation mix;
+#  - DRAM bytes (read + write) per full launch per cell (the capture's traffic / its cells).
+# COUNTS_SRC is the digest of the kernel sources the capture was taken on: when the sources
+# differ the bench line says so ("counts_stale") and gives no traffic.
+# 2D: impact2d (999,698 triangles), profiles/k_predict_impact2d.md; 3D: a reduced column
+# (30 x 30 x 180 cubes, 972,000 tetrahedra), profiles/column3d_kernels.md (the full column's
+# traffic scales with the cells: every per-cell array is read and written once per launch).
+FP64_FLOP_PER_CELL = {2: {"predict": 838.0, "update": 366.0, "nodes": 31.1, "moments": 120.0},
+                      3: {"predict": 2517.0, "update": 876.0, "nodes": 48.5, "moments": 408.0}}
+FP64_INSTR_PER_CELL = {2: {"predict": 518.0, "update": 238.0, "nodes": 25.0, "moments": 75.0},
+                       3: {"predict": 1503.0, "update": 560.0, "nodes": 44.2, "moments": 240.0}}
+TRAFFIC_PER_CELL = {2: {"predict": 292.70e6 / 999698, "update": 350.80e6 / 999698, "nodes": 182.10e6 / 999698,
+                        "moments": 150.70e6 / 999698},
+                    3: {"predict": 504.1, "update": 609.8, "nodes": 409.6, "moments": 198.3}}
+COUNTS_SRC = {2: "3a3f8158403aca92", 3: "3a3f8158403aca92"}
+KERNEL_SOURCES = ("lmood_kernels.cuh", "lmood_dev.cuh", "lmood_ops_impl.cuh")
+
+
+def kernel_source_digest() -> str:
+    """sha256 (first 16 hex digits) of the forward kernels' sources"""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2104_02139_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def fp64_peak_tflops(device) -> float:
@@ -157,14 +180,16 @@ class Clocks:
 
 
 def cpu_baseline(pb, budget_s: float = 12.0) -> dict:
-    """The oracle as it stands on the host cores: the first steps of the same workload."""
+    """The oracle as it stands on the host cores: the first steps of the same workload, as
+    many as the budget is expected to hold from the mean step time so far (at least one;
+    set-up excluded)."""
     import oracle as O
     O.build()
     t0 = time.perf_counter()
     o = O.Oracle(pb)
     setup = time.perf_counter() - t0
     steps, t = 0, 0.0
-    while steps < 2 or (t < budget_s and steps < 50):
+    while steps < 1 or (t + t / steps <= budget_s and steps < 50):
         s0 = time.perf_counter()
         o.step()
         t += time.perf_counter() - s0
@@ -242,6 +267,7 @@ def run_ours(args, rank, local, ws, dist):
     tuned = None if args.no_autotune else sim.autotune()
     for _ in range(2):  # re-capture the step graphs with the chosen launch shapes
         sim.step()
+    first_timed = sim.info.step
     sim.timing(True)
     clocks = Clocks(local)
     barrier(dist)
@@ -275,15 +301,20 @@ def run_ours(args, rank, local, ws, dist):
     fp64_peak = FP64_PEAK_TFLOPS  # an ALU-bound path: the peak derived from unit counts and clock
     hbm = {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
            "algorithmic_bytes_per_launch": kb[dom], "peak_source": how}
-    fpc = FP64_FLOP_PER_CELL.get(dom) if pb.mesh.dim == 2 else None
+    dim = pb.mesh.dim
+    fpc = FP64_FLOP_PER_CELL[dim].get(dom)
+    digest = kernel_source_digest()
+    stale = COUNTS_SRC[dim] is not None and COUNTS_SRC[dim] != digest
     if fpc:
         tf = fpc * N / (dom_ms / 1e3) / 1e12
+        tpc = TRAFFIC_PER_CELL[dim].get(dom)
         roof = {"bound": "alu", "kernel": dom, "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": tf / fp64_peak, "traffic": TRAFFIC_PER_LAUNCH.get(dom),
+                "frac": tf / fp64_peak, "traffic": None if (stale or tpc is None) else tpc * N,
                 "peak_source": "derived: 152 SMs x 2 DFMA lanes/clk x 2 FLOP x 2.07 GHz max SM clock",
                 "dgemm_measured": fp64_meas, "frac_of_dgemm": (tf / fp64_meas) if fp64_meas else None,
-                "fp64_flop_per_cell": fpc, "ms_per_launch": dom_ms, "hbm": hbm}
-        ipc = FP64_INSTR_PER_CELL.get(dom)
+                "fp64_flop_per_cell": fpc, "ms_per_launch": dom_ms, "hbm": hbm,
+                "counts_src": COUNTS_SRC[dim], "kernel_src": digest, "counts_stale": stale}
+        ipc = FP64_INSTR_PER_CELL[dim].get(dom)
         if ipc:
             gi = ipc * N / (dom_ms / 1e3) / 1e9
             roof["fp64_issue"] = {"achieved": gi, "peak": fp64_peak * 1e3 / 2, "unit": "G FP64 instr/s",
@@ -319,6 +350,12 @@ def run_ours(args, rank, local, ws, dist):
         e2e = {"value": ws * N * k2 / el, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "steps": k2}
 
+    impact = None
+    if not args.no_impact and args.workload != "impact2d":
+        sim.close()
+        sim.mesh.close()
+        impact = run_impact_windows(L, W, torch, args)
+
     batched = None
     if not args.no_batched:
         batched = run_batched(L, W, torch, local, value / ws, args)
@@ -335,7 +372,7 @@ def run_ours(args, rank, local, ws, dist):
 
     cb = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(make_workload(args.workload))
+        cb = cpu_baseline(pb)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -343,11 +380,60 @@ def run_ours(args, rank, local, ws, dist):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOADS[args.workload], "cells": N, "nodes": info["n_nodes"],
                            "lsq_pairs": info["stencil_nnz"], "parallelism": f"replicas x{ws}",
-                           "l2": "working set > L2 (no flush)", "troubled_cells_in_timed_steps": troubled},
+                           "l2": "working set > L2 (no flush)", "troubled_cells_in_timed_steps": troubled,
+                           "troubled_frac": troubled / (N * args.steps), "first_timed_step": first_timed},
                 "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": ck, "e2e": e2e,
-                "cpu_baseline": cb, "batched": batched, "variants": variants, "adjoint": adjoint,
+                "cpu_baseline": cb, "impact2d_windows": impact, "batched": batched, "variants": variants,
+                "adjoint": adjoint,
                 "launch": None if tuned is None else {k: v["chosen"] for k, v in tuned.items()}}
         print(json.dumps(line), flush=True)
+
+
+def run_impact_windows(L, W, torch, args) -> dict:
+    """The 2D impact (999,698 triangles, the shock problem of the configurations) in two timed
+    windows of K graph-captured steps each: early (from step 8, as the front forms) and mid-run
+    (from step args.midrun_from, with the compression front and its troubled band established).
+    Per window: cell-steps/s, the troubled fraction (cells sent down the cascade per cell-step),
+    the first-order fraction, MOOD rounds per step and the MOOD loop's share of the step time
+    (CUDA events around each stage)."""
+    pb = W.impact2d()
+    N = pb.mesh.n_cells
+    stream = torch.cuda.Stream()
+    sim = L.simulation(pb, stream=stream.cuda_stream, graph=0 if args.host_mode else 1)
+    k = max(10, args.steps)
+    out, taken = {}, 0
+    for name, first in (("early", 8), ("mid_run", args.midrun_from)):
+        while taken < first:
+            sim.step()
+            taken += 1
+        sim.timing(True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tr = p0 = it = 0
+        for _ in range(k):
+            info = sim.step()
+            tr += info.n_troubled
+            p0 += info.n_p0
+            it += info.mood_iters
+        e1.record(stream)
+        torch.cuda.synchronize()
+        taken += k
+        kt = sim.timing_read()
+        sim.timing(False)
+        ms = e0.elapsed_time(e1) / k
+        stage_ms = sum(v[0] for v in kt.values())
+        out[name] = {"first_step": first, "steps": k, "ms_per_step": ms, "value": N / (ms / 1e3), "unit": UNIT,
+                     "troubled_frac": tr / (N * k), "p0_frac": p0 / (N * k), "mood_rounds_per_step": it / k,
+                     "mood_ms_per_step": kt["mood"][0] / k,
+                     "mood_share": kt["mood"][0] / stage_ms if stage_ms > 0 else None,
+                     "t": float(sim.info.t)}
+    sim.close()
+    sim.mesh.close()
+    out["cells"] = N
+    out["what"] = ("impact2d in two windows of its run: troubled_frac = cells sent down the cascade per "
+                   "cell-step (the paper's 'troubled cells per step'), mood_share = MOOD loop time / step time")
+    return out
 
 
 def run_variants(L, W, torch, pb, plain_value, args) -> dict:
@@ -391,6 +477,21 @@ def run_variants(L, W, torch, pb, plain_value, args) -> dict:
             out[name]["vs_plain"] = v / plain_value
         sim.close()
         sim.mesh.close()
+    # the 40 x 40 configuration (3,042 triangles) as configured: 200 steps in one lmood_run,
+    # chained on the device (one host synchronisation for the run)
+    sim = L.simulation(small, stream=stream.cuda_stream)
+    sim.run(5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = sim.run(200)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    out["small_plain2d_run200_chained"] = {"cells": small.mesh.n_cells, "ms_per_step": el * 1e3 / 200,
+                                           "us_per_step": el * 1e6 / 200, "value": small.mesh.n_cells * 200 / el,
+                                           "unit": UNIT, "steps": 200, "host_syncs": info.syncs,
+                                           "timer": "host wall clock around lmood_run (includes its one sync)"}
+    sim.close()
+    sim.mesh.close()
     return out
 
 
@@ -512,8 +613,10 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="impact2d",
-                    help="impact2d (the metric's configuration, default) or a 3D configuration")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="column3d",
+                    help="column3d (the largest single-mesh configuration, default), impact2d or cube3d")
+    ap.add_argument("--no-impact", action="store_true", help="skip the impact2d early / mid-run windows")
+    ap.add_argument("--midrun-from", type=int, default=400, help="first step of the impact2d mid-run window")
     ap.add_argument("--host-mode", action="store_true",
                     help="host-driven MOOD rounds instead of graph-captured steps (same kernels; for profilers)")
     ap.add_argument("--no-fp64-peak", action="store_true", help="skip the DGEMM FP64 peak measurement")
@@ -527,7 +630,8 @@ def main():
     ap.add_argument("--case-adjoint", type=int, default=0,
                     help="with --case: then record this many steps on a tape and run its reverse pass once")
     ap.add_argument("--case-n", type=int, default=0,
-                    help="with --case: a smaller impact2d (lattice n x n) or cube3d (n^3 cubes) for multi-pass profiler captures")
+                    help="with --case: a smaller impact2d (lattice n x n), cube3d (n^3 cubes) or column3d "
+                         "(n x n x 6n cubes) for multi-pass profiler captures")
     ap.add_argument("--case-ckpt", type=int, default=0,
                     help="with --case-adjoint: the tape's checkpoint interval (0: store mode)")
     args = ap.parse_args()
@@ -537,7 +641,10 @@ def main():
         import workloads as W
         L.build()
         if args.case_n:
-            pb = {"impact2d": W.impact2d, "cube3d": W.cube3d}[args.workload](n=args.case_n)
+            if args.workload == "column3d":
+                pb = W.column3d(nxy=args.case_n, nz=6 * args.case_n)
+            else:
+                pb = {"impact2d": W.impact2d, "cube3d": W.cube3d}[args.workload](n=args.case_n)
         else:
             pb = make_workload(args.workload)
         sim = L.simulation(pb, graph=0 if args.host_mode else 1)
