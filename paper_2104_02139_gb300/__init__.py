@@ -40,7 +40,8 @@ class Params(C.Structure):
 class StepInfo(C.Structure):
     _fields_ = [("t", C.c_double), ("dt_used", C.c_double), ("dt_next", C.c_double), ("step", C.c_int64),
                 ("n_troubled", C.c_int32), ("n_p0", C.c_int32), ("mood_iters", C.c_int32),
-                ("n_parachute", C.c_int32), ("n_p0_eps", C.c_int32), ("n_lim", C.c_int32)]
+                ("n_parachute", C.c_int32), ("n_p0_eps", C.c_int32), ("n_lim", C.c_int32),
+                ("syncs", C.c_int32)]
 
 
 _lib = None
@@ -115,7 +116,8 @@ def _is_torch(a) -> bool:
 
 
 def _numel(shape) -> int:
-    return int(np.prod(shape, dtype=np.int64))
+    """element count of a field's shape; None (an id the library rejects without copying): any"""
+    return -1 if shape is None else int(np.prod(shape, dtype=np.int64))
 
 
 def _out_buffer(a, shape, what: str):
@@ -128,7 +130,7 @@ def _out_buffer(a, shape, what: str):
         if a.dtype != np.float64 or not a.flags.c_contiguous or not a.flags.writeable:
             raise ValueError(f"{what}: host destination must be a writeable C-contiguous float64 array "
                              f"(got {a.dtype}, contiguous={a.flags.c_contiguous})")
-        if a.size != n:
+        if n >= 0 and a.size != n:
             raise ValueError(f"{what}: destination has {a.size} elements, the field needs {n} {tuple(shape)}")
         return a.ctypes.data, 0
     if _is_torch(a):
@@ -136,7 +138,7 @@ def _out_buffer(a, shape, what: str):
         if a.dtype != torch.float64 or not a.is_cuda or not a.is_contiguous():
             raise ValueError(f"{what}: device destination must be a contiguous float64 CUDA tensor "
                              f"(got {a.dtype}, cuda={a.is_cuda}, contiguous={a.is_contiguous()})")
-        if a.numel() != n:
+        if n >= 0 and a.numel() != n:
             raise ValueError(f"{what}: destination has {a.numel()} elements, the field needs {n} {tuple(shape)}")
         return a.data_ptr(), 1
     raise TypeError(f"{what}: destination must be a numpy array or a torch CUDA tensor, not {type(a).__name__}")
@@ -154,11 +156,11 @@ def _in_buffer(a, shape, what: str):
         if not a.is_cuda:
             raise ValueError(f"{what}: a torch source must be a CUDA tensor (host data: pass numpy)")
         t = a if (a.dtype == torch.float64 and a.is_contiguous()) else a.to(torch.float64).contiguous()
-        if t.numel() != n:
+        if n >= 0 and t.numel() != n:
             raise ValueError(f"{what}: source has {t.numel()} elements, the field needs {n} {tuple(shape)}")
         return t, t.data_ptr(), 1, t is not a
     h = np.ascontiguousarray(a, dtype=np.float64)
-    if h.size != n:
+    if n >= 0 and h.size != n:
         raise ValueError(f"{what}: source has {h.size} elements, the field needs {n} {tuple(shape)}")
     return h, h.ctypes.data, 0, False
 
@@ -290,7 +292,7 @@ class State:
     def shape(self, field: int) -> tuple:
         d, nc, npn, nv = self.mesh.dim, self.mesh.n_cells, self.mesh.n_nodes, self.mesh.dim + 1
         if not 0 <= field <= FIELD_DT:
-            return (1,)  # the library rejects the id
+            return None  # the library rejects the id and copies nothing
         return {FIELD_X: (d, npn), FIELD_VP: (d, npn), FIELD_VSTAR: (d, npn), FIELD_V: (d, nc), FIELD_E: (nc,),
                 FIELD_F: (d * d, nc), FIELD_TAU: (nc,), FIELD_ORDER: (nc,), FIELD_MASS: (nc,),
                 FIELD_PKM: (d * (d + 1) // 2, nv, nc), FIELD_PKR: (d, nv, nc), FIELD_DT: (self.mesh.n_inst,)}[field]
@@ -299,7 +301,7 @@ class State:
         """Host copy as numpy (out None or a numpy array), or into a torch CUDA tensor; out
         must be float64, contiguous and of the field's size (checked before the copy)."""
         if out is None:
-            out = np.empty(self.shape(field))
+            out = np.empty(self.shape(field) or (1,))
         ptr, dev = _out_buffer(out, self.shape(field), "get")
         _check(lib().lmood_get(self.h, field, C.c_void_p(ptr), dev))
         return out
