@@ -108,6 +108,8 @@ typedef struct {
     int32_t n_parachute; /* P0 candidates that were not computable (then the status is an error) */
     int32_t n_p0_eps;    /* P0 cells accepted with a negative specific internal energy */
     int32_t n_lim;       /* cells advanced with Barth-Jespersen limited slopes (cascade 3) */
+    int32_t syncs;       /* host synchronisations of the mesh stream the call made (lmood_run:
+                            for all its steps; 1 when its steps were chained on the device) */
 } lmood_step_info;
 
 /* Field ids for lmood_get / lmood_set (layout, entity count n, components k). */
@@ -221,8 +223,14 @@ lmood_status lmood_state_destroy(lmood_state s);
  */
 lmood_status lmood_step(lmood_state s, lmood_step_info *info);
 
-/* nsteps calls of lmood_step; stops at the first error. last (may be NULL) gets the report
- * of the last step taken. */
+/* nsteps steps, exactly as nsteps calls of lmood_step (bitwise the same state and reports);
+ * stops at the first error, which it returns with the state after the last accepted step.
+ * last (may be NULL) gets the report of the last step taken (on an error: of the failing
+ * step). With params.graph = 1 and timing off, the steps are chained on the device: each
+ * step's graph runs behind a device-side gate that skips it once a step of the run has
+ * failed, all nsteps are launched back to back and the call synchronises once, at the end
+ * (last->syncs = 1); otherwise (and where the device cannot build the chained graph) it calls
+ * lmood_step nsteps times. */
 lmood_status lmood_run(lmood_state s, int64_t nsteps, lmood_step_info *last);
 
 /*

@@ -554,9 +554,12 @@ static void state_free(lmood_state s) {
     for (int p = 0; p < 2; ++p) {
         if (s->gexec[p]) cudaGraphExecDestroy(s->gexec[p]);
         if (s->graph[p]) cudaGraphDestroy(s->graph[p]);
+        if (s->cexec[p]) cudaGraphExecDestroy(s->cexec[p]);
+        if (s->cgraph[p]) cudaGraphDestroy(s->cgraph[p]);
         for (cudaEvent_t e : s->gev[p])
             if (e) cudaEventDestroy(e);
     }
+    if (s->h_run) cudaFreeHost(s->h_run);
     if (s->body_st) cudaStreamDestroy(s->body_st);
     if (s->cap_st) cudaStreamDestroy(s->cap_st);
     if (s->aux_st) cudaStreamDestroy(s->aux_st);
@@ -756,13 +759,89 @@ static PersistArgs persist_args(lmood_state s) {
     return a;
 }
 
-static lmood_status build_graph(lmood_state s, int par) {
+// zero n ints (a kernel instead of a memset node: it may sit in a conditional node's body)
+__global__ static void k_zero_ints(int *p, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0;
+}
+
+// Enqueue one whole step on st, which is capturing into graph G: the full-mesh kernels, the
+// MOOD loop as a conditional while node of G with handle h (created on G before the capture
+// began; its body is captured on body_st; graph = 3: one cooperative kernel node instead),
+// next dt and the step report in d_report. ev (nullptr: none) gets external event records
+// around the stages for the per-stage timing; in_body: G is the body of a conditional node
+// (the counters are then zeroed by a kernel rather than a memset node).
+static cudaError_t capture_step(lmood_state s, cudaGraph_t G, cudaGraphConditionalHandle h, cudaStream_t st,
+                                cudaEvent_t *ev, bool in_body, const char **where) {
     lmood_mesh M = s->M;
     const Ops &op = *M->ops;
     const Geo &g = M->geo;
-    cudaStream_t st = s->cap_st;
     const Fld &f = s->f;
     const int N = (int)M->nc, Np = (int)M->np;
+    auto mark = [&](int i) {
+        if (ev) cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
+    };
+    cudaError_t e = cudaSuccess;
+    if (in_body)
+        k_zero_ints<<<1, 32, 0, st>>>(f.cnt, CNT_N);
+    else
+        cudaMemsetAsync(f.cnt, 0, CNT_N * sizeof(int), st);
+    op.ctl_reset(s->ctl, st);
+    mark(0);
+    op.moments(g, f, st);
+    mark(6);
+    op.predict(g, f, s->kp, nullptr, nullptr, N, st);
+    mark(1);
+    op.nodes(g, f, nullptr, nullptr, Np, 0, st);
+    mark(2);
+    op.update(g, f, s->kp, nullptr, nullptr, N, s->tl[0], f.cnt + CNT_T0, st);
+    mark(3);
+    *where = "capture";
+    if (s->prm.graph == 3) {
+        // the MOOD loop as one cooperative kernel node with grid barriers
+        *where = "cooperative MOOD kernel node";
+        e = cudaMemsetAsync(s->bar, 0, 4 * sizeof(unsigned int), st);
+        if (e == cudaSuccess) e = op.mood_persistent(g, f, s->kp, persist_args(s), st);
+    } else {
+        op.loop_cond(h, f, s->ctl, st);
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+        cudaGraphNode_t wnode = nullptr;
+        cudaGraphNodeParams cp = {};
+        if (e == cudaSuccess) {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            e = cudaGraphAddNode(&wnode, G, deps, nullptr, ndeps, &cp);
+        }
+        if (e == cudaSuccess)
+            e = cudaStreamUpdateCaptureDependencies(st, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e == cudaSuccess) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(s->body_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                enqueue_mood_round(s, f, 0, N, s->body_st);
+                enqueue_mood_round(s, f, 1, N, s->body_st);
+                op.loop_cond(h, f, s->ctl, s->body_st);
+                cudaGraph_t bg = nullptr;
+                e = cudaStreamEndCapture(s->body_st, &bg);
+            }
+        }
+    }
+    if (e == cudaSuccess) {
+        mark(4);
+        op.dt_init(f, s->kp, M->n_inst, 0, st);
+        op.finalize(g, f, s->kp, st);
+        op.report(f, s->ctl, s->d_report, st);
+        mark(5);
+    }
+    return e;
+}
+
+static lmood_status build_graph(lmood_state s, int par) {
+    cudaStream_t st = s->cap_st;
     cudaGraph_t G = nullptr;
     LM_CUDA(cudaGraphCreate(&G, 0));
     s->graph[par] = G;
@@ -771,60 +850,9 @@ static lmood_status build_graph(lmood_state s, int par) {
     for (auto &e : s->gev[par]) LM_CUDA(cudaEventCreate(&e));
     cudaEvent_t *ev = s->gev[par];
     LM_CUDA(cudaStreamBeginCaptureToGraph(st, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    cudaMemsetAsync(f.cnt, 0, CNT_N * sizeof(int), st);
-    op.ctl_reset(s->ctl, st);
-    cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
-    op.moments(g, f, st);
-    cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
-    op.predict(g, f, s->kp, nullptr, nullptr, N, st);
-    cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
-    op.nodes(g, f, nullptr, nullptr, Np, 0, st);
-    cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
-    op.update(g, f, s->kp, nullptr, nullptr, N, s->tl[0], f.cnt + CNT_T0, st);
-    cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
-    cudaError_t e = cudaSuccess;
     const char *where = "capture";
-    if (s->prm.graph == 3) {
-        // the MOOD loop as one cooperative kernel node with grid barriers
-        where = "cooperative MOOD kernel node";
-        e = cudaMemsetAsync(s->bar, 0, 4 * sizeof(unsigned int), st);
-        if (e == cudaSuccess) e = op.mood_persistent(g, f, s->kp, persist_args(s), st);
-    } else {
-    op.loop_cond(h, f, s->ctl, st);
-    cudaStreamCaptureStatus cs;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t ndeps = 0;
-    e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
-    cudaGraphNode_t wnode = nullptr;
-    cudaGraphNodeParams cp = {};
-    if (e == cudaSuccess) {
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        e = cudaGraphAddNode(&wnode, G, deps, nullptr, ndeps, &cp);
-    }
-    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
-    if (e == cudaSuccess) {
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        e = cudaStreamBeginCaptureToGraph(s->body_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            enqueue_mood_round(s, f, 0, N, s->body_st);
-            enqueue_mood_round(s, f, 1, N, s->body_st);
-            op.loop_cond(h, f, s->ctl, s->body_st);
-            cudaGraph_t bg = nullptr;
-            e = cudaStreamEndCapture(s->body_st, &bg);
-        }
-    }
-    }
-    if (e == cudaSuccess) {
-        cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
-        op.dt_init(f, s->kp, M->n_inst, 0, st);
-        op.finalize(g, f, s->kp, st);
-        op.report(f, s->ctl, s->d_report, st);
-        cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
-        cudaMemcpyAsync(s->h_report, s->d_report, sizeof(Report), cudaMemcpyDeviceToHost, st);
-    }
+    cudaError_t e = capture_step(s, G, h, st, ev, false, &where);
+    if (e == cudaSuccess) cudaMemcpyAsync(s->h_report, s->d_report, sizeof(Report), cudaMemcpyDeviceToHost, st);
     cudaGraph_t out = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(st, &out);
     if (e == cudaSuccess && e2 != cudaSuccess) {
@@ -840,6 +868,120 @@ static lmood_status build_graph(lmood_state s, int par) {
         return fail(LMOOD_ERR_CUDA, std::string("lmood_step: building the step graph failed (") + where +
                                         "): " + cudaGetErrorString(e));
     }
+    return LMOOD_OK;
+}
+
+// chained runs: the gate of a step (run it unless an earlier step of the run failed) and
+// the bookkeeping after it (accepted: count it and advance t; refused: stop the run)
+__global__ static void k_run_gate(cudaGraphConditionalHandle h, const RunCtl *rc) {
+    cudaGraphSetConditional(h, rc->abort == 0 ? 1u : 0u);
+}
+
+__global__ static void k_run_account(RunCtl *rc, const Report *r) {
+    rc->last = *r;
+    rc->ran += 1;
+    if (r->err == 0 && r->n_para == 0) {
+        rc->done += 1;
+        rc->t += r->dt_used;
+        rc->mood_pairs += (r->mood_iters + 1) / 2;
+    } else {
+        rc->abort = 1;
+    }
+}
+
+// The chained step graph of the state's current buffer parity: k_run_gate, then an IF node
+// whose body is the whole step (capture_step) followed by k_run_account.
+static lmood_status build_chain_graph(lmood_state s, int par) {
+    cudaStream_t st = s->cap_st;
+    cudaGraph_t G = nullptr;
+    LM_CUDA(cudaGraphCreate(&G, 0));
+    s->cgraph[par] = G;
+    cudaGraphConditionalHandle hif{};
+    LM_CUDA(cudaGraphConditionalHandleCreate(&hif, G, 0, cudaGraphCondAssignDefault));
+    const char *where = "gate capture";
+    cudaError_t e = cudaStreamBeginCaptureToGraph(st, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    cudaGraphNodeParams cp = {};
+    if (e == cudaSuccess) {
+        k_run_gate<<<1, 1, 0, st>>>(hif, s->d_run);
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+        cudaGraphNode_t inode = nullptr;
+        if (e == cudaSuccess) {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = hif;
+            cp.conditional.type = cudaGraphCondTypeIf;
+            cp.conditional.size = 1;
+            where = "IF node";
+            e = cudaGraphAddNode(&inode, G, deps, nullptr, ndeps, &cp);
+        }
+        if (e == cudaSuccess)
+            e = cudaStreamUpdateCaptureDependencies(st, &inode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        cudaGraph_t gout = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(st, &gout);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraphConditionalHandle hw{};
+        where = "while handle in the IF body";
+        e = cudaGraphConditionalHandleCreate(&hw, body, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            e = capture_step(s, body, hw, st, nullptr, true, &where);
+            if (e == cudaSuccess) k_run_account<<<1, 1, 0, st>>>(s->d_run, s->d_report);
+            cudaGraph_t bout = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(st, &bout);
+            if (e == cudaSuccess && e2 != cudaSuccess) {
+                e = e2;
+                where = "end of the IF body's capture";
+            }
+        }
+    }
+    if (e == cudaSuccess) {
+        where = "instantiation";
+        e = cudaGraphInstantiate(&s->cexec[par], G, 0);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LMOOD_ERR_CUDA, std::string("lmood_run: building the chained step graph failed (") + where +
+                                        "): " + cudaGetErrorString(e));
+    }
+    return LMOOD_OK;
+}
+
+static void chain_destroy(lmood_state s) {
+    for (int p = 0; p < 2; ++p) {
+        if (s->cexec[p]) cudaGraphExecDestroy(s->cexec[p]);
+        if (s->cgraph[p]) cudaGraphDestroy(s->cgraph[p]);
+        s->cexec[p] = nullptr;
+        s->cgraph[p] = nullptr;
+    }
+    s->chain_built = false;
+}
+
+static lmood_status ensure_chain(lmood_state s) {
+    if (s->chain_built) return LMOOD_OK;
+    if (!s->body_st) LM_CUDA(cudaStreamCreateWithFlags(&s->body_st, cudaStreamNonBlocking));
+    if (!s->cap_st) LM_CUDA(cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking));
+    if (!s->d_run) {
+        lmood_status r = s->mem.alloc((void **)&s->d_run, sizeof(RunCtl));
+        if (r) return r;
+    }
+    if (!s->h_run) LM_CUDA(cudaMallocHost((void **)&s->h_run, sizeof(RunCtl)));
+    LM_CUDA(cudaStreamSynchronize(s->M->st));
+    for (int k = 0; k < 2; ++k) {
+        const int par = s->parity;
+        lmood_status r = build_chain_graph(s, par);
+        swap_state(s);
+        if (r) {
+            if (k == 0) swap_state(s);
+            chain_destroy(s);
+            return r;
+        }
+    }
+    s->chain_built = true;
     return LMOOD_OK;
 }
 
@@ -862,8 +1004,9 @@ static lmood_status ensure_graphs(lmood_state s) {
     return LMOOD_OK;
 }
 
-static lmood_status finish_step(lmood_state s, const Report &rep, lmood_step_info *info) {
+static lmood_status finish_step(lmood_state s, const Report &rep, lmood_step_info *info, int syncs) {
     lmood_step_info in{};
+    in.syncs = syncs;
     in.n_troubled = rep.n_troubled;
     in.mood_iters = rep.mood_iters;
     in.n_p0 = rep.n_p0;
@@ -928,7 +1071,7 @@ static lmood_status step_graph(lmood_state s, lmood_step_info *info) {
     else
         s->klaunch[LMOOD_K_MOOD] += 2 + 13 * ((rep.mood_iters + 1) / 2);  // ctl reset, first condition, bodies
     s->klaunch[LMOOD_K_FINALIZE] += 3;
-    return finish_step(s, rep, info);
+    return finish_step(s, rep, info, 1);
 }
 
 static lmood_status step_host(lmood_state s, lmood_step_info *info) {
@@ -947,6 +1090,7 @@ static lmood_status step_host(lmood_state s, lmood_step_info *info) {
     LM_CUDA(cudaMemcpyAsync(s->h_cnt, f.cnt, CNT_N * sizeof(int), cudaMemcpyDeviceToHost, st));
     lmood_status r = sync_check(s, "lmood_step");
     if (r) return r;
+    int syncs = 1;
     timing_drain(s);
     int cur = 0;
     int nT = s->h_cnt[CNT_T0];
@@ -955,6 +1099,7 @@ static lmood_status step_host(lmood_state s, lmood_step_info *info) {
         LM_CUDA(cudaMemcpyAsync(s->h_cnt, f.cnt, CNT_N * sizeof(int), cudaMemcpyDeviceToHost, st));
         LM_CUDA(cudaMemcpyAsync(s->h_report, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         if ((r = sync_check(s, "lmood_step (MOOD)"))) return r;
+        ++syncs;
         timing_drain(s);
         if (reinterpret_cast<const Ctl *>(s->h_report)->err) break;
         cur ^= 1;
@@ -968,7 +1113,7 @@ static lmood_status step_host(lmood_state s, lmood_step_info *info) {
     LM_CUDA(cudaMemcpyAsync(s->h_report, s->d_report, sizeof(Report), cudaMemcpyDeviceToHost, st));
     if ((r = sync_check(s, "lmood_step (finalize)"))) return r;
     timing_drain(s);
-    return finish_step(s, *s->h_report, info);
+    return finish_step(s, *s->h_report, info, syncs + 1);
 }
 
 // the whole step as one cooperative launch (params.graph = 2)
@@ -990,7 +1135,7 @@ static lmood_status step_persistent(lmood_state s, lmood_step_info *info) {
     timing_drain(s);
     if (s->h_cnt[0] != 0)
         return fail(LMOOD_ERR_TIMEOUT, "lmood_step (persistent): a grid barrier wait gave up; the state is unchanged");
-    return finish_step(s, *s->h_report, info);
+    return finish_step(s, *s->h_report, info, 1);
 }
 
 extern "C" lmood_status lmood_step(lmood_state s, lmood_step_info *info) {
@@ -1000,13 +1145,76 @@ extern "C" lmood_status lmood_step(lmood_state s, lmood_step_info *info) {
     return s->prm.graph ? step_graph(s, info) : step_host(s, info);
 }
 
+// nsteps chained step graphs launched back to back, one synchronisation at the end: each
+// step runs only if every earlier step of the run was accepted (k_run_gate), and the state
+// then holds the last accepted step, exactly as after that many lmood_step calls.
+static lmood_status run_chained(lmood_state s, int64_t nsteps, lmood_step_info *last) {
+    lmood_status r = ensure_chain(s);
+    if (r) return r;
+    cudaStream_t st = s->M->st;
+    RunCtl init{};
+    init.t = s->t;
+    *s->h_run = init;
+    LM_CUDA(cudaMemcpyAsync(s->d_run, s->h_run, sizeof(RunCtl), cudaMemcpyHostToDevice, st));
+    const int par0 = s->parity;
+    for (int64_t i = 0; i < nsteps; ++i) LM_CUDA(cudaGraphLaunch(s->cexec[(par0 + i) & 1], st));
+    LM_CUDA(cudaMemcpyAsync(s->h_run, s->d_run, sizeof(RunCtl), cudaMemcpyDeviceToHost, st));
+    if ((r = sync_check(s, "lmood_run (chained steps)"))) return r;
+    const RunCtl rc = *s->h_run;
+    s->klaunch[LMOOD_K_FINALIZE] += nsteps + 4 * (int64_t)rc.ran;  // gates; dt_init, finalize, report, account
+    s->klaunch[LMOOD_K_MOMENTS] += rc.ran;
+    s->klaunch[LMOOD_K_PREDICT] += rc.ran;
+    s->klaunch[LMOOD_K_NODES] += rc.ran;
+    s->klaunch[LMOOD_K_UPDATE] += rc.ran;
+    s->klaunch[LMOOD_K_MOOD] += 3 * (int64_t)rc.ran + 13 * (int64_t)rc.mood_pairs;
+    // the accepted steps, as lmood_step would have left the state after each
+    for (int i = 0; i < rc.done; ++i) swap_state(s);
+    if (rc.done > 0) s->at_init = false;
+    s->step += rc.done;
+    s->t = rc.t;
+    if (rc.ran == rc.done) {
+        // every step was accepted: the report of the last one
+        lmood_step_info in{};
+        const Report &rep = rc.last;
+        in.n_troubled = rep.n_troubled;
+        in.mood_iters = rep.mood_iters;
+        in.n_p0 = rep.n_p0;
+        in.n_parachute = rep.n_para;
+        in.n_p0_eps = rep.n_eps;
+        in.n_lim = rep.n_lim;
+        in.dt_used = rep.dt_used;
+        in.dt_next = rep.dt_next;
+        in.t = s->t;
+        in.step = s->step;
+        in.syncs = 1;
+        s->last = in;
+        if (last) *last = in;
+        return LMOOD_OK;
+    }
+    // the failing step (refused by finish_step's rules; the state holds the steps before it)
+    return finish_step(s, rc.last, last, 1);
+}
+
 extern "C" lmood_status lmood_run(lmood_state s, int64_t nsteps, lmood_step_info *last) {
     if (!s || nsteps < 0) return fail(LMOOD_ERR_ARG, "lmood_run: bad argument");
+    if (s->broken) return fail(LMOOD_ERR_STATE, "lmood_run: state unusable after an earlier CUDA error");
+    if (nsteps >= 2 && s->prm.graph == 1 && !s->timing && !s->chain_unsupported) {
+        lmood_status r = run_chained(s, nsteps, last);
+        if (r != LMOOD_ERR_CUDA || s->chain_built || s->broken) return r;
+        // the chained graph could not be built on this device / driver: step one at a time
+        s->chain_unsupported = true;
+        s->chain_err = lmood_last_error();
+    }
+    int syncs = 0;
     for (int64_t i = 0; i < nsteps; ++i) {
         lmood_status r = lmood_step(s, last);
+        syncs += s->last.syncs;
         if (r) return r;
     }
-    if (last && nsteps == 0) *last = s->last;
+    if (last) {
+        if (nsteps == 0) *last = s->last;
+        last->syncs = syncs;
+    }
     return LMOOD_OK;
 }
 
@@ -1158,6 +1366,7 @@ extern "C" lmood_status lmood_totals(lmood_state s, double *out5) {
 
 // the state's captured step graphs (re-captured at the next step)
 static void graphs_destroy(lmood_state s) {
+    chain_destroy(s);
     for (int p = 0; p < 2; ++p) {
         if (s->gexec[p]) cudaGraphExecDestroy(s->gexec[p]);
         if (s->graph[p]) cudaGraphDestroy(s->graph[p]);

@@ -11,6 +11,15 @@
 
 namespace lmood {
 
+// control block of a device-chained run: the steps that ran and were accepted, the time
+// after the last accepted one (accumulated in the order lmood_step does), the MOOD loop's
+// body launches (for the launch counts) and the report of the last step that ran
+struct RunCtl {
+    int abort, ran, done, mood_pairs;
+    double t;
+    Report last;
+};
+
 // sets the calling thread's last error message (read back with lmood_last_error) and returns st
 lmood_status fail(lmood_status st, const std::string &msg);
 
@@ -82,6 +91,14 @@ struct lmood_state_s {
     cudaEvent_t gev[2][7] = {};
     cudaStream_t cap_st = nullptr;   // private streams for capturing (the mesh's stream may be the
     cudaStream_t body_st = nullptr;  // legacy default stream, which cannot be captured)
+    // device-chained runs (lmood_run): per buffer parity a graph whose step sits in an IF node
+    // gated by the run's abort word, so that the steps of a run need no host synchronisation
+    bool chain_built = false, chain_unsupported = false;
+    std::string chain_err;                       // why the chained form could not be built
+    cudaGraph_t cgraph[2] = {nullptr, nullptr};
+    cudaGraphExec_t cexec[2] = {nullptr, nullptr};
+    lmood::RunCtl *d_run = nullptr;              // the run's control block (device)
+    lmood::RunCtl *h_run = nullptr;              //   and its pinned mirror
     unsigned int *bar = nullptr;  // persistent step: grid barrier state (device, 4 words)
     cudaStream_t aux_st = nullptr;   // lmood_set_fields: the geometry refresh beside the copies
     cudaEvent_t set_ev[2] = {};      //   (X and F copied; refresh done)
