@@ -19,6 +19,39 @@ def relerr(g: np.ndarray, o: np.ndarray) -> float:
     return float(d / scale)
 
 
+def relerr_rows(g: np.ndarray, o: np.ndarray) -> float:
+    """max over components (rows of the SoA field) of max |g - o| / max |o| over that
+    component: each component is held to its own scale (a small velocity component or an
+    off-diagonal of F is not measured against the largest one)."""
+    g2, o2 = g.reshape(-1, g.shape[-1]), o.reshape(-1, o.shape[-1])
+    floor = 1e-300 + 1e-12 * np.abs(o2).max()
+    return float(max(np.abs(g2[r] - o2[r]).max() / max(np.abs(o2[r]).max(), floor) for r in range(o2.shape[0])))
+
+
+def push_oracle_state(g, o):
+    """Give the CUDA state g the oracle o's dynamic state (x, v_p, v, e, F) and next dt, so
+    that both take their next step from the same state. The oracle's trajectory stays its own
+    (nothing flows from the CUDA path into the oracle). Returns the state."""
+    st = o.state()
+    g.set_fields({L.FIELD_X: st["x"], L.FIELD_VP: st["vp"], L.FIELD_V: st["v"], L.FIELD_E: st["e"],
+                  L.FIELD_F: st["F"], L.FIELD_DT: np.array([o.dt])})
+    return st
+
+
+def step_errors(g, o, before: dict) -> dict:
+    """After one step of both sides from the same state `before`: the field-wise relative
+    errors, the per-component relative errors, and the nodal solver's velocity v*_p (the
+    step's displacement divided by dt, compared on its own scale: x itself is ~1 while a step
+    moves it by ~1e-5, so x^{n+1} alone hides the displacement below its last bits)."""
+    out = {}
+    for name, fo, fg in FIELDS:
+        a, b = g.get(fg), o.get(fo)
+        out[name] = relerr(a, b)
+        out[name + "_rows"] = relerr_rows(a, b)
+    out["vstar_rows"] = relerr_rows(g.get(L.FIELD_VSTAR), o.get(O.F_VSTAR))
+    return out
+
+
 class Pair:
     def __init__(self, problem, **params):
         """params: step parameters of both sides; graph (the library's step form) goes to the
