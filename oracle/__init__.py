@@ -97,6 +97,7 @@ def lib():
         L.orc_debug_rdmp.argtypes = [C.c_void_p, C.c_long, C.c_double, C.POINTER(C.c_double),
                                      C.POINTER(C.c_double)]
         L.orc_debug_pad.argtypes = [C.c_void_p, C.c_long, dp, C.c_double, dp, C.c_double]
+        L.orc_threads.restype = C.c_int
         L.orc_mesh_bc_ndof.argtypes = [C.c_void_p, C.c_long]
         L.orc_mesh_bc_ndof.restype = C.c_int
         L.orc_mesh_set_bc_values.argtypes = [C.c_void_p, dp]
@@ -111,6 +112,11 @@ def default_params(cfl=0.4, **kw) -> Params:
     for k, v in kw.items():
         setattr(p, k, v)
     return p
+
+
+def threads() -> int:
+    """threads of the oracle's OpenMP loops"""
+    return lib().orc_threads()
 
 
 # ----------------------------------------------------------------------------- unit functions

@@ -99,6 +99,9 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -1458,6 +1461,15 @@ int orc_debug_rdmp(const OrcState *S, long c, real rho_new, real *lo, real *hi) 
 int orc_debug_pad(const OrcState *S, long c, const real *v, real e, const real *F, real V) {
     if (c < 0 || c >= S->M->nc) return -1;
     return pad_state(S->M->d, v, e, F, V, a0sq_of(S, c));
+}
+
+/* threads the oracle's OpenMP loops run on */
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* Mesh queries used by tests (stencil and BC resolution). */
