@@ -96,17 +96,16 @@ def kernel_bytes(dim: int, nc: int, npn: int, nnz: int) -> dict:
 #  - DRAM bytes (read + write) per full launch per cell (the capture's traffic / its cells).
 # COUNTS_SRC is the digest of the kernel sources the capture was taken on: when the sources
 # differ the bench line says so ("counts_stale") and gives no traffic.
-# 2D: impact2d (999,698 triangles), profiles/k_predict_impact2d.md; 3D: a reduced column
-# (30 x 30 x 180 cubes, 972,000 tetrahedra), profiles/column3d_kernels.md (the full column's
-# traffic scales with the cells: every per-cell array is read and written once per launch).
-FP64_FLOP_PER_CELL = {2: {"predict": 838.0, "update": 366.0, "nodes": 31.1, "moments": 120.0},
-                      3: {"predict": 2517.0, "update": 876.0, "nodes": 48.5, "moments": 408.0}}
-FP64_INSTR_PER_CELL = {2: {"predict": 518.0, "update": 238.0, "nodes": 25.0, "moments": 75.0},
-                       3: {"predict": 1503.0, "update": 560.0, "nodes": 44.2, "moments": 240.0}}
-TRAFFIC_PER_CELL = {2: {"predict": 292.70e6 / 999698, "update": 350.80e6 / 999698, "nodes": 182.10e6 / 999698,
-                        "moments": 150.70e6 / 999698},
-                    3: {"predict": 504.1, "update": 609.8, "nodes": 409.6, "moments": 198.3}}
-COUNTS_SRC = {2: "3a3f8158403aca92", 3: "3a3f8158403aca92"}
+# 2D: impact2d (999,698 triangles), 3D: a reduced column (30 x 30 x 180 cubes, 972,000
+# tetrahedra), both in profiles/column3d_kernels.md (the full meshes' traffic scales with the
+# cells: every per-cell array is read and written once per launch).
+FP64_FLOP_PER_CELL = {2: {"predict": 836.0, "update": 359.0, "nodes": 31.1, "moments": 120.0},
+                      3: {"predict": 2475.0, "update": 786.0, "nodes": 48.5, "moments": 408.0}}
+FP64_INSTR_PER_CELL = {2: {"predict": 508.0, "update": 231.0, "nodes": 25.0, "moments": 75.0},
+                       3: {"predict": 1453.0, "update": 487.0, "nodes": 44.2, "moments": 240.0}}
+TRAFFIC_PER_CELL = {2: {"predict": 292.0, "update": 349.0, "nodes": 181.9, "moments": 149.9},
+                    3: {"predict": 606.5, "update": 709.3, "nodes": 400.7, "moments": 198.1}}
+COUNTS_SRC = {2: "27a6ebce61ca4a86", 3: "27a6ebce61ca4a86"}
 KERNEL_SOURCES = ("lmood_kernels.cuh", "lmood_dev.cuh", "lmood_ops_impl.cuh")
 
 
@@ -266,6 +265,7 @@ def run_ours(args, rank, local, ws, dist):
     for _ in range(args.warmup):
         sim.step()
     tuned = None if args.no_autotune else sim.autotune()
+    sched = None if args.no_autotune or args.host_mode else sim.autotune_schedule()
     for _ in range(2):  # re-capture the step graphs with the chosen launch shapes
         sim.step()
     first_timed = sim.info.step
@@ -388,7 +388,12 @@ def run_ours(args, rank, local, ws, dist):
                 "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": ck, "e2e": e2e,
                 "cpu_baseline": cb, "impact2d_windows": impact, "batched": batched, "variants": variants,
                 "adjoint": adjoint,
-                "launch": None if tuned is None else {k: v["chosen"] for k, v in tuned.items()}}
+                "launch": None if tuned is None else {**{k: v["chosen"] for k, v in tuned.items()},
+                                                      **({} if sched is None else
+                                                         {"node_window": sched["node_window"]["chosen"],
+                                                          "step_form": sched["step_form"]["chosen"],
+                                                          "step_form_ms": sched["step_form"]["ms"],
+                                                          "node_window_ms": sched["node_window"]["ms"]})}}
         print(json.dumps(line), flush=True)
 
 

@@ -78,6 +78,8 @@ struct Fld {
     double *mom;                 // [NMOM][Np] least-squares moments of the cells around each node
     const double *im;            // 1 / m_c
     double *pkM, *pkR;
+    double *gf;                  // 3D: [D (D+1) + 1][N] the cells' face area vectors N_f and volume at
+                                 // x^n, written by the step's full-mesh predictor, read by its update
     unsigned char *order, *pflag;
     double *dtc;
     const double *dt;            // [n_inst] dt of this step

@@ -135,6 +135,14 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
     }
     double V, Nf[NV][D];
     simplex_faces<D>(xs, V, Nf);
+    if constexpr (D == 3 && !LISTED) {
+        // the geometry at x^n for this step's update (it would otherwise recompute it)
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+            for (int a = 0; a < D; ++a) f.gf[(k * D + a) * N + c] = Nf[k][a];
+        f.gf[NV * D * N + c] = V;
+    }
     double vc[D], Fc[DD];
 #pragma unroll
     for (int a = 0; a < D; ++a) vc[a] = f.v[a * N + c];
@@ -168,8 +176,18 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
             }
         }
     };
+    // T* N_k, the stress part of corner k's packet
+    auto stress_normal = [&](int k, const double(&Tst)[DD], double(&tn)[D]) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            double s = 0.0;
+#pragma unroll
+            for (int b = 0; b < D; ++b) s += Tst[a * D + b] * Nf[k][b];
+            tn[a] = s;
+        }
+    };
     // packet of corner k: M_cp and rhs_cp = M_cp v* - T* l n_p, with l n_p = -N_p / D
-    auto emit = [&](int k, const double(&vst)[D], const double(&Tst)[DD]) {
+    auto emit = [&](int k, const double(&vst)[D], const double(&tn)[D]) {
         double M[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
@@ -182,13 +200,10 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
         }
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            double mv = 0.0, tn = 0.0;
+            double mv = 0.0;
 #pragma unroll
-            for (int b = 0; b < D; ++b) {
-                mv += M[sidx<D>(a, b)] * vst[b];
-                tn += Tst[a * D + b] * Nf[k][b];
-            }
-            f.pkR[a * NC + k * N + c] = fma(tn, 1.0 / D, mv);
+            for (int b = 0; b < D; ++b) mv += M[sidx<D>(a, b)] * vst[b];
+            f.pkR[a * NC + k * N + c] = fma(tn[a], 1.0 / D, mv);
         }
     };
     if (ord != 1) {
@@ -239,7 +254,7 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
 #pragma unroll
             for (int a = 0; a < D; ++a) r[q][a] = fma(-wsum[a], qc, r[q][a]);
         }
-        double Gf[DD], Gi[DD], gs[NQ][D];
+        double Gf[DD], Gi[DD];
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -251,92 +266,99 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
         // an empty stencil gives G = 0 up to the rounding of the moment sums: no slopes
         const bool ok = npair > 0.0 && det<D>(Gf) > 1e-12 * (D == 2 ? t * t : t * t * t);
         inverse<D>(Gf, Gi);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q)
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                double s = 0.0;
-#pragma unroll
-                for (int b = 0; b < D; ++b) s += Gi[a * D + b] * r[q][b];
-                gs[q][a] = ok ? s : 0.0;
-            }
-        // cells reach level 3 only through a MOOD decrement, i.e. in list launches
-        if (LISTED && ord == 3) {
-            // Barth-Jespersen: scale each field's slope by the largest phi <= 1 that keeps its
-            // values at the cell's nodes within its range over the stencil and the cell
-            double lo[NQ], hi[NQ];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) lo[q] = hi[q] = q < D ? vc[q] : Fc[q - D];
-            for (int k = 0; k < NV; ++k) {
-                const int j1 = __ldg(g.n2c_off + nod[k] + 1);
-                for (int j = __ldg(g.n2c_off + nod[k]); j < j1; ++j) {
-                    int o = __ldg(g.n2c + j);
-#pragma unroll
-                    for (int kk = 0; kk < D; ++kk) o -= o >= N ? N : 0;
-#pragma unroll
-                    for (int q = 0; q < NQ; ++q) {
-                        const double qo = q < D ? f.v[q * N + o] : f.F[(q - D) * N + o];
-                        lo[q] = fmin(lo[q], qo);
-                        hi[q] = fmax(hi[q], qo);
-                    }
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const double qc = q < D ? vc[q] : Fc[q - D];
-                double phi = 1.0;
-#pragma unroll
-                for (int k = 0; k < NV; ++k) {
-                    double delta = 0.0;
-#pragma unroll
-                    for (int a = 0; a < D; ++a) delta += gs[q][a] * (xs[k][a] - xcc[a]);
-                    if (delta > 0.0) phi = fmin(phi, (hi[q] - qc) / delta);
-                    if (delta < 0.0) phi = fmin(phi, (lo[q] - qc) / delta);
-                }
-#pragma unroll
-                for (int a = 0; a < D; ++a) gs[q][a] *= phi;
-            }
-        }
         double dxs[NV][D];
 #pragma unroll
         for (int k = 0; k < NV; ++k)
 #pragma unroll
             for (int a = 0; a < D; ++a) dxs[k][a] = xs[k][a] - xcc[a];
-        // predictor, pass 1: dv/dt = (1/m) sum_q T(F_h(x_q)) l n_q. The corner values F_h are
-        // kept for pass 2 in 2D; in 3D (registers) pass 2 recomputes them.
-        constexpr int KEEP = D == 2 ? NV : 1;
-        double Fhk[KEEP][DD];
-        double dvdt[D];
+        // The reconstruction at corner k is q_c + g_q . dx_k with the slopes g_q = G^-1 r_q.
+        // The whole-mesh launch evaluates it as q_c + r_q . y_k with y_k = G^-1 dx_k (the same
+        // value; D^2 products per corner instead of D^2 per field), and forms the slopes of v
+        // alone (for dF/dt); a listed cell may limit its slopes (Barth-Jespersen), so there the
+        // slopes are formed and y_k = dx_k. rr holds r_q or g_q accordingly.
+        double rr[NQ][D], yk[NV][D], gv[DD];
+        if (!LISTED) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) dvdt[a] = 0.0;
+            for (int k = 0; k < NV; ++k)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double Fh[DD], T[DD];
+                for (int a = 0; a < D; ++a) {
+                    double s = 0.0;
 #pragma unroll
-            for (int q = 0; q < DD; ++q) {
-                double s = Fc[q];
+                    for (int b = 0; b < D; ++b) s += Gi[a * D + b] * dxs[k][b];
+                    yk[k][a] = ok ? s : 0.0;
+                }
 #pragma unroll
-                for (int a = 0; a < D; ++a) s += gs[D + q][a] * dxs[k][a];
-                Fh[q] = s;
-                if constexpr (D == 2) Fhk[k][q] = s;
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                for (int a = 0; a < D; ++a) rr[q][a] = r[q][a];
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int b = 0; b < D; ++b) s += Gi[a * D + b] * r[i][b];
+                    gv[i * D + a] = ok ? s : 0.0;
+                }
+        } else {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int b = 0; b < D; ++b) s += Gi[a * D + b] * r[q][b];
+                    rr[q][a] = ok ? s : 0.0;
+                }
+            // cells reach level 3 only through a MOOD decrement, i.e. in list launches
+            if (ord == 3) {
+                // Barth-Jespersen: scale each field's slope by the largest phi <= 1 that keeps
+                // its values at the cell's nodes within its range over the stencil and the cell
+                double lo[NQ], hi[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) lo[q] = hi[q] = q < D ? vc[q] : Fc[q - D];
+                for (int k = 0; k < NV; ++k) {
+                    const int j1 = __ldg(g.n2c_off + nod[k] + 1);
+                    for (int j = __ldg(g.n2c_off + nod[k]); j < j1; ++j) {
+                        int o = __ldg(g.n2c + j);
+#pragma unroll
+                        for (int kk = 0; kk < D; ++kk) o -= o >= N ? N : 0;
+#pragma unroll
+                        for (int q = 0; q < NQ; ++q) {
+                            const double qo = q < D ? f.v[q * N + o] : f.F[(q - D) * N + o];
+                            lo[q] = fmin(lo[q], qo);
+                            hi[q] = fmax(hi[q], qo);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const double qc = q < D ? vc[q] : Fc[q - D];
+                    double phi = 1.0;
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) {
+                        double delta = 0.0;
+#pragma unroll
+                        for (int a = 0; a < D; ++a) delta += rr[q][a] * dxs[k][a];
+                        if (delta > 0.0) phi = fmin(phi, (hi[q] - qc) / delta);
+                        if (delta < 0.0) phi = fmin(phi, (lo[q] - qc) / delta);
+                    }
+#pragma unroll
+                    for (int a = 0; a < D; ++a) rr[q][a] *= phi;
+                }
             }
-            cell_stress<D, MAT>(prm, Fh, muc, kap, eps_c, T);
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
+            for (int k = 0; k < NV; ++k)
 #pragma unroll
-                for (int b = 0; b < D; ++b) dvdt[i] = fma(T[i * D + b], Nf[k][b], dvdt[i]);
-            }
+                for (int a = 0; a < D; ++a) yk[k][a] = dxs[k][a];
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int a = 0; a < D; ++a) gv[i * D + a] = rr[i][a];
         }
-        // half step: dt/2 dv/dt and dt/2 dF/dt with dF/dt = L^ F_c (Eq. GCLL)
+        // half step of F: dt/2 dF/dt with dF/dt = L^ F_c (Eq. GCLL)
         const double dt = f.dt[g.cell_inst ? __ldg(g.cell_inst + c) : 0];
-        const double hv = -0.5 * dt * f.im[c] * (1.0 / D);
-#pragma unroll
-        for (int a = 0; a < D; ++a) dvdt[a] *= hv;
-        double gv[DD], dFdt[DD];
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-            for (int a = 0; a < D; ++a) gv[i * D + a] = gs[i][a];
+        double dFdt[DD];
         matmul<D>(gv, Fc, dFdt);
         // stiffened gas: the internal energy at the half step, d eps/dt = T_c : L^ / rho
         double eps_h = eps_c;
@@ -347,42 +369,62 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
             for (int q = 0; q < DD; ++q) pw += Tc[q] * gv[q];
             eps_h = eps_c + 0.5 * dt * pw * V / f.m[c];
         }
-        // pass 2: corner values at t^{n+1/2} and packets (the velocity's half-step increment
-        // added to the cell value once)
+        // per corner k, from the reconstructed value F_h(x_k): the stress T(F_h) of
+        // dv/dt = (1/m) sum_q T(F_h(x_q)) l n_q, and the stress T* = T(F_h + dt/2 dF/dt) at
+        // t^{n+1/2}, of which the packet needs T* N_k (F_h is formed once per corner)
+        double dvdt[D], tn[NV][D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) dvdt[a] = 0.0;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double Fh[DD], Fs[DD], T[DD];
+#pragma unroll
+            for (int q = 0; q < DD; ++q) {
+                double s = Fc[q];
+#pragma unroll
+                for (int a = 0; a < D; ++a) s += rr[D + q][a] * yk[k][a];
+                Fh[q] = s;
+                Fs[q] = fma(0.5 * dt, dFdt[q], s);
+            }
+            cell_stress<D, MAT>(prm, Fh, muc, kap, eps_c, T);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+#pragma unroll
+                for (int b = 0; b < D; ++b) dvdt[i] = fma(T[i * D + b], Nf[k][b], dvdt[i]);
+            }
+            cell_stress<D, MAT>(prm, Fs, muc, kap, eps_h, T);
+            stress_normal(k, T, tn[k]);
+        }
+        // half step of v: dt/2 dv/dt, added to the cell value once
+        const double hv = -0.5 * dt * f.im[c] * (1.0 / D);
+#pragma unroll
+        for (int a = 0; a < D; ++a) dvdt[a] *= hv;
         face_matrices();
         double vch[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) vch[i] = vc[i] + dvdt[i];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double vst[D], Fs[DD], T[DD];
+            double vst[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) {
                 double s = vch[i];
 #pragma unroll
-                for (int a = 0; a < D; ++a) s += gs[i][a] * dxs[k][a];
+                for (int a = 0; a < D; ++a) s += rr[i][a] * yk[k][a];
                 vst[i] = s;
             }
-#pragma unroll
-            for (int q = 0; q < DD; ++q) {
-                if constexpr (D == 2) {
-                    Fs[q] = fma(0.5 * dt, dFdt[q], Fhk[k][q]);
-                } else {
-                    double s = Fc[q];
-#pragma unroll
-                    for (int a = 0; a < D; ++a) s += gs[D + q][a] * dxs[k][a];
-                    Fs[q] = fma(0.5 * dt, dFdt[q], s);
-                }
-            }
-            cell_stress<D, MAT>(prm, Fs, muc, kap, eps_h, T);
-            emit(k, vst, T);
+            emit(k, vst, tn[k]);
         }
     } else {
         double T[DD];
         cell_stress<D, MAT>(prm, Fc, muc, kap, eps_c, T);
         face_matrices();
 #pragma unroll
-        for (int k = 0; k < NV; ++k) emit(k, vc, T);
+        for (int k = 0; k < NV; ++k) {
+            double tn[D];
+            stress_normal(k, T, tn);
+            emit(k, vc, tn);
+        }
     }
 }
 
@@ -668,13 +710,12 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
     const int ord = f.order[c];
     const double dt = f.dt[g.cell_inst ? __ldg(g.cell_inst + c) : 0];
     int nod[NV];
-    double xs0[NV][D], xs1[NV][D], vsn[NV][D];
+    double xs1[NV][D], vsn[NV][D];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         nod[k] = __ldg(g.c2n + k * N + c);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            xs0[k][a] = f.x[a * Np + nod[k]];
             xs1[k][a] = f.x1[a * Np + nod[k]];
             vsn[k][a] = f.vs[a * Np + nod[k]];
         }
@@ -703,7 +744,21 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
     for (int a = 0; a < D; ++a) v1[a] = fma(dtm, sf[a], f.v[a * N + c]);
     const double e1 = fma(dtm, sfv, f.e[c]);
     double V0, Nf0[NV][D], V1, Nf1[NV][D];
-    simplex_faces<D>(xs0, V0, Nf0);
+    if constexpr (D == 3) {
+        // the geometry at x^n as this step's full-mesh predictor computed it
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+            for (int a = 0; a < D; ++a) Nf0[k][a] = f.gf[(k * D + a) * N + c];
+        V0 = f.gf[NV * D * N + c];
+    } else {
+        double xs0[NV][D];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+            for (int a = 0; a < D; ++a) xs0[k][a] = f.x[a * Np + nod[k]];
+        simplex_faces<D>(xs0, V0, Nf0);
+    }
     simplex_faces<D>(xs1, V1, Nf1);
     // 1 / |w_c| at x^n is rho^n / m_c (rho^n = m_c / |w_c(x^n)| is stored); at x^{n+1} one division
     const double iV0 = f.rho[c] * im, iV1 = 1.0 / V1;
@@ -765,10 +820,14 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
     if (prm.mood) {
         int ps = pad_state<D>(v1, e1, F1, V1, a0sq_of(prm, muc, kap));
         if (prm.eos && ps == 0) {  // stiffened gas: p + p_inf > 0 (a real sound speed)
-            double eps1 = e1;
+            double eps1 = e1, Fg[DD];
 #pragma unroll
             for (int a = 0; a < D; ++a) eps1 -= 0.5 * v1[a] * v1[a];
-            if (!(sg_pressure<D>(prm, F1, muc, eps1) + prm.pinf > 0.0)) ps = 1;
+            // a copy: the shear energy of the family takes its argument's address, which would
+            // put F1 in local memory on every path
+#pragma unroll
+            for (int q = 0; q < DD; ++q) Fg[q] = F1[q];
+            if (!(sg_pressure<D>(prm, Fg, muc, eps1) + prm.pinf > 0.0)) ps = 1;
         }
         if (ord != 1) {
             bool bad = ps != 0;
@@ -793,10 +852,12 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
     // next impedance and dt candidate: C_CFL L_c / a = C_CFL (2 D V / area) (m / V) / z
     double z1;
     if (prm.eos) {
-        double eps1 = e1;
+        double eps1 = e1, Fg[DD];
 #pragma unroll
         for (int a = 0; a < D; ++a) eps1 -= 0.5 * v1[a] * v1[a];
-        z1 = impedance_sg<D>(prm, F1, rho1, muc, eps1);
+#pragma unroll
+        for (int q = 0; q < DD; ++q) Fg[q] = F1[q];  // (a copy, as above)
+        z1 = impedance_sg<D>(prm, Fg, rho1, muc, eps1);
     } else {
         z1 = impedance<D>(F1, rho1, muc, kap);
     }
