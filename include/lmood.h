@@ -278,6 +278,28 @@ lmood_status lmood_mesh_info(lmood_mesh m, int64_t *out6);
  * chosen4 (may be NULL) the chosen sizes in the same kernel order. Synchronises. */
 lmood_status lmood_autotune(lmood_state s, int reps, double *ms12, int32_t *chosen4);
 
+/* Autotuning of the step's schedule beyond the block sizes (the paper has no counterpart:
+ * launch shapes of this implementation; the per-cell and per-node arithmetic is the same in
+ * every schedule, so later steps are bitwise the same as without tuning):
+ *  - the order in which the whole-mesh node kernels (moments, nodal solve) take the nodes: the
+ *    nodes of each window of W consecutive ones in order of their cell count (a warp's lanes
+ *    then run loops of one length while a block still reads one neighbourhood), W = 32, 256
+ *    (the order lmood_mesh_create sets), 2048, or 0 (the nodes in their own order); timed by
+ *    reps launches of the two kernels (<= 0: 5) and the fastest kept for the mesh (every
+ *    state on it);
+ *  - the step form, when the state was created with graph 1 or 2 and its material allows the
+ *    persistent form (neo-Hookean): reps lmood_step calls in each form (host synchronisation
+ *    included) from the state as it is, the state copied aside on the device before and
+ *    restored after each trial (fields, time, step count and report unchanged), and the state
+ *    switched to the faster form.
+ * ms_window4 (may be NULL): mean ms of one moments + nodal-solve pass per candidate W in the
+ * order above; window (may be NULL): the chosen W; ms_form2 (may be NULL): ms per step of
+ * graph 1 and graph 2 (-1 when not timed); form (may be NULL): the chosen graph, -1 when the
+ * form was not tuned. Errors: LMOOD_ERR_ARG with timing on; LMOOD_ERR_OOM (the state copy);
+ * a trial step's own error (the state is then that of the failed trial's start). Synchronises. */
+lmood_status lmood_autotune_schedule(lmood_state s, int reps, double *ms_window4, int32_t *window,
+                                     double *ms_form2, int32_t *form);
+
 enum { LMOOD_K_PREDICT = 0, LMOOD_K_NODES = 1, LMOOD_K_UPDATE = 2, LMOOD_K_MOOD = 3, LMOOD_K_FINALIZE = 4,
        LMOOD_K_MOMENTS = 5, LMOOD_NK = 6 };
 lmood_status lmood_timing(lmood_state s, int enable);

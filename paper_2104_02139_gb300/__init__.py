@@ -49,7 +49,8 @@ EXPORTS = ("lmood_params_default", "lmood_mesh_create", "lmood_mesh_destroy", "l
            "lmood_mesh_set_bc_values", "lmood_mesh_set_btag", "lmood_mesh_set_contact",
            "lmood_state_init", "lmood_state_destroy", "lmood_step", "lmood_run", "lmood_get", "lmood_set",
            "lmood_get_fields", "lmood_set_fields",
-           "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_autotune", "lmood_totals_noalloc",
+           "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_autotune", "lmood_autotune_schedule",
+           "lmood_totals_noalloc",
            "lmood_tape_record",
            "lmood_tape_backward", "lmood_tape_replay", "lmood_tape_info", "lmood_tape_destroy", "lmood_last_error")
 K_PREDICT, K_NODES, K_UPDATE, K_MOOD, K_FINALIZE, K_MOMENTS, NK = range(7)
@@ -85,6 +86,8 @@ def lib():
         L.lmood_timing_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.lmood_totals_noalloc.argtypes = [C.c_int, C.c_int64, vp, vp, vp, vp, vp]
         L.lmood_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int32)]
+        L.lmood_autotune_schedule.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                                              C.POINTER(C.c_double), C.POINTER(C.c_int32)]
         L.lmood_tape_record.argtypes = [vp, C.c_int64, C.c_int64, C.POINTER(vp), C.POINTER(StepInfo)]
         L.lmood_tape_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
         L.lmood_tape_replay.argtypes = [vp, vp, C.c_int64]
@@ -354,6 +357,19 @@ class State:
         for k, name in enumerate(("moments", "predict", "nodes", "update")):
             out[name] = {"chosen": ch[k], "ms": {cand[k][v]: ms[k * 3 + v] for v in range(3)}}
         return out
+
+    def autotune_schedule(self, reps: int = 5) -> dict:
+        """lmood_autotune_schedule: node-window size of the whole-mesh node kernels (32, 256,
+        2048, 0 = own order) and the step form (graph 1 or 2), each timed and the fastest kept"""
+        msw = (C.c_double * 4)()
+        w = C.c_int32()
+        msf = (C.c_double * 2)()
+        fm = C.c_int32()
+        _check(lib().lmood_autotune_schedule(self.h, reps, msw, C.byref(w), msf, C.byref(fm)))
+        if fm.value > 0:
+            self.params.graph = fm.value
+        return {"node_window": {"chosen": w.value, "ms": dict(zip((32, 256, 2048, 0), list(msw)))},
+                "step_form": {"chosen": fm.value, "ms": {1: msf[0], 2: msf[1]}}}
 
     def timing(self, enable: bool):
         _check(lib().lmood_timing(self.h, 1 if enable else 0))

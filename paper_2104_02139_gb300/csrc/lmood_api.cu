@@ -2,6 +2,7 @@
 // corner adjacency, boundary-condition resolution), state buffers, and the host
 // side of the step (kernel sequence and the MOOD loop over compacted lists).
 #include <algorithm>
+#include <chrono>
 #include <array>
 #include <functional>
 #include <cmath>
@@ -645,6 +646,7 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
     A((void **)&f.rlo, Np * nd);
     A((void **)&f.rhi, Np * nd);
     A((void **)&s->mu, N * nd);
+    if (D == 3) A((void **)&f.gf, (size_t)(D * NV + 1) * N * nd);
     A((void **)&f.pkM, (size_t)NS * NV * N * nd);
     A((void **)&f.pkR, (size_t)D * NV * N * nd);
     A((void **)&f.order, N);
@@ -1443,6 +1445,176 @@ extern "C" lmood_status lmood_autotune(lmood_state s, int reps, double *ms12, in
             for (int v = 0; v < 3; ++v) ms12[k * 3 + v] = times[k][v];
     if (chosen4)
         for (int k = 0; k < 4; ++k) chosen4[k] = *slot[k];
+    return LMOOD_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// schedule autotuning: the node order of the whole-mesh node kernels and the step form
+// ---------------------------------------------------------------------------------------
+// the nodes of each window of W consecutive ones in order of their cell count (stable; W <= 0:
+// the nodes in their own order)
+static void node_order(const std::vector<int> &off, int64_t W, std::vector<int> &perm) {
+    const int64_t Np = (int64_t)off.size() - 1;
+    perm.resize(Np);
+    if (W <= 0) {
+        for (int64_t p = 0; p < Np; ++p) perm[p] = (int)p;
+        return;
+    }
+    int max_deg = 0;
+    for (int64_t p = 0; p < Np; ++p) max_deg = std::max(max_deg, off[p + 1] - off[p]);
+    std::vector<int64_t> first(max_deg + 2);
+    for (int64_t w0 = 0; w0 < Np; w0 += W) {
+        const int64_t w1 = std::min(Np, w0 + W);
+        std::fill(first.begin(), first.end(), 0);
+        for (int64_t p = w0; p < w1; ++p) first[off[p + 1] - off[p] + 1]++;
+        first[0] = w0;
+        for (int d2 = 0; d2 <= max_deg; ++d2) first[d2 + 1] += first[d2];
+        for (int64_t p = w0; p < w1; ++p) perm[first[off[p + 1] - off[p]]++] = (int)p;
+    }
+}
+
+// the dynamic state of s (the fields a step reads and writes, and the host counters), copied
+// aside on the device so that trial steps can be undone exactly
+struct StateCopy {
+    std::vector<std::pair<void *, size_t>> parts;  // (device copy, bytes) in the order of fields()
+    double t = 0.0;
+    int64_t step = 0;
+    bool at_init = false;
+    lmood_step_info last{};
+    static std::vector<std::pair<void *, size_t>> fields(lmood_state s) {
+        lmood_mesh M = s->M;
+        const size_t D = M->dim, N = M->nc, Np = M->np, nd = sizeof(double);
+        Fld &f = s->f;
+        return {{f.x, D * Np * nd}, {f.vp, D * Np * nd}, {f.v, D * N * nd}, {f.e, N * nd}, {f.F, D * D * N * nd},
+                {f.xc, D * N * nd}, {f.rho, N * nd}, {f.z, N * nd}, {s->tau, N * nd}, {f.order, N},
+                {const_cast<double *>(f.dt), (size_t)M->n_inst * nd}};
+    }
+    lmood_status save(lmood_state s) {
+        for (auto &pb : fields(s)) {
+            void *d = nullptr;
+            if (cudaMalloc(&d, pb.second) != cudaSuccess) {
+                cudaGetLastError();
+                release();
+                return fail(LMOOD_ERR_OOM, "lmood_autotune_schedule: no device memory for the state copy");
+            }
+            parts.push_back({d, pb.second});
+            LM_CUDA(cudaMemcpyAsync(d, pb.first, pb.second, cudaMemcpyDeviceToDevice, s->M->st));
+        }
+        t = s->t;
+        step = s->step;
+        at_init = s->at_init;
+        last = s->last;
+        return LMOOD_OK;
+    }
+    // into the state's current buffers (whichever parity the trial steps left)
+    lmood_status restore(lmood_state s) {
+        auto cur = fields(s);
+        for (size_t i = 0; i < cur.size(); ++i)
+            LM_CUDA(cudaMemcpyAsync(cur[i].first, parts[i].first, parts[i].second, cudaMemcpyDeviceToDevice, s->M->st));
+        s->t = t;
+        s->step = step;
+        s->at_init = at_init;
+        s->last = last;
+        return LMOOD_OK;
+    }
+    void release() {
+        for (auto &pb : parts) cudaFree(pb.first);
+        parts.clear();
+    }
+};
+
+extern "C" lmood_status lmood_autotune_schedule(lmood_state s, int reps, double *ms_window4, int32_t *window,
+                                                double *ms_form2, int32_t *form) {
+    if (!s) return fail(LMOOD_ERR_ARG, "lmood_autotune_schedule: NULL state");
+    if (s->broken) return fail(LMOOD_ERR_STATE, "lmood_autotune_schedule: state unusable after an earlier CUDA error");
+    if (s->timing) return fail(LMOOD_ERR_ARG, "lmood_autotune_schedule: switch timing off first");
+    if (reps <= 0) reps = 5;
+    lmood_mesh M = s->M;
+    const Ops &op = *M->ops;
+    cudaStream_t st = M->st;
+    Fld &f = s->f;
+    const int Np = (int)M->np;
+    cudaEvent_t e0, e1;
+    LM_CUDA(cudaEventCreate(&e0));
+    LM_CUDA(cudaEventCreate(&e1));
+    lmood_status r = LMOOD_OK;
+    // 1. node order: the moments and the nodal solve over the whole mesh, per window size
+    const int cand[4] = {32, 256, 2048, 0};
+    double tw[4] = {};
+    std::vector<int> off(Np + 1), perm;
+    int *d_perm = const_cast<int *>(M->geo.node_perm);
+    cudaError_t err = cudaMemcpyAsync(off.data(), M->geo.n2c_off, (Np + 1) * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    int best = 1;
+    for (int v = 0; v < 4 && err == cudaSuccess; ++v) {
+        node_order(off, cand[v], perm);
+        err = cudaMemcpyAsync(d_perm, perm.data(), Np * sizeof(int), cudaMemcpyHostToDevice, st);
+        if (err != cudaSuccess) break;
+        auto launch = [&] {
+            op.moments(M->geo, f, st);
+            op.nodes(M->geo, f, nullptr, nullptr, Np, 0, st);
+        };
+        launch();  // warm
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < reps; ++k) launch();
+        cudaEventRecord(e1, st);
+        err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        tw[v] = ms / reps;
+        if (tw[v] < tw[best]) best = v;
+    }
+    if (err == cudaSuccess) {
+        node_order(off, cand[best], perm);
+        err = cudaMemcpyAsync(d_perm, perm.data(), Np * sizeof(int), cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    }
+    if (err != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        s->broken = true;
+        return fail(LMOOD_ERR_CUDA, std::string("lmood_autotune_schedule: ") + cudaGetErrorString(err));
+    }
+    if (ms_window4)
+        for (int v = 0; v < 4; ++v) ms_window4[v] = tw[v];
+    if (window) *window = cand[best];
+    // 2. step form: reps steps (lmood_step, host synchronisation included) from the state as it
+    // is, once per form, the state restored after each; only between the captured form (1) and
+    // the persistent one (2), and only where the persistent form applies (neo-Hookean material)
+    double tf[2] = {-1.0, -1.0};
+    int chosen = s->prm.graph;
+    const bool both = (s->prm.graph == 1 || s->prm.graph == 2) && s->mat.shear_a == -1.0 && s->mat.eos == 0;
+    if (both) {
+        StateCopy keep;
+        r = keep.save(s);
+        const int g0 = s->prm.graph;
+        for (int v = 0; v < 2 && r == LMOOD_OK; ++v) {
+            s->prm.graph = v + 1;
+            r = lmood_step(s, nullptr);  // warm (graphs captured, lists sized)
+            if (r == LMOOD_OK) r = keep.restore(s);
+            if (r == LMOOD_OK && cudaStreamSynchronize(st) != cudaSuccess) r = sync_check(s, "lmood_autotune_schedule");
+            const auto t0 = std::chrono::steady_clock::now();
+            for (int k = 0; k < reps && r == LMOOD_OK; ++k) r = lmood_step(s, nullptr);
+            const auto t1 = std::chrono::steady_clock::now();
+            tf[v] = std::chrono::duration<double, std::milli>(t1 - t0).count() / reps;
+            if (r == LMOOD_OK) r = keep.restore(s);
+        }
+        if (r == LMOOD_OK) r = sync_check(s, "lmood_autotune_schedule (restore)");
+        keep.release();
+        s->prm.graph = g0;
+        if (r == LMOOD_OK) {
+            chosen = tf[1] < tf[0] ? 2 : 1;
+            s->prm.graph = chosen;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r) return r;
+    if (ms_form2) {
+        ms_form2[0] = tf[0];
+        ms_form2[1] = tf[1];
+    }
+    if (form) *form = both ? chosen : -1;
     return LMOOD_OK;
 }
 
