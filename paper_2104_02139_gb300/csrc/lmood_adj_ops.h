@@ -33,8 +33,12 @@ struct AdjBuf {
     double *cr;                       // corner records of update and nodal solve [NC][CR]
     double *cp;                       // corner records of the predictor [NC][CP]
     double *cc;                       // cell records of the predictor [N][CC]
-    double *lm;                       // node moment adjoints [Np][NMOM] (aliases cr)
+    double *lm;                       // node moment adjoints [Np][NMOM]
     double *cd;                       // corner records of the cell gather: lx [NC][D]
+    // the reverse predictor of the second-order cells in four kernels (adj::PredRec): the cell's
+    // forward intermediates [N][F_LEN], each corner's [NC][K_LEN], the corners' pass-2 and
+    // pass-1 products [NC][Q2_LEN], [NC][Q1_LEN]
+    double *pf, *pk, *q2, *q1;
 };
 
 struct AdjOps {
@@ -47,8 +51,10 @@ struct AdjOps {
     void (*predict)(const Geo &, const Fld &, const Prm &, const AdjBuf &, int force_p0, cudaStream_t);
     // nodes: adjoints of the node moments, summed over the corners around each node
     void (*momsum)(const Geo &, const Fld &, const AdjBuf &, cudaStream_t);
-    // cells: reverse of the node moments (per corner of the cell), centroid and impedance of t^n
-    void (*cells)(const Geo &, const Fld &, const Prm &, const AdjBuf &, cudaStream_t);
+    // cells: reverse of the node moments (per corner of the cell), centroid and impedance of t^n;
+    // tail: first the second-order cells' corner-matrix and geometry part of the predictor's
+    // reverse (after predict without force_p0)
+    void (*cells)(const Geo &, const Fld &, const Prm &, const AdjBuf &, int tail, cudaStream_t);
     // nodes: gather of the per-corner position adjoints
     void (*gather)(const Geo &, const AdjBuf &, cudaStream_t);
     // cells: impedance of the initial state (after the t^0 predictor's reverse)

@@ -16,14 +16,22 @@ template <int D> void adj_nodes(const Geo &g, const Fld &f, const AdjBuf &a, int
 }
 template <int D>
 void adj_predict(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, int force_p0, cudaStream_t s) {
+    if (!force_p0) {
+        const int nc = (D + 1) * g.N;
+        k_adj_pred_fw<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+        k_adj_pred_c2<D><<<adj_blocks(nc, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+        k_adj_pred_c1<D><<<adj_blocks(nc, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+        k_adj_pred_fin<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+        // (the second-order cells' corner-matrix and geometry part runs in k_adj_cells)
+    }
     k_adj_predict<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a, force_p0);
 }
 template <int D> void adj_momsum(const Geo &g, const Fld &f, const AdjBuf &a, cudaStream_t s) {
     (void)f;
     k_adj_momsum<D><<<adj_blocks(g.Np, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, a);
 }
-template <int D> void adj_cells(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, cudaStream_t s) {
-    k_adj_cells<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+template <int D> void adj_cells(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, int tail, cudaStream_t s) {
+    k_adj_cells<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a, tail);
 }
 template <int D> void adj_gather(const Geo &g, const AdjBuf &a, cudaStream_t s) {
     k_adj_gather<D><<<adj_blocks(g.Np, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, a);

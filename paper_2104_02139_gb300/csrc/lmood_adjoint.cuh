@@ -479,6 +479,489 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Product of predict_fw, in pieces that the reverse pass runs as separate kernels for the
+// second-order (P1) cells, so that none of them holds the whole cell's forward intermediates
+// and adjoint accumulators at once:
+//   predict_fw_rec      (cell)   the forward intermediates: record PF of the cell and PK of
+//                                each corner (the reconstructed F_h, v*, M_k)
+//   predict_corner2_vjp (corner) reverse of the packet R_k = M_k v*_k + (1/D) T(F*_k) N_k,
+//                                F*_k = F_h,k + dt/2 dF/dt: record Q2 of the corner
+//   predict_corner1_vjp (corner) reverse of dv = hv sum_k T(F_h,k) N_k, given the adjoint of
+//                                dv (sum over the cell's corners of Q2's lv*): record Q1
+//   predict_finish_vjp  (cell)   the rest: v* and F_h of the slopes, dF/dt, least squares,
+//                                corner matrices, geometry
+// predict_vjp below composes them (and keeps the first-order cells' product whole).
+// ---------------------------------------------------------------------------------------
+template <int D> struct PredRec {
+    static constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + DD;
+    // cell record: slopes gs [NQ][D], G^-1 [DD], d_k = x_k - x_c [NV][D], dF/dt [DD], face
+    // area vectors N [NV][D], D / |N_f| [NV], slopes taken (1) or not (0)
+    static constexpr int F_GS = 0, F_GI = F_GS + NQ * D, F_DK = F_GI + DD, F_DFDT = F_DK + NV * D, F_N = F_DFDT + DD,
+                         F_INU = F_N + NV * D, F_OK = F_INU + NV, F_LEN = F_OK + 1;
+    // corner record: F_h [DD], v* [D], M_k [NS]
+    static constexpr int K_FH = 0, K_VST = DD, K_M = DD + D, K_LEN = DD + D + NS;
+    // pass-2 products of a corner: lv* [D], lF* [DD], lN_k [D], lmu, lkappa
+    static constexpr int Q2_LV = 0, Q2_LF = D, Q2_LN = D + DD, Q2_MU = 2 * D + DD, Q2_KAP = Q2_MU + 1,
+                         Q2_LEN = Q2_KAP + 1;
+    // pass-1 products of a corner: lF_h [DD], lN_k [D], lmu, lkappa
+    static constexpr int Q1_LF = 0, Q1_LN = DD, Q1_MU = DD + D, Q1_KAP = Q1_MU + 1, Q1_LEN = Q1_KAP + 1;
+};
+
+LMOOD_HD double adj_rsqrt(double x) {
+#ifdef __CUDA_ARCH__
+    return rsqrt(x);
+#else
+    return 1.0 / sqrt(x);
+#endif
+}
+
+#ifdef __CUDA_ARCH__
+#define LMOOD_UNROLL _Pragma("unroll")
+#else
+#define LMOOD_UNROLL
+#endif
+
+// forward intermediates of a P1 cell: pf [F_LEN]; corner k's record at pk + k * kstride. The
+// least-squares sums follow the forward kernel's grouping (G symmetric; the q_c terms of the
+// D+1 nodes gathered into one): the same values up to rounding.
+template <int D>
+LMOOD_HD void predict_fw_rec(const double *xs, const Mom<D> &mom, const double *vc, const double *Fc, double z,
+                             double mu, double kap, double im, double dt, double *pf, double *pk, long kstride) {
+    using Q = Sz<D>;
+    using P = PredRec<D>;
+    constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ;
+    double V, xcc[D], N[NV * D];
+    faces<D>(xs, V, N);
+    LMOOD_UNROLL
+    for (int i = 0; i < NV * D; ++i) pf[P::F_N + i] = N[i];
+    LMOOD_UNROLL
+    for (int a = 0; a < D; ++a) {
+        double s = 0.0;
+        LMOOD_UNROLL
+        for (int k = 0; k < NV; ++k) s += xs[k * D + a];
+        xcc[a] = s * (1.0 / NV);
+    }
+    double dk[NV][D];
+    LMOOD_UNROLL
+    for (int k = 0; k < NV; ++k)
+        LMOOD_UNROLL
+        for (int a = 0; a < D; ++a) {
+            dk[k][a] = xs[k * D + a] - xcc[a];
+            pf[P::F_DK + k * D + a] = dk[k][a];
+        }
+    // least squares from the node moments: G = sum_k (S2 + S1 d^t + d w^t), w = S1 + n d,
+    // r_q = sum_k (T_q + d U_q) - (sum_k w) q_c
+    double Gs[NS], r[NQ][D], wsum[D], npair = -NV;  // (node, other cell) pairs of the stencil
+    LMOOD_UNROLL
+    for (int k = 0; k < NV; ++k) {
+        const double nk = mom(k, Q::M_N);
+        npair += nk;
+        double S1[D], w[D];
+        LMOOD_UNROLL
+        for (int a = 0; a < D; ++a) {
+            S1[a] = mom(k, Q::M_S1 + a);
+            w[a] = S1[a] + nk * dk[k][a];
+            wsum[a] = k == 0 ? w[a] : wsum[a] + w[a];
+        }
+        LMOOD_UNROLL
+        for (int a = 0; a < D; ++a)
+            LMOOD_UNROLL
+            for (int b = a; b < D; ++b) {
+                const int sb = sym<D>(a, b);
+                const double g = mom(k, Q::M_S2 + sb) + S1[a] * dk[k][b] + dk[k][a] * w[b];
+                Gs[sb] = k == 0 ? g : Gs[sb] + g;
+            }
+        LMOOD_UNROLL
+        for (int q = 0; q < NQ; ++q) {
+            const double uq = mom(k, Q::M_U + q);
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) {
+                const double t = mom(k, Q::M_T + q * D + a) + dk[k][a] * uq;
+                r[q][a] = k == 0 ? t : r[q][a] + t;
+            }
+        }
+    }
+    LMOOD_UNROLL
+    for (int q = 0; q < NQ; ++q) {
+        const double qc = q < D ? vc[q] : Fc[q - D];
+        LMOOD_UNROLL
+        for (int a = 0; a < D; ++a) r[q][a] -= wsum[a] * qc;
+    }
+    double G[DD];
+    LMOOD_UNROLL
+    for (int a = 0; a < D; ++a)
+        LMOOD_UNROLL
+        for (int b = 0; b < D; ++b) G[a * D + b] = Gs[sym<D>(a, b)];
+    double tr = 0.0;
+    LMOOD_UNROLL
+    for (int a = 0; a < D; ++a) tr += G[a * D + a];
+    const double t = tr * (1.0 / D);
+    const bool ok = npair > 0.0 && det<D>(G) > 1e-12 * (D == 2 ? t * t : t * t * t);
+    pf[P::F_OK] = ok ? 1.0 : 0.0;
+    double Gi[DD];
+    inverse<D>(G, Gi);
+    LMOOD_UNROLL
+    for (int i = 0; i < DD; ++i) pf[P::F_GI + i] = Gi[i];
+    double gs[NQ][D];
+    LMOOD_UNROLL
+    for (int q = 0; q < NQ; ++q)
+        LMOOD_UNROLL
+        for (int a = 0; a < D; ++a) {
+            double s = 0.0;
+            LMOOD_UNROLL
+            for (int b = 0; b < D; ++b) s += Gi[a * D + b] * r[q][b];
+            gs[q][a] = ok ? s : 0.0;
+            pf[P::F_GS + q * D + a] = gs[q][a];
+        }
+    // corner matrices M_k = sum_{f != k} W_f, W_f = (z / |u_f|) u_f u_f^t, u_f = N_f / D
+    double W[NV][NS];
+    LMOOD_UNROLL
+    for (int f = 0; f < NV; ++f) {
+        double ss = 0.0;
+        LMOOD_UNROLL
+        for (int a = 0; a < D; ++a) ss += N[f * D + a] * N[f * D + a];
+        const double inu = D * adj_rsqrt(ss);
+        pf[P::F_INU + f] = inu;
+        const double w = z * inu * (1.0 / (D * D));
+        LMOOD_UNROLL
+        for (int a = 0; a < D; ++a)
+            LMOOD_UNROLL
+            for (int b = a; b < D; ++b) W[f][sym<D>(a, b)] = w * N[f * D + a] * N[f * D + b];
+    }
+    // F_h at the corners and dv = hv sum_k T(F_h,k) N_k
+    double dv[D] = {};
+    LMOOD_UNROLL
+    for (int k = 0; k < NV; ++k) {
+        double *rk = pk + k * kstride;
+        LMOOD_UNROLL
+        for (int s2 = 0; s2 < NS; ++s2) {
+            double acc = 0.0;
+            LMOOD_UNROLL
+            for (int f = 0; f < NV; ++f)
+                if (f != k) acc += W[f][s2];
+            rk[P::K_M + s2] = acc;
+        }
+        double T[DD], Fh[DD];
+        LMOOD_UNROLL
+        for (int q = 0; q < DD; ++q) {
+            double s = Fc[q];
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) s += gs[D + q][a] * dk[k][a];
+            Fh[q] = s;
+            rk[P::K_FH + q] = s;
+        }
+        stress<D>(Fh, mu, kap, T);
+        LMOOD_UNROLL
+        for (int i = 0; i < D; ++i)
+            LMOOD_UNROLL
+            for (int b = 0; b < D; ++b) dv[i] += T[i * D + b] * N[k * D + b];
+    }
+    const double hv = -0.5 * dt * im * (1.0 / D);
+    LMOOD_UNROLL
+    for (int k = 0; k < NV; ++k) {
+        double *rk = pk + k * kstride;
+        LMOOD_UNROLL
+        for (int i = 0; i < D; ++i) {
+            double s = vc[i];
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) s += gs[i][a] * dk[k][a];
+            rk[P::K_VST + i] = s + hv * dv[i];
+        }
+    }
+    double gv[DD], dFdt[DD];
+    LMOOD_UNROLL
+    for (int i = 0; i < D; ++i)
+        LMOOD_UNROLL
+        for (int a = 0; a < D; ++a) gv[i * D + a] = gs[i][a];
+    mm<D>(gv, Fc, dFdt);
+    LMOOD_UNROLL
+    for (int i = 0; i < DD; ++i) pf[P::F_DFDT + i] = dFdt[i];
+}
+
+// reverse of corner k's packet R_k = M_k v*_k + (1/D) T(F*_k) N_k, F*_k = F_h,k + dt/2 dF/dt,
+// from lR_k [D]; adds lR_k (x) v*_k to lM_k [NS] and writes q2 [Q2_LEN]
+template <int D>
+LMOOD_HD void predict_corner2_vjp(const double *pf, const double *rk, int k, double mu, double kap, double dt,
+                                  const double *lR_k, double *lM_k, double *q2) {
+    using P = PredRec<D>;
+    constexpr int DD = D * D;
+    const double *N = pf + P::F_N + k * D, *vst = rk + P::K_VST;
+    double Fs[DD], lT[DD] = {}, lFs[DD] = {}, T[DD], lvst[D] = {}, lmu = 0.0, lkap = 0.0;
+    for (int q = 0; q < DD; ++q) Fs[q] = rk[P::K_FH + q] + 0.5 * dt * pf[P::F_DFDT + q];
+    for (int a = 0; a < D; ++a) {
+        const double l = lR_k[a];
+        for (int b = 0; b < D; ++b) {
+            lvst[b] += rk[P::K_M + sym<D>(a, b)] * l;
+            lM_k[sym<D>(a, b)] += l * vst[b];
+            lT[a * D + b] += l * N[b] * (1.0 / D);
+        }
+    }
+    stress_vjp<D>(Fs, mu, kap, lT, lFs, lmu, lkap, T);
+    for (int b = 0; b < D; ++b) {
+        double s = 0.0;
+        for (int a = 0; a < D; ++a) s += lR_k[a] * T[a * D + b];
+        q2[P::Q2_LN + b] = s * (1.0 / D);
+    }
+    for (int a = 0; a < D; ++a) q2[P::Q2_LV + a] = lvst[a];
+    for (int q = 0; q < DD; ++q) q2[P::Q2_LF + q] = lFs[q];
+    q2[P::Q2_MU] = lmu;
+    q2[P::Q2_KAP] = lkap;
+}
+
+// reverse of corner k's term of dv = hv sum_k T(F_h,k) N_k, given lacc = hv * (adjoint of dv);
+// writes q1 [Q1_LEN]
+template <int D>
+LMOOD_HD void predict_corner1_vjp(const double *pf, const double *rk, int k, double mu, double kap,
+                                  const double *lacc, double *q1) {
+    using P = PredRec<D>;
+    constexpr int DD = D * D;
+    const double *N = pf + P::F_N + k * D;
+    double lT[DD], lF[DD] = {}, T[DD], lmu = 0.0, lkap = 0.0;
+    for (int i = 0; i < D; ++i)
+        for (int b = 0; b < D; ++b) lT[i * D + b] = lacc[i] * N[b];
+    stress_vjp<D>(rk + P::K_FH, mu, kap, lT, lF, lmu, lkap, T);
+    for (int b = 0; b < D; ++b) {
+        double s = 0.0;
+        for (int i = 0; i < D; ++i) s += lacc[i] * T[i * D + b];
+        q1[P::Q1_LN + b] = s;
+    }
+    for (int q = 0; q < DD; ++q) q1[P::Q1_LF + q] = lF[q];
+    q1[P::Q1_MU] = lmu;
+    q1[P::Q1_KAP] = lkap;
+}
+
+// reverse of the corner matrices M_k = sum_{f != k} W_f (lmk(k): the final adjoint of M_k,
+// NS values) and of the geometry (faces N, centroid): accumulates lz and lxs, given
+// lN [NV][D] and lxcc [D]
+template <int D, class LMK>
+LMOOD_HD void predict_tail_vjp(const double *xs, const double *N, const double *inu, double z, LMK &&lmk,
+                               double *lN, const double *lxcc, double *lxs, double &lz) {
+    constexpr int NV = D + 1, NS = D * (D + 1) / 2;
+    for (int f = 0; f < NV; ++f) {
+        double lW[NS] = {}, u[D];
+        for (int k = 0; k < NV; ++k)
+            if (k != f)
+                for (int s2 = 0; s2 < NS; ++s2) lW[s2] += lmk(k)[s2];
+        for (int a = 0; a < D; ++a) u[a] = N[f * D + a] * (1.0 / D);
+        // full symmetric lW: stored entry s = (a <= b) used once
+        double uWu = 0.0, lWu[D] = {};
+        for (int a = 0; a < D; ++a)
+            for (int b = a; b < D; ++b) {
+                const double l = lW[sym<D>(a, b)];
+                uWu += l * u[a] * u[b];
+                lWu[a] += l * u[b];
+                lWu[b] += l * u[a];
+            }
+        lz += uWu * inu[f];
+        const double c1 = z * inu[f], c3 = c1 * inu[f] * inu[f];
+        for (int a = 0; a < D; ++a) lN[f * D + a] += (c1 * lWu[a] - c3 * uWu * u[a]) * (1.0 / D);
+    }
+    faces_vjp<D>(xs, 0.0, lN, lxs);
+    for (int k = 0; k < NV; ++k)
+        for (int a = 0; a < D; ++a) lxs[k * D + a] += lxcc[a] * (1.0 / NV);
+}
+
+// the rest of a P1 cell's product, from the corner products: q2k(k) and q1k(k) give the
+// records Q2, Q1 of corner k, lmk(k) the final adjoint of the corner matrix M_k (NS values).
+// Accumulates lxs, lvc, lFc, lz and stores the node-moment adjoints through mout. (The loops
+// run field by field, reading the slopes and the corner products as they go, so that few of
+// them are live at once.)
+template <int D, class Q2K, class Q1K, class MO>
+LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const double *Fc, double dt, const double *pf,
+                                 Q2K &&q2k, Q1K &&q1k, double *lxs, double *lxcc, MO &&mout, double *lvc,
+                                 double *lFc) {
+    using Q = Sz<D>;
+    using P = PredRec<D>;
+    constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ;
+    const double *gs = pf + P::F_GS, *Gi = pf + P::F_GI, *dk = pf + P::F_DK;
+    // lxs collects the adjoints of d_k = x_k - x_c directly (lxcc their negated sum)
+    double lgs[NQ][D], ldFdt[DD];
+    // v*_k = v_c + gs_v d_k + dv
+    LMOOD_UNROLL
+    for (int i = 0; i < D; ++i) {
+        double l[NV];
+        LMOOD_UNROLL
+        for (int k = 0; k < NV; ++k) {
+            l[k] = q2k(k)[P::Q2_LV + i];
+            lvc[i] += l[k];
+        }
+        LMOOD_UNROLL
+        for (int a = 0; a < D; ++a) {
+            const double g = gs[i * D + a];
+            double s = 0.0;
+            LMOOD_UNROLL
+            for (int k = 0; k < NV; ++k) {
+                s += l[k] * dk[k * D + a];
+                lxs[k * D + a] += l[k] * g;
+                lxcc[a] -= l[k] * g;
+            }
+            lgs[i][a] = s;
+        }
+    }
+    // F*_k = F_h,k + dt/2 dF/dt, F_h,k = F_c + gs_F d_k
+    LMOOD_UNROLL
+    for (int q = 0; q < DD; ++q) {
+        double l[NV], sfs = 0.0;
+        LMOOD_UNROLL
+        for (int k = 0; k < NV; ++k) {
+            const double lfs = q2k(k)[P::Q2_LF + q];
+            sfs += lfs;
+            l[k] = lfs + q1k(k)[P::Q1_LF + q];
+            lFc[q] += l[k];
+        }
+        ldFdt[q] = 0.5 * dt * sfs;
+        LMOOD_UNROLL
+        for (int a = 0; a < D; ++a) {
+            const double g = gs[(D + q) * D + a];
+            double s = 0.0;
+            LMOOD_UNROLL
+            for (int k = 0; k < NV; ++k) {
+                s += l[k] * dk[k * D + a];
+                lxs[k * D + a] += l[k] * g;
+                lxcc[a] -= l[k] * g;
+            }
+            lgs[D + q][a] = s;
+        }
+    }
+    // dF/dt = gv F_c: lgv = ldFdt F_c^t, lF_c += gv^t ldFdt
+    LMOOD_UNROLL
+    for (int i = 0; i < D; ++i)
+        LMOOD_UNROLL
+        for (int j = 0; j < D; ++j) {
+            double s = 0.0, u = 0.0;
+            LMOOD_UNROLL
+            for (int k = 0; k < D; ++k) {
+                s += ldFdt[i * D + k] * Fc[j * D + k];
+                u += gs[k * D + i] * ldFdt[k * D + j];
+            }
+            lgs[i][j] += s;
+            lFc[i * D + j] += u;
+        }
+    // least squares: gs = Gi r
+    if (pf[P::F_OK] != 0.0) {
+        // gs_q = G^{-1} r_q, G symmetric: lr_q = G^{-1} lgs_q (in place), lG = -sum_q lr_q gs_q^t
+        LMOOD_UNROLL
+        for (int q = 0; q < NQ; ++q) {
+            double lr[D];
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) {
+                double s = 0.0;
+                LMOOD_UNROLL
+                for (int b = 0; b < D; ++b) s += Gi[a * D + b] * lgs[q][b];
+                lr[a] = s;
+            }
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) lgs[q][a] = lr[a];
+        }
+        auto lr = [&](int q, int a) { return lgs[q][a]; };
+        double lG[DD] = {};
+        LMOOD_UNROLL
+        for (int q = 0; q < NQ; ++q)
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a)
+                LMOOD_UNROLL
+                for (int b = 0; b < D; ++b) lG[a * D + b] -= lr(q, a) * gs[q * D + b];
+        // the -w_k q_c terms of r summed over k: lw_k += lwq (the same for every k), and
+        // lq_c -= lr_q . sum_k w_k
+        double lwq[D] = {}, wsum[D] = {};
+        LMOOD_UNROLL
+        for (int q = 0; q < NQ; ++q) {
+            const double qc = q < D ? vc[q] : Fc[q - D];
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) lwq[a] -= lr(q, a) * qc;
+        }
+        LMOOD_UNROLL
+        for (int k = 0; k < NV; ++k) {
+            const double nk = mom(k, Q::M_N);
+            double S1[D], w[D], lS1[D] = {}, lw[D] = {}, lS2[NS] = {}, ln_ = 0.0, ldk[D] = {};
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) {
+                S1[a] = mom(k, Q::M_S1 + a);
+                w[a] = S1[a] + nk * dk[k * D + a];
+            }
+            // G += S2 + S1 d^t + d w^t
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a)
+                LMOOD_UNROLL
+                for (int b = 0; b < D; ++b) {
+                    const double l = lG[a * D + b];
+                    lS2[sym<D>(a, b)] += l;
+                    lS1[a] += l * dk[k * D + b];
+                    ldk[b] += l * S1[a];
+                    ldk[a] += l * w[b];
+                    lw[b] += l * dk[k * D + a];
+                }
+            // r_q += T_q + d U_q - w q_c
+            LMOOD_UNROLL
+            for (int q = 0; q < NQ; ++q) {
+                const double Uq = mom(k, Q::M_U + q);
+                double lU = 0.0;
+                LMOOD_UNROLL
+                for (int a = 0; a < D; ++a) {
+                    const double l = lr(q, a);
+                    mout(k, Q::M_T + q * D + a, l);
+                    ldk[a] += l * Uq;
+                    lU += l * dk[k * D + a];
+                }
+                mout(k, Q::M_U + q, lU);
+            }
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) {
+                lw[a] += lwq[a];
+                wsum[a] += w[a];
+            }
+            // w = S1 + n d
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) {
+                lS1[a] += lw[a];
+                ldk[a] += nk * lw[a];
+                ln_ += lw[a] * dk[k * D + a];
+            }
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) {
+                mout(k, Q::M_S1 + a, lS1[a]);
+                lxs[k * D + a] += ldk[a];
+                lxcc[a] -= ldk[a];
+            }
+            LMOOD_UNROLL
+            for (int s2 = 0; s2 < NS; ++s2) mout(k, Q::M_S2 + s2, lS2[s2]);
+            mout(k, Q::M_N, ln_);
+        }
+        LMOOD_UNROLL
+        for (int q = 0; q < NQ; ++q) {
+            double lq = 0.0;
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) lq -= lr(q, a) * wsum[a];
+            if (q < D) lvc[q] += lq;
+            else lFc[q - D] += lq;
+        }
+    } else {
+        for (int k = 0; k < NV; ++k)
+            for (int j = 0; j < Q::NMOM; ++j) mout(k, j, 0.0);
+    }
+}
+
+// the corner matrices' and the geometry's part of a P1 cell's product (predict_tail_vjp with
+// the face vectors of the record and lN from the corner products)
+template <int D, class LMK, class Q2K, class Q1K>
+LMOOD_HD void predict_tail_p1_vjp(const double *xs, double z, const double *pf, LMK &&lmk, Q2K &&q2k, Q1K &&q1k,
+                                  const double *lxcc, double *lxs, double &lz) {
+    using P = PredRec<D>;
+    constexpr int NV = D + 1;
+    double lN[NV * D];
+    LMOOD_UNROLL
+    for (int k = 0; k < NV; ++k)
+        LMOOD_UNROLL
+        for (int b = 0; b < D; ++b) lN[k * D + b] = q2k(k)[P::Q2_LN + b] + q1k(k)[P::Q1_LN + b];
+    predict_tail_vjp<D>(xs, pf + P::F_N, pf + P::F_INU, z, lmk, lN, lxcc, lxs, lz);
+}
+
+template <int D, class MO>
+LMOOD_HD void predict_p0_vjp(const double *xs, const double *vc, const double *Fc, double z, double mu, double kap,
+                             double *lM, const double *lR, double *lxs, MO &&mout, double *lvc, double *lFc,
+                             double &lz, double &lmu, double &lkap);
+
 // Product of predict_fw: (lM [NV][NS], lR [NV][D]) -> accumulates lxs [NV][D], lvc [D],
 // lFc [DD], lz, lmu, lkap, and stores the adjoints of the node moments through
 // mout(k, j, value) (every (k, j) exactly once; zero where the packets do not depend on them).
@@ -487,16 +970,48 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
                           double kap, double im, double dt, int ord, const double *lM_in, const double *lR, double *lxs,
                           MO &&mout, double *lvc, double *lFc, double &lz, double &lmu, double &lkap) {
     using Q = Sz<D>;
-    constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ, NM = Q::NMOM;
-    double V, N[NV * D], xcc[D];
-    faces<D>(xs, V, N);
-    for (int a = 0; a < D; ++a) {
-        double s = 0.0;
-        for (int k = 0; k < NV; ++k) s += xs[k * D + a];
-        xcc[a] = s * (1.0 / NV);
+    using P = PredRec<D>;
+    constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NM = Q::NMOM;
+    double lM[NV * NS];
+    for (int i = 0; i < NV * NS; ++i) lM[i] = lM_in[i];
+    if (ord != 1) {
+        double pf[P::F_LEN], pk[NV * P::K_LEN], q2[NV][P::Q2_LEN], q1[NV][P::Q1_LEN];
+        predict_fw_rec<D>(xs, mom, vc, Fc, z, mu, kap, im, dt, pf, pk, P::K_LEN);
+        double ldv[D] = {};
+        for (int k = 0; k < NV; ++k) {
+            predict_corner2_vjp<D>(pf, pk + k * P::K_LEN, k, mu, kap, dt, lR + k * D, lM + k * NS, q2[k]);
+            for (int a = 0; a < D; ++a) ldv[a] += q2[k][P::Q2_LV + a];
+        }
+        const double hv = -0.5 * dt * im * (1.0 / D);
+        double lacc[D];
+        for (int a = 0; a < D; ++a) lacc[a] = hv * ldv[a];
+        for (int k = 0; k < NV; ++k) predict_corner1_vjp<D>(pf, pk + k * P::K_LEN, k, mu, kap, lacc, q1[k]);
+        for (int k = 0; k < NV; ++k) {
+            lmu += q2[k][P::Q2_MU] + q1[k][P::Q1_MU];
+            lkap += q2[k][P::Q2_KAP] + q1[k][P::Q1_KAP];
+        }
+        double lxcc[D] = {};
+        auto q2k = [&](int k) { return (const double *)q2[k]; };
+        auto q1k = [&](int k) { return (const double *)q1[k]; };
+        predict_finish_vjp<D>(mom, vc, Fc, dt, pf, q2k, q1k, lxs, lxcc, mout, lvc, lFc);
+        predict_tail_p1_vjp<D>(xs, z, pf, [&](int k) { return (const double *)(lM + k * NS); }, q2k, q1k, lxcc, lxs,
+                               lz);
+        return;
     }
-    // M_k = sum_{f != k} W_f, W_f = (z / |u_f|) u_f u_f^t, u_f = N_f / D
-    double Mo[NV * NS], inu[NV];  // inu = 1 / |u_f|
+    predict_p0_vjp<D>(xs, vc, Fc, z, mu, kap, lM, lR, lxs, mout, lvc, lFc, lz, lmu, lkap);
+}
+
+// the product for a first-order cell: R_k = M_k v_c + (1/D) T(F_c) N_k (lM [NV][NS] is
+// updated in place; the node moments do not enter)
+template <int D, class MO>
+LMOOD_HD void predict_p0_vjp(const double *xs, const double *vc, const double *Fc, double z, double mu, double kap,
+                             double *lM, const double *lR, double *lxs, MO &&mout, double *lvc, double *lFc,
+                             double &lz, double &lmu, double &lkap) {
+    using Q = Sz<D>;
+    constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NM = Q::NMOM;
+    double V, N[NV * D], inu[NV], lN[NV * D] = {}, lxcc[D] = {};
+    faces<D>(xs, V, N);
+    double Mo[NV * NS];
     {
         double W[NV][NS];
         for (int f = 0; f < NV; ++f) {
@@ -515,250 +1030,24 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
                 Mo[k * NS + s2] = acc;
             }
     }
-    auto Mfull = [&](int k, int a, int b) { return Mo[k * NS + sym<D>(a, b)]; };
-    double lM[NV * NS], lN[NV * D] = {}, lxcc[D] = {};
-    for (int i = 0; i < NV * NS; ++i) lM[i] = lM_in[i];
-    // R_k = M_k vst_k + (1/D) T_k N_k: the parts that do not need T_k (lvst, lM, lT)
-    auto packet_rhs_vjp = [&](int k, const double *vst, double *lvst, double *lT) {
+    double T[DD], lT[DD] = {}, lF[DD] = {};
+    for (int k = 0; k < NV; ++k)
         for (int a = 0; a < D; ++a) {
             const double l = lR[k * D + a];
             for (int b = 0; b < D; ++b) {
-                lvst[b] += Mfull(k, a, b) * l;
-                lM[k * NS + sym<D>(a, b)] += l * vst[b];
+                lvc[b] += Mo[k * NS + sym<D>(a, b)] * l;
+                lM[k * NS + sym<D>(a, b)] += l * vc[b];
                 lT[a * D + b] += l * N[k * D + b] * (1.0 / D);
             }
         }
-    };
-    // ... and the part that does: lN_k += (1/D) T_k^t lR_k
-    auto packet_rhs_vjp_T = [&](int k, const double *T) {
+    stress_vjp<D>(Fc, mu, kap, lT, lF, lmu, lkap, T);
+    for (int k = 0; k < NV; ++k)
         for (int a = 0; a < D; ++a)
             for (int b = 0; b < D; ++b) lN[k * D + b] += lR[k * D + a] * T[a * D + b] * (1.0 / D);
-    };
-    auto zero_moments = [&]() {
-        for (int k = 0; k < NV; ++k)
-            for (int j = 0; j < NM; ++j) mout(k, j, 0.0);
-    };
-    if (ord == 1) {
-        double T[DD], lT[DD] = {}, lF[DD] = {};
-        for (int k = 0; k < NV; ++k) {
-            double lvst[D] = {};
-            packet_rhs_vjp(k, vc, lvst, lT);
-            for (int a = 0; a < D; ++a) lvc[a] += lvst[a];
-        }
-        stress_vjp<D>(Fc, mu, kap, lT, lF, lmu, lkap, T);
-        for (int k = 0; k < NV; ++k) packet_rhs_vjp_T(k, T);
-        for (int q = 0; q < DD; ++q) lFc[q] += lF[q];
-        zero_moments();
-    } else {
-        // ---- recompute the forward intermediates
-        double G[DD] = {}, r[NQ][D] = {}, qc[NQ], dk[NV][D], npair = -NV;
-        for (int q = 0; q < NQ; ++q) qc[q] = q < D ? vc[q] : Fc[q - D];
-        for (int k = 0; k < NV; ++k) {
-            const double nk = mom(k, Q::M_N);
-            npair += nk;
-            double S1[D], w[D];
-            for (int a = 0; a < D; ++a) {
-                dk[k][a] = xs[k * D + a] - xcc[a];
-                S1[a] = mom(k, Q::M_S1 + a);
-                w[a] = S1[a] + nk * dk[k][a];
-            }
-            for (int a = 0; a < D; ++a)
-                for (int b = 0; b < D; ++b) G[a * D + b] += mom(k, Q::M_S2 + sym<D>(a, b)) + S1[a] * dk[k][b] + dk[k][a] * w[b];
-            for (int q = 0; q < NQ; ++q)
-                for (int a = 0; a < D; ++a)
-                    r[q][a] += mom(k, Q::M_T + q * D + a) + dk[k][a] * mom(k, Q::M_U + q) - w[a] * qc[q];
-        }
-        double tr = 0.0;
-        for (int a = 0; a < D; ++a) tr += G[a * D + a];
-        const double t = tr * (1.0 / D);
-        const bool ok = npair > 0.0 && det<D>(G) > 1e-12 * (D == 2 ? t * t : t * t * t);
-        double Gi[DD], gs[NQ][D];
-        inverse<D>(G, Gi);
-        for (int q = 0; q < NQ; ++q)
-            for (int a = 0; a < D; ++a) {
-                double s = 0.0;
-                for (int b = 0; b < D; ++b) s += Gi[a * D + b] * r[q][b];
-                gs[q][a] = ok ? s : 0.0;
-            }
-        auto Fh_of = [&](int k, double *Fh) {
-            for (int q = 0; q < DD; ++q) {
-                double s = Fc[q];
-                for (int a = 0; a < D; ++a) s += gs[D + q][a] * dk[k][a];
-                Fh[q] = s;
-            }
-        };
-        double gv[DD], dFdt[DD], dvraw[D] = {};
-        const double hv = -0.5 * dt * im * (1.0 / D);
-        for (int k = 0; k < NV; ++k) {
-            double Fh[DD], T[DD];
-            Fh_of(k, Fh);
-            stress<D>(Fh, mu, kap, T);
-            for (int i = 0; i < D; ++i)
-                for (int b = 0; b < D; ++b) dvraw[i] += T[i * D + b] * N[k * D + b];
-        }
-        for (int i = 0; i < D; ++i)
-            for (int a = 0; a < D; ++a) gv[i * D + a] = gs[i][a];
-        mm<D>(gv, Fc, dFdt);
-        // ---- reverse of pass 2 (the corner predictor and packets)
-        double lgs[NQ][D] = {}, ldk[NV][D] = {}, ldv[D] = {}, ldFdt[DD] = {}, lFh[NV][DD] = {};
-        for (int k = 0; k < NV; ++k) {
-            double vst[D], Fs[DD], T[DD], lvst[D] = {}, lT[DD] = {}, lFs[DD] = {};
-            for (int i = 0; i < D; ++i) {
-                double s = vc[i];
-                for (int a = 0; a < D; ++a) s += gs[i][a] * dk[k][a];
-                vst[i] = s + hv * dvraw[i];
-            }
-            Fh_of(k, Fs);
-            for (int q = 0; q < DD; ++q) Fs[q] += 0.5 * dt * dFdt[q];
-            packet_rhs_vjp(k, vst, lvst, lT);
-            stress_vjp<D>(Fs, mu, kap, lT, lFs, lmu, lkap, T);
-            packet_rhs_vjp_T(k, T);
-            for (int q = 0; q < DD; ++q) {
-                lFh[k][q] += lFs[q];
-                ldFdt[q] += 0.5 * dt * lFs[q];
-            }
-            for (int i = 0; i < D; ++i) {
-                lvc[i] += lvst[i];
-                ldv[i] += lvst[i];
-                for (int a = 0; a < D; ++a) {
-                    lgs[i][a] += lvst[i] * dk[k][a];
-                    ldk[k][a] += lvst[i] * gs[i][a];
-                }
-            }
-        }
-        // dFdt = gv Fc
-        double lgv[DD];
-        mmt<D>(ldFdt, Fc, lgv);  // lgv = ldFdt Fc^t
-        {
-            double t2[DD];
-            mtm<D>(gv, ldFdt, t2);  // lFc += gv^t ldFdt
-            for (int q = 0; q < DD; ++q) lFc[q] += t2[q];
-        }
-        for (int i = 0; i < D; ++i)
-            for (int a = 0; a < D; ++a) lgs[i][a] += lgv[i * D + a];
-        // ---- reverse of pass 1: dv = hv sum_k T(Fh_k) N_k
-        double lacc[D];
-        for (int i = 0; i < D; ++i) lacc[i] = hv * ldv[i];
-        for (int k = 0; k < NV; ++k) {
-            double Fh[DD], T[DD], lT[DD], lF[DD] = {};
-            Fh_of(k, Fh);
-            for (int i = 0; i < D; ++i)
-                for (int b = 0; b < D; ++b) lT[i * D + b] = lacc[i] * N[k * D + b];
-            stress_vjp<D>(Fh, mu, kap, lT, lF, lmu, lkap, T);
-            for (int i = 0; i < D; ++i)
-                for (int b = 0; b < D; ++b) lN[k * D + b] += lacc[i] * T[i * D + b];
-            for (int q = 0; q < DD; ++q) lFh[k][q] += lF[q];
-        }
-        // Fh_k = Fc + gsF dk
-        for (int k = 0; k < NV; ++k)
-            for (int q = 0; q < DD; ++q) {
-                lFc[q] += lFh[k][q];
-                for (int a = 0; a < D; ++a) {
-                    lgs[D + q][a] += lFh[k][q] * dk[k][a];
-                    ldk[k][a] += lFh[k][q] * gs[D + q][a];
-                }
-            }
-        // ---- least squares: gs = Gi r
-        if (ok) {
-            // gs_q = G^{-1} r_q, G symmetric: lr_q = G^{-1} lgs_q, lG = -sum_q lr_q gs_q^t
-            double lr[NQ][D], lG[DD] = {};
-            for (int q = 0; q < NQ; ++q)
-                for (int a = 0; a < D; ++a) {
-                    double s = 0.0;
-                    for (int b = 0; b < D; ++b) s += Gi[a * D + b] * lgs[q][b];
-                    lr[q][a] = s;
-                }
-            for (int q = 0; q < NQ; ++q)
-                for (int a = 0; a < D; ++a)
-                    for (int b = 0; b < D; ++b) lG[a * D + b] -= lr[q][a] * gs[q][b];
-            // the -w_k q_c terms of r summed over k: lw_k += lwq (the same for every k), and
-            // lq_c -= lr_q . sum_k w_k
-            double lwq[D] = {}, wsum[D] = {};
-            for (int q = 0; q < NQ; ++q)
-                for (int a = 0; a < D; ++a) lwq[a] -= lr[q][a] * qc[q];
-            for (int k = 0; k < NV; ++k) {
-                const double nk = mom(k, Q::M_N);
-                double S1[D], w[D], lS1[D] = {}, lw[D] = {}, lS2[NS] = {}, ln_ = 0.0;
-                for (int a = 0; a < D; ++a) {
-                    S1[a] = mom(k, Q::M_S1 + a);
-                    w[a] = S1[a] + nk * dk[k][a];
-                }
-                // G += S2 + S1 d^t + d w^t
-                for (int a = 0; a < D; ++a)
-                    for (int b = 0; b < D; ++b) {
-                        const double l = lG[a * D + b];
-                        lS2[sym<D>(a, b)] += l;
-                        lS1[a] += l * dk[k][b];
-                        ldk[k][b] += l * S1[a];
-                        ldk[k][a] += l * w[b];
-                        lw[b] += l * dk[k][a];
-                    }
-                // r_q += T_q + d U_q - w q_c
-                for (int q = 0; q < NQ; ++q) {
-                    const double Uq = mom(k, Q::M_U + q);
-                    double lU = 0.0;
-                    for (int a = 0; a < D; ++a) {
-                        const double l = lr[q][a];
-                        mout(k, Q::M_T + q * D + a, l);
-                        ldk[k][a] += l * Uq;
-                        lU += l * dk[k][a];
-                    }
-                    mout(k, Q::M_U + q, lU);
-                }
-                for (int a = 0; a < D; ++a) {
-                    lw[a] += lwq[a];
-                    wsum[a] += w[a];
-                }
-                // w = S1 + n d
-                for (int a = 0; a < D; ++a) {
-                    lS1[a] += lw[a];
-                    ldk[k][a] += nk * lw[a];
-                    ln_ += lw[a] * dk[k][a];
-                }
-                for (int a = 0; a < D; ++a) mout(k, Q::M_S1 + a, lS1[a]);
-                for (int s2 = 0; s2 < NS; ++s2) mout(k, Q::M_S2 + s2, lS2[s2]);
-                mout(k, Q::M_N, ln_);
-            }
-            for (int q = 0; q < NQ; ++q) {
-                double lq = 0.0;
-                for (int a = 0; a < D; ++a) lq -= lr[q][a] * wsum[a];
-                if (q < D) lvc[q] += lq;
-                else lFc[q - D] += lq;
-            }
-        } else {
-            zero_moments();
-        }
-        // d_k = xs_k - xcc
-        for (int k = 0; k < NV; ++k)
-            for (int a = 0; a < D; ++a) {
-                lxs[k * D + a] += ldk[k][a];
-                lxcc[a] -= ldk[k][a];
-            }
-    }
-    // ---- M_k = sum_{f != k} W_f;  W_f = (z / |u_f|) u_f u_f^t, u_f = N_f / D
-    for (int f = 0; f < NV; ++f) {
-        double lW[NS] = {}, u[D];
-        for (int k = 0; k < NV; ++k)
-            if (k != f)
-                for (int s2 = 0; s2 < NS; ++s2) lW[s2] += lM[k * NS + s2];
-        for (int a = 0; a < D; ++a) u[a] = N[f * D + a] * (1.0 / D);
-        // full symmetric lW: stored entry s = (a <= b) used once
-        double uWu = 0.0, lWu[D] = {};
-        for (int a = 0; a < D; ++a)
-            for (int b = a; b < D; ++b) {
-                const double l = lW[sym<D>(a, b)];
-                uWu += l * u[a] * u[b];
-                lWu[a] += l * u[b];
-                lWu[b] += l * u[a];
-            }
-        lz += uWu * inu[f];
-        const double c1 = z * inu[f], c3 = c1 * inu[f] * inu[f];
-        for (int a = 0; a < D; ++a) lN[f * D + a] += (c1 * lWu[a] - c3 * uWu * u[a]) * (1.0 / D);
-    }
-    // ---- geometry: N(xs), xcc = mean(xs)
-    faces_vjp<D>(xs, 0.0, lN, lxs);
+    for (int q = 0; q < DD; ++q) lFc[q] += lF[q];
     for (int k = 0; k < NV; ++k)
-        for (int a = 0; a < D; ++a) lxs[k * D + a] += lxcc[a] * (1.0 / NV);
+        for (int j = 0; j < NM; ++j) mout(k, j, 0.0);
+    predict_tail_vjp<D>(xs, N, inu, z, [&](int k) { return (const double *)(lM + k * NS); }, lN, lxcc, lxs, lz);
 }
 
 // ---------------------------------------------------------------------------------------

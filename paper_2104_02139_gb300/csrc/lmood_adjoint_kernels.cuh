@@ -135,40 +135,88 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_nodes(Geo g, Fld f
 }
 
 // ---------------------------------------------------------------------------------------
-// force_p0: the t^0 packets (every cell first order)
-#ifndef LMOOD_ADJ_PREDICT_MINB
-#define LMOOD_ADJ_PREDICT_MINB 1  // resident blocks of 128 asked of the compiler (2D)
-#endif
-template <int D>
-__global__ void __launch_bounds__(128, D == 2 ? LMOOD_ADJ_PREDICT_MINB : 1) k_adj_predict(Geo g, Fld f, Prm prm,
-                                                                                          AdjBuf a, int force_p0) {
+// Reverse of geometry, least squares, predictor and packets. A first-order cell's product is
+// small and stays whole (k_adj_predict); a second-order cell's runs as four kernels, so that
+// no thread holds the cell's forward intermediates and all its adjoint accumulators at once:
+//   k_adj_pred_fw  cells   : forward intermediates -> records pf (cell), pk (corners)
+//   k_adj_pred_c2  corners : reverse of the packet R_k (one stress product) -> q2, lM_k
+//   k_adj_pred_c1  corners : reverse of the corner's term of dv (one stress product) -> q1
+//   k_adj_predict  cells   : the rest (slopes, least squares, corner matrices, geometry), and
+//                            the whole product of the first-order cells
+// force_p0: the t^0 packets (every cell first order; only k_adj_predict runs).
+// ---------------------------------------------------------------------------------------
+template <int D> __device__ __forceinline__ bool second_order(const Fld &f, int c, int force_p0) {
+    return !force_p0 && f.order[c] != 1;
+}
+
+template <int D> __global__ void __launch_bounds__(128) k_adj_pred_fw(Geo g, Fld f, Prm prm, AdjBuf a) {
     using Q = adj::Sz<D>;
-    using R = AdjRec<D>;
-    constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NX = NV * D;
+    using P = adj::PredRec<D>;
+    constexpr int NV = Q::NV, DD = Q::DD, NX = NV * D;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
+    if (c >= g.N || !second_order<D>(f, c, 0)) return;
     const int N = g.N, Np = g.Np;
-    double xs[NX], vc[D], Fc[DD], lM[NV * NS], lR[NX];
+    double xs[NX], vc[D], Fc[DD];
     adj::Mom<D> mom;
     mom.stride = Np;
     for (int k = 0; k < NV; ++k) {
         const int p = g.c2n[k * N + c];
         mom.p[k] = f.mom + p;
         for (int b = 0; b < D; ++b) xs[k * D + b] = f.x[b * Np + p];
-        const double *r = a.cr + (size_t)(k * N + c) * R::CR;
-        for (int b = 0; b < D; ++b) lR[k * D + b] = r[R::CR_R + b];
-        for (int s = 0; s < NS; ++s) lM[k * NS + s] = r[R::CR_M + s];
     }
     for (int b = 0; b < D; ++b) vc[b] = f.v[b * N + c];
     for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
     const double mu = f.mu[c], kap = kappa_of(prm, mu), dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
-    const int ord = force_p0 ? 1 : f.order[c];
-    double lxs[NX] = {}, lvc[D] = {}, lF[DD] = {}, lz = 0.0, lmu = 0.0, lkap = 0.0;
-    double *ccr = a.cc + (size_t)c * R::CC;
-    // node-moment adjoints: the parts equal at every corner (lT, lS2) into the cell record
-    // (stored once, at k = 0), the others into the corner records
-    auto mout = [&](int k, int j, double v) {
-        double *cpr = a.cp + (size_t)(k * N + c) * R::CP;
+    adj::predict_fw_rec<D>(xs, mom, vc, Fc, f.z[c], mu, kap, f.im[c], dt, a.pf + (size_t)c * P::F_LEN,
+                           a.pk + (size_t)c * P::K_LEN, (long)N * P::K_LEN);
+}
+
+template <int D> __global__ void __launch_bounds__(128) k_adj_pred_c2(Geo g, Fld f, Prm prm, AdjBuf a) {
+    using R = AdjRec<D>;
+    using P = adj::PredRec<D>;
+    constexpr int NS = R::NS;
+    const int N = g.N;
+    const int cid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cid >= (D + 1) * N) return;
+    const int c = cell_of_corner<D>(cid, N), k = (cid - c) / N;
+    if (!second_order<D>(f, c, 0)) return;
+    const double mu = f.mu[c], kap = kappa_of(prm, mu), dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
+    double *cr = a.cr + (size_t)cid * R::CR;
+    double lR[D], lM[NS];
+    for (int b = 0; b < D; ++b) lR[b] = cr[R::CR_R + b];
+    for (int s2 = 0; s2 < NS; ++s2) lM[s2] = cr[R::CR_M + s2];
+    adj::predict_corner2_vjp<D>(a.pf + (size_t)c * P::F_LEN, a.pk + (size_t)cid * P::K_LEN, k, mu, kap, dt, lR, lM,
+                                a.q2 + (size_t)cid * P::Q2_LEN);
+    for (int s2 = 0; s2 < NS; ++s2) cr[R::CR_M + s2] = lM[s2];
+}
+
+template <int D> __global__ void __launch_bounds__(128) k_adj_pred_c1(Geo g, Fld f, Prm prm, AdjBuf a) {
+    using P = adj::PredRec<D>;
+    const int N = g.N;
+    const int cid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cid >= (D + 1) * N) return;
+    const int c = cell_of_corner<D>(cid, N), k = (cid - c) / N;
+    if (!second_order<D>(f, c, 0)) return;
+    const double mu = f.mu[c], kap = kappa_of(prm, mu), dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
+    // the adjoint of dv = hv sum_k T(F_h,k) N_k is the sum of the corners' lv*
+    double lacc[D] = {};
+    for (int kk = 0; kk <= D; ++kk)
+        for (int b = 0; b < D; ++b) lacc[b] += a.q2[(size_t)(kk * N + c) * P::Q2_LEN + P::Q2_LV + b];
+    const double hv = -0.5 * dt * f.im[c] * (1.0 / D);
+    for (int b = 0; b < D; ++b) lacc[b] *= hv;
+    adj::predict_corner1_vjp<D>(a.pf + (size_t)c * P::F_LEN, a.pk + (size_t)cid * P::K_LEN, k, mu, kap, lacc,
+                                a.q1 + (size_t)cid * P::Q1_LEN);
+}
+
+// node-moment adjoint writer of cell c: the parts equal at every corner (lT, lS2) into the
+// cell record (stored once, at k = 0), the others into the corner records
+template <int D> struct MomOut {
+    double *cp, *ccr;
+    int N, c;
+    __device__ void operator()(int k, int j, double v) const {
+        using Q = adj::Sz<D>;
+        using R = AdjRec<D>;
+        double *cpr = cp + (size_t)(k * N + c) * R::CP;
         if (j >= Q::M_T) {
             if (k == 0) ccr[R::CC_T + (j - Q::M_T)] = v;
         } else if (j >= Q::M_U) {
@@ -180,15 +228,85 @@ __global__ void __launch_bounds__(128, D == 2 ? LMOOD_ADJ_PREDICT_MINB : 1) k_ad
         } else {
             cpr[R::CP_N] = v;
         }
-    };
-    adj::predict_vjp<D>(xs, mom, vc, Fc, f.z[c], mu, kap, f.im[c], dt, ord, lM, lR, lxs, mout, lvc, lF, lz, lmu,
-                        lkap);
-    for (int k = 0; k < NV; ++k)
+    }
+};
+
+template <int D>
+__device__ __forceinline__ void adj_predict_out(const AdjBuf &a, const Prm &prm, int N, int c, const double *lxs,
+                                                const double *lvc, const double *lF, double lz, double lmu,
+                                                double lkap) {
+    using R = AdjRec<D>;
+    for (int k = 0; k <= D; ++k)
         for (int b = 0; b < D; ++b) a.cp[(size_t)(k * N + c) * R::CP + R::CP_X + b] = lxs[k * D + b];
     for (int b = 0; b < D; ++b) a.lv0[b * N + c] += lvc[b];
-    for (int q = 0; q < DD; ++q) a.lF0[q * N + c] += lF[q];
+    for (int q = 0; q < D * D; ++q) a.lF0[q * N + c] += lF[q];
     a.lz0[c] = lz;
     a.lmu[c] += lmu + lkap * kappa_mu_factor<D>(prm);
+}
+
+// the rest of a second-order cell's product (after k_adj_pred_c1) but the corner matrices and
+// the geometry: the slopes, dF/dt and the least squares; writes the position adjoints of
+// d_k = x_k - x_c (the corner records) and x_c (lxcc, into the pass-1 records' spare room:
+// the pass-1 records are consumed here)
+template <int D> __global__ void __launch_bounds__(128) k_adj_pred_fin(Geo g, Fld f, Prm prm, AdjBuf a) {
+    using Q = adj::Sz<D>;
+    using R = AdjRec<D>;
+    using P = adj::PredRec<D>;
+    constexpr int NV = Q::NV, DD = Q::DD, NX = NV * D;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N || !second_order<D>(f, c, 0)) return;
+    const int N = g.N, Np = g.Np;
+    double vc[D], Fc[DD];
+    adj::Mom<D> mom;
+    mom.stride = Np;
+    for (int k = 0; k < NV; ++k) mom.p[k] = f.mom + g.c2n[k * N + c];
+    for (int b = 0; b < D; ++b) vc[b] = f.v[b * N + c];
+    for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
+    const double dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
+    double lxs[NX] = {}, lxcc[D] = {}, lvc[D] = {}, lF[DD] = {}, lmu = 0.0, lkap = 0.0;
+    for (int k = 0; k < NV; ++k) {
+        const double *q2 = a.q2 + (size_t)(k * N + c) * P::Q2_LEN, *q1 = a.q1 + (size_t)(k * N + c) * P::Q1_LEN;
+        lmu += q2[P::Q2_MU] + q1[P::Q1_MU];
+        lkap += q2[P::Q2_KAP] + q1[P::Q1_KAP];
+    }
+    adj::predict_finish_vjp<D>(
+        mom, vc, Fc, dt, a.pf + (size_t)c * P::F_LEN,
+        [&](int k) { return (const double *)(a.q2 + (size_t)(k * N + c) * P::Q2_LEN); },
+        [&](int k) { return (const double *)(a.q1 + (size_t)(k * N + c) * P::Q1_LEN); }, lxs, lxcc,
+        MomOut<D>{a.cp, a.cc + (size_t)c * R::CC, N, c}, lvc, lF);
+    for (int k = 0; k < NV; ++k)
+        for (int b = 0; b < D; ++b) a.cp[(size_t)(k * N + c) * R::CP + R::CP_X + b] = lxs[k * D + b];
+    // lxcc for the tail, in the first corner's pass-1 record (its lF_h is consumed)
+    for (int b = 0; b < D; ++b) a.q1[(size_t)c * P::Q1_LEN + P::Q1_LF + b] = lxcc[b];
+    for (int b = 0; b < D; ++b) a.lv0[b * N + c] += lvc[b];
+    for (int q = 0; q < DD; ++q) a.lF0[q * N + c] += lF[q];
+    a.lmu[c] += lmu + lkap * kappa_mu_factor<D>(prm);
+}
+
+// the whole product of a first-order cell (force_p0: every cell, the t^0 packets)
+template <int D>
+__global__ void __launch_bounds__(128) k_adj_predict(Geo g, Fld f, Prm prm, AdjBuf a, int force_p0) {
+    using Q = adj::Sz<D>;
+    using R = AdjRec<D>;
+    constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NX = NV * D;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N || second_order<D>(f, c, force_p0)) return;
+    const int N = g.N, Np = g.Np;
+    double xs[NX], vc[D], Fc[DD], lM[NV * NS], lR[NX];
+    for (int k = 0; k < NV; ++k) {
+        const int p = g.c2n[k * N + c];
+        for (int b = 0; b < D; ++b) xs[k * D + b] = f.x[b * Np + p];
+        const double *r = a.cr + (size_t)(k * N + c) * R::CR;
+        for (int b = 0; b < D; ++b) lR[k * D + b] = r[R::CR_R + b];
+        for (int s = 0; s < NS; ++s) lM[k * NS + s] = r[R::CR_M + s];
+    }
+    for (int b = 0; b < D; ++b) vc[b] = f.v[b * N + c];
+    for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
+    const double mu = f.mu[c], kap = kappa_of(prm, mu);
+    double lxs[NX] = {}, lvc[D] = {}, lF[DD] = {}, lz = 0.0, lmu = 0.0, lkap = 0.0;
+    adj::predict_p0_vjp<D>(xs, vc, Fc, f.z[c], mu, kap, lM, lR, lxs, MomOut<D>{a.cp, a.cc + (size_t)c * R::CC, N, c},
+                           lvc, lF, lz, lmu, lkap);
+    adj_predict_out<D>(a, prm, N, c, lxs, lvc, lF, lz, lmu, lkap);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -221,18 +339,35 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_momsum(Geo g, AdjB
 // per cell: the reverse of the node moments at its corners (the cell as a neighbour of each
 // of its nodes), of its centroid x_c = mean of its nodes, and of the impedance
 // z^n = Z(F^n, m / V(x^n), mu)
-template <int D> __global__ void __launch_bounds__(128) k_adj_cells(Geo g, Fld f, Prm prm, AdjBuf a) {
+template <int D> __global__ void __launch_bounds__(128) k_adj_cells(Geo g, Fld f, Prm prm, AdjBuf a, int tail) {
     using Q = adj::Sz<D>;
+    using R = AdjRec<D>;
+    using P = adj::PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NQ = Q::NQ, NX = NV * D, NM = Q::NMOM;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     const int N = g.N, Np = g.Np;
     double xs[NX], xc[D], q[NQ], lxc[D] = {}, lq[NQ] = {}, lxp[NX] = {};
+    for (int k = 0; k < NV; ++k) {
+        const int p = g.c2n[k * N + c];
+        for (int b = 0; b < D; ++b) xs[k * D + b] = f.x[b * Np + p];
+    }
+    // a second-order cell's predictor product ends here: its corner matrices and geometry
+    // (lz^n, and position adjoints into lxp); lxcc was left in the first corner's pass-1 record
+    if (tail && second_order<D>(f, c, 0)) {
+        double lxcc[D], lz = 0.0;
+        for (int b = 0; b < D; ++b) lxcc[b] = a.q1[(size_t)c * P::Q1_LEN + P::Q1_LF + b];
+        adj::predict_tail_p1_vjp<D>(
+            xs, f.z[c], a.pf + (size_t)c * P::F_LEN,
+            [&](int k) { return (const double *)(a.cr + (size_t)(k * N + c) * R::CR + R::CR_M); },
+            [&](int k) { return (const double *)(a.q2 + (size_t)(k * N + c) * P::Q2_LEN); },
+            [&](int k) { return (const double *)(a.q1 + (size_t)(k * N + c) * P::Q1_LEN); }, lxcc, lxp, lz);
+        a.lz0[c] = lz;
+    }
     for (int b = 0; b < D; ++b) xc[b] = f.xc[b * N + c];
     for (int i = 0; i < NQ; ++i) q[i] = i < D ? f.v[i * N + c] : f.F[(i - D) * N + c];
     for (int k = 0; k < NV; ++k) {
         const int p = g.c2n[k * N + c];
-        for (int b = 0; b < D; ++b) xs[k * D + b] = f.x[b * Np + p];
         const double *lm = a.lm + (size_t)p * NM;
         adj::moments_corner_vjp<D>([&](int j) { return lm[j]; }, xc, xs + k * D, q, lxc, lq, lxp + k * D);
     }

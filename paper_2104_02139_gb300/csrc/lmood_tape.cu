@@ -170,7 +170,7 @@ void reverse_step(lmood_tape t, AdjBuf &a, const Fld &f) {
     ao.nodes(M->geo, f, a, 0, st);
     ao.predict(M->geo, f, kr, a, 0, st);
     ao.momsum(M->geo, f, a, st);
-    ao.cells(M->geo, f, kr, a, st);
+    ao.cells(M->geo, f, kr, a, 1, st);
     ao.gather(M->geo, a, st);
     std::swap(a.lv0, a.lv1);
     std::swap(a.lF0, a.lF1);
@@ -263,8 +263,16 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     A((void **)&a.cp, (size_t)CP * NC * nd);
     A((void **)&a.cc, (size_t)CC * N * nd);
     A((void **)&a.cd, (size_t)D * NC * nd);
-    if ((int64_t)nmom * Np <= (int64_t)CR * NC) a.lm = a.cr;  // written after the corner records are consumed
-    else A((void **)&a.lm, (size_t)nmom * Np * nd);          // (meshes with unreferenced nodes)
+    {
+        const int FL = (D + DD) * D + DD + (D + 1) * D + DD + (D + 1) * D + (D + 1) + 1;  // adj::PredRec<D>
+        const int KL = DD + D + NS, Q2L = 2 * D + DD + 2, Q1L = DD + D + 2;
+        A((void **)&a.pf, (size_t)FL * N * nd);
+        A((void **)&a.pk, (size_t)KL * NC * nd);
+        A((void **)&a.q2, (size_t)Q2L * NC * nd);
+        A((void **)&a.q1, (size_t)Q1L * NC * nd);
+    }
+    // (its own buffer: the cell kernel after the moment sums still reads the corner records)
+    A((void **)&a.lm, (size_t)nmom * Np * nd);
     if (r) {
         tape_free(t);
         return r;
