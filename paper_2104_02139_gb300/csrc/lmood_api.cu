@@ -521,6 +521,7 @@ void lmood::swap_state(lmood_state s) {
     std::swap(f.rho, f.rho1);
     std::swap(s->tau, f.tau1);
     std::swap(f.z, f.z1);
+    std::swap(f.gf, f.gf1);
     double *dt = const_cast<double *>(f.dt);
     f.dt = (const double *)f.dtn;
     f.dtn = (unsigned long long *)dt;
@@ -646,7 +647,8 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
     A((void **)&f.rlo, Np * nd);
     A((void **)&f.rhi, Np * nd);
     A((void **)&s->mu, N * nd);
-    if (D == 3) A((void **)&f.gf, (size_t)(D * NV + 1) * N * nd);
+    A((void **)&f.gf, (size_t)(D * NV + 1 + NV) * N * nd);  // CellGeo<D>::LEN
+    A((void **)&f.gf1, (size_t)(D * NV + 1 + NV) * N * nd);
     A((void **)&f.pkM, (size_t)NS * NV * N * nd);
     A((void **)&f.pkR, (size_t)D * NV * N * nd);
     A((void **)&f.order, N);
@@ -1487,6 +1489,7 @@ struct StateCopy {
         Fld &f = s->f;
         return {{f.x, D * Np * nd}, {f.vp, D * Np * nd}, {f.v, D * N * nd}, {f.e, N * nd}, {f.F, D * D * N * nd},
                 {f.xc, D * N * nd}, {f.rho, N * nd}, {f.z, N * nd}, {s->tau, N * nd}, {f.order, N},
+                {f.gf, (D * (D + 1) + 1 + (D + 1)) * N * nd},
                 {const_cast<double *>(f.dt), (size_t)M->n_inst * nd}};
     }
     lmood_status save(lmood_state s) {

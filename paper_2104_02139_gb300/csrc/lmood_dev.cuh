@@ -78,8 +78,9 @@ struct Fld {
     double *mom;                 // [NMOM][Np] least-squares moments of the cells around each node
     const double *im;            // 1 / m_c
     double *pkM, *pkR;
-    double *gf;                  // 3D: [D (D+1) + 1][N] the cells' face area vectors N_f and volume at
-                                 // x^n, written by the step's full-mesh predictor, read by its update
+    double *gf, *gf1;            // [CellGeo<D>::LEN][N] the cells' geometry at x^n / x^{n+1} (face area
+                                 // vectors, volume, 1 / |N_f|): the update writes that of x^{n+1}, which
+                                 // the next step's predictor and update read
     unsigned char *order, *pflag;
     double *dtc;
     const double *dt;            // [n_inst] dt of this step
@@ -155,6 +156,50 @@ __device__ __forceinline__ void simplex_faces(const double (&xs)[D + 1][D], doub
             Nf[k][2] = s * (u0 * w1 - u1 * w0);
         }
     }
+}
+
+// A cell's geometry at one set of node positions, kept per cell from the kernel that computes it
+// (the update, at x^{n+1}; init and refresh at the current positions) for the next ones that
+// need it: face area vectors N_f [D+1][D], volume |w_c|, 1 / |N_f| [D+1]. Component i of
+// cell c at gf[i * N + c].
+template <int D> struct CellGeo {
+    static constexpr int NV = D + 1, NF = 0, VOL = NV * D, RS = NV * D + 1, LEN = NV * D + 1 + NV;
+};
+
+// 1 / |N_f| of each face, and |N_f|^2
+template <int D>
+__device__ __forceinline__ void face_rnorms(const double (&Nf)[D + 1][D], double (&rs)[D + 1], double (&ss)[D + 1]) {
+#pragma unroll
+    for (int k = 0; k < D + 1; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) s += Nf[k][a] * Nf[k][a];
+        ss[k] = s;
+        rs[k] = rsqrt(s);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void store_cell_geo(double *gf, int N, int c, const double (&Nf)[D + 1][D], double V,
+                                               const double (&rs)[D + 1]) {
+    using G = CellGeo<D>;
+#pragma unroll
+    for (int k = 0; k < D + 1; ++k) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) gf[(G::NF + k * D + a) * N + c] = Nf[k][a];
+        gf[(G::RS + k) * N + c] = rs[k];
+    }
+    gf[G::VOL * N + c] = V;
+}
+
+template <int D>
+__device__ __forceinline__ void load_cell_geo(const double *gf, int N, int c, double (&Nf)[D + 1][D], double &V) {
+    using G = CellGeo<D>;
+#pragma unroll
+    for (int k = 0; k < D + 1; ++k)
+#pragma unroll
+        for (int a = 0; a < D; ++a) Nf[k][a] = gf[(G::NF + k * D + a) * N + c];
+    V = gf[G::VOL * N + c];
 }
 
 template <int D>

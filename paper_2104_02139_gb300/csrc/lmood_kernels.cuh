@@ -133,16 +133,9 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
 #pragma unroll
         for (int a = 0; a < D; ++a) xs[k][a] = f.x[a * Np + nod[k]];
     }
+    // the geometry at x^n, as the previous step's update (or init / refresh) left it
     double V, Nf[NV][D];
-    simplex_faces<D>(xs, V, Nf);
-    if constexpr (D == 3 && !LISTED) {
-        // the geometry at x^n for this step's update (it would otherwise recompute it)
-#pragma unroll
-        for (int k = 0; k < NV; ++k)
-#pragma unroll
-            for (int a = 0; a < D; ++a) f.gf[(k * D + a) * N + c] = Nf[k][a];
-        f.gf[NV * D * N + c] = V;
-    }
+    load_cell_geo<D>(f.gf, N, c, Nf, V);
     double vc[D], Fc[DD];
 #pragma unroll
     for (int a = 0; a < D; ++a) vc[a] = f.v[a * N + c];
@@ -164,10 +157,7 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             // with u = N_f / D: z / |u| u u^t = (z / (D |N_f|)) N_f N_f^t
-            double s = 0.0;
-#pragma unroll
-            for (int a = 0; a < D; ++a) s += Nf[k][a] * Nf[k][a];
-            const double w = z * rsqrt(s) * (1.0 / D);
+            const double w = z * f.gf[(CellGeo<D>::RS + k) * N + c] * (1.0 / D);
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 const double wa = w * Nf[k][a];
@@ -743,23 +733,13 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
 #pragma unroll
     for (int a = 0; a < D; ++a) v1[a] = fma(dtm, sf[a], f.v[a * N + c]);
     const double e1 = fma(dtm, sfv, f.e[c]);
-    double V0, Nf0[NV][D], V1, Nf1[NV][D];
-    if constexpr (D == 3) {
-        // the geometry at x^n as this step's full-mesh predictor computed it
-#pragma unroll
-        for (int k = 0; k < NV; ++k)
-#pragma unroll
-            for (int a = 0; a < D; ++a) Nf0[k][a] = f.gf[(k * D + a) * N + c];
-        V0 = f.gf[NV * D * N + c];
-    } else {
-        double xs0[NV][D];
-#pragma unroll
-        for (int k = 0; k < NV; ++k)
-#pragma unroll
-            for (int a = 0; a < D; ++a) xs0[k][a] = f.x[a * Np + nod[k]];
-        simplex_faces<D>(xs0, V0, Nf0);
-    }
+    // the geometry at x^n as the previous step left it; that of x^{n+1} computed and kept for
+    // the next step
+    double V0, Nf0[NV][D], V1, Nf1[NV][D], rs1[NV], ss1[NV];
+    load_cell_geo<D>(f.gf, N, c, Nf0, V0);
     simplex_faces<D>(xs1, V1, Nf1);
+    face_rnorms<D>(Nf1, rs1, ss1);
+    store_cell_geo<D>(f.gf1, N, c, Nf1, V1, rs1);
     // 1 / |w_c| at x^n is rho^n / m_c (rho^n = m_c / |w_c(x^n)| is stored); at x^{n+1} one division
     const double iV0 = f.rho[c] * im, iV1 = 1.0 / V1;
     double Fn[DD], F1[DD];
@@ -811,12 +791,7 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
     f.tau1[c] = V1 * im;
     double area1 = 0.0;  // sum of the face measures at x^{n+1} (in-sphere diameter 2 D V / area)
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double s = 0.0;
-#pragma unroll
-        for (int a = 0; a < D; ++a) s += Nf1[k][a] * Nf1[k][a];
-        area1 += sqrt(s);
-    }
+    for (int k = 0; k < NV; ++k) area1 += ss1[k] * rs1[k];  // |N_f| = |N_f|^2 / |N_f|
     if (prm.mood) {
         int ps = pad_state<D>(v1, e1, F1, V1, a0sq_of(prm, muc, kap));
         if (prm.eos && ps == 0) {  // stiffened gas: p + p_inf > 0 (a real sound speed)
@@ -1092,8 +1067,10 @@ __global__ void __launch_bounds__(kCellBlock) k_init_cells(Geo g, Fld f, Prm prm
 #pragma unroll
         for (int a = 0; a < D; ++a) xs[k][a] = f.x[a * Np + p];
     }
-    double V, Nf[NV][D];
+    double V, Nf[NV][D], rs[NV], ss[NV];
     simplex_faces<D>(xs, V, Nf);
+    face_rnorms<D>(Nf, rs, ss);
+    store_cell_geo<D>(f.gf, N, c, Nf, V, rs);
     const double mc = rho0 * V;
     m_out[c] = mc;
     im_out[c] = 1.0 / mc;
@@ -1150,8 +1127,10 @@ template <int D> __global__ void __launch_bounds__(kCellBlock) k_refresh(Geo g, 
 #pragma unroll
         for (int a = 0; a < D; ++a) xs[k][a] = f.x[a * g.Np + p];
     }
-    double V, Nf[NV][D];
+    double V, Nf[NV][D], rs[NV], ss[NV];
     simplex_faces<D>(xs, V, Nf);
+    face_rnorms<D>(Nf, rs, ss);
+    store_cell_geo<D>(f.gf, g.N, c, Nf, V, rs);  // as the update stores it
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         double s = 0.0;
@@ -1174,6 +1153,25 @@ template <int D> __global__ void __launch_bounds__(kCellBlock) k_refresh(Geo g, 
     } else {
         f.z[c] = impedance<D>(F, rho, muc, kappa_of(prm, muc));
     }
+}
+
+// the cells' geometry at the current positions alone (a view of a recorded state, whose x^n
+// geometry no update has left)
+template <int D> __global__ void __launch_bounds__(kCellBlock) k_geometry(Geo g, Fld f) {
+    constexpr int NV = D + 1;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    double xs[NV][D];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int p = g.c2n[k * g.N + c];
+#pragma unroll
+        for (int a = 0; a < D; ++a) xs[k][a] = f.x[a * g.Np + p];
+    }
+    double V, Nf[NV][D], rs[NV], ss[NV];
+    simplex_faces<D>(xs, V, Nf);
+    face_rnorms<D>(Nf, rs, ss);
+    store_cell_geo<D>(f.gf, g.N, c, Nf, V, rs);
 }
 
 // sums of m, m v, m e (diagnostic; atomics, so the last bits depend on scheduling)

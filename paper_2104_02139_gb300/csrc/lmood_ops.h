@@ -37,6 +37,8 @@ struct Ops {
     void (*init_cells)(const Geo &, const Fld &, const Prm &, double rho0, double *m, double *im, int f_given,
                        cudaStream_t);
     void (*refresh)(const Geo &, const Fld &, const Prm &, cudaStream_t);
+    // the cells' geometry at the current positions into f.gf (views of recorded states)
+    void (*geometry)(const Geo &, const Fld &, cudaStream_t);
     void (*totals)(const Geo &, const Fld &, double *out, cudaStream_t);
     // the whole step as one cooperative launch (neo-Hookean material)
     cudaError_t (*persistent)(const Geo &, const Fld &, const Prm &, const PersistArgs &, cudaStream_t);

@@ -107,6 +107,9 @@ void init_cells(const Geo &g, const Fld &f, const Prm &p, double rho0, double *m
                 cudaStream_t s) {
     k_init_cells<D><<<blocks(g.N, kCellBlock), kCellBlock, 0, s>>>(g, f, p, rho0, m, im, f_given);
 }
+template <int D> void geometry(const Geo &g, const Fld &f, cudaStream_t s) {
+    k_geometry<D><<<blocks(g.N, kCellBlock), kCellBlock, 0, s>>>(g, f);
+}
 template <int D> void refresh(const Geo &g, const Fld &f, const Prm &p, cudaStream_t s) {
     k_refresh<D><<<blocks(g.N, kCellBlock), kCellBlock, 0, s>>>(g, f, p);
 }
@@ -152,7 +155,7 @@ template <int D> cudaError_t mood_persistent(const Geo &g, const Fld &f, const P
 #define LMOOD_OPS_TABLE(D)                                                                                  \
     static const Ops table = {D, Dim<D>::NMOM, moments<D>, predict<D>, nodes<D>,  update<D>,     mark_nodes<D>, mark_cells<D>, \
                               round_begin, ctl_reset,  loop_cond, report,        dt_init,       finalize,   \
-                              init_cells<D>, refresh<D>, totals<D>, persistent<D>, mood_persistent<D>};                                      \
+                              init_cells<D>, refresh<D>, geometry<D>, totals<D>, persistent<D>, mood_persistent<D>};                                      \
     return table;
 
 }  // namespace lmood

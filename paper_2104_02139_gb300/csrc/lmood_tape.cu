@@ -31,6 +31,8 @@ struct lmood_tape_s {
     double *seg = nullptr;          // checkpoint mode: [C] snapshots of a segment's states after
                                     // its first (the first is its checkpoint)
     unsigned char *tmp_order = nullptr;  // [N] scratch orders of the initial packets
+    double *gf = nullptr, *gf1 = nullptr;  // the views' cell geometry at x^n, x^{n+1} (the state's
+                                           // own buffers carry its current geometry)
     AdjBuf a{};
     DevAllocs mem;
 };
@@ -139,6 +141,8 @@ Fld view(lmood_tape t, const Fld &base, const Snap &cur, const Snap &nxt, const 
     fr.mom = q.mom;
     fr.dt = t->dts + j * M->n_inst;
     fr.order = t->masks + j * M->nc;
+    fr.gf = t->gf;
+    fr.gf1 = t->gf1;
     return fr;
 }
 
@@ -151,6 +155,7 @@ void replay_view(lmood_tape t, const Fld &fr) {
     Prm kr = s->kp;
     kr.base_order = 0;
     kr.mood = 0;
+    op.geometry(M->geo, fr, st);  // the view's x^n geometry (the state's own is of another time)
     op.moments(M->geo, fr, st);
     op.predict(M->geo, fr, kr, nullptr, nullptr, (int)M->nc, st);
     op.nodes(M->geo, fr, nullptr, nullptr, (int)M->np, 0, st);
@@ -247,6 +252,8 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
         A((void **)&t->seg, t->C * sd * nd);
     }
     A((void **)&t->tmp_order, (size_t)N);
+    A((void **)&t->gf, (size_t)(D * NV + 1 + NV) * N * nd);  // CellGeo<D>::LEN
+    A((void **)&t->gf1, (size_t)(D * NV + 1 + NV) * N * nd);
     AdjBuf &a = t->a;
     A((void **)&a.lv1, D * N * nd);
     A((void **)&a.lv0, D * N * nd);
@@ -376,6 +383,7 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
         f0.order = t->tmp_order;
         Prm p0 = s->kp;
         p0.base_order = 1;
+        op.geometry(M->geo, f0, st);
         op.predict(M->geo, f0, p0, nullptr, nullptr, (int)N, st);
         AdjBuf ai = a;
         ai.lv0 = a.lv1;
