@@ -397,50 +397,91 @@ def run_ours(args, rank, local, ws, dist):
         print(json.dumps(line), flush=True)
 
 
+def _timed_window(sim, N, k, stream, torch) -> dict:
+    """k graph-captured steps of sim under CUDA events (per-stage timing on): cell-steps/s, the
+    troubled and first-order fractions, MOOD rounds and MOOD loop time per step."""
+    sim.timing(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tr = p0 = it = 0
+    for _ in range(k):
+        info = sim.step()
+        tr += info.n_troubled
+        p0 += info.n_p0
+        it += info.mood_iters
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kt = sim.timing_read()
+    sim.timing(False)
+    ms = e0.elapsed_time(e1) / k
+    stage_ms = sum(v[0] for v in kt.values())
+    mood_ms = kt["mood"][0] / k
+    return {"steps": k, "ms_per_step": ms, "value": N / (ms / 1e3), "unit": UNIT,
+            "troubled_frac": tr / (N * k), "p0_frac": p0 / (N * k), "mood_rounds_per_step": it / k,
+            "mood_ms_per_step": mood_ms, "mood_share": kt["mood"][0] / stage_ms if stage_ms > 0 else None,
+            "mood_us_per_round": 1e3 * mood_ms / (it / k) if it else None,
+            "mood_ns_per_troubled_cell": 1e6 * mood_ms / (tr / k) if tr else None,
+            "t": float(sim.info.t)}
+
+
 def run_impact_windows(L, W, torch, args) -> dict:
     """The 2D impact (999,698 triangles, the shock problem of the configurations) in two timed
     windows of K graph-captured steps each: early (from step 8, as the front forms) and mid-run
     (from step args.midrun_from, with the compression front and its troubled band established).
     Per window: cell-steps/s, the troubled fraction (cells sent down the cascade per cell-step),
     the first-order fraction, MOOD rounds per step and the MOOD loop's share of the step time
-    (CUDA events around each stage)."""
+    (CUDA events around each stage). Then the MOOD load curve: the early window again with the
+    RDMP relaxations delta0, delta1 scaled by 0.1, 0.01 and 0 (a stricter detection, so that
+    more cells go down the cascade: the cost of the MOOD loop against the troubled fraction),
+    and the same impact on a 19,602-triangle mesh, where the troubled band is a few percent
+    of the cells as on the paper's meshes."""
     pb = W.impact2d()
     N = pb.mesh.n_cells
     stream = torch.cuda.Stream()
-    sim = L.simulation(pb, stream=stream.cuda_stream, graph=0 if args.host_mode else 1)
+    graph = 0 if args.host_mode else 1
+    sim = L.simulation(pb, stream=stream.cuda_stream, graph=graph)
     k = max(10, args.steps)
     out, taken = {}, 0
     for name, first in (("early", 8), ("mid_run", args.midrun_from)):
         while taken < first:
             sim.step()
             taken += 1
-        sim.timing(True)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        tr = p0 = it = 0
-        for _ in range(k):
-            info = sim.step()
-            tr += info.n_troubled
-            p0 += info.n_p0
-            it += info.mood_iters
-        e1.record(stream)
-        torch.cuda.synchronize()
+        out[name] = {"first_step": first, **_timed_window(sim, N, k, stream, torch)}
         taken += k
-        kt = sim.timing_read()
-        sim.timing(False)
-        ms = e0.elapsed_time(e1) / k
-        stage_ms = sum(v[0] for v in kt.values())
-        out[name] = {"first_step": first, "steps": k, "ms_per_step": ms, "value": N / (ms / 1e3), "unit": UNIT,
-                     "troubled_frac": tr / (N * k), "p0_frac": p0 / (N * k), "mood_rounds_per_step": it / k,
-                     "mood_ms_per_step": kt["mood"][0] / k,
-                     "mood_share": kt["mood"][0] / stage_ms if stage_ms > 0 else None,
-                     "t": float(sim.info.t)}
     sim.close()
     sim.mesh.close()
+    d0 = L.params_default(2)
+    load = []
+    for scale in (0.1, 0.01, 0.0):
+        sim = L.simulation(pb, stream=stream.cuda_stream, graph=graph, delta0=d0.delta0 * scale,
+                           delta1=d0.delta1 * scale)
+        try:
+            for _ in range(8):
+                sim.step()
+            load.append({"delta_scale": scale, "first_step": 8, **_timed_window(sim, N, k, stream, torch)})
+        except L.LmoodError as e:  # a status of the library (e.g. the MOOD round limit), not a crash
+            load.append({"delta_scale": scale, "error": str(e)})
+        sim.close()
+        sim.mesh.close()
+    # the same impact at a resolution like the paper's meshes (100 x 100 points, 19,602
+    # triangles): the front's band of cells is then a few percent of the mesh
+    pbs = W.impact2d(n=100)
+    sim = L.simulation(pbs, stream=stream.cuda_stream, graph=graph)
+    try:
+        for _ in range(8):
+            sim.step()
+        load.append({"delta_scale": 1.0, "cells": pbs.mesh.n_cells, "first_step": 8,
+                     **_timed_window(sim, pbs.mesh.n_cells, k, stream, torch)})
+    except L.LmoodError as e:
+        load.append({"delta_scale": 1.0, "cells": pbs.mesh.n_cells, "error": str(e)})
+    sim.close()
+    sim.mesh.close()
+    out["mood_load"] = load
     out["cells"] = N
     out["what"] = ("impact2d in two windows of its run: troubled_frac = cells sent down the cascade per "
-                   "cell-step (the paper's 'troubled cells per step'), mood_share = MOOD loop time / step time")
+                   "cell-step (the paper's 'troubled cells per step'), mood_share = MOOD loop time / step time; "
+                   "mood_load: the early window with delta0, delta1 scaled down (stricter RDMP)")
     return out
 
 

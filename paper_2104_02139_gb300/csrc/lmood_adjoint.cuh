@@ -223,9 +223,8 @@ template <int D> LMOOD_HD void faces(const double *xs, double &V, double *N) {  
     }
 }
 
-template <int D> LMOOD_HD void faces_vjp(const double *xs, double lV, const double *lN, double *lxs) {
-    double V, N[(D + 1) * D];
-    faces<D>(xs, V, N);
+// product of faces at xs, with N = faces(xs) already formed by the caller
+template <int D> LMOOD_HD void faces_vjp_n(const double *xs, const double *N, double lV, const double *lN, double *lxs) {
     for (int k = 0; k < D + 1; ++k)
         for (int a = 0; a < D; ++a) lxs[k * D + a] += lV * (N[k * D + a] * (-1.0 / D));
     if constexpr (D == 2) {
@@ -256,6 +255,12 @@ template <int D> LMOOD_HD void faces_vjp(const double *xs, double lV, const doub
             }
         }
     }
+}
+
+template <int D> LMOOD_HD void faces_vjp(const double *xs, double lV, const double *lN, double *lxs) {
+    double V, N[(D + 1) * D];
+    faces<D>(xs, V, N);
+    faces_vjp_n<D>(xs, N, lV, lN, lxs);
 }
 
 // velocity gradient L = -(1/(D V)) sum_k v_k (x) N_k and its product; the _iv forms take
@@ -1093,74 +1098,12 @@ LMOOD_HD void update_fw(const double *xs0, const double *xs1, const double *vs, 
     z1 = impedance<D>(F1, m / V1, mu, kap);
 }
 
-// Product of update_fw: (lv1, lF1, lz1) -> accumulates lxs0, lxs1, lvs, lvp0, lvp1 [NV][D],
-// lM [NV][NS], lR [NV][D], lv [D], lF [DD], lmu, lkap. Recomputes only what the product
-// needs (F1 and the impedance term only where used; lz1 = 0 drops the impedance).
+// Product of update_fw in two parts. The velocity part, v1 = v + dt im sum_k (M_k vs_k - R_k):
+// accumulates lvs [NV][D], lM [NV][NS], lR [NV][D] and lv [D] from lv1.
 template <int D>
-LMOOD_HD void update_vjp(const double *xs0, const double *xs1, const double *vs, const double *vp0, const double *vp1,
-                         const double *M, const double *R, const double *v, const double *F, double m, double im,
-                         double mu, double kap, double dt, int ord, const double *lv1, const double *lF1_in, double lz1,
-                         double *lxs0, double *lxs1, double *lvs, double *lvp0, double *lvp1, double *lM, double *lR,
-                         double *lv, double *lF, double &lmu, double &lkap) {
-    using Q = Sz<D>;
-    constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS;
-    (void)R;
-    (void)v;
-    double V0, N0[NV * D], V1, N1[NV * D], lN0[NV * D] = {}, lN1[NV * D] = {}, lV0 = 0.0, lV1 = 0.0;
-    faces<D>(xs0, V0, N0);
-    faces<D>(xs1, V1, N1);
-    const double iV0 = 1.0 / V0, iV1 = 1.0 / V1;
-    double lF1[DD];
-    for (int q = 0; q < DD; ++q) lF1[q] = lF1_in[q];
-    if (ord != 1) {
-        double L0[DD], L1[DD], A[DD], Bm[DD], Ai[DD], Rm[DD], F1[DD];
-        velgrad_iv<D>(vp0, N0, iV0, L0);
-        velgrad_iv<D>(vp1, N1, iV1, L1);
-        for (int i = 0; i < D; ++i)
-            for (int j = 0; j < D; ++j) {
-                A[i * D + j] = (i == j ? 1.0 : 0.0) - 0.5 * dt * L1[i * D + j];
-                Bm[i * D + j] = (i == j ? 1.0 : 0.0) + 0.5 * dt * L0[i * D + j];
-            }
-        mm<D>(Bm, F, Rm);
-        inverse<D>(A, Ai);
-        mm<D>(Ai, Rm, F1);
-        if (lz1 != 0.0) {  // z1 = Z(F1, m / V1)
-            double lrho = 0.0;
-            impedance_vjp<D>(F1, m * iV1, mu, kap, lz1, lF1, lrho, lmu, lkap);
-            lV1 -= lrho * m * iV1 * iV1;
-        }
-        // F1 = Ai Rm, Rm = Bm F
-        double lRm[DD], lA[DD], lBm[DD], t[DD], lL0[DD], lL1[DD];
-        mtm<D>(Ai, lF1, lRm);       // lRm = Ai^t lF1
-        mmt<D>(lRm, F1, lA);        // lA = -lRm F1^t
-        mmt<D>(lRm, F, lBm);        // lBm = lRm F^t
-        mtm<D>(Bm, lRm, t);         // lF += Bm^t lRm
-        for (int q = 0; q < DD; ++q) {
-            lF[q] += t[q];
-            lL1[q] = 0.5 * dt * lA[q];  // A = I - dt/2 L1, lA was -(...) -> +dt/2
-            lL0[q] = 0.5 * dt * lBm[q];
-        }
-        velgrad_vjp_iv<D>(vp1, N1, iV1, L1, lL1, lvp1, lN1, lV1);
-        velgrad_vjp_iv<D>(vp0, N0, iV0, L0, lL0, lvp0, lN0, lV0);
-    } else {
-        double Ls[DD], t[DD], lLs[DD];
-        velgrad_iv<D>(vs, N0, iV0, Ls);
-        if (lz1 != 0.0) {
-            double LF[DD], F1[DD], lrho = 0.0;
-            mm<D>(Ls, F, LF);
-            for (int q = 0; q < DD; ++q) F1[q] = F[q] + dt * LF[q];
-            impedance_vjp<D>(F1, m * iV1, mu, kap, lz1, lF1, lrho, lmu, lkap);
-            lV1 -= lrho * m * iV1 * iV1;
-        }
-        mtm<D>(Ls, lF1, t);
-        for (int q = 0; q < DD; ++q) lF[q] += lF1[q] + dt * t[q];
-        mmt<D>(lF1, F, lLs);
-        for (int q = 0; q < DD; ++q) lLs[q] *= dt;
-        velgrad_vjp_iv<D>(vs, N0, iV0, Ls, lLs, lvs, lN0, lV0);
-    }
-    faces_vjp<D>(xs0, lV0, lN0, lxs0);
-    faces_vjp<D>(xs1, lV1, lN1, lxs1);
-    // v1 = v + dt im sum_k (M_k vs_k - R_k)
+LMOOD_HD void update_force_vjp(const double *vs, const double *M, double im, double dt, const double *lv1,
+                               double *lvs, double *lM, double *lR, double *lv) {
+    constexpr int NV = D + 1, NS = D * (D + 1) / 2;
     for (int a = 0; a < D; ++a) lv[a] += lv1[a];
     for (int k = 0; k < NV; ++k)
         for (int a = 0; a < D; ++a) {
@@ -1171,6 +1114,132 @@ LMOOD_HD void update_vjp(const double *xs0, const double *xs1, const double *vs,
                 lvs[k * D + b] += M[k * NS + sym<D>(a, b)] * lf;
             }
         }
+}
+
+// The deformation part (F^{n+1} from the velocity gradients at both levels, or the first-order
+// step with v*, and the impedance of F^{n+1}): (lF1, lz1) -> accumulates lF [DD], lmu, lkap.
+// The corners' nodal values are read when needed through ld(i, u) (u [NV][D] <- 0 v*, 1 x^n,
+// 2 x^{n+1}, 3 v_p^n, 4 v_p^{n+1}), and each nodal adjoint is handed over once, whole, through
+// out(i, l) (l [NV][D]: 0 lvs, 1 lxs0, 2 lxs1, 3 lvp0, 4 lvp1; zeros where it has no term), so
+// that a caller holds neither all inputs nor all outputs at once. Recomputes only what the
+// product needs (F1 and the impedance term only where used; lz1 = 0 drops the impedance).
+template <int D, class LD, class OUT>
+LMOOD_HD void update_deform_vjp(LD &&ld, OUT &&out, const double *F, double m, double mu, double kap, double dt,
+                                int ord, const double *lF1_in, double lz1, double *lF, double &lmu, double &lkap) {
+    using Q = Sz<D>;
+    constexpr int NV = Q::NV, DD = Q::DD, NX = NV * D;
+    double lF1[DD], xs[NX], u[NX], N0[NX], V0, l[NX], lN[NX];
+    for (int q = 0; q < DD; ++q) lF1[q] = lF1_in[q];
+    ld(1, xs);
+    faces<D>(xs, V0, N0);
+    const double iV0 = 1.0 / V0;
+    if (ord != 1) {
+        double N1[NX], V1, L0[DD], L1[DD], lL0[DD], lL1[DD], lV1 = 0.0, lV0 = 0.0;
+        ld(2, xs);
+        faces<D>(xs, V1, N1);
+        const double iV1 = 1.0 / V1;
+        ld(3, u);
+        velgrad_iv<D>(u, N0, iV0, L0);
+        ld(4, u);
+        velgrad_iv<D>(u, N1, iV1, L1);
+        {
+            double A[DD], Bm[DD], Ai[DD], Rm[DD], F1[DD];
+            for (int i = 0; i < D; ++i)
+                for (int j = 0; j < D; ++j) {
+                    A[i * D + j] = (i == j ? 1.0 : 0.0) - 0.5 * dt * L1[i * D + j];
+                    Bm[i * D + j] = (i == j ? 1.0 : 0.0) + 0.5 * dt * L0[i * D + j];
+                }
+            mm<D>(Bm, F, Rm);
+            inverse<D>(A, Ai);
+            mm<D>(Ai, Rm, F1);
+            if (lz1 != 0.0) {  // z1 = Z(F1, m / V1)
+                double lrho = 0.0;
+                impedance_vjp<D>(F1, m * iV1, mu, kap, lz1, lF1, lrho, lmu, lkap);
+                lV1 -= lrho * m * iV1 * iV1;
+            }
+            // F1 = Ai Rm, Rm = Bm F
+            double lRm[DD], lA[DD], lBm[DD], t[DD];
+            mtm<D>(Ai, lF1, lRm);  // lRm = Ai^t lF1
+            mmt<D>(lRm, F1, lA);   // lA = -lRm F1^t
+            mmt<D>(lRm, F, lBm);   // lBm = lRm F^t
+            mtm<D>(Bm, lRm, t);    // lF += Bm^t lRm
+            for (int q = 0; q < DD; ++q) {
+                lF[q] += t[q];
+                lL1[q] = 0.5 * dt * lA[q];  // A = I - dt/2 L1, lA was -(...) -> +dt/2
+                lL0[q] = 0.5 * dt * lBm[q];
+            }
+        }
+        // level n+1: u holds v_p^{n+1}, xs holds x^{n+1}
+        for (int i = 0; i < NX; ++i) l[i] = lN[i] = 0.0;
+        velgrad_vjp_iv<D>(u, N1, iV1, L1, lL1, l, lN, lV1);
+        out(4, l);
+        for (int i = 0; i < NX; ++i) l[i] = 0.0;
+        faces_vjp_n<D>(xs, N1, lV1, lN, l);
+        out(2, l);
+        // level n
+        for (int i = 0; i < NX; ++i) l[i] = lN[i] = 0.0;
+        ld(3, u);
+        velgrad_vjp_iv<D>(u, N0, iV0, L0, lL0, l, lN, lV0);
+        out(3, l);
+        for (int i = 0; i < NX; ++i) l[i] = 0.0;
+        ld(1, xs);
+        faces_vjp_n<D>(xs, N0, lV0, lN, l);
+        out(1, l);
+        for (int i = 0; i < NX; ++i) l[i] = 0.0;
+        out(0, l);
+    } else {
+        double Ls[DD], t[DD], lLs[DD], lV1 = 0.0, lV0 = 0.0;
+        ld(0, u);
+        velgrad_iv<D>(u, N0, iV0, Ls);
+        if (lz1 != 0.0) {
+            double LF[DD], F1[DD], lrho = 0.0, V1, N1[NX];
+            ld(2, xs);
+            faces<D>(xs, V1, N1);
+            const double iV1 = 1.0 / V1;
+            mm<D>(Ls, F, LF);
+            for (int q = 0; q < DD; ++q) F1[q] = F[q] + dt * LF[q];
+            impedance_vjp<D>(F1, m * iV1, mu, kap, lz1, lF1, lrho, lmu, lkap);
+            lV1 -= lrho * m * iV1 * iV1;
+            for (int i = 0; i < NX; ++i) l[i] = lN[i] = 0.0;
+            faces_vjp_n<D>(xs, N1, lV1, lN, l);
+            out(2, l);
+            ld(1, xs);
+        } else {
+            for (int i = 0; i < NX; ++i) l[i] = 0.0;
+            out(2, l);
+        }
+        mtm<D>(Ls, lF1, t);
+        for (int q = 0; q < DD; ++q) lF[q] += lF1[q] + dt * t[q];
+        mmt<D>(lF1, F, lLs);
+        for (int q = 0; q < DD; ++q) lLs[q] *= dt;
+        for (int i = 0; i < NX; ++i) l[i] = lN[i] = 0.0;
+        velgrad_vjp_iv<D>(u, N0, iV0, Ls, lLs, l, lN, lV0);
+        out(0, l);
+        for (int i = 0; i < NX; ++i) l[i] = 0.0;
+        faces_vjp_n<D>(xs, N0, lV0, lN, l);
+        out(1, l);
+        for (int i = 0; i < NX; ++i) l[i] = 0.0;
+        out(3, l);
+        out(4, l);
+    }
+}
+
+// Product of update_fw: (lv1, lF1, lz1) -> accumulates lxs0, lxs1, lvs, lvp0, lvp1 [NV][D],
+// lM [NV][NS], lR [NV][D], lv [D], lF [DD], lmu, lkap.
+template <int D>
+LMOOD_HD void update_vjp(const double *xs0, const double *xs1, const double *vs, const double *vp0, const double *vp1,
+                         const double *M, const double *R, const double *v, const double *F, double m, double im,
+                         double mu, double kap, double dt, int ord, const double *lv1, const double *lF1, double lz1,
+                         double *lxs0, double *lxs1, double *lvs, double *lvp0, double *lvp1, double *lM, double *lR,
+                         double *lv, double *lF, double &lmu, double &lkap) {
+    (void)R;
+    (void)v;
+    update_force_vjp<D>(vs, M, im, dt, lv1, lvs, lM, lR, lv);
+    const double *in[5] = {vs, xs0, xs1, vp0, vp1};
+    double *acc[5] = {lvs, lxs0, lxs1, lvp0, lvp1};
+    update_deform_vjp<D>([&](int i, double *u) { for (int j = 0; j < (D + 1) * D; ++j) u[j] = in[i][j]; },
+                         [&](int i, const double *l) { for (int j = 0; j < (D + 1) * D; ++j) acc[i][j] += l[j]; }, F,
+                         m, mu, kap, dt, ord, lF1, lz1, lF, lmu, lkap);
 }
 
 // Node moments: product for one corner (node p, cell c'): with dx = x_c' - x_p, accumulate

@@ -41,42 +41,48 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_update(Geo g, Fld 
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     const int N = g.N, Np = g.Np, NC = NV * N;
-    double xs0[NX], xs1[NX], vs[NX], vp0[NX], vp1[NX], M[NV * NS], v[D], F[DD];
-    for (int k = 0; k < NV; ++k) {
-        const int p = g.c2n[k * N + c];
-        for (int b = 0; b < D; ++b) {
-            xs0[k * D + b] = f.x[b * Np + p];
-            xs1[k * D + b] = f.x1[b * Np + p];
-            vs[k * D + b] = f.vs[b * Np + p];
-            vp0[k * D + b] = f.vp[b * Np + p];
-            vp1[k * D + b] = f.vp1[b * Np + p];
-        }
-        for (int s = 0; s < NS; ++s) M[k * NS + s] = f.pkM[s * NC + k * N + c];
-    }
-    for (int b = 0; b < D; ++b) v[b] = f.v[b * N + c];
-    for (int q = 0; q < DD; ++q) F[q] = f.F[q * N + c];
-    double lv1[D], lF1[DD];
-    for (int b = 0; b < D; ++b) lv1[b] = a.lv1[b * N + c];
-    for (int q = 0; q < DD; ++q) lF1[q] = a.lF1[q * N + c];
     const double mu = f.mu[c], kap = kappa_of(prm, mu), dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
     const int ord = f.order[c];
-    double l0[NX] = {}, l1[NX] = {}, lvs[NX] = {}, lp0[NX] = {}, lp1[NX] = {}, lM[NV * NS] = {}, lR[NX] = {},
-           lv[D] = {}, lF[DD] = {}, lmu = 0.0, lkap = 0.0;
-    adj::update_vjp<D>(xs0, xs1, vs, vp0, vp1, M, nullptr, v, F, f.m[c], f.im[c], mu, kap, dt, ord, lv1, lF1, 0.0,
-                       l0, l1, lvs, lp0, lp1, lM, lR, lv, lF, lmu, lkap);
-    for (int k = 0; k < NV; ++k) {
-        double *r = a.cr + (size_t)(k * N + c) * R::CR;
-        for (int s = 0; s < NS; ++s) r[R::CR_M + s] = lM[k * NS + s];
-        for (int b = 0; b < D; ++b) {
-            r[R::CR_R + b] = lR[k * D + b];
-            r[R::CR_U + 0 * D + b] = lvs[k * D + b];
-            r[R::CR_U + 1 * D + b] = l0[k * D + b];
-            r[R::CR_U + 2 * D + b] = l1[k * D + b];
-            r[R::CR_U + 3 * D + b] = lp0[k * D + b];
-            r[R::CR_U + 4 * D + b] = lp1[k * D + b];
+    // the velocity part first: its adjoints go to the corner records and lv0 at once, so that
+    // none of its values is live in the deformation part
+    {
+        double vs[NX], M[NV * NS], lv1[D], lvs[NX] = {}, lv[D] = {}, lM[NV * NS] = {}, lR[NX] = {};
+        for (int k = 0; k < NV; ++k) {
+            const int p = g.c2n[k * N + c];
+            for (int b = 0; b < D; ++b) vs[k * D + b] = f.vs[b * Np + p];
+            for (int s = 0; s < NS; ++s) M[k * NS + s] = f.pkM[s * NC + k * N + c];
         }
+        for (int b = 0; b < D; ++b) lv1[b] = a.lv1[b * N + c];
+        adj::update_force_vjp<D>(vs, M, f.im[c], dt, lv1, lvs, lM, lR, lv);
+        for (int k = 0; k < NV; ++k) {
+            double *r = a.cr + (size_t)(k * N + c) * R::CR;
+            for (int s = 0; s < NS; ++s) r[R::CR_M + s] = lM[k * NS + s];
+            for (int b = 0; b < D; ++b) {
+                r[R::CR_R + b] = lR[k * D + b];
+                r[R::CR_U + b] = lvs[k * D + b];
+            }
+        }
+        for (int b = 0; b < D; ++b) a.lv0[b * N + c] = lv[b];
     }
-    for (int b = 0; b < D; ++b) a.lv0[b * N + c] = lv[b];
+    int pn[NV];
+    for (int k = 0; k < NV; ++k) pn[k] = g.c2n[k * N + c];
+    double F[DD], lF1[DD], lF[DD] = {}, lmu = 0.0, lkap = 0.0;
+    for (int q = 0; q < DD; ++q) F[q] = f.F[q * N + c];
+    for (int q = 0; q < DD; ++q) lF1[q] = a.lF1[q * N + c];
+    // nodal inputs read at their use; nodal adjoints stored as they are formed (record slot i
+    // of CR_U; the deformation part's lvs added to the velocity part's, stored above)
+    auto ld = [&](int i, double *u) {
+        const double *src = i == 0 ? f.vs : i == 1 ? f.x : i == 2 ? f.x1 : i == 3 ? f.vp : f.vp1;
+        for (int k = 0; k < NV; ++k)
+            for (int b = 0; b < D; ++b) u[k * D + b] = src[b * Np + pn[k]];
+    };
+    auto out = [&](int i, const double *l) {
+        for (int k = 0; k < NV; ++k) {
+            double *r = a.cr + (size_t)(k * N + c) * R::CR + R::CR_U + i * D;
+            for (int b = 0; b < D; ++b) r[b] = i == 0 ? r[b] + l[k * D + b] : l[k * D + b];
+        }
+    };
+    adj::update_deform_vjp<D>(ld, out, F, f.m[c], mu, kap, dt, ord, lF1, 0.0, lF, lmu, lkap);
     for (int q = 0; q < DD; ++q) a.lF0[q * N + c] = lF[q];
     a.lmu[c] += lmu + lkap * kappa_mu_factor<D>(prm);
 }

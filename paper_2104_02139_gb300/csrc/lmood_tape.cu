@@ -146,8 +146,10 @@ Fld view(lmood_tape t, const Fld &base, const Snap &cur, const Snap &nxt, const 
     return fr;
 }
 
-// the step kernels through a view (orders as recorded, no detection): t^n -> products, t^{n+1}
-void replay_view(lmood_tape t, const Fld &fr) {
+// the step kernels through a view (orders as recorded, no detection): t^n -> products, t^{n+1}.
+// geo: compute the view's x^n geometry first (else f.gf already holds it: the previous replay's
+// update wrote it, as the recorded step read it)
+void replay_view(lmood_tape t, const Fld &fr, bool geo) {
     lmood_state s = t->s;
     lmood_mesh M = s->M;
     const Ops &op = *M->ops;
@@ -155,7 +157,7 @@ void replay_view(lmood_tape t, const Fld &fr) {
     Prm kr = s->kp;
     kr.base_order = 0;
     kr.mood = 0;
-    op.geometry(M->geo, fr, st);  // the view's x^n geometry (the state's own is of another time)
+    if (geo) op.geometry(M->geo, fr, st);  // the state's own geometry is of another time
     op.moments(M->geo, fr, st);
     op.predict(M->geo, fr, kr, nullptr, nullptr, (int)M->nc, st);
     op.nodes(M->geo, fr, nullptr, nullptr, (int)M->np, 0, st);
@@ -369,7 +371,10 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
             const int64_t b = k * t->C, len = std::min(t->C, t->n - b);
             auto S = [&](int64_t i) { return i == 0 ? ck(k) : snap_at(t->seg + (i - 1) * sd, D, N, Np); };
             auto P = [&](int64_t i) { return prod_at(t->prod + i * t->pd, D, N, Np); };
-            for (int64_t i = 0; i < len; ++i) replay_view(t, view(t, f, S(i), S(i + 1), P(i), b + i));
+            for (int64_t i = 0; i < len; ++i) {
+                replay_view(t, view(t, f, S(i), S(i + 1), P(i), b + i), i == 0);
+                std::swap(t->gf, t->gf1);  // the update's x^{n+1} geometry is the next replay's x^n
+            }
             for (int64_t i = len - 1; i >= 0; --i) reverse_step(t, a, view(t, f, S(i), S(i + 1), P(i), b + i));
         }
     }
