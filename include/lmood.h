@@ -330,10 +330,15 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  * (x, v_p per node; v, F per cell) and of the per-cell mu; the adjoint is the exact transpose
  * of its linearisation, written by hand kernel by kernel (no atomics, deterministic).
  * Only the two-level cascade (P1 -> P0) is differentiated: a recorded step that used the
- * limited level returns LMOOD_ERR_ARG, and so do a mesh with traction, pressure,
- * prescribed-velocity or contact faces, a shear energy other than the neo-Hookean one
- * (a = -1) and the stiffened gas. Energy e has no influence on the other fields, so it
- * carries no adjoint.
+ * limited level returns LMOOD_ERR_ARG, and so do a shear energy other than the neo-Hookean one
+ * (a = -1) and the stiffened gas. Boundary faces of every kind are differentiated: slip and
+ * clamped nodes, traction and pressure faces (their forces depend on the faces' area vectors,
+ * hence on the positions), prescribed-velocity faces and contact walls (their multiplier
+ * steps, with the set of walls a node is in contact with, and whether each multiplier step
+ * applies, frozen like the order mask); the boundary values and contact walls themselves are
+ * constants. lmood_tape_backward returns LMOOD_ERR_STATE if the mesh's boundary values, tags or
+ * contact walls were changed after the recording. Energy e has no influence on the other
+ * fields, so it carries no adjoint.
  *
  * lmood_tape_record: runs n_steps ordinary lmood_step calls on s (the forward pass, with the
  *   MOOD loop and the dt rule as configured) and records what the reverse pass needs: the dt
@@ -359,7 +364,8 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  *   cell masses), grad_v [dim][n_cells], grad_F [dim*dim][n_cells], and grad_mu [n_cells]
  *   (accumulated over the steps; mu enters the stress, the impedance and kappa). When the tape
  *   starts from a just-initialised state, grad_v, grad_F and grad_mu are the gradients with
- *   respect to the inputs of lmood_state_init and grad_vp is zero. Any output may be NULL.
+ *   respect to the inputs of lmood_state_init, grad_x includes the positions' part of the
+ *   initial nodal solve (at the same fixed masses), and grad_vp is zero. Any output may be NULL.
  *   Pointers are device pointers when is_device != 0 (ordered on the mesh's stream), else
  *   host pointers (the call synchronises). s's fields are left as they are, except the
  *   diagnostic fields PKM and PKR when the tape starts from a just-initialised state. Results

@@ -332,17 +332,22 @@ def tangent_lib():
         build()
         _tlib = C.CDLL(_TLIB)
         vp = C.c_void_p
-        _tlib.orct_run.argtypes = [C.c_int, C.c_long, vp, C.c_long, vp, C.c_long, vp, vp, C.c_double, C.c_double,
-                                   vp, vp, vp, vp, vp, vp, C.POINTER(Params), C.c_long] + [vp] * 10
+        _tlib.orct_run.argtypes = [C.c_int, C.c_long, vp, vp, C.c_double, C.c_long, vp, C.c_long, vp, vp, vp, C.c_int, vp,
+                                   C.c_double, C.c_double, C.c_double, vp, vp, vp, vp, vp, vp, C.POINTER(Params),
+                                   C.c_long] + [vp] * 10
         _tlib.orct_run.restype = C.c_int
     return _tlib
 
 
-def tangent(problem, n_steps: int, dv=None, dmu=None, dF=None, params: Params | None = None, **kw) -> dict:
+def tangent(problem, n_steps: int, dv=None, dmu=None, dF=None, dx=None, x_shift: float = 0.0,
+            params: Params | None = None, **kw) -> dict:
     """The oracle's n-step map and its directional derivative (forward mode, dual numbers):
     the final state x, vp [d][np], v [d][nc], F [d*d][nc] and their derivatives dx, dvp, dv,
-    dF along the direction (dv [d][nc], dmu [nc], dF [d*d][nc]; None = 0) of the initial data,
-    with each step's order mask and dt held at the run's own (masks [n][nc] int8, dts [n])."""
+    dF along the direction (dv [d][nc], dmu [nc], dF [d*d][nc], dx [d][np] of the positions at
+    fixed cell masses; None = 0) of the initial data, with each step's order mask and dt held
+    at the run's own (masks [n][nc] int8, dts [n]). The problem's boundary values and contact
+    walls apply as constants. x_shift: start from the positions x + x_shift dx (masses and slip
+    directions of x), for central differences along dx."""
     m = problem.mesh
     d, nc, npn = m.dim, m.n_cells, m.n_nodes
     prm = params or default_params(problem.cfl, **kw)
@@ -361,8 +366,13 @@ def tangent(problem, n_steps: int, dv=None, dmu=None, dF=None, params: Params | 
     out["masks"] = np.zeros((n_steps, nc), np.int8)
     out["dts"] = np.zeros(n_steps)
     nb = m.btag.size
-    rc = tangent_lib().orct_run(d, npn, arr(m.x), nc, arr(m.c2n, np.int32), nb,
+    bcval = getattr(problem, "bcval", None)
+    contact = getattr(problem, "contact", None)
+    planes, ceps = (np.asarray(contact[0], dtype=np.float64), float(contact[1])) if contact is not None else (None, 0.0)
+    rc = tangent_lib().orct_run(d, npn, arr(m.x), arr(dx), x_shift, nc, arr(m.c2n, np.int32), nb,
                                 arr(m.bface, np.int32) if nb else None, arr(m.btag, np.int32) if nb else None,
+                                arr(bcval) if (bcval is not None and nb) else None,
+                                0 if planes is None else len(planes), arr(planes), ceps,
                                 problem.rho0, problem.lam, arr(problem.mu), arr(dmu), arr(problem.v), arr(dv),
                                 arr(problem.F), arr(dF), C.byref(prm), n_steps,
                                 *(out[k].ctypes.data for k in ("x", "dx", "vp", "dvp", "v", "dv", "F", "dF")),

@@ -15,7 +15,8 @@
  * contraction). Seeding the derivative parts of the initial data (v per cell, mu per cell, F
  * per cell) with a direction delta gives, after n steps, J(state^N) delta exactly (up to
  * rounding), where J is the Jacobian of the n-step map with every step's order mask and dt
- * held at the values the run takes: the derivative parts of dt are dropped after every step,
+ * held at the values the run takes (and, with boundary faces, every contact and multiplier
+ * decision, which are comparisons too): the derivative parts of dt are dropped after every step,
  * which is what "dt frozen" means (the adjoint of the library differentiates the same map;
  * its readings A1 and A2: the masses are fixed, and the initial first-order nodal solve of
  * v_p^0 is differentiated through).
@@ -108,14 +109,22 @@ void split_soa(const real *a, long n, int k, double *val, double *dir) {
 
 /*
  * Run n_steps oracle steps from the initial data (v [d][nc], mu [nc], F [d*d][nc] or NULL = I)
- * with derivative parts (dv, dmu, dF; each may be NULL = 0), dt's derivative dropped at
- * initialisation and after every step. Outputs (each may be NULL): the final state's values
- * and derivatives, SoA like the oracle's orc_get (x, vp [d][np]; v [d][nc]; F [d*d][nc]), the
- * order mask of every step masks [n_steps][nc] and its dt dts [n_steps]. Returns the oracle's
- * status (0 ok; the first failing step stops the run).
+ * with derivative parts (dv, dmu, dF, and dx [d][np] of the node positions; each may be
+ * NULL = 0), dt's derivative dropped at initialisation and after every step. The mesh's
+ * boundary values bcval [d][nb] (NULL: zero) and contact walls (n_planes planes [n][2d],
+ * threshold eps) are constants. A direction dx of the positions is taken at fixed cell masses:
+ * the masses and the mesh's own data (slip directions) are those of x, the run starts from the
+ * positions x + x_shift dx with derivative part dx, and the initial first-order nodal solve of
+ * v_p^0 is done again there (x_shift != 0 gives the values of a displaced start, whose central
+ * differences pin the derivative part). Outputs (each may be NULL): the
+ * final state's values and derivatives, SoA like the oracle's orc_get (x, vp [d][np]; v [d][nc];
+ * F [d*d][nc]), the order mask of every step masks [n_steps][nc] and its dt dts [n_steps].
+ * Returns the oracle's status (0 ok; the first failing step stops the run).
  */
-extern "C" int orct_run(int d, long np, const double *x_soa, long nc, const int *c2n_soa, long nb,
-                        const int *bf_soa, const int *btag, double rho0, double lam, const double *mu,
+extern "C" int orct_run(int d, long np, const double *x_soa, const double *dx_soa, double x_shift, long nc,
+                        const int *c2n_soa,
+                        long nb, const int *bf_soa, const int *btag, const double *bcval_soa, int n_planes,
+                        const double *planes, double contact_eps, double rho0, double lam, const double *mu,
                         const double *dmu, const double *v_soa, const double *dv_soa, const double *F_soa,
                         const double *dF_soa, const OrcParams *prm, long n_steps, double *x_out, double *dx_out,
                         double *vp_out, double *dvp_out, double *v_out, double *dv_out, double *F_out,
@@ -127,6 +136,20 @@ extern "C" int orct_run(int d, long np, const double *x_soa, long nc, const int 
     int st = orc_mesh_new(d, np, xr, nc, c2n_soa, nb, bf_soa, btag, &M);
     free(xr);
     if (st) return st;
+    if (bcval_soa && nb > 0) {
+        real *bv = dual_array(nb * d, bcval_soa, nullptr);
+        st = orc_mesh_set_bc_values(M, bv);
+        free(bv);
+    }
+    if (st == ORC_OK && n_planes > 0) {
+        real *pl = dual_array(n_planes * 2 * d, planes, nullptr);
+        st = orc_mesh_set_contact(M, n_planes, pl, contact_eps);
+        free(pl);
+    }
+    if (st) {
+        orc_mesh_free(M);
+        return st;
+    }
     real *mur = dual_array(nc, mu, dmu);
     real *vr = dual_array(nc * d, v_soa, dv_soa);
     real *Fr = F_soa ? dual_array(nc * dd, F_soa, dF_soa) : nullptr;
@@ -138,6 +161,19 @@ extern "C" int orct_run(int d, long np, const double *x_soa, long nc, const int 
     if (st) {
         orc_mesh_free(M);
         return st;
+    }
+    if (dx_soa) {
+        for (long p = 0; p < np; ++p)
+            for (int a = 0; a < d; ++a)
+                S->x[p * d + a] = Dual(S->x[p * d + a].v + x_shift * dx_soa[a * np + p], dx_soa[a * np + p]);
+        // the initial first-order nodal solve again, at the positions with their derivative
+        // and the masses held (the oracle's own initialisation steps, in its order)
+        Work w = work_new(M);
+        phase_geometry(S, S->x, &w);
+        for (long c = 0; c < nc; ++c) S->tau[c] = w.V[c] / S->m[c];
+        phase_packets(S, S->order, 0.0, &w);
+        for (long p = 0; p < np; ++p) node_solve_one(M, S->x, w.pkM, w.pkR, p, S->vp + p * d);
+        work_free(&w);
     }
     S->dt = Dual(S->dt.v);  // dt frozen
     for (long s = 0; s < n_steps && st == ORC_OK; ++s) {

@@ -39,6 +39,10 @@ struct AdjBuf {
     // forward intermediates [N][F_LEN], each corner's [NC][K_LEN], the corners' pass-2 and
     // pass-1 products [NC][Q2_LEN], [NC][Q1_LEN]
     double *pf, *pk, *q2, *q1;
+    // boundary faces of traction, pressure or velocity kind [nbf][D][D]: per node of the face
+    // (slot i for its node i) the adjoint of the face's area vector from that node's solve,
+    // then (k_adj_faces) the adjoint of that node's position; NULL when the mesh has none
+    double *bf;
 };
 
 struct AdjOps {
@@ -55,7 +59,10 @@ struct AdjOps {
     // tail: first the second-order cells' corner-matrix and geometry part of the predictor's
     // reverse (after predict without force_p0)
     void (*cells)(const Geo &, const Fld &, const Prm &, const AdjBuf &, int tail, cudaStream_t);
-    // nodes: gather of the per-corner position adjoints
+    // boundary faces: the area-vector adjoints left by the nodal solves -> the face nodes'
+    // position adjoints (no launch when AdjBuf::bf is NULL)
+    void (*faces)(const Geo &, const Fld &, const AdjBuf &, cudaStream_t);
+    // nodes: gather of the per-corner (and per-face) position adjoints
     void (*gather)(const Geo &, const AdjBuf &, cudaStream_t);
     // cells: impedance of the initial state (after the t^0 predictor's reverse)
     void (*z0)(const Geo &, const Fld &, const Prm &, const AdjBuf &, cudaStream_t);

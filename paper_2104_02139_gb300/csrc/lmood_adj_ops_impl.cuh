@@ -12,7 +12,8 @@ template <int D> void adj_update(const Geo &g, const Fld &f, const Prm &p, const
     k_adj_update<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
 }
 template <int D> void adj_nodes(const Geo &g, const Fld &f, const AdjBuf &a, int init_mode, cudaStream_t s) {
-    k_adj_nodes<D><<<adj_blocks(g.Np, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, f, a, init_mode);
+    k_adj_nodes<D, false><<<adj_blocks(g.Np, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, f, a, init_mode);
+    if (a.bf) k_adj_nodes<D, true><<<adj_blocks(g.Np, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, f, a, init_mode);
 }
 template <int D>
 void adj_predict(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, int force_p0, cudaStream_t s) {
@@ -36,6 +37,9 @@ template <int D> void adj_cells(const Geo &g, const Fld &f, const Prm &p, const 
 template <int D> void adj_gather(const Geo &g, const AdjBuf &a, cudaStream_t s) {
     k_adj_gather<D><<<adj_blocks(g.Np, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, a);
 }
+template <int D> void adj_faces(const Geo &g, const Fld &f, const AdjBuf &a, cudaStream_t s) {
+    if (a.bf && g.nbf > 0) k_adj_faces<D><<<adj_blocks(g.nbf, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, f, a);
+}
 template <int D> void adj_z0(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, cudaStream_t s) {
     k_adj_z0<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
 }
@@ -44,7 +48,7 @@ template <int D> void adj_z0(const Geo &g, const Fld &f, const Prm &p, const Adj
 
 #define LMOOD_ADJ_OPS_TABLE(D)                                                                              \
     static const AdjOps table = {D, adj_update<D>, adj_nodes<D>, adj_predict<D>, adj_momsum<D>, adj_cells<D>, \
-                                 adj_gather<D>, adj_z0<D>};                                                  \
+                                 adj_faces<D>, adj_gather<D>, adj_z0<D>};                                    \
     return table;
 
 }  // namespace lmood

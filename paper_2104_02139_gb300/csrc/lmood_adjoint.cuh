@@ -363,6 +363,221 @@ LMOOD_HD void node_solve_vjp(const double *M, const double *b, int nd, const dou
 
 
 // ---------------------------------------------------------------------------------------
+// Boundary faces of the nodal solve. bface_area: the outward area vector of a boundary face
+// from its D nodes xq [D][D] (2D edge (q0, q1): (y1 - y0, x0 - x1); 3D triangle:
+// (1/2) (x1 - x0) x (x2 - x0)); bface_area_vjp accumulates lxq from lN.
+// ---------------------------------------------------------------------------------------
+template <int D> LMOOD_HD void bface_area(const double *xq, double *N) {
+    if constexpr (D == 2) {
+        N[0] = xq[3] - xq[1];
+        N[1] = xq[0] - xq[2];
+    } else {
+        double u[3], w[3];
+        for (int a = 0; a < 3; ++a) {
+            u[a] = xq[3 + a] - xq[a];
+            w[a] = xq[6 + a] - xq[a];
+        }
+        N[0] = 0.5 * (u[1] * w[2] - u[2] * w[1]);
+        N[1] = 0.5 * (u[2] * w[0] - u[0] * w[2]);
+        N[2] = 0.5 * (u[0] * w[1] - u[1] * w[0]);
+    }
+}
+
+template <int D> LMOOD_HD void bface_area_vjp(const double *xq, const double *lN, double *lxq) {
+    if constexpr (D == 2) {
+        lxq[3] += lN[0];
+        lxq[1] -= lN[0];
+        lxq[0] += lN[1];
+        lxq[2] -= lN[1];
+    } else {
+        double u[3], w[3];
+        for (int a = 0; a < 3; ++a) {
+            u[a] = xq[3 + a] - xq[a];
+            w[a] = xq[6 + a] - xq[a];
+        }
+        // N = (1/2) u x w: lu = (1/2) w x lN, lw = (1/2) lN x u
+        const double lu[3] = {0.5 * (w[1] * lN[2] - w[2] * lN[1]), 0.5 * (w[2] * lN[0] - w[0] * lN[2]),
+                              0.5 * (w[0] * lN[1] - w[1] * lN[0])};
+        const double lw[3] = {0.5 * (lN[1] * u[2] - lN[2] * u[1]), 0.5 * (lN[2] * u[0] - lN[0] * u[2]),
+                              0.5 * (lN[0] * u[1] - lN[1] * u[0])};
+        for (int a = 0; a < 3; ++a) {
+            lxq[3 + a] += lu[a];
+            lxq[6 + a] += lw[a];
+            lxq[a] -= lu[a] + lw[a];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Nodal solve with traction, pressure and prescribed-velocity faces and contact walls (Eqs.
+// pBC, vBC1, vBC; Sect. "Boundary condition treatments"), pure form. b0: the corners' sum;
+// the node's boundary faces j < nf are read through fc(j, tag, N, val) (N [D] the face's
+// outward area vector at x^n, val [D] its value: traction vector, pressure in val[0],
+// prescribed velocity; faces of other tags are skipped) when ext; walls: nw planes (point,
+// unit normal into the body) [nw][2D], threshold eps, the node's position xp. v = K b with
+// b = b0 + the traction and pressure forces (each face's share N / D), then the multiplier
+// step v -= T K d, T = (v . d - g) / (d . K d) of the velocity faces (d = sum N / D, g = sum
+// val . N / D), then the same step with d = n, g = 0 for each wall the node is within eps of
+// and moving into.
+// ---------------------------------------------------------------------------------------
+template <int D> struct BcSolve {
+    double b[D], v0[D], dv[D], gsum, w1[D], wd, T1, v[D];
+    bool p1;
+    bool act[kMaxContact];
+    double vb[kMaxContact][D], ww[kMaxContact][D], Tw[kMaxContact], wn[kMaxContact];
+};
+
+template <int D, class FC>
+LMOOD_HD void node_solve_bc_fw(const double *M, const double *b0, int nd, const double *t, bool ext, int nf, FC &&fc,
+                               int nw, const double *planes, double eps, const double *xp, BcSolve<D> &r) {
+    int nvel = 0;
+    r.gsum = 0.0;
+    for (int a = 0; a < D; ++a) {
+        r.b[a] = b0[a];
+        r.dv[a] = 0.0;
+    }
+    if (ext)
+        for (int j = 0; j < nf; ++j) {
+            int tag;
+            double N[D], val[D];
+            fc(j, tag, N, val);
+            if (tag == TAG_TRACTION) {
+                double ar = 0.0;
+                for (int a = 0; a < D; ++a) ar += N[a] * N[a];
+                ar = sqrt(ar) * (1.0 / D);
+                for (int a = 0; a < D; ++a) r.b[a] += ar * val[a];
+            } else if (tag == TAG_PRESSURE) {
+                for (int a = 0; a < D; ++a) r.b[a] -= val[0] * N[a] * (1.0 / D);
+            } else if (tag == TAG_VELOCITY) {
+                for (int a = 0; a < D; ++a) {
+                    r.dv[a] += N[a] * (1.0 / D);
+                    r.gsum += val[a] * N[a] * (1.0 / D);
+                }
+                ++nvel;
+            }
+        }
+    node_solve<D>(M, r.b, nd, t, r.v0);
+    for (int a = 0; a < D; ++a) r.v[a] = r.v0[a];
+    r.p1 = false;
+    if (nvel > 0) {
+        node_solve<D>(M, r.dv, nd, t, r.w1);
+        double wd = 0.0, vd = 0.0;
+        for (int a = 0; a < D; ++a) {
+            wd += r.w1[a] * r.dv[a];
+            vd += r.v0[a] * r.dv[a];
+        }
+        if (wd > 0.0) {
+            r.p1 = true;
+            r.wd = wd;
+            r.T1 = (vd - r.gsum) / wd;
+            for (int a = 0; a < D; ++a) r.v[a] -= r.T1 * r.w1[a];
+        }
+    }
+    for (int k = 0; k < kMaxContact; ++k) {
+        r.act[k] = false;
+        if (k >= nw) continue;
+        const double *P = planes + 2 * D * k, *n = P + D;
+        double dist = 0.0, vn = 0.0;
+        for (int a = 0; a < D; ++a) {
+            dist += n[a] * (xp[a] - P[a]);
+            vn += n[a] * r.v[a];
+        }
+        if (!(dist < eps && vn < 0.0)) continue;
+        double w[D], wn = 0.0;
+        node_solve<D>(M, n, nd, t, w);
+        for (int a = 0; a < D; ++a) wn += w[a] * n[a];
+        if (wn > 0.0) {
+            r.act[k] = true;
+            r.wn[k] = wn;
+            r.Tw[k] = vn / wn;
+            for (int a = 0; a < D; ++a) {
+                r.vb[k][a] = r.v[a];
+                r.ww[k][a] = w[a];
+                r.v[a] -= r.Tw[k] * w[a];
+            }
+        }
+    }
+}
+
+template <int D, class FC>
+LMOOD_HD void node_solve_bc(const double *M, const double *b0, int nd, const double *t, bool ext, int nf, FC &&fc,
+                            int nw, const double *planes, double eps, const double *xp, double *v) {
+    BcSolve<D> r;
+    node_solve_bc_fw<D>(M, b0, nd, t, ext, nf, fc, nw, planes, eps, xp, r);
+    for (int a = 0; a < D; ++a) v[a] = r.v[a];
+}
+
+// Product: lv -> lb [D] (the adjoint of b0), lM (full D x D, accumulated), and ln(j, lN) for
+// every face j < nf (lN [D] the adjoint of its area vector; zero for faces of other tags).
+// The walls a node is in contact with, and whether each multiplier step applies, are those
+// of the forward evaluation (a frozen active set, like the MOOD mask).
+template <int D, class FC, class LN>
+LMOOD_HD void node_solve_bc_vjp(const double *M, const double *b0, int nd, const double *t, bool ext, int nf, FC &&fc,
+                                int nw, const double *planes, double eps, const double *xp, const double *lv_in,
+                                double *lb, double *lM, LN &&ln) {
+    BcSolve<D> r;
+    node_solve_bc_fw<D>(M, b0, nd, t, ext, nf, fc, nw, planes, eps, xp, r);
+    double lv[D], kl[D];
+    for (int a = 0; a < D; ++a) lv[a] = lv_in[a];
+    // v' = v - T w, T = (v . d - g) / (w . d), w = K d: lT = -lv' . w, lw = -T lv', then through
+    // T to v, w (and d, g); through w = K d to M (-(K lw) (x) w) and d (K lw)
+    for (int k = kMaxContact - 1; k >= 0; --k) {
+        if (!r.act[k]) continue;
+        const double *n = planes + 2 * D * k + D;
+        double lT = 0.0, lw[D];
+        for (int a = 0; a < D; ++a) lT -= lv[a] * r.ww[k][a];
+        const double lvn = lT / r.wn[k], lwn = -lT * r.Tw[k] / r.wn[k];
+        for (int a = 0; a < D; ++a) {
+            lw[a] = -r.Tw[k] * lv[a] + lwn * n[a];
+            lv[a] += lvn * n[a];
+        }
+        node_solve<D>(M, lw, nd, t, kl);
+        for (int a = 0; a < D; ++a)
+            for (int c = 0; c < D; ++c) lM[a * D + c] -= kl[a] * r.ww[k][c];
+    }
+    double ldv[D] = {}, lgsum = 0.0;
+    if (r.p1) {
+        double lT = 0.0, lw[D];
+        for (int a = 0; a < D; ++a) lT -= lv[a] * r.w1[a];
+        const double lvd = lT / r.wd, lwd = -lT * r.T1 / r.wd;
+        lgsum = -lT / r.wd;
+        for (int a = 0; a < D; ++a) {
+            lw[a] = -r.T1 * lv[a] + lwd * r.dv[a];
+            ldv[a] += lvd * r.v0[a] + lwd * r.w1[a];
+            lv[a] += lvd * r.dv[a];
+        }
+        node_solve<D>(M, lw, nd, t, kl);
+        for (int a = 0; a < D; ++a) {
+            ldv[a] += kl[a];
+            for (int c = 0; c < D; ++c) lM[a * D + c] -= kl[a] * r.w1[c];
+        }
+    }
+    node_solve<D>(M, lv, nd, t, lb);  // v0 = K b: lb = K lv, lM -= lb (x) v0
+    for (int a = 0; a < D; ++a)
+        for (int c = 0; c < D; ++c) lM[a * D + c] -= lb[a] * r.v0[c];
+    if (!ext) return;
+    for (int j = 0; j < nf; ++j) {
+        int tag;
+        double N[D], val[D], lN[D] = {};
+        fc(j, tag, N, val);
+        if (tag == TAG_TRACTION) {
+            double nn = 0.0, lbt = 0.0;
+            for (int a = 0; a < D; ++a) {
+                nn += N[a] * N[a];
+                lbt += lb[a] * val[a];
+            }
+            const double s = lbt / (sqrt(nn) * D);
+            for (int a = 0; a < D; ++a) lN[a] = s * N[a];
+        } else if (tag == TAG_PRESSURE) {
+            for (int a = 0; a < D; ++a) lN[a] = -val[0] * lb[a] * (1.0 / D);
+        } else if (tag == TAG_VELOCITY) {
+            for (int a = 0; a < D; ++a) lN[a] = (ldv[a] + lgsum * val[a]) * (1.0 / D);
+        }
+        ln(j, lN);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Cell predictor and corner packets (pure form of k_predict for orders 1 and 2).
 // Inputs: xs [NV][D] node positions at t^n; mom(k, j) = moment j of node k (accessor with a
 // stride); vc, Fc, z, mu, kappa, 1/m, dt; ord. Outputs: M [NV][NS] (symmetric storage),

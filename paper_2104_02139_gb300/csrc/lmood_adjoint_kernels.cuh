@@ -88,12 +88,17 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_update(Geo g, Fld 
 }
 
 // ---------------------------------------------------------------------------------------
-// init_mode: the t^0 nodal solve v_p^0 = v*_p (no motion); lam v*_p = lam v_p^0.
-template <int D> __global__ void __launch_bounds__(128) k_adj_nodes(Geo g, Fld f, AdjBuf a, int init_mode) {
+// init_mode: the t^0 nodal solve v_p^0 = v*_p (no motion); lam v*_p = lam v_p^0. BC: the
+// nodes with traction / pressure / velocity faces or contact walls (a second launch, only on
+// meshes that have them), else the others (the first keeps the common kernel's registers low).
+template <int D, bool BC>
+__global__ void __launch_bounds__(128) k_adj_nodes(Geo g, Fld f, AdjBuf a, int init_mode) {
     using R = AdjRec<D>;
     constexpr int NV = D + 1;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.Np) return;
+    const unsigned char ndf = g.bc_ndof[p];
+    if (((ndf & (BC_EXT | BC_CONTACT)) != 0) != BC) return;
     const int N = g.N, Np = g.Np, NC = NV * N;
     double M[D * D] = {}, b[D] = {}, lvs[D] = {}, lx0[D] = {}, lx1[D] = {}, lvp0[D] = {}, lvp1[D] = {};
     const int j0 = g.n2c_off[p], j1 = g.n2c_off[p + 1];
@@ -127,7 +132,36 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_nodes(Geo g, Fld f
             a.lvp0[r * Np + p] = -lvp1t + lvp0[r];
         }
     }
-    adj::node_solve_vjp<D>(M, b, g.bc_ndof[p] & BC_NDOF, tv, lvs, lb, lM);
+    if constexpr (!BC) {
+        adj::node_solve_vjp<D>(M, b, ndf & BC_NDOF, tv, lvs, lb, lM);
+    } else {
+        // traction / pressure / velocity faces and contact walls: the faces' area-vector
+        // adjoints go to the node's slot of each face record (summed and moved to the face's
+        // nodes by k_adj_faces)
+        const int jb0 = g.nbf_off[p], nf = g.nbf_off[p + 1] - jb0, nb = g.nbf;
+        auto fc = [&](int j, int &tag, double *N, double *val) {
+            const int fid = g.nbf_idx[jb0 + j];
+            tag = g.bf_tag[fid];
+            if (tag < TAG_TRACTION || tag > TAG_VELOCITY) return;
+            double xq[D * D];
+            for (int i = 0; i < D; ++i)
+                for (int c = 0; c < D; ++c) xq[i * D + c] = f.x[c * Np + g.bf_nodes[i * nb + fid]];
+            adj::bface_area<D>(xq, N);
+            for (int c = 0; c < D; ++c) val[c] = g.bf_val[c * nb + fid];
+        };
+        auto ln = [&](int j, const double *lN) {
+            const int fid = g.nbf_idx[jb0 + j], tag = g.bf_tag[fid];
+            if (tag < TAG_TRACTION || tag > TAG_VELOCITY) return;
+            int i = 0;
+            while (i < D - 1 && g.bf_nodes[i * nb + fid] != p) ++i;
+            for (int c = 0; c < D; ++c) a.bf[((size_t)fid * D + i) * D + c] = lN[c];
+        };
+        double xp[D];
+        for (int c = 0; c < D; ++c) xp[c] = f.x[c * Np + p];
+        const int nw = (ndf & BC_CONTACT) ? (int)g.contact[0] : 0;
+        adj::node_solve_bc_vjp<D>(M, b, ndf & BC_NDOF, tv, (ndf & BC_EXT) != 0, nf, fc, nw, g.contact + 2,
+                                  g.contact[1], xp, lvs, lb, lM, ln);
+    }
     for (int j = j0; j < j1; ++j) {
         double *r = a.cr + (size_t)g.n2c[j] * R::CR;
         for (int q = 0; q < D; ++q) r[R::CR_R + q] = (init_mode ? 0.0 : r[R::CR_R + q]) + lb[q];
@@ -405,7 +439,35 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_gather(Geo g, AdjB
         const size_t cid = g.n2c[j];
         for (int b = 0; b < D; ++b) l[b] += a.cp[cid * R::CP + R::CP_X + b] + a.cd[cid * D + b];
     }
+    if (a.bf && (g.bc_ndof[p] & BC_EXT))  // the node's share of its boundary faces' products
+        for (int j = g.nbf_off[p]; j < g.nbf_off[p + 1]; ++j) {
+            const int fid = g.nbf_idx[j], tag = g.bf_tag[fid];
+            if (tag < TAG_TRACTION || tag > TAG_VELOCITY) continue;
+            int i = 0;
+            while (i < D - 1 && g.bf_nodes[i * g.nbf + fid] != p) ++i;
+            for (int b = 0; b < D; ++b) l[b] += a.bf[((size_t)fid * D + i) * D + b];
+        }
     for (int b = 0; b < D; ++b) a.lx0[b * Np + p] += l[b];
+}
+
+// boundary faces of traction, pressure or velocity kind: the area-vector adjoints the face's
+// D nodes left in its record (k_adj_nodes) summed, and their product with respect to the
+// face's node positions written back into the same record, slot i for the face's node i
+template <int D> __global__ void __launch_bounds__(128) k_adj_faces(Geo g, Fld f, AdjBuf a) {
+    const int fid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (fid >= g.nbf) return;
+    const int tag = g.bf_tag[fid];
+    if (tag < TAG_TRACTION || tag > TAG_VELOCITY) return;
+    const int nb = g.nbf, Np = g.Np;
+    double *r = a.bf + (size_t)fid * D * D;
+    double lN[D] = {}, xq[D * D], lxq[D * D] = {};
+    for (int i = 0; i < D; ++i)
+        for (int c = 0; c < D; ++c) {
+            lN[c] += r[i * D + c];
+            xq[i * D + c] = f.x[c * Np + g.bf_nodes[i * nb + fid]];
+        }
+    adj::bface_area_vjp<D>(xq, lN, lxq);
+    for (int i = 0; i < D * D; ++i) r[i] = lxq[i];
 }
 
 // impedance of the initial state only (the t^0 packets' z): lmu and lF from lz0
@@ -424,6 +486,13 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_z0(Geo g, Fld f, P
     adj::impedance_vjp<D>(F, f.m[c] / V, mu, kap, a.lz0[c], lF, lrho, lmu, lkap);
     for (int q = 0; q < DD; ++q) a.lF0[q * N + c] += lF[q];
     a.lmu[c] += lmu + lkap * kappa_mu_factor<D>(prm);
+    // rho = m / V at fixed m: the positions' part, added to the corners' records of the t^0
+    // packets' product (k_adj_predict wrote them)
+    using R = AdjRec<D>;
+    double lxs[NX] = {}, lN0[NX] = {};
+    adj::faces_vjp<D>(xs, -lrho * f.m[c] / (V * V), lN0, lxs);
+    for (int k = 0; k < NV; ++k)
+        for (int b = 0; b < D; ++b) a.cp[(size_t)(k * N + c) * R::CP + R::CP_X + b] += lxs[k * D + b];
 }
 
 }  // namespace lmood

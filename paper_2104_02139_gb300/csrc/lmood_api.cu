@@ -440,6 +440,7 @@ extern "C" lmood_status lmood_mesh_set_bc_values(lmood_mesh m, const double *val
     LM_CUDA(cudaMemcpyAsync(m->d_bfval, values, (size_t)m->dim * m->nb * sizeof(double),
                             is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->st));
     if (!is_device) LM_CUDA(cudaStreamSynchronize(m->st));
+    ++m->bc_version;
     return LMOOD_OK;
 }
 
@@ -458,6 +459,7 @@ extern "C" lmood_status lmood_mesh_set_contact(lmood_mesh m, int n_planes, const
     }
     LM_CUDA(cudaMemcpyAsync(m->d_contact, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, m->st));
     LM_CUDA(cudaStreamSynchronize(m->st));
+    ++m->bc_version;
     return LMOOD_OK;
 }
 
@@ -479,6 +481,7 @@ extern "C" lmood_status lmood_mesh_set_btag(lmood_mesh m, const int32_t *btag) {
     LM_CUDA(cudaStreamSynchronize(m->st));
     m->h_btag = tags;
     m->has_ext = has_ext;
+    ++m->bc_version;
     return LMOOD_OK;
 }
 

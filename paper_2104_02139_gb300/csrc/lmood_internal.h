@@ -68,6 +68,7 @@ struct lmood_mesh_s {
     unsigned char *d_ndof = nullptr, *d_btag = nullptr;
     double *d_bct = nullptr, *d_bfval = nullptr, *d_contact = nullptr;
     bool has_ext = false;         // some face has a traction / pressure / velocity / contact tag
+    uint64_t bc_version = 0;      // counts the changes of boundary values, tags and contact walls
     lmood::DevAllocs mem;
 };
 

@@ -22,6 +22,7 @@ struct lmood_tape_s {
     lmood_state s = nullptr;
     const AdjOps *aop = nullptr;
     int64_t n = 0, C = 1, n_ck = 0, bytes = 0, pd = 0;
+    uint64_t bc_version = 0;        // the mesh's boundary data the steps were taken with
     bool at_init = false, store = false;
     double *prod = nullptr;         // store mode: [n] products of each step (pkM, pkR, v*, moments);
                                     // checkpoint mode: [C] products of the segment's steps
@@ -178,6 +179,7 @@ void reverse_step(lmood_tape t, AdjBuf &a, const Fld &f) {
     ao.predict(M->geo, f, kr, a, 0, st);
     ao.momsum(M->geo, f, a, st);
     ao.cells(M->geo, f, kr, a, 1, st);
+    ao.faces(M->geo, f, a, st);
     ao.gather(M->geo, a, st);
     std::swap(a.lv0, a.lv1);
     std::swap(a.lF0, a.lF1);
@@ -217,9 +219,6 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     if (n_steps < 1 || checkpoint_every < 0)
         return fail(LMOOD_ERR_ARG, "lmood_tape_record: n_steps must be >= 1 and checkpoint_every >= 0");
     lmood_mesh M = s->M;
-    if (M->has_ext)
-        return fail(LMOOD_ERR_ARG, "lmood_tape_record: the mesh has traction, pressure, prescribed-velocity or "
-                                   "contact faces, which have no adjoint");
     if (s->mat.shear_a != -1.0 || s->mat.eos != 0)
         return fail(LMOOD_ERR_ARG, "lmood_tape_record: the adjoint covers the neo-Hookean material (a = -1, "
                                    "volumetric law of Eq. EOS_neoHook) only");
@@ -234,6 +233,7 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     t->C = t->store ? 1 : std::min(checkpoint_every, n_steps);
     t->n_ck = t->store ? n_steps + 1 : (n_steps + t->C - 1) / t->C;
     t->at_init = s->at_init;
+    t->bc_version = M->bc_version;
     const int64_t sd = snap_doubles(D, N, Np);
     t->pd = prod_doubles(D, nmom, N, Np);
     const size_t nd = sizeof(double);
@@ -282,6 +282,7 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     }
     // (its own buffer: the cell kernel after the moment sums still reads the corner records)
     A((void **)&a.lm, (size_t)nmom * Np * nd);
+    if (M->has_ext && M->nb > 0) A((void **)&a.bf, (size_t)M->nb * DD * nd);
     if (r) {
         tape_free(t);
         return r;
@@ -346,6 +347,9 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
     if (!t || !t->s) return fail(LMOOD_ERR_ARG, "lmood_tape_backward: NULL tape");
     lmood_state s = t->s;
     if (s->broken) return fail(LMOOD_ERR_STATE, "lmood_tape_backward: state unusable after an earlier CUDA error");
+    if (s->M->bc_version != t->bc_version)
+        return fail(LMOOD_ERR_STATE, "lmood_tape_backward: the mesh's boundary values, tags or contact walls changed "
+                                     "after the tape was recorded");
     lmood_mesh M = s->M;
     const int D = M->dim;
     const int64_t N = M->nc, Np = M->np, sd = snap_doubles(D, N, Np);
@@ -393,9 +397,15 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
         AdjBuf ai = a;
         ai.lv0 = a.lv1;
         ai.lF0 = a.lF1;
+        ai.lx0 = a.lx1;
         ao.nodes(M->geo, f0, ai, 1, st);
         ao.predict(M->geo, f0, p0, ai, 1, st);
         ao.z0(M->geo, f0, p0, ai, st);
+        // the positions' part of the initial solve (packets, impedance, boundary faces; the
+        // corners' records of the cell gather carry nothing here)
+        LM_CUDA(cudaMemsetAsync(a.cd, 0, (size_t)D * (D + 1) * N * sizeof(double), st));
+        ao.faces(M->geo, f0, ai, st);
+        ao.gather(M->geo, ai, st);
         LM_CUDA(cudaMemsetAsync(a.lvp1, 0, D * Np * sizeof(double), st));
     }
     cudaError_t le = cudaGetLastError();

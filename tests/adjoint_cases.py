@@ -1,0 +1,33 @@
+"""Small problems for the adjoint's reference checks (CPU tangent pins and GPU tests): one
+per kind of boundary face, and a smooth direction of the node positions."""
+import numpy as np
+
+import workloads as W
+
+
+def bc_case(name):
+    """small problems with each kind of boundary face (the GPU parity tests' set-ups)"""
+    if name == "piston2d":
+        return W.piston2d(n=11)
+    if name == "rebound2d":
+        return W.rebound2d(n=9, gap=0.3 / 8)  # within the capture distance, moving in: in contact at once
+    if name == "pressure_traction2d":
+        m = W.tri_mesh(9, 3, bc={"x0": W.PRESSURE, "x1": W.TRACTION, "y0": W.SLIP, "y1": W.PRESSURE})
+        val = W.side_values(m, W.PRESSURE, (0.02, 0.0)) + W.side_values(m, W.TRACTION, (0.01, -0.02))
+        p = W.cell_points(m)
+        v = 0.02 * np.stack([np.sin(np.pi * p[:, 1]), np.cos(np.pi * p[:, 0])])
+        return W.Problem("pt2d", m, 1.0, 2.0, np.full(m.n_cells, 1.0), v, 0.4, 10, bcval=val)
+    bc = {"x0": W.VELOCITY, "x1": W.PRESSURE, "y0": W.SLIP, "y1": W.CLAMPED, "z0": W.TRACTION}
+    m = W.tet_mesh(3, 3, 3, 5, bc=bc)
+    val = W.side_values(m, W.VELOCITY, (0.02, 0.0, 0.0)) + W.side_values(m, W.PRESSURE, (-0.01, 0, 0)) \
+        + W.side_values(m, W.TRACTION, (0.0, 0.005, -0.01))
+    p = W.cell_points(m)
+    v = 0.01 * np.stack([np.sin(np.pi * p[:, 1]), np.cos(np.pi * p[:, 2]), np.sin(np.pi * p[:, 0])])
+    return W.Problem("box3d_bc", m, 1.0, 2.0, np.full(m.n_cells, 1.0), v, 0.25, 10, bcval=val)
+
+
+def smooth_positions_direction(m):
+    """a smooth displacement field of the nodes, 0.1 in amplitude (a random one strains single
+    cells and moves cells near an RDMP threshold across it)"""
+    x = m.x
+    return 0.1 * np.stack([np.sin(np.pi * (x[0] + 0.3 * a)) * np.cos(np.pi * x[1] + 0.2 * a) for a in range(m.dim)])

@@ -347,6 +347,103 @@ template <int D> void check_update(int ord) {
     }
 }
 
+// nodal solve with traction / pressure / velocity faces and two active contact walls (one
+// more wall out of reach), free or with one direction fixed; perturbs M, b and the faces' node
+// positions
+template <int D> void check_node_solve_bc() {
+    constexpr int NF = 5;  // traction, pressure, velocity, velocity, slip (skipped)
+    const int tags[NF] = {lmood::TAG_TRACTION, lmood::TAG_PRESSURE, lmood::TAG_VELOCITY, lmood::TAG_VELOCITY,
+                          lmood::TAG_SLIP};
+    for (int nd = D - 1; nd <= D; ++nd)
+        for (int t = 0; t < 3; ++t) {
+            double M[D * D], dM[D * D], b[D], db[D], lv[D], tv[6] = {0, 0, 0, 0, 0, 0}, A[D * D];
+            for (int i = 0; i < D * D; ++i) A[i] = U(-1, 1);
+            for (int i = 0; i < D; ++i)
+                for (int j = 0; j < D; ++j) {
+                    double s = (i == j ? 2.0 : 0.0);
+                    for (int k = 0; k < D; ++k) s += A[i * D + k] * A[j * D + k];
+                    M[i * D + j] = s;
+                }
+            for (int i = 0; i < D; ++i)
+                for (int j = i; j < D; ++j) dM[i * D + j] = dM[j * D + i] = U(-1, 1);
+            for (int a = 0; a < D; ++a) {
+                b[a] = U(-1, 1);
+                db[a] = U(-1, 1);
+                lv[a] = U(-1, 1);
+            }
+            const double th = U(0, 3.14);
+            tv[0] = cos(th);
+            tv[1] = sin(th);
+            if (D == 3) tv[5] = 1.0;
+            double xq[NF][D * D], dxq[NF][D * D], val[NF][D], xp[D];
+            for (int j = 0; j < NF; ++j) {
+                for (int i = 0; i < D * D; ++i) {
+                    xq[j][i] = U(-1, 1);
+                    dxq[j][i] = U(-1, 1);
+                }
+                for (int a = 0; a < D; ++a) val[j][a] = U(-1, 1);
+            }
+            for (int a = 0; a < D; ++a) xp[a] = U(-1, 1);
+            auto fc_of = [&](double (*x)[D * D]) {
+                return [x, &tags, &val](int j, int &tag, double *N, double *v) {
+                    tag = tags[j];
+                    bface_area<D>(x[j], N);
+                    for (int a = 0; a < D; ++a) v[a] = val[j][a];
+                };
+            };
+            // walls: normals against the velocity each meets, the node 0.5 eps from them (as
+            // many as leave the node a free direction), then one out of reach
+            const double eps = 0.1;
+            const int n_act = nd == D ? 2 : nd - 1;
+            double planes[3 * 2 * D], v[D];
+            int nw = 0;
+            for (int k = 0; k <= n_act; ++k) {
+                node_solve_bc<D>(M, b, nd, tv, true, NF, fc_of(xq), nw, planes, eps, xp, v);
+                double n[D], nn = 0.0;
+                for (int a = 0; a < D; ++a) {
+                    n[a] = -v[a] + 0.3 * U(-1, 1);
+                    nn += n[a] * n[a];
+                }
+                nn = sqrt(nn);
+                const double dist = k == n_act ? 3.0 * eps : 0.5 * eps;
+                for (int a = 0; a < D; ++a) {
+                    planes[2 * D * k + D + a] = n[a] / nn;
+                    planes[2 * D * k + a] = xp[a] - dist * n[a] / nn;
+                }
+                ++nw;
+            }
+            const double h = 1e-6;
+            double Mp[D * D], Mm[D * D], bp[D], bm[D], vp_[D], vm_[D], xqp[NF][D * D], xqm[NF][D * D];
+            for (int i = 0; i < D * D; ++i) {
+                Mp[i] = M[i] + h * dM[i];
+                Mm[i] = M[i] - h * dM[i];
+            }
+            for (int a = 0; a < D; ++a) {
+                bp[a] = b[a] + h * db[a];
+                bm[a] = b[a] - h * db[a];
+            }
+            for (int j = 0; j < NF; ++j)
+                for (int i = 0; i < D * D; ++i) {
+                    xqp[j][i] = xq[j][i] + h * dxq[j][i];
+                    xqm[j][i] = xq[j][i] - h * dxq[j][i];
+                }
+            node_solve_bc<D>(Mp, bp, nd, tv, true, NF, fc_of(xqp), nw, planes, eps, xp, vp_);
+            node_solve_bc<D>(Mm, bm, nd, tv, true, NF, fc_of(xqm), nw, planes, eps, xp, vm_);
+            double fd = 0.0;
+            for (int a = 0; a < D; ++a) fd += lv[a] * (vp_[a] - vm_[a]) / (2 * h);
+            double lb[D], lM[D * D] = {}, an = 0.0;
+            node_solve_bc_vjp<D>(M, b, nd, tv, true, NF, fc_of(xq), nw, planes, eps, xp, lv, lb, lM,
+                                 [&](int j, const double *lN) {
+                                     double lx[D * D] = {};
+                                     bface_area_vjp<D>(xq[j], lN, lx);
+                                     for (int i = 0; i < D * D; ++i) an += lx[i] * dxq[j][i];
+                                 });
+            for (int a = 0; a < D; ++a) an += lb[a] * db[a];
+            for (int i = 0; i < D * D; ++i) an += lM[i] * dM[i];
+            report(D == 2 ? "nodesolvebc2" : "nodesolvebc3", fd, an);
+        }
+}
+
 template <int D> void check_moments() {
     using Q = Sz<D>;
     constexpr int NM = Q::NMOM, NQ = Q::NQ;
@@ -401,6 +498,8 @@ int main() {
     check_faces_velgrad<3>();
     check_node_solve<2>();
     check_node_solve<3>();
+    check_node_solve_bc<2>();
+    check_node_solve_bc<3>();
     check_moments<2>();
     check_moments<3>();
     for (int ord = 1; ord <= 2; ++ord) {

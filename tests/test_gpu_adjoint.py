@@ -18,6 +18,7 @@ import pytest
 import oracle as O
 import paper_2104_02139_gb300 as L
 import workloads as W
+from adjoint_cases import bc_case
 
 pytestmark = pytest.mark.gpu
 
@@ -178,9 +179,18 @@ def test_adjoint_fd_3d_clamped_column():
     out, masks = _check_init_grads(pb, 4, {}, seed=15)
 
 
-def test_adjoint_fd_mid_run_state():
-    """A tape that starts after some steps: gradients of x, v_p, v, F (via lmood_set) and mu."""
-    pb, lam, rng = _setup(W.plain2d(n=10), 16)
+@pytest.mark.parametrize("name", ["piston2d", "rebound2d", "pressure_traction2d", "box3d_bc"])
+def test_adjoint_fd_boundary_faces(name):
+    """Traction, pressure and prescribed-velocity faces and contact walls, MOOD active, the
+    finite differences through the tape's replay (recorded masks and dt)."""
+    _check_init_grads(bc_case(name), 5, {}, seed=24, frozen=True)
+
+
+@pytest.mark.parametrize("name", ["plain2d", "piston2d", "rebound2d", "box3d_bc"])
+def test_adjoint_fd_mid_run_state(name):
+    """A tape that starts after some steps: gradients of x, v_p, v, F (via lmood_set) and mu;
+    with boundary faces the position direction moves them (their forces and multipliers)."""
+    pb, lam, rng = _setup(W.plain2d(n=10) if name == "plain2d" else bc_case(name), 16)
     prm = {"dt_fixed": _dt_fixed(pb), "mood": 0}
     pre, n = 3, 5
     st, tape, g = _grad(pb, n, prm, lam, pre=pre)

@@ -3,11 +3,14 @@
 1. The oracle's tangent build (the oracle's own source compiled with dual numbers, a CPU
    forward-mode derivative of the same frozen-mask map that shares nothing with the CUDA
    adjoint): for seeded adjoints lam of the final state (x, v_p, v, F) and seeded directions
-   delta of the initial v0, mu and F0, <grad, delta> from the tape's reverse pass must equal
-   <lam, J delta> from the tangent to 1e-6 relative, over 12 steps with MOOD active (first-order
-   cells in the masks) and the adaptive dt, in 2D (slip walls; the impact against a wall) and
-   3D (slip walls; the clamped column). The two runs' masks must be identical at every step
-   and their dt equal to 1e-12, so both differentiate the same map.
+   delta of the initial v0, mu, F0 and node positions (at fixed masses, through the initial
+   nodal solve), <grad, delta> from the tape's reverse pass must equal <lam, J delta> from the
+   tangent to 1e-6 relative, over 12 steps with MOOD active (first-order cells in the masks)
+   and the adaptive dt, in 2D (slip walls; the impact against a wall) and 3D (slip walls; the
+   clamped column), and with traction, pressure and prescribed-velocity faces and contact
+   walls (the piston, a block rebounding on a wall, a block under pressure and traction, a 3D
+   box with every kind of face). The two runs' masks must be identical at every step and their
+   dt equal to 1e-12, so both differentiate the same map.
 2. The adjoint configuration at full size (511,104 tetrahedra, 400 steps, a checkpoint every
    20 steps): the gradient of J = sum over cells with initial centroid z > 0.5 of m |v|^2 / 2
    along two random directions of v0 and two of mu (each cell's mu direction scaled by its mu,
@@ -22,6 +25,7 @@ import pytest
 import oracle as O
 import paper_2104_02139_gb300 as L
 import workloads as W
+from adjoint_cases import bc_case, smooth_positions_direction
 
 pytestmark = pytest.mark.gpu
 
@@ -45,9 +49,11 @@ def _case(name):
     elif name == "cube3d":
         pb = W.cube3d(n=4)
         pb.v *= 4.0
-    else:
+    elif name == "column3d":
         pb = W.column3d(nxy=3, nz=12)
         pb.v *= 8.0
+    else:
+        pb = bc_case(name)
     return pb
 
 
@@ -62,7 +68,8 @@ def _perturbed_material(pb, rng):
     return dataclasses.replace(pb, F=F, mu=mu)
 
 
-@pytest.mark.parametrize("name", ["plain2d", "impact2d", "cube3d", "column3d"])
+@pytest.mark.parametrize("name", ["plain2d", "impact2d", "cube3d", "column3d", "piston2d", "rebound2d",
+                                  "pressure_traction2d", "box3d_bc"])
 def test_adjoint_matches_the_oracle_tangent(name):
     rng = np.random.default_rng(31)
     pb = _perturbed_material(_case(name), rng)
@@ -79,7 +86,7 @@ def test_adjoint_matches_the_oracle_tangent(name):
         dts.append(twin.step().dt_used)
         masks.append(twin.get(L.FIELD_ORDER).astype(np.int8))
     dirs = {"v": rng.standard_normal((d, nc)), "mu": rng.standard_normal(nc) * pb.mu,
-            "F": rng.standard_normal((d * d, nc))}
+            "F": rng.standard_normal((d * d, nc)), "x": smooth_positions_direction(pb.mesh)}
     out = {}
     for k, delta in dirs.items():
         t = O.tangent(pb, n, **{"d" + k: delta})

@@ -121,11 +121,30 @@ def test_device_values_equal_host_values():
     assert np.array_equal(a.get(L.FIELD_X), b.get(L.FIELD_X))
 
 
-def test_tape_refuses_external_faces():
-    st = L.simulation(W.piston2d(n=8))
-    with pytest.raises(L.LmoodError) as e:
-        L.Tape(st, 2)
-    assert e.value.status == L.ERR_ARG
+def test_tape_backward_refuses_changed_boundary_data():
+    """the reverse pass uses the mesh's boundary data: a change after the recording (values,
+    tags or contact walls) makes lmood_tape_backward return LMOOD_ERR_STATE, before which it
+    runs"""
+    pb = W.piston2d(n=8)
+    for change in ("values", "tags", "contact"):
+        st = L.simulation(pb)
+        tape = L.Tape(st, 2)
+        g = tape.backward(lam_v=np.ones((2, pb.mesh.n_cells)))
+        assert np.isfinite(g["v"]).all()
+        if change == "values":
+            st.mesh.set_bc_values(pb.bcval * 2.0)
+        elif change == "tags":
+            tags = pb.mesh.btag.copy()
+            tags[tags == W.SLIP] = W.CLAMPED
+            st.mesh.set_btag(tags)
+        else:
+            st.mesh.set_contact(np.array([[-0.5, 0.0, 1.0, 0.0]]), 0.01)
+        with pytest.raises(L.LmoodError) as e:
+            tape.backward(lam_v=np.ones((2, pb.mesh.n_cells)))
+        assert e.value.status == L.ERR_STATE
+        tape.close()
+        st.close()
+        st.mesh.close()
 
 
 def test_contact_rebound_parity():

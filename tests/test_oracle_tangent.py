@@ -6,7 +6,11 @@ operations); its derivative parts equal central differences of the plain oracle'
 (step 1e-6, masks of the perturbed runs checked equal to the tangent run's, dt fixed so that
 the differenced map is the frozen-dt map the tangent differentiates) to 1e-6 relative, in 2D
 and 3D, with MOOD active and first-order cells in the mask, for directions of v0, mu and F0;
-and they are linear in the direction.
+and they are linear in the direction. With traction, pressure and prescribed-velocity faces
+and contact walls (the piston, the block rebounding on a wall, a block under pressure and
+traction, a 3D box with every kind of face) the same holds for directions of v0, mu, F0 and
+of the initial node positions at fixed masses (central differences of the tangent build's
+values from displaced starts), checked per output field.
 """
 import dataclasses
 
@@ -14,6 +18,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from adjoint_cases import bc_case, smooth_positions_direction
 
 FIELDS = ("x", "vp", "v", "F")
 
@@ -103,3 +108,54 @@ def test_tangent_is_linear_in_the_direction(orc):
     t0 = orc.tangent(pb, 4)
     for k in FIELDS:
         assert not np.any(t0["d" + k]), k
+
+
+@pytest.mark.parametrize("name", ["piston2d", "rebound2d", "pressure_traction2d", "box3d_bc"])
+def test_tangent_with_boundary_faces_against_central_differences(orc, name):
+    """traction, pressure and prescribed-velocity faces and contact walls (their multiplier
+    steps differentiated with the contact set frozen), and a direction of the initial node
+    positions at fixed masses (central differences of the tangent build's values from
+    displaced starts)"""
+    rng = np.random.default_rng(17)
+    pb = bc_case(name)
+    d, nc, npn = pb.mesh.dim, pb.mesh.n_cells, pb.mesh.n_nodes
+    pb = dataclasses.replace(pb, mu=np.asarray(pb.mu, dtype=float) * (1.0 + 0.1 * rng.random(nc)),
+                             F=np.tile(np.eye(d).ravel()[:, None], (1, nc)))
+    n = 5
+    prm = {"dt_fixed": 0.5 * orc.Oracle(pb).dt}
+    lam = {"x": rng.standard_normal((d, npn)), "vp": rng.standard_normal((d, npn)),
+           "v": rng.standard_normal((d, nc)), "F": rng.standard_normal((d * d, nc))}
+    dirs = {"v": rng.standard_normal((d, nc)), "mu": rng.standard_normal(nc) * pb.mu,
+            "F": rng.standard_normal((d * d, nc)), "x": smooth_positions_direction(pb.mesh)}
+    h = 1e-5  # (these small runs are weakly sensitive to some directions: a larger step keeps rounding small)
+    for name_dir, delta in dirs.items():
+        t = orc.tangent(pb, n, **{"d" + name_dir: delta}, **prm)
+        ad = {k: float((t["d" + k] * lam[k]).sum()) for k in FIELDS}
+        runs = []
+        for sgn in (1.0, -1.0):
+            if name_dir == "x":
+                r = orc.tangent(pb, n, dx=delta, x_shift=sgn * h, **prm)
+                st, masks = {k: r[k] for k in FIELDS}, list(r["masks"])
+            else:
+                base = {"v": pb.v, "mu": pb.mu, "F": pb.F}[name_dir]
+                st, masks = _plain(orc, dataclasses.replace(pb, **{name_dir: base + sgn * h * delta}), n, **prm)
+            for s in range(n):
+                assert np.array_equal(masks[s], t["masks"][s]), f"mask changed under the perturbation at step {s}"
+            runs.append(st)
+        # per output field (their sum cancels in part, and the rounding of the differenced runs
+        # is relative to the largest of them)
+        fd = {k: float(((runs[0][k] - runs[1][k]) * lam[k]).sum()) / (2 * h) for k in FIELDS}
+        scale = max(abs(v) for v in ad.values())
+        for k in FIELDS:
+            assert abs(ad[k] - fd[k]) <= 1e-6 * scale, (name, name_dir, k, ad[k], fd[k])
+
+
+def test_tangent_position_direction_at_rest_shift_is_the_oracle(orc):
+    """x_shift = 0 with a position direction leaves the values those of the plain oracle (the
+    initial nodal solve done again at the same positions gives the same v_p^0)"""
+    pb = bc_case("piston2d")
+    rng = np.random.default_rng(20)
+    t = orc.tangent(pb, 4, dx=rng.standard_normal((pb.mesh.dim, pb.mesh.n_nodes)))
+    ref, _ = _plain(orc, pb, 4)
+    for k in FIELDS:
+        assert np.array_equal(t[k], ref[k]), k
