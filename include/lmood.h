@@ -330,8 +330,9 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  * (x, v_p per node; v, F per cell) and of the per-cell mu; the adjoint is the exact transpose
  * of its linearisation, written by hand kernel by kernel (no atomics, deterministic).
  * Only the two-level cascade (P1 -> P0) is differentiated: a recorded step that used the
- * limited level returns LMOOD_ERR_ARG, and so do a shear energy other than the neo-Hookean one
- * (a = -1) and the stiffened gas. Boundary faces of every kind are differentiated: slip and
+ * limited level returns LMOOD_ERR_ARG, and so does the stiffened gas (its pressure depends on
+ * the internal energy); the neo-Hookean law and every a of the shear energy family (Eq.
+ * familiy_energies) are differentiated. Boundary faces of every kind are differentiated: slip and
  * clamped nodes, traction and pressure faces (their forces depend on the faces' area vectors,
  * hence on the positions), prescribed-velocity faces and contact walls (their multiplier
  * steps, with the set of walls a node is in contact with, and whether each multiplier step

@@ -350,7 +350,7 @@ def tangent(problem, n_steps: int, dv=None, dmu=None, dF=None, dx=None, x_shift:
     directions of x), for central differences along dx."""
     m = problem.mesh
     d, nc, npn = m.dim, m.n_cells, m.n_nodes
-    prm = params or default_params(problem.cfl, **kw)
+    prm = params or default_params(problem.cfl, **{"shear_a": getattr(problem, "shear_a", -1.0), **kw})
     keep = []
 
     def arr(a, dtype=np.float64):

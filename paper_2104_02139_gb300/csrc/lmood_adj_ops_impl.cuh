@@ -15,17 +15,22 @@ template <int D> void adj_nodes(const Geo &g, const Fld &f, const AdjBuf &a, int
     k_adj_nodes<D, false><<<adj_blocks(g.Np, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, f, a, init_mode);
     if (a.bf) k_adj_nodes<D, true><<<adj_blocks(g.Np, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, f, a, init_mode);
 }
-template <int D>
-void adj_predict(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, int force_p0, cudaStream_t s) {
+template <int D, bool FAM>
+void adj_predict_m(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, int force_p0, cudaStream_t s) {
     if (!force_p0) {
         const int nc = (D + 1) * g.N;
-        k_adj_pred_fw<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
-        k_adj_pred_c2<D><<<adj_blocks(nc, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
-        k_adj_pred_c1<D><<<adj_blocks(nc, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+        k_adj_pred_fw<D, FAM><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+        k_adj_pred_c2<D, FAM><<<adj_blocks(nc, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+        k_adj_pred_c1<D, FAM><<<adj_blocks(nc, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
         k_adj_pred_fin<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
         // (the second-order cells' corner-matrix and geometry part runs in k_adj_cells)
     }
-    k_adj_predict<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a, force_p0);
+    k_adj_predict<D, FAM><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a, force_p0);
+}
+template <int D>
+void adj_predict(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, int force_p0, cudaStream_t s) {
+    if (p.shear_a == -1.0) adj_predict_m<D, false>(g, f, p, a, force_p0, s);
+    else adj_predict_m<D, true>(g, f, p, a, force_p0, s);
 }
 template <int D> void adj_momsum(const Geo &g, const Fld &f, const AdjBuf &a, cudaStream_t s) {
     (void)f;

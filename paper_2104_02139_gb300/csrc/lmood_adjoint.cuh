@@ -166,6 +166,128 @@ LMOOD_HD void stress_vjp(const double *F, double mu, double kap, const double *l
         }
 }
 
+// ---------------------------------------------------------------------------------------
+// Stress of the shear energy family (Eq. familiy_energies with the volumetric part of Eq.
+// EOS_neoHook; a = -1 is the neo-Hookean law above): with Bbar = J^{-2/3} F F^t (plane strain
+// in 2D), I1 = tr Bbar, I2 = (I1^2 - tr Bbar^2) / 2,
+//   T = -p I + (mu / J) dev(c1 Bbar - c2 Bbar^2),  c1 = -a + (1 + a) I1 I2 / 3,
+//   c2 = (1 + a) I2 / 3,  p = -(kap/2)(J - 1 + log J / J),
+// and its product lamT -> (lamF, lam_mu, lam_kappa). Worked in 3 x 3 (2D: F33 = 1, the
+// in-plane block of T and of lamT).
+// ---------------------------------------------------------------------------------------
+struct FamStress {
+    double J, invJ, lJ, Jm23, B[9], B2[9], I1, I2, c1, c2, X[9], trX, p;
+};
+
+template <int D> LMOOD_HD void family_parts(const double *F, double mu, double kap, double a, FamStress &q) {
+    double F3[9];
+    for (int i = 0; i < 9; ++i) F3[i] = 0.0;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) F3[i * 3 + j] = F[i * D + j];
+    if (D == 2) F3[8] = 1.0;
+    q.J = det<3>(F3);
+    const double rc = adj_rcbrt(q.J);
+    q.Jm23 = rc * rc;
+    q.invJ = q.Jm23 * rc;
+    q.lJ = adj_log(q.J);
+    double C[9];
+    mmt<3>(F3, F3, C);
+    for (int i = 0; i < 9; ++i) q.B[i] = q.Jm23 * C[i];
+    mm<3>(q.B, q.B, q.B2);
+    q.I1 = q.B[0] + q.B[4] + q.B[8];
+    q.I2 = 0.5 * (q.I1 * q.I1 - (q.B2[0] + q.B2[4] + q.B2[8]));
+    q.c1 = -a + (1.0 + a) * q.I1 * q.I2 * (1.0 / 3.0);
+    q.c2 = (1.0 + a) * q.I2 * (1.0 / 3.0);
+    for (int i = 0; i < 9; ++i) q.X[i] = q.c1 * q.B[i] - q.c2 * q.B2[i];
+    q.trX = q.X[0] + q.X[4] + q.X[8];
+    q.p = -0.5 * kap * (q.J - 1.0 + q.lJ * q.invJ);
+    (void)mu;
+}
+
+template <int D> LMOOD_HD void stress_family_fw(const double *F, double mu, double kap, double a, double *T) {
+    FamStress q;
+    family_parts<D>(F, mu, kap, a, q);
+    const double s = mu * q.invJ;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j)
+            T[i * D + j] = (i == j ? -q.p - s * q.trX * (1.0 / 3.0) : 0.0) + s * q.X[i * 3 + j];
+}
+
+template <int D>
+LMOOD_HD void stress_family_vjp(const double *F, double mu, double kap, double a, const double *lT, double *lF,
+                                double &lmu, double &lkap, double *T_out = nullptr) {
+    FamStress q;
+    family_parts<D>(F, mu, kap, a, q);
+    const double s = mu * q.invJ;
+    if (T_out)
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j)
+                T_out[i * D + j] = (i == j ? -q.p - s * q.trX * (1.0 / 3.0) : 0.0) + s * q.X[i * 3 + j];
+    // lamT in 3 x 3 (zero outside the in-plane block in 2D); Y = dev(lamT)
+    double Y[9], tr = 0.0;
+    for (int i = 0; i < 9; ++i) Y[i] = 0.0;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) Y[i * 3 + j] = lT[i * D + j];
+    for (int i = 0; i < 3; ++i) tr += Y[i * 4];
+    const double lp = -tr;  // T = -p I + ...
+    for (int i = 0; i < 3; ++i) Y[i * 4] -= tr * (1.0 / 3.0);
+    double YX = 0.0;
+    for (int i = 0; i < 9; ++i) YX += Y[i] * q.X[i];
+    // s dev(X): lX = s Y, ls = <Y, X>, s = mu / J
+    lmu += YX * q.invJ;
+    double lJv = -s * YX * q.invJ;
+    // p = -(kap/2)(J - 1 + log J / J)
+    lkap += lp * (-0.5) * (q.J - 1.0 + q.lJ * q.invJ);
+    lJv += lp * (-0.5 * kap) * (1.0 + (1.0 - q.lJ) * q.invJ * q.invJ);
+    // X = c1 B - c2 B^2 (B symmetric)
+    double lc1 = 0.0, lc2 = 0.0, lB[9], lXB[9], BlX[9];
+    for (int i = 0; i < 9; ++i) {
+        lc1 += s * Y[i] * q.B[i];
+        lc2 -= s * Y[i] * q.B2[i];
+    }
+    double lX[9];
+    for (int i = 0; i < 9; ++i) lX[i] = s * Y[i];
+    mm<3>(lX, q.B, lXB);
+    mm<3>(q.B, lX, BlX);
+    for (int i = 0; i < 9; ++i) lB[i] = q.c1 * lX[i] - q.c2 * (lXB[i] + BlX[i]);
+    // c1 = -a + (1+a) I1 I2 / 3, c2 = (1+a) I2 / 3; I2 = (I1^2 - tr B^2) / 2; I1 = tr B
+    const double ap = (1.0 + a) * (1.0 / 3.0);
+    const double lI2 = lc1 * ap * q.I1 + lc2 * ap;
+    const double lI1 = lc1 * ap * q.I2 + lI2 * q.I1;
+    for (int i = 0; i < 9; ++i) lB[i] -= lI2 * q.B[i];
+    for (int i = 0; i < 3; ++i) lB[i * 4] += lI1;
+    // B = J^{-2/3} F F^t: lC = J^{-2/3} lB, lJ -= (2 / (3 J)) <lB, B>
+    double lBB = 0.0;
+    for (int i = 0; i < 9; ++i) lBB += lB[i] * q.B[i];
+    lJv -= (2.0 / 3.0) * q.invJ * lBB;
+    // lF3 = J^{-2/3} (lB + lB^t) F3 + lJ cof(F3); the in-plane block in 2D
+    double F3[9], Cf[9];
+    for (int i = 0; i < 9; ++i) F3[i] = 0.0;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) F3[i * 3 + j] = F[i * D + j];
+    if (D == 2) F3[8] = 1.0;
+    cofactor<3>(F3, Cf);
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            double t = 0.0;
+            for (int k = 0; k < 3; ++k) t += (lB[i * 3 + k] + lB[k * 3 + i]) * F3[k * 3 + j];
+            lF[i * D + j] += q.Jm23 * t + lJv * Cf[i * 3 + j];
+        }
+}
+
+// the material's stress and product: the neo-Hookean law (a = -1) or the family
+template <int D> LMOOD_HD void stress_m(const double *F, double mu, double kap, double a, double *T) {
+    if (a == -1.0) stress<D>(F, mu, kap, T);
+    else stress_family_fw<D>(F, mu, kap, a, T);
+}
+
+template <int D>
+LMOOD_HD void stress_m_vjp(const double *F, double mu, double kap, double a, const double *lT, double *lF, double &lmu,
+                           double &lkap, double *T_out = nullptr) {
+    if (a == -1.0) stress_vjp<D>(F, mu, kap, lT, lF, lmu, lkap, T_out);
+    else stress_family_vjp<D>(F, mu, kap, a, lT, lF, lmu, lkap, T_out);
+}
+
 // impedance z = sqrt(rho (K + 4 mu / (3 J))), K = (kap/2)(J + (1 - log J)/J)
 template <int D> LMOOD_HD double impedance(const double *F, double rho, double mu, double kap) {
     const double J = det<D>(F), invJ = 1.0 / J;
@@ -591,7 +713,7 @@ template <int D> struct Mom {
 
 template <int D>
 LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, const double *Fc, double z, double mu,
-                         double kap, double im, double dt, int ord, double *Mo, double *Ro) {
+                         double kap, double im, double dt, int ord, double *Mo, double *Ro, double sa = -1.0) {
     using Q = Sz<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ;
     double V, N[NV * D], xcc[D], W[NV][NS];
@@ -621,7 +743,7 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
     auto Mfull = [&](int k, int a, int b) { return Mo[k * NS + sym<D>(a, b)]; };
     if (ord == 1) {
         double T[DD];
-        stress<D>(Fc, mu, kap, T);
+        stress_m<D>(Fc, mu, kap, sa, T);
         for (int k = 0; k < NV; ++k)
             for (int a = 0; a < D; ++a) {
                 double s = 0.0;
@@ -670,7 +792,7 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
             for (int a = 0; a < D; ++a) s += gs[D + q][a] * (xs[k * D + a] - xcc[a]);
             Fh[q] = s;
         }
-        stress<D>(Fh, mu, kap, T);
+        stress_m<D>(Fh, mu, kap, sa, T);
         for (int i = 0; i < D; ++i)
             for (int b = 0; b < D; ++b) dv[i] += T[i * D + b] * N[k * D + b];
     }
@@ -690,7 +812,7 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
             for (int a = 0; a < D; ++a) s += gs[D + q][a] * (xs[k * D + a] - xcc[a]);
             Fs[q] = s + 0.5 * dt * dFdt[q];
         }
-        stress<D>(Fs, mu, kap, T);
+        stress_m<D>(Fs, mu, kap, sa, T);
         for (int a = 0; a < D; ++a) {
             double s = 0.0;
             for (int b = 0; b < D; ++b) s += Mfull(k, a, b) * vst[b] + T[a * D + b] * N[k * D + b] * (1.0 / D);
@@ -747,7 +869,8 @@ LMOOD_HD double adj_rsqrt(double x) {
 // D+1 nodes gathered into one): the same values up to rounding.
 template <int D>
 LMOOD_HD void predict_fw_rec(const double *xs, const Mom<D> &mom, const double *vc, const double *Fc, double z,
-                             double mu, double kap, double im, double dt, double *pf, double *pk, long kstride) {
+                             double mu, double kap, double im, double dt, double *pf, double *pk, long kstride,
+                             double sa = -1.0) {
     using Q = Sz<D>;
     using P = PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ;
@@ -871,7 +994,7 @@ LMOOD_HD void predict_fw_rec(const double *xs, const Mom<D> &mom, const double *
             Fh[q] = s;
             rk[P::K_FH + q] = s;
         }
-        stress<D>(Fh, mu, kap, T);
+        stress_m<D>(Fh, mu, kap, sa, T);
         LMOOD_UNROLL
         for (int i = 0; i < D; ++i)
             LMOOD_UNROLL
@@ -903,7 +1026,7 @@ LMOOD_HD void predict_fw_rec(const double *xs, const Mom<D> &mom, const double *
 // from lR_k [D]; adds lR_k (x) v*_k to lM_k [NS] and writes q2 [Q2_LEN]
 template <int D>
 LMOOD_HD void predict_corner2_vjp(const double *pf, const double *rk, int k, double mu, double kap, double dt,
-                                  const double *lR_k, double *lM_k, double *q2) {
+                                  const double *lR_k, double *lM_k, double *q2, double sa = -1.0) {
     using P = PredRec<D>;
     constexpr int DD = D * D;
     const double *N = pf + P::F_N + k * D, *vst = rk + P::K_VST;
@@ -917,7 +1040,7 @@ LMOOD_HD void predict_corner2_vjp(const double *pf, const double *rk, int k, dou
             lT[a * D + b] += l * N[b] * (1.0 / D);
         }
     }
-    stress_vjp<D>(Fs, mu, kap, lT, lFs, lmu, lkap, T);
+    stress_m_vjp<D>(Fs, mu, kap, sa, lT, lFs, lmu, lkap, T);
     for (int b = 0; b < D; ++b) {
         double s = 0.0;
         for (int a = 0; a < D; ++a) s += lR_k[a] * T[a * D + b];
@@ -933,14 +1056,14 @@ LMOOD_HD void predict_corner2_vjp(const double *pf, const double *rk, int k, dou
 // writes q1 [Q1_LEN]
 template <int D>
 LMOOD_HD void predict_corner1_vjp(const double *pf, const double *rk, int k, double mu, double kap,
-                                  const double *lacc, double *q1) {
+                                  const double *lacc, double *q1, double sa = -1.0) {
     using P = PredRec<D>;
     constexpr int DD = D * D;
     const double *N = pf + P::F_N + k * D;
     double lT[DD], lF[DD] = {}, T[DD], lmu = 0.0, lkap = 0.0;
     for (int i = 0; i < D; ++i)
         for (int b = 0; b < D; ++b) lT[i * D + b] = lacc[i] * N[b];
-    stress_vjp<D>(rk + P::K_FH, mu, kap, lT, lF, lmu, lkap, T);
+    stress_m_vjp<D>(rk + P::K_FH, mu, kap, sa, lT, lF, lmu, lkap, T);
     for (int b = 0; b < D; ++b) {
         double s = 0.0;
         for (int i = 0; i < D; ++i) s += lacc[i] * T[i * D + b];
@@ -1180,7 +1303,7 @@ LMOOD_HD void predict_tail_p1_vjp(const double *xs, double z, const double *pf, 
 template <int D, class MO>
 LMOOD_HD void predict_p0_vjp(const double *xs, const double *vc, const double *Fc, double z, double mu, double kap,
                              double *lM, const double *lR, double *lxs, MO &&mout, double *lvc, double *lFc,
-                             double &lz, double &lmu, double &lkap);
+                             double &lz, double &lmu, double &lkap, double sa = -1.0);
 
 // Product of predict_fw: (lM [NV][NS], lR [NV][D]) -> accumulates lxs [NV][D], lvc [D],
 // lFc [DD], lz, lmu, lkap, and stores the adjoints of the node moments through
@@ -1188,7 +1311,8 @@ LMOOD_HD void predict_p0_vjp(const double *xs, const double *vc, const double *F
 template <int D, class MO>
 LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc, const double *Fc, double z, double mu,
                           double kap, double im, double dt, int ord, const double *lM_in, const double *lR, double *lxs,
-                          MO &&mout, double *lvc, double *lFc, double &lz, double &lmu, double &lkap) {
+                          MO &&mout, double *lvc, double *lFc, double &lz, double &lmu, double &lkap,
+                          double sa = -1.0) {
     using Q = Sz<D>;
     using P = PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NM = Q::NMOM;
@@ -1196,16 +1320,16 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
     for (int i = 0; i < NV * NS; ++i) lM[i] = lM_in[i];
     if (ord != 1) {
         double pf[P::F_LEN], pk[NV * P::K_LEN], q2[NV][P::Q2_LEN], q1[NV][P::Q1_LEN];
-        predict_fw_rec<D>(xs, mom, vc, Fc, z, mu, kap, im, dt, pf, pk, P::K_LEN);
+        predict_fw_rec<D>(xs, mom, vc, Fc, z, mu, kap, im, dt, pf, pk, P::K_LEN, sa);
         double ldv[D] = {};
         for (int k = 0; k < NV; ++k) {
-            predict_corner2_vjp<D>(pf, pk + k * P::K_LEN, k, mu, kap, dt, lR + k * D, lM + k * NS, q2[k]);
+            predict_corner2_vjp<D>(pf, pk + k * P::K_LEN, k, mu, kap, dt, lR + k * D, lM + k * NS, q2[k], sa);
             for (int a = 0; a < D; ++a) ldv[a] += q2[k][P::Q2_LV + a];
         }
         const double hv = -0.5 * dt * im * (1.0 / D);
         double lacc[D];
         for (int a = 0; a < D; ++a) lacc[a] = hv * ldv[a];
-        for (int k = 0; k < NV; ++k) predict_corner1_vjp<D>(pf, pk + k * P::K_LEN, k, mu, kap, lacc, q1[k]);
+        for (int k = 0; k < NV; ++k) predict_corner1_vjp<D>(pf, pk + k * P::K_LEN, k, mu, kap, lacc, q1[k], sa);
         for (int k = 0; k < NV; ++k) {
             lmu += q2[k][P::Q2_MU] + q1[k][P::Q1_MU];
             lkap += q2[k][P::Q2_KAP] + q1[k][P::Q1_KAP];
@@ -1218,7 +1342,7 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
                                lz);
         return;
     }
-    predict_p0_vjp<D>(xs, vc, Fc, z, mu, kap, lM, lR, lxs, mout, lvc, lFc, lz, lmu, lkap);
+    predict_p0_vjp<D>(xs, vc, Fc, z, mu, kap, lM, lR, lxs, mout, lvc, lFc, lz, lmu, lkap, sa);
 }
 
 // the product for a first-order cell: R_k = M_k v_c + (1/D) T(F_c) N_k (lM [NV][NS] is
@@ -1226,7 +1350,7 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
 template <int D, class MO>
 LMOOD_HD void predict_p0_vjp(const double *xs, const double *vc, const double *Fc, double z, double mu, double kap,
                              double *lM, const double *lR, double *lxs, MO &&mout, double *lvc, double *lFc,
-                             double &lz, double &lmu, double &lkap) {
+                             double &lz, double &lmu, double &lkap, double sa) {
     using Q = Sz<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NM = Q::NMOM;
     double V, N[NV * D], inu[NV], lN[NV * D] = {}, lxcc[D] = {};
@@ -1260,7 +1384,7 @@ LMOOD_HD void predict_p0_vjp(const double *xs, const double *vc, const double *F
                 lT[a * D + b] += l * N[k * D + b] * (1.0 / D);
             }
         }
-    stress_vjp<D>(Fc, mu, kap, lT, lF, lmu, lkap, T);
+    stress_m_vjp<D>(Fc, mu, kap, sa, lT, lF, lmu, lkap, T);
     for (int k = 0; k < NV; ++k)
         for (int a = 0; a < D; ++a)
             for (int b = 0; b < D; ++b) lN[k * D + b] += lR[k * D + a] * T[a * D + b] * (1.0 / D);

@@ -189,7 +189,9 @@ template <int D> __device__ __forceinline__ bool second_order(const Fld &f, int 
     return !force_p0 && f.order[c] != 1;
 }
 
-template <int D> __global__ void __launch_bounds__(128) k_adj_pred_fw(Geo g, Fld f, Prm prm, AdjBuf a) {
+// FAM: the shear energy family (a = prm.shear_a); else the neo-Hookean law, whose instance
+// compiles no family code
+template <int D, bool FAM> __global__ void __launch_bounds__(128) k_adj_pred_fw(Geo g, Fld f, Prm prm, AdjBuf a) {
     using Q = adj::Sz<D>;
     using P = adj::PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NX = NV * D;
@@ -208,10 +210,10 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_pred_fw(Geo g, Fld
     for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
     const double mu = f.mu[c], kap = kappa_of(prm, mu), dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
     adj::predict_fw_rec<D>(xs, mom, vc, Fc, f.z[c], mu, kap, f.im[c], dt, a.pf + (size_t)c * P::F_LEN,
-                           a.pk + (size_t)c * P::K_LEN, (long)N * P::K_LEN);
+                           a.pk + (size_t)c * P::K_LEN, (long)N * P::K_LEN, FAM ? prm.shear_a : -1.0);
 }
 
-template <int D> __global__ void __launch_bounds__(128) k_adj_pred_c2(Geo g, Fld f, Prm prm, AdjBuf a) {
+template <int D, bool FAM> __global__ void __launch_bounds__(128) k_adj_pred_c2(Geo g, Fld f, Prm prm, AdjBuf a) {
     using R = AdjRec<D>;
     using P = adj::PredRec<D>;
     constexpr int NS = R::NS;
@@ -226,11 +228,11 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_pred_c2(Geo g, Fld
     for (int b = 0; b < D; ++b) lR[b] = cr[R::CR_R + b];
     for (int s2 = 0; s2 < NS; ++s2) lM[s2] = cr[R::CR_M + s2];
     adj::predict_corner2_vjp<D>(a.pf + (size_t)c * P::F_LEN, a.pk + (size_t)cid * P::K_LEN, k, mu, kap, dt, lR, lM,
-                                a.q2 + (size_t)cid * P::Q2_LEN);
+                                a.q2 + (size_t)cid * P::Q2_LEN, FAM ? prm.shear_a : -1.0);
     for (int s2 = 0; s2 < NS; ++s2) cr[R::CR_M + s2] = lM[s2];
 }
 
-template <int D> __global__ void __launch_bounds__(128) k_adj_pred_c1(Geo g, Fld f, Prm prm, AdjBuf a) {
+template <int D, bool FAM> __global__ void __launch_bounds__(128) k_adj_pred_c1(Geo g, Fld f, Prm prm, AdjBuf a) {
     using P = adj::PredRec<D>;
     const int N = g.N;
     const int cid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -245,7 +247,7 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_pred_c1(Geo g, Fld
     const double hv = -0.5 * dt * f.im[c] * (1.0 / D);
     for (int b = 0; b < D; ++b) lacc[b] *= hv;
     adj::predict_corner1_vjp<D>(a.pf + (size_t)c * P::F_LEN, a.pk + (size_t)cid * P::K_LEN, k, mu, kap, lacc,
-                                a.q1 + (size_t)cid * P::Q1_LEN);
+                                a.q1 + (size_t)cid * P::Q1_LEN, FAM ? prm.shear_a : -1.0);
 }
 
 // node-moment adjoint writer of cell c: the parts equal at every corner (lT, lS2) into the
@@ -324,7 +326,7 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_pred_fin(Geo g, Fl
 }
 
 // the whole product of a first-order cell (force_p0: every cell, the t^0 packets)
-template <int D>
+template <int D, bool FAM>
 __global__ void __launch_bounds__(128) k_adj_predict(Geo g, Fld f, Prm prm, AdjBuf a, int force_p0) {
     using Q = adj::Sz<D>;
     using R = AdjRec<D>;
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(128) k_adj_predict(Geo g, Fld f, Prm prm, AdjB
     const double mu = f.mu[c], kap = kappa_of(prm, mu);
     double lxs[NX] = {}, lvc[D] = {}, lF[DD] = {}, lz = 0.0, lmu = 0.0, lkap = 0.0;
     adj::predict_p0_vjp<D>(xs, vc, Fc, f.z[c], mu, kap, lM, lR, lxs, MomOut<D>{a.cp, a.cc + (size_t)c * R::CC, N, c},
-                           lvc, lF, lz, lmu, lkap);
+                           lvc, lF, lz, lmu, lkap, FAM ? prm.shear_a : -1.0);
     adj_predict_out<D>(a, prm, N, c, lxs, lvc, lF, lz, lmu, lkap);
 }
 

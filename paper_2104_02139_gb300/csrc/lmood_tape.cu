@@ -219,9 +219,9 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     if (n_steps < 1 || checkpoint_every < 0)
         return fail(LMOOD_ERR_ARG, "lmood_tape_record: n_steps must be >= 1 and checkpoint_every >= 0");
     lmood_mesh M = s->M;
-    if (s->mat.shear_a != -1.0 || s->mat.eos != 0)
-        return fail(LMOOD_ERR_ARG, "lmood_tape_record: the adjoint covers the neo-Hookean material (a = -1, "
-                                   "volumetric law of Eq. EOS_neoHook) only");
+    if (s->mat.eos != 0)
+        return fail(LMOOD_ERR_ARG, "lmood_tape_record: the adjoint covers the volumetric law of Eq. EOS_neoHook "
+                                   "(any a of the shear energy family) only, not the stiffened gas");
     const int D = M->dim, NV = D + 1, NS = D * (D + 1) / 2, DD = D * D;
     const int64_t N = M->nc, Np = M->np, NC = NV * N;
     const int nmom = M->ops->nmom;

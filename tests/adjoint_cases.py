@@ -1,5 +1,8 @@
 """Small problems for the adjoint's reference checks (CPU tangent pins and GPU tests): one
-per kind of boundary face, and a smooth direction of the node positions."""
+per kind of boundary face, the shear energy family, and a smooth direction of the node
+positions."""
+import dataclasses
+
 import numpy as np
 
 import workloads as W
@@ -31,3 +34,13 @@ def smooth_positions_direction(m):
     cells and moves cells near an RDMP threshold across it)"""
     x = m.x
     return 0.1 * np.stack([np.sin(np.pi * (x[0] + 0.3 * a)) * np.cos(np.pi * x[1] + 0.2 * a) for a in range(m.dim)])
+
+
+def family_case(name):
+    """the shear energy family of Eq. familiy_energies with a != -1: a = 0 on a slip cube,
+    a = 0.5 on the impact"""
+    if name == "cube3d_a0":
+        pb = W.cube3d(n=4)
+        pb.v *= 4.0
+        return dataclasses.replace(pb, shear_a=0.0)
+    return dataclasses.replace(W.impact2d(n=20), shear_a=0.5)

@@ -60,6 +60,51 @@ template <int D> void check_stress() {
     }
 }
 
+// the shear energy family (a != -1), and a = -1 through the dispatch against the neo-Hookean
+// routine itself
+template <int D> void check_stress_family() {
+    constexpr int DD = D * D;
+    const double as[4] = {0.0, 0.5, -0.5, 1.0};
+    for (int t = 0; t < 4; ++t) {
+        const double a = as[t];
+        double F[DD], lT[DD], dF[DD], mu = U(0.5, 2), kap = U(1, 4), dmu = U(-1, 1), dk = U(-1, 1);
+        randF<D>(F, 0.2);
+        for (int i = 0; i < DD; ++i) {
+            lT[i] = U(-1, 1);
+            dF[i] = U(-1, 1);
+        }
+        const double h = 1e-6;
+        double Fp[DD], Fm[DD], Tp[DD], Tm[DD];
+        for (int i = 0; i < DD; ++i) {
+            Fp[i] = F[i] + h * dF[i];
+            Fm[i] = F[i] - h * dF[i];
+        }
+        stress_m<D>(Fp, mu + h * dmu, kap + h * dk, a, Tp);
+        stress_m<D>(Fm, mu - h * dmu, kap - h * dk, a, Tm);
+        double fd = 0.0;
+        for (int i = 0; i < DD; ++i) fd += lT[i] * (Tp[i] - Tm[i]) / (2 * h);
+        double lF[DD] = {}, lmu = 0, lkap = 0, T[DD], T2[DD];
+        stress_m_vjp<D>(F, mu, kap, a, lT, lF, lmu, lkap, T);
+        stress_m<D>(F, mu, kap, a, T2);
+        double an = lmu * dmu + lkap * dk, dT = 0.0;
+        for (int i = 0; i < DD; ++i) {
+            an += lF[i] * dF[i];
+            dT = fmax(dT, fabs(T[i] - T2[i]));
+        }
+        report(D == 2 ? "stressfam2" : "stressfam3", fd, an);
+        report(D == 2 ? "stressfamT2" : "stressfamT3", 1.0, 1.0 + dT);  // T_out equals the forward
+    }
+    // the family's formula at a = -1 (not the dispatch) is the neo-Hookean stress
+    for (int t = 0; t < 2; ++t) {
+        double F[DD], T1[DD], T2[DD], mu = U(0.5, 2), kap = U(1, 4), dT = 0.0;
+        randF<D>(F, 0.2);
+        stress<D>(F, mu, kap, T1);
+        stress_family_fw<D>(F, mu, kap, -1.0, T2);
+        for (int i = 0; i < DD; ++i) dT = fmax(dT, fabs(T1[i] - T2[i]));
+        report(D == 2 ? "stressfamNH2" : "stressfamNH3", 1.0, 1.0 + dT);
+    }
+}
+
 template <int D> void check_impedance() {
     constexpr int DD = D * D;
     for (int t = 0; t < 5; ++t) {
@@ -229,7 +274,7 @@ template <int D> struct Patch {
     }
 };
 
-template <int D> void check_predict(int ord) {
+template <int D> void check_predict(int ord, double sa = -1.0) {
     using Q = Sz<D>;
     constexpr int NV = D + 1, NS = Q::NS, DD = D * D, NM = Q::NMOM;
     for (int t = 0; t < 4; ++t) {
@@ -252,7 +297,7 @@ template <int D> void check_predict(int ord) {
             for (int a = 0; a < D; ++a) Q2.vc[a] += s * dvc[a];
             for (int q = 0; q < DD; ++q) Q2.Fc[q] += s * dF[q];
             predict_fw<D>(Q2.xs, Q2.acc(Q2.mom), Q2.vc, Q2.Fc, P.z + s * dz, P.mu + s * dmu, P.kap + s * dk, P.im, P.dt,
-                          ord, Mo, Ro);
+                          ord, Mo, Ro, sa);
         };
         double Mp[NV * NS], Rp[NV * D], Mm[NV * NS], Rm[NV * D];
         eval(h, Mp, Rp);
@@ -263,14 +308,15 @@ template <int D> void check_predict(int ord) {
         double lxs[NV * D] = {}, lmom[NV * NM] = {}, lvc[D] = {}, lF[DD] = {}, lz = 0, lmu = 0, lkap = 0;
         for (int i = 0; i < NV * NM; ++i) lmom[i] = 1e300;  // every entry must be stored exactly once
         predict_vjp<D>(P.xs, P.acc(P.mom), P.vc, P.Fc, P.z, P.mu, P.kap, P.im, P.dt, ord, lM, lR, lxs,
-                       [&](int k, int j, double v) { lmom[k * NM + j] = v; }, lvc, lF, lz, lmu, lkap);
+                       [&](int k, int j, double v) { lmom[k * NM + j] = v; }, lvc, lF, lz, lmu, lkap, sa);
         double an = lz * dz + lmu * dmu + lkap * dk;
         for (int i = 0; i < NV * D; ++i) an += lxs[i] * dxs[i];
         for (int i = 0; i < NV * NM; ++i) an += lmom[i] * dmom[i];
         for (int a = 0; a < D; ++a) an += lvc[a] * dvc[a];
         for (int q = 0; q < DD; ++q) an += lF[q] * dF[q];
         char name[32];
-        std::snprintf(name, sizeof name, "predict%d_ord%d", D, ord);
+        if (sa == -1.0) std::snprintf(name, sizeof name, "predict%d_ord%d", D, ord);
+        else std::snprintf(name, sizeof name, "predictfam%d_ord%d", D, ord);
         report(name, fd, an);
     }
 }
@@ -492,6 +538,8 @@ template <int D> void check_moments() {
 int main() {
     check_stress<2>();
     check_stress<3>();
+    check_stress_family<2>();
+    check_stress_family<3>();
     check_impedance<2>();
     check_impedance<3>();
     check_faces_velgrad<2>();
@@ -505,6 +553,8 @@ int main() {
     for (int ord = 1; ord <= 2; ++ord) {
         check_predict<2>(ord);
         check_predict<3>(ord);
+        check_predict<2>(ord, 0.0);
+        check_predict<3>(ord, 0.5);
         check_update<2>(ord);
         check_update<3>(ord);
     }

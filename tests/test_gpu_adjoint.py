@@ -18,7 +18,7 @@ import pytest
 import oracle as O
 import paper_2104_02139_gb300 as L
 import workloads as W
-from adjoint_cases import bc_case
+from adjoint_cases import bc_case, family_case
 
 pytestmark = pytest.mark.gpu
 
@@ -184,6 +184,12 @@ def test_adjoint_fd_boundary_faces(name):
     """Traction, pressure and prescribed-velocity faces and contact walls, MOOD active, the
     finite differences through the tape's replay (recorded masks and dt)."""
     _check_init_grads(bc_case(name), 5, {}, seed=24, frozen=True)
+
+
+@pytest.mark.parametrize("name", ["cube3d_a0", "impact2d_a05"])
+def test_adjoint_fd_shear_family(name):
+    """the shear energy family (a != -1): its stress and product in the predictor's reverse"""
+    _check_init_grads(family_case(name), 5, {}, seed=25, frozen=True)
 
 
 @pytest.mark.parametrize("name", ["plain2d", "piston2d", "rebound2d", "box3d_bc"])

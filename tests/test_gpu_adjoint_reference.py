@@ -9,7 +9,8 @@
    and the adaptive dt, in 2D (slip walls; the impact against a wall) and 3D (slip walls; the
    clamped column), and with traction, pressure and prescribed-velocity faces and contact
    walls (the piston, a block rebounding on a wall, a block under pressure and traction, a 3D
-   box with every kind of face). The two runs' masks must be identical at every step and their
+   box with every kind of face), and with the shear energy family (a = 0, a = 0.5). The two
+   runs' masks must be identical at every step and their
    dt equal to 1e-12, so both differentiate the same map.
 2. The adjoint configuration at full size (511,104 tetrahedra, 400 steps, a checkpoint every
    20 steps): the gradient of J = sum over cells with initial centroid z > 0.5 of m |v|^2 / 2
@@ -25,7 +26,7 @@ import pytest
 import oracle as O
 import paper_2104_02139_gb300 as L
 import workloads as W
-from adjoint_cases import bc_case, smooth_positions_direction
+from adjoint_cases import bc_case, family_case, smooth_positions_direction
 
 pytestmark = pytest.mark.gpu
 
@@ -52,6 +53,8 @@ def _case(name):
     elif name == "column3d":
         pb = W.column3d(nxy=3, nz=12)
         pb.v *= 8.0
+    elif name in ("cube3d_a0", "impact2d_a05"):
+        pb = family_case(name)
     else:
         pb = bc_case(name)
     return pb
@@ -69,7 +72,7 @@ def _perturbed_material(pb, rng):
 
 
 @pytest.mark.parametrize("name", ["plain2d", "impact2d", "cube3d", "column3d", "piston2d", "rebound2d",
-                                  "pressure_traction2d", "box3d_bc"])
+                                  "pressure_traction2d", "box3d_bc", "cube3d_a0", "impact2d_a05"])
 def test_adjoint_matches_the_oracle_tangent(name):
     rng = np.random.default_rng(31)
     pb = _perturbed_material(_case(name), rng)
