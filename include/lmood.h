@@ -210,6 +210,12 @@ lmood_status lmood_mesh_set_btag(lmood_mesh m, const int32_t *btag);
 lmood_status lmood_state_init(lmood_mesh m, const lmood_material *mat, const double *mu_cell,
                               const double *v_cell, const double *F_cell, const lmood_params *prm,
                               lmood_state *out);
+/* The same with mu_cell, v_cell and F_cell (NULL: identity) in device memory, read in order on
+ * the mesh's stream (the caller makes them ready there); mu > 0 is checked on the device
+ * (LMOOD_ERR_ARG). Nothing of the inputs goes through host memory. */
+lmood_status lmood_state_init_device(lmood_mesh m, const lmood_material *mat, const double *mu_cell,
+                                     const double *v_cell, const double *F_cell, const lmood_params *prm,
+                                     lmood_state *out);
 lmood_status lmood_state_destroy(lmood_state s);
 
 /*

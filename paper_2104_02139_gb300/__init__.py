@@ -47,7 +47,7 @@ class StepInfo(C.Structure):
 _lib = None
 EXPORTS = ("lmood_params_default", "lmood_mesh_create", "lmood_mesh_destroy", "lmood_mesh_info",
            "lmood_mesh_set_bc_values", "lmood_mesh_set_btag", "lmood_mesh_set_contact",
-           "lmood_state_init", "lmood_state_destroy", "lmood_step", "lmood_run", "lmood_get", "lmood_set",
+           "lmood_state_init", "lmood_state_init_device", "lmood_state_destroy", "lmood_step", "lmood_run", "lmood_get", "lmood_set",
            "lmood_get_fields", "lmood_set_fields",
            "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_autotune", "lmood_autotune_schedule",
            "lmood_totals_noalloc",
@@ -74,6 +74,8 @@ def lib():
         L.lmood_mesh_set_btag.argtypes = [vp, vp]
         L.lmood_mesh_set_contact.argtypes = [vp, C.c_int, vp, C.c_double]
         L.lmood_state_init.argtypes = [vp, C.POINTER(Material), vp, vp, vp, C.POINTER(Params), C.POINTER(vp)]
+        L.lmood_state_init_device.argtypes = [vp, C.POINTER(Material), vp, vp, vp, C.POINTER(Params),
+                                              C.POINTER(vp)]
         L.lmood_state_destroy.argtypes = [vp]
         L.lmood_step.argtypes = [vp, C.POINTER(StepInfo)]
         L.lmood_run.argtypes = [vp, C.c_int64, C.POINTER(StepInfo)]
@@ -256,19 +258,35 @@ class State:
 
     def __init__(self, mesh: Mesh, rho0, lam, mu, v, F=None, params: Params | None = None, vol_coeff=0,
                  shear_a=-1.0, stiffened_gas=None):
-        """stiffened_gas: None, or (gamma, p_inf, p0) for the stiffened-gas volumetric law"""
+        """stiffened_gas: None, or (gamma, p_inf, p0) for the stiffened-gas volumetric law.
+        mu, v, F: host arrays, or torch CUDA tensors (all of them; lmood_state_init_device, the
+        data never leaves the device)"""
         self.mesh = mesh
         self.params = params or params_default(mesh.dim)
         mat = Material(rho0=rho0, lambda_=lam, vol_coeff=vol_coeff, shear_a=shear_a)
         if stiffened_gas is not None:
             mat.eos = 1
             mat.gamma, mat.p_inf, mat.p0 = stiffened_gas
-        mu = _host(mu, np.float64)
-        v = _host(v, np.float64)
-        F = _host(F, np.float64)
         h = C.c_void_p()
-        _check(lib().lmood_state_init(mesh.h, C.byref(mat), _ptr(mu), _ptr(v), _ptr(F), C.byref(self.params),
-                                      C.byref(h)))
+        nc, d = mesh.n_cells, mesh.dim
+        if _is_torch(mu) or _is_torch(v) or _is_torch(F):
+            if not (_is_torch(mu) and _is_torch(v) and (F is None or _is_torch(F))):
+                raise TypeError("State: mu, v and F must be all host arrays or all CUDA tensors")
+            import torch
+            kept = [_in_buffer(a, shp, f"State ({k})") for a, shp, k in
+                    ((mu, (nc,), "mu"), (v, (d, nc), "v"), (F, (d * d, nc), "F")) if a is not None]
+            torch.cuda.current_stream().synchronize()  # the inputs are ready before the mesh's stream reads them
+            ptrs = [C.c_void_p(k[1]) for k in kept] + ([None] if F is None else [])
+            _check(lib().lmood_state_init_device(mesh.h, C.byref(mat), *ptrs, C.byref(self.params), C.byref(h)))
+            if any(k[3] for k in kept):
+                _sync_after_copy()
+            del kept
+        else:
+            mu = _host(mu, np.float64)
+            v = _host(v, np.float64)
+            F = _host(F, np.float64)
+            _check(lib().lmood_state_init(mesh.h, C.byref(mat), _ptr(mu), _ptr(v), _ptr(F), C.byref(self.params),
+                                          C.byref(h)))
         self.h = h
         self.info = StepInfo()
 
@@ -474,12 +492,16 @@ def rollout(problem, n_steps: int, v0, mu, F0=None, checkpoint_every: int = 0, *
             pb = problem
             m = pb.mesh
             mesh = Mesh(m.dim, m.x, m.c2n, m.bface, m.btag)
+            if getattr(pb, "bcval", None) is not None:
+                mesh.set_bc_values(pb.bcval)
+            if getattr(pb, "contact", None) is not None:
+                mesh.set_contact(*pb.contact)
             p = params_default(m.dim, cfl=pb.cfl)
             for k, v in params.items():
                 setattr(p, k, v)
-            Fh = None if F0_ is None else F0_.detach().cpu().numpy()
-            state = State(mesh, pb.rho0, pb.lam, mu_.detach().cpu().numpy(), v0_.detach().cpu().numpy(), Fh, p,
-                          shear_a=getattr(pb, "shear_a", -1.0))
+            # the initial data stay on the device (lmood_state_init_device)
+            state = State(mesh, pb.rho0, pb.lam, mu_.detach(), v0_.detach(), None if F0_ is None else F0_.detach(),
+                          p, shear_a=getattr(pb, "shear_a", -1.0))
             tape = Tape(state, n_steps, checkpoint_every)
             outs = []
             for fid in (FIELD_X, FIELD_VP, FIELD_V, FIELD_F):

@@ -593,9 +593,31 @@ lmood_status lmood::sync_check(lmood_state s, const char *where) {
     return LMOOD_OK;
 }
 
+// counts the entries of mu that are not > 0 (NaN included) into *bad
+__global__ static void k_count_nonpositive(const double *mu, int64_t n, int *bad) {
+    int k = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        k += !(mu[i] > 0.0);
+    if (k) atomicAdd(bad, k);
+}
+
+static lmood_status state_init(lmood_mesh M, const lmood_material *mat, const double *mu_cell, const double *v_cell,
+                               const double *F_cell, const lmood_params *prm, lmood_state *out, bool dev);
+
 extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat, const double *mu_cell,
                                          const double *v_cell, const double *F_cell, const lmood_params *prm,
                                          lmood_state *out) {
+    return state_init(M, mat, mu_cell, v_cell, F_cell, prm, out, false);
+}
+
+extern "C" lmood_status lmood_state_init_device(lmood_mesh M, const lmood_material *mat, const double *mu_cell,
+                                                const double *v_cell, const double *F_cell, const lmood_params *prm,
+                                                lmood_state *out) {
+    return state_init(M, mat, mu_cell, v_cell, F_cell, prm, out, true);
+}
+
+static lmood_status state_init(lmood_mesh M, const lmood_material *mat, const double *mu_cell, const double *v_cell,
+                               const double *F_cell, const lmood_params *prm, lmood_state *out, bool dev) {
     if (!out) return fail(LMOOD_ERR_ARG, "lmood_state_init: out is NULL");
     *out = nullptr;
     if (!M || !mat || !mu_cell || !v_cell || !prm) return fail(LMOOD_ERR_ARG, "lmood_state_init: NULL argument");
@@ -611,8 +633,9 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
         return fail(LMOOD_ERR_ARG, "lmood_state_init: bad parameters");
     const int D = M->dim, NV = D + 1, NS = D * (D + 1) / 2;
     const int64_t N = M->nc, Np = M->np;
-    for (int64_t c = 0; c < N; ++c)
-        if (!(mu_cell[c] > 0)) return fail(LMOOD_ERR_ARG, "lmood_state_init: mu must be positive");
+    if (!dev)
+        for (int64_t c = 0; c < N; ++c)
+            if (!(mu_cell[c] > 0)) return fail(LMOOD_ERR_ARG, "lmood_state_init: mu must be positive");
     auto *s = new lmood_state_s();
     s->M = M;
     s->prm = *prm;
@@ -687,8 +710,23 @@ extern "C" lmood_status lmood_state_init(lmood_mesh M, const lmood_material *mat
     f.mu = s->mu;
     f.dt = dt0;
     f.dtn = (unsigned long long *)dt1;
+    if (dev) {  // mu > 0 checked on the device before anything else reads the inputs
+        cudaMemsetAsync(f.cnt, 0, sizeof(int), st);
+        k_count_nonpositive<<<256, 256, 0, st>>>(mu_cell, N, f.cnt);
+        if (cudaMemcpyAsync(s->h_cnt, f.cnt, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaGetLastError();
+            state_free(s);
+            return fail(LMOOD_ERR_CUDA, "lmood_state_init_device: checking mu");
+        }
+        if (s->h_cnt[0]) {
+            state_free(s);
+            return fail(LMOOD_ERR_ARG, "lmood_state_init_device: mu must be positive");
+        }
+    }
     auto H2D = [&](void *d, const void *h, size_t b) {
-        if (r == LMOOD_OK && cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        if (r == LMOOD_OK &&
+            cudaMemcpyAsync(d, h, b, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st) != cudaSuccess)
             r = fail(LMOOD_ERR_CUDA, "lmood_state_init: upload");
     };
     if (cudaMemcpyAsync(f.x, M->x0, D * Np * nd, cudaMemcpyDeviceToDevice, st) != cudaSuccess)

@@ -329,6 +329,48 @@ def test_torch_rollout_autograd():
     assert _rel(ad, fd) <= 1e-6, (ad, fd)
 
 
+def test_state_init_from_device_tensors():
+    """lmood_state_init_device (the rollout's path: the initial data stay on the device) gives
+    the state lmood_state_init gives from the same values in host memory, bitwise, and refuses
+    a non-positive mu on the device"""
+    import torch
+    pb, lam, rng = _setup(bc_case("piston2d"), 27)
+    host = L.simulation(pb)
+    m = pb.mesh
+    mesh = L.Mesh(m.dim, m.x, m.c2n, m.bface, m.btag)
+    mesh.set_bc_values(pb.bcval)
+    dev = L.State(mesh, pb.rho0, pb.lam, torch.tensor(pb.mu, device="cuda"), torch.tensor(pb.v, device="cuda"),
+                  torch.tensor(pb.F, device="cuda"), L.params_default(m.dim, cfl=pb.cfl))
+    for _ in range(2):
+        for k, fid in OUT_FIELDS + (("e", L.FIELD_E),):
+            assert np.array_equal(host.get(fid), dev.get(fid)), k
+        host.step()
+        dev.step()
+    bad = np.array(pb.mu)
+    bad[5] = 0.0
+    with pytest.raises(L.LmoodError) as e:
+        L.State(mesh, pb.rho0, pb.lam, torch.tensor(bad, device="cuda"), torch.tensor(pb.v, device="cuda"), None,
+                L.params_default(m.dim, cfl=pb.cfl))
+    assert e.value.status == L.ERR_ARG
+
+
+def test_torch_rollout_boundary_faces():
+    """the rollout on a problem with prescribed-velocity faces (the piston): gradients of v0 and
+    mu equal the tape's"""
+    import torch
+    pb, lam, rng = _setup(bc_case("piston2d"), 28)
+    n = 4
+    v0 = torch.tensor(pb.v, dtype=torch.float64, device="cuda", requires_grad=True)
+    mu = torch.tensor(pb.mu, dtype=torch.float64, device="cuda", requires_grad=True)
+    x, vp, v, F = L.rollout(pb, n, v0, mu, torch.tensor(pb.F, device="cuda"), checkpoint_every=2)
+    ((v * v).sum() + x.sum()).backward()
+    st = L.simulation(pb)
+    tape = L.Tape(st, n)
+    g = tape.backward(lam_x=np.ones((pb.mesh.dim, pb.mesh.n_nodes)), lam_v=2 * st.get(L.FIELD_V))
+    np.testing.assert_allclose(v0.grad.cpu().numpy(), g["v"], rtol=1e-12, atol=1e-14 * np.abs(g["v"]).max())
+    np.testing.assert_allclose(mu.grad.cpu().numpy(), g["mu"], rtol=1e-12, atol=1e-14 * np.abs(g["mu"]).max())
+
+
 def test_tape_errors():
     pb = W.plain2d(n=6)
     st = L.simulation(pb)
