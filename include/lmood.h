@@ -244,7 +244,8 @@ lmood_status lmood_run(lmood_state s, int64_t nsteps, lmood_step_info *last);
  * is_device != 0 (ordered on the mesh's stream), else a host pointer (the call
  * synchronises). Sizes and layouts are those of the field ids above; set accepts X, VP, V,
  * E, F and DT (replacing the dynamic state, e.g. to restart from a checkpoint; setting X
- * also refreshes the derived cell geometry).
+ * or F also refreshes the derived cell geometry, density and impedance, and with the
+ * stiffened gas so does setting V or E, on which its impedance depends).
  * Errors: LMOOD_ERR_ARG for an unknown or read-only field id.
  */
 lmood_status lmood_get(lmood_state s, int field, void *dst, int is_device);
@@ -253,7 +254,8 @@ lmood_status lmood_set(lmood_state s, int field, const void *src, int is_device)
 /*
  * Several fields in one call: the n copies are queued on the mesh's stream back to back and,
  * for host pointers, the call synchronises once at the end (set: the derived cell geometry
- * is refreshed once, after the last copy, when X or F is among the fields). fields[i] and
+ * is refreshed once, after the last copy, when X or F is among the fields, or with the
+ * stiffened gas V or E). fields[i] and
  * dst[i] / src[i] as for lmood_get / lmood_set; all host or all device (is_device).
  * Errors: LMOOD_ERR_ARG for a NULL pointer, an unknown or (set) read-only field id, or ORDER
  * requested twice in one get; every argument is checked before the first copy.
@@ -336,16 +338,18 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  * (x, v_p per node; v, F per cell) and of the per-cell mu; the adjoint is the exact transpose
  * of its linearisation, written by hand kernel by kernel (no atomics, deterministic).
  * Only the two-level cascade (P1 -> P0) is differentiated: a recorded step that used the
- * limited level returns LMOOD_ERR_ARG, and so does the stiffened gas (its pressure depends on
- * the internal energy); the neo-Hookean law and every a of the shear energy family (Eq.
- * familiy_energies) are differentiated. Boundary faces of every kind are differentiated: slip and
+ * limited level returns LMOOD_ERR_ARG. Every material is differentiated: the neo-Hookean law,
+ * every a of the shear energy family (Eq. familiy_energies) and the stiffened gas (whose
+ * pressure depends on the internal energy e, which then carries an adjoint: see
+ * lmood_tape_backward_e). Boundary faces of every kind are differentiated: slip and
  * clamped nodes, traction and pressure faces (their forces depend on the faces' area vectors,
  * hence on the positions), prescribed-velocity faces and contact walls (their multiplier
  * steps, with the set of walls a node is in contact with, and whether each multiplier step
  * applies, frozen like the order mask); the boundary values and contact walls themselves are
  * constants. lmood_tape_backward returns LMOOD_ERR_STATE if the mesh's boundary values, tags or
- * contact walls were changed after the recording. Energy e has no influence on the other
- * fields, so it carries no adjoint.
+ * contact walls were changed after the recording. With the volumetric law of Eq. EOS_neoHook
+ * the energy e has no influence on the other fields; lmood_tape_backward takes no adjoint of
+ * it, lmood_tape_backward_e does.
  *
  * lmood_tape_record: runs n_steps ordinary lmood_step calls on s (the forward pass, with the
  *   MOOD loop and the dt rule as configured) and records what the reverse pass needs: the dt
@@ -384,7 +388,9 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  *   so it can go on with lmood_step. Synchronises once per step.
  * lmood_tape_info: out4[0] steps, [1] checkpoint interval (0: store mode), [2] 1 if the tape
  *   starts from a just-initialised state, [3] device bytes held.
- * Destroy the tape before its state.
+ * Destroy the tape before its state. (Destroyed out of order -- a mesh before its states, a
+ * state before its tapes, as a garbage collector may do -- the dependent handles stay
+ * destroyable and every other call on them returns an error.)
  */
 typedef struct lmood_tape_s *lmood_tape;
 lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_t checkpoint_every, lmood_tape *out,
@@ -392,6 +398,14 @@ lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_t checkpoin
 lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, const double *lam_vp, const double *lam_v,
                                  const double *lam_F, double *grad_x, double *grad_vp, double *grad_v,
                                  double *grad_F, double *grad_mu, int is_device);
+/* The same with the energy: lam_e [n_cells] the adjoint of the final e (NULL = 0) and grad_e
+ * [n_cells] the gradient with respect to the starting e (NULL: not wanted; zero when the tape
+ * starts from a just-initialised state, whose e is a function of v, F and mu, through which
+ * the gradient then goes). With the stiffened gas e enters the pressure, so it always carries
+ * an adjoint; with the volumetric law of Eq. EOS_neoHook it has none unless lam_e is given. */
+lmood_status lmood_tape_backward_e(lmood_tape t, const double *lam_x, const double *lam_vp, const double *lam_v,
+                                   const double *lam_F, const double *lam_e, double *grad_x, double *grad_vp,
+                                   double *grad_v, double *grad_F, double *grad_e, double *grad_mu, int is_device);
 lmood_status lmood_tape_replay(lmood_tape t, lmood_state s2, int64_t n_steps);
 lmood_status lmood_tape_info(lmood_tape t, int64_t *out4);
 lmood_status lmood_tape_destroy(lmood_tape t);

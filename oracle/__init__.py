@@ -334,7 +334,7 @@ def tangent_lib():
         vp = C.c_void_p
         _tlib.orct_run.argtypes = [C.c_int, C.c_long, vp, vp, C.c_double, C.c_long, vp, C.c_long, vp, vp, vp, C.c_int, vp,
                                    C.c_double, C.c_double, C.c_double, vp, vp, vp, vp, vp, vp, C.POINTER(Params),
-                                   C.c_long] + [vp] * 10
+                                   C.c_long] + [vp] * 12
         _tlib.orct_run.restype = C.c_int
     return _tlib
 
@@ -342,15 +342,19 @@ def tangent_lib():
 def tangent(problem, n_steps: int, dv=None, dmu=None, dF=None, dx=None, x_shift: float = 0.0,
             params: Params | None = None, **kw) -> dict:
     """The oracle's n-step map and its directional derivative (forward mode, dual numbers):
-    the final state x, vp [d][np], v [d][nc], F [d*d][nc] and their derivatives dx, dvp, dv,
-    dF along the direction (dv [d][nc], dmu [nc], dF [d*d][nc], dx [d][np] of the positions at
+    the final state x, vp [d][np], v [d][nc], F [d*d][nc], e [nc] and their derivatives dx,
+    dvp, dv, dF, de along the direction (dv [d][nc], dmu [nc], dF [d*d][nc], dx [d][np] of the positions at
     fixed cell masses; None = 0) of the initial data, with each step's order mask and dt held
     at the run's own (masks [n][nc] int8, dts [n]). The problem's boundary values and contact
     walls apply as constants. x_shift: start from the positions x + x_shift dx (masses and slip
     directions of x), for central differences along dx."""
     m = problem.mesh
     d, nc, npn = m.dim, m.n_cells, m.n_nodes
-    prm = params or default_params(problem.cfl, **{"shear_a": getattr(problem, "shear_a", -1.0), **kw})
+    sgkw = {}
+    sg = getattr(problem, "stiffened_gas", None)
+    if sg is not None:
+        sgkw = {"eos": 1, "gamma": sg[0], "p_inf": sg[1], "p0": sg[2]}
+    prm = params or default_params(problem.cfl, **{"shear_a": getattr(problem, "shear_a", -1.0), **sgkw, **kw})
     keep = []
 
     def arr(a, dtype=np.float64):
@@ -362,7 +366,8 @@ def tangent(problem, n_steps: int, dv=None, dmu=None, dF=None, dx=None, x_shift:
 
     out = {k: np.zeros(shape) for k, shape in (("x", (d, npn)), ("dx", (d, npn)), ("vp", (d, npn)),
                                                 ("dvp", (d, npn)), ("v", (d, nc)), ("dv", (d, nc)),
-                                                ("F", (d * d, nc)), ("dF", (d * d, nc)))}
+                                                ("F", (d * d, nc)), ("dF", (d * d, nc)), ("e", (nc,)),
+                                                ("de", (nc,)))}
     out["masks"] = np.zeros((n_steps, nc), np.int8)
     out["dts"] = np.zeros(n_steps)
     nb = m.btag.size
@@ -375,7 +380,7 @@ def tangent(problem, n_steps: int, dv=None, dmu=None, dF=None, dx=None, x_shift:
                                 0 if planes is None else len(planes), arr(planes), ceps,
                                 problem.rho0, problem.lam, arr(problem.mu), arr(dmu), arr(problem.v), arr(dv),
                                 arr(problem.F), arr(dF), C.byref(prm), n_steps,
-                                *(out[k].ctypes.data for k in ("x", "dx", "vp", "dvp", "v", "dv", "F", "dF")),
+                                *(out[k].ctypes.data for k in ("x", "dx", "vp", "dvp", "v", "dv", "F", "dF", "e", "de")),
                                 out["masks"].ctypes.data, out["dts"].ctypes.data)
     if rc:
         raise OracleError(f"orct_run: {ERR.get(rc, rc)}")

@@ -118,7 +118,7 @@ void split_soa(const real *a, long n, int k, double *val, double *dir) {
  * v_p^0 is done again there (x_shift != 0 gives the values of a displaced start, whose central
  * differences pin the derivative part). Outputs (each may be NULL): the
  * final state's values and derivatives, SoA like the oracle's orc_get (x, vp [d][np]; v [d][nc];
- * F [d*d][nc]), the order mask of every step masks [n_steps][nc] and its dt dts [n_steps].
+ * F [d*d][nc]; e [nc]), the order mask of every step masks [n_steps][nc] and its dt dts [n_steps].
  * Returns the oracle's status (0 ok; the first failing step stops the run).
  */
 extern "C" int orct_run(int d, long np, const double *x_soa, const double *dx_soa, double x_shift, long nc,
@@ -128,7 +128,7 @@ extern "C" int orct_run(int d, long np, const double *x_soa, const double *dx_so
                         const double *dmu, const double *v_soa, const double *dv_soa, const double *F_soa,
                         const double *dF_soa, const OrcParams *prm, long n_steps, double *x_out, double *dx_out,
                         double *vp_out, double *dvp_out, double *v_out, double *dv_out, double *F_out,
-                        double *dF_out, signed char *masks, double *dts) {
+                        double *dF_out, double *e_out, double *de_out, signed char *masks, double *dts) {
     if ((d != 2 && d != 3) || !x_soa || !c2n_soa || !mu || !v_soa || !prm || n_steps < 0) return ORC_ERR_ARG;
     const int dd = d * d;
     real *xr = dual_array(np * d, x_soa, nullptr);
@@ -188,6 +188,7 @@ extern "C" int orct_run(int d, long np, const double *x_soa, const double *dx_so
         split_soa(S->vp, np, d, vp_out, dvp_out);
         split_soa(S->v, nc, d, v_out, dv_out);
         split_soa(S->F, nc, dd, F_out, dF_out);
+        split_soa(S->e, nc, 1, e_out, de_out);
     }
     orc_state_free(S);
     orc_mesh_free(M);

@@ -52,7 +52,7 @@ EXPORTS = ("lmood_params_default", "lmood_mesh_create", "lmood_mesh_destroy", "l
            "lmood_totals", "lmood_timing", "lmood_timing_read", "lmood_autotune", "lmood_autotune_schedule",
            "lmood_totals_noalloc",
            "lmood_tape_record",
-           "lmood_tape_backward", "lmood_tape_replay", "lmood_tape_info", "lmood_tape_destroy", "lmood_last_error")
+           "lmood_tape_backward", "lmood_tape_backward_e", "lmood_tape_replay", "lmood_tape_info", "lmood_tape_destroy", "lmood_last_error")
 K_PREDICT, K_NODES, K_UPDATE, K_MOOD, K_FINALIZE, K_MOMENTS, NK = range(7)
 K_NAMES = ("predict", "nodes", "update", "mood", "finalize", "moments")
 
@@ -92,6 +92,7 @@ def lib():
                                               C.POINTER(C.c_double), C.POINTER(C.c_int32)]
         L.lmood_tape_record.argtypes = [vp, C.c_int64, C.c_int64, C.POINTER(vp), C.POINTER(StepInfo)]
         L.lmood_tape_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
+        L.lmood_tape_backward_e.argtypes = [vp] + [vp] * 11 + [C.c_int]
         L.lmood_tape_replay.argtypes = [vp, vp, C.c_int64]
         L.lmood_tape_info.argtypes = [vp, C.POINTER(C.c_int64)]
         L.lmood_tape_destroy.argtypes = [vp]
@@ -420,14 +421,14 @@ class Tape:
         _check(lib().lmood_tape_info(self.h, o))
         return dict(zip(("steps", "checkpoint_every", "through_init", "bytes"), list(o)))
 
-    def backward(self, lam_x=None, lam_vp=None, lam_v=None, lam_F=None, out=None) -> dict:
+    def backward(self, lam_x=None, lam_vp=None, lam_v=None, lam_F=None, lam_e=None, out=None) -> dict:
         """Adjoints of the final state in (numpy host arrays, or torch CUDA tensors; None = 0);
-        gradients with respect to the start of the tape out, as a dict x, vp, v, F, mu of the
+        gradients with respect to the start of the tape out, as a dict x, vp, v, F, e, mu of the
         same kind (numpy unless the inputs are torch tensors, or given in out)."""
         st = self.state
         shapes = {"x": st.shape(FIELD_X), "vp": st.shape(FIELD_VP), "v": st.shape(FIELD_V), "F": st.shape(FIELD_F),
-                  "mu": (st.mesh.n_cells,)}
-        ins = (lam_x, lam_vp, lam_v, lam_F)
+                  "e": (st.mesh.n_cells,), "mu": (st.mesh.n_cells,)}
+        ins = (lam_x, lam_vp, lam_v, lam_F, lam_e)
         dev = any(a is not None and hasattr(a, "data_ptr") for a in ins)
         if out is None:
             if dev:
@@ -437,7 +438,7 @@ class Tape:
                 out = {k: np.empty(v) for k, v in shapes.items()}
 
         kept, args = [], []
-        for a, k in zip(ins, ("x", "vp", "v", "F")):
+        for a, k in zip(ins, ("x", "vp", "v", "F", "e")):
             if a is None:
                 args.append(None)
                 continue
@@ -446,7 +447,7 @@ class Tape:
             kept.append(_in_buffer(a, shapes[k], f"backward (lam_{k})"))
             args.append(C.c_void_p(kept[-1][1]))
         optr = []
-        for k in ("x", "vp", "v", "F", "mu"):
+        for k in ("x", "vp", "v", "F", "e", "mu"):
             o = out.get(k)
             if o is None:
                 optr.append(None)
@@ -455,7 +456,7 @@ class Tape:
             if odev != int(dev):
                 raise ValueError("backward: gradients must live where the adjoint inputs do (host or device)")
             optr.append(C.c_void_p(ptr))
-        _check(lib().lmood_tape_backward(self.h, *args, *optr, 1 if dev else 0))
+        _check(lib().lmood_tape_backward_e(self.h, *args, *optr, 1 if dev else 0))
         if any(c[3] for c in kept):
             _sync_after_copy()
         del kept

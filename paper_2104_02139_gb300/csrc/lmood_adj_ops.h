@@ -27,6 +27,8 @@ template <int D> struct AdjRec {
 
 struct AdjBuf {
     double *lv1, *lF1, *lv0, *lF0;    // cells: [D][N], [D*D][N]
+    double *lE1, *lE0;                // cells: adjoints of e (NULL: not carried -- the
+                                      // neo-Hookean volumetric law with no energy term in J)
     double *lz0;                      // cells: adjoint of z^n (scratch of one step)
     double *lmu;                      // cells: d/d mu, accumulated over the steps
     double *lx1, *lvp1, *lx0, *lvp0;  // nodes: [D][Np]
@@ -66,6 +68,8 @@ struct AdjOps {
     void (*gather)(const Geo &, const AdjBuf &, cudaStream_t);
     // cells: impedance of the initial state (after the t^0 predictor's reverse)
     void (*z0)(const Geo &, const Fld &, const Prm &, const AdjBuf &, cudaStream_t);
+    // cells: the adjoint of the initial energy e^0 (a function of v, F, mu) moved to v, F, mu
+    void (*e0)(const Geo &, const Fld &, const Prm &, const AdjBuf &, cudaStream_t);
 };
 
 const AdjOps &adj_ops_dim2();

@@ -288,6 +288,131 @@ LMOOD_HD void stress_m_vjp(const double *F, double mu, double kap, double a, con
     else stress_family_vjp<D>(F, mu, kap, a, lT, lF, lmu, lkap, T_out);
 }
 
+// ---------------------------------------------------------------------------------------
+// Stiffened gas (Eq. EOS_stiffened_gas, incomplete form): p = (gam - 1) (rho0 / J)
+// (eps - Psi_s(F)) - gam pinf with Psi_s the shear energy of the family (a = -1: the
+// neo-Hookean one) and eps the specific internal energy; T = -p I + the shear stress
+// (kappa = 0); impedance z = sqrt(rho (gam (p + pinf) + 4 mu / (3 J))). With their products.
+// ---------------------------------------------------------------------------------------
+struct SgMat {
+    double gam, pinf, rho0;
+};
+
+// Psi_s = mu / (4 rho0) (-2a (I1 - 3) + (1 + a)/3 (I2^2 - 9)) of Bbar (a = -1: mu / (2 rho0)
+// (I1 - 3)); the product l -> lF, lmu
+template <int D> LMOOD_HD double shear_energy_a(const double *F, double rho0, double mu, double a) {
+    FamStress q;
+    family_parts<D>(F, mu, 0.0, a, q);
+    return mu / (4.0 * rho0) * (-2.0 * a * (q.I1 - 3.0) + (1.0 + a) * (1.0 / 3.0) * (q.I2 * q.I2 - 9.0));
+}
+
+template <int D>
+LMOOD_HD void shear_energy_a_vjp(const double *F, double rho0, double mu, double a, double l, double *lF, double &lmu) {
+    FamStress q;
+    family_parts<D>(F, mu, 0.0, a, q);
+    const double g = -2.0 * a * (q.I1 - 3.0) + (1.0 + a) * (1.0 / 3.0) * (q.I2 * q.I2 - 9.0);
+    lmu += l * g / (4.0 * rho0);
+    const double lg = l * mu / (4.0 * rho0);
+    const double lI2 = lg * (2.0 / 3.0) * (1.0 + a) * q.I2;
+    const double lI1 = lg * (-2.0 * a) + lI2 * q.I1;
+    double lB[9], lBB = 0.0;
+    for (int i = 0; i < 9; ++i) lB[i] = -lI2 * q.B[i];
+    for (int i = 0; i < 3; ++i) lB[i * 4] += lI1;
+    for (int i = 0; i < 9; ++i) lBB += lB[i] * q.B[i];
+    const double lJv = -(2.0 / 3.0) * q.invJ * lBB;
+    double F3[9], Cf[9];
+    for (int i = 0; i < 9; ++i) F3[i] = 0.0;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) F3[i * 3 + j] = F[i * D + j];
+    if (D == 2) F3[8] = 1.0;
+    cofactor<3>(F3, Cf);
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            double t = 0.0;
+            for (int k = 0; k < 3; ++k) t += (lB[i * 3 + k] + lB[k * 3 + i]) * F3[k * 3 + j];
+            lF[i * D + j] += q.Jm23 * t + lJv * Cf[i * 3 + j];
+        }
+}
+
+template <int D>
+LMOOD_HD double sg_pressure_a(const double *F, double mu, double a, const SgMat &sg, double eps) {
+    return (sg.gam - 1.0) * (sg.rho0 / det<D>(F)) * (eps - shear_energy_a<D>(F, sg.rho0, mu, a)) - sg.gam * sg.pinf;
+}
+
+// product of p: lp -> lF, lmu, leps
+template <int D>
+LMOOD_HD void sg_pressure_a_vjp(const double *F, double mu, double a, const SgMat &sg, double eps, double lp,
+                                double *lF, double &lmu, double &leps) {
+    const double J = det<D>(F), iJ = 1.0 / J, k = (sg.gam - 1.0) * sg.rho0 * iJ;
+    const double psi = shear_energy_a<D>(F, sg.rho0, mu, a);
+    leps += lp * k;
+    shear_energy_a_vjp<D>(F, sg.rho0, mu, a, -lp * k, lF, lmu);
+    const double lJ = -lp * k * (eps - psi) * iJ;
+    double C[D * D];
+    cofactor<D>(F, C);
+    for (int i = 0; i < D * D; ++i) lF[i] += lJ * C[i];
+}
+
+template <int D>
+LMOOD_HD void stress_sg_a(const double *F, double mu, double a, const SgMat &sg, double eps, double *T) {
+    stress_m<D>(F, mu, 0.0, a, T);
+    const double p = sg_pressure_a<D>(F, mu, a, sg, eps);
+    for (int i = 0; i < D; ++i) T[i * D + i] -= p;
+}
+
+template <int D>
+LMOOD_HD void stress_sg_a_vjp(const double *F, double mu, double a, const SgMat &sg, double eps, const double *lT,
+                              double *lF, double &lmu, double &leps, double *T_out = nullptr) {
+    double lkap = 0.0;
+    stress_m_vjp<D>(F, mu, 0.0, a, lT, lF, lmu, lkap, T_out);
+    double lp = 0.0;
+    for (int i = 0; i < D; ++i) lp -= lT[i * D + i];
+    sg_pressure_a_vjp<D>(F, mu, a, sg, eps, lp, lF, lmu, leps);
+    if (T_out) {
+        const double p = sg_pressure_a<D>(F, mu, a, sg, eps);
+        for (int i = 0; i < D; ++i) T_out[i * D + i] -= p;
+    }
+}
+
+template <int D>
+LMOOD_HD double impedance_sg_a(const double *F, double rho, double mu, double a, const SgMat &sg, double eps) {
+    const double p = sg_pressure_a<D>(F, mu, a, sg, eps);
+    return sqrt(rho * (sg.gam * (p + sg.pinf) + (4.0 / 3.0) * mu / det<D>(F)));
+}
+
+// product of z: lz -> lF, lrho, lmu, leps
+template <int D>
+LMOOD_HD void impedance_sg_a_vjp(const double *F, double rho, double mu, double a, const SgMat &sg, double eps,
+                                 double lz, double *lF, double &lrho, double &lmu, double &leps) {
+    const double J = det<D>(F), iJ = 1.0 / J;
+    const double p = sg_pressure_a<D>(F, mu, a, sg, eps);
+    const double Y = sg.gam * (p + sg.pinf) + (4.0 / 3.0) * mu * iJ;
+    const double z = sqrt(rho * Y), lX = lz * 0.5 / z;
+    lrho += lX * Y;
+    const double lY = lX * rho;
+    lmu += lY * (4.0 / 3.0) * iJ;
+    const double lJ = -lY * (4.0 / 3.0) * mu * iJ * iJ;
+    double C[D * D];
+    cofactor<D>(F, C);
+    for (int i = 0; i < D * D; ++i) lF[i] += lJ * C[i];
+    sg_pressure_a_vjp<D>(F, mu, a, sg, eps, lY * sg.gam, lF, lmu, leps);
+}
+
+// the material's stress with the energy: the stiffened gas when sg is given, else stress_m
+template <int D>
+LMOOD_HD void stress_x(const double *F, double mu, double kap, double a, const SgMat *sg, double eps, double *T) {
+    if (sg) stress_sg_a<D>(F, mu, a, *sg, eps, T);
+    else stress_m<D>(F, mu, kap, a, T);
+}
+
+template <int D>
+LMOOD_HD void stress_x_vjp(const double *F, double mu, double kap, double a, const SgMat *sg, double eps,
+                           const double *lT, double *lF, double &lmu, double &lkap, double &leps,
+                           double *T_out = nullptr) {
+    if (sg) stress_sg_a_vjp<D>(F, mu, a, *sg, eps, lT, lF, lmu, leps, T_out);
+    else stress_m_vjp<D>(F, mu, kap, a, lT, lF, lmu, lkap, T_out);
+}
+
 // impedance z = sqrt(rho (K + 4 mu / (3 J))), K = (kap/2)(J + (1 - log J)/J)
 template <int D> LMOOD_HD double impedance(const double *F, double rho, double mu, double kap) {
     const double J = det<D>(F), invJ = 1.0 / J;
@@ -713,7 +838,8 @@ template <int D> struct Mom {
 
 template <int D>
 LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, const double *Fc, double z, double mu,
-                         double kap, double im, double dt, int ord, double *Mo, double *Ro, double sa = -1.0) {
+                         double kap, double im, double dt, int ord, double *Mo, double *Ro, double sa = -1.0,
+                         const SgMat *sg = nullptr, double ec = 0.0) {
     using Q = Sz<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ;
     double V, N[NV * D], xcc[D], W[NV][NS];
@@ -741,9 +867,14 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
             Mo[k * NS + s] = acc;
         }
     auto Mfull = [&](int k, int a, int b) { return Mo[k * NS + sym<D>(a, b)]; };
+    double eps = 0.0;  // the stiffened gas: eps = e - |v|^2 / 2
+    if (sg) {
+        eps = ec;
+        for (int a = 0; a < D; ++a) eps -= 0.5 * vc[a] * vc[a];
+    }
     if (ord == 1) {
         double T[DD];
-        stress_m<D>(Fc, mu, kap, sa, T);
+        stress_x<D>(Fc, mu, kap, sa, sg, eps, T);
         for (int k = 0; k < NV; ++k)
             for (int a = 0; a < D; ++a) {
                 double s = 0.0;
@@ -792,7 +923,7 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
             for (int a = 0; a < D; ++a) s += gs[D + q][a] * (xs[k * D + a] - xcc[a]);
             Fh[q] = s;
         }
-        stress_m<D>(Fh, mu, kap, sa, T);
+        stress_x<D>(Fh, mu, kap, sa, sg, eps, T);
         for (int i = 0; i < D; ++i)
             for (int b = 0; b < D; ++b) dv[i] += T[i * D + b] * N[k * D + b];
     }
@@ -800,6 +931,13 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
     for (int i = 0; i < D; ++i)
         for (int a = 0; a < D; ++a) gv[i * D + a] = gs[i][a];
     mm<D>(gv, Fc, dFdt);
+    double eps_h = eps;  // the stiffened gas: eps at the half step
+    if (sg) {
+        double Tc[DD], pw = 0.0;
+        stress_x<D>(Fc, mu, kap, sa, sg, eps, Tc);
+        for (int q = 0; q < DD; ++q) pw += Tc[q] * gv[q];
+        eps_h = eps + 0.5 * dt * pw * V * im;
+    }
     for (int k = 0; k < NV; ++k) {
         double vst[D], Fs[DD], T[DD];
         for (int i = 0; i < D; ++i) {
@@ -812,7 +950,7 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
             for (int a = 0; a < D; ++a) s += gs[D + q][a] * (xs[k * D + a] - xcc[a]);
             Fs[q] = s + 0.5 * dt * dFdt[q];
         }
-        stress_m<D>(Fs, mu, kap, sa, T);
+        stress_x<D>(Fs, mu, kap, sa, sg, eps_h, T);
         for (int a = 0; a < D; ++a) {
             double s = 0.0;
             for (int b = 0; b < D; ++b) s += Mfull(k, a, b) * vst[b] + T[a * D + b] * N[k * D + b] * (1.0 / D);
@@ -838,16 +976,19 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
 template <int D> struct PredRec {
     static constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + DD;
     // cell record: slopes gs [NQ][D], G^-1 [DD], d_k = x_k - x_c [NV][D], dF/dt [DD], face
-    // area vectors N [NV][D], D / |N_f| [NV], slopes taken (1) or not (0)
+    // area vectors N [NV][D], D / |N_f| [NV], slopes taken (1) or not (0), the volume, and for
+    // the stiffened gas the specific internal energy at t^n and at the half step
     static constexpr int F_GS = 0, F_GI = F_GS + NQ * D, F_DK = F_GI + DD, F_DFDT = F_DK + NV * D, F_N = F_DFDT + DD,
-                         F_INU = F_N + NV * D, F_OK = F_INU + NV, F_LEN = F_OK + 1;
+                         F_INU = F_N + NV * D, F_OK = F_INU + NV, F_V = F_OK + 1, F_EPS = F_V + 1, F_EPH = F_EPS + 1,
+                         F_LEN = F_EPH + 1;
     // corner record: F_h [DD], v* [D], M_k [NS]
     static constexpr int K_FH = 0, K_VST = DD, K_M = DD + D, K_LEN = DD + D + NS;
-    // pass-2 products of a corner: lv* [D], lF* [DD], lN_k [D], lmu, lkappa
+    // pass-2 products of a corner: lv* [D], lF* [DD], lN_k [D], lmu, lkappa, leps (half step)
     static constexpr int Q2_LV = 0, Q2_LF = D, Q2_LN = D + DD, Q2_MU = 2 * D + DD, Q2_KAP = Q2_MU + 1,
-                         Q2_LEN = Q2_KAP + 1;
-    // pass-1 products of a corner: lF_h [DD], lN_k [D], lmu, lkappa
-    static constexpr int Q1_LF = 0, Q1_LN = DD, Q1_MU = DD + D, Q1_KAP = Q1_MU + 1, Q1_LEN = Q1_KAP + 1;
+                         Q2_EPS = Q2_KAP + 1, Q2_LEN = Q2_EPS + 1;
+    // pass-1 products of a corner: lF_h [DD], lN_k [D], lmu, lkappa, leps (t^n)
+    static constexpr int Q1_LF = 0, Q1_LN = DD, Q1_MU = DD + D, Q1_KAP = Q1_MU + 1, Q1_EPS = Q1_KAP + 1,
+                         Q1_LEN = Q1_EPS + 1;
 };
 
 LMOOD_HD double adj_rsqrt(double x) {
@@ -870,7 +1011,7 @@ LMOOD_HD double adj_rsqrt(double x) {
 template <int D>
 LMOOD_HD void predict_fw_rec(const double *xs, const Mom<D> &mom, const double *vc, const double *Fc, double z,
                              double mu, double kap, double im, double dt, double *pf, double *pk, long kstride,
-                             double sa = -1.0) {
+                             double sa = -1.0, const SgMat *sg = nullptr, double ec = 0.0) {
     using Q = Sz<D>;
     using P = PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ;
@@ -878,6 +1019,13 @@ LMOOD_HD void predict_fw_rec(const double *xs, const Mom<D> &mom, const double *
     faces<D>(xs, V, N);
     LMOOD_UNROLL
     for (int i = 0; i < NV * D; ++i) pf[P::F_N + i] = N[i];
+    pf[P::F_V] = V;
+    double eps_c = 0.0;  // the stiffened gas: eps = e - |v|^2 / 2
+    if (sg) {
+        eps_c = ec;
+        for (int a = 0; a < D; ++a) eps_c -= 0.5 * vc[a] * vc[a];
+    }
+    pf[P::F_EPS] = eps_c;
     LMOOD_UNROLL
     for (int a = 0; a < D; ++a) {
         double s = 0.0;
@@ -994,7 +1142,7 @@ LMOOD_HD void predict_fw_rec(const double *xs, const Mom<D> &mom, const double *
             Fh[q] = s;
             rk[P::K_FH + q] = s;
         }
-        stress_m<D>(Fh, mu, kap, sa, T);
+        stress_x<D>(Fh, mu, kap, sa, sg, eps_c, T);
         LMOOD_UNROLL
         for (int i = 0; i < D; ++i)
             LMOOD_UNROLL
@@ -1020,17 +1168,27 @@ LMOOD_HD void predict_fw_rec(const double *xs, const Mom<D> &mom, const double *
     mm<D>(gv, Fc, dFdt);
     LMOOD_UNROLL
     for (int i = 0; i < DD; ++i) pf[P::F_DFDT + i] = dFdt[i];
+    // the stiffened gas: eps at the half step, eps_h = eps + dt/2 (T_c : gv) V / m
+    double eps_h = eps_c;
+    if (sg) {
+        double Tc[DD], pw = 0.0;
+        stress_x<D>(Fc, mu, kap, sa, sg, eps_c, Tc);
+        for (int i = 0; i < DD; ++i) pw += Tc[i] * gv[i];
+        eps_h = eps_c + 0.5 * dt * pw * V * im;
+    }
+    pf[P::F_EPH] = eps_h;
 }
 
 // reverse of corner k's packet R_k = M_k v*_k + (1/D) T(F*_k) N_k, F*_k = F_h,k + dt/2 dF/dt,
 // from lR_k [D]; adds lR_k (x) v*_k to lM_k [NS] and writes q2 [Q2_LEN]
 template <int D>
 LMOOD_HD void predict_corner2_vjp(const double *pf, const double *rk, int k, double mu, double kap, double dt,
-                                  const double *lR_k, double *lM_k, double *q2, double sa = -1.0) {
+                                  const double *lR_k, double *lM_k, double *q2, double sa = -1.0,
+                                  const SgMat *sg = nullptr) {
     using P = PredRec<D>;
     constexpr int DD = D * D;
     const double *N = pf + P::F_N + k * D, *vst = rk + P::K_VST;
-    double Fs[DD], lT[DD] = {}, lFs[DD] = {}, T[DD], lvst[D] = {}, lmu = 0.0, lkap = 0.0;
+    double Fs[DD], lT[DD] = {}, lFs[DD] = {}, T[DD], lvst[D] = {}, lmu = 0.0, lkap = 0.0, leps = 0.0;
     for (int q = 0; q < DD; ++q) Fs[q] = rk[P::K_FH + q] + 0.5 * dt * pf[P::F_DFDT + q];
     for (int a = 0; a < D; ++a) {
         const double l = lR_k[a];
@@ -1040,7 +1198,7 @@ LMOOD_HD void predict_corner2_vjp(const double *pf, const double *rk, int k, dou
             lT[a * D + b] += l * N[b] * (1.0 / D);
         }
     }
-    stress_m_vjp<D>(Fs, mu, kap, sa, lT, lFs, lmu, lkap, T);
+    stress_x_vjp<D>(Fs, mu, kap, sa, sg, sg ? pf[P::F_EPH] : 0.0, lT, lFs, lmu, lkap, leps, T);
     for (int b = 0; b < D; ++b) {
         double s = 0.0;
         for (int a = 0; a < D; ++a) s += lR_k[a] * T[a * D + b];
@@ -1050,20 +1208,21 @@ LMOOD_HD void predict_corner2_vjp(const double *pf, const double *rk, int k, dou
     for (int q = 0; q < DD; ++q) q2[P::Q2_LF + q] = lFs[q];
     q2[P::Q2_MU] = lmu;
     q2[P::Q2_KAP] = lkap;
+    q2[P::Q2_EPS] = leps;
 }
 
 // reverse of corner k's term of dv = hv sum_k T(F_h,k) N_k, given lacc = hv * (adjoint of dv);
 // writes q1 [Q1_LEN]
 template <int D>
 LMOOD_HD void predict_corner1_vjp(const double *pf, const double *rk, int k, double mu, double kap,
-                                  const double *lacc, double *q1, double sa = -1.0) {
+                                  const double *lacc, double *q1, double sa = -1.0, const SgMat *sg = nullptr) {
     using P = PredRec<D>;
     constexpr int DD = D * D;
     const double *N = pf + P::F_N + k * D;
-    double lT[DD], lF[DD] = {}, T[DD], lmu = 0.0, lkap = 0.0;
+    double lT[DD], lF[DD] = {}, T[DD], lmu = 0.0, lkap = 0.0, leps = 0.0;
     for (int i = 0; i < D; ++i)
         for (int b = 0; b < D; ++b) lT[i * D + b] = lacc[i] * N[b];
-    stress_m_vjp<D>(rk + P::K_FH, mu, kap, sa, lT, lF, lmu, lkap, T);
+    stress_x_vjp<D>(rk + P::K_FH, mu, kap, sa, sg, sg ? pf[P::F_EPS] : 0.0, lT, lF, lmu, lkap, leps, T);
     for (int b = 0; b < D; ++b) {
         double s = 0.0;
         for (int i = 0; i < D; ++i) s += lacc[i] * T[i * D + b];
@@ -1072,6 +1231,7 @@ LMOOD_HD void predict_corner1_vjp(const double *pf, const double *rk, int k, dou
     for (int q = 0; q < DD; ++q) q1[P::Q1_LF + q] = lF[q];
     q1[P::Q1_MU] = lmu;
     q1[P::Q1_KAP] = lkap;
+    q1[P::Q1_EPS] = leps;
 }
 
 // reverse of the corner matrices M_k = sum_{f != k} W_f (lmk(k): the final adjoint of M_k,
@@ -1113,7 +1273,8 @@ LMOOD_HD void predict_tail_vjp(const double *xs, const double *N, const double *
 template <int D, class Q2K, class Q1K, class MO>
 LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const double *Fc, double dt, const double *pf,
                                  Q2K &&q2k, Q1K &&q1k, double *lxs, double *lxcc, MO &&mout, double *lvc,
-                                 double *lFc) {
+                                 double *lFc, const SgMat *sg = nullptr, double mu = 0.0, double sa = -1.0,
+                                 double im = 0.0, double *lmu = nullptr, double *le = nullptr) {
     using Q = Sz<D>;
     using P = PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ;
@@ -1181,6 +1342,37 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
             lgs[i][j] += s;
             lFc[i * D + j] += u;
         }
+    // the stiffened gas: eps_h = eps + dt/2 (T_c : gv) V / m, the corners' stresses at eps
+    // (pass 1) and eps_h (pass 2); eps = e - |v|^2 / 2
+    if (sg) {
+        const double V = pf[P::F_V], c = 0.5 * dt * V * im;
+        double leh = 0.0, lec = 0.0;
+        LMOOD_UNROLL
+        for (int k = 0; k < NV; ++k) {
+            leh += q2k(k)[P::Q2_EPS];
+            lec += q1k(k)[P::Q1_EPS];
+        }
+        lec += leh;
+        double lTc[DD], Tc[DD], lk = 0.0;
+        LMOOD_UNROLL
+        for (int i = 0; i < DD; ++i) lTc[i] = c * leh * gs[i];  // gs [0..D)[D] is gv
+        stress_x_vjp<D>(Fc, mu, 0.0, sa, sg, pf[P::F_EPS], lTc, lFc, *lmu, lk, lec, Tc);
+        double pw = 0.0;
+        LMOOD_UNROLL
+        for (int i = 0; i < DD; ++i) pw += Tc[i] * gs[i];
+        LMOOD_UNROLL
+        for (int i = 0; i < D; ++i)
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) lgs[i][a] += c * leh * Tc[i * D + a];
+        const double lV = 0.5 * dt * pw * im * leh, *N = pf + P::F_N;  // dV / dx_k = -N_k / D
+        LMOOD_UNROLL
+        for (int k = 0; k < NV; ++k)
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) lxs[k * D + a] -= lV * N[k * D + a] * (1.0 / D);
+        *le += lec;
+        LMOOD_UNROLL
+        for (int a = 0; a < D; ++a) lvc[a] -= lec * vc[a];
+    }
     // least squares: gs = Gi r
     if (pf[P::F_OK] != 0.0) {
         // gs_q = G^{-1} r_q, G symmetric: lr_q = G^{-1} lgs_q (in place), lG = -sum_q lr_q gs_q^t
@@ -1303,7 +1495,8 @@ LMOOD_HD void predict_tail_p1_vjp(const double *xs, double z, const double *pf, 
 template <int D, class MO>
 LMOOD_HD void predict_p0_vjp(const double *xs, const double *vc, const double *Fc, double z, double mu, double kap,
                              double *lM, const double *lR, double *lxs, MO &&mout, double *lvc, double *lFc,
-                             double &lz, double &lmu, double &lkap, double sa = -1.0);
+                             double &lz, double &lmu, double &lkap, double sa = -1.0, const SgMat *sg = nullptr,
+                             double ec = 0.0, double *le = nullptr);
 
 // Product of predict_fw: (lM [NV][NS], lR [NV][D]) -> accumulates lxs [NV][D], lvc [D],
 // lFc [DD], lz, lmu, lkap, and stores the adjoints of the node moments through
@@ -1312,7 +1505,7 @@ template <int D, class MO>
 LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc, const double *Fc, double z, double mu,
                           double kap, double im, double dt, int ord, const double *lM_in, const double *lR, double *lxs,
                           MO &&mout, double *lvc, double *lFc, double &lz, double &lmu, double &lkap,
-                          double sa = -1.0) {
+                          double sa = -1.0, const SgMat *sg = nullptr, double ec = 0.0, double *le = nullptr) {
     using Q = Sz<D>;
     using P = PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NM = Q::NMOM;
@@ -1320,16 +1513,16 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
     for (int i = 0; i < NV * NS; ++i) lM[i] = lM_in[i];
     if (ord != 1) {
         double pf[P::F_LEN], pk[NV * P::K_LEN], q2[NV][P::Q2_LEN], q1[NV][P::Q1_LEN];
-        predict_fw_rec<D>(xs, mom, vc, Fc, z, mu, kap, im, dt, pf, pk, P::K_LEN, sa);
+        predict_fw_rec<D>(xs, mom, vc, Fc, z, mu, kap, im, dt, pf, pk, P::K_LEN, sa, sg, ec);
         double ldv[D] = {};
         for (int k = 0; k < NV; ++k) {
-            predict_corner2_vjp<D>(pf, pk + k * P::K_LEN, k, mu, kap, dt, lR + k * D, lM + k * NS, q2[k], sa);
+            predict_corner2_vjp<D>(pf, pk + k * P::K_LEN, k, mu, kap, dt, lR + k * D, lM + k * NS, q2[k], sa, sg);
             for (int a = 0; a < D; ++a) ldv[a] += q2[k][P::Q2_LV + a];
         }
         const double hv = -0.5 * dt * im * (1.0 / D);
         double lacc[D];
         for (int a = 0; a < D; ++a) lacc[a] = hv * ldv[a];
-        for (int k = 0; k < NV; ++k) predict_corner1_vjp<D>(pf, pk + k * P::K_LEN, k, mu, kap, lacc, q1[k], sa);
+        for (int k = 0; k < NV; ++k) predict_corner1_vjp<D>(pf, pk + k * P::K_LEN, k, mu, kap, lacc, q1[k], sa, sg);
         for (int k = 0; k < NV; ++k) {
             lmu += q2[k][P::Q2_MU] + q1[k][P::Q1_MU];
             lkap += q2[k][P::Q2_KAP] + q1[k][P::Q1_KAP];
@@ -1337,12 +1530,12 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
         double lxcc[D] = {};
         auto q2k = [&](int k) { return (const double *)q2[k]; };
         auto q1k = [&](int k) { return (const double *)q1[k]; };
-        predict_finish_vjp<D>(mom, vc, Fc, dt, pf, q2k, q1k, lxs, lxcc, mout, lvc, lFc);
+        predict_finish_vjp<D>(mom, vc, Fc, dt, pf, q2k, q1k, lxs, lxcc, mout, lvc, lFc, sg, mu, sa, im, &lmu, le);
         predict_tail_p1_vjp<D>(xs, z, pf, [&](int k) { return (const double *)(lM + k * NS); }, q2k, q1k, lxcc, lxs,
                                lz);
         return;
     }
-    predict_p0_vjp<D>(xs, vc, Fc, z, mu, kap, lM, lR, lxs, mout, lvc, lFc, lz, lmu, lkap, sa);
+    predict_p0_vjp<D>(xs, vc, Fc, z, mu, kap, lM, lR, lxs, mout, lvc, lFc, lz, lmu, lkap, sa, sg, ec, le);
 }
 
 // the product for a first-order cell: R_k = M_k v_c + (1/D) T(F_c) N_k (lM [NV][NS] is
@@ -1350,7 +1543,8 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
 template <int D, class MO>
 LMOOD_HD void predict_p0_vjp(const double *xs, const double *vc, const double *Fc, double z, double mu, double kap,
                              double *lM, const double *lR, double *lxs, MO &&mout, double *lvc, double *lFc,
-                             double &lz, double &lmu, double &lkap, double sa) {
+                             double &lz, double &lmu, double &lkap, double sa, const SgMat *sg, double ec,
+                             double *le) {
     using Q = Sz<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NM = Q::NMOM;
     double V, N[NV * D], inu[NV], lN[NV * D] = {}, lxcc[D] = {};
@@ -1384,7 +1578,16 @@ LMOOD_HD void predict_p0_vjp(const double *xs, const double *vc, const double *F
                 lT[a * D + b] += l * N[k * D + b] * (1.0 / D);
             }
         }
-    stress_m_vjp<D>(Fc, mu, kap, sa, lT, lF, lmu, lkap, T);
+    double eps = 0.0, leps = 0.0;  // the stiffened gas: eps = e - |v|^2 / 2
+    if (sg) {
+        eps = ec;
+        for (int a = 0; a < D; ++a) eps -= 0.5 * vc[a] * vc[a];
+    }
+    stress_x_vjp<D>(Fc, mu, kap, sa, sg, eps, lT, lF, lmu, lkap, leps, T);
+    if (sg) {
+        *le += leps;
+        for (int a = 0; a < D; ++a) lvc[a] -= leps * vc[a];
+    }
     for (int k = 0; k < NV; ++k)
         for (int a = 0; a < D; ++a)
             for (int b = 0; b < D; ++b) lN[k * D + b] += lR[k * D + a] * T[a * D + b] * (1.0 / D);
@@ -1402,17 +1605,20 @@ LMOOD_HD void predict_p0_vjp(const double *xs, const double *vc, const double *F
 template <int D>
 LMOOD_HD void update_fw(const double *xs0, const double *xs1, const double *vs, const double *vp0, const double *vp1,
                         const double *M, const double *R, const double *v, const double *F, double m, double im,
-                        double mu, double kap, double dt, int ord, double *v1, double *F1, double &z1) {
+                        double mu, double kap, double dt, int ord, double *v1, double *F1, double &z1,
+                        double e = 0.0, double *e1 = nullptr) {
     using Q = Sz<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS;
-    double sf[D] = {};
+    double sf[D] = {}, sfv = 0.0;
     for (int k = 0; k < NV; ++k)
         for (int a = 0; a < D; ++a) {
             double s = -R[k * D + a];
             for (int b = 0; b < D; ++b) s += M[k * NS + sym<D>(a, b)] * vs[k * D + b];
             sf[a] += s;
+            sfv += s * vs[k * D + a];
         }
     for (int a = 0; a < D; ++a) v1[a] = v[a] + dt * im * sf[a];
+    if (e1) *e1 = e + dt * im * sfv;  // e^{n+1} = e^n + dt/m sum_k f_k . v*_k
     double V0, N0[NV * D], V1, N1[NV * D];
     faces<D>(xs0, V0, N0);
     faces<D>(xs1, V1, N1);
@@ -1437,22 +1643,35 @@ LMOOD_HD void update_fw(const double *xs0, const double *xs1, const double *vs, 
     z1 = impedance<D>(F1, m / V1, mu, kap);
 }
 
-// Product of update_fw in two parts. The velocity part, v1 = v + dt im sum_k (M_k vs_k - R_k):
-// accumulates lvs [NV][D], lM [NV][NS], lR [NV][D] and lv [D] from lv1.
+// Product of update_fw in two parts. The velocity part, v1 = v + dt im sum_k f_k with
+// f_k = M_k vs_k - R_k, and (R given) the energy e1 = e + dt im sum_k f_k . vs_k:
+// accumulates lvs [NV][D], lM [NV][NS], lR [NV][D] and lv [D] from lv1 and le1 (the
+// adjoint of e^n is le1 itself).
 template <int D>
 LMOOD_HD void update_force_vjp(const double *vs, const double *M, double im, double dt, const double *lv1,
-                               double *lvs, double *lM, double *lR, double *lv) {
+                               double *lvs, double *lM, double *lR, double *lv, double le1 = 0.0,
+                               const double *R = nullptr) {
     constexpr int NV = D + 1, NS = D * (D + 1) / 2;
     for (int a = 0; a < D; ++a) lv[a] += lv1[a];
-    for (int k = 0; k < NV; ++k)
+    const double dtm = dt * im;
+    for (int k = 0; k < NV; ++k) {
+        double fk[D];
+        if (R)
+            for (int a = 0; a < D; ++a) {
+                double s = -R[k * D + a];
+                for (int b = 0; b < D; ++b) s += M[k * NS + sym<D>(a, b)] * vs[k * D + b];
+                fk[a] = s;
+            }
         for (int a = 0; a < D; ++a) {
-            const double lf = dt * im * lv1[a];
+            const double lf = dtm * (R ? lv1[a] + le1 * vs[k * D + a] : lv1[a]);
             lR[k * D + a] -= lf;
             for (int b = 0; b < D; ++b) {
                 lM[k * NS + sym<D>(a, b)] += lf * vs[k * D + b];
                 lvs[k * D + b] += M[k * NS + sym<D>(a, b)] * lf;
             }
+            if (R) lvs[k * D + a] += dtm * le1 * fk[a];
         }
+    }
 }
 
 // The deformation part (F^{n+1} from the velocity gradients at both levels, or the first-order
@@ -1570,10 +1789,9 @@ LMOOD_HD void update_vjp(const double *xs0, const double *xs1, const double *vs,
                          const double *M, const double *R, const double *v, const double *F, double m, double im,
                          double mu, double kap, double dt, int ord, const double *lv1, const double *lF1, double lz1,
                          double *lxs0, double *lxs1, double *lvs, double *lvp0, double *lvp1, double *lM, double *lR,
-                         double *lv, double *lF, double &lmu, double &lkap) {
-    (void)R;
+                         double *lv, double *lF, double &lmu, double &lkap, double le1 = 0.0) {
     (void)v;
-    update_force_vjp<D>(vs, M, im, dt, lv1, lvs, lM, lR, lv);
+    update_force_vjp<D>(vs, M, im, dt, lv1, lvs, lM, lR, lv, le1, R);
     const double *in[5] = {vs, xs0, xs1, vp0, vp1};
     double *acc[5] = {lvs, lxs0, lxs1, lvp0, lvp1};
     update_deform_vjp<D>([&](int i, double *u) { for (int j = 0; j < (D + 1) * D; ++j) u[j] = in[i][j]; },

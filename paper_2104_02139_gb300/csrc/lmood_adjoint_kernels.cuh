@@ -34,7 +34,8 @@ template <int D> __device__ __forceinline__ double kappa_mu_factor(const Prm &pr
 }
 
 // ---------------------------------------------------------------------------------------
-template <int D> __global__ void __launch_bounds__(128) k_adj_update(Geo g, Fld f, Prm prm, AdjBuf a) {
+// E: the energy adjoint is carried (a.lE1, a.lE0): the energy equation's terms join the force part
+template <int D, bool E> __global__ void __launch_bounds__(128) k_adj_update(Geo g, Fld f, Prm prm, AdjBuf a) {
     using Q = adj::Sz<D>;
     using R = AdjRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NX = NV * D;
@@ -46,14 +47,22 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_update(Geo g, Fld 
     // the velocity part first: its adjoints go to the corner records and lv0 at once, so that
     // none of its values is live in the deformation part
     {
-        double vs[NX], M[NV * NS], lv1[D], lvs[NX] = {}, lv[D] = {}, lM[NV * NS] = {}, lR[NX] = {};
+        double vs[NX], M[NV * NS], lv1[D], lvs[NX] = {}, lv[D] = {}, lM[NV * NS] = {}, lR[NX] = {}, Rk[E ? NX : 1];
         for (int k = 0; k < NV; ++k) {
             const int p = g.c2n[k * N + c];
             for (int b = 0; b < D; ++b) vs[k * D + b] = f.vs[b * Np + p];
             for (int s = 0; s < NS; ++s) M[k * NS + s] = f.pkM[s * NC + k * N + c];
+            if (E)
+                for (int b = 0; b < D; ++b) Rk[k * D + b] = f.pkR[b * NC + k * N + c];
         }
         for (int b = 0; b < D; ++b) lv1[b] = a.lv1[b * N + c];
-        adj::update_force_vjp<D>(vs, M, f.im[c], dt, lv1, lvs, lM, lR, lv);
+        if (E) {
+            const double le1 = a.lE1[c];
+            adj::update_force_vjp<D>(vs, M, f.im[c], dt, lv1, lvs, lM, lR, lv, le1, Rk);
+            a.lE0[c] = le1;  // e^{n+1} = e^n + ...
+        } else {
+            adj::update_force_vjp<D>(vs, M, f.im[c], dt, lv1, lvs, lM, lR, lv);
+        }
         for (int k = 0; k < NV; ++k) {
             double *r = a.cr + (size_t)(k * N + c) * R::CR;
             for (int s = 0; s < NS; ++s) r[R::CR_M + s] = lM[k * NS + s];
@@ -189,9 +198,11 @@ template <int D> __device__ __forceinline__ bool second_order(const Fld &f, int 
     return !force_p0 && f.order[c] != 1;
 }
 
-// FAM: the shear energy family (a = prm.shear_a); else the neo-Hookean law, whose instance
-// compiles no family code
-template <int D, bool FAM> __global__ void __launch_bounds__(128) k_adj_pred_fw(Geo g, Fld f, Prm prm, AdjBuf a) {
+// MAT: 0 the neo-Hookean law, 1 the shear energy family (a = prm.shear_a), 2 the stiffened gas
+// (with that shear energy); the neo-Hookean instances compile no code of the others
+template <int MAT> __device__ __forceinline__ double mat_a(const Prm &prm) { return MAT ? prm.shear_a : -1.0; }
+
+template <int D, int MAT> __global__ void __launch_bounds__(128) k_adj_pred_fw(Geo g, Fld f, Prm prm, AdjBuf a) {
     using Q = adj::Sz<D>;
     using P = adj::PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NX = NV * D;
@@ -209,11 +220,13 @@ template <int D, bool FAM> __global__ void __launch_bounds__(128) k_adj_pred_fw(
     for (int b = 0; b < D; ++b) vc[b] = f.v[b * N + c];
     for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
     const double mu = f.mu[c], kap = kappa_of(prm, mu), dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
+    const adj::SgMat sgm{prm.gamma, prm.pinf, prm.rho0};
     adj::predict_fw_rec<D>(xs, mom, vc, Fc, f.z[c], mu, kap, f.im[c], dt, a.pf + (size_t)c * P::F_LEN,
-                           a.pk + (size_t)c * P::K_LEN, (long)N * P::K_LEN, FAM ? prm.shear_a : -1.0);
+                           a.pk + (size_t)c * P::K_LEN, (long)N * P::K_LEN, mat_a<MAT>(prm), MAT == 2 ? &sgm : nullptr,
+                           f.e[c]);
 }
 
-template <int D, bool FAM> __global__ void __launch_bounds__(128) k_adj_pred_c2(Geo g, Fld f, Prm prm, AdjBuf a) {
+template <int D, int MAT> __global__ void __launch_bounds__(128) k_adj_pred_c2(Geo g, Fld f, Prm prm, AdjBuf a) {
     using R = AdjRec<D>;
     using P = adj::PredRec<D>;
     constexpr int NS = R::NS;
@@ -223,16 +236,17 @@ template <int D, bool FAM> __global__ void __launch_bounds__(128) k_adj_pred_c2(
     const int c = cell_of_corner<D>(cid, N), k = (cid - c) / N;
     if (!second_order<D>(f, c, 0)) return;
     const double mu = f.mu[c], kap = kappa_of(prm, mu), dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
+    const adj::SgMat sgm{prm.gamma, prm.pinf, prm.rho0};
     double *cr = a.cr + (size_t)cid * R::CR;
     double lR[D], lM[NS];
     for (int b = 0; b < D; ++b) lR[b] = cr[R::CR_R + b];
     for (int s2 = 0; s2 < NS; ++s2) lM[s2] = cr[R::CR_M + s2];
     adj::predict_corner2_vjp<D>(a.pf + (size_t)c * P::F_LEN, a.pk + (size_t)cid * P::K_LEN, k, mu, kap, dt, lR, lM,
-                                a.q2 + (size_t)cid * P::Q2_LEN, FAM ? prm.shear_a : -1.0);
+                                a.q2 + (size_t)cid * P::Q2_LEN, mat_a<MAT>(prm), MAT == 2 ? &sgm : nullptr);
     for (int s2 = 0; s2 < NS; ++s2) cr[R::CR_M + s2] = lM[s2];
 }
 
-template <int D, bool FAM> __global__ void __launch_bounds__(128) k_adj_pred_c1(Geo g, Fld f, Prm prm, AdjBuf a) {
+template <int D, int MAT> __global__ void __launch_bounds__(128) k_adj_pred_c1(Geo g, Fld f, Prm prm, AdjBuf a) {
     using P = adj::PredRec<D>;
     const int N = g.N;
     const int cid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -240,6 +254,7 @@ template <int D, bool FAM> __global__ void __launch_bounds__(128) k_adj_pred_c1(
     const int c = cell_of_corner<D>(cid, N), k = (cid - c) / N;
     if (!second_order<D>(f, c, 0)) return;
     const double mu = f.mu[c], kap = kappa_of(prm, mu), dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
+    const adj::SgMat sgm{prm.gamma, prm.pinf, prm.rho0};
     // the adjoint of dv = hv sum_k T(F_h,k) N_k is the sum of the corners' lv*
     double lacc[D] = {};
     for (int kk = 0; kk <= D; ++kk)
@@ -247,7 +262,7 @@ template <int D, bool FAM> __global__ void __launch_bounds__(128) k_adj_pred_c1(
     const double hv = -0.5 * dt * f.im[c] * (1.0 / D);
     for (int b = 0; b < D; ++b) lacc[b] *= hv;
     adj::predict_corner1_vjp<D>(a.pf + (size_t)c * P::F_LEN, a.pk + (size_t)cid * P::K_LEN, k, mu, kap, lacc,
-                                a.q1 + (size_t)cid * P::Q1_LEN, FAM ? prm.shear_a : -1.0);
+                                a.q1 + (size_t)cid * P::Q1_LEN, mat_a<MAT>(prm), MAT == 2 ? &sgm : nullptr);
 }
 
 // node-moment adjoint writer of cell c: the parts equal at every corner (lT, lS2) into the
@@ -290,7 +305,7 @@ __device__ __forceinline__ void adj_predict_out(const AdjBuf &a, const Prm &prm,
 // the geometry: the slopes, dF/dt and the least squares; writes the position adjoints of
 // d_k = x_k - x_c (the corner records) and x_c (lxcc, into the pass-1 records' spare room:
 // the pass-1 records are consumed here)
-template <int D> __global__ void __launch_bounds__(128) k_adj_pred_fin(Geo g, Fld f, Prm prm, AdjBuf a) {
+template <int D, int MAT> __global__ void __launch_bounds__(128) k_adj_pred_fin(Geo g, Fld f, Prm prm, AdjBuf a) {
     using Q = adj::Sz<D>;
     using R = AdjRec<D>;
     using P = adj::PredRec<D>;
@@ -305,17 +320,20 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_pred_fin(Geo g, Fl
     for (int b = 0; b < D; ++b) vc[b] = f.v[b * N + c];
     for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
     const double dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
-    double lxs[NX] = {}, lxcc[D] = {}, lvc[D] = {}, lF[DD] = {}, lmu = 0.0, lkap = 0.0;
+    double lxs[NX] = {}, lxcc[D] = {}, lvc[D] = {}, lF[DD] = {}, lmu = 0.0, lkap = 0.0, le = 0.0;
     for (int k = 0; k < NV; ++k) {
         const double *q2 = a.q2 + (size_t)(k * N + c) * P::Q2_LEN, *q1 = a.q1 + (size_t)(k * N + c) * P::Q1_LEN;
         lmu += q2[P::Q2_MU] + q1[P::Q1_MU];
         lkap += q2[P::Q2_KAP] + q1[P::Q1_KAP];
     }
+    const adj::SgMat sgm{prm.gamma, prm.pinf, prm.rho0};
     adj::predict_finish_vjp<D>(
         mom, vc, Fc, dt, a.pf + (size_t)c * P::F_LEN,
         [&](int k) { return (const double *)(a.q2 + (size_t)(k * N + c) * P::Q2_LEN); },
         [&](int k) { return (const double *)(a.q1 + (size_t)(k * N + c) * P::Q1_LEN); }, lxs, lxcc,
-        MomOut<D>{a.cp, a.cc + (size_t)c * R::CC, N, c}, lvc, lF);
+        MomOut<D>{a.cp, a.cc + (size_t)c * R::CC, N, c}, lvc, lF, MAT == 2 ? &sgm : nullptr, f.mu[c],
+        mat_a<MAT>(prm), f.im[c], &lmu, &le);
+    if (MAT == 2) a.lE0[c] += le;
     for (int k = 0; k < NV; ++k)
         for (int b = 0; b < D; ++b) a.cp[(size_t)(k * N + c) * R::CP + R::CP_X + b] = lxs[k * D + b];
     // lxcc for the tail, in the first corner's pass-1 record (its lF_h is consumed)
@@ -326,7 +344,7 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_pred_fin(Geo g, Fl
 }
 
 // the whole product of a first-order cell (force_p0: every cell, the t^0 packets)
-template <int D, bool FAM>
+template <int D, int MAT>
 __global__ void __launch_bounds__(128) k_adj_predict(Geo g, Fld f, Prm prm, AdjBuf a, int force_p0) {
     using Q = adj::Sz<D>;
     using R = AdjRec<D>;
@@ -345,10 +363,12 @@ __global__ void __launch_bounds__(128) k_adj_predict(Geo g, Fld f, Prm prm, AdjB
     for (int b = 0; b < D; ++b) vc[b] = f.v[b * N + c];
     for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
     const double mu = f.mu[c], kap = kappa_of(prm, mu);
-    double lxs[NX] = {}, lvc[D] = {}, lF[DD] = {}, lz = 0.0, lmu = 0.0, lkap = 0.0;
+    const adj::SgMat sgm{prm.gamma, prm.pinf, prm.rho0};
+    double lxs[NX] = {}, lvc[D] = {}, lF[DD] = {}, lz = 0.0, lmu = 0.0, lkap = 0.0, le = 0.0;
     adj::predict_p0_vjp<D>(xs, vc, Fc, f.z[c], mu, kap, lM, lR, lxs, MomOut<D>{a.cp, a.cc + (size_t)c * R::CC, N, c},
-                           lvc, lF, lz, lmu, lkap, FAM ? prm.shear_a : -1.0);
+                           lvc, lF, lz, lmu, lkap, mat_a<MAT>(prm), MAT == 2 ? &sgm : nullptr, f.e[c], &le);
     adj_predict_out<D>(a, prm, N, c, lxs, lvc, lF, lz, lmu, lkap);
+    if (MAT == 2) a.lE0[c] += le;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -381,7 +401,8 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_momsum(Geo g, AdjB
 // per cell: the reverse of the node moments at its corners (the cell as a neighbour of each
 // of its nodes), of its centroid x_c = mean of its nodes, and of the impedance
 // z^n = Z(F^n, m / V(x^n), mu)
-template <int D> __global__ void __launch_bounds__(128) k_adj_cells(Geo g, Fld f, Prm prm, AdjBuf a, int tail) {
+// SG: the stiffened gas (its impedance depends on the energy)
+template <int D, bool SG> __global__ void __launch_bounds__(128) k_adj_cells(Geo g, Fld f, Prm prm, AdjBuf a, int tail) {
     using Q = adj::Sz<D>;
     using R = AdjRec<D>;
     using P = adj::PredRec<D>;
@@ -420,7 +441,16 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_cells(Geo g, Fld f
     double V, Nf[NX];
     adj::faces<D>(xs, V, Nf);
     const double mu = f.mu[c], kap = kappa_of(prm, mu);
-    adj::impedance_vjp<D>(F, f.m[c] / V, mu, kap, a.lz0[c], lF, lrho, lmu, lkap);
+    if (SG) {  // z = z(F, rho, mu, eps), eps = e - |v|^2 / 2
+        const adj::SgMat sgm{prm.gamma, prm.pinf, prm.rho0};
+        double eps = f.e[c], leps = 0.0;
+        for (int b = 0; b < D; ++b) eps -= 0.5 * q[b] * q[b];
+        adj::impedance_sg_a_vjp<D>(F, f.m[c] / V, mu, prm.shear_a, sgm, eps, a.lz0[c], lF, lrho, lmu, leps);
+        a.lE0[c] += leps;
+        for (int b = 0; b < D; ++b) a.lv0[b * N + c] -= leps * q[b];
+    } else {
+        adj::impedance_vjp<D>(F, f.m[c] / V, mu, kap, a.lz0[c], lF, lrho, lmu, lkap);
+    }
     for (int i = 0; i < DD; ++i) a.lF0[i * N + c] += lF[i] + lq[D + i];
     a.lmu[c] += lmu + lkap * kappa_mu_factor<D>(prm);
     const double lV = lrho * (-f.m[c] / (V * V));
@@ -485,7 +515,16 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_z0(Geo g, Fld f, P
     for (int q = 0; q < DD; ++q) F[q] = f.F[q * N + c];
     adj::faces<D>(xs, V, Nf);
     const double mu = f.mu[c], kap = kappa_of(prm, mu);
-    adj::impedance_vjp<D>(F, f.m[c] / V, mu, kap, a.lz0[c], lF, lrho, lmu, lkap);
+    if (prm.eos) {  // the stiffened gas: z depends on eps = e - |v|^2 / 2
+        const adj::SgMat sgm{prm.gamma, prm.pinf, prm.rho0};
+        double eps = f.e[c], leps = 0.0;
+        for (int b = 0; b < D; ++b) eps -= 0.5 * f.v[b * N + c] * f.v[b * N + c];
+        adj::impedance_sg_a_vjp<D>(F, f.m[c] / V, mu, prm.shear_a, sgm, eps, a.lz0[c], lF, lrho, lmu, leps);
+        a.lE0[c] += leps;
+        for (int b = 0; b < D; ++b) a.lv0[b * N + c] -= leps * f.v[b * N + c];
+    } else {
+        adj::impedance_vjp<D>(F, f.m[c] / V, mu, kap, a.lz0[c], lF, lrho, lmu, lkap);
+    }
     for (int q = 0; q < DD; ++q) a.lF0[q * N + c] += lF[q];
     a.lmu[c] += lmu + lkap * kappa_mu_factor<D>(prm);
     // rho = m / V at fixed m: the positions' part, added to the corners' records of the t^0
@@ -495,6 +534,35 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_z0(Geo g, Fld f, P
     adj::faces_vjp<D>(xs, -lrho * f.m[c] / (V * V), lN0, lxs);
     for (int k = 0; k < NV; ++k)
         for (int b = 0; b < D; ++b) a.cp[(size_t)(k * N + c) * R::CP + R::CP_X + b] += lxs[k * D + b];
+}
+
+// the initial energy e^0 = |v|^2 / 2 + Psi(F) (Eq. EOS_neoHook with the family's shear energy)
+// or, for the stiffened gas, |v|^2 / 2 + eps_v(F) + Psi_s(F) with eps_v the volumetric energy of
+// the pressure p0 at rho0 / det F: its adjoint (lE0) moved to v, F, mu
+template <int D> __global__ void __launch_bounds__(128) k_adj_e0(Geo g, Fld f, Prm prm, AdjBuf a) {
+    constexpr int DD = D * D;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    const int N = g.N;
+    const double le = a.lE0[c];
+    double F[DD], lF[DD] = {}, lmu = 0.0;
+    for (int q = 0; q < DD; ++q) F[q] = f.F[q * N + c];
+    const double mu = f.mu[c];
+    for (int b = 0; b < D; ++b) a.lv0[b * N + c] += le * f.v[b * N + c];
+    adj::shear_energy_a_vjp<D>(F, prm.rho0, mu, prm.shear_a, le, lF, lmu);
+    double C[DD];
+    adj::cofactor<D>(F, C);
+    const double J = adj::det<D>(F);
+    double lJ;
+    if (prm.eos) {  // eps_v = (p0 + gam pinf) J / ((gam - 1) rho0)
+        lJ = le * (prm.p0 + prm.gamma * prm.pinf) / ((prm.gamma - 1.0) * prm.rho0);
+    } else {  // Psi_v = kap / (4 rho0) ((J - 1)^2 + log^2 J)
+        const double kap = kappa_of(prm, mu), lj = adj::adj_log(J);
+        lJ = le * kap / (4.0 * prm.rho0) * (2.0 * (J - 1.0) + 2.0 * lj / J);
+        lmu += le * ((J - 1.0) * (J - 1.0) + lj * lj) / (4.0 * prm.rho0) * kappa_mu_factor<D>(prm);
+    }
+    for (int q = 0; q < DD; ++q) a.lF0[q * N + c] += lF[q] + lJ * C[q];
+    a.lmu[c] += lmu;
 }
 
 }  // namespace lmood

@@ -418,6 +418,10 @@ extern "C" lmood_status lmood_mesh_create(int dim, int64_t n_nodes, const double
 extern "C" lmood_status lmood_mesh_destroy(lmood_mesh m) {
     if (!m) return fail(LMOOD_ERR_ARG, "lmood_mesh_destroy: NULL");
     cudaStreamSynchronize(m->st);
+    for (lmood_state s : m->states) {  // destroyed out of order: the states can only be destroyed now
+        s->M = nullptr;
+        s->broken = true;
+    }
     m->mem.release();
     delete m;
     return LMOOD_OK;
@@ -554,7 +558,12 @@ static Prm kernel_params(const lmood_params &p, const lmood_material &m) {
 }
 
 static void state_free(lmood_state s) {
-    if (s->M) cudaStreamSynchronize(s->M->st);
+    tapes_orphan(s);
+    if (s->M) {
+        cudaStreamSynchronize(s->M->st);
+        auto &v = s->M->states;
+        v.erase(std::remove(v.begin(), v.end(), s), v.end());
+    }
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
     for (int p = 0; p < 2; ++p) {
         if (s->gexec[p]) cudaGraphExecDestroy(s->gexec[p]);
@@ -760,6 +769,7 @@ static lmood_status state_init(lmood_mesh M, const lmood_material *mat, const do
         return r;
     }
     s->at_init = true;
+    M->states.push_back(s);
     *out = s;
     return LMOOD_OK;
 }
@@ -1321,6 +1331,7 @@ static lmood_status set_target(lmood_state s, int field, void **dst, size_t *byt
 
 extern "C" lmood_status lmood_get_fields(lmood_state s, int n, const int *fields, void *const *dst, int is_device) {
     if (!s || n < 0 || (n > 0 && (!fields || !dst))) return fail(LMOOD_ERR_ARG, "lmood_get_fields: bad argument");
+    if (!s->M) return fail(LMOOD_ERR_STATE, "lmood_get_fields: the state's mesh was destroyed");
     for (int i = 0; i < n; ++i) {
         if (!dst[i]) return fail(LMOOD_ERR_ARG, "lmood_get_fields: NULL destination");
         if (fields[i] < 0 || fields[i] > LMOOD_FIELD_DT) return fail(LMOOD_ERR_ARG, "lmood_get_fields: unknown field id");
@@ -1342,6 +1353,7 @@ extern "C" lmood_status lmood_get_fields(lmood_state s, int n, const int *fields
 
 extern "C" lmood_status lmood_set_fields(lmood_state s, int n, const int *fields, const void *const *src, int is_device) {
     if (!s || n < 0 || (n > 0 && (!fields || !src))) return fail(LMOOD_ERR_ARG, "lmood_set_fields: bad argument");
+    if (!s->M) return fail(LMOOD_ERR_STATE, "lmood_set_fields: the state's mesh was destroyed");
     for (int i = 0; i < n; ++i) {  // validate everything before the first copy
         void *dst = nullptr;
         size_t bytes = 0;
@@ -1352,8 +1364,11 @@ extern "C" lmood_status lmood_set_fields(lmood_state s, int n, const int *fields
     lmood_mesh M = s->M;
     cudaStream_t st = M->st;
     auto is_geo = [&](int i) { return fields[i] == LMOOD_FIELD_X || fields[i] == LMOOD_FIELD_F; };
-    int n_geo = 0;
-    for (int i = 0; i < n; ++i) n_geo += is_geo(i);
+    int n_geo = 0, n_eps = 0;  // (the stiffened gas's impedance depends on eps = e - |v|^2 / 2 too)
+    for (int i = 0; i < n; ++i) {
+        n_geo += is_geo(i);
+        n_eps += s->mat.eos != 0 && (fields[i] == LMOOD_FIELD_V || fields[i] == LMOOD_FIELD_E);
+    }
     // derived cell geometry, density and impedance from the new x and F; the refresh reads
     // nothing else for the volumetric law of Eq. EOS_neoHook, so it runs on a side stream while
     // the other fields are copied (the stiffened gas's impedance also needs v and e)
@@ -1385,7 +1400,7 @@ extern "C" lmood_status lmood_set_fields(lmood_state s, int n, const int *fields
         }
     }
     if (side) LM_CUDA(cudaStreamWaitEvent(st, s->set_ev[1], 0));
-    else if (n_geo > 0) refresh(st);
+    else if (n_geo > 0 || n_eps > 0) refresh(st);
     if (!is_device) return sync_check(s, "lmood_set_fields");
     return LMOOD_OK;
 }
@@ -1402,6 +1417,7 @@ extern "C" lmood_status lmood_set(lmood_state s, int field, const void *src, int
 
 extern "C" lmood_status lmood_totals(lmood_state s, double *out5) {
     if (!s || !out5) return fail(LMOOD_ERR_ARG, "lmood_totals: NULL argument");
+    if (!s->M) return fail(LMOOD_ERR_STATE, "lmood_totals: the state's mesh was destroyed");
     cudaStream_t st = s->M->st;
     LM_CUDA(cudaMemsetAsync(s->totals, 0, 5 * sizeof(double), st));
     s->M->ops->totals(s->M->geo, s->f, s->totals, st);
@@ -1664,6 +1680,7 @@ extern "C" lmood_status lmood_autotune_schedule(lmood_state s, int reps, double 
 
 extern "C" lmood_status lmood_timing(lmood_state s, int enable) {
     if (!s) return fail(LMOOD_ERR_ARG, "lmood_timing: NULL state");
+    if (!s->M) return fail(LMOOD_ERR_STATE, "lmood_timing: the state's mesh was destroyed");
     if (enable && s->ev.empty()) {
         s->ev.resize(2 * kMaxPending);
         for (auto &e : s->ev) LM_CUDA(cudaEventCreate(&e));
@@ -1682,6 +1699,7 @@ extern "C" lmood_status lmood_timing(lmood_state s, int enable) {
 
 extern "C" lmood_status lmood_timing_read(lmood_state s, double *ms, int64_t *launches) {
     if (!s || !ms || !launches) return fail(LMOOD_ERR_ARG, "lmood_timing_read: NULL argument");
+    if (!s->M) return fail(LMOOD_ERR_STATE, "lmood_timing_read: the state's mesh was destroyed");
     for (int i = 0; i < LMOOD_NK; ++i) {
         ms[i] = s->kms[i];
         launches[i] = s->klaunch[i];

@@ -69,11 +69,14 @@ struct lmood_mesh_s {
     double *d_bct = nullptr, *d_bfval = nullptr, *d_contact = nullptr;
     bool has_ext = false;         // some face has a traction / pressure / velocity / contact tag
     uint64_t bc_version = 0;      // counts the changes of boundary values, tags and contact walls
+    std::vector<lmood_state_s *> states;  // the live states on this mesh (orphaned when it goes)
     lmood::DevAllocs mem;
 };
 
+struct lmood_tape_s;
 struct lmood_state_s {
-    lmood_mesh M = nullptr;
+    lmood_mesh M = nullptr;          // NULL once the mesh was destroyed first: unusable but destroyable
+    std::vector<lmood_tape_s *> tapes;  // the live tapes of this state (orphaned when it goes)
     lmood_params prm{};
     lmood_material mat{};
     lmood::Prm kp{};
@@ -129,4 +132,9 @@ void swap_state(lmood_state s);
 // synchronises the mesh stream; a CUDA error marks the state unusable
 lmood_status sync_check(lmood_state s, const char *where);
 
+}  // namespace lmood
+
+namespace lmood {
+// the state is going: its remaining tapes become orphans (destroyable, nothing else)
+void tapes_orphan(lmood_state_s *s);
 }  // namespace lmood

@@ -14,6 +14,7 @@
 #include <string>
 
 #include "lmood_adj_ops.h"
+#include "lmood_adjoint.cuh"
 #include "lmood_internal.h"
 
 using namespace lmood;
@@ -183,6 +184,7 @@ void reverse_step(lmood_tape t, AdjBuf &a, const Fld &f) {
     ao.gather(M->geo, a, st);
     std::swap(a.lv0, a.lv1);
     std::swap(a.lF0, a.lF1);
+    std::swap(a.lE0, a.lE1);
     std::swap(a.lx0, a.lx1);
     std::swap(a.lvp0, a.lvp1);
 }
@@ -203,12 +205,21 @@ lmood_status copy_out(double *dst, const double *src, int64_t n, int is_device, 
 }
 
 void tape_free(lmood_tape t) {
-    if (t->s && t->s->M) cudaStreamSynchronize(t->s->M->st);
+    if (t->s) {
+        if (t->s->M) cudaStreamSynchronize(t->s->M->st);
+        auto &v = t->s->tapes;
+        v.erase(std::remove(v.begin(), v.end(), t), v.end());
+    }
     t->mem.release();
     delete t;
 }
 
 }  // namespace
+
+void lmood::tapes_orphan(lmood_state_s *s) {
+    for (lmood_tape t : s->tapes) t->s = nullptr;
+    s->tapes.clear();
+}
 
 extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_t checkpoint_every, lmood_tape *out,
                                           lmood_step_info *last) {
@@ -219,9 +230,6 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     if (n_steps < 1 || checkpoint_every < 0)
         return fail(LMOOD_ERR_ARG, "lmood_tape_record: n_steps must be >= 1 and checkpoint_every >= 0");
     lmood_mesh M = s->M;
-    if (s->mat.eos != 0)
-        return fail(LMOOD_ERR_ARG, "lmood_tape_record: the adjoint covers the volumetric law of Eq. EOS_neoHook "
-                                   "(any a of the shear energy family) only, not the stiffened gas");
     const int D = M->dim, NV = D + 1, NS = D * (D + 1) / 2, DD = D * D;
     const int64_t N = M->nc, Np = M->np, NC = NV * N;
     const int nmom = M->ops->nmom;
@@ -262,6 +270,8 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     A((void **)&a.lF1, DD * N * nd);
     A((void **)&a.lF0, DD * N * nd);
     A((void **)&a.lz0, N * nd);
+    A((void **)&a.lE1, N * nd);
+    A((void **)&a.lE0, N * nd);
     A((void **)&a.lmu, N * nd);
     A((void **)&a.lx1, D * Np * nd);
     A((void **)&a.lx0, D * Np * nd);
@@ -273,8 +283,10 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     A((void **)&a.cc, (size_t)CC * N * nd);
     A((void **)&a.cd, (size_t)D * NC * nd);
     {
-        const int FL = (D + DD) * D + DD + (D + 1) * D + DD + (D + 1) * D + (D + 1) + 1;  // adj::PredRec<D>
-        const int KL = DD + D + NS, Q2L = 2 * D + DD + 2, Q1L = DD + D + 2;
+        const int FL = D == 2 ? adj::PredRec<2>::F_LEN : adj::PredRec<3>::F_LEN;
+        const int KL = D == 2 ? adj::PredRec<2>::K_LEN : adj::PredRec<3>::K_LEN;
+        const int Q2L = D == 2 ? adj::PredRec<2>::Q2_LEN : adj::PredRec<3>::Q2_LEN;
+        const int Q1L = D == 2 ? adj::PredRec<2>::Q1_LEN : adj::PredRec<3>::Q1_LEN;
         A((void **)&a.pf, (size_t)FL * N * nd);
         A((void **)&a.pk, (size_t)KL * NC * nd);
         A((void **)&a.q2, (size_t)Q2L * NC * nd);
@@ -336,6 +348,7 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
         tape_free(t);
         return r;
     }
+    s->tapes.push_back(t);
     *out = t;
     return LMOOD_OK;
 }
@@ -344,7 +357,15 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
                                             const double *lam_v, const double *lam_F, double *grad_x,
                                             double *grad_vp, double *grad_v, double *grad_F, double *grad_mu,
                                             int is_device) {
-    if (!t || !t->s) return fail(LMOOD_ERR_ARG, "lmood_tape_backward: NULL tape");
+    return lmood_tape_backward_e(t, lam_x, lam_vp, lam_v, lam_F, nullptr, grad_x, grad_vp, grad_v, grad_F, nullptr,
+                                 grad_mu, is_device);
+}
+
+extern "C" lmood_status lmood_tape_backward_e(lmood_tape t, const double *lam_x, const double *lam_vp,
+                                              const double *lam_v, const double *lam_F, const double *lam_e,
+                                              double *grad_x, double *grad_vp, double *grad_v, double *grad_F,
+                                              double *grad_e, double *grad_mu, int is_device) {
+    if (!t || !t->s) return fail(LMOOD_ERR_ARG, "lmood_tape_backward: NULL tape, or its state was destroyed");
     lmood_state s = t->s;
     if (s->broken) return fail(LMOOD_ERR_STATE, "lmood_tape_backward: state unusable after an earlier CUDA error");
     if (s->M->bc_version != t->bc_version)
@@ -357,11 +378,15 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
     Fld &f = s->f;
     const Ops &op = *M->ops;
     const AdjOps &ao = *t->aop;
-    // adjoints of the final state
+    // adjoints of the final state; the energy's only when it is given or has influence (the
+    // stiffened gas's pressure depends on it)
     AdjBuf a = t->a;
+    const bool with_e = lam_e || s->mat.eos != 0;
+    if (!with_e) a.lE0 = a.lE1 = nullptr;
     lmood_status r;
     if ((r = copy_in(a.lx1, lam_x, D * Np, is_device, st)) || (r = copy_in(a.lvp1, lam_vp, D * Np, is_device, st)) ||
-        (r = copy_in(a.lv1, lam_v, D * N, is_device, st)) || (r = copy_in(a.lF1, lam_F, D * D * N, is_device, st)))
+        (r = copy_in(a.lv1, lam_v, D * N, is_device, st)) || (r = copy_in(a.lF1, lam_F, D * D * N, is_device, st)) ||
+        (with_e && (r = copy_in(a.lE1, lam_e, N, is_device, st))))
         return r;
     LM_CUDA(cudaMemsetAsync(a.lmu, 0, N * sizeof(double), st));
     auto ck = [&](int64_t i) { return snap_at(t->ck + i * sd, D, N, Np); };
@@ -398,9 +423,11 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
         ai.lv0 = a.lv1;
         ai.lF0 = a.lF1;
         ai.lx0 = a.lx1;
+        ai.lE0 = a.lE1;
         ao.nodes(M->geo, f0, ai, 1, st);
         ao.predict(M->geo, f0, p0, ai, 1, st);
         ao.z0(M->geo, f0, p0, ai, st);
+        ao.e0(M->geo, f0, p0, ai, st);  // e^0 is a function of v, F, mu
         // the positions' part of the initial solve (packets, impedance, boundary faces; the
         // corners' records of the cell gather carry nothing here)
         LM_CUDA(cudaMemsetAsync(a.cd, 0, (size_t)D * (D + 1) * N * sizeof(double), st));
@@ -413,17 +440,23 @@ extern "C" lmood_status lmood_tape_backward(lmood_tape t, const double *lam_x, c
         s->broken = true;
         return fail(LMOOD_ERR_CUDA, std::string("lmood_tape_backward: ") + cudaGetErrorString(le));
     }
+    if (grad_e && (!with_e || t->at_init)) {  // e has no influence, or the start's e is derived
+        LM_CUDA(cudaMemsetAsync(t->a.lE1, 0, N * sizeof(double), st));
+        a.lE1 = t->a.lE1;
+    }
     if ((r = copy_out(grad_x, a.lx1, D * Np, is_device, st)) || (r = copy_out(grad_vp, a.lvp1, D * Np, is_device, st)) ||
         (r = copy_out(grad_v, a.lv1, D * N, is_device, st)) || (r = copy_out(grad_F, a.lF1, D * D * N, is_device, st)) ||
-        (r = copy_out(grad_mu, a.lmu, N, is_device, st)))
+        (r = copy_out(grad_e, a.lE1, N, is_device, st)) || (r = copy_out(grad_mu, a.lmu, N, is_device, st)))
         return r;
     if (!is_device) return sync_check(s, "lmood_tape_backward");
     return LMOOD_OK;
 }
 
 extern "C" lmood_status lmood_tape_replay(lmood_tape t, lmood_state s2, int64_t n_steps) {
-    if (!t || !t->s || !s2) return fail(LMOOD_ERR_ARG, "lmood_tape_replay: NULL argument");
-    if (s2->broken) return fail(LMOOD_ERR_STATE, "lmood_tape_replay: state unusable after an earlier CUDA error");
+    if (!t || !t->s || !s2) return fail(LMOOD_ERR_ARG, "lmood_tape_replay: NULL argument, or the tape's state was destroyed");
+    if (s2->broken || !t->s->M)
+        return fail(LMOOD_ERR_STATE, "lmood_tape_replay: a state is unusable (an earlier CUDA error, or its mesh was "
+                                     "destroyed)");
     const lmood_mesh M = s2->M, Mt = t->s->M;
     if (M->dim != Mt->dim || M->nc != Mt->nc || M->np != Mt->np || M->n_inst != Mt->n_inst)
         return fail(LMOOD_ERR_ARG, "lmood_tape_replay: the state's mesh differs in size from the tape's");

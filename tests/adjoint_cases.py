@@ -1,6 +1,6 @@
 """Small problems for the adjoint's reference checks (CPU tangent pins and GPU tests): one
-per kind of boundary face, the shear energy family, and a smooth direction of the node
-positions."""
+per kind of boundary face, the shear energy family, the stiffened gas, and a smooth direction
+of the node positions."""
 import dataclasses
 
 import numpy as np
@@ -44,3 +44,24 @@ def family_case(name):
         pb.v *= 4.0
         return dataclasses.replace(pb, shear_a=0.0)
     return dataclasses.replace(W.impact2d(n=20), shear_a=0.5)
+
+
+def sg_case(name):
+    """the stiffened gas (Eq. EOS_stiffened_gas): a 2D block pushed by a piston against an
+    outer pressure (a = -1), and a 3D block (a = 0, symmetry walls x = 0, y = 0) falling on a
+    contact floor it is within the capture distance of, as the jelly drop, in units of order
+    one"""
+    if name == "sgwave2d":
+        bc = {"x0": W.VELOCITY, "y0": W.SLIP, "y1": W.SLIP, "x1": W.PRESSURE}
+        m = W.tri_mesh(10, 11, bc=bc)
+        val = W.side_values(m, W.VELOCITY, (0.02, 0.0)) + W.side_values(m, W.PRESSURE, (0.3, 0.0))
+        p = W.cell_points(m)
+        v = 0.02 * np.stack([np.sin(np.pi * p[:, 1]), np.cos(np.pi * p[:, 0])])
+        return W.Problem("sgwave", m, 1.0, 0.0, np.full(m.n_cells, 0.1), v, 0.4, 10, bcval=val,
+                         stiffened_gas=(2.2, 1.0, 0.3))
+    m = W.tet_mesh(3, 3, 3, 10, bc={"x0": W.SLIP, "y0": W.SLIP, "z0": W.CONTACT})
+    p = W.cell_points(m)
+    v = np.stack([0.05 * np.sin(np.pi * p[:, 1]), 0.05 * np.sin(np.pi * p[:, 0]), np.full(m.n_cells, -0.3)])
+    planes = np.array([[0.0, 0.0, -0.02, 0.0, 0.0, 1.0]])
+    return W.Problem("sgdrop3d", m, 1.0, 0.0, np.full(m.n_cells, 0.5), v, 0.25, 10, contact=(planes, 0.05),
+                     stiffened_gas=(1.8, 2.0, 0.5), shear_a=0.0)

@@ -105,6 +105,68 @@ template <int D> void check_stress_family() {
     }
 }
 
+// the stiffened gas: its stress and impedance with the energy (a = -1 and a = 0.3), and the
+// shear energy of the family
+template <int D> void check_stiffened_gas() {
+    constexpr int DD = D * D;
+    const SgMat sg{2.2, 1.5, 1.1};
+    const double as[2] = {-1.0, 0.3};
+    for (int t = 0; t < 6; ++t) {
+        const double a = as[t & 1];
+        double F[DD], dF[DD], lT[DD], mu = U(0.5, 2), dmu = U(-1, 1), eps = U(4, 6), de = U(-1, 1);  // p + pinf > 0
+        double rho = U(0.5, 2), dr = U(-1, 1);
+        randF<D>(F, 0.2);
+        for (int i = 0; i < DD; ++i) {
+            dF[i] = U(-1, 1);
+            lT[i] = U(-1, 1);
+        }
+        const double h = 1e-6;
+        double Fp[DD], Fm[DD];
+        for (int i = 0; i < DD; ++i) {
+            Fp[i] = F[i] + h * dF[i];
+            Fm[i] = F[i] - h * dF[i];
+        }
+        // shear energy
+        {
+            const double fd = (shear_energy_a<D>(Fp, sg.rho0, mu + h * dmu, a) -
+                               shear_energy_a<D>(Fm, sg.rho0, mu - h * dmu, a)) / (2 * h);
+            double lF[DD] = {}, lmu = 0.0;
+            shear_energy_a_vjp<D>(F, sg.rho0, mu, a, 1.0, lF, lmu);
+            double an = lmu * dmu;
+            for (int i = 0; i < DD; ++i) an += lF[i] * dF[i];
+            report(D == 2 ? "sgpsi2" : "sgpsi3", fd, an);
+        }
+        // stress
+        {
+            double Tp[DD], Tm[DD];
+            stress_sg_a<D>(Fp, mu + h * dmu, a, sg, eps + h * de, Tp);
+            stress_sg_a<D>(Fm, mu - h * dmu, a, sg, eps - h * de, Tm);
+            double fd = 0.0;
+            for (int i = 0; i < DD; ++i) fd += lT[i] * (Tp[i] - Tm[i]) / (2 * h);
+            double lF[DD] = {}, lmu = 0.0, le = 0.0, T[DD], T2[DD], dT = 0.0;
+            stress_sg_a_vjp<D>(F, mu, a, sg, eps, lT, lF, lmu, le, T);
+            stress_sg_a<D>(F, mu, a, sg, eps, T2);
+            double an = lmu * dmu + le * de;
+            for (int i = 0; i < DD; ++i) {
+                an += lF[i] * dF[i];
+                dT = fmax(dT, fabs(T[i] - T2[i]));
+            }
+            report(D == 2 ? "sgstress2" : "sgstress3", fd, an);
+            report(D == 2 ? "sgstressT2" : "sgstressT3", 1.0, 1.0 + dT);
+        }
+        // impedance
+        {
+            const double fd = (impedance_sg_a<D>(Fp, rho + h * dr, mu + h * dmu, a, sg, eps + h * de) -
+                               impedance_sg_a<D>(Fm, rho - h * dr, mu - h * dmu, a, sg, eps - h * de)) / (2 * h);
+            double lF[DD] = {}, lr = 0.0, lmu = 0.0, le = 0.0;
+            impedance_sg_a_vjp<D>(F, rho, mu, a, sg, eps, 1.0, lF, lr, lmu, le);
+            double an = lr * dr + lmu * dmu + le * de;
+            for (int i = 0; i < DD; ++i) an += lF[i] * dF[i];
+            report(D == 2 ? "sgimp2" : "sgimp3", fd, an);
+        }
+    }
+}
+
 template <int D> void check_impedance() {
     constexpr int DD = D * D;
     for (int t = 0; t < 5; ++t) {
@@ -274,7 +336,7 @@ template <int D> struct Patch {
     }
 };
 
-template <int D> void check_predict(int ord, double sa = -1.0) {
+template <int D> void check_predict(int ord, double sa = -1.0, const SgMat *sg = nullptr) {
     using Q = Sz<D>;
     constexpr int NV = D + 1, NS = Q::NS, DD = D * D, NM = Q::NMOM;
     for (int t = 0; t < 4; ++t) {
@@ -285,6 +347,7 @@ template <int D> void check_predict(int ord, double sa = -1.0) {
         for (int i = 0; i < NV * D; ++i) lR[i] = U(-1, 1);
         // direction
         double dxs[NV * D], dmom[NV * NM], dvc[D], dF[DD], dz = U(-1, 1), dmu = U(-1, 1), dk = U(-1, 1);
+        const double ec = U(1, 3), dec = U(-1, 1);  // the stiffened gas's specific total energy
         for (int i = 0; i < NV * D; ++i) dxs[i] = U(-1, 1) * 0.05;
         for (int i = 0; i < NV * NM; ++i) dmom[i] = U(-1, 1) * 0.01;
         for (int a = 0; a < D; ++a) dvc[a] = U(-1, 1);
@@ -297,7 +360,7 @@ template <int D> void check_predict(int ord, double sa = -1.0) {
             for (int a = 0; a < D; ++a) Q2.vc[a] += s * dvc[a];
             for (int q = 0; q < DD; ++q) Q2.Fc[q] += s * dF[q];
             predict_fw<D>(Q2.xs, Q2.acc(Q2.mom), Q2.vc, Q2.Fc, P.z + s * dz, P.mu + s * dmu, P.kap + s * dk, P.im, P.dt,
-                          ord, Mo, Ro, sa);
+                          ord, Mo, Ro, sa, sg, ec + s * dec);
         };
         double Mp[NV * NS], Rp[NV * D], Mm[NV * NS], Rm[NV * D];
         eval(h, Mp, Rp);
@@ -305,17 +368,19 @@ template <int D> void check_predict(int ord, double sa = -1.0) {
         double fd = 0.0;
         for (int i = 0; i < NV * NS; ++i) fd += lM[i] * (Mp[i] - Mm[i]) / (2 * h);
         for (int i = 0; i < NV * D; ++i) fd += lR[i] * (Rp[i] - Rm[i]) / (2 * h);
-        double lxs[NV * D] = {}, lmom[NV * NM] = {}, lvc[D] = {}, lF[DD] = {}, lz = 0, lmu = 0, lkap = 0;
+        double lxs[NV * D] = {}, lmom[NV * NM] = {}, lvc[D] = {}, lF[DD] = {}, lz = 0, lmu = 0, lkap = 0, le = 0;
         for (int i = 0; i < NV * NM; ++i) lmom[i] = 1e300;  // every entry must be stored exactly once
         predict_vjp<D>(P.xs, P.acc(P.mom), P.vc, P.Fc, P.z, P.mu, P.kap, P.im, P.dt, ord, lM, lR, lxs,
-                       [&](int k, int j, double v) { lmom[k * NM + j] = v; }, lvc, lF, lz, lmu, lkap, sa);
-        double an = lz * dz + lmu * dmu + lkap * dk;
+                       [&](int k, int j, double v) { lmom[k * NM + j] = v; }, lvc, lF, lz, lmu, lkap, sa, sg, ec,
+                       &le);
+        double an = lz * dz + lmu * dmu + lkap * dk + le * dec;
         for (int i = 0; i < NV * D; ++i) an += lxs[i] * dxs[i];
         for (int i = 0; i < NV * NM; ++i) an += lmom[i] * dmom[i];
         for (int a = 0; a < D; ++a) an += lvc[a] * dvc[a];
         for (int q = 0; q < DD; ++q) an += lF[q] * dF[q];
         char name[32];
-        if (sa == -1.0) std::snprintf(name, sizeof name, "predict%d_ord%d", D, ord);
+        if (sg) std::snprintf(name, sizeof name, "predictsg%d_ord%d", D, ord);
+        else if (sa == -1.0) std::snprintf(name, sizeof name, "predict%d_ord%d", D, ord);
         else std::snprintf(name, sizeof name, "predictfam%d_ord%d", D, ord);
         report(name, fd, an);
     }
@@ -354,8 +419,8 @@ template <int D> void check_update(int ord) {
         for (int i = 0; i < NV * NS; ++i) dM[i] = U(-1, 1);
         for (int a = 0; a < D; ++a) dv[a] = U(-1, 1);
         for (int q = 0; q < DD; ++q) dF[q] = U(-1, 1);
-        const double h = 1e-7;
-        auto eval = [&](double s, double *v1, double *F1, double &z1) {
+        const double h = 1e-7, e0 = U(0.5, 2), de = U(-1, 1), le1 = U(-1, 1);  // the energy equation too
+        auto eval = [&](double s, double *v1, double *F1, double &z1, double &e1) {
             double a0[NX], a1[NX], avs[NX], ap0[NX], ap1[NX], aM[NV * NS], aR[NX], av[D], aF[DD];
             for (int i = 0; i < NX; ++i) {
                 a0[i] = xs0[i] + s * d0[i];
@@ -369,19 +434,19 @@ template <int D> void check_update(int ord) {
             for (int a = 0; a < D; ++a) av[a] = v[a] + s * dv[a];
             for (int q = 0; q < DD; ++q) aF[q] = F[q] + s * dF[q];
             update_fw<D>(a0, a1, avs, ap0, ap1, aM, aR, av, aF, m, 1.0 / m, mu + s * dmu, kap + s * dk, dt, ord, v1, F1,
-                         z1);
+                         z1, e0 + s * de, &e1);
         };
-        double v1p[D], F1p[DD], z1p, v1m[D], F1m[DD], z1m;
-        eval(h, v1p, F1p, z1p);
-        eval(-h, v1m, F1m, z1m);
-        double fd = lz1 * (z1p - z1m) / (2 * h);
+        double v1p[D], F1p[DD], z1p, e1p, v1m[D], F1m[DD], z1m, e1m;
+        eval(h, v1p, F1p, z1p, e1p);
+        eval(-h, v1m, F1m, z1m, e1m);
+        double fd = lz1 * (z1p - z1m) / (2 * h) + le1 * (e1p - e1m) / (2 * h);
         for (int a = 0; a < D; ++a) fd += lv1[a] * (v1p[a] - v1m[a]) / (2 * h);
         for (int q = 0; q < DD; ++q) fd += lF1[q] * (F1p[q] - F1m[q]) / (2 * h);
         double l0[NX] = {}, l1[NX] = {}, lvs[NX] = {}, lp0[NX] = {}, lp1[NX] = {}, lM[NV * NS] = {}, lR[NX] = {},
                lv[D] = {}, lF[DD] = {}, lmu = 0, lkap = 0;
         update_vjp<D>(xs0, xs1, vs, vp0, vp1, M, R, v, F, m, 1.0 / m, mu, kap, dt, ord, lv1, lF1, lz1, l0, l1, lvs, lp0,
-                      lp1, lM, lR, lv, lF, lmu, lkap);
-        double an = lmu * dmu + lkap * dk;
+                      lp1, lM, lR, lv, lF, lmu, lkap, le1);
+        double an = lmu * dmu + lkap * dk + le1 * de;  // e^n's adjoint is le1
         for (int i = 0; i < NX; ++i)
             an += l0[i] * d0[i] + l1[i] * d1[i] + lvs[i] * dvs[i] + lp0[i] * dp0[i] + lp1[i] * dp1[i] + lR[i] * dR[i];
         for (int i = 0; i < NV * NS; ++i) an += lM[i] * dM[i];
@@ -540,6 +605,8 @@ int main() {
     check_stress<3>();
     check_stress_family<2>();
     check_stress_family<3>();
+    check_stiffened_gas<2>();
+    check_stiffened_gas<3>();
     check_impedance<2>();
     check_impedance<3>();
     check_faces_velgrad<2>();
@@ -555,6 +622,9 @@ int main() {
         check_predict<3>(ord);
         check_predict<2>(ord, 0.0);
         check_predict<3>(ord, 0.5);
+        const SgMat sg{2.2, 1.5, 1.1};
+        check_predict<2>(ord, -1.0, &sg);
+        check_predict<3>(ord, 0.3, &sg);
         check_update<2>(ord);
         check_update<3>(ord);
     }

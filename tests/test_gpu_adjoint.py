@@ -18,11 +18,11 @@ import pytest
 import oracle as O
 import paper_2104_02139_gb300 as L
 import workloads as W
-from adjoint_cases import bc_case, family_case
+from adjoint_cases import bc_case, family_case, sg_case
 
 pytestmark = pytest.mark.gpu
 
-OUT_FIELDS = (("x", L.FIELD_X), ("vp", L.FIELD_VP), ("v", L.FIELD_V), ("F", L.FIELD_F))
+OUT_FIELDS = (("x", L.FIELD_X), ("vp", L.FIELD_VP), ("v", L.FIELD_V), ("F", L.FIELD_F), ("e", L.FIELD_E))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -44,7 +44,7 @@ def _setup(pb, seed):
     mu = np.asarray(pb.mu, dtype=float) * (1.0 + 0.1 * rng.random(nc))
     pb = dataclasses.replace(pb, F=F, mu=mu)
     lam = {"x": rng.standard_normal((d, npn)), "vp": rng.standard_normal((d, npn)),
-           "v": rng.standard_normal((d, nc)), "F": rng.standard_normal((d * d, nc))}
+           "v": rng.standard_normal((d, nc)), "F": rng.standard_normal((d * d, nc)), "e": rng.standard_normal(nc)}
     return pb, lam, rng
 
 
@@ -94,7 +94,7 @@ def _grad(pb, n, prm, lam, pre=0, ckpt=0):
     if pre:
         st.run(pre)
     tape = L.Tape(st, n, ckpt)
-    g = tape.backward(lam_x=lam["x"], lam_vp=lam["vp"], lam_v=lam["v"], lam_F=lam["F"])
+    g = tape.backward(lam_x=lam["x"], lam_vp=lam["vp"], lam_v=lam["v"], lam_F=lam["F"], lam_e=lam.get("e"))
     return st, tape, g
 
 
@@ -121,7 +121,7 @@ def _check_init_grads(pb, n, prm, seed, tol=1e-6, eps=1e-6, frozen=False):
         ("mu", lambda e: (dataclasses.replace(pb, mu=pb.mu + e * dmu), None), smu, float((g["mu"] * dmu).sum())),
         ("F", lambda e: (dataclasses.replace(pb, F=pb.F + e * dF), None), sF, float((g["F"] * dF).sum())),
     ]
-    assert np.all(g["vp"] == 0.0)
+    assert np.all(g["vp"] == 0.0) and np.all(g["e"] == 0.0)  # the start's v_p and e are derived
     out = {}
     for name, make, eps, ad in cases:
         fd = _fd(pb, n, prm, lam, masks, make, eps, tape=tape if frozen else None)
@@ -163,7 +163,7 @@ def test_replay_reproduces_the_recorded_run():
         st = L.simulation(pb)
         tape = L.Tape(st, 5, 2)
         other = tape.replay(L.simulation(pb))
-        for k, fid in OUT_FIELDS + (("e", L.FIELD_E),):
+        for k, fid in OUT_FIELDS:
             a, b = st.get(fid), other.get(fid)
             assert np.abs(a - b).max() <= 1e-13 * max(np.abs(a).max(), 1e-300), k
         assert np.array_equal(st.get(L.FIELD_DT), other.get(L.FIELD_DT)) or \
@@ -192,11 +192,19 @@ def test_adjoint_fd_shear_family(name):
     _check_init_grads(family_case(name), 5, {}, seed=25, frozen=True)
 
 
-@pytest.mark.parametrize("name", ["plain2d", "piston2d", "rebound2d", "box3d_bc"])
+@pytest.mark.parametrize("name", ["sgwave2d", "sgdrop3d"])
+def test_adjoint_fd_stiffened_gas(name):
+    """the stiffened gas (its pressure depends on e, which carries an adjoint)"""
+    _check_init_grads(sg_case(name), 5, {}, seed=26, frozen=True)
+
+
+@pytest.mark.parametrize("name", ["plain2d", "piston2d", "rebound2d", "box3d_bc", "sgwave2d"])
 def test_adjoint_fd_mid_run_state(name):
-    """A tape that starts after some steps: gradients of x, v_p, v, F (via lmood_set) and mu;
-    with boundary faces the position direction moves them (their forces and multipliers)."""
-    pb, lam, rng = _setup(W.plain2d(n=10) if name == "plain2d" else bc_case(name), 16)
+    """A tape that starts after some steps: gradients of x, v_p, v, F, e (via lmood_set) and
+    mu; with boundary faces the position direction moves them (their forces and multipliers);
+    with the stiffened gas e enters the pressure."""
+    pb = W.plain2d(n=10) if name == "plain2d" else (sg_case(name) if name.startswith("sg") else bc_case(name))
+    pb, lam, rng = _setup(pb, 16)
     prm = {"dt_fixed": _dt_fixed(pb), "mood": 0}
     pre, n = 3, 5
     st, tape, g = _grad(pb, n, prm, lam, pre=pre)
@@ -204,13 +212,14 @@ def test_adjoint_fd_mid_run_state(name):
     _, masks = _run(pb, n, prm, pre=pre)
     base = L.simulation(pb, **prm)
     base.run(pre)
-    x0, vp0, v0, F0 = (base.get(f) for f in (L.FIELD_X, L.FIELD_VP, L.FIELD_V, L.FIELD_F))
+    x0, vp0, v0, F0, e0 = (base.get(f) for f in (L.FIELD_X, L.FIELD_VP, L.FIELD_V, L.FIELD_F, L.FIELD_E))
     d, nc, npn = pb.mesh.dim, pb.mesh.n_cells, pb.mesh.n_nodes
     h = np.sqrt((base.get(L.FIELD_TAU) * base.get(L.FIELD_MASS)).mean())  # a cell size
     dirs = {"x": rng.standard_normal((d, npn)), "vp": rng.standard_normal((d, npn)),
-            "v": rng.standard_normal((d, nc)), "F": rng.standard_normal((d * d, nc))}
-    scale = {"x": 1e-5 * h, "vp": 1e-6, "v": 1e-6, "F": 1e-6}
-    fields = {"x": (L.FIELD_X, x0), "vp": (L.FIELD_VP, vp0), "v": (L.FIELD_V, v0), "F": (L.FIELD_F, F0)}
+            "v": rng.standard_normal((d, nc)), "F": rng.standard_normal((d * d, nc)), "e": rng.standard_normal(nc)}
+    scale = {"x": 1e-5 * h, "vp": 1e-6, "v": 1e-6, "F": 1e-6, "e": 1e-6}
+    fields = {"x": (L.FIELD_X, x0), "vp": (L.FIELD_VP, vp0), "v": (L.FIELD_V, v0), "F": (L.FIELD_F, F0),
+              "e": (L.FIELD_E, e0)}
     for k, (fid, val) in fields.items():
         dk = dirs[k]
 
@@ -229,7 +238,7 @@ def test_adjoint_vs_oracle_fd():
     st, tape, g = _grad(pb, n, prm, lam)
     dv = rng.standard_normal(pb.v.shape)
     dmu = rng.standard_normal(pb.mesh.n_cells)
-    ofields = (("x", O.F_X), ("vp", O.F_VP), ("v", O.F_V), ("F", O.F_F))
+    ofields = (("x", O.F_X), ("vp", O.F_VP), ("v", O.F_V), ("F", O.F_F), ("e", O.F_E))
 
     def Jo(p):
         o = O.Oracle(p, **prm)
@@ -342,7 +351,7 @@ def test_state_init_from_device_tensors():
     dev = L.State(mesh, pb.rho0, pb.lam, torch.tensor(pb.mu, device="cuda"), torch.tensor(pb.v, device="cuda"),
                   torch.tensor(pb.F, device="cuda"), L.params_default(m.dim, cfl=pb.cfl))
     for _ in range(2):
-        for k, fid in OUT_FIELDS + (("e", L.FIELD_E),):
+        for k, fid in OUT_FIELDS:
             assert np.array_equal(host.get(fid), dev.get(fid)), k
         host.step()
         dev.step()

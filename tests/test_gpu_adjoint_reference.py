@@ -2,16 +2,17 @@
 
 1. The oracle's tangent build (the oracle's own source compiled with dual numbers, a CPU
    forward-mode derivative of the same frozen-mask map that shares nothing with the CUDA
-   adjoint): for seeded adjoints lam of the final state (x, v_p, v, F) and seeded directions
-   delta of the initial v0, mu, F0 and node positions (at fixed masses, through the initial
-   nodal solve), <grad, delta> from the tape's reverse pass must equal <lam, J delta> from the
-   tangent to 1e-6 relative, over 12 steps with MOOD active (first-order cells in the masks)
-   and the adaptive dt, in 2D (slip walls; the impact against a wall) and 3D (slip walls; the
-   clamped column), and with traction, pressure and prescribed-velocity faces and contact
-   walls (the piston, a block rebounding on a wall, a block under pressure and traction, a 3D
-   box with every kind of face), and with the shear energy family (a = 0, a = 0.5). The two
-   runs' masks must be identical at every step and their
-   dt equal to 1e-12, so both differentiate the same map.
+   adjoint): for seeded adjoints lam of the final state (x, v_p, v, F, e) and seeded
+   directions delta of the initial v0, mu, F0 and node positions (at fixed masses, through the
+   initial nodal solve), <grad, delta> from the tape's reverse pass must equal <lam, J delta>
+   from the tangent to 1e-6 relative, over 12 steps with MOOD active (first-order cells in the
+   masks) and the adaptive dt: in 2D (slip walls; the impact against a wall) and 3D (slip
+   walls; the clamped column); with traction, pressure and prescribed-velocity faces and
+   contact walls (the piston, a block rebounding on a wall, a block under pressure and
+   traction, a 3D box with every kind of face); with the shear energy family (a = 0, a = 0.5);
+   and with the stiffened gas (a 2D piston against a pressure; a 3D block on a contact floor).
+   The two runs' masks must be identical at every step and their dt equal to 1e-12, so both
+   differentiate the same map.
 2. The adjoint configuration at full size (511,104 tetrahedra, 400 steps, a checkpoint every
    20 steps): the gradient of J = sum over cells with initial centroid z > 0.5 of m |v|^2 / 2
    along two random directions of v0 and two of mu (each cell's mu direction scaled by its mu,
@@ -26,7 +27,7 @@ import pytest
 import oracle as O
 import paper_2104_02139_gb300 as L
 import workloads as W
-from adjoint_cases import bc_case, family_case, smooth_positions_direction
+from adjoint_cases import bc_case, family_case, sg_case, smooth_positions_direction
 
 pytestmark = pytest.mark.gpu
 
@@ -55,6 +56,8 @@ def _case(name):
         pb.v *= 8.0
     elif name in ("cube3d_a0", "impact2d_a05"):
         pb = family_case(name)
+    elif name in ("sgwave2d", "sgdrop3d"):
+        pb = sg_case(name)
     else:
         pb = bc_case(name)
     return pb
@@ -72,17 +75,18 @@ def _perturbed_material(pb, rng):
 
 
 @pytest.mark.parametrize("name", ["plain2d", "impact2d", "cube3d", "column3d", "piston2d", "rebound2d",
-                                  "pressure_traction2d", "box3d_bc", "cube3d_a0", "impact2d_a05"])
+                                  "pressure_traction2d", "box3d_bc", "cube3d_a0", "impact2d_a05", "sgwave2d",
+                                  "sgdrop3d"])
 def test_adjoint_matches_the_oracle_tangent(name):
     rng = np.random.default_rng(31)
     pb = _perturbed_material(_case(name), rng)
     n = 12
     d, nc, npn = pb.mesh.dim, pb.mesh.n_cells, pb.mesh.n_nodes
     lam = {"x": rng.standard_normal((d, npn)), "vp": rng.standard_normal((d, npn)),
-           "v": rng.standard_normal((d, nc)), "F": rng.standard_normal((d * d, nc))}
+           "v": rng.standard_normal((d, nc)), "F": rng.standard_normal((d * d, nc)), "e": rng.standard_normal(nc)}
     st = L.simulation(pb)
     tape = L.Tape(st, n, 4)
-    g = tape.backward(lam_x=lam["x"], lam_vp=lam["vp"], lam_v=lam["v"], lam_F=lam["F"])
+    g = tape.backward(lam_x=lam["x"], lam_vp=lam["vp"], lam_v=lam["v"], lam_F=lam["F"], lam_e=lam["e"])
     twin = L.simulation(pb)
     masks, dts = [], []
     for _ in range(n):

@@ -79,3 +79,24 @@ def test_empty_and_null_inputs():
     assert lib.lmood_mesh_create(2, 3, None, 1, None, 0, None, None, None, 1, None, C.byref(h)) == L.ERR_ARG
     assert lib.lmood_step(None, None) == L.ERR_ARG
     assert lib.lmood_get(None, 0, None, 0) == L.ERR_ARG
+
+
+def test_destruction_in_any_order():
+    """A mesh destroyed before its state, a state before its tape (as a garbage collector may
+    order them): the dependent handles stay destroyable, every other call on them is an error."""
+    pb = W.plain2d(n=8)
+    st = L.simulation(pb)
+    tape = L.Tape(st, 2)
+    st.close()  # the state goes first: its tape is an orphan
+    with pytest.raises(L.LmoodError):
+        tape.backward(lam_v=np.ones((2, pb.mesh.n_cells)))
+    tape.close()
+    st2 = L.simulation(pb)
+    tape2 = L.Tape(st2, 2)
+    st2.mesh.close()  # the mesh goes first: its state can only be destroyed now
+    assert st2.step_status() == L.ERR_STATE
+    with pytest.raises(L.LmoodError) as e:
+        st2.get(L.FIELD_V)
+    assert e.value.status == L.ERR_STATE
+    st2.close()
+    tape2.close()

@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from adjoint_cases import bc_case, smooth_positions_direction
+from adjoint_cases import bc_case, sg_case, smooth_positions_direction
 
 FIELDS = ("x", "vp", "v", "F")
 
@@ -147,6 +147,42 @@ def test_tangent_with_boundary_faces_against_central_differences(orc, name):
         fd = {k: float(((runs[0][k] - runs[1][k]) * lam[k]).sum()) / (2 * h) for k in FIELDS}
         scale = max(abs(v) for v in ad.values())
         for k in FIELDS:
+            assert abs(ad[k] - fd[k]) <= 1e-6 * scale, (name, name_dir, k, ad[k], fd[k])
+
+
+@pytest.mark.parametrize("name", ["sgwave2d", "sgdrop3d"])
+def test_tangent_stiffened_gas_against_central_differences(orc, name):
+    """the stiffened gas, whose pressure depends on the internal energy: the derivative of the
+    final (x, v_p, v, F, e) along directions of v0, mu, F0 and of the initial positions"""
+    rng = np.random.default_rng(23)
+    pb = sg_case(name)
+    d, nc, npn = pb.mesh.dim, pb.mesh.n_cells, pb.mesh.n_nodes
+    pb = dataclasses.replace(pb, mu=np.asarray(pb.mu, dtype=float) * (1.0 + 0.1 * rng.random(nc)),
+                             F=np.tile(np.eye(d).ravel()[:, None], (1, nc)))
+    n = 4
+    prm = {"dt_fixed": 0.5 * orc.Oracle(pb).dt}
+    fields = FIELDS + ("e",)
+    lam = {"x": rng.standard_normal((d, npn)), "vp": rng.standard_normal((d, npn)),
+           "v": rng.standard_normal((d, nc)), "F": rng.standard_normal((d * d, nc)), "e": rng.standard_normal(nc)}
+    dirs = {"v": rng.standard_normal((d, nc)), "mu": rng.standard_normal(nc) * pb.mu,
+            "F": 0.1 * rng.standard_normal((d * d, nc)), "x": 0.1 * smooth_positions_direction(pb.mesh)}
+    h = 1e-5  # (the rounding of the differenced runs dominates at 1e-6 for the weaker directions)
+    for name_dir, delta in dirs.items():
+        t = orc.tangent(pb, n, **{"d" + name_dir: delta}, **prm)
+        ad = {k: float((t["d" + k] * lam[k]).sum()) for k in fields}
+        runs = []
+        for sgn in (1.0, -1.0):
+            if name_dir == "x":
+                r = orc.tangent(pb, n, dx=delta, x_shift=sgn * h, **prm)
+            else:
+                base = {"v": pb.v, "mu": pb.mu, "F": pb.F}[name_dir]
+                r = orc.tangent(dataclasses.replace(pb, **{name_dir: base + sgn * h * delta}), n, **prm)
+            for s in range(n):
+                assert np.array_equal(r["masks"][s], t["masks"][s]), f"mask changed under the perturbation at step {s}"
+            runs.append(r)
+        fd = {k: float(((runs[0][k] - runs[1][k]) * lam[k]).sum()) / (2 * h) for k in fields}
+        scale = max(abs(v) for v in ad.values())
+        for k in fields:
             assert abs(ad[k] - fd[k]) <= 1e-6 * scale, (name, name_dir, k, ad[k], fd[k])
 
 
