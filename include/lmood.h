@@ -337,8 +337,9 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  * and time step frozen at their recorded values. Each step is then a smooth map of the state
  * (x, v_p per node; v, F per cell) and of the per-cell mu; the adjoint is the exact transpose
  * of its linearisation, written by hand kernel by kernel (no atomics, deterministic).
- * Only the two-level cascade (P1 -> P0) is differentiated: a recorded step that used the
- * limited level returns LMOOD_ERR_ARG. Every material is differentiated: the neo-Hookean law,
+ * Both cascades are differentiated: at the limited level (P1 with Barth-Jespersen slopes) each
+ * field's factor phi is differentiated with the corner and the stencil bound that set it
+ * frozen (the bound's adjoint goes to the cell that holds it). Every material is differentiated: the neo-Hookean law,
  * every a of the shear energy family (Eq. familiy_energies) and the stiffened gas (whose
  * pressure depends on the internal energy e, which then carries an adjoint: see
  * lmood_tape_backward_e). Boundary faces of every kind are differentiated: slip and

@@ -45,6 +45,9 @@ struct AdjBuf {
     // (slot i for its node i) the adjoint of the face's area vector from that node's solve,
     // then (k_adj_faces) the adjoint of that node's position; NULL when the mesh has none
     double *bf;
+    // cells at the limited (Barth-Jespersen) level of this step: their records [N][B_LEN]
+    // (adj::PredRec<D>::B_*); NULL when the step has none
+    double *bj;
 };
 
 struct AdjOps {
@@ -68,6 +71,9 @@ struct AdjOps {
     void (*gather)(const Geo &, const AdjBuf &, cudaStream_t);
     // cells: impedance of the initial state (after the t^0 predictor's reverse)
     void (*z0)(const Geo &, const Fld &, const Prm &, const AdjBuf &, cudaStream_t);
+    // cells: the adjoints of the stencil bounds that set the limited cells' factors, gathered
+    // into the cells that hold those bounds (no launch when AdjBuf::bj is NULL)
+    void (*bj_gather)(const Geo &, const Fld &, const AdjBuf &, cudaStream_t);
     // cells: the adjoint of the initial energy e^0 (a function of v, F, mu) moved to v, F, mu
     void (*e0)(const Geo &, const Fld &, const Prm &, const AdjBuf &, cudaStream_t);
 };

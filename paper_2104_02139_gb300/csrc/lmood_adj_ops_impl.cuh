@@ -20,10 +20,13 @@ template <int D, int MAT>
 void adj_predict_m(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, int force_p0, cudaStream_t s) {
     if (!force_p0) {
         const int nc = (D + 1) * g.N;
-        k_adj_pred_fw<D, MAT><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+        k_adj_pred_fw<D, MAT, false><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+        if (a.bj) k_adj_pred_fw<D, MAT, true><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
         k_adj_pred_c2<D, MAT><<<adj_blocks(nc, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
         k_adj_pred_c1<D, MAT><<<adj_blocks(nc, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
-        k_adj_pred_fin<D, MAT == 2 ? 2 : 0><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+        constexpr int MF = MAT == 2 ? 2 : 0;
+        k_adj_pred_fin<D, MF, false><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
+        if (a.bj) k_adj_pred_fin<D, MF, true><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
         // (the second-order cells' corner-matrix and geometry part runs in k_adj_cells)
     }
     k_adj_predict<D, MAT><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a, force_p0);
@@ -48,6 +51,9 @@ template <int D> void adj_gather(const Geo &g, const AdjBuf &a, cudaStream_t s) 
 template <int D> void adj_faces(const Geo &g, const Fld &f, const AdjBuf &a, cudaStream_t s) {
     if (a.bf && g.nbf > 0) k_adj_faces<D><<<adj_blocks(g.nbf, kAdjNodeBlock), kAdjNodeBlock, 0, s>>>(g, f, a);
 }
+template <int D> void adj_bj_gather(const Geo &g, const Fld &f, const AdjBuf &a, cudaStream_t s) {
+    if (a.bj) k_adj_bj_gather<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, a);
+}
 template <int D> void adj_e0(const Geo &g, const Fld &f, const Prm &p, const AdjBuf &a, cudaStream_t s) {
     if (a.lE0) k_adj_e0<D><<<adj_blocks(g.N, kAdjCellBlock), kAdjCellBlock, 0, s>>>(g, f, p, a);
 }
@@ -59,7 +65,7 @@ template <int D> void adj_z0(const Geo &g, const Fld &f, const Prm &p, const Adj
 
 #define LMOOD_ADJ_OPS_TABLE(D)                                                                              \
     static const AdjOps table = {D, adj_update<D>, adj_nodes<D>, adj_predict<D>, adj_momsum<D>, adj_cells<D>, \
-                                 adj_faces<D>, adj_gather<D>, adj_z0<D>, adj_e0<D>};                         \
+                                 adj_faces<D>, adj_gather<D>, adj_z0<D>, adj_bj_gather<D>, adj_e0<D>};       \
     return table;
 
 }  // namespace lmood

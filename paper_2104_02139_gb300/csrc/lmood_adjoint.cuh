@@ -824,6 +824,115 @@ LMOOD_HD void node_solve_bc_vjp(const double *M, const double *b0, int nd, const
     }
 }
 
+// the reverse predictor's records (see the product of predict_fw below)
+template <int D> struct PredRec {
+    static constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + DD;
+    // cell record: slopes gs [NQ][D], G^-1 [DD], d_k = x_k - x_c [NV][D], dF/dt [DD], face
+    // area vectors N [NV][D], D / |N_f| [NV], slopes taken (1) or not (0), the volume, and for
+    // the stiffened gas the specific internal energy at t^n and at the half step
+    static constexpr int F_GS = 0, F_GI = F_GS + NQ * D, F_DK = F_GI + DD, F_DFDT = F_DK + NV * D, F_N = F_DFDT + DD,
+                         F_INU = F_N + NV * D, F_OK = F_INU + NV, F_V = F_OK + 1, F_EPS = F_V + 1, F_EPH = F_EPS + 1,
+                         F_LEN = F_EPH + 1;
+    // corner record: F_h [DD], v* [D], M_k [NS]
+    static constexpr int K_FH = 0, K_VST = DD, K_M = DD + D, K_LEN = DD + D + NS;
+    // pass-2 products of a corner: lv* [D], lF* [DD], lN_k [D], lmu, lkappa, leps (half step)
+    static constexpr int Q2_LV = 0, Q2_LF = D, Q2_LN = D + DD, Q2_MU = 2 * D + DD, Q2_KAP = Q2_MU + 1,
+                         Q2_EPS = Q2_KAP + 1, Q2_LEN = Q2_EPS + 1;
+    // pass-1 products of a corner: lF_h [DD], lN_k [D], lmu, lkappa, leps (t^n)
+    static constexpr int Q1_LF = 0, Q1_LN = DD, Q1_MU = DD + D, Q1_KAP = Q1_MU + 1, Q1_EPS = Q1_KAP + 1,
+                         Q1_LEN = Q1_EPS + 1;
+    // Barth-Jespersen record of a cell at the limited level: the unlimited slopes [NQ][D], per
+    // field the factor phi, the corner that set it (-1: phi = 1), which bound (+1 the
+    // stencil's maximum, -1 its minimum, 0 none; +-2 when the cell itself holds it), the cell
+    // that holds that bound (filled by the kernel), and the adjoint of that bound (the reverse
+    // pass's output)
+    static constexpr int B_G = 0, B_PHI = NQ * D, B_K = B_PHI + NQ, B_SEL = B_K + NQ, B_T = B_SEL + NQ,
+                         B_LE = B_T + NQ, B_LEN = B_LE + NQ;
+};
+
+// Barth-Jespersen limiter of a cell at the limited level (the cascade's middle level): each
+// field's slopes gs [NQ][D] scaled by the largest phi <= 1 that keeps its values at the cell's
+// nodes (d_k = x_k - x_c, dk [NV][D]) within [lo, hi], the field's range over the stencil and
+// the cell; the unlimited slopes, phi and the choice that set it go to the record bjr, the
+// limited slopes to gs and gs_out
+template <int D>
+LMOOD_HD void bj_limit(const double *vc, const double *Fc, const double (&dk)[D + 1][D], const double *lo,
+                       const double *hi, double (&gs)[D + D * D][D], double *gs_out, double *bjr) {
+    using P = PredRec<D>;
+    constexpr int NV = D + 1, NQ = D + D * D;
+    for (int q = 0; q < NQ; ++q) {
+        const double qc = q < D ? vc[q] : Fc[q - D];
+        double phi = 1.0;
+        int ks = -1, sel = 0;
+        for (int k = 0; k < NV; ++k) {
+            double delta = 0.0;
+            for (int a = 0; a < D; ++a) delta += gs[q][a] * dk[k][a];
+            if (delta > 0.0) {
+                const double cnd = (hi[q] - qc) / delta;
+                if (cnd < phi) {
+                    phi = cnd;
+                    ks = k;
+                    sel = 1;
+                }
+            }
+            if (delta < 0.0) {
+                const double cnd = (lo[q] - qc) / delta;
+                if (cnd < phi) {
+                    phi = cnd;
+                    ks = k;
+                    sel = -1;
+                }
+            }
+        }
+        bjr[P::B_PHI + q] = phi;
+        bjr[P::B_K + q] = ks;
+        bjr[P::B_SEL + q] = sel;
+        for (int a = 0; a < D; ++a) {
+            bjr[P::B_G + q * D + a] = gs[q][a];
+            gs[q][a] *= phi;
+            gs_out[q * D + a] = gs[q][a];
+        }
+    }
+}
+
+// reverse of bj_limit: lgs [NQ][D] the adjoint of the limited slopes in, of the unlimited ones
+// out; accumulates the adjoints of the cell's values (lvc, lFc) and of d_k (lxs, lxcc as in
+// predict_finish_vjp); the adjoint of the bound that set phi goes to bjr[B_LE + q]
+template <int D>
+LMOOD_HD void bj_limit_vjp(const double *dk, double (&lgs)[D + D * D][D], double *lvc, double *lFc, double *lxs,
+                           double *lxcc, double *bjr) {
+    using P = PredRec<D>;
+    constexpr int NQ = D + D * D;
+    for (int q = 0; q < NQ; ++q) {
+        const double phi = bjr[P::B_PHI + q], *g = bjr + P::B_G + q * D;
+        const int ks = (int)bjr[P::B_K + q];
+        double lphi = 0.0;
+        for (int a = 0; a < D; ++a) {
+            lphi += lgs[q][a] * g[a];
+            lgs[q][a] *= phi;
+        }
+        double lb = 0.0;
+        // phi = (bound - q_c) / delta, delta = g . d_ks; a bound held by the cell itself
+        // (|sel| = 2) is q_c: phi = 0 whatever q_c and delta, no adjoint (the products through
+        // q_c and the bound would cancel, each ~ 1 / delta with delta at rounding level in a
+        // uniform region)
+        if (ks >= 0 && (int)bjr[P::B_SEL + q] * (int)bjr[P::B_SEL + q] == 1) {
+            double delta = 0.0;
+            for (int a = 0; a < D; ++a) delta += g[a] * dk[ks * D + a];
+            lb = lphi / delta;
+            if (q < D) lvc[q] -= lb;
+            else lFc[q - D] -= lb;
+            const double ld = -lphi * phi / delta;
+            for (int a = 0; a < D; ++a) {
+                lgs[q][a] += ld * dk[ks * D + a];
+                lxs[ks * D + a] += ld * g[a];
+                lxcc[a] -= ld * g[a];
+            }
+        }
+        bjr[P::B_LE + q] = lb;
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Cell predictor and corner packets (pure form of k_predict for orders 1 and 2).
 // Inputs: xs [NV][D] node positions at t^n; mom(k, j) = moment j of node k (accessor with a
@@ -839,7 +948,8 @@ template <int D> struct Mom {
 template <int D>
 LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, const double *Fc, double z, double mu,
                          double kap, double im, double dt, int ord, double *Mo, double *Ro, double sa = -1.0,
-                         const SgMat *sg = nullptr, double ec = 0.0) {
+                         const SgMat *sg = nullptr, double ec = 0.0, const double *bjlo = nullptr,
+                         const double *bjhi = nullptr) {
     using Q = Sz<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ;
     double V, N[NV * D], xcc[D], W[NV][NS];
@@ -914,6 +1024,12 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
             for (int b = 0; b < D; ++b) s += Gi[a * D + b] * r[q][b];
             gs[q][a] = ok ? s : 0.0;
         }
+    if (bjlo) {  // the limited level
+        double dkk[NV][D], rec[PredRec<D>::B_LEN], gso[NQ * D];
+        for (int k = 0; k < NV; ++k)
+            for (int a = 0; a < D; ++a) dkk[k][a] = xs[k * D + a] - xcc[a];
+        bj_limit<D>(vc, Fc, dkk, bjlo, bjhi, gs, gso, rec);
+    }
     double dv[D] = {}, dFdt[DD], gv[DD];
     const double hv = -0.5 * dt * im * (1.0 / D);
     for (int k = 0; k < NV; ++k) {
@@ -973,23 +1089,6 @@ LMOOD_HD void predict_fw(const double *xs, const Mom<D> &mom, const double *vc, 
 //                                corner matrices, geometry
 // predict_vjp below composes them (and keeps the first-order cells' product whole).
 // ---------------------------------------------------------------------------------------
-template <int D> struct PredRec {
-    static constexpr int NV = D + 1, DD = D * D, NS = D * (D + 1) / 2, NQ = D + DD;
-    // cell record: slopes gs [NQ][D], G^-1 [DD], d_k = x_k - x_c [NV][D], dF/dt [DD], face
-    // area vectors N [NV][D], D / |N_f| [NV], slopes taken (1) or not (0), the volume, and for
-    // the stiffened gas the specific internal energy at t^n and at the half step
-    static constexpr int F_GS = 0, F_GI = F_GS + NQ * D, F_DK = F_GI + DD, F_DFDT = F_DK + NV * D, F_N = F_DFDT + DD,
-                         F_INU = F_N + NV * D, F_OK = F_INU + NV, F_V = F_OK + 1, F_EPS = F_V + 1, F_EPH = F_EPS + 1,
-                         F_LEN = F_EPH + 1;
-    // corner record: F_h [DD], v* [D], M_k [NS]
-    static constexpr int K_FH = 0, K_VST = DD, K_M = DD + D, K_LEN = DD + D + NS;
-    // pass-2 products of a corner: lv* [D], lF* [DD], lN_k [D], lmu, lkappa, leps (half step)
-    static constexpr int Q2_LV = 0, Q2_LF = D, Q2_LN = D + DD, Q2_MU = 2 * D + DD, Q2_KAP = Q2_MU + 1,
-                         Q2_EPS = Q2_KAP + 1, Q2_LEN = Q2_EPS + 1;
-    // pass-1 products of a corner: lF_h [DD], lN_k [D], lmu, lkappa, leps (t^n)
-    static constexpr int Q1_LF = 0, Q1_LN = DD, Q1_MU = DD + D, Q1_KAP = Q1_MU + 1, Q1_EPS = Q1_KAP + 1,
-                         Q1_LEN = Q1_EPS + 1;
-};
 
 LMOOD_HD double adj_rsqrt(double x) {
 #ifdef __CUDA_ARCH__
@@ -1011,7 +1110,8 @@ LMOOD_HD double adj_rsqrt(double x) {
 template <int D>
 LMOOD_HD void predict_fw_rec(const double *xs, const Mom<D> &mom, const double *vc, const double *Fc, double z,
                              double mu, double kap, double im, double dt, double *pf, double *pk, long kstride,
-                             double sa = -1.0, const SgMat *sg = nullptr, double ec = 0.0) {
+                             double sa = -1.0, const SgMat *sg = nullptr, double ec = 0.0, double *bjr = nullptr,
+                             const double *bjlo = nullptr, const double *bjhi = nullptr) {
     using Q = Sz<D>;
     using P = PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ;
@@ -1105,6 +1205,7 @@ LMOOD_HD void predict_fw_rec(const double *xs, const Mom<D> &mom, const double *
             gs[q][a] = ok ? s : 0.0;
             pf[P::F_GS + q * D + a] = gs[q][a];
         }
+    if (bjr) bj_limit<D>(vc, Fc, dk, bjlo, bjhi, gs, pf + P::F_GS, bjr);
     // corner matrices M_k = sum_{f != k} W_f, W_f = (z / |u_f|) u_f u_f^t, u_f = N_f / D
     double W[NV][NS];
     LMOOD_UNROLL
@@ -1274,7 +1375,8 @@ template <int D, class Q2K, class Q1K, class MO>
 LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const double *Fc, double dt, const double *pf,
                                  Q2K &&q2k, Q1K &&q1k, double *lxs, double *lxcc, MO &&mout, double *lvc,
                                  double *lFc, const SgMat *sg = nullptr, double mu = 0.0, double sa = -1.0,
-                                 double im = 0.0, double *lmu = nullptr, double *le = nullptr) {
+                                 double im = 0.0, double *lmu = nullptr, double *le = nullptr,
+                                 double *bjr = nullptr) {
     using Q = Sz<D>;
     using P = PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ;
@@ -1373,6 +1475,8 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
         LMOOD_UNROLL
         for (int a = 0; a < D; ++a) lvc[a] -= lec * vc[a];
     }
+    if (bjr) bj_limit_vjp<D>(dk, lgs, lvc, lFc, lxs, lxcc, bjr);  // the limited level
+    const double *gu = bjr ? bjr + P::B_G : gs;                   // the least squares' own slopes
     // least squares: gs = Gi r
     if (pf[P::F_OK] != 0.0) {
         // gs_q = G^{-1} r_q, G symmetric: lr_q = G^{-1} lgs_q (in place), lG = -sum_q lr_q gs_q^t
@@ -1396,7 +1500,7 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
             LMOOD_UNROLL
             for (int a = 0; a < D; ++a)
                 LMOOD_UNROLL
-                for (int b = 0; b < D; ++b) lG[a * D + b] -= lr(q, a) * gs[q * D + b];
+                for (int b = 0; b < D; ++b) lG[a * D + b] -= lr(q, a) * gu[q * D + b];
         // the -w_k q_c terms of r summed over k: lw_k += lwq (the same for every k), and
         // lq_c -= lr_q . sum_k w_k
         double lwq[D] = {}, wsum[D] = {};
@@ -1505,7 +1609,8 @@ template <int D, class MO>
 LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc, const double *Fc, double z, double mu,
                           double kap, double im, double dt, int ord, const double *lM_in, const double *lR, double *lxs,
                           MO &&mout, double *lvc, double *lFc, double &lz, double &lmu, double &lkap,
-                          double sa = -1.0, const SgMat *sg = nullptr, double ec = 0.0, double *le = nullptr) {
+                          double sa = -1.0, const SgMat *sg = nullptr, double ec = 0.0, double *le = nullptr,
+                          const double *bjlo = nullptr, const double *bjhi = nullptr, double *bjr = nullptr) {
     using Q = Sz<D>;
     using P = PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NM = Q::NMOM;
@@ -1513,7 +1618,8 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
     for (int i = 0; i < NV * NS; ++i) lM[i] = lM_in[i];
     if (ord != 1) {
         double pf[P::F_LEN], pk[NV * P::K_LEN], q2[NV][P::Q2_LEN], q1[NV][P::Q1_LEN];
-        predict_fw_rec<D>(xs, mom, vc, Fc, z, mu, kap, im, dt, pf, pk, P::K_LEN, sa, sg, ec);
+        predict_fw_rec<D>(xs, mom, vc, Fc, z, mu, kap, im, dt, pf, pk, P::K_LEN, sa, sg, ec, bjlo ? bjr : nullptr,
+                          bjlo, bjhi);
         double ldv[D] = {};
         for (int k = 0; k < NV; ++k) {
             predict_corner2_vjp<D>(pf, pk + k * P::K_LEN, k, mu, kap, dt, lR + k * D, lM + k * NS, q2[k], sa, sg);
@@ -1530,7 +1636,8 @@ LMOOD_HD void predict_vjp(const double *xs, const Mom<D> &mom, const double *vc,
         double lxcc[D] = {};
         auto q2k = [&](int k) { return (const double *)q2[k]; };
         auto q1k = [&](int k) { return (const double *)q1[k]; };
-        predict_finish_vjp<D>(mom, vc, Fc, dt, pf, q2k, q1k, lxs, lxcc, mout, lvc, lFc, sg, mu, sa, im, &lmu, le);
+        predict_finish_vjp<D>(mom, vc, Fc, dt, pf, q2k, q1k, lxs, lxcc, mout, lvc, lFc, sg, mu, sa, im, &lmu, le,
+                              bjlo ? bjr : nullptr);
         predict_tail_p1_vjp<D>(xs, z, pf, [&](int k) { return (const double *)(lM + k * NS); }, q2k, q1k, lxcc, lxs,
                                lz);
         return;

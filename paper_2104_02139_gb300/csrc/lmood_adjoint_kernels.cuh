@@ -202,12 +202,14 @@ template <int D> __device__ __forceinline__ bool second_order(const Fld &f, int 
 // (with that shear energy); the neo-Hookean instances compile no code of the others
 template <int MAT> __device__ __forceinline__ double mat_a(const Prm &prm) { return MAT ? prm.shear_a : -1.0; }
 
-template <int D, int MAT> __global__ void __launch_bounds__(128) k_adj_pred_fw(Geo g, Fld f, Prm prm, AdjBuf a) {
+// BJ: the cells at the limited level (order 3) alone, else the other second-order cells
+template <int D, int MAT, bool BJ>
+__global__ void __launch_bounds__(128) k_adj_pred_fw(Geo g, Fld f, Prm prm, AdjBuf a) {
     using Q = adj::Sz<D>;
     using P = adj::PredRec<D>;
-    constexpr int NV = Q::NV, DD = Q::DD, NX = NV * D;
+    constexpr int NV = Q::NV, DD = Q::DD, NX = NV * D, NQ = Q::NQ;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N || !second_order<D>(f, c, 0)) return;
+    if (c >= g.N || !second_order<D>(f, c, 0) || (f.order[c] == 3) != BJ) return;
     const int N = g.N, Np = g.Np;
     double xs[NX], vc[D], Fc[DD];
     adj::Mom<D> mom;
@@ -221,9 +223,46 @@ template <int D, int MAT> __global__ void __launch_bounds__(128) k_adj_pred_fw(G
     for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
     const double mu = f.mu[c], kap = kappa_of(prm, mu), dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
     const adj::SgMat sgm{prm.gamma, prm.pinf, prm.rho0};
+    double lo[BJ ? NQ : 1], hi[BJ ? NQ : 1];
+    int tlo[BJ ? NQ : 1], thi[BJ ? NQ : 1];
+    double *bjr = nullptr;
+    if constexpr (BJ) {
+        // each field's range over the cells around the cell's nodes and the cell, and the cells
+        // that hold its ends: on a tie the cell itself, else the smallest cell id (the choice of
+        // a derivative where the range is not differentiable; the oracle's, whose stencil is in
+        // ascending order)
+        for (int q = 0; q < NQ; ++q) {
+            lo[q] = hi[q] = q < D ? vc[q] : Fc[q - D];
+            tlo[q] = thi[q] = c;
+        }
+        for (int k = 0; k < NV; ++k) {
+            const int p = g.c2n[k * N + c];
+            for (int j = g.n2c_off[p]; j < g.n2c_off[p + 1]; ++j) {
+                const int o = cell_of_corner<D>(g.n2c[j], N);
+                for (int q = 0; q < NQ; ++q) {
+                    const double qo = q < D ? f.v[q * N + o] : f.F[(q - D) * N + o];
+                    if (qo < lo[q] || (qo == lo[q] && tlo[q] != c && o < tlo[q])) {
+                        lo[q] = qo;
+                        tlo[q] = o;
+                    }
+                    if (qo > hi[q] || (qo == hi[q] && thi[q] != c && o < thi[q])) {
+                        hi[q] = qo;
+                        thi[q] = o;
+                    }
+                }
+            }
+        }
+        bjr = a.bj + (size_t)c * P::B_LEN;
+    }
     adj::predict_fw_rec<D>(xs, mom, vc, Fc, f.z[c], mu, kap, f.im[c], dt, a.pf + (size_t)c * P::F_LEN,
                            a.pk + (size_t)c * P::K_LEN, (long)N * P::K_LEN, mat_a<MAT>(prm), MAT == 2 ? &sgm : nullptr,
-                           f.e[c]);
+                           f.e[c], bjr, BJ ? lo : nullptr, BJ ? hi : nullptr);
+    if constexpr (BJ)
+        for (int q = 0; q < NQ; ++q) {
+            const int sel = (int)bjr[P::B_SEL + q], t = sel > 0 ? thi[q] : sel < 0 ? tlo[q] : -1;
+            bjr[P::B_T + q] = t == c ? -1 : t;
+            if (t == c) bjr[P::B_SEL + q] = 2 * sel;  // the cell's own value: phi = 0 identically
+        }
 }
 
 template <int D, int MAT> __global__ void __launch_bounds__(128) k_adj_pred_c2(Geo g, Fld f, Prm prm, AdjBuf a) {
@@ -305,13 +344,14 @@ __device__ __forceinline__ void adj_predict_out(const AdjBuf &a, const Prm &prm,
 // the geometry: the slopes, dF/dt and the least squares; writes the position adjoints of
 // d_k = x_k - x_c (the corner records) and x_c (lxcc, into the pass-1 records' spare room:
 // the pass-1 records are consumed here)
-template <int D, int MAT> __global__ void __launch_bounds__(128) k_adj_pred_fin(Geo g, Fld f, Prm prm, AdjBuf a) {
+template <int D, int MAT, bool BJ>
+__global__ void __launch_bounds__(128) k_adj_pred_fin(Geo g, Fld f, Prm prm, AdjBuf a) {
     using Q = adj::Sz<D>;
     using R = AdjRec<D>;
     using P = adj::PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NX = NV * D;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N || !second_order<D>(f, c, 0)) return;
+    if (c >= g.N || !second_order<D>(f, c, 0) || (f.order[c] == 3) != BJ) return;
     const int N = g.N, Np = g.Np;
     double vc[D], Fc[DD];
     adj::Mom<D> mom;
@@ -332,7 +372,7 @@ template <int D, int MAT> __global__ void __launch_bounds__(128) k_adj_pred_fin(
         [&](int k) { return (const double *)(a.q2 + (size_t)(k * N + c) * P::Q2_LEN); },
         [&](int k) { return (const double *)(a.q1 + (size_t)(k * N + c) * P::Q1_LEN); }, lxs, lxcc,
         MomOut<D>{a.cp, a.cc + (size_t)c * R::CC, N, c}, lvc, lF, MAT == 2 ? &sgm : nullptr, f.mu[c],
-        mat_a<MAT>(prm), f.im[c], &lmu, &le);
+        mat_a<MAT>(prm), f.im[c], &lmu, &le, BJ ? a.bj + (size_t)c * P::B_LEN : nullptr);
     if (MAT == 2) a.lE0[c] += le;
     for (int k = 0; k < NV; ++k)
         for (int b = 0; b < D; ++b) a.cp[(size_t)(k * N + c) * R::CP + R::CP_X + b] = lxs[k * D + b];
@@ -534,6 +574,42 @@ template <int D> __global__ void __launch_bounds__(128) k_adj_z0(Geo g, Fld f, P
     adj::faces_vjp<D>(xs, -lrho * f.m[c] / (V * V), lN0, lxs);
     for (int k = 0; k < NV; ++k)
         for (int b = 0; b < D; ++b) a.cp[(size_t)(k * N + c) * R::CP + R::CP_X + b] += lxs[k * D + b];
+}
+
+// the adjoints of the bounds that set the limited cells' factors: cell o adds those of the
+// limited cells around its nodes that name it (each such cell once: it is skipped at a node
+// of o when it also holds one of o's earlier nodes); no atomics, a fixed order
+template <int D> __global__ void __launch_bounds__(128) k_adj_bj_gather(Geo g, Fld f, AdjBuf a) {
+    using P = adj::PredRec<D>;
+    constexpr int NV = D + 1, NQ = D + D * D;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= g.N) return;
+    const int N = g.N;
+    double l[NQ];
+    for (int q = 0; q < NQ; ++q) l[q] = 0.0;
+    bool any = false;
+    for (int k = 0; k < NV; ++k) {
+        const int p = g.c2n[k * N + o];
+        for (int j = g.n2c_off[p]; j < g.n2c_off[p + 1]; ++j) {
+            const int c = cell_of_corner<D>(g.n2c[j], N);
+            if (f.order[c] != 3) continue;
+            bool seen = false;
+            for (int kk = 0; kk < k; ++kk) {
+                const int pk = g.c2n[kk * N + o];
+                for (int jj = 0; jj < NV; ++jj) seen |= g.c2n[jj * N + c] == pk;
+            }
+            if (seen) continue;
+            const double *r = a.bj + (size_t)c * P::B_LEN;
+            for (int q = 0; q < NQ; ++q)
+                if ((int)r[P::B_T + q] == o) {
+                    l[q] += r[P::B_LE + q];
+                    any = true;
+                }
+        }
+    }
+    if (!any) return;
+    for (int b = 0; b < D; ++b) a.lv0[b * N + o] += l[b];
+    for (int q = 0; q < D * D; ++q) a.lF0[q * N + o] += l[D + q];
 }
 
 // the initial energy e^0 = |v|^2 / 2 + Psi(F) (Eq. EOS_neoHook with the family's shear energy)

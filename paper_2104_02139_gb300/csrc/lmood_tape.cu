@@ -35,6 +35,9 @@ struct lmood_tape_s {
     unsigned char *tmp_order = nullptr;  // [N] scratch orders of the initial packets
     double *gf = nullptr, *gf1 = nullptr;  // the views' cell geometry at x^n, x^{n+1} (the state's
                                            // own buffers carry its current geometry)
+    std::vector<char> bjs;          // [n] 1 if step j has cells at the limited (Barth-Jespersen) level
+    double *bj = nullptr;           // their reverse records [N][B_LEN] (allocated when some step has)
+    int *bjl = nullptr, *bjn = nullptr;  // the list of those cells in a replay, and its length
     AdjBuf a{};
     DevAllocs mem;
 };
@@ -97,6 +100,23 @@ cudaError_t copy_snap(const Snap &dst, const Snap &src, int D, int64_t N, int64_
 
 // one step of the forward scheme on the state's buffers with the recorded dt and orders
 // (t^n in the current buffers -> packets, v*_p and t^{n+1} in the candidate buffers)
+// the cells at the limited level (order 3) into a list
+__global__ static void k_order3_list(const unsigned char *order, int n, int *list, int *cnt) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n && order[c] == 3) list[atomicAdd(cnt, 1)] = c;
+}
+
+// a replay's predictor: every cell in one launch (its orders given), then the cells at the
+// limited level again with their limited slopes (a list launch, as the MOOD loop computed them)
+void replay_predict(lmood_tape t, int64_t j, const Ops &op, const Geo &geo, const Fld &f, const Prm &kr, int N,
+                    cudaStream_t st) {
+    op.predict(geo, f, kr, nullptr, nullptr, N, st);
+    if (!t->bjs[j]) return;
+    cudaMemsetAsync(t->bjn, 0, sizeof(int), st);
+    k_order3_list<<<(N + 255) / 256, 256, 0, st>>>(f.order, N, t->bjl, t->bjn);
+    op.predict(geo, f, kr, t->bjl, t->bjn, N, st);
+}
+
 lmood_status replay_step(lmood_tape t, int64_t j, lmood_state s) {
     lmood_mesh M = s->M;
     const Ops &op = *M->ops;
@@ -110,7 +130,7 @@ lmood_status replay_step(lmood_tape t, int64_t j, lmood_state s) {
     kr.base_order = 0;  // orders as recorded
     kr.mood = 0;        // no detection: the mask is frozen
     op.moments(M->geo, f, st);
-    op.predict(M->geo, f, kr, nullptr, nullptr, N, st);
+    replay_predict(t, j, op, M->geo, f, kr, N, st);
     op.nodes(M->geo, f, nullptr, nullptr, Np, 0, st);
     op.update(M->geo, f, kr, nullptr, nullptr, N, s->tl[0], f.cnt + CNT_T0, st);
     return LMOOD_OK;
@@ -151,7 +171,7 @@ Fld view(lmood_tape t, const Fld &base, const Snap &cur, const Snap &nxt, const 
 // the step kernels through a view (orders as recorded, no detection): t^n -> products, t^{n+1}.
 // geo: compute the view's x^n geometry first (else f.gf already holds it: the previous replay's
 // update wrote it, as the recorded step read it)
-void replay_view(lmood_tape t, const Fld &fr, bool geo) {
+void replay_view(lmood_tape t, const Fld &fr, bool geo, int64_t j) {
     lmood_state s = t->s;
     lmood_mesh M = s->M;
     const Ops &op = *M->ops;
@@ -161,13 +181,13 @@ void replay_view(lmood_tape t, const Fld &fr, bool geo) {
     kr.mood = 0;
     if (geo) op.geometry(M->geo, fr, st);  // the state's own geometry is of another time
     op.moments(M->geo, fr, st);
-    op.predict(M->geo, fr, kr, nullptr, nullptr, (int)M->nc, st);
+    replay_predict(t, j, op, M->geo, fr, kr, (int)M->nc, st);
     op.nodes(M->geo, fr, nullptr, nullptr, (int)M->np, 0, st);
     op.update(M->geo, fr, kr, nullptr, nullptr, (int)M->nc, s->tl[0], fr.cnt + CNT_T0, st);
 }
 
 // the reverse kernels of one step, reading t^n, t^{n+1} and the step's products through f
-void reverse_step(lmood_tape t, AdjBuf &a, const Fld &f) {
+void reverse_step(lmood_tape t, AdjBuf &a, const Fld &f, int64_t j) {
     lmood_state s = t->s;
     lmood_mesh M = s->M;
     const AdjOps &ao = *t->aop;
@@ -175,9 +195,11 @@ void reverse_step(lmood_tape t, AdjBuf &a, const Fld &f) {
     Prm kr = s->kp;
     kr.base_order = 0;
     kr.mood = 0;
+    a.bj = t->bjs[j] ? t->bj : nullptr;
     ao.update(M->geo, f, kr, a, st);
     ao.nodes(M->geo, f, a, 0, st);
     ao.predict(M->geo, f, kr, a, 0, st);
+    ao.bj_gather(M->geo, f, a, st);
     ao.momsum(M->geo, f, a, st);
     ao.cells(M->geo, f, kr, a, 1, st);
     ao.faces(M->geo, f, a, st);
@@ -237,6 +259,7 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     t->s = s;
     t->aop = D == 2 ? &adj_ops_dim2() : &adj_ops_dim3();
     t->n = n_steps;
+    t->bjs.assign((size_t)n_steps, 0);
     t->store = checkpoint_every == 0;
     t->C = t->store ? 1 : std::min(checkpoint_every, n_steps);
     t->n_ck = t->store ? n_steps + 1 : (n_steps + t->C - 1) / t->C;
@@ -317,10 +340,17 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
             tape_free(t);
             return r;
         }
-        if (info.n_lim > 0) {
-            tape_free(t);
-            return fail(LMOOD_ERR_ARG, "lmood_tape_record: step " + std::to_string(info.step) +
-                                           " used the limited (Barth-Jespersen) level, which has no adjoint");
+        t->bjs[j] = info.n_lim > 0;
+        if (info.n_lim > 0 && !t->bj) {  // the first step with limited cells: their buffers
+            const size_t BL = D == 2 ? adj::PredRec<2>::B_LEN : adj::PredRec<3>::B_LEN;
+            lmood_status ra = t->mem.alloc((void **)&t->bj, BL * N * nd);
+            if (!ra) ra = t->mem.alloc((void **)&t->bjl, N * sizeof(int));
+            if (!ra) ra = t->mem.alloc((void **)&t->bjn, sizeof(int));
+            if (ra) {
+                tape_free(t);
+                return ra;
+            }
+            t->bytes += (int64_t)(BL * N * nd + N * sizeof(int) + sizeof(int));
         }
         e = cudaMemcpyAsync(t->masks + j * N, f.order, N, cudaMemcpyDeviceToDevice, st);
         if (t->store && e == cudaSuccess) {
@@ -393,7 +423,7 @@ extern "C" lmood_status lmood_tape_backward_e(lmood_tape t, const double *lam_x,
     // store mode: step j reads states j, j+1 and products j of the tape
     auto stored = [&](int64_t j) { return view(t, f, ck(j), ck(j + 1), prod_at(t->prod + j * t->pd, D, N, Np), j); };
     if (t->store) {
-        for (int64_t j = t->n - 1; j >= 0; --j) reverse_step(t, a, stored(j));
+        for (int64_t j = t->n - 1; j >= 0; --j) reverse_step(t, a, stored(j), j);
     } else {
         // the segment's states: S(0) = its checkpoint, S(i) = seg[i - 1]; products P(i) = prod[i]
         for (int64_t k = t->n_ck - 1; k >= 0; --k) {
@@ -401,10 +431,10 @@ extern "C" lmood_status lmood_tape_backward_e(lmood_tape t, const double *lam_x,
             auto S = [&](int64_t i) { return i == 0 ? ck(k) : snap_at(t->seg + (i - 1) * sd, D, N, Np); };
             auto P = [&](int64_t i) { return prod_at(t->prod + i * t->pd, D, N, Np); };
             for (int64_t i = 0; i < len; ++i) {
-                replay_view(t, view(t, f, S(i), S(i + 1), P(i), b + i), i == 0);
+                replay_view(t, view(t, f, S(i), S(i + 1), P(i), b + i), i == 0, b + i);
                 std::swap(t->gf, t->gf1);  // the update's x^{n+1} geometry is the next replay's x^n
             }
-            for (int64_t i = len - 1; i >= 0; --i) reverse_step(t, a, view(t, f, S(i), S(i + 1), P(i), b + i));
+            for (int64_t i = len - 1; i >= 0; --i) reverse_step(t, a, view(t, f, S(i), S(i + 1), P(i), b + i), b + i);
         }
     }
     if (t->at_init) {
@@ -424,6 +454,7 @@ extern "C" lmood_status lmood_tape_backward_e(lmood_tape t, const double *lam_x,
         ai.lF0 = a.lF1;
         ai.lx0 = a.lx1;
         ai.lE0 = a.lE1;
+        ai.bj = nullptr;  // the t^0 packets are first order
         ao.nodes(M->geo, f0, ai, 1, st);
         ao.predict(M->geo, f0, p0, ai, 1, st);
         ao.z0(M->geo, f0, p0, ai, st);

@@ -386,6 +386,72 @@ template <int D> void check_predict(int ord, double sa = -1.0, const SgMat *sg =
     }
 }
 
+// the Barth-Jespersen level: the stencil's bounds placed so that several fields are limited,
+// and perturbed too (the adjoint of the bound that set each field's phi)
+template <int D> void check_predict_bj() {
+    using Q = Sz<D>;
+    using P = PredRec<D>;
+    constexpr int NV = D + 1, NS = Q::NS, DD = D * D, NM = Q::NMOM, NQ = Q::NQ;
+    for (int t = 0; t < 4; ++t) {
+        Patch<D> Pt;
+        Pt.make();
+        double lM[NV * NS], lR[NV * D], lo[NQ], hi[NQ], dlo[NQ], dhi[NQ];
+        for (int i = 0; i < NV * NS; ++i) lM[i] = U(-1, 1);
+        for (int i = 0; i < NV * D; ++i) lR[i] = U(-1, 1);
+        for (int q = 0; q < NQ; ++q) {  // bounds close to the cell's value: most fields limited
+            const double qc = q < D ? Pt.vc[q] : Pt.Fc[q - D];
+            lo[q] = qc - U(0.001, 0.02) * 0.05;  // (0.05: the patch's cell size)
+            hi[q] = qc + U(0.001, 0.02) * 0.05;
+            dlo[q] = U(-1, 1) * 0.01;
+            dhi[q] = U(-1, 1) * 0.01;
+        }
+        double dxs[NV * D], dmom[NV * NM], dvc[D], dF[DD], dz = U(-1, 1), dmu = U(-1, 1), dk = U(-1, 1);
+        for (int i = 0; i < NV * D; ++i) dxs[i] = U(-1, 1) * 0.05;
+        for (int i = 0; i < NV * NM; ++i) dmom[i] = U(-1, 1) * 0.01;
+        for (int a = 0; a < D; ++a) dvc[a] = U(-1, 1) * 0.01;
+        for (int q = 0; q < DD; ++q) dF[q] = U(-1, 1) * 0.01;
+        const double h = 1e-7;
+        auto eval = [&](double s, double *Mo, double *Ro) {
+            Patch<D> Q2 = Pt;
+            double lo2[NQ], hi2[NQ];
+            for (int i = 0; i < NV * D; ++i) Q2.xs[i] += s * dxs[i];
+            for (int i = 0; i < NV * NM; ++i) Q2.mom[i] += s * dmom[i];
+            for (int a = 0; a < D; ++a) Q2.vc[a] += s * dvc[a];
+            for (int q = 0; q < DD; ++q) Q2.Fc[q] += s * dF[q];
+            for (int q = 0; q < NQ; ++q) {
+                lo2[q] = lo[q] + s * dlo[q];
+                hi2[q] = hi[q] + s * dhi[q];
+            }
+            predict_fw<D>(Q2.xs, Q2.acc(Q2.mom), Q2.vc, Q2.Fc, Pt.z + s * dz, Pt.mu + s * dmu, Pt.kap + s * dk, Pt.im,
+                          Pt.dt, 2, Mo, Ro, -1.0, nullptr, 0.0, lo2, hi2);
+        };
+        double Mp[NV * NS], Rp[NV * D], Mm[NV * NS], Rm[NV * D];
+        eval(h, Mp, Rp);
+        eval(-h, Mm, Rm);
+        double fd = 0.0;
+        for (int i = 0; i < NV * NS; ++i) fd += lM[i] * (Mp[i] - Mm[i]) / (2 * h);
+        for (int i = 0; i < NV * D; ++i) fd += lR[i] * (Rp[i] - Rm[i]) / (2 * h);
+        double lxs[NV * D] = {}, lmom[NV * NM] = {}, lvc[D] = {}, lF[DD] = {}, lz = 0, lmu = 0, lkap = 0, le = 0;
+        double rec[P::B_LEN];
+        predict_vjp<D>(Pt.xs, Pt.acc(Pt.mom), Pt.vc, Pt.Fc, Pt.z, Pt.mu, Pt.kap, Pt.im, Pt.dt, 2, lM, lR, lxs,
+                       [&](int k, int j, double v) { lmom[k * NM + j] = v; }, lvc, lF, lz, lmu, lkap, -1.0, nullptr,
+                       0.0, &le, lo, hi, rec);
+        double an = lz * dz + lmu * dmu + lkap * dk;
+        int limited = 0;
+        for (int i = 0; i < NV * D; ++i) an += lxs[i] * dxs[i];
+        for (int i = 0; i < NV * NM; ++i) an += lmom[i] * dmom[i];
+        for (int a = 0; a < D; ++a) an += lvc[a] * dvc[a];
+        for (int q = 0; q < DD; ++q) an += lF[q] * dF[q];
+        for (int q = 0; q < NQ; ++q) {
+            const int sel = (int)rec[P::B_SEL + q];
+            an += rec[P::B_LE + q] * (sel > 0 ? dhi[q] : sel < 0 ? dlo[q] : 0.0);
+            limited += sel != 0;
+        }
+        report(D == 2 ? "predictbj2" : "predictbj3", fd, an);
+        report(D == 2 ? "predictbjlimited2" : "predictbjlimited3", 1.0, limited > 0 ? 1.0 : 0.0);
+    }
+}
+
 template <int D> void check_update(int ord) {
     using Q = Sz<D>;
     constexpr int NV = D + 1, NS = Q::NS, DD = D * D, NX = NV * D;
@@ -616,6 +682,8 @@ int main() {
     check_node_solve_bc<2>();
     check_node_solve_bc<3>();
     check_moments<2>();
+    check_predict_bj<2>();
+    check_predict_bj<3>();
     check_moments<3>();
     for (int ord = 1; ord <= 2; ++ord) {
         check_predict<2>(ord);

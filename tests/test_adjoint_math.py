@@ -35,3 +35,4 @@ def test_vjps_against_finite_differences():
         for o in (1, 2):
             assert f"predict{d}_ord{o}" in names and f"update{d}_ord{o}" in names
             assert f"predictfam{d}_ord{o}" in names and f"predictsg{d}_ord{o}" in names
+        assert f"predictbj{d}" in names and f"predictbjlimited{d}" in names

@@ -192,6 +192,16 @@ def test_adjoint_fd_shear_family(name):
     _check_init_grads(family_case(name), 5, {}, seed=25, frozen=True)
 
 
+def test_adjoint_fd_limited_level():
+    """the three-level cascade: cells at the limited level (Barth-Jespersen slopes) in the
+    recorded masks, finite differences through the tape's replay (which recomputes them with
+    their limited slopes)"""
+    pb = W.impact2d(n=24)
+    pb.v += 1e-3 * np.random.default_rng(30).standard_normal(pb.v.shape)  # no ties in the stencils' ranges
+    out, masks = _check_init_grads(pb, 6, {"cascade": 3}, seed=29, frozen=True)
+    assert sum(int((m == 3).sum()) for m in masks) > 0, "no cell at the limited level"
+
+
 @pytest.mark.parametrize("name", ["sgwave2d", "sgdrop3d"])
 def test_adjoint_fd_stiffened_gas(name):
     """the stiffened gas (its pressure depends on e, which carries an adjoint)"""
