@@ -341,15 +341,25 @@ def run_ours(args, rank, local, ws, dist):
         nbytes = sum(b.nbytes for b in bufs.values())
         k2 = max(5, args.steps // 4)
         torch.cuda.synchronize()
+        part = [0.0, 0.0, 0.0]  # host wall time of the set (H2D + refresh), the step, the get (D2H)
         t0 = time.perf_counter()
         for _ in range(k2):
+            ta = time.perf_counter()
             sim.set_fields(bufs)
+            tb = time.perf_counter()
             sim.step()
+            tc = time.perf_counter()
             sim.get_fields(bufs)
+            td = time.perf_counter()
+            part[0] += tb - ta
+            part[1] += tc - tb
+            part[2] += td - tc
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t0, dist)
         e2e = {"value": ws * N * k2 / el, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "steps": k2}
+               "steps": k2,
+               "ms_per_step": {"set_h2d": 1e3 * part[0] / k2, "step": 1e3 * part[1] / k2, "get_d2h": 1e3 * part[2] / k2},
+               "gb_per_s": {"h2d": nbytes * k2 / part[0] / 1e9, "d2h": nbytes * k2 / part[2] / 1e9}}
 
     impact = None
     if not args.no_impact and args.workload != "impact2d":
@@ -557,8 +567,13 @@ def run_batched(L, W, torch, local, plain_value, args) -> dict:
                        graph=0 if args.host_mode else 1)
     for _ in range(3):
         sim.step()
+    tuned = None
     if not args.no_autotune:
-        sim.autotune()
+        blocks = sim.autotune()
+        sched = sim.autotune_schedule()
+        tuned = {"blocks": {k2: v["chosen"] for k2, v in blocks.items()},
+                 "node_window": sched["node_window"]["chosen"], "step_form": sched["step_form"]["chosen"],
+                 "step_form_ms": sched["step_form"]["ms"]}
         sim.step()
     k = max(10, args.steps // 5)
     torch.cuda.synchronize()
@@ -576,7 +591,7 @@ def run_batched(L, W, torch, local, plain_value, args) -> dict:
             "plain_2d_value": plain_value, "instances": len(probs),
             "cells": pb.mesh.n_cells, "steps": k, "ms_per_step": ms / k, "troubled_cells": tr,
             "dt_min": float(dt.min()), "dt_max": float(dt.max()), "mesh_generation_s": gen,
-            "launch": "one launch per stage for all instances, graph-captured steps"}
+            "launch": "one launch per stage for all instances, graph-captured steps", "autotuned": tuned}
 
 
 def run_adjoint(L, W, torch, args) -> dict:

@@ -6,7 +6,7 @@ The oracle advances along its own trajectory from the seeded initial data; a fre
 CUDA state takes the same steps. Its MOOD masks must equal the oracle's after every step and
 its state must be within 1e-8 (relative, field-wise) after the run and at checkpoints along
 it; a second CUDA state set to the oracle's state at intervals must take that step within
-1e-11 of the oracle's step (the per-step bar). Configurations: the 2D impact (999,698
+1e-11 of the oracle's step (the per-step bar, field-wise; per component within 1e-10). Configurations: the 2D impact (999,698
 triangles, 2000 steps), the 3D cube of the adjoint configuration (511,104 tetrahedra, 400
 steps), the 256-instance batch's smallest, largest and two random instances (500 steps, the
 batch free-running), and the bending column (5,989,500 tetrahedra) over its first 100 steps
@@ -26,7 +26,11 @@ pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(os.environ.get("LMOOD_CONFIGURED_RUNS") != "1",
                                  reason="long: set LMOOD_CONFIGURED_RUNS=1 to run the configured lengths")]
 
-TOL_STEP, TOL_RUN = 1e-11, 1e-8
+# the state's relative error per step (field-wise) and after the run; each component of a
+# field on its own scale (rows) is reported and held to TOL_ROWS: in the column the transverse
+# rows of v_p and v*_p are far smaller than the lateral one, and its rounding shows at
+# ~1e-11 of them
+TOL_STEP, TOL_RUN, TOL_ROWS = 1e-11, 1e-8, 1e-10
 STATE = ((L.FIELD_X, O.F_X), (L.FIELD_VP, O.F_VP), (L.FIELD_V, O.F_V), (L.FIELD_E, O.F_E), (L.FIELD_F, O.F_F),
          (L.FIELD_TAU, O.F_TAU))
 
@@ -43,7 +47,7 @@ def _configured(pb, n, resync_every, check_every):
     o = O.Oracle(pb)
     g = L.simulation(pb)
     h = L.simulation(pb)
-    worst_step, worst_run, troubled, rounds = 0.0, 0.0, 0, 0
+    worst_step, worst_rows, worst_run, troubled, rounds = 0.0, 0.0, 0.0, 0, 0
     for s in range(n):
         before = push_oracle_state(h, o) if s % resync_every == resync_every - 1 else None
         ig = g.step()
@@ -57,18 +61,21 @@ def _configured(pb, n, resync_every, check_every):
             h.step()
             err = step_errors(h, o, before)
             err["dt"] = abs(h.get(L.FIELD_DT)[0] - o.dt) / o.dt
-            assert max(err.values()) <= TOL_STEP, (s + 1, err)
-            worst_step = max(worst_step, max(err.values()))
+            fw = max(v for k, v in err.items() if not k.endswith("_rows"))
+            rw = max(v for k, v in err.items() if k.endswith("_rows"))
+            assert fw <= TOL_STEP and rw <= TOL_ROWS, (s + 1, err)
+            worst_step, worst_rows = max(worst_step, fw), max(worst_rows, rw)
         if (s + 1) % check_every == 0 or s == n - 1:
             e = max(relerr(g.get(fg), o.get(fo)) for fg, fo in STATE)
             assert e <= TOL_RUN, (s + 1, e)
             worst_run = max(worst_run, e)
-    return worst_step, worst_run, troubled, rounds, e
+    return worst_step, worst_run, troubled, rounds, e, worst_rows
 
 
 def _report(name, n, r):
     print(f"{name} {n} steps: state after the run {r[4]:.2e} (worst along it {r[1]:.2e}), per-step worst "
-          f"{r[0]:.2e}, troubled cell-events {r[2]}, MOOD rounds {r[3]}, masks identical at every step")
+          f"{r[0]:.2e} (per component {r[5]:.2e}), troubled cell-events {r[2]}, MOOD rounds {r[3]}, masks "
+          f"identical at every step")
 
 
 def test_impact2d_2000_steps():
