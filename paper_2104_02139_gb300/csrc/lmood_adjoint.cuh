@@ -166,6 +166,55 @@ LMOOD_HD void stress_vjp(const double *F, double mu, double kap, const double *l
         }
 }
 
+// The same product for a rank-one adjoint lT = l n^t, the form in which the predictor's
+// packets and dv/dt use the stress (T n): with u = F^t n and v = F^t l, lT : B = u . v and
+// (lB + lB^t) F = cj (l u^t + n v^t) for lB = cj l n^t, so B = F F^t is never formed
+// (tr B = |F|^2, plus 1 for the plane-strain F33). Tl_out (may be NULL) receives T l (= l^t T,
+// T symmetric).
+template <int D>
+LMOOD_HD void stress_vjp_r1(const double *F, double mu, double kap, const double *l, const double *n, double *lF,
+                            double &lmu, double &lkap, double *Tl_out = nullptr) {
+    double C[D * D];
+    cofactor<D>(F, C);
+    double J = 0.0;
+    for (int b = 0; b < D; ++b) J += F[b] * C[b];  // det F along the first row
+    const double lJ = adj_log(J), rc = adj_rcbrt(J), Jm23 = rc * rc, invJ = Jm23 * rc;
+    const double J53 = invJ * Jm23, cj = mu * J53;
+    double u[D], v[D], tr = D == 2 ? 1.0 : 0.0, ln = 0.0, uv = 0.0;
+    for (int j = 0; j < D; ++j) {
+        double su = 0.0, sv = 0.0;
+        for (int i = 0; i < D; ++i) {
+            su += F[i * D + j] * n[i];
+            sv += F[i * D + j] * l[i];
+        }
+        u[j] = su;
+        v[j] = sv;
+        uv += su * sv;
+        ln += l[j] * n[j];
+    }
+    for (int q = 0; q < D * D; ++q) tr += F[q] * F[q];
+    const double p0 = J - 1.0 + lJ * invJ;  // p = -(kap/2) p0
+    if (Tl_out) {
+        const double diag = 0.5 * kap * p0 - cj * tr * (1.0 / 3.0);
+        for (int i = 0; i < D; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < D; ++j) s += F[i * D + j] * v[j];  // (B l)_i
+            Tl_out[i] = cj * s + diag * l[i];
+        }
+    }
+    // T = cj B + diag I, diag = -p - cj tr / 3: lcj = u . v - (l . n) tr / 3, lp = -(l . n),
+    // ltr = -(l . n) cj / 3
+    const double lcj = uv - ln * tr * (1.0 / 3.0), ltr2 = -ln * cj * (2.0 / 3.0);
+    lmu += lcj * J53;
+    lkap += ln * 0.5 * p0;
+    const double lJv = lcj * (-5.0 / 3.0) * cj * invJ + ln * 0.5 * kap * (1.0 + (1.0 - lJ) * invJ * invJ);
+    for (int i = 0; i < D; ++i) {
+        const double cl = cj * l[i], cn = cj * n[i];
+        for (int j = 0; j < D; ++j)
+            lF[i * D + j] += cl * u[j] + cn * v[j] + ltr2 * F[i * D + j] + lJv * C[i * D + j];
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Stress of the shear energy family (Eq. familiy_energies with the volumetric part of Eq.
 // EOS_neoHook; a = -1 is the neo-Hookean law above): with Bbar = J^{-2/3} F F^t (plane strain
@@ -1289,21 +1338,30 @@ LMOOD_HD void predict_corner2_vjp(const double *pf, const double *rk, int k, dou
     using P = PredRec<D>;
     constexpr int DD = D * D;
     const double *N = pf + P::F_N + k * D, *vst = rk + P::K_VST;
-    double Fs[DD], lT[DD] = {}, lFs[DD] = {}, T[DD], lvst[D] = {}, lmu = 0.0, lkap = 0.0, leps = 0.0;
+    double Fs[DD], lFs[DD] = {}, lvst[D] = {}, lmu = 0.0, lkap = 0.0, leps = 0.0;
     for (int q = 0; q < DD; ++q) Fs[q] = rk[P::K_FH + q] + 0.5 * dt * pf[P::F_DFDT + q];
     for (int a = 0; a < D; ++a) {
         const double l = lR_k[a];
         for (int b = 0; b < D; ++b) {
             lvst[b] += rk[P::K_M + sym<D>(a, b)] * l;
             lM_k[sym<D>(a, b)] += l * vst[b];
-            lT[a * D + b] += l * N[b] * (1.0 / D);
         }
     }
-    stress_x_vjp<D>(Fs, mu, kap, sa, sg, sg ? pf[P::F_EPH] : 0.0, lT, lFs, lmu, lkap, leps, T);
-    for (int b = 0; b < D; ++b) {
-        double s = 0.0;
-        for (int a = 0; a < D; ++a) s += lR_k[a] * T[a * D + b];
-        q2[P::Q2_LN + b] = s * (1.0 / D);
+    if (!sg && sa == -1.0) {  // neo-Hookean: the rank-one product, lT = lR_k (N_k / D)^t
+        double n[D], Tl[D];
+        for (int b = 0; b < D; ++b) n[b] = N[b] * (1.0 / D);
+        stress_vjp_r1<D>(Fs, mu, kap, lR_k, n, lFs, lmu, lkap, Tl);
+        for (int b = 0; b < D; ++b) q2[P::Q2_LN + b] = Tl[b] * (1.0 / D);
+    } else {
+        double lT[DD], T[DD];
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b) lT[a * D + b] = lR_k[a] * N[b] * (1.0 / D);
+        stress_x_vjp<D>(Fs, mu, kap, sa, sg, sg ? pf[P::F_EPH] : 0.0, lT, lFs, lmu, lkap, leps, T);
+        for (int b = 0; b < D; ++b) {
+            double s = 0.0;
+            for (int a = 0; a < D; ++a) s += lR_k[a] * T[a * D + b];
+            q2[P::Q2_LN + b] = s * (1.0 / D);
+        }
     }
     for (int a = 0; a < D; ++a) q2[P::Q2_LV + a] = lvst[a];
     for (int q = 0; q < DD; ++q) q2[P::Q2_LF + q] = lFs[q];
@@ -1320,14 +1378,19 @@ LMOOD_HD void predict_corner1_vjp(const double *pf, const double *rk, int k, dou
     using P = PredRec<D>;
     constexpr int DD = D * D;
     const double *N = pf + P::F_N + k * D;
-    double lT[DD], lF[DD] = {}, T[DD], lmu = 0.0, lkap = 0.0, leps = 0.0;
-    for (int i = 0; i < D; ++i)
-        for (int b = 0; b < D; ++b) lT[i * D + b] = lacc[i] * N[b];
-    stress_x_vjp<D>(rk + P::K_FH, mu, kap, sa, sg, sg ? pf[P::F_EPS] : 0.0, lT, lF, lmu, lkap, leps, T);
-    for (int b = 0; b < D; ++b) {
-        double s = 0.0;
-        for (int i = 0; i < D; ++i) s += lacc[i] * T[i * D + b];
-        q1[P::Q1_LN + b] = s;
+    double lF[DD] = {}, lmu = 0.0, lkap = 0.0, leps = 0.0;
+    if (!sg && sa == -1.0) {  // neo-Hookean: the rank-one product, lT = lacc N_k^t
+        stress_vjp_r1<D>(rk + P::K_FH, mu, kap, lacc, N, lF, lmu, lkap, q1 + P::Q1_LN);
+    } else {
+        double lT[DD], T[DD];
+        for (int i = 0; i < D; ++i)
+            for (int b = 0; b < D; ++b) lT[i * D + b] = lacc[i] * N[b];
+        stress_x_vjp<D>(rk + P::K_FH, mu, kap, sa, sg, sg ? pf[P::F_EPS] : 0.0, lT, lF, lmu, lkap, leps, T);
+        for (int b = 0; b < D; ++b) {
+            double s = 0.0;
+            for (int i = 0; i < D; ++i) s += lacc[i] * T[i * D + b];
+            q1[P::Q1_LN + b] = s;
+        }
     }
     for (int q = 0; q < DD; ++q) q1[P::Q1_LF + q] = lF[q];
     q1[P::Q1_MU] = lmu;
@@ -1381,17 +1444,26 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
     using P = PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ;
     const double *gs = pf + P::F_GS, *Gi = pf + P::F_GI, *dk = pf + P::F_DK;
-    // lxs collects the adjoints of d_k = x_k - x_c directly (lxcc their negated sum)
-    double lgs[NQ][D], ldFdt[DD];
+    // lxs collects the adjoints of d_k = x_k - x_c directly; lxcc gets their negated sum once,
+    // at the end (lx0: what lxs held on entry)
+    double lgs[NQ][D], ldFdt[DD], lx0[D];
+    LMOOD_UNROLL
+    for (int a = 0; a < D; ++a) {
+        double s = 0.0;
+        LMOOD_UNROLL
+        for (int k = 0; k < NV; ++k) s += lxs[k * D + a];
+        lx0[a] = s;
+    }
     // v*_k = v_c + gs_v d_k + dv
     LMOOD_UNROLL
     for (int i = 0; i < D; ++i) {
-        double l[NV];
+        double l[NV], ls = 0.0;
         LMOOD_UNROLL
         for (int k = 0; k < NV; ++k) {
             l[k] = q2k(k)[P::Q2_LV + i];
-            lvc[i] += l[k];
+            ls += l[k];
         }
+        lvc[i] += ls;
         LMOOD_UNROLL
         for (int a = 0; a < D; ++a) {
             const double g = gs[i * D + a];
@@ -1400,7 +1472,6 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
             for (int k = 0; k < NV; ++k) {
                 s += l[k] * dk[k * D + a];
                 lxs[k * D + a] += l[k] * g;
-                lxcc[a] -= l[k] * g;
             }
             lgs[i][a] = s;
         }
@@ -1408,14 +1479,15 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
     // F*_k = F_h,k + dt/2 dF/dt, F_h,k = F_c + gs_F d_k
     LMOOD_UNROLL
     for (int q = 0; q < DD; ++q) {
-        double l[NV], sfs = 0.0;
+        double l[NV], sfs = 0.0, ls = 0.0;
         LMOOD_UNROLL
         for (int k = 0; k < NV; ++k) {
             const double lfs = q2k(k)[P::Q2_LF + q];
             sfs += lfs;
             l[k] = lfs + q1k(k)[P::Q1_LF + q];
-            lFc[q] += l[k];
+            ls += l[k];
         }
+        lFc[q] += ls;
         ldFdt[q] = 0.5 * dt * sfs;
         LMOOD_UNROLL
         for (int a = 0; a < D; ++a) {
@@ -1425,7 +1497,6 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
             for (int k = 0; k < NV; ++k) {
                 s += l[k] * dk[k * D + a];
                 lxs[k * D + a] += l[k] * g;
-                lxcc[a] -= l[k] * g;
             }
             lgs[D + q][a] = s;
         }
@@ -1446,6 +1517,7 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
         }
     // the stiffened gas: eps_h = eps + dt/2 (T_c : gv) V / m, the corners' stresses at eps
     // (pass 1) and eps_h (pass 2); eps = e - |v|^2 / 2
+    double lVsg = 0.0;
     if (sg) {
         const double V = pf[P::F_V], c = 0.5 * dt * V * im;
         double leh = 0.0, lec = 0.0;
@@ -1466,16 +1538,15 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
         for (int i = 0; i < D; ++i)
             LMOOD_UNROLL
             for (int a = 0; a < D; ++a) lgs[i][a] += c * leh * Tc[i * D + a];
-        const double lV = 0.5 * dt * pw * im * leh, *N = pf + P::F_N;  // dV / dx_k = -N_k / D
-        LMOOD_UNROLL
-        for (int k = 0; k < NV; ++k)
-            LMOOD_UNROLL
-            for (int a = 0; a < D; ++a) lxs[k * D + a] -= lV * N[k * D + a] * (1.0 / D);
+        lVsg = 0.5 * dt * pw * im * leh;  // dV / dx_k = -N_k / D, applied at the end
         *le += lec;
         LMOOD_UNROLL
         for (int a = 0; a < D; ++a) lvc[a] -= lec * vc[a];
     }
-    if (bjr) bj_limit_vjp<D>(dk, lgs, lvc, lFc, lxs, lxcc, bjr);  // the limited level
+    if (bjr) {  // the limited level (its centroid part is taken with the others at the end)
+        double lxcc_bj[D] = {};
+        bj_limit_vjp<D>(dk, lgs, lvc, lFc, lxs, lxcc_bj, bjr);
+    }
     const double *gu = bjr ? bjr + P::B_G : gs;                   // the least squares' own slopes
     // least squares: gs = Gi r
     if (pf[P::F_OK] != 0.0) {
@@ -1494,13 +1565,19 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
             for (int a = 0; a < D; ++a) lgs[q][a] = lr[a];
         }
         auto lr = [&](int q, int a) { return lgs[q][a]; };
-        double lG[DD] = {};
+        // G = G^t is formed from its upper triangle Gs: lGs_ab = lG_ab + lG_ba (a < b), lG_aa,
+        // with lG = -sum_q lr_q gu_q^t
+        double lGs[NS] = {};
         LMOOD_UNROLL
         for (int q = 0; q < NQ; ++q)
             LMOOD_UNROLL
             for (int a = 0; a < D; ++a)
                 LMOOD_UNROLL
-                for (int b = 0; b < D; ++b) lG[a * D + b] -= lr(q, a) * gu[q * D + b];
+                for (int b = a; b < D; ++b) {
+                    double t = lr(q, a) * gu[q * D + b];
+                    if (b != a) t += lr(q, b) * gu[q * D + a];
+                    lGs[sym<D>(a, b)] -= t;
+                }
         // the -w_k q_c terms of r summed over k: lw_k += lwq (the same for every k), and
         // lq_c -= lr_q . sum_k w_k
         double lwq[D] = {}, wsum[D] = {};
@@ -1519,12 +1596,12 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
                 S1[a] = mom(k, Q::M_S1 + a);
                 w[a] = S1[a] + nk * dk[k * D + a];
             }
-            // G += S2 + S1 d^t + d w^t
+            // Gs_ab += S2_ab + S1_a d_b + d_a w_b (a <= b)
             LMOOD_UNROLL
             for (int a = 0; a < D; ++a)
                 LMOOD_UNROLL
-                for (int b = 0; b < D; ++b) {
-                    const double l = lG[a * D + b];
+                for (int b = a; b < D; ++b) {
+                    const double l = lGs[sym<D>(a, b)];
                     lS2[sym<D>(a, b)] += l;
                     lS1[a] += l * dk[k * D + b];
                     ldk[b] += l * S1[a];
@@ -1561,7 +1638,6 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
             for (int a = 0; a < D; ++a) {
                 mout(k, Q::M_S1 + a, lS1[a]);
                 lxs[k * D + a] += ldk[a];
-                lxcc[a] -= ldk[a];
             }
             LMOOD_UNROLL
             for (int s2 = 0; s2 < NS; ++s2) mout(k, Q::M_S2 + s2, lS2[s2]);
@@ -1578,6 +1654,21 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
     } else {
         for (int k = 0; k < NV; ++k)
             for (int j = 0; j < Q::NMOM; ++j) mout(k, j, 0.0);
+    }
+    // x_c = mean of the x_k: the d_k adjoints' negated sum
+    LMOOD_UNROLL
+    for (int a = 0; a < D; ++a) {
+        double s = 0.0;
+        LMOOD_UNROLL
+        for (int k = 0; k < NV; ++k) s += lxs[k * D + a];
+        lxcc[a] -= s - lx0[a];
+    }
+    if (sg) {
+        const double *N = pf + P::F_N;
+        LMOOD_UNROLL
+        for (int k = 0; k < NV; ++k)
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) lxs[k * D + a] -= lVsg * N[k * D + a] * (1.0 / D);
     }
 }
 
@@ -1788,9 +1879,11 @@ LMOOD_HD void update_force_vjp(const double *vs, const double *M, double im, dou
 // out(i, l) (l [NV][D]: 0 lvs, 1 lxs0, 2 lxs1, 3 lvp0, 4 lvp1; zeros where it has no term), so
 // that a caller holds neither all inputs nor all outputs at once. Recomputes only what the
 // product needs (F1 and the impedance term only where used; lz1 = 0 drops the impedance).
+// F1_in (may be NULL): F^{n+1} as the forward step produced it, used instead of recomputing it.
 template <int D, class LD, class OUT>
 LMOOD_HD void update_deform_vjp(LD &&ld, OUT &&out, const double *F, double m, double mu, double kap, double dt,
-                                int ord, const double *lF1_in, double lz1, double *lF, double &lmu, double &lkap) {
+                                int ord, const double *lF1_in, double lz1, double *lF, double &lmu, double &lkap,
+                                const double *F1_in = nullptr) {
     using Q = Sz<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NX = NV * D;
     double lF1[DD], xs[NX], u[NX], N0[NX], V0, l[NX], lN[NX];
@@ -1808,15 +1901,20 @@ LMOOD_HD void update_deform_vjp(LD &&ld, OUT &&out, const double *F, double m, d
         ld(4, u);
         velgrad_iv<D>(u, N1, iV1, L1);
         {
-            double A[DD], Bm[DD], Ai[DD], Rm[DD], F1[DD];
+            double A[DD], Bm[DD], Ai[DD], F1[DD];
             for (int i = 0; i < D; ++i)
                 for (int j = 0; j < D; ++j) {
                     A[i * D + j] = (i == j ? 1.0 : 0.0) - 0.5 * dt * L1[i * D + j];
                     Bm[i * D + j] = (i == j ? 1.0 : 0.0) + 0.5 * dt * L0[i * D + j];
                 }
-            mm<D>(Bm, F, Rm);
             inverse<D>(A, Ai);
-            mm<D>(Ai, Rm, F1);
+            if (F1_in) {
+                for (int q = 0; q < DD; ++q) F1[q] = F1_in[q];
+            } else {
+                double Rm[DD];
+                mm<D>(Bm, F, Rm);
+                mm<D>(Ai, Rm, F1);
+            }
             if (lz1 != 0.0) {  // z1 = Z(F1, m / V1)
                 double lrho = 0.0;
                 impedance_vjp<D>(F1, m * iV1, mu, kap, lz1, lF1, lrho, lmu, lkap);

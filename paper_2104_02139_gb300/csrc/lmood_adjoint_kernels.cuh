@@ -75,8 +75,9 @@ template <int D, bool E> __global__ void __launch_bounds__(128) k_adj_update(Geo
     }
     int pn[NV];
     for (int k = 0; k < NV; ++k) pn[k] = g.c2n[k * N + c];
-    double F[DD], lF1[DD], lF[DD] = {}, lmu = 0.0, lkap = 0.0;
+    double F[DD], F1[DD], lF1[DD], lF[DD] = {}, lmu = 0.0, lkap = 0.0;
     for (int q = 0; q < DD; ++q) F[q] = f.F[q * N + c];
+    for (int q = 0; q < DD; ++q) F1[q] = f.F1[q * N + c];  // F^{n+1} of the recorded step
     for (int q = 0; q < DD; ++q) lF1[q] = a.lF1[q * N + c];
     // nodal inputs read at their use; nodal adjoints stored as they are formed (record slot i
     // of CR_U; the deformation part's lvs added to the velocity part's, stored above)
@@ -91,7 +92,7 @@ template <int D, bool E> __global__ void __launch_bounds__(128) k_adj_update(Geo
             for (int b = 0; b < D; ++b) r[b] = i == 0 ? r[b] + l[k * D + b] : l[k * D + b];
         }
     };
-    adj::update_deform_vjp<D>(ld, out, F, f.m[c], mu, kap, dt, ord, lF1, 0.0, lF, lmu, lkap);
+    adj::update_deform_vjp<D>(ld, out, F, f.m[c], mu, kap, dt, ord, lF1, 0.0, lF, lmu, lkap, F1);
     for (int q = 0; q < DD; ++q) a.lF0[q * N + c] = lF[q];
     a.lmu[c] += lmu + lkap * kappa_mu_factor<D>(prm);
 }

@@ -60,6 +60,43 @@ template <int D> void check_stress() {
     }
 }
 
+// the rank-one form (lT = l n^t): its product against central differences of l^t T(F) n, and
+// its T l against the forward stress
+template <int D> void check_stress_r1() {
+    constexpr int DD = D * D;
+    for (int t = 0; t < 5; ++t) {
+        double F[DD], l[D], n[D], dF[DD], mu = U(0.5, 2), kap = U(1, 4), dmu = U(-1, 1), dk = U(-1, 1);
+        randF<D>(F, 0.2);
+        for (int i = 0; i < D; ++i) {
+            l[i] = U(-1, 1);
+            n[i] = U(-1, 1);
+        }
+        for (int i = 0; i < DD; ++i) dF[i] = U(-1, 1);
+        const double h = 1e-6;
+        double Fp[DD], Fm[DD], Tp[DD], Tm[DD], T[DD];
+        for (int i = 0; i < DD; ++i) {
+            Fp[i] = F[i] + h * dF[i];
+            Fm[i] = F[i] - h * dF[i];
+        }
+        stress<D>(Fp, mu + h * dmu, kap + h * dk, Tp);
+        stress<D>(Fm, mu - h * dmu, kap - h * dk, Tm);
+        double fd = 0.0;
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) fd += l[i] * (Tp[i * D + j] - Tm[i * D + j]) / (2 * h) * n[j];
+        double lF[DD] = {}, lmu = 0, lkap = 0, Tl[D];
+        stress_vjp_r1<D>(F, mu, kap, l, n, lF, lmu, lkap, Tl);
+        double an = lmu * dmu + lkap * dk;
+        for (int i = 0; i < DD; ++i) an += lF[i] * dF[i];
+        report(D == 2 ? "stressr1_2" : "stressr1_3", fd, an);
+        stress<D>(F, mu, kap, T);
+        for (int i = 0; i < D; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < D; ++j) s += T[i * D + j] * l[j];
+            report(D == 2 ? "stressr1T_2" : "stressr1T_3", s, Tl[i]);
+        }
+    }
+}
+
 // the shear energy family (a != -1), and a = -1 through the dispatch against the neo-Hookean
 // routine itself
 template <int D> void check_stress_family() {
@@ -521,6 +558,26 @@ template <int D> void check_update(int ord) {
         char name[32];
         std::snprintf(name, sizeof name, "update%d_ord%d", D, ord);
         report(name, fd, an);
+        // the deformation part given F^{n+1} as the forward produced it equals the one that
+        // recomputes it (the same linearisation point)
+        double v1z[D], F1z[DD], z1z, e1z;
+        eval(0.0, v1z, F1z, z1z, e1z);
+        const double *in[5] = {vs, xs0, xs1, vp0, vp1};
+        double w[5][NX];
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < NX; ++j) w[i][j] = U(-1, 1);
+        double sum[2];
+        for (int pass = 0; pass < 2; ++pass) {
+            double lFd[DD] = {}, lmud = 0, lkapd = 0, acc = 0.0;
+            update_deform_vjp<D>([&](int i, double *u) { for (int j = 0; j < NX; ++j) u[j] = in[i][j]; },
+                                 [&](int i, const double *l) { for (int j = 0; j < NX; ++j) acc += w[i][j] * l[j]; },
+                                 F, m, mu, kap, dt, ord, lF1, lz1, lFd, lmud, lkapd, pass ? F1z : nullptr);
+            acc += lmud * dmu + lkapd * dk;
+            for (int q = 0; q < DD; ++q) acc += lFd[q] * dF[q];
+            sum[pass] = acc;
+        }
+        std::snprintf(name, sizeof name, "updateF1in%d_ord%d", D, ord);
+        report(name, sum[0], sum[1]);
     }
 }
 
@@ -669,6 +726,8 @@ template <int D> void check_moments() {
 int main() {
     check_stress<2>();
     check_stress<3>();
+    check_stress_r1<2>();
+    check_stress_r1<3>();
     check_stress_family<2>();
     check_stress_family<3>();
     check_stiffened_gas<2>();

@@ -29,10 +29,11 @@ def test_vjps_against_finite_differences():
         names.add(name)
         assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-9), (name, fd, an)
     for d in (2, 3):
-        for part in ("stress", "stressfam", "stressfamT", "stressfamNH", "sgpsi", "sgstress", "sgstressT", "sgimp",
+        for part in ("stress", "stressr1_", "stressr1T_", "stressfam", "stressfamT", "stressfamNH", "sgpsi", "sgstress", "sgstressT", "sgimp",
                      "impedance", "faces", "velgrad", "nodesolve", "nodesolvebc", "moments"):
             assert f"{part}{d}" in names
         for o in (1, 2):
             assert f"predict{d}_ord{o}" in names and f"update{d}_ord{o}" in names
+            assert f"updateF1in{d}_ord{o}" in names
             assert f"predictfam{d}_ord{o}" in names and f"predictsg{d}_ord{o}" in names
         assert f"predictbj{d}" in names and f"predictbjlimited{d}" in names
