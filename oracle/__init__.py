@@ -94,6 +94,7 @@ def lib():
         L.orc_mesh_stencil.argtypes = [C.c_void_p, C.c_long, np.ctypeslib.ndpointer(np.int64), C.c_long]
         L.orc_mesh_stencil.restype = C.c_long
         L.orc_debug_corner_values.argtypes = [C.c_void_p, C.c_long, C.c_int, dp, dp, dp]
+        L.orc_debug_predictor.argtypes = [C.c_void_p, C.c_int, C.c_double, dp, dp]
         L.orc_debug_rdmp.argtypes = [C.c_void_p, C.c_long, C.c_double, C.POINTER(C.c_double),
                                      C.POINTER(C.c_double)]
         L.orc_debug_pad.argtypes = [C.c_void_p, C.c_long, dp, C.c_double, dp, C.c_double]
@@ -276,6 +277,15 @@ class Oracle:
         out, lo, hi = np.zeros((d + 1) * nq), np.zeros(nq), np.zeros(nq)
         lib().orc_debug_corner_values(self._h.state, c, level, out, lo, hi)
         return out.reshape(d + 1, nq), lo, hi
+
+    def predictor(self, level: int, dt: float):
+        """(v* [nc][nv][d], F* [nc][nv][d][d]): the predictor's corner values of every cell at
+        the given level (1, 2 or 3) from the current state with time step dt (reading R8)"""
+        d, nc = self.d, self.nc
+        ov, oF = np.zeros(nc * (d + 1) * d), np.zeros(nc * (d + 1) * d * d)
+        if lib().orc_debug_predictor(self._h.state, level, dt, ov, oF) != 0:
+            raise OracleError("orc_debug_predictor: bad level")
+        return ov.reshape(nc, d + 1, d), oF.reshape(nc, d + 1, d, d)
 
     def rdmp(self, c: int, rho_new: float):
         """(admissible, lo, hi): the RDMP decision of Eq. RDMP for a candidate density of cell

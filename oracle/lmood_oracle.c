@@ -37,8 +37,10 @@
  *      v*_cp = v_h(x_p) + dt/2 (1/m_c) sum_q T(F_h(x_q)) (ln)_cq,
  *      F*_cp = F_h(x_p) + dt/2 L^_c F_c with L^_c the reconstructed velocity gradient,
  *      T*_cp = T(F*_cp). First-order (P0) cells use v*_cp = v_c^n, T*_cp = T(F_c^n).
- *      Parity unpinned: the predictor's exact form has no independent reference; only its
- *      observed second order (swinging plate) is pinned.
+ *      The paper gives no formula to compare with; the form is pinned by what the method must
+ *      do (tests/test_oracle_predictor.py): reproduce to round-off the exact homogeneous
+ *      motion x = (I + t L) F0 X (uniform stress, constant particle velocities), and approach
+ *      small-amplitude elastic P and S waves at (x_p, t^{n+1/2}) at second order in h.
  *  R9  reconstruction: least squares about cell centroids over the stencil V_c = all cells
  *      sharing a node with c (the "Voronoi neighbours" of Sect. "Algorithm"; the same set
  *      bounds the RDMP), each neighbour weighted by the number of nodes it shares with c
@@ -844,6 +846,66 @@ static void phase_slopes(const OrcState *S, const int *order, Work *w) {
  *    reading R8; Eqs. Mcp^n, nodal_solver^n):
  *    M_cp   = z_c sum_{f containing p} |l n|_cpf n_cpf (x) n_cpf
  *    rhs_cp = M_cp v*_cp - T*_cp (l n)_cp         so that f_cp = M_cp v*_p - rhs_cp */
+/* the predictor of cell c (reading R8): v*_cp, F*_cp and T*_cp = T(F*_cp) at the cell's
+ * corners for its order (P0: v*_cp = v_c, F*_cp = F_c); eps: the cell's specific internal
+ * energy at t^n */
+static void predict_cell(const OrcState *S, const Work *w, long c, int order_c, real dt, real eps,
+                         real vstar[MAXV][MAXD], real Fstar[MAXV][9], real Tstar[MAXV][9]) {
+    const OrcMesh *M = S->M;
+    int d = M->d, nv = M->nv, dd = d * d;
+    const real *ln = w->ln + c * nv * d;
+    const real *vc = S->v + c * d, *Fc = S->F + c * dd;
+    real rho = S->m[c] / w->V[c];
+    if (order_c != 1) {
+        const real *gv = w->gv + c * dd, *gF = w->gF + c * dd * d;
+        real vh[MAXV][MAXD], Fh[MAXV][9], dvdt[MAXD] = {0, 0, 0}, dFdt[9];
+        for (int k = 0; k < nv; ++k) {
+            int p = M->c2n[c * nv + k];
+            real dx[3];
+            for (int a = 0; a < d; ++a) dx[a] = S->x[p * d + a] - w->xc[c * d + a];
+            for (int i = 0; i < d; ++i) {
+                real s = vc[i];
+                for (int a = 0; a < d; ++a) s += gv[i * d + a] * dx[a];
+                vh[k][i] = s;
+            }
+            for (int i = 0; i < dd; ++i) {
+                real s = Fc[i];
+                for (int a = 0; a < d; ++a) s += gF[i * d + a] * dx[a];
+                Fh[k][i] = s;
+            }
+            real Tk[9], Tn[3];
+            stress_state(S, c, Fh[k], eps, Tk);
+            matvec_n(d, Tk, ln + k * d, Tn);
+            for (int i = 0; i < d; ++i) dvdt[i] += Tn[i];
+        }
+        for (int i = 0; i < d; ++i) dvdt[i] /= S->m[c];
+        matmul_n(d, gv, Fc, dFdt); /* dF/dt = L^ F (Eq. GCLL) with L^ the reconstructed gradient */
+        /* stiffened gas: the internal energy at the half step, d eps/dt = T : L^ / rho with
+         * the cell's stress (reading R18) */
+        real eps_h = eps;
+        if (S->prm.eos != 0) {
+            real Tc[9], pw = 0.0;
+            stress_state(S, c, Fc, eps, Tc);
+            for (int i = 0; i < dd; ++i) pw += Tc[i] * gv[i];
+            eps_h = eps + 0.5 * dt * pw / rho;
+        }
+        for (int k = 0; k < nv; ++k) {
+            real *Fs = Fstar[k];
+            for (int i = 0; i < d; ++i) vstar[k][i] = vh[k][i] + 0.5 * dt * dvdt[i];
+            for (int i = 0; i < dd; ++i) Fs[i] = Fh[k][i] + 0.5 * dt * dFdt[i];
+            stress_state(S, c, Fs, eps_h, Tstar[k]);
+        }
+    } else {
+        real T0[9];
+        stress_state(S, c, Fc, eps, T0);
+        for (int k = 0; k < nv; ++k) {
+            for (int i = 0; i < d; ++i) vstar[k][i] = vc[i];
+            memcpy(Fstar[k], Fc, sizeof(real) * dd);
+            memcpy(Tstar[k], T0, sizeof(real) * dd);
+        }
+    }
+}
+
 static void phase_packets(const OrcState *S, const int *order, real dt, Work *w) {
     const OrcMesh *M = S->M;
     int d = M->d, nv = M->nv, dd = d * d;
@@ -855,54 +917,8 @@ static void phase_packets(const OrcState *S, const int *order, real dt, Work *w)
         real eps = S->e[c];  /* specific internal energy (enters the stiffened gas only) */
         for (int i = 0; i < d; ++i) eps -= 0.5 * vc[i] * vc[i];
         real z = rho * sound_speed_state(S, c, Fc, rho, eps);
-        real vstar[MAXV][MAXD], Tstar[MAXV][9];
-        if (order[c] != 1) {
-            const real *gv = w->gv + c * dd, *gF = w->gF + c * dd * d;
-            real vh[MAXV][MAXD], Fh[MAXV][9], dvdt[MAXD] = {0, 0, 0}, dFdt[9];
-            for (int k = 0; k < nv; ++k) {
-                int p = M->c2n[c * nv + k];
-                real dx[3];
-                for (int a = 0; a < d; ++a) dx[a] = S->x[p * d + a] - w->xc[c * d + a];
-                for (int i = 0; i < d; ++i) {
-                    real s = vc[i];
-                    for (int a = 0; a < d; ++a) s += gv[i * d + a] * dx[a];
-                    vh[k][i] = s;
-                }
-                for (int i = 0; i < dd; ++i) {
-                    real s = Fc[i];
-                    for (int a = 0; a < d; ++a) s += gF[i * d + a] * dx[a];
-                    Fh[k][i] = s;
-                }
-                real Tk[9], Tn[3];
-                stress_state(S, c, Fh[k], eps, Tk);
-                matvec_n(d, Tk, ln + k * d, Tn);
-                for (int i = 0; i < d; ++i) dvdt[i] += Tn[i];
-            }
-            for (int i = 0; i < d; ++i) dvdt[i] /= S->m[c];
-            matmul_n(d, gv, Fc, dFdt); /* dF/dt = L^ F (Eq. GCLL) with L^ the reconstructed gradient */
-            /* stiffened gas: the internal energy at the half step, d eps/dt = T : L^ / rho with
-             * the cell's stress (reading R18) */
-            real eps_h = eps;
-            if (S->prm.eos != 0) {
-                real Tc[9], pw = 0.0;
-                stress_state(S, c, Fc, eps, Tc);
-                for (int i = 0; i < dd; ++i) pw += Tc[i] * gv[i];
-                eps_h = eps + 0.5 * dt * pw / rho;
-            }
-            for (int k = 0; k < nv; ++k) {
-                real Fs[9];
-                for (int i = 0; i < d; ++i) vstar[k][i] = vh[k][i] + 0.5 * dt * dvdt[i];
-                for (int i = 0; i < dd; ++i) Fs[i] = Fh[k][i] + 0.5 * dt * dFdt[i];
-                stress_state(S, c, Fs, eps_h, Tstar[k]);
-            }
-        } else {
-            real T0[9];
-            stress_state(S, c, Fc, eps, T0);
-            for (int k = 0; k < nv; ++k) {
-                for (int i = 0; i < d; ++i) vstar[k][i] = vc[i];
-                memcpy(Tstar[k], T0, sizeof(real) * dd);
-            }
-        }
+        real vstar[MAXV][MAXD], Fstar[MAXV][9], Tstar[MAXV][9];
+        predict_cell(S, w, c, order[c], dt, eps, vstar, Fstar, Tstar);
         for (int k = 0; k < nv; ++k) {
             real *Mk = w->pkM + (c * nv + k) * dd, *Rk = w->pkR + (c * nv + k) * d;
             memset(Mk, 0, sizeof(real) * dd);
@@ -1402,6 +1418,34 @@ int orc_set_state(OrcState *S, const real *x, const real *vp, const real *v, con
     if (e) for (long c = 0; c < nc; ++c) S->e[c] = e[c];
     if (F) for (long c = 0; c < nc; ++c) for (int a = 0; a < dd; ++a) S->F[c * dd + a] = F[a * nc + c];
     if (dt > 0) S->dt = dt;
+    return ORC_OK;
+}
+
+/* The predictor of every cell at the given level (1 first order, 2 unlimited, 3
+ * Barth-Jespersen) from the current state with the time step dt: v*_cp out_v [nc][nv][d] and
+ * F*_cp out_F [nc][nv][d*d] (the values the corner packets are built from). Used by tests. */
+int orc_debug_predictor(const OrcState *S, int level, real dt, real *out_v, real *out_F) {
+    const OrcMesh *M = S->M;
+    if (level < 1 || level > 3) return ORC_ERR_ARG;
+    int d = M->d, nv = M->nv, dd = d * d;
+    Work w = work_new(M);
+    int *order = ORC_NEW(int, M->nc);
+    for (long i = 0; i < M->nc; ++i) order[i] = level;
+    phase_geometry(S, S->x, &w);
+    phase_slopes(S, order, &w);
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < M->nc; ++c) {
+        real eps = S->e[c];
+        for (int i = 0; i < d; ++i) eps -= 0.5 * S->v[c * d + i] * S->v[c * d + i];
+        real vstar[MAXV][MAXD], Fstar[MAXV][9], Tstar[MAXV][9];
+        predict_cell(S, &w, c, level, dt, eps, vstar, Fstar, Tstar);
+        for (int k = 0; k < nv; ++k) {
+            for (int i = 0; i < d; ++i) out_v[(c * nv + k) * d + i] = vstar[k][i];
+            for (int i = 0; i < dd; ++i) out_F[(c * nv + k) * dd + i] = Fstar[k][i];
+        }
+    }
+    free(order);
+    work_free(&w);
     return ORC_OK;
 }
 
