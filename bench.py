@@ -99,13 +99,13 @@ def kernel_bytes(dim: int, nc: int, npn: int, nnz: int) -> dict:
 # 2D: impact2d (999,698 triangles), 3D: a reduced column (30 x 30 x 180 cubes, 972,000
 # tetrahedra), both in profiles/column3d_kernels.md (the full meshes' traffic scales with the
 # cells: every per-cell array is read and written once per launch).
-FP64_FLOP_PER_CELL = {2: {"predict": 797.0, "update": 339.0, "nodes": 31.1, "moments": 120.0},
-                      3: {"predict": 2333.0, "update": 829.0, "nodes": 48.5, "moments": 408.0}}
-FP64_INSTR_PER_CELL = {2: {"predict": 481.0, "update": 215.0, "nodes": 25.0, "moments": 75.0},
-                       3: {"predict": 1348.0, "update": 518.0, "nodes": 44.2, "moments": 240.0}}
-TRAFFIC_PER_CELL = {2: {"predict": 371.8, "update": 468.9, "nodes": 183.4, "moments": 150.5},
-                    3: {"predict": 643.5, "update": 832.2, "nodes": 443.4, "moments": 198.2}}
-COUNTS_SRC = {2: "a292f013c2bc66f4", 3: "a292f013c2bc66f4"}
+FP64_FLOP_PER_CELL = {2: {"predict": 797.0, "update": 325.0, "nodes": 31.1, "moments": 120.0},
+                      3: {"predict": 2333.0, "update": 688.0, "nodes": 48.5, "moments": 408.0}}
+FP64_INSTR_PER_CELL = {2: {"predict": 481.0, "update": 210.0, "nodes": 25.0, "moments": 75.0},
+                       3: {"predict": 1348.0, "update": 429.0, "nodes": 44.2, "moments": 240.0}}
+TRAFFIC_PER_CELL = {2: {"predict": 372.2, "update": 463.9, "nodes": 183.6, "moments": 150.1},
+                    3: {"predict": 641.7, "update": 859.8, "nodes": 412.3, "moments": 198.6}}
+COUNTS_SRC = {2: "c4ddfbddef50d099", 3: "c4ddfbddef50d099"}
 KERNEL_SOURCES = ("lmood_kernels.cuh", "lmood_dev.cuh", "lmood_ops_impl.cuh")
 
 

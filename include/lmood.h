@@ -243,9 +243,10 @@ lmood_status lmood_run(lmood_state s, int64_t nsteps, lmood_step_info *last);
  * Copy a field out of (get) or into (set) the state. dst/src is a device pointer when
  * is_device != 0 (ordered on the mesh's stream), else a host pointer (the call
  * synchronises). Sizes and layouts are those of the field ids above; set accepts X, VP, V,
- * E, F and DT (replacing the dynamic state, e.g. to restart from a checkpoint; setting X
- * or F also refreshes the derived cell geometry, density and impedance, and with the
- * stiffened gas so does setting V or E, on which its impedance depends).
+ * E, F and DT (replacing the dynamic state, e.g. to restart from a checkpoint; setting X,
+ * VP or F also refreshes the derived cell geometry (with the velocity gradient of v_p that
+ * the next update uses as L^n), density and impedance, and with the stiffened gas so does
+ * setting V or E, on which its impedance depends).
  * Errors: LMOOD_ERR_ARG for an unknown or read-only field id.
  */
 lmood_status lmood_get(lmood_state s, int field, void *dst, int is_device);
@@ -254,7 +255,7 @@ lmood_status lmood_set(lmood_state s, int field, const void *src, int is_device)
 /*
  * Several fields in one call: the n copies are queued on the mesh's stream back to back and,
  * for host pointers, the call synchronises once at the end (set: the derived cell geometry
- * is refreshed once, after the last copy, when X or F is among the fields, or with the
+ * is refreshed once, after the last copy, when X, VP or F is among the fields, or with the
  * stiffened gas V or E). fields[i] and
  * dst[i] / src[i] as for lmood_get / lmood_set; all host or all device (is_device).
  * Errors: LMOOD_ERR_ARG for a NULL pointer, an unknown or (set) read-only field id, or ORDER

@@ -682,8 +682,8 @@ static lmood_status state_init(lmood_mesh M, const lmood_material *mat, const do
     A((void **)&f.rlo, Np * nd);
     A((void **)&f.rhi, Np * nd);
     A((void **)&s->mu, N * nd);
-    A((void **)&f.gf, (size_t)(D * NV + 1 + NV) * N * nd);  // CellGeo<D>::LEN
-    A((void **)&f.gf1, (size_t)(D * NV + 1 + NV) * N * nd);
+    A((void **)&f.gf, (size_t)cell_geo_len(D) * N * nd);
+    A((void **)&f.gf1, (size_t)cell_geo_len(D) * N * nd);
     A((void **)&f.pkM, (size_t)NS * NV * N * nd);
     A((void **)&f.pkR, (size_t)D * NV * N * nd);
     A((void **)&f.order, N);
@@ -757,6 +757,7 @@ static lmood_status state_init(lmood_mesh M, const lmood_material *mat, const do
         std::swap(s->tau, f.tau1);
         op.predict(M->geo, f, p0, nullptr, nullptr, (int)N, st);
         op.nodes(M->geo, f, nullptr, nullptr, (int)Np, 1, st);
+        op.geometry(M->geo, f, st);  // the geometry record's velocity gradient, of v_p^0
         op.dt_init(f, p0, M->n_inst, 1, st);
         op.finalize(M->geo, f, p0, st);
         double *dt = const_cast<double *>(f.dt);
@@ -1363,15 +1364,18 @@ extern "C" lmood_status lmood_set_fields(lmood_state s, int n, const int *fields
     }
     lmood_mesh M = s->M;
     cudaStream_t st = M->st;
-    auto is_geo = [&](int i) { return fields[i] == LMOOD_FIELD_X || fields[i] == LMOOD_FIELD_F; };
+    auto is_geo = [&](int i) {
+        return fields[i] == LMOOD_FIELD_X || fields[i] == LMOOD_FIELD_VP || fields[i] == LMOOD_FIELD_F;
+    };
     int n_geo = 0, n_eps = 0;  // (the stiffened gas's impedance depends on eps = e - |v|^2 / 2 too)
     for (int i = 0; i < n; ++i) {
         n_geo += is_geo(i);
         n_eps += s->mat.eos != 0 && (fields[i] == LMOOD_FIELD_V || fields[i] == LMOOD_FIELD_E);
     }
-    // derived cell geometry, density and impedance from the new x and F; the refresh reads
-    // nothing else for the volumetric law of Eq. EOS_neoHook, so it runs on a side stream while
-    // the other fields are copied (the stiffened gas's impedance also needs v and e)
+    // derived cell geometry (with the velocity gradient of v_p), density and impedance from the
+    // new x, v_p and F; the refresh reads nothing else for the volumetric law of Eq.
+    // EOS_neoHook, so it runs on a side stream while the other fields are copied (the stiffened
+    // gas's impedance also needs v and e)
     const bool side = n_geo > 0 && n_geo < n && s->mat.eos == 0;
     auto refresh = [&](cudaStream_t rs) {
         Fld &f = s->f;
@@ -1383,7 +1387,7 @@ extern "C" lmood_status lmood_set_fields(lmood_state s, int n, const int *fields
         LM_CUDA(cudaStreamCreateWithFlags(&s->aux_st, cudaStreamNonBlocking));
         for (auto &e : s->set_ev) LM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    for (int pass = 0; pass < 2; ++pass) {  // X and F first
+    for (int pass = 0; pass < 2; ++pass) {  // X, v_p and F first
         for (int i = 0; i < n; ++i) {
             if (is_geo(i) != (pass == 0)) continue;
             void *dst = nullptr;
@@ -1546,7 +1550,7 @@ struct StateCopy {
         Fld &f = s->f;
         return {{f.x, D * Np * nd}, {f.vp, D * Np * nd}, {f.v, D * N * nd}, {f.e, N * nd}, {f.F, D * D * N * nd},
                 {f.xc, D * N * nd}, {f.rho, N * nd}, {f.z, N * nd}, {s->tau, N * nd}, {f.order, N},
-                {f.gf, (D * (D + 1) + 1 + (D + 1)) * N * nd},
+                {f.gf, (size_t)cell_geo_len((int)D) * N * nd},
                 {const_cast<double *>(f.dt), (size_t)M->n_inst * nd}};
     }
     lmood_status save(lmood_state s) {

@@ -160,11 +160,14 @@ __device__ __forceinline__ void simplex_faces(const double (&xs)[D + 1][D], doub
 
 // A cell's geometry at one set of node positions, kept per cell from the kernel that computes it
 // (the update, at x^{n+1}; init and refresh at the current positions) for the next ones that
-// need it: face area vectors N_f [D+1][D], volume |w_c|, 1 / |N_f| [D+1]. Component i of
-// cell c at gf[i * N + c].
+// need it: face area vectors N_f [D+1][D], volume |w_c|, 1 / |N_f| [D+1], and the velocity
+// gradient L = (1/|w_c|) sum_p v_p (x) (l n)_cp [D*D] of the node velocities at the same time
+// level (the next update's L^n). Component i of cell c at gf[i * N + c].
 template <int D> struct CellGeo {
-    static constexpr int NV = D + 1, NF = 0, VOL = NV * D, RS = NV * D + 1, LEN = NV * D + 1 + NV;
+    static constexpr int NV = D + 1, NF = 0, VOL = NV * D, RS = NV * D + 1, LG = NV * D + 1 + NV,
+                         LEN = NV * D + 1 + NV + D * D;
 };
+inline int cell_geo_len(int D) { return D == 2 ? CellGeo<2>::LEN : CellGeo<3>::LEN; }
 
 // 1 / |N_f| of each face, and |N_f|^2
 template <int D>
@@ -190,6 +193,16 @@ __device__ __forceinline__ void store_cell_geo(double *gf, int N, int c, const d
         gf[(G::RS + k) * N + c] = rs[k];
     }
     gf[G::VOL * N + c] = V;
+}
+
+template <int D> __device__ __forceinline__ void store_cell_grad(double *gf, int N, int c, const double (&L)[D * D]) {
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) gf[(CellGeo<D>::LG + q) * N + c] = L[q];
+}
+
+template <int D> __device__ __forceinline__ void load_cell_grad(const double *gf, int N, int c, double (&L)[D * D]) {
+#pragma unroll
+    for (int q = 0; q < D * D; ++q) L[q] = gf[(CellGeo<D>::LG + q) * N + c];
 }
 
 template <int D>

@@ -735,28 +735,30 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
     const double e1 = fma(dtm, sfv, f.e[c]);
     // the geometry at x^n as the previous step left it; that of x^{n+1} computed and kept for
     // the next step
-    double V0, Nf0[NV][D], V1, Nf1[NV][D], rs1[NV], ss1[NV];
-    load_cell_geo<D>(f.gf, N, c, Nf0, V0);
+    const double V0 = f.gf[CellGeo<D>::VOL * N + c];
+    double V1, Nf1[NV][D], rs1[NV], ss1[NV];
     simplex_faces<D>(xs1, V1, Nf1);
     face_rnorms<D>(Nf1, rs1, ss1);
     store_cell_geo<D>(f.gf1, N, c, Nf1, V1, rs1);
-    // 1 / |w_c| at x^n is rho^n / m_c (rho^n = m_c / |w_c(x^n)| is stored); at x^{n+1} one division
-    const double iV0 = f.rho[c] * im, iV1 = 1.0 / V1;
+    const double iV1 = 1.0 / V1;
     double Fn[DD], F1[DD];
 #pragma unroll
     for (int q = 0; q < DD; ++q) Fn[q] = f.F[q * N + c];
-    if (ord != 1) {
-        double vn[NV][D], L0[DD], L1[DD], A[DD], Bm[DD], Ai[DD], R[DD];
-#pragma unroll
-        for (int k = 0; k < NV; ++k)
-#pragma unroll
-            for (int a = 0; a < D; ++a) vn[k][a] = f.vp[a * Np + nod[k]];
-        vel_gradient<D>(vn, Nf0, iV0, L0);
+    // the velocity gradient of v_p^{n+1} at x^{n+1}: this step's L^{n+1}, kept as the next
+    // step's L^n
+    double L1[DD];
+    {
+        double vn[NV][D];
 #pragma unroll
         for (int k = 0; k < NV; ++k)
 #pragma unroll
             for (int a = 0; a < D; ++a) vn[k][a] = f.vp1[a * Np + nod[k]];
         vel_gradient<D>(vn, Nf1, iV1, L1);
+        store_cell_grad<D>(f.gf1, N, c, L1);
+    }
+    if (ord != 1) {
+        double L0[DD], A[DD], Bm[DD], Ai[DD], R[DD];
+        load_cell_grad<D>(f.gf, N, c, L0);  // L^n, as the previous update (or a refresh) left it
 #pragma unroll
         for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -769,8 +771,10 @@ __device__ __forceinline__ void update_cell(const Geo &g, const Fld &f, const Pr
         inverse<D>(A, Ai);
         matmul<D>(Ai, R, F1);
     } else {
-        double Ls[DD], LF[DD];
-        vel_gradient<D>(vsn, Nf0, iV0, Ls);
+        // 1 / |w_c| at x^n is rho^n / m_c (rho^n = m_c / |w_c(x^n)| is stored)
+        double Nf0[NV][D], V0g, Ls[DD], LF[DD];
+        load_cell_geo<D>(f.gf, N, c, Nf0, V0g);
+        vel_gradient<D>(vsn, Nf0, f.rho[c] * im, Ls);
         matmul<D>(Ls, Fn, LF);
 #pragma unroll
         for (int q = 0; q < DD; ++q) F1[q] = fma(dt, LF[q], Fn[q]);
@@ -1053,6 +1057,22 @@ static __global__ void __launch_bounds__(256) k_finalize(Geo g, Fld f, Prm prm) 
 
 // initial cell state: m = rho0 |w_c|, 1/m, centroid, rho, tau, F (identity when not given),
 // e = |v|^2/2 + Psi(F), impedance, acoustic dt candidate
+// the velocity gradient of the current v_p on the cell's geometry at the current x, kept in the
+// geometry record as the update keeps its L^{n+1} (the same arithmetic: one division for 1/|w_c|)
+template <int D>
+__device__ __forceinline__ void cell_grad_current(const Geo &g, const Fld &f, int c, const double (&Nf)[D + 1][D],
+                                                  double V) {
+    double vn[D + 1][D], L[D * D];
+#pragma unroll
+    for (int k = 0; k < D + 1; ++k) {
+        const int p = g.c2n[k * g.N + c];
+#pragma unroll
+        for (int a = 0; a < D; ++a) vn[k][a] = f.vp[a * g.Np + p];
+    }
+    vel_gradient<D>(vn, Nf, 1.0 / V, L);
+    store_cell_grad<D>(f.gf, g.N, c, L);
+}
+
 template <int D>
 __global__ void __launch_bounds__(kCellBlock) k_init_cells(Geo g, Fld f, Prm prm, double rho0, double *m_out,
                                                            double *im_out, int f_given) {
@@ -1071,9 +1091,9 @@ __global__ void __launch_bounds__(kCellBlock) k_init_cells(Geo g, Fld f, Prm prm
     simplex_faces<D>(xs, V, Nf);
     face_rnorms<D>(Nf, rs, ss);
     store_cell_geo<D>(f.gf, N, c, Nf, V, rs);
-    const double mc = rho0 * V;
+    const double mc = rho0 * V, imc = 1.0 / mc;
     m_out[c] = mc;
-    im_out[c] = 1.0 / mc;
+    im_out[c] = imc;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         double s = 0.0;
@@ -1081,9 +1101,9 @@ __global__ void __launch_bounds__(kCellBlock) k_init_cells(Geo g, Fld f, Prm prm
         for (int k = 0; k < NV; ++k) s += xs[k][a];
         f.xc[a * N + c] = s * (1.0 / NV);
     }
-    const double rho = mc / V;
+    const double rho = mc * (1.0 / V);  // as the update and a refresh compute rho and tau
     f.rho[c] = rho;
-    f.tau1[c] = V / mc;
+    f.tau1[c] = V * imc;
     double F[DD];
 #pragma unroll
     for (int q = 0; q < DD; ++q) {
@@ -1114,8 +1134,8 @@ __global__ void __launch_bounds__(kCellBlock) k_init_cells(Geo g, Fld f, Prm prm
     f.dtc[c] = prm.cfl * insphere<D>(V, Nf) * rho / z;
 }
 
-// derived quantities of the current positions and F: centroid, rho = m / |w_c|,
-// tau = |w_c| / m, impedance z
+// derived quantities of the current positions, v_p and F: the cell geometry record (with the
+// velocity gradient of v_p), centroid, rho = m / |w_c|, tau = |w_c| / m, impedance z
 template <int D> __global__ void __launch_bounds__(kCellBlock) k_refresh(Geo g, Fld f, Prm prm) {
     constexpr int NV = D + 1, DD = D * D;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1131,6 +1151,7 @@ template <int D> __global__ void __launch_bounds__(kCellBlock) k_refresh(Geo g, 
     simplex_faces<D>(xs, V, Nf);
     face_rnorms<D>(Nf, rs, ss);
     store_cell_geo<D>(f.gf, g.N, c, Nf, V, rs);  // as the update stores it
+    cell_grad_current<D>(g, f, c, Nf, V);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         double s = 0.0;
@@ -1155,8 +1176,9 @@ template <int D> __global__ void __launch_bounds__(kCellBlock) k_refresh(Geo g, 
     }
 }
 
-// the cells' geometry at the current positions alone (a view of a recorded state, whose x^n
-// geometry no update has left)
+// the cells' geometry at the current positions and the velocity gradient of the current v_p
+// alone (the initial state once v_p^0 is known, or a view of a recorded state, whose x^n
+// record no update has left)
 template <int D> __global__ void __launch_bounds__(kCellBlock) k_geometry(Geo g, Fld f) {
     constexpr int NV = D + 1;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1172,6 +1194,7 @@ template <int D> __global__ void __launch_bounds__(kCellBlock) k_geometry(Geo g,
     simplex_faces<D>(xs, V, Nf);
     face_rnorms<D>(Nf, rs, ss);
     store_cell_geo<D>(f.gf, g.N, c, Nf, V, rs);
+    cell_grad_current<D>(g, f, c, Nf, V);
 }
 
 // sums of m, m v, m e (diagnostic; atomics, so the last bits depend on scheduling)

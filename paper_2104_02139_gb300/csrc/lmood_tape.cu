@@ -285,8 +285,8 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
         A((void **)&t->seg, t->C * sd * nd);
     }
     A((void **)&t->tmp_order, (size_t)N);
-    A((void **)&t->gf, (size_t)(D * NV + 1 + NV) * N * nd);  // CellGeo<D>::LEN
-    A((void **)&t->gf1, (size_t)(D * NV + 1 + NV) * N * nd);
+    A((void **)&t->gf, (size_t)cell_geo_len(D) * N * nd);
+    A((void **)&t->gf1, (size_t)cell_geo_len(D) * N * nd);
     AdjBuf &a = t->a;
     A((void **)&a.lv1, D * N * nd);
     A((void **)&a.lv0, D * N * nd);

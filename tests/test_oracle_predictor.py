@@ -4,10 +4,11 @@ T(F_h(x_q)) (l n)_q, F*_cp = F_h(x_p) + dt/2 L^ F_c), independent of the step's 
 1. An exact solution it must reproduce to round-off: the homogeneous motion with constant
    particle velocities, x = (I + t L) F0 X (F(t) = (I + t L) F0 uniform, so the stress is
    uniform: no acceleration). From a state at t0 > 0 the corner values at t0 + dt/2 are
-   v*_cp = L F0 X_p and F*_cp = (I + (t0 + dt/2) L) F0, on any mesh and in every cell. A dt in place of dt/2, a dropped dF/dt, a transposed L^ or
-   F_c L^ in place of L^ F_c (L is not symmetric and F0 does not commute with it), or a normal of the wrong corner in the
-   stress sum (the sum of a uniform T over the corners vanishes only with each corner's own
-   l n_q) makes it fail.
+   v*_cp = L F0 X_p and F*_cp = (I + (t0 + dt/2) L) F0, on any mesh and in every cell. A dt
+   in place of dt/2, a dropped dF/dt, a transposed L^ or F_c L^ in place of L^ F_c (L is not
+   symmetric and F0 does not commute with it), or a normal of the wrong corner in the stress
+   sum (the sum of a uniform T over the corners vanishes only with each corner's own l n_q)
+   makes it fail.
 2. Its local order on a smooth solution: small-amplitude plane P and S waves, where the
    neo-Hookean law reduces to linear elasticity with the Lame constants (lambda, mu), have the
    exact solution u = a_p sin(k.X - w_p t) k^ + a_s sin(k.X - w_s t) s^; the predicted corner
