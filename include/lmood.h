@@ -356,11 +356,13 @@ lmood_status lmood_totals_noalloc(int dim, int64_t n_cells, const double *m, con
  * lmood_tape_record: runs n_steps ordinary lmood_step calls on s (the forward pass, with the
  *   MOOD loop and the dt rule as configured) and records what the reverse pass needs: the dt
  *   and the final order mask of every step, and
- *     checkpoint_every = 0 (store mode): every state and every step's corner packets, nodal
- *       solver velocities and node moments; the reverse pass reads them in place (fastest).
- *       Device memory: about n_steps + 1 states plus n_steps step products (a state is
- *       (4 dim + dim^2 + 3) doubles per cell-or-node; the products (dim+1)(dim(dim+1)/2 + dim)
- *       doubles per cell and dim + 1 + dim + dim(dim+1)/2 + (dim + dim^2)(dim + 1) per node);
+ *     checkpoint_every = 0 (store mode): every state and every step's corner packets, the
+ *       predictor's stress sums, nodal solver velocities and node moments (while recording,
+ *       the steps also write the stress sums, which ordinary steps skip); the reverse pass
+ *       reads them in place (fastest). Device memory: about n_steps + 1 states plus n_steps
+ *       step products (a state is (4 dim + dim^2 + 3) doubles per cell-or-node; the products
+ *       (dim+1)(dim(dim+1)/2 + dim) + dim doubles per cell and
+ *       dim + 1 + dim + dim(dim+1)/2 + (dim + dim^2)(dim + 1) per node);
  *     checkpoint_every = C >= 1: a checkpoint of the state every C steps; the reverse pass
  *       rebuilds each segment from its checkpoint (one replay of each step, keeping the
  *       segment's states and products) and runs its reverse kernels on them. Device memory:

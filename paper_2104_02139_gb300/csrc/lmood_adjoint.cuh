@@ -1155,12 +1155,16 @@ LMOOD_HD double adj_rsqrt(double x) {
 
 // forward intermediates of a P1 cell: pf [F_LEN]; corner k's record at pk + k * kstride. The
 // least-squares sums follow the forward kernel's grouping (G symmetric; the q_c terms of the
-// D+1 nodes gathered into one): the same values up to rounding.
+// D+1 nodes gathered into one): the same values up to rounding. dvk (may be NULL): the stress
+// sum sum_k T(F_h,k) N_k of the half-step velocity increment dv = hv sum_k T(F_h,k) N_k as the
+// forward step formed it, component i at dvk[i * dvs]; given, it is taken instead of
+// re-evaluating its D+1 stresses.
 template <int D>
 LMOOD_HD void predict_fw_rec(const double *xs, const Mom<D> &mom, const double *vc, const double *Fc, double z,
                              double mu, double kap, double im, double dt, double *pf, double *pk, long kstride,
                              double sa = -1.0, const SgMat *sg = nullptr, double ec = 0.0, double *bjr = nullptr,
-                             const double *bjlo = nullptr, const double *bjhi = nullptr) {
+                             const double *bjlo = nullptr, const double *bjhi = nullptr,
+                             const double *dvk = nullptr, long dvs = 0) {
     using Q = Sz<D>;
     using P = PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ;
@@ -1292,13 +1296,17 @@ LMOOD_HD void predict_fw_rec(const double *xs, const Mom<D> &mom, const double *
             Fh[q] = s;
             rk[P::K_FH + q] = s;
         }
-        stress_x<D>(Fh, mu, kap, sa, sg, eps_c, T);
-        LMOOD_UNROLL
-        for (int i = 0; i < D; ++i)
+        if (!dvk) {
+            stress_x<D>(Fh, mu, kap, sa, sg, eps_c, T);
             LMOOD_UNROLL
-            for (int b = 0; b < D; ++b) dv[i] += T[i * D + b] * N[k * D + b];
+            for (int i = 0; i < D; ++i)
+                LMOOD_UNROLL
+                for (int b = 0; b < D; ++b) dv[i] += T[i * D + b] * N[k * D + b];
+        }
     }
     const double hv = -0.5 * dt * im * (1.0 / D);
+    LMOOD_UNROLL
+    for (int i = 0; i < D; ++i) dv[i] = hv * (dvk ? dvk[i * dvs] : dv[i]);
     LMOOD_UNROLL
     for (int k = 0; k < NV; ++k) {
         double *rk = pk + k * kstride;
@@ -1307,7 +1315,7 @@ LMOOD_HD void predict_fw_rec(const double *xs, const Mom<D> &mom, const double *
             double s = vc[i];
             LMOOD_UNROLL
             for (int a = 0; a < D; ++a) s += gs[i][a] * dk[k][a];
-            rk[P::K_VST + i] = s + hv * dv[i];
+            rk[P::K_VST + i] = s + dv[i];
         }
     }
     double gv[DD], dFdt[DD];

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(128) k_adj_pred_fw(Geo g, Fld f, Prm prm, AdjB
     }
     adj::predict_fw_rec<D>(xs, mom, vc, Fc, f.z[c], mu, kap, f.im[c], dt, a.pf + (size_t)c * P::F_LEN,
                            a.pk + (size_t)c * P::K_LEN, (long)N * P::K_LEN, mat_a<MAT>(prm), MAT == 2 ? &sgm : nullptr,
-                           f.e[c], bjr, BJ ? lo : nullptr, BJ ? hi : nullptr);
+                           f.e[c], bjr, BJ ? lo : nullptr, BJ ? hi : nullptr, f.dvs ? f.dvs + c : nullptr, (long)N);
     if constexpr (BJ)
         for (int q = 0; q < NQ; ++q) {
             const int sel = (int)bjr[P::B_SEL + q], t = sel > 0 ? thi[q] : sel < 0 ? tlo[q] : -1;

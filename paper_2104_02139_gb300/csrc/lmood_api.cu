@@ -1445,6 +1445,8 @@ static void graphs_destroy(lmood_state s) {
     s->graphs_built = false;
 }
 
+void lmood::graphs_reset(lmood_state_s *s) { graphs_destroy(s); }
+
 extern "C" lmood_status lmood_autotune(lmood_state s, int reps, double *ms12, int32_t *chosen4) {
     if (!s) return fail(LMOOD_ERR_ARG, "lmood_autotune: NULL state");
     if (s->broken) return fail(LMOOD_ERR_STATE, "lmood_autotune: state unusable after an earlier CUDA error");

@@ -78,9 +78,14 @@ struct Fld {
     double *mom;                 // [NMOM][Np] least-squares moments of the cells around each node
     const double *im;            // 1 / m_c
     double *pkM, *pkR;
+    double *dvs;                 // [D][N] or NULL: the predictor's stress sum sum_q T(F_h(x_q)) N_q of
+                                 // the second-order cells (its half-step velocity increment is
+                                 // -dt/2 (1/(D m)) times it), written when set (a tape's record of the
+                                 // step: the reverse pass reads it instead of re-evaluating the D+1
+                                 // stresses it takes)
     double *gf, *gf1;            // [CellGeo<D>::LEN][N] the cells' geometry at x^n / x^{n+1} (face area
-                                 // vectors, volume, 1 / |N_f|): the update writes that of x^{n+1}, which
-                                 // the next step's predictor and update read
+                                 // vectors, volume, 1 / |N_f|, velocity gradient): the update writes that
+                                 // of x^{n+1}, which the next step's predictor and update read
     unsigned char *order, *pflag;
     double *dtc;
     const double *dt;            // [n_inst] dt of this step

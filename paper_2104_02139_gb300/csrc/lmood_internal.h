@@ -137,4 +137,6 @@ lmood_status sync_check(lmood_state s, const char *where);
 namespace lmood {
 // the state is going: its remaining tapes become orphans (destroyable, nothing else)
 void tapes_orphan(lmood_state_s *s);
+// drop the state's captured step graphs (they hold its field pointers; re-captured at the next step)
+void graphs_reset(lmood_state_s *s);
 }  // namespace lmood

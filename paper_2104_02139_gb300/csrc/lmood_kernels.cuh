@@ -387,6 +387,10 @@ __device__ __forceinline__ void predict_cell(const Geo &g, const Fld &f, const P
         }
         // half step of v: dt/2 dv/dt, added to the cell value once
         const double hv = -0.5 * dt * f.im[c] * (1.0 / D);
+        if (f.dvs) {  // the sum itself (its scaling by hv stays fused into v_c + dv below)
+#pragma unroll
+            for (int a = 0; a < D; ++a) f.dvs[a * N + c] = dvdt[a];
+        }
 #pragma unroll
         for (int a = 0; a < D; ++a) dvdt[a] *= hv;
         face_matrices();

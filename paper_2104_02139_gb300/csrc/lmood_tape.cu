@@ -25,8 +25,10 @@ struct lmood_tape_s {
     int64_t n = 0, C = 1, n_ck = 0, bytes = 0, pd = 0;
     uint64_t bc_version = 0;        // the mesh's boundary data the steps were taken with
     bool at_init = false, store = false;
-    double *prod = nullptr;         // store mode: [n] products of each step (pkM, pkR, v*, moments);
-                                    // checkpoint mode: [C] products of the segment's steps
+    double *prod = nullptr;         // store mode: [n] products of each step (pkM, pkR, the
+                                    // predictor's stress sums, the nodal v*_p, moments); checkpoint
+                                    // mode: [C] products of the segment's steps
+    double *dvb = nullptr;          // store mode: the predictor's stress sums the recorded steps write
     double *dts = nullptr;          // [n][n_inst]
     unsigned char *masks = nullptr; // [n][N]
     double *ck = nullptr;           // [n_ck] snapshots of the states at steps 0, C, 2C, ...
@@ -68,11 +70,13 @@ Snap cur_of(const Fld &f) { return Snap{f.x, f.vp, f.v, f.F, f.e, f.z, f.rho, f.
 
 // the products of one step the reverse kernels read, one contiguous block
 struct Prod {
-    double *pkM, *pkR, *vs, *mom;
+    double *pkM, *pkR, *dvs, *vs, *mom;
 };
 
+// a step's products: the corner packets, the second-order cells' predictor stress sums (of
+// their half-step velocity increments), the nodal solver's v*_p and the node moments
 int64_t prod_doubles(int D, int nmom, int64_t N, int64_t Np) {
-    return (int64_t)(D * (D + 1) / 2 + D) * (D + 1) * N + (int64_t)(D + nmom) * Np;
+    return (int64_t)(D * (D + 1) / 2 + D) * (D + 1) * N + (int64_t)D * N + (int64_t)(D + nmom) * Np;
 }
 
 Prod prod_at(double *base, int D, int64_t N, int64_t Np) {
@@ -80,7 +84,8 @@ Prod prod_at(double *base, int D, int64_t N, int64_t Np) {
     Prod q;
     q.pkM = base;
     q.pkR = q.pkM + (int64_t)D * (D + 1) / 2 * NC;
-    q.vs = q.pkR + D * NC;
+    q.dvs = q.pkR + D * NC;
+    q.vs = q.dvs + D * N;
     q.mom = q.vs + D * Np;
     return q;
 }
@@ -159,6 +164,7 @@ Fld view(lmood_tape t, const Fld &base, const Snap &cur, const Snap &nxt, const 
     fr.xc1 = nxt.xc;
     fr.pkM = q.pkM;
     fr.pkR = q.pkR;
+    fr.dvs = q.dvs;  // a replay's predictor writes them, the reverse pass reads them
     fr.vs = q.vs;
     fr.mom = q.mom;
     fr.dt = t->dts + j * M->n_inst;
@@ -280,6 +286,7 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     A((void **)&t->ck, t->n_ck * sd * nd);
     if (t->store) {
         A((void **)&t->prod, n_steps * t->pd * nd);
+        A((void **)&t->dvb, (size_t)D * N * nd);
     } else {
         A((void **)&t->prod, t->C * t->pd * nd);
         A((void **)&t->seg, t->C * sd * nd);
@@ -324,6 +331,25 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
     }
     cudaStream_t st = M->st;
     Fld &f = s->f;
+    // while the whole trajectory is recorded, the steps also write the second-order cells'
+    // predictor stress sums (into dvb, copied into each step's products); the state's
+    // step graphs are re-captured with and again without them
+    struct DvOn {
+        lmood_state s;
+        bool on;
+        DvOn(lmood_state s_, double *buf) : s(s_), on(buf != nullptr) {
+            if (on) {
+                s->f.dvs = buf;
+                graphs_reset(s);
+            }
+        }
+        ~DvOn() {
+            if (on) {
+                s->f.dvs = nullptr;
+                graphs_reset(s);
+            }
+        }
+    } dv_on(s, t->dvb);
     for (int64_t j = 0; j < n_steps; ++j) {
         cudaError_t e = cudaSuccess;
         if (j % t->C == 0) e = copy_snap(snap_at(t->ck + (j / t->C) * sd, D, N, Np), cur_of(f), D, N, Np, st);
@@ -355,10 +381,10 @@ extern "C" lmood_status lmood_tape_record(lmood_state s, int64_t n_steps, int64_
         e = cudaMemcpyAsync(t->masks + j * N, f.order, N, cudaMemcpyDeviceToDevice, st);
         if (t->store && e == cudaSuccess) {
             const Prod q = prod_at(t->prod + j * t->pd, D, N, Np);
-            const std::pair<double *, const double *> cp[4] = {{q.pkM, f.pkM}, {q.pkR, f.pkR}, {q.vs, f.vs},
-                                                               {q.mom, f.mom}};
-            const int64_t len[4] = {NS * NC, D * NC, D * Np, nmom * Np};
-            for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+            const std::pair<double *, const double *> cp[5] = {{q.pkM, f.pkM}, {q.pkR, f.pkR}, {q.dvs, f.dvs},
+                                                               {q.vs, f.vs}, {q.mom, f.mom}};
+            const int64_t len[5] = {NS * NC, D * NC, D * N, D * Np, nmom * Np};
+            for (int i = 0; i < 5 && e == cudaSuccess; ++i)
                 e = cudaMemcpyAsync(cp[i].first, cp[i].second, len[i] * nd, cudaMemcpyDeviceToDevice, st);
         }
         if (e != cudaSuccess) {
