@@ -103,9 +103,9 @@ FP64_FLOP_PER_CELL = {2: {"predict": 797.0, "update": 325.0, "nodes": 31.1, "mom
                       3: {"predict": 2333.0, "update": 688.0, "nodes": 48.5, "moments": 408.0}}
 FP64_INSTR_PER_CELL = {2: {"predict": 481.0, "update": 210.0, "nodes": 25.0, "moments": 75.0},
                        3: {"predict": 1348.0, "update": 429.0, "nodes": 44.2, "moments": 240.0}}
-TRAFFIC_PER_CELL = {2: {"predict": 372.8, "update": 464.2, "nodes": 183.6, "moments": 150.7},
-                    3: {"predict": 641.6, "update": 860.2, "nodes": 411.9, "moments": 198.8}}
-COUNTS_SRC = {2: "189918f457b4299c", 3: "189918f457b4299c"}
+TRAFFIC_PER_CELL = {2: {"predict": 373.2, "update": 464.5, "nodes": 181.6, "moments": 150.4},
+                    3: {"predict": 643.0, "update": 860.1, "nodes": 413.0, "moments": 198.3}}
+COUNTS_SRC = {2: "e26cc0dd37eaaecf", 3: "e26cc0dd37eaaecf"}
 KERNEL_SOURCES = ("lmood_kernels.cuh", "lmood_dev.cuh", "lmood_ops_impl.cuh")
 
 

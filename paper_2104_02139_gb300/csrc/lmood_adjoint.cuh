@@ -607,6 +607,36 @@ LMOOD_HD void velgrad_vjp(const double *vn, const double *N, double V, const dou
 // Nodal solve with a projector: v = K b, K = P (P^t M P)^{-1} P^t (free: M^{-1}; clamped: 0).
 // Product: lb = K lv, lM = -lb (x) v (full matrix).
 // ---------------------------------------------------------------------------------------
+// the Galerkin solve on ND free directions t_i: v = sum_i al_i t_i, (t_i . M t_j) al = t_i . b
+// (ND a compile-time count, so that the small arrays stay in registers)
+template <int D, int ND>
+LMOOD_HD void node_solve_proj(const double *M, const double *b, const double *t /*[2][3]*/, double *v) {
+    double A[ND * ND], r[ND], al[ND];
+    for (int i = 0; i < ND; ++i) {
+        double s = 0.0;
+        for (int a = 0; a < D; ++a) s += t[i * 3 + a] * b[a];
+        r[i] = s;
+        for (int j = 0; j < ND; ++j) {
+            double q = 0.0;
+            for (int a = 0; a < D; ++a)
+                for (int c = 0; c < D; ++c) q += t[i * 3 + a] * M[a * D + c] * t[j * 3 + c];
+            A[i * ND + j] = q;
+        }
+    }
+    if constexpr (ND == 1) {
+        al[0] = r[0] / A[0];
+    } else {
+        const double dA = A[0] * A[3] - A[1] * A[2];
+        al[0] = (A[3] * r[0] - A[1] * r[1]) / dA;
+        al[1] = (-A[2] * r[0] + A[0] * r[1]) / dA;
+    }
+    for (int a = 0; a < D; ++a) {
+        double s = 0.0;
+        for (int i = 0; i < ND; ++i) s += al[i] * t[i * 3 + a];
+        v[a] = s;
+    }
+}
+
 template <int D>
 LMOOD_HD void node_solve(const double *M, const double *b, int nd, const double *t /*[2][3]*/, double *v) {
     if (nd == D) {
@@ -619,31 +649,10 @@ LMOOD_HD void node_solve(const double *M, const double *b, int nd, const double 
         }
     } else if (nd == 0) {
         for (int a = 0; a < D; ++a) v[a] = 0.0;
+    } else if (nd == 1) {
+        node_solve_proj<D, 1>(M, b, t, v);
     } else {
-        double A[4], r[2], al[2] = {0.0, 0.0};
-        for (int i = 0; i < nd; ++i) {
-            double s = 0.0;
-            for (int a = 0; a < D; ++a) s += t[i * 3 + a] * b[a];
-            r[i] = s;
-            for (int j = 0; j < nd; ++j) {
-                double q = 0.0;
-                for (int a = 0; a < D; ++a)
-                    for (int c = 0; c < D; ++c) q += t[i * 3 + a] * M[a * D + c] * t[j * 3 + c];
-                A[i * nd + j] = q;
-            }
-        }
-        if (nd == 1) {
-            al[0] = r[0] / A[0];
-        } else {
-            const double dA = A[0] * A[3] - A[1] * A[2];
-            al[0] = (A[3] * r[0] - A[1] * r[1]) / dA;
-            al[1] = (-A[2] * r[0] + A[0] * r[1]) / dA;
-        }
-        for (int a = 0; a < D; ++a) {
-            double s = 0.0;
-            for (int i = 0; i < nd; ++i) s += al[i] * t[i * 3 + a];
-            v[a] = s;
-        }
+        node_solve_proj<D, 2>(M, b, t, v);
     }
 }
 
@@ -1447,7 +1456,8 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
                                  Q2K &&q2k, Q1K &&q1k, double *lxs, double *lxcc, MO &&mout, double *lvc,
                                  double *lFc, const SgMat *sg = nullptr, double mu = 0.0, double sa = -1.0,
                                  double im = 0.0, double *lmu = nullptr, double *le = nullptr,
-                                 double *bjr = nullptr) {
+                                 double *bjr = nullptr, long qs = 1) {
+    // (vc, Fc: component i at [i * qs], read where they are used)
     using Q = Sz<D>;
     using P = PredRec<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NS = Q::NS, NQ = Q::NQ;
@@ -1517,7 +1527,7 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
             double s = 0.0, u = 0.0;
             LMOOD_UNROLL
             for (int k = 0; k < D; ++k) {
-                s += ldFdt[i * D + k] * Fc[j * D + k];
+                s += ldFdt[i * D + k] * Fc[(j * D + k) * qs];
                 u += gs[k * D + i] * ldFdt[k * D + j];
             }
             lgs[i][j] += s;
@@ -1535,10 +1545,13 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
             lec += q1k(k)[P::Q1_EPS];
         }
         lec += leh;
-        double lTc[DD], Tc[DD], lk = 0.0;
+        double lTc[DD], Tc[DD], lk = 0.0, Fcc[DD];
         LMOOD_UNROLL
-        for (int i = 0; i < DD; ++i) lTc[i] = c * leh * gs[i];  // gs [0..D)[D] is gv
-        stress_x_vjp<D>(Fc, mu, 0.0, sa, sg, pf[P::F_EPS], lTc, lFc, *lmu, lk, lec, Tc);
+        for (int i = 0; i < DD; ++i) {
+            lTc[i] = c * leh * gs[i];  // gs [0..D)[D] is gv
+            Fcc[i] = Fc[i * qs];
+        }
+        stress_x_vjp<D>(Fcc, mu, 0.0, sa, sg, pf[P::F_EPS], lTc, lFc, *lmu, lk, lec, Tc);
         double pw = 0.0;
         LMOOD_UNROLL
         for (int i = 0; i < DD; ++i) pw += Tc[i] * gs[i];
@@ -1549,7 +1562,7 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
         lVsg = 0.5 * dt * pw * im * leh;  // dV / dx_k = -N_k / D, applied at the end
         *le += lec;
         LMOOD_UNROLL
-        for (int a = 0; a < D; ++a) lvc[a] -= lec * vc[a];
+        for (int a = 0; a < D; ++a) lvc[a] -= lec * vc[a * qs];
     }
     if (bjr) {  // the limited level (its centroid part is taken with the others at the end)
         double lxcc_bj[D] = {};
@@ -1558,7 +1571,19 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
     const double *gu = bjr ? bjr + P::B_G : gs;                   // the least squares' own slopes
     // least squares: gs = Gi r
     if (pf[P::F_OK] != 0.0) {
-        // gs_q = G^{-1} r_q, G symmetric: lr_q = G^{-1} lgs_q (in place), lG = -sum_q lr_q gs_q^t
+        // r_q = sum_k (T_q,k + d_k U_q,k) - (sum_k w_k) q_c with w_k = S1_k + n_k d_k; taken field
+        // by field, so that one field's adjoint lr_q is live at a time: wsum first
+        double wsum[D] = {};
+        LMOOD_UNROLL
+        for (int k = 0; k < NV; ++k) {
+            const double nk = mom(k, Q::M_N);
+            LMOOD_UNROLL
+            for (int a = 0; a < D; ++a) wsum[a] += mom(k, Q::M_S1 + a) + nk * dk[k * D + a];
+        }
+        // gs_q = G^{-1} r_q, G symmetric: lr_q = G^{-1} lgs_q; G = G^t is formed from its upper
+        // triangle Gs: lGs_ab = lG_ab + lG_ba (a < b), lG_aa, with lG = -sum_q lr_q gu_q^t; the
+        // -w_k q_c terms: lw_k += lwq (the same for every k) and lq_c -= lr_q . wsum
+        double lGs[NS] = {}, lwq[D] = {}, ldkr[NV][D] = {};
         LMOOD_UNROLL
         for (int q = 0; q < NQ; ++q) {
             double lr[D];
@@ -1570,39 +1595,45 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
                 lr[a] = s;
             }
             LMOOD_UNROLL
-            for (int a = 0; a < D; ++a) lgs[q][a] = lr[a];
-        }
-        auto lr = [&](int q, int a) { return lgs[q][a]; };
-        // G = G^t is formed from its upper triangle Gs: lGs_ab = lG_ab + lG_ba (a < b), lG_aa,
-        // with lG = -sum_q lr_q gu_q^t
-        double lGs[NS] = {};
-        LMOOD_UNROLL
-        for (int q = 0; q < NQ; ++q)
-            LMOOD_UNROLL
             for (int a = 0; a < D; ++a)
                 LMOOD_UNROLL
                 for (int b = a; b < D; ++b) {
-                    double t = lr(q, a) * gu[q * D + b];
-                    if (b != a) t += lr(q, b) * gu[q * D + a];
+                    double t = lr[a] * gu[q * D + b];
+                    if (b != a) t += lr[b] * gu[q * D + a];
                     lGs[sym<D>(a, b)] -= t;
                 }
-        // the -w_k q_c terms of r summed over k: lw_k += lwq (the same for every k), and
-        // lq_c -= lr_q . sum_k w_k
-        double lwq[D] = {}, wsum[D] = {};
-        LMOOD_UNROLL
-        for (int q = 0; q < NQ; ++q) {
-            const double qc = q < D ? vc[q] : Fc[q - D];
+            const double qc = q < D ? vc[q * qs] : Fc[(q - D) * qs];
+            double lq = 0.0;
             LMOOD_UNROLL
-            for (int a = 0; a < D; ++a) lwq[a] -= lr(q, a) * qc;
+            for (int a = 0; a < D; ++a) {
+                lwq[a] -= lr[a] * qc;
+                lq -= lr[a] * wsum[a];
+            }
+            if (q < D) lvc[q] += lq;
+            else lFc[q - D] += lq;
+            // r_q += T_q,k + d_k U_q,k at each node k
+            LMOOD_UNROLL
+            for (int k = 0; k < NV; ++k) {
+                const double Uq = mom(k, Q::M_U + q);
+                double lU = 0.0;
+                LMOOD_UNROLL
+                for (int a = 0; a < D; ++a) {
+                    mout(k, Q::M_T + q * D + a, lr[a]);
+                    ldkr[k][a] += lr[a] * Uq;
+                    lU += lr[a] * dk[k * D + a];
+                }
+                mout(k, Q::M_U + q, lU);
+            }
         }
         LMOOD_UNROLL
         for (int k = 0; k < NV; ++k) {
             const double nk = mom(k, Q::M_N);
-            double S1[D], w[D], lS1[D] = {}, lw[D] = {}, lS2[NS] = {}, ln_ = 0.0, ldk[D] = {};
+            double S1[D], w[D], lS1[D] = {}, lw[D] = {}, lS2[NS] = {}, ln_ = 0.0, ldk[D];
             LMOOD_UNROLL
             for (int a = 0; a < D; ++a) {
                 S1[a] = mom(k, Q::M_S1 + a);
                 w[a] = S1[a] + nk * dk[k * D + a];
+                ldk[a] = ldkr[k][a];
             }
             // Gs_ab += S2_ab + S1_a d_b + d_a w_b (a <= b)
             LMOOD_UNROLL
@@ -1616,28 +1647,10 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
                     ldk[a] += l * w[b];
                     lw[b] += l * dk[k * D + a];
                 }
-            // r_q += T_q + d U_q - w q_c
-            LMOOD_UNROLL
-            for (int q = 0; q < NQ; ++q) {
-                const double Uq = mom(k, Q::M_U + q);
-                double lU = 0.0;
-                LMOOD_UNROLL
-                for (int a = 0; a < D; ++a) {
-                    const double l = lr(q, a);
-                    mout(k, Q::M_T + q * D + a, l);
-                    ldk[a] += l * Uq;
-                    lU += l * dk[k * D + a];
-                }
-                mout(k, Q::M_U + q, lU);
-            }
-            LMOOD_UNROLL
-            for (int a = 0; a < D; ++a) {
-                lw[a] += lwq[a];
-                wsum[a] += w[a];
-            }
             // w = S1 + n d
             LMOOD_UNROLL
             for (int a = 0; a < D; ++a) {
+                lw[a] += lwq[a];
                 lS1[a] += lw[a];
                 ldk[a] += nk * lw[a];
                 ln_ += lw[a] * dk[k * D + a];
@@ -1650,14 +1663,6 @@ LMOOD_HD void predict_finish_vjp(const Mom<D> &mom, const double *vc, const doub
             LMOOD_UNROLL
             for (int s2 = 0; s2 < NS; ++s2) mout(k, Q::M_S2 + s2, lS2[s2]);
             mout(k, Q::M_N, ln_);
-        }
-        LMOOD_UNROLL
-        for (int q = 0; q < NQ; ++q) {
-            double lq = 0.0;
-            LMOOD_UNROLL
-            for (int a = 0; a < D; ++a) lq -= lr(q, a) * wsum[a];
-            if (q < D) lvc[q] += lq;
-            else lFc[q - D] += lq;
         }
     } else {
         for (int k = 0; k < NV; ++k)
@@ -1888,14 +1893,18 @@ LMOOD_HD void update_force_vjp(const double *vs, const double *M, double im, dou
 // that a caller holds neither all inputs nor all outputs at once. Recomputes only what the
 // product needs (F1 and the impedance term only where used; lz1 = 0 drops the impedance).
 // F1_in (may be NULL): F^{n+1} as the forward step produced it, used instead of recomputing it.
+// F, lF1_in and F1_in hold component q at [q * fs] (a cell's column of structure-of-arrays
+// fields, or fs = 1), and are read where they are used.
 template <int D, class LD, class OUT>
 LMOOD_HD void update_deform_vjp(LD &&ld, OUT &&out, const double *F, double m, double mu, double kap, double dt,
                                 int ord, const double *lF1_in, double lz1, double *lF, double &lmu, double &lkap,
-                                const double *F1_in = nullptr) {
+                                const double *F1_in = nullptr, long fs = 1) {
     using Q = Sz<D>;
     constexpr int NV = Q::NV, DD = Q::DD, NX = NV * D;
     double lF1[DD], xs[NX], u[NX], N0[NX], V0, l[NX], lN[NX];
-    for (int q = 0; q < DD; ++q) lF1[q] = lF1_in[q];
+    auto get = [&](const double *p, double *o) {
+        for (int q = 0; q < DD; ++q) o[q] = p[q * fs];
+    };
     ld(1, xs);
     faces<D>(xs, V0, N0);
     const double iV0 = 1.0 / V0;
@@ -1909,20 +1918,22 @@ LMOOD_HD void update_deform_vjp(LD &&ld, OUT &&out, const double *F, double m, d
         ld(4, u);
         velgrad_iv<D>(u, N1, iV1, L1);
         {
-            double A[DD], Bm[DD], Ai[DD], F1[DD];
+            double A[DD], Bm[DD], Ai[DD], F1[DD], Fn[DD];
             for (int i = 0; i < D; ++i)
                 for (int j = 0; j < D; ++j) {
                     A[i * D + j] = (i == j ? 1.0 : 0.0) - 0.5 * dt * L1[i * D + j];
                     Bm[i * D + j] = (i == j ? 1.0 : 0.0) + 0.5 * dt * L0[i * D + j];
                 }
             inverse<D>(A, Ai);
+            get(F, Fn);
             if (F1_in) {
-                for (int q = 0; q < DD; ++q) F1[q] = F1_in[q];
+                get(F1_in, F1);
             } else {
                 double Rm[DD];
-                mm<D>(Bm, F, Rm);
+                mm<D>(Bm, Fn, Rm);
                 mm<D>(Ai, Rm, F1);
             }
+            get(lF1_in, lF1);
             if (lz1 != 0.0) {  // z1 = Z(F1, m / V1)
                 double lrho = 0.0;
                 impedance_vjp<D>(F1, m * iV1, mu, kap, lz1, lF1, lrho, lmu, lkap);
@@ -1932,7 +1943,7 @@ LMOOD_HD void update_deform_vjp(LD &&ld, OUT &&out, const double *F, double m, d
             double lRm[DD], lA[DD], lBm[DD], t[DD];
             mtm<D>(Ai, lF1, lRm);  // lRm = Ai^t lF1
             mmt<D>(lRm, F1, lA);   // lA = -lRm F1^t
-            mmt<D>(lRm, F, lBm);   // lBm = lRm F^t
+            mmt<D>(lRm, Fn, lBm);  // lBm = lRm F^t
             mtm<D>(Bm, lRm, t);    // lF += Bm^t lRm
             for (int q = 0; q < DD; ++q) {
                 lF[q] += t[q];
@@ -1959,16 +1970,18 @@ LMOOD_HD void update_deform_vjp(LD &&ld, OUT &&out, const double *F, double m, d
         for (int i = 0; i < NX; ++i) l[i] = 0.0;
         out(0, l);
     } else {
-        double Ls[DD], t[DD], lLs[DD], lV1 = 0.0, lV0 = 0.0;
+        double Ls[DD], t[DD], lLs[DD], lV1 = 0.0, lV0 = 0.0, Fn[DD];
         ld(0, u);
         velgrad_iv<D>(u, N0, iV0, Ls);
+        get(F, Fn);
+        get(lF1_in, lF1);
         if (lz1 != 0.0) {
             double LF[DD], F1[DD], lrho = 0.0, V1, N1[NX];
             ld(2, xs);
             faces<D>(xs, V1, N1);
             const double iV1 = 1.0 / V1;
-            mm<D>(Ls, F, LF);
-            for (int q = 0; q < DD; ++q) F1[q] = F[q] + dt * LF[q];
+            mm<D>(Ls, Fn, LF);
+            for (int q = 0; q < DD; ++q) F1[q] = Fn[q] + dt * LF[q];
             impedance_vjp<D>(F1, m * iV1, mu, kap, lz1, lF1, lrho, lmu, lkap);
             lV1 -= lrho * m * iV1 * iV1;
             for (int i = 0; i < NX; ++i) l[i] = lN[i] = 0.0;
@@ -1981,7 +1994,7 @@ LMOOD_HD void update_deform_vjp(LD &&ld, OUT &&out, const double *F, double m, d
         }
         mtm<D>(Ls, lF1, t);
         for (int q = 0; q < DD; ++q) lF[q] += lF1[q] + dt * t[q];
-        mmt<D>(lF1, F, lLs);
+        mmt<D>(lF1, Fn, lLs);
         for (int q = 0; q < DD; ++q) lLs[q] *= dt;
         for (int i = 0; i < NX; ++i) l[i] = lN[i] = 0.0;
         velgrad_vjp_iv<D>(u, N0, iV0, Ls, lLs, l, lN, lV0);

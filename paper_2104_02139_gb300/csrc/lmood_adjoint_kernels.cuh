@@ -75,10 +75,7 @@ template <int D, bool E> __global__ void __launch_bounds__(128) k_adj_update(Geo
     }
     int pn[NV];
     for (int k = 0; k < NV; ++k) pn[k] = g.c2n[k * N + c];
-    double F[DD], F1[DD], lF1[DD], lF[DD] = {}, lmu = 0.0, lkap = 0.0;
-    for (int q = 0; q < DD; ++q) F[q] = f.F[q * N + c];
-    for (int q = 0; q < DD; ++q) F1[q] = f.F1[q * N + c];  // F^{n+1} of the recorded step
-    for (int q = 0; q < DD; ++q) lF1[q] = a.lF1[q * N + c];
+    double lF[DD] = {}, lmu = 0.0, lkap = 0.0;
     // nodal inputs read at their use; nodal adjoints stored as they are formed (record slot i
     // of CR_U; the deformation part's lvs added to the velocity part's, stored above)
     auto ld = [&](int i, double *u) {
@@ -92,7 +89,9 @@ template <int D, bool E> __global__ void __launch_bounds__(128) k_adj_update(Geo
             for (int b = 0; b < D; ++b) r[b] = i == 0 ? r[b] + l[k * D + b] : l[k * D + b];
         }
     };
-    adj::update_deform_vjp<D>(ld, out, F, f.m[c], mu, kap, dt, ord, lF1, 0.0, lF, lmu, lkap, F1);
+    // F^n, the adjoint of F^{n+1} and F^{n+1} of the recorded step read where they are used
+    adj::update_deform_vjp<D>(ld, out, f.F + c, f.m[c], mu, kap, dt, ord, a.lF1 + c, 0.0, lF, lmu, lkap, f.F1 + c,
+                              (long)N);
     for (int q = 0; q < DD; ++q) a.lF0[q * N + c] = lF[q];
     a.lmu[c] += lmu + lkap * kappa_mu_factor<D>(prm);
 }
@@ -354,12 +353,9 @@ __global__ void __launch_bounds__(128) k_adj_pred_fin(Geo g, Fld f, Prm prm, Adj
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N || !second_order<D>(f, c, 0) || (f.order[c] == 3) != BJ) return;
     const int N = g.N, Np = g.Np;
-    double vc[D], Fc[DD];
     adj::Mom<D> mom;
     mom.stride = Np;
     for (int k = 0; k < NV; ++k) mom.p[k] = f.mom + g.c2n[k * N + c];
-    for (int b = 0; b < D; ++b) vc[b] = f.v[b * N + c];
-    for (int q = 0; q < DD; ++q) Fc[q] = f.F[q * N + c];
     const double dt = f.dt[g.cell_inst ? g.cell_inst[c] : 0];
     double lxs[NX] = {}, lxcc[D] = {}, lvc[D] = {}, lF[DD] = {}, lmu = 0.0, lkap = 0.0, le = 0.0;
     for (int k = 0; k < NV; ++k) {
@@ -369,11 +365,11 @@ __global__ void __launch_bounds__(128) k_adj_pred_fin(Geo g, Fld f, Prm prm, Adj
     }
     const adj::SgMat sgm{prm.gamma, prm.pinf, prm.rho0};
     adj::predict_finish_vjp<D>(
-        mom, vc, Fc, dt, a.pf + (size_t)c * P::F_LEN,
+        mom, f.v + c, f.F + c, dt, a.pf + (size_t)c * P::F_LEN,
         [&](int k) { return (const double *)(a.q2 + (size_t)(k * N + c) * P::Q2_LEN); },
         [&](int k) { return (const double *)(a.q1 + (size_t)(k * N + c) * P::Q1_LEN); }, lxs, lxcc,
         MomOut<D>{a.cp, a.cc + (size_t)c * R::CC, N, c}, lvc, lF, MAT == 2 ? &sgm : nullptr, f.mu[c],
-        mat_a<MAT>(prm), f.im[c], &lmu, &le, BJ ? a.bj + (size_t)c * P::B_LEN : nullptr);
+        mat_a<MAT>(prm), f.im[c], &lmu, &le, BJ ? a.bj + (size_t)c * P::B_LEN : nullptr, (long)N);
     if (MAT == 2) a.lE0[c] += le;
     for (int k = 0; k < NV; ++k)
         for (int b = 0; b < D; ++b) a.cp[(size_t)(k * N + c) * R::CP + R::CP_X + b] = lxs[k * D + b];

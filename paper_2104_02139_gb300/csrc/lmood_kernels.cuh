@@ -448,6 +448,53 @@ __global__ void __launch_bounds__(B, D == 2 ? 512 / B : 1) k_predict(Geo g, Fld 
 // ---------------------------------------------------------------------------------------
 // Galerkin solve of M v = rhs on the node's free subspace (Eq. sBC1): nd = D free, 0 clamped,
 // else the span of the node's nd tangent vectors
+// the Galerkin solve on the node's ND free directions t_i (ND a compile-time count, so that the
+// small arrays stay in registers)
+template <int D, int ND>
+__device__ __forceinline__ void solve_K_proj(const Geo &g, const double (&M)[D * D], int p, const double (&rhs)[D],
+                                             double (&v)[D]) {
+    const int Np = g.Np;
+    double t[ND][D], A[ND * ND], r[ND], al[ND];
+#pragma unroll
+    for (int i = 0; i < ND; ++i)
+#pragma unroll
+        for (int a = 0; a < D; ++a) t[i][a] = g.bc_t[(i * 3 + a) * Np + p];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) s += t[i][a] * rhs[a];
+        r[i] = s;
+#pragma unroll
+        for (int j = 0; j < ND; ++j) {
+            double q = 0.0;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                double mt = 0.0;
+#pragma unroll
+                for (int c = 0; c < D; ++c) mt += M[a * D + c] * t[j][c];
+                q += t[i][a] * mt;
+            }
+            A[i * ND + j] = q;
+        }
+    }
+    if constexpr (ND == 1) {
+        al[0] = r[0] / A[0];
+    } else {
+        const double dA = A[0] * A[3] - A[1] * A[2];
+        const double idA = 1.0 / dA;
+        al[0] = (A[3] * idA) * r[0] + (-A[1] * idA) * r[1];
+        al[1] = (-A[2] * idA) * r[0] + (A[0] * idA) * r[1];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < ND; ++i) s += al[i] * t[i][a];
+        v[a] = s;
+    }
+}
+
 template <int D>
 __device__ __forceinline__ void solve_K(const Geo &g, const double (&M)[D * D], int nd, int p, const double (&rhs)[D],
                                         double (&v)[D]) {
@@ -466,44 +513,10 @@ __device__ __forceinline__ void solve_K(const Geo &g, const double (&M)[D * D], 
     } else if (nd == 0) {
 #pragma unroll
         for (int a = 0; a < D; ++a) v[a] = 0.0;
+    } else if (nd == 1) {
+        solve_K_proj<D, 1>(g, M, p, rhs, v);
     } else {
-        double t[2][D], A[4], r[2], al[2];
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int a = 0; a < D; ++a) t[i][a] = g.bc_t[(i * 3 + a) * Np + p];
-        for (int i = 0; i < nd; ++i) {
-            double s = 0.0;
-#pragma unroll
-            for (int a = 0; a < D; ++a) s += t[i][a] * rhs[a];
-            r[i] = s;
-            for (int j = 0; j < nd; ++j) {
-                double q = 0.0;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    double mt = 0.0;
-#pragma unroll
-                    for (int c = 0; c < D; ++c) mt += M[a * D + c] * t[j][c];
-                    q += t[i][a] * mt;
-                }
-                A[i * nd + j] = q;
-            }
-        }
-        if (nd == 1) {
-            al[0] = r[0] / A[0];
-            al[1] = 0.0;
-        } else {
-            const double dA = A[0] * A[3] - A[1] * A[2];
-            const double idA = 1.0 / dA;
-            al[0] = (A[3] * idA) * r[0] + (-A[1] * idA) * r[1];
-            al[1] = (-A[2] * idA) * r[0] + (A[0] * idA) * r[1];
-        }
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            double s = 0.0;
-            for (int i = 0; i < nd; ++i) s += al[i] * t[i][a];
-            v[a] = s;
-        }
+        solve_K_proj<D, 2>(g, M, p, rhs, v);
     }
 }
 

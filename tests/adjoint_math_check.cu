@@ -566,18 +566,29 @@ template <int D> void check_update(int ord) {
         double w[5][NX];
         for (int i = 0; i < 5; ++i)
             for (int j = 0; j < NX; ++j) w[i][j] = U(-1, 1);
-        double sum[2];
-        for (int pass = 0; pass < 2; ++pass) {
+        // pass 2: the same inputs as pass 1 read with a stride (a cell's column of SoA fields)
+        double Fs2[2 * DD], lF1s2[2 * DD], F1s2[2 * DD];
+        for (int q = 0; q < DD; ++q) {
+            Fs2[2 * q] = F[q];
+            lF1s2[2 * q] = lF1[q];
+            F1s2[2 * q] = F1z[q];
+            Fs2[2 * q + 1] = lF1s2[2 * q + 1] = F1s2[2 * q + 1] = 1e300;  // never read
+        }
+        double sum[3];
+        for (int pass = 0; pass < 3; ++pass) {
             double lFd[DD] = {}, lmud = 0, lkapd = 0, acc = 0.0;
             update_deform_vjp<D>([&](int i, double *u) { for (int j = 0; j < NX; ++j) u[j] = in[i][j]; },
                                  [&](int i, const double *l) { for (int j = 0; j < NX; ++j) acc += w[i][j] * l[j]; },
-                                 F, m, mu, kap, dt, ord, lF1, lz1, lFd, lmud, lkapd, pass ? F1z : nullptr);
+                                 pass == 2 ? Fs2 : F, m, mu, kap, dt, ord, pass == 2 ? lF1s2 : lF1, lz1, lFd, lmud,
+                                 lkapd, pass == 2 ? F1s2 : pass ? F1z : nullptr, pass == 2 ? 2 : 1);
             acc += lmud * dmu + lkapd * dk;
             for (int q = 0; q < DD; ++q) acc += lFd[q] * dF[q];
             sum[pass] = acc;
         }
         std::snprintf(name, sizeof name, "updateF1in%d_ord%d", D, ord);
         report(name, sum[0], sum[1]);
+        std::snprintf(name, sizeof name, "updatestride%d_ord%d", D, ord);
+        report(name, sum[1], sum[2]);
     }
 }
 

@@ -34,6 +34,6 @@ def test_vjps_against_finite_differences():
             assert f"{part}{d}" in names
         for o in (1, 2):
             assert f"predict{d}_ord{o}" in names and f"update{d}_ord{o}" in names
-            assert f"updateF1in{d}_ord{o}" in names
+            assert f"updateF1in{d}_ord{o}" in names and f"updatestride{d}_ord{o}" in names
             assert f"predictfam{d}_ord{o}" in names and f"predictsg{d}_ord{o}" in names
         assert f"predictbj{d}" in names and f"predictbjlimited{d}" in names
