@@ -147,22 +147,24 @@ def _tag_faces(x_rows: np.ndarray, faces: np.ndarray, lo, hi, bc: dict) -> tuple
 
 # ----------------------------------------------------------------------------- 2D
 def tri_mesh(n: int, seed: int, lx: float = 1.0, ly: float = 1.0, jitter: float = 0.25,
-             bc: dict | None = None) -> Mesh:
-    """Seeded jittered Delaunay triangulation of an n x n lattice on [0,lx]x[0,ly].
+             bc: dict | None = None, ny: int | None = None) -> Mesh:
+    """Seeded jittered Delaunay triangulation of an n x ny lattice (ny = n by default) on
+    [0,lx]x[0,ly].
 
     Interior points move by U(-jitter, jitter)*h per axis, side points only along their side,
-    corners stay. 2(n-1)^2 triangles (Euler's formula for a convex point set with 4(n-1)
-    hull points), checked.
+    corners stay. 2(n-1)(ny-1) triangles (Euler's formula for a convex point set with
+    2(n-1) + 2(ny-1) hull points), checked.
     """
     from scipy.spatial import Delaunay
 
     rng = np.random.default_rng(seed)
-    hx, hy = lx / (n - 1), ly / (n - 1)
-    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    ny = n if ny is None else ny
+    hx, hy = lx / (n - 1), ly / (ny - 1)
+    i, j = np.meshgrid(np.arange(n), np.arange(ny), indexing="ij")
     x = i * hx
     y = j * hy
-    jx = rng.uniform(-jitter, jitter, (n, n)) * hx
-    jy = rng.uniform(-jitter, jitter, (n, n)) * hy
+    jx = rng.uniform(-jitter, jitter, (n, ny)) * hx
+    jy = rng.uniform(-jitter, jitter, (n, ny)) * hy
     jx[0, :] = 0.0
     jx[-1, :] = 0.0
     jy[:, 0] = 0.0
@@ -176,7 +178,7 @@ def tri_mesh(n: int, seed: int, lx: float = 1.0, ly: float = 1.0, jitter: float 
     pts = np.stack([x.ravel(), y.ravel()], axis=1)
     tri = Delaunay(pts)
     cells = tri.simplices.astype(np.int64)
-    if cells.shape[0] != 2 * (n - 1) ** 2 or len(tri.coplanar):
+    if cells.shape[0] != 2 * (n - 1) * (ny - 1) or len(tri.coplanar):
         raise ValueError("unexpected triangulation size")
     cells = _orient(pts, cells)
     pts, cells = _renumber(pts, cells)
@@ -355,6 +357,29 @@ def swinging_plate(n: int, jitter: float = 0.0, seed: int = 7, u0: float = 5e-4)
                       np.cos(0.5 * np.pi * p[:, 0]) * np.sin(0.5 * np.pi * p[:, 1])])
     return Problem(f"swing_n{n}", m, rho0, lam, np.full(m.n_cells, mu), v, 0.4, 0,
                    meta={"omega": omega, "u0": u0, "t_final": math.pi / omega, "amp": a})
+
+
+def be_plate(nx: int = 61, ny: int = 11, seed: int = 11, amp: float = 1.0) -> Problem:
+    """Elastic vibration of a beryllium plate (Sect. "Elastic vibration of a beryllium plate"):
+    [-0.03, 0.03] x [-0.005, 0.005] m, free boundaries, rho0 = 1845, E = 3.1827e11, nu = 0.0539,
+    v0 = (0, A omega [a1 (sinh x' + sin x') - a2 (cosh x' + cos x')]), x' = alpha (x + L/2),
+    alpha = 78.834, A = 4.3369e-5 (times amp), omega = 2.3597e5, a1 = 56.6368, a2 = 57.6455
+    (the first free-free bending mode of an Euler-Bernoulli plate); t_final = 3e-5; a jittered
+    nx x ny lattice (the paper uses 5,344 GMSH triangles). CFL 0.4."""
+    L, H = 0.06, 0.01
+    rho0, E, nu = 1845.0, 3.1827e11, 0.0539
+    mu = E / (2 * (1 + nu))
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    m = tri_mesh(nx, seed, L, H, ny=ny)
+    m.x[0] -= 0.5 * L
+    m.x[1] -= 0.5 * H
+    p = cell_points(m)
+    alpha, A, omega, a1, a2 = 78.834, 4.3369e-5 * amp, 2.3597e5, 56.6368, 57.6455
+    xp = alpha * (p[:, 0] + 0.5 * L)
+    vy = A * omega * (a1 * (np.sinh(xp) + np.sin(xp)) - a2 * (np.cosh(xp) + np.cos(xp)))
+    return Problem(f"be_plate_{nx}x{ny}", m, rho0, lam, np.full(m.n_cells, mu), np.stack([np.zeros_like(vy), vy]),
+                   0.4, 0, meta={"L": L, "H": H, "E": E, "nu": nu, "omega": omega, "alpha": alpha,
+                                 "t_final": 3e-5})
 
 
 def _batch_instance(args) -> Problem:
