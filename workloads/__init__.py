@@ -382,6 +382,31 @@ def be_plate(nx: int = 61, ny: int = 11, seed: int = 11, amp: float = 1.0) -> Pr
                                  "t_final": 3e-5})
 
 
+def blake3d(nr: int = 100, nlat: int = 2, aperture_deg: float = 4.0, seed: int = 12) -> Problem:
+    """Blake's problem (Sect. "Blake's problem"): a shell 0.1 m <= r <= 1 m, rho0 = 3000,
+    E = 62.5e9, nu = 0.25, at rest, the inner face driven by a pressure 1e6 Pa from t = 0, the
+    outer face free; t_final = 1.6e-4 (the front then reaches r = 0.9). As in the paper, a
+    needle of the shell stands in for it, its lateral faces slip walls (planes through the
+    centre: symmetry planes of the radial solution): the jittered Kuhn lattice of the unit cube
+    (nr radial x nlat x nlat cubes) mapped by (xi, eta, zeta) -> r(xi) d(eta, zeta), r = 0.1 +
+    0.9 xi, d the unit vector along (1, tan(A (eta - 1/2)), tan(A (zeta - 1/2))), A the aperture
+    (the paper's is 1 degree; any aperture gives the same radial solution), so that each
+    lateral face lies in one plane through the centre. CFL 0.25."""
+    r_in, r_out, p0 = 0.1, 1.0, 1.0e6
+    rho0, E, nu = 3000.0, 62.5e9, 0.25
+    mu = E / (2 * (1 + nu))
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    m = tet_mesh(nr, nlat, nlat, seed, bc={"x0": PRESSURE, "y0": SLIP, "y1": SLIP, "z0": SLIP, "z1": SLIP})
+    A = math.radians(aperture_deg)
+    xi, eta, zeta = m.x
+    d = np.stack([np.ones_like(xi), np.tan(A * (eta - 0.5)), np.tan(A * (zeta - 0.5))])
+    d /= np.sqrt((d * d).sum(axis=0))
+    m.x = np.ascontiguousarray((r_in + (r_out - r_in) * xi) * d)
+    return Problem(f"blake3d_{nr}x{nlat}", m, rho0, lam, np.full(m.n_cells, mu), np.zeros((3, m.n_cells)), 0.25, 0,
+                   bcval=side_values(m, PRESSURE, (p0, 0.0, 0.0)),
+                   meta={"r_in": r_in, "p0": p0, "E": E, "nu": nu, "t_final": 1.6e-4})
+
+
 def _batch_instance(args) -> Problem:
     i, n, mu, amp, steps = args
     m = tri_mesh(n, 1000 + i, bc={"x0": SLIP, "x1": SLIP, "y0": SLIP, "y1": SLIP})
