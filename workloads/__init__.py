@@ -407,6 +407,26 @@ def blake3d(nr: int = 100, nlat: int = 2, aperture_deg: float = 4.0, seed: int =
                    meta={"r_in": r_in, "p0": p0, "E": E, "nu": nu, "t_final": 1.6e-4})
 
 
+def swinging_cube(n: int, jitter: float = 0.1, seed: int = 13, u0: float = 5e-4) -> Problem:
+    """A 3D counterpart of the swinging plate (Sect. "2D swinging plate"): [0,2]^3, slip walls,
+    rho0 = 1100, E = 1.7e7, nu = 0.45, v(x,0) = omega U0 (sin(k x) cos(k y) cos(k z),
+    -cos(k x) sin(k y) cos(k z), 0), k = pi/2: a divergence-free standing shear wave whose normal
+    velocity and shear tractions vanish on the walls, omega = k sqrt(3 mu / rho0)."""
+    E, nu, rho0 = 1.7e7, 0.45, 1100.0
+    mu = E / (2 * (1 + nu))
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    k = 0.5 * math.pi
+    omega = k * math.sqrt(3.0 * mu / rho0)
+    m = tet_mesh(n, n, n, seed, 2.0, 2.0, 2.0, jitter=jitter,
+                 bc={s: SLIP for s in ("x0", "x1", "y0", "y1", "z0", "z1")})
+    p = cell_points(m)
+    a = omega * u0
+    s, c = np.sin(k * p), np.cos(k * p)
+    v = a * np.stack([s[:, 0] * c[:, 1] * c[:, 2], -c[:, 0] * s[:, 1] * c[:, 2], np.zeros(len(p))])
+    return Problem(f"swing_cube_n{n}", m, rho0, lam, np.full(m.n_cells, mu), v, 0.25, 0,
+                   meta={"omega": omega, "u0": u0, "t_final": math.pi / omega, "amp": a, "k": k})
+
+
 def _batch_instance(args) -> Problem:
     i, n, mu, amp, steps = args
     m = tri_mesh(n, 1000 + i, bc={"x0": SLIP, "x1": SLIP, "y0": SLIP, "y1": SLIP})
