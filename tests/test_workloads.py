@@ -39,3 +39,37 @@ def test_concat_offsets():
         owner[pb.mesh.c2n[k]] = inst
     for k in range(3):
         assert np.array_equal(owner[pb.mesh.c2n[k]], inst)
+
+
+def _volumes(m):
+    x = m.x.T[m.c2n.T]  # [nc, d+1, d]
+    e = x[:, 1:] - x[:, :1]
+    return np.linalg.det(e) if m.dim == 3 else e[:, 0, 0] * e[:, 1, 1] - e[:, 0, 1] * e[:, 1, 0]
+
+
+def test_paper_problem_meshes():
+    """the beryllium plate, Blake's needle and the swinging cube: positively oriented cells
+    that fill their domains, boundary faces tagged as the problems state"""
+    be = W.be_plate(nx=13, ny=4)
+    assert be.mesh.n_cells == 2 * 12 * 3 and be.mesh.btag.size == 0  # free boundaries only
+    assert np.all(_volumes(be.mesh) > 0)
+    assert abs(_volumes(be.mesh).sum() / 2 - 0.06 * 0.01) < 1e-15
+    cube = W.swinging_cube(3)
+    assert cube.mesh.n_cells == 6 * 27 and np.all(_volumes(cube.mesh) > 0)
+    assert abs(_volumes(cube.mesh).sum() / 6 - 8.0) < 1e-12
+    assert np.all(cube.mesh.btag == W.SLIP) and cube.mesh.btag.size == 6 * 2 * 9
+    # Blake's needle: the lateral slip faces lie in planes through the centre, the pressure
+    # face on the sphere r = 0.1, the free outer face on r = 1 (not tagged)
+    bl = W.blake3d(nr=6, nlat=2)
+    m = bl.mesh
+    assert np.all(_volumes(m) > 0)
+    xf = m.x.T[m.bface.T]  # [nb, 3, 3]
+    slip = m.btag == W.SLIP
+    nrm = np.cross(xf[:, 1] - xf[:, 0], xf[:, 2] - xf[:, 0])
+    nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+    assert np.abs((nrm[slip, None, :] * xf[slip]).sum(axis=2)).max() < 1e-14  # n . x = 0
+    pr = m.btag == W.PRESSURE
+    assert pr.sum() == 2 * 2 * 2 and np.abs(np.linalg.norm(xf[pr], axis=2) - 0.1).max() < 1e-15
+    assert np.all(bl.bcval[0, pr] == 1e6) and np.all(bl.bcval[:, ~pr] == 0.0)
+    r = np.linalg.norm(m.x, axis=0)
+    assert abs(r.min() - 0.1) < 1e-15 and abs(r.max() - 1.0) < 1e-15
