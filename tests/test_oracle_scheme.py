@@ -328,6 +328,38 @@ def test_parachute_first_order_has_no_troubled_cells(orc):
     assert o.info.n_troubled == 0 and o.info.n_p0 == pb.mesh.n_cells
 
 
+def test_parachute_failure_leaves_the_state(orc):
+    """a cell whose first-order candidate cannot be computed (Sect. "Limiting: a posteriori MOOD
+    loop": the parachute scheme must produce an admissible state): a NaN velocity, or an
+    inverted F (det F < 0) that the first-order update keeps inverted; the step reports the
+    parachute failure and leaves the state and the time as they were, and the oracle stays
+    usable: from the clean state it steps as a fresh run does"""
+    pb = W.plain2d(n=12)
+    clean = orc.Oracle(pb)
+    clean.step(2)
+    s0, t0, dt0 = clean.state(), clean.t, clean.dt
+    clean.step()
+    ref = clean.state()
+    for field, bad in (("v", lambda a: a.__setitem__((0, 5), np.nan)),
+                       ("F", lambda a: a.__setitem__((slice(0, 1), 7), -a[0, 7]))):
+        o = orc.Oracle(pb)
+        o.step(2)
+        arr = o.state()[field].copy()
+        bad(arr)
+        o.set_state(**{field: arr})
+        before = o.state()
+        rc = o.step(check=False)
+        assert orc.ERR[rc] == "parachute failure" and o.info.n_parachute >= 1, (field, rc)
+        after = o.state()
+        for k in before:
+            assert np.array_equal(after[k], before[k], equal_nan=True), (field, k)
+        assert o.t == t0
+        o.set_state(x=s0["x"], vp=s0["vp"], v=s0["v"], e=s0["e"], F=s0["F"], dt=dt0)
+        o.step()
+        for k in ref:
+            assert np.array_equal(o.state()[k], ref[k]), (field, k)
+
+
 # ----------------------------------------------------------------------------- time step
 def test_dt_rules(orc):
     """dt^0 = C_CFL min L_c/a_c with a = sqrt((lambda + 2 mu)/rho0) at rest (Eq. CFL2);
