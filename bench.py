@@ -239,6 +239,8 @@ def reference_steps(pb, steps: int, warmup: int) -> dict:
     state (x, v_p, v, e, F, dt) restored before every step. Consecutive steps are not taken:
     from the column's second step on MOOD cascades start, and the oracle recomputes the whole
     mesh for each of their rounds (minutes of host time per step)."""
+    if steps < 1 or warmup < 0:
+        raise ValueError("the reference arm needs --steps >= 1 and --warmup >= 0")
     import oracle as O
     O.build()
     t0 = time.perf_counter()
