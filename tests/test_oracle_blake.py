@@ -16,9 +16,10 @@ with wd = w0 sqrt(1 - zeta^2): the front tau = 0 carries the jump v_r = p0 a / (
 The needle of the shell (`workloads.blake3d`) has slip walls on its lateral planes through the
 centre, the pressure on its inner face and a free outer face; the oracle runs the paper's
 scheme (P1 -> P0 MOOD cascade) to t = 1.6e-4, when the front reaches r = 0.9. Its radial
-velocity must approach the exact one as the mesh is refined: behind the front, away from the
-first cells at the loaded face (where the paper also sees perturbations), and over all cells
-with the front smeared over a few cells; the front must stand where c puts it."""
+velocity, pressure and radial deviatoric stress (the paper's figures plot the last two) must
+approach the exact ones as the mesh is refined: behind the front, away from the first cells at
+the loaded face (where the paper also sees perturbations), and over all cells with the front
+smeared over a few cells; the front must stand where c puts it."""
 import math
 
 import numpy as np
@@ -92,7 +93,9 @@ def test_exact_solution_meets_its_equations():
     assert vout == 0.0 and vin == pytest.approx(p0 * a / (rho * c * rf), rel=1e-6)
 
 
-def _radial_velocity(orc, pb):
+def _radial_fields(orc, pb, mu, K):
+    """radius, radial velocity, pressure -tr(T)/3 and radial deviatoric stress r.T.r + p of each
+    cell after the run (T from the cell's F by the oracle's stress)"""
     o = orc.Oracle(pb)
     tf = pb.meta["t_final"]
     while o.t < tf:
@@ -101,9 +104,16 @@ def _radial_velocity(orc, pb):
     xc = x[:, pb.mesh.c2n].mean(axis=1)
     r = np.sqrt((xc * xc).sum(axis=0))
     vr = (o.get(orc.F_V) * xc).sum(axis=0) / r
+    F = o.get(orc.F_F)
+    p, srr = np.empty(r.size), np.empty(r.size)
+    for c in range(r.size):
+        T = orc.stress(F[:, c].reshape(3, 3), mu, K)
+        p[c] = -np.trace(T) / 3.0
+        rh = xc[:, c] / r[c]
+        srr[c] = rh @ T @ rh + p[c]
     t = o.t
     o.close()
-    return r, vr, t
+    return r, vr, p, srr, t
 
 
 def _front(r, vr, nr, a=0.1, b=1.0):
@@ -124,19 +134,34 @@ def test_oracle_converges_to_blakes_solution(orc):
     m = W.blake3d(nr=4).meta
     a, p0 = m["r_in"], m["p0"]
     rho, E, nu = 3000.0, m["E"], m["nu"]
-    c = math.sqrt(E * (1 - nu) / ((1 + nu) * (1 - 2 * nu)) / rho)
-    smooth, whole, front_err = [], [], []
+    mu = E / (2 * (1 + nu))
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    K = lam + 2 * mu / 3
+    c = math.sqrt((lam + 2 * mu) / rho)
+    err = {k: [] for k in ("v_smooth", "v_whole", "front", "p_smooth", "p_whole", "s_smooth", "s_whole")}
     for nr in (50, 100):
-        r, vr, t = _radial_velocity(orc, W.blake3d(nr=nr))
-        _, ve, _ = blake_exact(r, t, a, p0, rho, E, nu)
+        r, vr, p, srr, t = _radial_fields(orc, W.blake3d(nr=nr), mu, K)
+        ue, ve, pe = blake_exact(r, t, a, p0, rho, E, nu)
+        h = 1e-6
+        dudr = (blake_exact(r + h, t, a, p0, rho, E, nu)[0] - blake_exact(r - h, t, a, p0, rho, E, nu)[0]) / (2 * h)
+        se = (lam + 2 * mu) * dudr + 2 * lam * ue / r + pe  # sigma_rr + p
         front = a + c * t
-        vmax = p0 * a / (rho * c * front)  # the jump at the front, the largest |v_r|
+        vmax = p0 * a / (rho * c * front)  # the jump of v_r at the front, the largest |v_r|
+        smax = p0 * a / front  # the jump of sigma_rr at the front
         behind = (r > 1.5 * a) & (r < front - 0.1)
-        smooth.append(np.abs(vr - ve)[behind].mean() / vmax)
-        whole.append(np.abs(vr - ve).mean() / vmax)
-        front_err.append(abs(_front(r, vr, nr) - front))
-    # 1,200 and 2,400 tetrahedra: radial cells of 0.018 and 0.009 (measured: smooth 1.8 % and
-    # 0.63 % of the jump, whole mesh 8.2 % and 3.4 %, front 0.027 and 0.014 ahead of a + c t)
-    assert smooth[1] < 0.01 and smooth[0] / smooth[1] > 2.0
-    assert whole[1] < 0.05 and whole[0] / whole[1] > 1.8
-    assert front_err[1] < 0.025 and front_err[1] < 0.7 * front_err[0]
+        err["v_smooth"].append(np.abs(vr - ve)[behind].mean() / vmax)
+        err["v_whole"].append(np.abs(vr - ve).mean() / vmax)
+        err["front"].append(abs(_front(r, vr, nr) - front))
+        err["p_smooth"].append(np.abs(p - pe)[behind].mean() / smax)
+        err["p_whole"].append(np.abs(p - pe).mean() / smax)
+        err["s_smooth"].append(np.abs(srr - se)[behind].mean() / smax)
+        err["s_whole"].append(np.abs(srr - se).mean() / smax)
+    # 1,200 and 2,400 tetrahedra: radial cells of 0.018 and 0.009. Measured: v_r 1.8 % and 0.63 %
+    # of its jump behind the front, 8.2 % and 3.4 % over all cells; the front 0.027 and 0.014
+    # ahead of a + c t; p 2.8 % and 1.4 %, 7.4 % and 4.0 %, and the radial deviatoric stress
+    # 1.2 % and 0.45 %, 3.7 % and 1.9 % of the jump of sigma_rr
+    bars = {"v_smooth": (0.01, 2.0), "v_whole": (0.05, 1.8), "p_smooth": (0.02, 1.7), "p_whole": (0.06, 1.6),
+            "s_smooth": (0.01, 2.0), "s_whole": (0.03, 1.7)}
+    for k, (bar, ratio) in bars.items():
+        assert err[k][1] < bar and err[k][0] / err[k][1] > ratio, (k, err[k])
+    assert err["front"][1] < 0.025 and err["front"][1] < 0.7 * err["front"][0], err["front"]
